@@ -1,0 +1,357 @@
+#!/usr/bin/env python3
+"""Benchmark of the forest hot path on the 111,000-row AIWC-shaped workload.
+
+One step = fit a 500-tree forest (presort/rank, Philox bootstrap, breadth-first growth, pack)
+on 111,000 rows x 32 features, predict 1,000,000 queries, and select the fastest of 15
+devices for 64 kernels. Inputs are resident in device memory when the timed region starts;
+L2 is flushed between steps. Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (oracle/, plain C, trees spread over the host cores) on
+a bounded sample of the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1811_00156_gb300 import synth  # noqa: E402
+
+ROWS_TREES_UNIT = "rows·trees/s"
+METRIC = "fit rows·trees/s (bit-exact forest) + predict queries/s"
+T_TREES, MTRY, MIN_NODE = 500, 10, 5
+N_QUERIES = 1_000_000
+SEL_KERNELS, SEL_DEVICES = 64, 15
+WORKLOAD = ("aiwc-111000: fit 500 trees (mtry 10, min_node 5, bootstrap) on 111,000 rows x 32 "
+            "features + predict 1,000,000 queries + select device for 64 kernels x 15 devices")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+# ------------------------------------------------------------------------------ clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.path = os.path.join(tempfile.gettempdir(), f"aiwcrf_clocks_{os.getpid()}.csv")
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------ oracle timing
+def oracle_fit_sample(wl, n_trees: int, threads: int, first: int = 0):
+    """Oracle as it stands, one tree per task, tasks spread over `threads` host threads."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(threads) as ex:
+        list(ex.map(lambda t: oracle.fit(wl.X, wl.y, T_TREES, MTRY, MIN_NODE, seed=synth.FOREST_SEED,
+                                         t0=t, t1=t + 1), range(first, first + n_trees)))
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(wl):
+    cores = os.cpu_count() or 1
+    n_trees = max(8, 8 * cores)
+    secs = oracle_fit_sample(wl, n_trees, cores)
+    return {"value": wl.n_rows * n_trees / secs, "unit": ROWS_TREES_UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_trees} of the 500 trees on all 111,000 rows ({secs:.1f} s wall, "
+                      f"one tree per thread task)"}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    wl = synth.scaled_forest_workload()
+    cores = os.cpu_count() or 1
+    per_step = max(2, cores)
+    for w in range(args.warmup):
+        oracle_fit_sample(wl, min(per_step, 2), cores, first=w)
+    times = []
+    for k in range(args.steps):
+        times.append(oracle_fit_sample(wl, per_step, cores, first=(k * per_step) % T_TREES))
+    tot = sum(times)
+    value = wl.n_rows * per_step * args.steps / tot
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": ROWS_TREES_UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "rows": wl.n_rows, "features": 32,
+                                           "trees": T_TREES, "sample_trees_per_step": per_step},
+           "cpu_baseline": {"value": value, "unit": ROWS_TREES_UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{per_step} trees per step on all 111,000 rows, one tree per thread task"},
+           "e2e": {"value": value, "unit": ROWS_TREES_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ------------------------------------------------------------------------------ ours
+def source_sha():
+    h = hashlib.sha256()
+    for f in ("fit.cu", "predict.cu", "internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1811_00156_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel: str, sha: str):
+    """Per-launch DRAM traffic of `kernel` from the committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(kernel)
+    if not e or e.get("source_sha") != sha:
+        return None
+    return e.get("bytes_per_launch")
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl")
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1811_00156_gb300 import aiwcrf as A
+    A.load()
+
+    dev = torch.device("cuda", local_rank)
+    wl = synth.scaled_forest_workload()
+    N, F = wl.n_rows, wl.n_features
+    Xq_h = synth.queries(N_QUERIES)
+    kfeat_h = np.ascontiguousarray(synth.queries(SEL_KERNELS, seed=99)[:30])
+    X = torch.from_numpy(wl.X).to(dev)
+    y = torch.from_numpy(wl.y).to(dev)
+    Xq = torch.from_numpy(Xq_h).to(dev)
+    kfeat = torch.from_numpy(kfeat_h).to(dev)
+    psum = torch.empty(N_QUERIES, dtype=torch.int64, device=dev)
+    pred = torch.empty(N_QUERIES, dtype=torch.int64, device=dev)
+    best = torch.empty(SEL_KERNELS, dtype=torch.int32, device=dev)
+    selp = torch.empty(SEL_KERNELS * SEL_DEVICES, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    devices = list(range(SEL_DEVICES))
+    T_total = T_TREES * world
+    params = A.params(T_TREES, MTRY, MIN_NODE, seed=synth.FOREST_SEED, first_tree=rank * T_TREES)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev: ev[0].record(stream)
+        forest = A.aiwcrf_fit(params, X, y)
+        if ev: ev[1].record(stream)
+        if world == 1:
+            A.aiwcrf_predict(forest, Xq, pred)
+        else:
+            A.aiwcrf_predict_sum(forest, Xq, psum)
+            dist.all_reduce(psum)
+            A.aiwcrf_round_mean(psum, T_total, pred)
+        if ev: ev[2].record(stream)
+        A.aiwcrf_select_device(forest, kfeat, 2, devices, best, selp)
+        if ev: ev[3].record(stream)
+        return forest
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local_rank)
+    clocks.start()
+    A.aiwcrf_profile_enable(True)
+    A.aiwcrf_profile_read()
+    launches0 = A.aiwcrf_launch_count()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    stats = None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))                      # write 256 MB (> L2) between steps
+        f = step(evs[k])
+        stats = f.stats()
+        del f
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = A.aiwcrf_launch_count() - launches0
+    prof = A.aiwcrf_profile_read()
+    A.aiwcrf_profile_enable(False)
+    clk = clocks.stop()
+
+    fit_ms = sum(e[0].elapsed_time(e[1]) for e in evs)
+    pred_ms = sum(e[1].elapsed_time(e[2]) for e in evs)
+    sel_ms = sum(e[2].elapsed_time(e[3]) for e in evs)
+    step_ms = sum(e[0].elapsed_time(e[3]) for e in evs)
+    t = torch.tensor([fit_ms, pred_ms, sel_ms, step_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    fit_ms, pred_ms, sel_ms, step_ms = t.tolist()
+    K = args.steps
+    value = N * T_TREES * world * K / (fit_ms / 1e3)
+
+    # roofline of the dominant kernel class, from the events recorded around each launch
+    peak, peak_kind = measured_peaks()
+    big_rows = stats["rows_evaluated"] - stats["rows_evaluated_small"]
+    big_part = stats["rows_partitioned"] - stats["rows_partitioned_small"]
+    per_eval = 4 + 8 + 2 * MTRY                   # row entry + target + mtry ranks
+    per_part = 4 + 2 + 4                          # row entry + chosen rank, entry written
+    alg = {
+        "level_big": K * (big_rows * per_eval + big_part * per_part),
+        "level_small": K * (stats["rows_evaluated_small"] * per_eval + stats["rows_partitioned_small"] * per_part),
+        "predict": K * N_QUERIES * (F * 4 + 8),
+    }
+    sha = source_sha()
+    kernels = {}
+    for name, (n_launch, ms) in prof.items():
+        if n_launch == 0:
+            continue
+        entry = {"launches": n_launch, "total_ms": ms, "share": None}
+        if name in alg and ms > 0:
+            entry["alg_bytes"] = alg[name]
+            entry["achieved_gbs"] = alg[name] / (ms / 1e3) / 1e9
+        kernels[name] = entry
+    tot_ms = sum(v["total_ms"] for v in kernels.values()) or 1.0
+    for v in kernels.values():
+        v["share"] = v["total_ms"] / tot_ms
+    dom = max((k for k in kernels if k in ("level_big", "level_small")), key=lambda k: kernels[k]["total_ms"])
+    d = kernels[dom]
+    n_l = d["launches"]
+    traffic = ncu_traffic(dom, sha)
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": d["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                "frac": d["achieved_gbs"] / peak, "peak_source": f"hbm_gbs of {peak_kind} peaks",
+                "traffic": traffic, "alg_bytes_per_launch": d["alg_bytes"] / n_l,
+                "ms_per_launch": d["total_ms"] / n_l}
+
+    out = {"metric": METRIC, "value": value, "unit": ROWS_TREES_UNIT, "n_gpus": world, "steps": K,
+           "warmup": args.warmup, "ms_per_step": step_ms / K, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "rows": N, "features": F, "trees_per_gpu": T_TREES,
+                      "queries": N_QUERIES, "select": f"{SEL_KERNELS}x{SEL_DEVICES}",
+                      "seeds": {"data": synth.DATA_SEED, "forest": synth.FOREST_SEED, "queries": synth.QUERY_SEED},
+                      "l2": "flushed between steps (256 MB write); fit working set and queries exceed L2",
+                      "parallelism": f"tree-sharded x{world}" if world > 1 else "1 GPU"},
+           "predict": {"value": N_QUERIES * K / (pred_ms / 1e3), "unit": "queries/s", "ms": pred_ms / K,
+                       "trees": T_total},
+           "select": {"ms": sel_ms / K, "kernels": SEL_KERNELS, "devices": SEL_DEVICES},
+           "fit_ms": fit_ms / K, "fit_stats": stats, "roofline": roofline, "kernels": kernels,
+           "gpu_launches": launches, "clocks": clk, "parity": "bit-exact vs oracle (tests/test_gpu_parity.py)"}
+
+    if not args.no_e2e:
+        out["e2e"] = e2e(A, wl, Xq_h, kfeat_h, params, devices, world, dev, max(1, min(K, 3)))
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def e2e(A, wl, Xq_h, kfeat_h, params, devices, world, dev, steps):
+    """The same step through the C ABI with pinned HOST buffers: the library copies inputs in
+    and results out inside the timed region."""
+    import torch
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()        # noqa: E731
+    X, y, Xq, kf = pin(wl.X), pin(wl.y), pin(Xq_h), pin(kfeat_h)
+    pred = torch.empty(Xq.shape[1], dtype=torch.int64).pin_memory().numpy()
+    best = torch.empty(kf.shape[1], dtype=torch.int32).pin_memory().numpy()
+    selp = torch.empty(kf.shape[1] * len(devices), dtype=torch.int64).pin_memory().numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        f = A.aiwcrf_fit(params, X, y)
+        A.aiwcrf_predict(f, Xq, pred)
+        A.aiwcrf_select_device(f, kf, 2, devices, best, selp)
+        del f
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    h2d = X.nbytes + y.nbytes + Xq.nbytes + kf.nbytes + 4 * len(devices)
+    d2h = pred.nbytes + best.nbytes + selp.nbytes
+    return {"value": wl.n_rows * params.num_trees * world * steps / secs, "unit": ROWS_TREES_UNIT,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * secs / steps,
+            "steps": steps, "note": "host clock around fit + predict + select with pinned host arrays"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * aiwcrf.h -- C ABI of the GB300 random-forest library for AIWC performance prediction.
+ *
+ * The method (arXiv 1811.00156): architecture-independent AIWC features of an OpenCL kernel,
+ * plus a device id and a problem-size class, are the predictors of a random-forest regression
+ * (Sec. III-B: ranger, num.trees / mtry / min.node.size) whose response is the kernel's
+ * execution time, here log10 seconds in Q32.32 fixed point. The fitted model is queried to
+ * predict times (Sec. I: "querying the model is computationally inexpensive"; Sec. V) and to
+ * pick the fastest device for a kernel (Sec. VI).
+ *
+ * Conventions for every call:
+ *  - Return 0 (AIWCRF_OK) on success, a negative AIWCRF_E_* code on failure; the failing call's
+ *    message is available from aiwcrf_last_error() on the same host thread.
+ *  - Array arguments may be host or device pointers; the library checks each one. Host inputs
+ *    are copied to the device on the given stream; host outputs are written back and the call
+ *    synchronises the stream before returning. With device outputs the call is stream-ordered
+ *    and the results are valid once the stream reaches that point.
+ *  - The caller owns every array it passes. The library owns each aiwcrf_forest until
+ *    aiwcrf_forest_free().
+ *  - cuda_stream is a cudaStream_t (NULL = the legacy default stream). The device is the
+ *    current CUDA device of the calling thread.
+ *  - Matrices are column-major float32: element (feature f, row r) of an F x N matrix is at
+ *    [f * N + r].
+ *  - Targets, leaf values and predictions are int64 Q32.32 (value * 2^32).
+ *  - There is no CPU fallback: without a usable CUDA device every call fails with
+ *    AIWCRF_E_CUDA.
+ */
+#ifndef AIWCRF_H
+#define AIWCRF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AIWCRF_OK               0
+#define AIWCRF_E_INVALID_ARG   -1   /* null pointer, size or parameter out of range */
+#define AIWCRF_E_NAN_INPUT     -2   /* NaN in the training features */
+#define AIWCRF_E_BAD_POINTER   -3   /* pointer is neither host memory nor memory of this device */
+#define AIWCRF_E_OOM           -4   /* device allocation failed */
+#define AIWCRF_E_CUDA          -5   /* a CUDA runtime call or kernel launch failed */
+#define AIWCRF_E_TIMEOUT       -6   /* a bounded device-side wait gave up */
+#define AIWCRF_E_CORRUPT       -7   /* serialized forest failed validation */
+#define AIWCRF_E_LIMIT         -8   /* a documented size limit was exceeded (see below) */
+
+/* Size limits (checked; AIWCRF_E_LIMIT or AIWCRF_E_INVALID_ARG when exceeded):
+ *   n_rows <= 4,194,303 (2^22 - 1); |y| <= 2^40 (|log10 t| < 256);
+ *   n_features <= 128; each feature column has at most 65,536 distinct values;
+ *   num_trees <= 1,048,576; a bootstrap multiplicity above 255 (probability ~ 1e-500) fails. */
+#define AIWCRF_MAX_ROWS       ((1 << 22) - 1)
+#define AIWCRF_MAX_FEATURES   128
+#define AIWCRF_MAX_ABS_Y      (1LL << 40)
+#define AIWCRF_MAX_TREES      (1 << 20)
+
+typedef struct aiwcrf_forest aiwcrf_forest;   /* opaque, owned by the library */
+
+/* Fit parameters: the three ranger parameters the paper tunes (Sec. III-B: num.trees, mtry,
+ * min.node.size) plus depth limit, seed and bootstrap switch. */
+typedef struct {
+    int32_t num_trees;      /* >= 1 */
+    int32_t mtry;           /* features tried per node, >= 1 (values above n_features try all) */
+    int32_t min_node_size;  /* >= 1; a node with sum of multiplicities <= this is a leaf */
+    int32_t max_depth;      /* 0 = unlimited; else nodes at this depth are leaves */
+    uint64_t seed;          /* Philox4x32-10 key */
+    int32_t bootstrap;      /* 1: n_rows draws with replacement per tree; 0: every row once */
+    int32_t reserved;       /* must be 0 */
+    int64_t first_tree;     /* global index of this forest's tree 0 (for tree-sharded fits;
+                               tree t uses random counters of tree first_tree + t). >= 0 */
+} aiwcrf_fit_params;
+
+/* Per-fit counters, for byte accounting and tests. */
+typedef struct {
+    int64_t num_trees;
+    int64_t total_nodes;
+    int64_t levels;              /* depth of the deepest tree + 1 */
+    int64_t rows_evaluated;      /* sum over searched nodes of their distinct in-bag rows */
+    int64_t rows_partitioned;    /* sum over split nodes of their distinct in-bag rows */
+    int64_t nodes_evaluated;     /* nodes whose split was searched */
+    int64_t nodes_small;         /* of those, searched by one warp (<= 32 distinct rows) */
+    int64_t rows_evaluated_small;    /* rows_evaluated of the warp-searched nodes */
+    int64_t rows_partitioned_small;  /* rows_partitioned of the warp-searched nodes */
+    int32_t n_features;
+    int32_t mtry;
+} aiwcrf_fit_stats;
+
+/* Fit a forest (Sec. III-B). X: F x N column-major float32 (no NaN); y: N int64 Q32.32.
+ * Presorts and ranks every column once, draws each tree's bootstrap and per-node mtry
+ * features with Philox4x32-10, grows all trees breadth first with an exact integer split
+ * search (maximise S_L^2/n_L + S_R^2/n_R; ties: lowest feature, then lowest threshold; split
+ * only with a strict gain), and packs the trees. On success *out receives a new forest. */
+int aiwcrf_fit(const aiwcrf_fit_params *params, const float *X, const int64_t *y,
+               int64_t n_rows, int32_t n_features, void *cuda_stream, aiwcrf_forest **out);
+
+/* Batched fit of n_subsets forests on row subsets of one matrix, grown together (the
+ * leave-one-kernel-out experiment of Alg. 1 / Table III trains one forest per omitted kernel).
+ * Subset g is subset_rows[subset_offsets[g] .. subset_offsets[g+1]) (host int64 offsets,
+ * n_subsets + 1 of them; rows strictly increasing, host or device int32). Forest g equals
+ * aiwcrf_fit with the same params on the matrix of those rows. out: n_subsets handles. */
+int aiwcrf_fit_subsets(const aiwcrf_fit_params *params, const float *X, const int64_t *y,
+                       int64_t n_rows, int32_t n_features, const int64_t *subset_offsets,
+                       const int32_t *subset_rows, int32_t n_subsets, void *cuda_stream,
+                       aiwcrf_forest **out);
+
+/* Predict (Sec. I, Sec. V). Xq: F x Q column-major float32. out_pred[q] = floor((2P + T)/(2T))
+ * with P the exact sum of the T leaf values reached (x <= threshold goes left; a NaN feature
+ * goes right). out_var (or NULL): per query two uint64 words (low, high) of the exact
+ * unsigned 128-bit V = T * sum(v^2) - P^2 (T^2 times the ensemble variance). */
+int aiwcrf_predict(const aiwcrf_forest *forest, const float *Xq, int64_t n_queries,
+                   int64_t *out_pred, uint64_t *out_var, void *cuda_stream);
+
+/* Raw per-query sums P over this forest's trees (for forests split across processes by
+ * tree: add the shards' sums, then aiwcrf_round_mean with the total tree count). */
+int aiwcrf_predict_sum(const aiwcrf_forest *forest, const float *Xq, int64_t n_queries,
+                       int64_t *out_sum, void *cuda_stream);
+
+/* out[q] = floor((2 sums[q] + total_trees) / (2 total_trees)). */
+int aiwcrf_round_mean(const int64_t *sums, int64_t n, int64_t total_trees, int64_t *out,
+                      void *cuda_stream);
+
+/* Device selection (Sec. VI: which device runs a kernel fastest). kfeat: (F-2) x K
+ * column-major kernel features; query (k, j) is kfeat[:, k] with device_ids[j] and
+ * size_class appended as the last two features. out_best[k] = the device id with the
+ * smallest prediction (ties: lower device id). out_pred (or NULL): K x D row-major
+ * predictions. device_ids: host array of D ids. */
+int aiwcrf_select_device(const aiwcrf_forest *forest, const float *kfeat, int32_t n_kernels,
+                         int32_t size_class, const int32_t *device_ids, int32_t n_devices,
+                         int32_t *out_best, int64_t *out_pred, void *cuda_stream);
+
+/* Counters of the fit that produced the forest (zeros for a deserialized forest). */
+int aiwcrf_forest_stats(const aiwcrf_forest *forest, aiwcrf_fit_stats *out);
+
+/* Number of trees, packed nodes (including alignment padding) and features. */
+int aiwcrf_forest_info(const aiwcrf_forest *forest, int64_t *num_trees, int64_t *num_nodes,
+                       int32_t *n_features);
+
+/* Versioned little-endian blob of the packed forest, into a host buffer. With buf == NULL or
+ * cap too small, *needed receives the size and AIWCRF_E_INVALID_ARG is returned for a short
+ * non-NULL buffer. Layout: "AIWCRF01", u32 version (1), u32 n_features, i64 num_trees,
+ * i64 num_nodes, i64 tree_offset[num_trees + 1], u64 node[num_nodes]. Node encoding: bit 63
+ * set = leaf with value bits 0..62 (sign-extended); else bits 0..31 threshold (float32),
+ * bits 32..55 left-child index within the tree (right = left + 1), bits 56..62 feature.
+ * Trees are padded to an even node count with one unreachable leaf of value 0. */
+int aiwcrf_forest_serialize(const aiwcrf_forest *forest, void *buf, size_t cap, size_t *needed);
+
+/* Rebuild a forest on the current device from a blob (validated: AIWCRF_E_CORRUPT). */
+int aiwcrf_forest_deserialize(const void *buf, size_t len, aiwcrf_forest **out);
+
+int aiwcrf_forest_free(aiwcrf_forest *forest);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *aiwcrf_last_error(void);
+
+/* Optional per-kernel timing with CUDA events recorded on the launching stream around each
+ * library kernel launch. Off by default. aiwcrf_profile_read synchronises the events and
+ * returns, per kernel class k < n (names via aiwcrf_profile_name), the launch count and the
+ * summed duration in milliseconds; it then clears the record. */
+int aiwcrf_profile_enable(int32_t on);
+int aiwcrf_profile_read(int32_t n, int64_t *launches, double *total_ms);
+const char *aiwcrf_profile_name(int32_t k);
+int32_t aiwcrf_profile_num_classes(void);
+
+/* Number of CUDA kernels this library has launched in this process (all devices). */
+int64_t aiwcrf_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AIWCRF_H */

@@ -265,8 +265,8 @@ static int64_t push_node(otree *tr)
     return tr->count++;
 }
 
-/* sort context for qsort (single threaded per call) */
-static const float *g_col;
+/* sort context for qsort: one per host thread, so trees may be grown on several threads */
+static _Thread_local const float *g_col;
 static int cmp_rows_by_value(const void *pa, const void *pb)
 {
     int64_t a = *(const int64_t *)pa, b = *(const int64_t *)pb;

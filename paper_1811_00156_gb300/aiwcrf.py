@@ -1,0 +1,240 @@
+"""Thin ctypes binding of libaiwcrf.so (include/aiwcrf.h). Argument marshalling only: every
+step of fit, predict and device selection runs in the library's CUDA kernels.
+
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays. CUDA tensors are passed by device
+pointer on torch's current stream; host arrays are staged by the library itself.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libaiwcrf.so")
+
+AIWCRF_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "NAN_INPUT", -3: "BAD_POINTER", -4: "OOM", -5: "CUDA",
+          -6: "TIMEOUT", -7: "CORRUPT", -8: "LIMIT"}
+
+
+class AiwcrfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class FitParams(C.Structure):
+    _fields_ = [("num_trees", C.c_int32), ("mtry", C.c_int32), ("min_node_size", C.c_int32),
+                ("max_depth", C.c_int32), ("seed", C.c_uint64), ("bootstrap", C.c_int32),
+                ("reserved", C.c_int32), ("first_tree", C.c_int64)]
+
+
+class FitStats(C.Structure):
+    _fields_ = [("num_trees", C.c_int64), ("total_nodes", C.c_int64), ("levels", C.c_int64),
+                ("rows_evaluated", C.c_int64), ("rows_partitioned", C.c_int64),
+                ("nodes_evaluated", C.c_int64), ("nodes_small", C.c_int64),
+                ("rows_evaluated_small", C.c_int64), ("rows_partitioned_small", C.c_int64),
+                ("n_features", C.c_int32), ("mtry", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ["aiwcrf_fit", "aiwcrf_fit_subsets", "aiwcrf_predict", "aiwcrf_predict_sum",
+           "aiwcrf_round_mean", "aiwcrf_select_device", "aiwcrf_forest_stats", "aiwcrf_forest_info",
+           "aiwcrf_forest_serialize", "aiwcrf_forest_deserialize", "aiwcrf_forest_free",
+           "aiwcrf_last_error", "aiwcrf_profile_enable", "aiwcrf_profile_read",
+           "aiwcrf_profile_name", "aiwcrf_profile_num_classes", "aiwcrf_launch_count"]
+
+_lib = None
+_lock = threading.Lock()
+_vp = C.c_void_p
+
+
+def load():
+    """Load the library. Raises if it has not been built: there is no fallback."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        L.aiwcrf_fit.argtypes = [C.POINTER(FitParams), _vp, _vp, C.c_int64, C.c_int32, _vp, C.POINTER(_vp)]
+        L.aiwcrf_fit_subsets.argtypes = [C.POINTER(FitParams), _vp, _vp, C.c_int64, C.c_int32, _vp, _vp,
+                                         C.c_int32, _vp, C.POINTER(_vp)]
+        L.aiwcrf_predict.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp]
+        L.aiwcrf_predict_sum.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
+        L.aiwcrf_round_mean.argtypes = [_vp, C.c_int64, C.c_int64, _vp, _vp]
+        L.aiwcrf_select_device.argtypes = [_vp, _vp, C.c_int32, C.c_int32, _vp, C.c_int32, _vp, _vp, _vp]
+        L.aiwcrf_forest_stats.argtypes = [_vp, C.POINTER(FitStats)]
+        L.aiwcrf_forest_info.argtypes = [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
+        L.aiwcrf_forest_serialize.argtypes = [_vp, _vp, C.c_size_t, C.POINTER(C.c_size_t)]
+        L.aiwcrf_forest_deserialize.argtypes = [_vp, C.c_size_t, C.POINTER(_vp)]
+        L.aiwcrf_forest_free.argtypes = [_vp]
+        L.aiwcrf_last_error.restype = C.c_char_p
+        L.aiwcrf_profile_enable.argtypes = [C.c_int32]
+        L.aiwcrf_profile_read.argtypes = [C.c_int32, _vp, _vp]
+        L.aiwcrf_profile_name.argtypes = [C.c_int32]
+        L.aiwcrf_profile_name.restype = C.c_char_p
+        L.aiwcrf_profile_num_classes.restype = C.c_int32
+        L.aiwcrf_launch_count.restype = C.c_int64
+        for name in EXPORTS:
+            if name not in ("aiwcrf_last_error", "aiwcrf_profile_name", "aiwcrf_profile_num_classes",
+                            "aiwcrf_launch_count"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+        return L
+
+
+def _check(rc: int):
+    if rc != AIWCRF_OK:
+        msg = load().aiwcrf_last_error().decode(errors="replace")
+        raise AiwcrfError(rc, msg)
+
+
+def _ptr(a):
+    """Pointer of a torch tensor or numpy array (must be contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return a.ctypes.data
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return a.data_ptr()
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+
+
+def _shape(a):
+    return tuple(a.shape)
+
+
+class Forest:
+    """A fitted forest owned by the library (freed on garbage collection)."""
+
+    def __init__(self, handle: int):
+        self._h = _vp(handle)
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().aiwcrf_forest_free(self._h)
+        self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        T, nn, F = C.c_int64(), C.c_int64(), C.c_int32()
+        _check(load().aiwcrf_forest_info(self._h, C.byref(T), C.byref(nn), C.byref(F)))
+        return dict(num_trees=T.value, num_nodes=nn.value, n_features=F.value)
+
+    def stats(self) -> dict:
+        st = FitStats()
+        _check(load().aiwcrf_forest_stats(self._h, C.byref(st)))
+        return st.as_dict()
+
+    def serialize(self) -> bytes:
+        need = C.c_size_t()
+        _check(load().aiwcrf_forest_serialize(self._h, None, 0, C.byref(need)))
+        buf = C.create_string_buffer(need.value)
+        _check(load().aiwcrf_forest_serialize(self._h, buf, need.value, C.byref(need)))
+        return buf.raw
+
+
+def aiwcrf_fit(params: FitParams, X, y, stream=None) -> Forest:
+    F, N = _shape(X)
+    h = _vp()
+    _check(load().aiwcrf_fit(C.byref(params), _ptr(X), _ptr(y), N, F, _stream(stream), C.byref(h)))
+    return Forest(h.value)
+
+
+def aiwcrf_fit_subsets(params: FitParams, X, y, offsets, rows, stream=None) -> list:
+    F, N = _shape(X)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    G = int(offsets.size - 1)
+    hs = (_vp * G)()
+    _check(load().aiwcrf_fit_subsets(C.byref(params), _ptr(X), _ptr(y), N, F, offsets.ctypes.data,
+                                     _ptr(rows), G, _stream(stream), hs))
+    return [Forest(hs[g]) for g in range(G)]
+
+
+def aiwcrf_predict(forest: Forest, Xq, out_pred, out_var=None, stream=None):
+    F, Q = _shape(Xq)
+    _check(load().aiwcrf_predict(forest.handle, _ptr(Xq), Q, _ptr(out_pred), _ptr(out_var), _stream(stream)))
+    return out_pred
+
+
+def aiwcrf_predict_sum(forest: Forest, Xq, out_sum, stream=None):
+    F, Q = _shape(Xq)
+    _check(load().aiwcrf_predict_sum(forest.handle, _ptr(Xq), Q, _ptr(out_sum), _stream(stream)))
+    return out_sum
+
+
+def aiwcrf_round_mean(sums, total_trees: int, out, stream=None):
+    n = int(np.prod(_shape(sums)))
+    _check(load().aiwcrf_round_mean(_ptr(sums), n, total_trees, _ptr(out), _stream(stream)))
+    return out
+
+
+def aiwcrf_select_device(forest: Forest, kfeat, size_class: int, device_ids, out_best, out_pred=None,
+                         stream=None):
+    Fm2, K = _shape(kfeat)
+    dev = np.ascontiguousarray(device_ids, dtype=np.int32)
+    _check(load().aiwcrf_select_device(forest.handle, _ptr(kfeat), K, int(size_class), dev.ctypes.data,
+                                       int(dev.size), _ptr(out_best), _ptr(out_pred), _stream(stream)))
+    return out_best
+
+
+def aiwcrf_forest_deserialize(blob: bytes) -> Forest:
+    h = _vp()
+    buf = C.create_string_buffer(blob, len(blob))
+    _check(load().aiwcrf_forest_deserialize(buf, len(blob), C.byref(h)))
+    return Forest(h.value)
+
+
+def aiwcrf_profile_enable(on: bool):
+    _check(load().aiwcrf_profile_enable(1 if on else 0))
+
+
+def aiwcrf_profile_read() -> dict:
+    L = load()
+    n = int(L.aiwcrf_profile_num_classes())
+    launches = np.zeros(n, np.int64)
+    ms = np.zeros(n, np.float64)
+    _check(L.aiwcrf_profile_read(n, launches.ctypes.data, ms.ctypes.data))
+    return {L.aiwcrf_profile_name(k).decode(): (int(launches[k]), float(ms[k])) for k in range(n)}
+
+
+def aiwcrf_launch_count() -> int:
+    return int(load().aiwcrf_launch_count())
+
+
+def params(num_trees: int, mtry: int, min_node_size: int, max_depth: int = 0, seed: int = 156,
+           bootstrap: bool = True, first_tree: int = 0) -> FitParams:
+    return FitParams(num_trees, mtry, min_node_size, max_depth, seed, 1 if bootstrap else 0, 0, first_tree)
+
+
+def decode_forest(blob: bytes) -> dict:
+    """Parse a serialized forest (layout in include/aiwcrf.h) into numpy arrays."""
+    assert blob[:8] == b"AIWCRF01"
+    version, F = np.frombuffer(blob, np.uint32, 2, 8)
+    T, nn = np.frombuffer(blob, np.int64, 2, 16)
+    off = np.frombuffer(blob, np.int64, int(T) + 1, 32)
+    nodes = np.frombuffer(blob, np.uint64, int(nn), 32 + 8 * (int(T) + 1))
+    return dict(version=int(version), F=int(F), T=int(T), tree_off=off.copy(), nodes=nodes.copy())

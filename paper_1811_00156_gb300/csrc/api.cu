@@ -1,0 +1,522 @@
+// api.cu -- the extern "C" boundary declared in include/aiwcrf.h.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace aiwcrf {
+
+static thread_local std::string g_last_error;
+
+void set_error(int code, const std::string &msg)
+{
+    g_last_error = "aiwcrf error " + std::to_string(code) + ": " + msg;
+}
+
+int fail(int code, const std::string &msg)
+{
+    set_error(code, msg);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    cudaGetLastError();   // clear a sticky launch error where possible
+    return fail(AIWCRF_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static std::atomic<long long> g_launches{0};
+
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------- profiling (CUDA events)
+namespace {
+struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+std::vector<cudaEvent_t> g_event_pool;
+thread_local std::vector<std::pair<int, cudaEvent_t>> t_open;
+
+cudaEvent_t take_event()
+{
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+const char *kProfNames[kProfNum] = {"rank",    "bootstrap", "level_big", "level_small", "scan",
+                                    "finalize", "pack",      "predict",   "select"};
+}  // namespace
+
+void prof_begin(cudaStream_t s, int cls)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on) return;
+    cudaEvent_t e = take_event();
+    cudaEventRecord(e, s);
+    t_open.push_back({cls, e});
+}
+
+void prof_end(cudaStream_t s, int cls)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on) return;
+    for (size_t i = t_open.size(); i-- > 0;) {
+        if (t_open[i].first == cls) {
+            cudaEvent_t b = take_event();
+            cudaEventRecord(b, s);
+            g_prof.push_back({cls, t_open[i].second, b});
+            t_open.erase(t_open.begin() + (long)i);
+            return;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- pointer staging
+namespace {
+
+enum PtrKind { kPtrHost, kPtrDevice, kPtrBad };
+
+PtrKind classify(const void *p, int device)
+{
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return kPtrHost;
+    }
+    switch (at.type) {
+    case cudaMemoryTypeUnregistered:
+    case cudaMemoryTypeHost:
+        return kPtrHost;
+    case cudaMemoryTypeDevice:
+    case cudaMemoryTypeManaged:
+        return at.device == device ? kPtrDevice : kPtrBad;
+    default:
+        return kPtrBad;
+    }
+}
+
+// An input array: device pointers pass through; host arrays are copied to a stream-ordered
+// device buffer.
+struct InArg {
+    const void *dev = nullptr;
+    void *owned = nullptr;
+    cudaStream_t s = nullptr;
+    ~InArg() { if (owned) cudaFreeAsync(owned, s); }
+};
+
+int stage_in(InArg &a, const void *p, size_t bytes, int device, cudaStream_t s, const char *name)
+{
+    a.s = s;
+    const PtrKind k = classify(p, device);
+    if (k == kPtrBad) return fail(AIWCRF_E_BAD_POINTER, std::string(name) + " is memory of another device");
+    if (k == kPtrDevice) { a.dev = p; return AIWCRF_OK; }
+    cudaError_t e = cudaMallocAsync(&a.owned, bytes ? bytes : 1, s);
+    if (e != cudaSuccess) return fail(AIWCRF_E_OOM, std::string("staging ") + name + ": " + cudaGetErrorString(e));
+    if (bytes) {
+        e = cudaMemcpyAsync(a.owned, p, bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, name);
+    }
+    a.dev = a.owned;
+    return AIWCRF_OK;
+}
+
+// An output array: device pointers pass through; host arrays get a device buffer that is
+// copied back by finish().
+struct OutArg {
+    void *dev = nullptr;
+    void *owned = nullptr;
+    void *host = nullptr;
+    size_t bytes = 0;
+    cudaStream_t s = nullptr;
+    ~OutArg() { if (owned) cudaFreeAsync(owned, s); }
+};
+
+int stage_out(OutArg &a, void *p, size_t bytes, int device, cudaStream_t s, const char *name)
+{
+    a.s = s;
+    if (!p) return AIWCRF_OK;
+    const PtrKind k = classify(p, device);
+    if (k == kPtrBad) return fail(AIWCRF_E_BAD_POINTER, std::string(name) + " is memory of another device");
+    if (k == kPtrDevice) { a.dev = p; return AIWCRF_OK; }
+    cudaError_t e = cudaMallocAsync(&a.owned, bytes ? bytes : 1, s);
+    if (e != cudaSuccess) return fail(AIWCRF_E_OOM, std::string("staging ") + name + ": " + cudaGetErrorString(e));
+    a.dev = a.owned;
+    a.host = p;
+    a.bytes = bytes;
+    return AIWCRF_OK;
+}
+
+int finish_out(OutArg &a)
+{
+    if (!a.host || !a.bytes) return AIWCRF_OK;
+    cudaError_t e = cudaMemcpyAsync(a.host, a.dev, a.bytes, cudaMemcpyDeviceToHost, a.s);
+    if (e != cudaSuccess) return cuda_fail(e, "copy of an output to the host");
+    return AIWCRF_OK;
+}
+
+int sync_if(bool any_host, cudaStream_t s)
+{
+    if (!any_host) return AIWCRF_OK;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return AIWCRF_OK;
+}
+
+int current_device(int *dev)
+{
+    cudaError_t e = cudaGetDevice(dev);
+    if (e != cudaSuccess) return cuda_fail(e, "no usable CUDA device");
+    return AIWCRF_OK;
+}
+
+int check_params(const aiwcrf_fit_params *p, int64_t n_rows, int32_t n_features)
+{
+    if (!p) return fail(AIWCRF_E_INVALID_ARG, "params is NULL");
+    if (p->num_trees < 1 || p->num_trees > AIWCRF_MAX_TREES)
+        return fail(AIWCRF_E_INVALID_ARG, "num_trees must be in [1, 2^20]");
+    if (p->mtry < 1) return fail(AIWCRF_E_INVALID_ARG, "mtry must be >= 1");
+    if (p->min_node_size < 1) return fail(AIWCRF_E_INVALID_ARG, "min_node_size must be >= 1");
+    if (p->max_depth < 0) return fail(AIWCRF_E_INVALID_ARG, "max_depth must be >= 0");
+    if (p->bootstrap != 0 && p->bootstrap != 1) return fail(AIWCRF_E_INVALID_ARG, "bootstrap must be 0 or 1");
+    if (p->reserved != 0) return fail(AIWCRF_E_INVALID_ARG, "reserved must be 0");
+    if (p->first_tree < 0 || p->first_tree + p->num_trees > 0xFFFFFFFFll)
+        return fail(AIWCRF_E_INVALID_ARG, "first_tree out of range");
+    if (n_rows < 1) return fail(AIWCRF_E_INVALID_ARG, "n_rows must be >= 1");
+    if (n_rows > AIWCRF_MAX_ROWS) return fail(AIWCRF_E_LIMIT, "n_rows exceeds 2^22 - 1");
+    if (n_features < 1 || n_features > AIWCRF_MAX_FEATURES)
+        return fail(AIWCRF_E_INVALID_ARG, "n_features must be in [1, 128]");
+    return AIWCRF_OK;
+}
+
+}  // namespace
+}  // namespace aiwcrf
+
+using namespace aiwcrf;
+
+extern "C" {
+
+const char *aiwcrf_last_error(void) { return g_last_error.c_str(); }
+
+int aiwcrf_fit(const aiwcrf_fit_params *params, const float *X, const int64_t *y, int64_t n_rows,
+               int32_t n_features, void *cuda_stream, aiwcrf_forest **out)
+{
+    g_last_error.clear();
+    int rc = check_params(params, n_rows, n_features);
+    if (rc) return rc;
+    if (!X || !y || !out) return fail(AIWCRF_E_INVALID_ARG, "X, y and out must not be NULL");
+    int dev;
+    if ((rc = current_device(&dev))) return rc;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    InArg ax, ay;
+    if ((rc = stage_in(ax, X, sizeof(float) * (size_t)n_features * (size_t)n_rows, dev, s, "X"))) return rc;
+    if ((rc = stage_in(ay, y, sizeof(int64_t) * (size_t)n_rows, dev, s, "y"))) return rc;
+    std::vector<aiwcrf_forest *> fs;
+    rc = fit_batch(*params, (const float *)ax.dev, (const int64_t *)ay.dev, n_rows, n_features, {}, nullptr, 1, s, fs);
+    if (rc) return rc;
+    *out = fs[0];
+    return AIWCRF_OK;
+}
+
+int aiwcrf_fit_subsets(const aiwcrf_fit_params *params, const float *X, const int64_t *y, int64_t n_rows,
+                       int32_t n_features, const int64_t *subset_offsets, const int32_t *subset_rows,
+                       int32_t n_subsets, void *cuda_stream, aiwcrf_forest **out)
+{
+    g_last_error.clear();
+    int rc = check_params(params, n_rows, n_features);
+    if (rc) return rc;
+    if (!X || !y || !out || !subset_offsets || !subset_rows || n_subsets < 1)
+        return fail(AIWCRF_E_INVALID_ARG, "X, y, subsets and out must be given, n_subsets >= 1");
+    if ((int64_t)n_subsets * params->num_trees > (int64_t)AIWCRF_MAX_TREES * 16)
+        return fail(AIWCRF_E_LIMIT, "too many trees in one batch");
+    int dev;
+    if ((rc = current_device(&dev))) return rc;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    std::vector<int64_t> off(subset_offsets, subset_offsets + n_subsets + 1);
+    if (off[0] != 0) return fail(AIWCRF_E_INVALID_ARG, "subset_offsets[0] must be 0");
+    for (int32_t g = 0; g < n_subsets; ++g)
+        if (off[(size_t)g + 1] <= off[(size_t)g]) return fail(AIWCRF_E_INVALID_ARG, "every subset needs >= 1 row");
+    const int64_t total = off[(size_t)n_subsets];
+    // row validity (increasing, within range) is checked on the host copy
+    std::vector<int32_t> rows((size_t)total);
+    if (classify(subset_rows, dev) == kPtrDevice) {
+        cudaError_t e = cudaMemcpyAsync(rows.data(), subset_rows, sizeof(int32_t) * (size_t)total, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "reading subset_rows");
+    } else {
+        std::memcpy(rows.data(), subset_rows, sizeof(int32_t) * (size_t)total);
+    }
+    for (int32_t g = 0; g < n_subsets; ++g)
+        for (int64_t k = off[(size_t)g]; k < off[(size_t)g + 1]; ++k) {
+            if (rows[(size_t)k] < 0 || rows[(size_t)k] >= n_rows || (k > off[(size_t)g] && rows[(size_t)k] <= rows[(size_t)k - 1]))
+                return fail(AIWCRF_E_INVALID_ARG, "subset rows must be strictly increasing row indices");
+        }
+    InArg ax, ay, ar;
+    if ((rc = stage_in(ax, X, sizeof(float) * (size_t)n_features * (size_t)n_rows, dev, s, "X"))) return rc;
+    if ((rc = stage_in(ay, y, sizeof(int64_t) * (size_t)n_rows, dev, s, "y"))) return rc;
+    if ((rc = stage_in(ar, rows.data(), sizeof(int32_t) * (size_t)total, dev, s, "subset_rows"))) return rc;
+    std::vector<aiwcrf_forest *> fs;
+    rc = fit_batch(*params, (const float *)ax.dev, (const int64_t *)ay.dev, n_rows, n_features, off,
+                   (const int32_t *)ar.dev, n_subsets, s, fs);
+    if (rc) return rc;
+    for (int32_t g = 0; g < n_subsets; ++g) out[g] = fs[(size_t)g];
+    cudaStreamSynchronize(s);   // the staged host copy of the rows must outlive its transfer
+    return AIWCRF_OK;
+}
+
+static int predict_common(const aiwcrf_forest *f, const float *Xq, int64_t Q, int64_t *out_sum, int64_t *out_pred,
+                          uint64_t *out_var, void *cuda_stream)
+{
+    if (!f) return fail(AIWCRF_E_INVALID_ARG, "forest is NULL");
+    if (Q < 0 || Q > ((int64_t)1 << 36)) return fail(AIWCRF_E_INVALID_ARG, "n_queries out of range");
+    if (Q > 0 && !Xq) return fail(AIWCRF_E_INVALID_ARG, "Xq is NULL");
+    int dev, rc;
+    if ((rc = current_device(&dev))) return rc;
+    if (dev != f->device) return fail(AIWCRF_E_BAD_POINTER, "the forest lives on another device");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    InArg aq;
+    OutArg os, op, ov;
+    if (Q == 0) return AIWCRF_OK;
+    if ((rc = stage_in(aq, Xq, sizeof(float) * (size_t)f->F * (size_t)Q, dev, s, "Xq"))) return rc;
+    if ((rc = stage_out(os, out_sum, sizeof(int64_t) * (size_t)Q, dev, s, "out_sum"))) return rc;
+    if ((rc = stage_out(op, out_pred, sizeof(int64_t) * (size_t)Q, dev, s, "out_pred"))) return rc;
+    if ((rc = stage_out(ov, out_var, 2 * sizeof(uint64_t) * (size_t)Q, dev, s, "out_var"))) return rc;
+    rc = predict_launch(f, (const float *)aq.dev, Q, (int64_t *)os.dev, (int64_t *)op.dev, (uint64_t *)ov.dev,
+                        f->T, s);
+    if (rc) return rc;
+    if ((rc = finish_out(os)) || (rc = finish_out(op)) || (rc = finish_out(ov))) return rc;
+    return sync_if(os.host || op.host || ov.host, s);
+}
+
+int aiwcrf_predict(const aiwcrf_forest *forest, const float *Xq, int64_t n_queries, int64_t *out_pred,
+                   uint64_t *out_var, void *cuda_stream)
+{
+    g_last_error.clear();
+    if (!out_pred) return fail(AIWCRF_E_INVALID_ARG, "out_pred is NULL");
+    return predict_common(forest, Xq, n_queries, nullptr, out_pred, out_var, cuda_stream);
+}
+
+int aiwcrf_predict_sum(const aiwcrf_forest *forest, const float *Xq, int64_t n_queries, int64_t *out_sum,
+                       void *cuda_stream)
+{
+    g_last_error.clear();
+    if (!out_sum) return fail(AIWCRF_E_INVALID_ARG, "out_sum is NULL");
+    return predict_common(forest, Xq, n_queries, out_sum, nullptr, nullptr, cuda_stream);
+}
+
+int aiwcrf_round_mean(const int64_t *sums, int64_t n, int64_t total_trees, int64_t *out, void *cuda_stream)
+{
+    g_last_error.clear();
+    if (n < 0 || total_trees < 1) return fail(AIWCRF_E_INVALID_ARG, "n must be >= 0 and total_trees >= 1");
+    if (n > 0 && (!sums || !out)) return fail(AIWCRF_E_INVALID_ARG, "sums and out must not be NULL");
+    if (n == 0) return AIWCRF_OK;
+    int dev, rc;
+    if ((rc = current_device(&dev))) return rc;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    InArg a;
+    OutArg o;
+    if ((rc = stage_in(a, sums, sizeof(int64_t) * (size_t)n, dev, s, "sums"))) return rc;
+    if ((rc = stage_out(o, out, sizeof(int64_t) * (size_t)n, dev, s, "out"))) return rc;
+    if ((rc = round_mean_launch((const int64_t *)a.dev, n, total_trees, (int64_t *)o.dev, s))) return rc;
+    if ((rc = finish_out(o))) return rc;
+    return sync_if(o.host != nullptr, s);
+}
+
+int aiwcrf_select_device(const aiwcrf_forest *forest, const float *kfeat, int32_t n_kernels, int32_t size_class,
+                         const int32_t *device_ids, int32_t n_devices, int32_t *out_best, int64_t *out_pred,
+                         void *cuda_stream)
+{
+    g_last_error.clear();
+    if (!forest || !kfeat || !device_ids || !out_best)
+        return fail(AIWCRF_E_INVALID_ARG, "forest, kfeat, device_ids and out_best must not be NULL");
+    if (n_kernels < 1 || n_devices < 1 || (int64_t)n_kernels * n_devices > ((int64_t)1 << 31))
+        return fail(AIWCRF_E_INVALID_ARG, "n_kernels and n_devices must be >= 1");
+    if (forest->F < 3) return fail(AIWCRF_E_INVALID_ARG, "the forest needs >= 3 features (kernel, device, size)");
+    int dev, rc;
+    if ((rc = current_device(&dev))) return rc;
+    if (dev != forest->device) return fail(AIWCRF_E_BAD_POINTER, "the forest lives on another device");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int64_t Qn = (int64_t)n_kernels * n_devices;
+    InArg ak, ad;
+    OutArg ob, op;
+    if ((rc = stage_in(ak, kfeat, sizeof(float) * (size_t)(forest->F - 2) * (size_t)n_kernels, dev, s, "kfeat"))) return rc;
+    if ((rc = stage_in(ad, device_ids, sizeof(int32_t) * (size_t)n_devices, dev, s, "device_ids"))) return rc;
+    if ((rc = stage_out(ob, out_best, sizeof(int32_t) * (size_t)n_kernels, dev, s, "out_best"))) return rc;
+    if ((rc = stage_out(op, out_pred, sizeof(int64_t) * (size_t)Qn, dev, s, "out_pred"))) return rc;
+    float *d_q = nullptr;
+    int64_t *d_p = nullptr;
+    cudaError_t e = cudaMallocAsync(&d_q, sizeof(float) * (size_t)forest->F * (size_t)Qn, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_p, sizeof(int64_t) * (size_t)Qn, s);
+    if (e != cudaSuccess) {
+        if (d_q) cudaFreeAsync(d_q, s);
+        return fail(AIWCRF_E_OOM, "select_device scratch");
+    }
+    rc = select_launch(forest, (const float *)ak.dev, n_kernels, size_class, (const int32_t *)ad.dev, n_devices,
+                       (int32_t *)ob.dev, (int64_t *)op.dev, d_q, d_p, s);
+    cudaFreeAsync(d_q, s);
+    cudaFreeAsync(d_p, s);
+    if (rc) return rc;
+    if ((rc = finish_out(ob)) || (rc = finish_out(op))) return rc;
+    // device_ids is usually a host array: its staged copy must be consumed before returning
+    return sync_if(true, s);
+}
+
+int aiwcrf_forest_stats(const aiwcrf_forest *forest, aiwcrf_fit_stats *out)
+{
+    g_last_error.clear();
+    if (!forest || !out) return fail(AIWCRF_E_INVALID_ARG, "forest and out must not be NULL");
+    *out = forest->stats;
+    return AIWCRF_OK;
+}
+
+int aiwcrf_forest_info(const aiwcrf_forest *forest, int64_t *num_trees, int64_t *num_nodes, int32_t *n_features)
+{
+    g_last_error.clear();
+    if (!forest) return fail(AIWCRF_E_INVALID_ARG, "forest is NULL");
+    if (num_trees) *num_trees = forest->T;
+    if (num_nodes) *num_nodes = forest->num_nodes;
+    if (n_features) *n_features = forest->F;
+    return AIWCRF_OK;
+}
+
+static const char kMagic[8] = {'A', 'I', 'W', 'C', 'R', 'F', '0', '1'};
+
+int aiwcrf_forest_serialize(const aiwcrf_forest *forest, void *buf, size_t cap, size_t *needed)
+{
+    g_last_error.clear();
+    if (!forest || !needed) return fail(AIWCRF_E_INVALID_ARG, "forest and needed must not be NULL");
+    const size_t bytes = 8 + 4 + 4 + 8 + 8 + 8 * (size_t)(forest->T + 1) + 8 * (size_t)forest->num_nodes;
+    *needed = bytes;
+    if (!buf) return AIWCRF_OK;
+    if (cap < bytes) return fail(AIWCRF_E_INVALID_ARG, "buffer too small");
+    unsigned char *p = (unsigned char *)buf;
+    const uint32_t version = 1, F = (uint32_t)forest->F;
+    std::memcpy(p, kMagic, 8); p += 8;
+    std::memcpy(p, &version, 4); p += 4;
+    std::memcpy(p, &F, 4); p += 4;
+    std::memcpy(p, &forest->T, 8); p += 8;
+    std::memcpy(p, &forest->num_nodes, 8); p += 8;
+    std::memcpy(p, forest->tree_off.data(), 8 * (size_t)(forest->T + 1)); p += 8 * (size_t)(forest->T + 1);
+    cudaError_t e = cudaMemcpy(p, forest->d_nodes, 8 * (size_t)forest->num_nodes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading forest nodes");
+    return AIWCRF_OK;
+}
+
+int aiwcrf_forest_deserialize(const void *buf, size_t len, aiwcrf_forest **out)
+{
+    g_last_error.clear();
+    if (!buf || !out) return fail(AIWCRF_E_INVALID_ARG, "buf and out must not be NULL");
+    const unsigned char *p = (const unsigned char *)buf;
+    if (len < 32 || std::memcmp(p, kMagic, 8) != 0) return fail(AIWCRF_E_CORRUPT, "bad magic");
+    uint32_t version, F;
+    int64_t T, nn;
+    std::memcpy(&version, p + 8, 4);
+    std::memcpy(&F, p + 12, 4);
+    std::memcpy(&T, p + 16, 8);
+    std::memcpy(&nn, p + 24, 8);
+    if (version != 1 || F < 1 || F > AIWCRF_MAX_FEATURES || T < 1 || T > AIWCRF_MAX_TREES * 16ll || nn < 2 ||
+        nn > ((int64_t)1 << 40))
+        return fail(AIWCRF_E_CORRUPT, "bad header");
+    if (len != 32 + 8 * (size_t)(T + 1) + 8 * (size_t)nn) return fail(AIWCRF_E_CORRUPT, "bad length");
+    std::vector<int64_t> off((size_t)T + 1);
+    std::memcpy(off.data(), p + 32, 8 * (size_t)(T + 1));
+    const uint64_t *nodes = (const uint64_t *)(p + 32 + 8 * (size_t)(T + 1));
+    if (off[0] != 0 || off[(size_t)T] != nn) return fail(AIWCRF_E_CORRUPT, "bad tree offsets");
+    int64_t max_tree = 0;
+    for (int64_t t = 0; t < T; ++t) {
+        const int64_t a = off[(size_t)t], b = off[(size_t)t + 1], m = b - a;
+        if (m < 2 || (m & 1) || (a & 1) || m > (1ll << 24)) return fail(AIWCRF_E_CORRUPT, "bad tree size");
+        max_tree = m > max_tree ? m : max_tree;
+        // every split points strictly forward, inside its tree, at a real feature
+        for (int64_t j = 0; j < m; ++j) {
+            uint64_t nd;
+            std::memcpy(&nd, nodes + a + j, 8);
+            if (nd >> 63) continue;
+            const uint32_t fe = (uint32_t)(nd >> 56) & 0x7F, lc = (uint32_t)(nd >> 32) & 0xFFFFFF;
+            if (fe >= F || (int64_t)lc <= j || (int64_t)lc + 1 >= m) return fail(AIWCRF_E_CORRUPT, "bad node");
+        }
+    }
+    int dev, rc;
+    if ((rc = current_device(&dev))) return rc;
+    aiwcrf_forest *f = new aiwcrf_forest();
+    f->F = (int32_t)F; f->T = T; f->num_nodes = nn; f->max_tree_nodes = max_tree; f->device = dev;
+    f->tree_off = off;
+    cudaError_t e = cudaMalloc(&f->d_nodes, 8 * (size_t)nn);
+    if (e == cudaSuccess) e = cudaMalloc(&f->d_tree_off, 8 * (size_t)(T + 1));
+    if (e == cudaSuccess) e = cudaMemcpy(f->d_nodes, nodes, 8 * (size_t)nn, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(f->d_tree_off, off.data(), 8 * (size_t)(T + 1), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(f->d_nodes); cudaFree(f->d_tree_off);
+        delete f;
+        return cuda_fail(e, "uploading forest");
+    }
+    *out = f;
+    return AIWCRF_OK;
+}
+
+int aiwcrf_forest_free(aiwcrf_forest *forest)
+{
+    g_last_error.clear();
+    if (!forest) return AIWCRF_OK;
+    cudaFree(forest->d_nodes);
+    cudaFree(forest->d_tree_off);
+    delete forest;
+    return AIWCRF_OK;
+}
+
+int aiwcrf_profile_enable(int32_t on)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = on != 0;
+    return AIWCRF_OK;
+}
+
+int aiwcrf_profile_read(int32_t n, int64_t *launches, double *total_ms)
+{
+    std::vector<ProfRec> recs;
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        recs.swap(g_prof);
+    }
+    for (int32_t k = 0; k < n; ++k) { if (launches) launches[k] = 0; if (total_ms) total_ms[k] = 0.0; }
+    int rc = AIWCRF_OK;
+    for (auto &r : recs) {
+        cudaError_t e = cudaEventSynchronize(r.b);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) rc = cuda_fail(e, "reading profile events");
+        if (r.cls < n) {
+            if (launches) launches[r.cls] += 1;
+            if (total_ms) total_ms[r.cls] += ms;
+        }
+    }
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &r : recs) { g_event_pool.push_back(r.a); g_event_pool.push_back(r.b); }
+    return rc;
+}
+
+const char *aiwcrf_profile_name(int32_t k)
+{
+    return (k >= 0 && k < kProfNum) ? kProfNames[k] : "";
+}
+
+int32_t aiwcrf_profile_num_classes(void) { return kProfNum; }
+
+int64_t aiwcrf_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -1,0 +1,1242 @@
+// fit.cu -- random-forest growth on the GPU (the model of Sec. III-B, fitted breadth first).
+//
+// Pipeline of one fit (all trees of all forests of the batch grow together, level by level):
+//   rank_kernel        one-time stable LSD radix sort of every column; dense ranks (u16) and
+//                      the rank -> value table
+//   bootstrap_kernel   Philox draws per tree -> multiplicities -> in-bag row list (row | w<<24)
+//   per depth d:
+//     level_big_kernel   one CTA per node with > 32 distinct rows: mtry draw, shared-memory
+//                        histogram of (sum w | distinct rows, sum w*y) per rank for every tried
+//                        feature, block scan, exact argmax of the gain, stable partition
+//     level_small_kernel one warp per node with <= 32 distinct rows: the same search with a
+//                        register bitonic sort per feature instead of a histogram
+//     scan_*             exclusive scan of the split flags over the depth's nodes
+//     finalize_kernel    encodes each node, numbers the children breadth first, writes the
+//                        next depth's node table and its warp/CTA work lists
+//     tree_update_kernel per-tree node counts and next-depth offsets
+//   pack_kernel        scatters every finished node to its forest / tree / BFS position
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace aiwcrf {
+
+// ------------------------------------------------------------------------------------------
+// small device utilities
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint32_t float_key(float x)
+{
+    uint32_t b = __float_as_uint(x);
+    if (b == 0x80000000u) b = 0u;                      // -0 and +0 are one value
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);  // order-preserving unsigned key
+}
+
+__device__ __forceinline__ float key_float(uint32_t k)
+{
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+// inclusive block scan of one u32 per thread (blockDim multiple of 32, <= 1024)
+__device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t *warp_tmp, uint32_t &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) warp_tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < nw ? warp_tmp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += t;
+        }
+        if (lane < nw) warp_tmp[lane] = w;             // inclusive warp prefix
+    }
+    __syncthreads();
+    const uint32_t off = warp > 0 ? warp_tmp[warp - 1] : 0u;
+    total = warp_tmp[nw - 1];
+    __syncthreads();
+    return x + off;
+}
+
+// ------------------------------------------------------------------------------------------
+// a1: presort and rank, one CTA of 1024 threads per column
+// ------------------------------------------------------------------------------------------
+constexpr int kRankThreads = 1024;
+
+__global__ void __launch_bounds__(kRankThreads) rank_kernel(
+    const float *__restrict__ X, int64_t N, uint32_t *keyA, uint32_t *idxA, uint32_t *keyB,
+    uint32_t *idxB, uint16_t *__restrict__ R, float *__restrict__ vals, uint32_t *__restrict__ card,
+    uint32_t *err)
+{
+    __shared__ uint32_t hist[256];
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t wcnt[32][256];
+    __shared__ uint32_t tile_tot[256];
+    __shared__ uint32_t warp_tmp[32];
+    __shared__ uint32_t running;
+
+    const int f = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const size_t off = (size_t)f * (size_t)N;
+    uint32_t *kin = keyA + off, *iin = idxA + off, *kout = keyB + off, *iout = idxB + off;
+
+    int nan = 0;
+    for (int64_t i = tid; i < N; i += kRankThreads) {
+        const float x = X[off + i];
+        if (x != x) nan = 1;
+        kin[i] = float_key(x);
+        iin[i] = (uint32_t)i;
+    }
+    if (__syncthreads_or(nan)) {
+        if (tid == 0) atomicOr(err, kErrNaN);
+        return;
+    }
+    for (int k = tid; k < 32 * 256; k += kRankThreads) (&wcnt[0][0])[k] = 0u;
+
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 8 * pass;
+        if (tid < 256) hist[tid] = 0u;
+        __syncthreads();
+        for (int64_t i = tid; i < N; i += kRankThreads) atomicAdd(&hist[(kin[i] >> shift) & 255u], 1u);
+        __syncthreads();
+        // one digit holds every key: the pass is the identity permutation
+        if (__syncthreads_or(tid < 256 && hist[tid] == (uint32_t)N)) continue;
+        if (warp == 0) {                                         // exclusive scan of 256 counts
+            uint32_t loc[8], s = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) { loc[k] = s; s += hist[lane * 8 + k]; }
+            uint32_t x = s;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, x, o);
+                if (lane >= o) x += t;
+            }
+            const uint32_t ex = x - s;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) base[lane * 8 + k] = ex + loc[k];
+        }
+        __syncthreads();
+        for (int64_t t0 = 0; t0 < N; t0 += kRankThreads) {
+            const int64_t i = t0 + tid;
+            const bool valid = i < N;
+            const uint32_t k = valid ? kin[i] : 0u;
+            const uint32_t id = valid ? iin[i] : 0u;
+            const uint32_t d = (k >> shift) & 255u;
+            const uint32_t peers = __match_any_sync(kFull, valid ? d : (256u + lane));
+            const uint32_t rk = __popc(peers & lanemask_lt());
+            if (valid && rk == 0) wcnt[warp][d] = __popc(peers);
+            __syncthreads();
+            if (tid < 256) {
+                uint32_t run = 0;
+                for (int w = 0; w < 32; ++w) {
+                    const uint32_t c = wcnt[w][tid];
+                    wcnt[w][tid] = run;
+                    run += c;
+                }
+                tile_tot[tid] = run;
+            }
+            __syncthreads();
+            if (valid) {
+                const uint32_t pos = base[d] + wcnt[warp][d] + rk;
+                kout[pos] = k;
+                iout[pos] = id;
+            }
+            __syncthreads();
+            if (tid < 256) {
+                base[tid] += tile_tot[tid];
+                for (int w = 0; w < 32; ++w) wcnt[w][tid] = 0u;
+            }
+            __syncthreads();
+        }
+        uint32_t *t;
+        t = kin; kin = kout; kout = t;
+        t = iin; iin = iout; iout = t;
+    }
+
+    if (tid == 0) running = 0u;
+    __syncthreads();
+    int over = 0;
+    for (int64_t t0 = 0; t0 < N; t0 += kRankThreads) {
+        const int64_t i = t0 + tid;
+        const bool valid = i < N;
+        const uint32_t k = valid ? kin[i] : 0u;
+        const uint32_t flag = (valid && (i == 0 || kin[i - 1] != k)) ? 1u : 0u;
+        uint32_t tot;
+        const uint32_t incl = block_incl_scan(flag, warp_tmp, tot);
+        if (valid) {
+            const uint32_t r = running + incl - 1u;
+            if (r >= 65536u) over = 1;
+            else {
+                R[off + iin[i]] = (uint16_t)r;
+                if (flag) vals[off + r] = key_float(k);
+            }
+        }
+        __syncthreads();
+        if (tid == 0) running += tot;
+        __syncthreads();
+    }
+    if (over) atomicOr(err, kErrCard);
+    if (tid == 0) card[f] = running;
+}
+
+// ------------------------------------------------------------------------------------------
+// a2: bootstrap, one CTA per tree. Multiplicities are byte counters packed four to a word,
+// in shared memory when they fit, else in a per-tree global scratch.
+// ------------------------------------------------------------------------------------------
+constexpr int kBootThreads = 1024;
+
+struct BootArgs {
+    const int64_t *tree_pool_off;   // per tree: offset into sub_rows, or -1 for rows 0..len-1
+    const uint32_t *tree_pool_len;  // per tree: pool size
+    const uint32_t *tree_rng;       // per tree: global tree index used as Philox counter word 0
+    const int32_t *sub_rows;
+    const int64_t *y;
+    uint32_t seed_lo, seed_hi;
+    int bootstrap;
+    uint32_t *gcnt;                 // global byte counters (may be null)
+    int64_t gcnt_stride;            // words per tree
+    int smem_words;
+    uint32_t *rows_out;
+    int64_t row_cap;
+    NodeRec *root;
+    int32_t *small_list, *big_list;
+    uint32_t *counters;             // [0] small count, [1] big count
+    uint32_t *err;
+};
+
+__global__ void __launch_bounds__(kBootThreads) bootstrap_kernel(BootArgs a)
+{
+    extern __shared__ uint32_t sm_cnt[];
+    __shared__ uint32_t warp_tmp[32];
+    __shared__ unsigned long long red_n[32];
+    __shared__ long long red_s[32];
+    __shared__ uint32_t running;
+
+    const int t = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t n = a.tree_pool_len[t];
+    const int64_t poff = a.tree_pool_off[t];
+    const uint32_t words = (n + 3u) / 4u;
+    uint32_t *cnt = ((int)words <= a.smem_words) ? sm_cnt : a.gcnt + (size_t)t * (size_t)a.gcnt_stride;
+
+    if (a.bootstrap) {
+        for (uint32_t k = tid; k < words; k += kBootThreads) cnt[k] = 0u;
+        __syncthreads();
+        const uint32_t tg = a.tree_rng[t];
+        int overflow = 0;
+        for (uint32_t b = tid; b < words; b += kBootThreads) {
+            const uint4 u = philox10(make_uint4(tg, b, kDomBoot, 0u), a.seed_lo, a.seed_hi);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const uint32_t k = 4u * b + (uint32_t)w;
+                if (k < n) {
+                    const uint32_t j = __umulhi(uint4_word(u, w), n);
+                    const uint32_t sh = 8u * (j & 3u);
+                    const uint32_t old = atomicAdd(&cnt[j >> 2], 1u << sh);
+                    if (((old >> sh) & 255u) == 255u) overflow = 1;
+                }
+            }
+        }
+        if (overflow) atomicOr(a.err, kErrBootOverflow);
+        __syncthreads();
+    }
+
+    if (tid == 0) running = 0u;
+    __syncthreads();
+    unsigned long long acc_n = 0;
+    long long acc_s = 0;
+    uint32_t *out = a.rows_out + (size_t)t * (size_t)a.row_cap;
+    for (uint32_t b0 = 0; b0 < n; b0 += kBootThreads) {
+        const uint32_t j = b0 + tid;
+        uint32_t w = 0;
+        if (j < n) w = a.bootstrap ? ((cnt[j >> 2] >> (8u * (j & 3u))) & 255u) : 1u;
+        uint32_t tot;
+        const uint32_t incl = block_incl_scan(w > 0 ? 1u : 0u, warp_tmp, tot);
+        if (w > 0) {
+            const uint32_t row = poff < 0 ? j : (uint32_t)a.sub_rows[poff + j];
+            out[running + incl - 1u] = row | (w << kRowBits);
+            acc_n += w;
+            acc_s += (long long)w * a.y[row];
+        }
+        __syncthreads();
+        if (tid == 0) running += tot;
+        __syncthreads();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc_n += __shfl_xor_sync(kFull, acc_n, o);
+        acc_s += __shfl_xor_sync(kFull, acc_s, o);
+    }
+    if (lane == 0) { red_n[warp] = acc_n; red_s[warp] = acc_s; }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long sn = 0;
+        long long ss = 0;
+        for (int w = 0; w < kBootThreads / 32; ++w) { sn += red_n[w]; ss += red_s[w]; }
+        NodeRec r;
+        r.tree = (uint32_t)t; r.idx = 0u; r.start = 0u; r.len = running; r.n = (uint32_t)sn;
+        r.pad = 0u; r.S = ss;
+        a.root[t] = r;
+        if (running <= (uint32_t)kSmallNodeRows) a.small_list[atomicAdd(&a.counters[0], 1u)] = t;
+        else a.big_list[atomicAdd(&a.counters[1], 1u)] = t;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// a3/a4/a5: one depth of growth
+// ------------------------------------------------------------------------------------------
+struct LevelArgs {
+    const NodeRec *nodes;
+    const int32_t *list;
+    int32_t list_n;
+    const uint32_t *rows_in;
+    uint32_t *rows_out;
+    int64_t row_cap;
+    const uint16_t *R;
+    const float *vals;
+    const uint32_t *card;
+    int64_t N;
+    const int64_t *y;
+    const uint32_t *tree_rng;
+    int32_t F, mtry, min_node, max_depth, depth;
+    uint32_t seed_lo, seed_hi;
+    SplitRes *res;
+};
+
+__device__ __forceinline__ bool node_stops(const LevelArgs &a, const NodeRec &nd)
+{
+    return nd.n <= (uint32_t)a.min_node || (a.max_depth > 0 && a.depth >= a.max_depth);
+}
+
+// a3: the tried features of node (tree, depth, idx). Lane l of the warp evaluates the keys of
+// features l, l+32, ...; feature f is tried iff fewer than mtry features have a smaller
+// (key, index). Result: bit (f & 31) of mask[f >> 5].
+__device__ __forceinline__ void warp_mtry(const LevelArgs &a, uint32_t tg, uint32_t idx, uint32_t mask[4])
+{
+    const int lane = threadIdx.x & 31;
+    const int F = a.F, nch = (F + 31) >> 5;
+    uint32_t key[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        key[c] = 0xFFFFFFFFu;
+        mask[c] = 0u;
+        const int f = c * 32 + lane;
+        if (c < nch && f < F) {
+            const uint4 u = philox10(make_uint4(tg, (uint32_t)a.depth, idx, (kDomMtry << 16) | (uint32_t)(f >> 2)),
+                                     a.seed_lo, a.seed_hi);
+            key[c] = uint4_word(u, f & 3);
+        }
+    }
+    if (a.mtry >= F) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) mask[c] = __ballot_sync(kFull, c < nch && c * 32 + lane < F);
+        return;
+    }
+    uint32_t cnt[4] = {0u, 0u, 0u, 0u};
+    for (int c2 = 0; c2 < nch; ++c2) {
+        for (int s = 0; s < 32; ++s) {
+            const int g = c2 * 32 + s;
+            if (g >= F) break;
+            const uint32_t kg = __shfl_sync(kFull, key[c2], s);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int f = c * 32 + lane;
+                if (kg < key[c] || (kg == key[c] && g < f)) cnt[c]++;
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int f = c * 32 + lane;
+        mask[c] = __ballot_sync(kFull, c < nch && f < F && cnt[c] < (uint32_t)a.mtry);
+    }
+}
+
+__device__ __forceinline__ long long shfl_xor_ll(long long v, int m)
+{
+    return __shfl_xor_sync(kFull, v, m);
+}
+
+__device__ __forceinline__ long long shfl_up_ll(long long v, int m)
+{
+    return __shfl_up_sync(kFull, v, m);
+}
+
+__device__ __forceinline__ void write_leaf(SplitRes *res, int j, int kind, int64_t value)
+{
+    SplitRes r;
+    r.feature = kind; r.rank = 0u; r.thr_bits = 0u; r.nL = 0u; r.lenL = 0u; r.pad = 0u; r.v = value;
+    res[j] = r;
+}
+
+constexpr int kSmallThreads = 256;
+
+// one warp per node with at most 32 distinct rows
+__global__ void __launch_bounds__(kSmallThreads) level_small_kernel(LevelArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (kSmallThreads / 32) + (threadIdx.x >> 5);
+    if (gw >= a.list_n) return;                      // whole warp
+    const int j = a.list[gw];
+    const NodeRec nd = a.nodes[j];
+    if (node_stops(a, nd)) {
+        if (lane == 0) write_leaf(a.res, j, -2, round_mean(nd.S, nd.n));
+        return;
+    }
+    const size_t tb = (size_t)nd.tree * (size_t)a.row_cap + nd.start;
+    const bool valid = lane < (int)nd.len;
+    const uint32_t e = valid ? a.rows_in[tb + lane] : 0u;
+    const uint32_t row = e & kRowMask;
+    const uint32_t w = valid ? (e >> kRowBits) : 0u;
+    const long long wy = valid ? (long long)w * a.y[row] : 0ll;
+
+    uint32_t mask[4];
+    warp_mtry(a, a.tree_rng[nd.tree], nd.idx, mask);
+
+    Cand best = cand_none();
+    for (int c = 0; c < 4; ++c) {
+        uint32_t m = mask[c];
+        while (m) {
+            const int f = c * 32 + __ffs(m) - 1;
+            m &= m - 1;
+            const uint32_t rank = valid ? (uint32_t)a.R[(size_t)f * (size_t)a.N + row] : kRankSentinel;
+            uint32_t key = (rank << 13) | (w << 5) | (uint32_t)lane;    // unique per lane
+            long long v = wy;
+            // bitonic sort of (key, v) across the warp, ascending key
+#pragma unroll
+            for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+                for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                    const uint32_t ok = __shfl_xor_sync(kFull, key, jj);
+                    const long long ov = shfl_xor_ll(v, jj);
+                    const bool asc = (lane & k) == 0;
+                    const bool lower = (lane & jj) == 0;
+                    const bool take = (lower == asc) ? (ok < key) : (ok > key);
+                    if (take) { key = ok; v = ov; }
+                }
+            }
+            const uint32_t r = key >> 13;
+            uint32_t cw = (key >> 5) & 255u;
+            long long cs = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t tw = __shfl_up_sync(kFull, cw, o);
+                const long long ts = shfl_up_ll(cs, o);
+                if (lane >= o) { cw += tw; cs += ts; }
+            }
+            uint32_t nr = __shfl_down_sync(kFull, r, 1);
+            if (lane == 31) nr = kRankSentinel;
+            if (r != kRankSentinel && nr != kRankSentinel && r != nr) {
+                const i128_t delta = cand_delta(nd.n, nd.S, cw, cs);
+                if (delta != 0) {
+                    Cand cd;
+                    cd.h = cand_h(delta, nd.n, cw);
+                    cd.f = f; cd.r = r; cd.nL = cw; cd.lenL = (uint32_t)lane + 1u; cd.SL = cs;
+                    if (cand_better(cd, best, nd.n, nd.S)) best = cd;
+                }
+            }
+        }
+    }
+    best = warp_best(best, nd.n, nd.S);
+    if (best.h < 0.0f) {
+        if (lane == 0) write_leaf(a.res, j, -1, round_mean(nd.S, nd.n));
+        return;
+    }
+    const uint32_t rk = valid ? (uint32_t)a.R[(size_t)best.f * (size_t)a.N + row] : kRankSentinel;
+    const bool left = valid && rk <= best.r;
+    const uint32_t bl = __ballot_sync(kFull, left), bv = __ballot_sync(kFull, valid);
+    const uint32_t lenL = __popc(bl), lt = lanemask_lt();
+    const uint32_t pos = left ? __popc(bl & lt) : lenL + __popc(bv & ~bl & lt);
+    if (valid) a.rows_out[tb + pos] = e;
+    if (lane == 0) {
+        SplitRes sr;
+        sr.feature = best.f; sr.rank = best.r;
+        sr.thr_bits = __float_as_uint(a.vals[(size_t)best.f * (size_t)a.N + best.r]);
+        sr.nL = best.nL; sr.lenL = lenL; sr.pad = 0u; sr.v = best.SL;
+        a.res[j] = sr;
+    }
+}
+
+constexpr int kBigThreads = 256;
+constexpr int kBigWarps = kBigThreads / 32;
+
+// one CTA per node with more than 32 distinct rows; bin_cap bins of (u64 count, i64 sum)
+__global__ void __launch_bounds__(kBigThreads) level_big_kernel(LevelArgs a, int bin_cap)
+{
+    extern __shared__ unsigned long long sm_bins[];
+    unsigned long long *cntb = sm_bins;                               // (distinct << 32) | sum w
+    long long *sumb = reinterpret_cast<long long *>(sm_bins + bin_cap);
+    __shared__ int feats[AIWCRF_MAX_FEATURES];
+    __shared__ uint32_t fbase[AIWCRF_MAX_FEATURES + 1];
+    __shared__ unsigned long long carry_c[AIWCRF_MAX_FEATURES];
+    __shared__ long long carry_s[AIWCRF_MAX_FEATURES];
+    __shared__ unsigned long long tot_c[kBigThreads];
+    __shared__ long long tot_s[kBigThreads];
+    __shared__ int m_sh;
+    __shared__ Cand wbest[kBigWarps];
+    __shared__ Cand winner;
+    __shared__ uint32_t warp_tmp[32];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int j = a.list[blockIdx.x];
+    const NodeRec nd = a.nodes[j];
+    if (node_stops(a, nd)) {
+        if (tid == 0) write_leaf(a.res, j, -2, round_mean(nd.S, nd.n));
+        return;
+    }
+    const size_t tb = (size_t)nd.tree * (size_t)a.row_cap + nd.start;
+    const uint32_t *rin = a.rows_in + tb;
+
+    if (warp == 0) {
+        uint32_t mask[4];
+        warp_mtry(a, a.tree_rng[nd.tree], nd.idx, mask);
+        if (lane == 0) {
+            int m = 0;
+            uint32_t b = 0;
+            for (int c = 0; c < 4; ++c) {
+                uint32_t mm = mask[c];
+                while (mm) {
+                    const int f = c * 32 + __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    feats[m] = f;
+                    fbase[m] = b;
+                    carry_c[m] = 0ull;
+                    carry_s[m] = 0ll;
+                    b += a.card[f];
+                    ++m;
+                }
+            }
+            fbase[m] = b;
+            m_sh = m;
+        }
+    }
+    __syncthreads();
+    const int m = m_sh;
+    const uint32_t total_bins = fbase[m];
+    Cand best = cand_none();
+
+    for (uint32_t g0 = 0; g0 < total_bins; g0 += (uint32_t)bin_cap) {
+        const uint32_t g1 = min(total_bins, g0 + (uint32_t)bin_cap);
+        const int nb = (int)(g1 - g0);
+        for (int b = tid; b < nb; b += kBigThreads) { cntb[b] = 0ull; sumb[b] = 0ll; }
+        int k_lo = 0;
+        while (fbase[k_lo + 1] <= g0) ++k_lo;
+        int k_hi = k_lo;
+        while (k_hi + 1 < m && fbase[k_hi + 1] < g1) ++k_hi;
+        __syncthreads();
+
+        // histogram of this group's bins
+        for (uint32_t i = tid; i < nd.len; i += kBigThreads) {
+            const uint32_t e = rin[i];
+            const uint32_t row = e & kRowMask, w = e >> kRowBits;
+            const long long wy = (long long)w * a.y[row];
+            const unsigned long long inc = (1ull << 32) | w;
+            for (int k = k_lo; k <= k_hi; ++k) {
+                const uint32_t b = fbase[k] + (uint32_t)a.R[(size_t)feats[k] * (size_t)a.N + row];
+                if (b >= g0 && b < g1) {
+                    atomicAdd(&cntb[b - g0], inc);
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&sumb[b - g0]), (unsigned long long)wy);
+                }
+            }
+        }
+        __syncthreads();
+
+        // block inclusive prefix over the group's bins (unsegmented), in place
+        const int per = (nb + kBigThreads - 1) / kBigThreads;
+        const int lo = min(nb, tid * per), hi = min(nb, lo + per);
+        unsigned long long lc = 0;
+        long long ls = 0;
+        for (int b = lo; b < hi; ++b) { lc += cntb[b]; ls += sumb[b]; }
+        tot_c[tid] = lc;
+        tot_s[tid] = ls;
+        __syncthreads();
+        if (warp == 0) {            // exclusive scan of the 256 thread totals by one warp
+            unsigned long long c8[8];
+            long long s8[8];
+            unsigned long long cs = 0;
+            long long ss = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) { c8[k] = cs; s8[k] = ss; cs += tot_c[lane * 8 + k]; ss += tot_s[lane * 8 + k]; }
+            unsigned long long xc = cs;
+            long long xs = ss;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long tc = __shfl_up_sync(kFull, xc, o);
+                const long long ts = __shfl_up_sync(kFull, xs, o);
+                if (lane >= o) { xc += tc; xs += ts; }
+            }
+            xc -= cs;
+            xs -= ss;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) { tot_c[lane * 8 + k] = xc + c8[k]; tot_s[lane * 8 + k] = xs + s8[k]; }
+        }
+        __syncthreads();
+        {
+            unsigned long long rc = tot_c[tid];
+            long long rs = tot_s[tid];
+            for (int b = lo; b < hi; ++b) {
+                rc += cntb[b]; rs += sumb[b];
+                cntb[b] = rc; sumb[b] = rs;
+            }
+        }
+        __syncthreads();
+
+        // candidates of this thread's bins
+        if (lo < hi) {
+            int k = k_lo;
+            while (k < k_hi && fbase[k + 1] <= g0 + (uint32_t)lo) ++k;
+            for (int b = lo; b < hi; ++b) {
+                const uint32_t gb = g0 + (uint32_t)b;
+                while (fbase[k + 1] <= gb) ++k;
+                const unsigned long long pc = cntb[b];
+                const unsigned long long prev = b > 0 ? cntb[b - 1] : 0ull;
+                if ((uint32_t)(pc - prev) == 0u) continue;             // rank not present
+                const int fs = (int)(max(fbase[k], g0) - g0);          // feature's first bin here
+                const unsigned long long base_c = fs > 0 ? cntb[fs - 1] : 0ull;
+                const long long base_s = fs > 0 ? sumb[fs - 1] : 0ll;
+                const unsigned long long cw = pc - base_c + carry_c[k];
+                const uint32_t nL = (uint32_t)cw;
+                if (nL >= nd.n) continue;                               // last present rank
+                const long long SL = sumb[b] - base_s + carry_s[k];
+                const i128_t delta = cand_delta(nd.n, nd.S, nL, SL);
+                if (delta == 0) continue;
+                Cand cd;
+                cd.h = cand_h(delta, nd.n, nL);
+                cd.f = feats[k]; cd.r = gb - fbase[k]; cd.nL = nL; cd.lenL = (uint32_t)(cw >> 32); cd.SL = SL;
+                if (cand_better(cd, best, nd.n, nd.S)) best = cd;
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && fbase[k_hi + 1] > g1) {                        // feature continues
+            const int fs = (int)(max(fbase[k_hi], g0) - g0);
+            carry_c[k_hi] += cntb[nb - 1] - (fs > 0 ? cntb[fs - 1] : 0ull);
+            carry_s[k_hi] += sumb[nb - 1] - (fs > 0 ? sumb[fs - 1] : 0ll);
+        }
+        __syncthreads();
+    }
+
+    best = warp_best(best, nd.n, nd.S);
+    if (lane == 0) wbest[warp] = best;
+    __syncthreads();
+    if (warp == 0) {
+        Cand c = lane < kBigWarps ? wbest[lane] : cand_none();
+        c = warp_best(c, nd.n, nd.S);
+        if (lane == 0) winner = c;
+    }
+    __syncthreads();
+    const Cand win = winner;
+    if (win.h < 0.0f) {
+        if (tid == 0) write_leaf(a.res, j, -1, round_mean(nd.S, nd.n));
+        return;
+    }
+
+    // a5: stable partition of the node's rows into [left | right] at the same offsets
+    uint32_t run_l = 0u, run_r = 0u;           // block-uniform running counts
+    uint32_t *rout = a.rows_out + tb;
+    const uint16_t *rcol = a.R + (size_t)win.f * (size_t)a.N;
+    for (uint32_t b0 = 0; b0 < nd.len; b0 += kBigThreads) {
+        const uint32_t i = b0 + tid;
+        const bool valid = i < nd.len;
+        const uint32_t e = valid ? rin[i] : 0u;
+        const bool left = valid && (uint32_t)rcol[e & kRowMask] <= win.r;
+        uint32_t tot;
+        const uint32_t incl = block_incl_scan(left ? 1u : 0u, warp_tmp, tot);
+        if (valid) {
+            const uint32_t before_l = incl - (left ? 1u : 0u);
+            if (left) rout[run_l + before_l] = e;
+            else rout[win.lenL + run_r + ((uint32_t)tid - before_l)] = e;
+        }
+        run_l += tot;
+        run_r += min((uint32_t)kBigThreads, nd.len - b0) - tot;
+    }
+    if (tid == 0) {
+        SplitRes sr;
+        sr.feature = win.f; sr.rank = win.r;
+        sr.thr_bits = __float_as_uint(a.vals[(size_t)win.f * (size_t)a.N + win.r]);
+        sr.nL = win.nL; sr.lenL = win.lenL; sr.pad = 0u; sr.v = win.SL;
+        a.res[j] = sr;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// exclusive scan of the split flags (three passes, 4096 flags per block)
+// ------------------------------------------------------------------------------------------
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 4;
+constexpr int kScanTile = kScanThreads * kScanPer;
+
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const SplitRes *res, int n, uint32_t *block_sums)
+{
+    __shared__ uint32_t warp_tmp[32];
+    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanPer;
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) c += (base + k < n && res[base + k].feature >= 0) ? 1u : 0u;
+    uint32_t tot;
+    block_incl_scan(c, warp_tmp, tot);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(uint32_t *block_sums, int nblocks)
+{
+    __shared__ uint32_t warp_tmp[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0u;
+    __syncthreads();
+    for (int b0 = 0; b0 < nblocks; b0 += kScanThreads) {
+        const int b = b0 + threadIdx.x;
+        const uint32_t v = b < nblocks ? block_sums[b] : 0u;
+        uint32_t tot;
+        const uint32_t incl = block_incl_scan(v, warp_tmp, tot);
+        if (b < nblocks) block_sums[b] = carry + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) block_sums[nblocks] = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_write_kernel(const SplitRes *res, int n,
+                                                                  const uint32_t *block_sums, int nblocks,
+                                                                  uint32_t *excl)
+{
+    __shared__ uint32_t warp_tmp[32];
+    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanPer;
+    uint32_t fl[kScanPer], c = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        fl[k] = (base + k < n && res[base + k].feature >= 0) ? 1u : 0u;
+        c += fl[k];
+    }
+    uint32_t tot;
+    const uint32_t incl = block_incl_scan(c, warp_tmp, tot);
+    uint32_t run = block_sums[blockIdx.x] + incl - c;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        if (base + k < n) excl[base + k] = run;
+        run += fl[k];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) excl[n] = block_sums[nblocks];
+}
+
+// ------------------------------------------------------------------------------------------
+// finalize one depth
+// ------------------------------------------------------------------------------------------
+struct FinalArgs {
+    const NodeRec *nodes;
+    const SplitRes *res;
+    const uint32_t *excl;          // n + 1
+    const uint32_t *tree_off;      // T + 1: first node of each tree at this depth
+    const uint32_t *tree_base;     // T: nodes of each tree at lower depths
+    int n;
+    NodeRec *next;
+    int32_t *small_list, *big_list;
+    uint32_t *counters;            // [0] small, [1] big
+    PackedRec *packed;             // this depth's slice
+    GrowStats *stats;
+};
+
+__device__ __forceinline__ void push_list(int32_t *list, uint32_t *counter, bool want, int32_t value)
+{
+    const uint32_t b = __ballot_sync(kFull, want);
+    if (!b) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(b) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(counter, (uint32_t)__popc(b));
+    base = __shfl_sync(kFull, base, leader);
+    if (want) list[base + __popc(b & lanemask_lt())] = value;
+}
+
+__global__ void __launch_bounds__(256) finalize_kernel(FinalArgs a)
+{
+    __shared__ unsigned long long red[6][8];
+    const int jj = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = jj < a.n;
+    const int j = active ? jj : 0;
+    const NodeRec nd = a.nodes[j];
+    const SplitRes r = a.res[j];
+    const bool split = active && r.feature >= 0;
+    const uint32_t t = nd.tree;
+    const uint32_t first = a.tree_off[t];
+    const uint32_t cnt_t = a.tree_off[t + 1] - first;
+    const uint32_t g = a.excl[j];
+    const uint32_t local = g - a.excl[first];
+    const uint32_t base_t = a.tree_base[t];
+    NodeRec L, Rn;
+    if (active) {
+        PackedRec pr;
+        pr.tree = t;
+        pr.pos = base_t + nd.idx;
+        pr.node = split ? encode_split(r.feature, base_t + cnt_t + 2u * local, r.thr_bits) : encode_leaf(r.v);
+        a.packed[j] = pr;
+    }
+    if (split) {
+        L.tree = t; L.idx = 2u * local; L.start = nd.start; L.len = r.lenL; L.n = r.nL; L.pad = 0u; L.S = r.v;
+        Rn.tree = t; Rn.idx = 2u * local + 1u; Rn.start = nd.start + r.lenL; Rn.len = nd.len - r.lenL;
+        Rn.n = nd.n - r.nL; Rn.pad = 0u; Rn.S = nd.S - r.v;
+        a.next[2u * g] = L;
+        a.next[2u * g + 1u] = Rn;
+    }
+    push_list(a.small_list, &a.counters[0], split && L.len <= (uint32_t)kSmallNodeRows, (int32_t)(2u * g));
+    push_list(a.big_list, &a.counters[1], split && L.len > (uint32_t)kSmallNodeRows, (int32_t)(2u * g));
+    push_list(a.small_list, &a.counters[0], split && Rn.len <= (uint32_t)kSmallNodeRows, (int32_t)(2u * g + 1u));
+    push_list(a.big_list, &a.counters[1], split && Rn.len > (uint32_t)kSmallNodeRows, (int32_t)(2u * g + 1u));
+
+    const bool evald = active && r.feature != -2;
+    const bool small = nd.len <= (uint32_t)kSmallNodeRows;
+    unsigned long long v[6] = {evald ? nd.len : 0ull, split ? nd.len : 0ull, evald ? 1ull : 0ull,
+                               (evald && small) ? 1ull : 0ull, (evald && small) ? nd.len : 0ull,
+                               (split && small) ? nd.len : 0ull};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) red[k][warp] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        unsigned long long s = 0;
+        for (int w = 0; w < 8; ++w) s += red[threadIdx.x][w];
+        if (s) atomicAdd(&a.stats->rows_evaluated + threadIdx.x, s);   // GrowStats field order
+    }
+}
+
+__global__ void tree_update_kernel(const uint32_t *tree_off, uint32_t *tree_base, const uint32_t *excl,
+                                   uint32_t *next_tree_off, int T)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > T) return;
+    if (t < T) tree_base[t] += tree_off[t + 1] - tree_off[t];
+    next_tree_off[t] = 2u * excl[tree_off[t]];
+}
+
+__global__ void iota_kernel(uint32_t *v, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= n) v[i] = (uint32_t)i;
+}
+
+__global__ void pack_kernel(const PackedRec *packed, int64_t n, uint64_t *const *tree_dst)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const PackedRec p = packed[i];
+    tree_dst[p.tree][p.pos] = p.node;
+}
+
+// a tree with an odd node count is padded by one never-reached leaf of value 0
+__global__ void pad_kernel(const uint32_t *counts, int64_t T, uint64_t *const *tree_dst)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const uint32_t c = counts[t];
+    if (c & 1u) tree_dst[t][c] = 1ull << 63;
+}
+
+__global__ void check_y_kernel(const int64_t *y, int64_t n, uint32_t *err)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long long v = y[i];
+    if (v > AIWCRF_MAX_ABS_Y || v < -AIWCRF_MAX_ABS_Y) atomicOr(err, kErrY);
+}
+
+// ------------------------------------------------------------------------------------------
+// host driver
+// ------------------------------------------------------------------------------------------
+namespace {
+
+struct DevBuf {                // stream-ordered scratch allocation
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+class Scratch {
+public:
+    explicit Scratch(cudaStream_t s) : s_(s) {}
+    ~Scratch() { release(); }
+    template <class T>
+    T *get(size_t count, int *rc)
+    {
+        void *p = nullptr;
+        const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+        cudaError_t e = cudaMallocAsync(&p, bytes, s_);
+        if (e != cudaSuccess) {
+            *rc = fail(AIWCRF_E_OOM, std::string("device allocation of ") + std::to_string(bytes) +
+                                         " bytes failed: " + cudaGetErrorString(e));
+            return nullptr;
+        }
+        bufs_.push_back(p);
+        return static_cast<T *>(p);
+    }
+    void drop(void *p)
+    {
+        for (auto &b : bufs_)
+            if (b == p) { cudaFreeAsync(b, s_); b = nullptr; }
+    }
+    void release()
+    {
+        for (auto b : bufs_)
+            if (b) cudaFreeAsync(b, s_);
+        bufs_.clear();
+    }
+
+private:
+    cudaStream_t s_;
+    std::vector<void *> bufs_;
+};
+
+#define AIWCRF_LAUNCH_CHECK(what)                                   \
+    do {                                                            \
+        count_launches(1);                                          \
+        cudaError_t e_ = cudaGetLastError();                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);          \
+    } while (0)
+
+#define AIWCRF_CUDA(call)                                           \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);         \
+    } while (0)
+
+int check_err_flags(uint32_t err)
+{
+    if (err & kErrNaN) return fail(AIWCRF_E_NAN_INPUT, "NaN in the training features");
+    if (err & kErrY) return fail(AIWCRF_E_INVALID_ARG, "a target value exceeds |y| <= 2^40");
+    if (err & kErrCard) return fail(AIWCRF_E_LIMIT, "a feature column has more than 65,536 distinct values");
+    if (err & kErrBootOverflow) return fail(AIWCRF_E_LIMIT, "a bootstrap multiplicity exceeded 255");
+    if (err & kErrTimeout) return fail(AIWCRF_E_TIMEOUT, "a bounded device wait gave up");
+    return AIWCRF_OK;
+}
+
+}  // namespace
+
+int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, int64_t N, int32_t F,
+              const std::vector<int64_t> &sub_off, const int32_t *d_sub_rows, int32_t G,
+              cudaStream_t s, std::vector<aiwcrf_forest *> &out)
+{
+    int rc = AIWCRF_OK;
+    Scratch sc(s);
+    const int64_t Tper = p.num_trees;
+    const int64_t T = Tper * (int64_t)G;
+    if (T > (int64_t)AIWCRF_MAX_TREES * 16)
+        return fail(AIWCRF_E_LIMIT, "too many trees in one batch");
+
+    int device = 0;
+    AIWCRF_CUDA(cudaGetDevice(&device));
+    int max_smem_optin = 0;
+    AIWCRF_CUDA(cudaDeviceGetAttribute(&max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+
+    // per-tree pools
+    std::vector<int64_t> h_pool_off((size_t)T);
+    std::vector<uint32_t> h_pool_len((size_t)T), h_rng((size_t)T);
+    int64_t row_cap = 1;
+    for (int32_t g = 0; g < G; ++g) {
+        const int64_t off = d_sub_rows ? sub_off[(size_t)g] : -1;
+        const int64_t len = d_sub_rows ? sub_off[(size_t)g + 1] - sub_off[(size_t)g] : N;
+        row_cap = std::max(row_cap, len);
+        for (int64_t k = 0; k < Tper; ++k) {
+            const size_t t = (size_t)(g * Tper + k);
+            h_pool_off[t] = off;
+            h_pool_len[t] = (uint32_t)len;
+            h_rng[t] = (uint32_t)(p.first_tree + k);
+        }
+    }
+
+    uint32_t *d_err = sc.get<uint32_t>(1, &rc); if (rc) return rc;
+    GrowStats *d_stats = sc.get<GrowStats>(1, &rc); if (rc) return rc;
+    uint32_t *d_counters = sc.get<uint32_t>(4, &rc); if (rc) return rc;
+    AIWCRF_CUDA(cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s));
+    AIWCRF_CUDA(cudaMemsetAsync(d_stats, 0, sizeof(GrowStats), s));
+    AIWCRF_CUDA(cudaMemsetAsync(d_counters, 0, 4 * sizeof(uint32_t), s));
+
+    // a1: rank
+    uint16_t *d_R = sc.get<uint16_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
+    float *d_vals = sc.get<float>((size_t)F * (size_t)N, &rc); if (rc) return rc;
+    uint32_t *d_card = sc.get<uint32_t>((size_t)F, &rc); if (rc) return rc;
+    {
+        uint32_t *kA = sc.get<uint32_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
+        uint32_t *iA = sc.get<uint32_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
+        uint32_t *kB = sc.get<uint32_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
+        uint32_t *iB = sc.get<uint32_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
+        const int64_t yblocks = (N + 255) / 256;
+        check_y_kernel<<<(unsigned)yblocks, 256, 0, s>>>(dy, N, d_err);
+        AIWCRF_LAUNCH_CHECK("check_y_kernel");
+        prof_begin(s, kProfRank);
+        rank_kernel<<<F, kRankThreads, 0, s>>>(dX, N, kA, iA, kB, iB, d_R, d_vals, d_card, d_err);
+        AIWCRF_LAUNCH_CHECK("rank_kernel");
+        prof_end(s, kProfRank);
+        sc.drop(kA); sc.drop(iA); sc.drop(kB); sc.drop(iB);
+    }
+
+    // a2: bootstrap
+    int64_t *d_pool_off = sc.get<int64_t>((size_t)T, &rc); if (rc) return rc;
+    uint32_t *d_pool_len = sc.get<uint32_t>((size_t)T, &rc); if (rc) return rc;
+    uint32_t *d_rng = sc.get<uint32_t>((size_t)T, &rc); if (rc) return rc;
+    AIWCRF_CUDA(cudaMemcpyAsync(d_pool_off, h_pool_off.data(), sizeof(int64_t) * (size_t)T, cudaMemcpyHostToDevice, s));
+    AIWCRF_CUDA(cudaMemcpyAsync(d_pool_len, h_pool_len.data(), sizeof(uint32_t) * (size_t)T, cudaMemcpyHostToDevice, s));
+    AIWCRF_CUDA(cudaMemcpyAsync(d_rng, h_rng.data(), sizeof(uint32_t) * (size_t)T, cudaMemcpyHostToDevice, s));
+
+    uint32_t *rows_a = sc.get<uint32_t>((size_t)T * (size_t)row_cap, &rc); if (rc) return rc;
+    uint32_t *rows_b = sc.get<uint32_t>((size_t)T * (size_t)row_cap, &rc); if (rc) return rc;
+
+    size_t node_cap = (size_t)std::max<int64_t>(T, 1024);
+    NodeRec *nodes_cur = sc.get<NodeRec>(node_cap, &rc); if (rc) return rc;
+    NodeRec *nodes_nxt = sc.get<NodeRec>(2 * node_cap, &rc); if (rc) return rc;
+    size_t nxt_cap = 2 * node_cap;
+    int32_t *small_list = sc.get<int32_t>(node_cap, &rc); if (rc) return rc;
+    int32_t *big_list = sc.get<int32_t>(node_cap, &rc); if (rc) return rc;
+    size_t list_cap = node_cap;
+
+    {
+        const int boot_smem_words = std::min<int>((max_smem_optin - 1024) / 4, 56 * 1024);
+        const uint32_t words = (uint32_t)((row_cap + 3) / 4);
+        uint32_t *gcnt = nullptr;
+        int64_t gstride = 0;
+        if (p.bootstrap && (int)words > boot_smem_words) {
+            gstride = words;
+            gcnt = sc.get<uint32_t>((size_t)T * (size_t)words, &rc); if (rc) return rc;
+        }
+        const int smem_bytes = p.bootstrap ? (int)std::min<int64_t>((int64_t)words, boot_smem_words) * 4 : 0;
+        AIWCRF_CUDA(cudaFuncSetAttribute(bootstrap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         std::max(smem_bytes, 1)));
+        BootArgs ba;
+        ba.tree_pool_off = d_pool_off; ba.tree_pool_len = d_pool_len; ba.tree_rng = d_rng;
+        ba.sub_rows = d_sub_rows; ba.y = dy; ba.seed_lo = (uint32_t)p.seed; ba.seed_hi = (uint32_t)(p.seed >> 32);
+        ba.bootstrap = p.bootstrap; ba.gcnt = gcnt; ba.gcnt_stride = gstride;
+        ba.smem_words = (gcnt != nullptr) ? 0 : boot_smem_words;
+        ba.rows_out = rows_a; ba.row_cap = row_cap; ba.root = nodes_cur;
+        ba.small_list = small_list; ba.big_list = big_list; ba.counters = d_counters; ba.err = d_err;
+        prof_begin(s, kProfBoot);
+        bootstrap_kernel<<<(unsigned)T, kBootThreads, smem_bytes, s>>>(ba);
+        AIWCRF_LAUNCH_CHECK("bootstrap_kernel");
+        prof_end(s, kProfBoot);
+    }
+
+    // per-tree level bookkeeping
+    uint32_t *tree_off = sc.get<uint32_t>((size_t)T + 1, &rc); if (rc) return rc;
+    uint32_t *tree_off_nxt = sc.get<uint32_t>((size_t)T + 1, &rc); if (rc) return rc;
+    uint32_t *tree_base = sc.get<uint32_t>((size_t)T, &rc); if (rc) return rc;
+    iota_kernel<<<(unsigned)((T + 256) / 256), 256, 0, s>>>(tree_off, (int)T);
+    AIWCRF_LAUNCH_CHECK("iota_kernel");
+    AIWCRF_CUDA(cudaMemsetAsync(tree_base, 0, sizeof(uint32_t) * (size_t)T, s));
+
+    size_t packed_cap = (size_t)std::max<int64_t>(4 * T, 4096);
+    PackedRec *packed = sc.get<PackedRec>(packed_cap, &rc); if (rc) return rc;
+    size_t packed_n = 0;
+
+    SplitRes *res = sc.get<SplitRes>(node_cap, &rc); if (rc) return rc;
+    size_t res_cap = node_cap;
+    uint32_t *excl = sc.get<uint32_t>(node_cap + 1, &rc); if (rc) return rc;
+    size_t excl_cap = node_cap + 1;
+    uint32_t *block_sums = sc.get<uint32_t>(node_cap / kScanTile + 2, &rc); if (rc) return rc;
+    size_t bs_cap = node_cap / kScanTile + 2;
+
+    uint32_t *h_cnt = nullptr;
+    AIWCRF_CUDA(cudaMallocHost(&h_cnt, 8 * sizeof(uint32_t)));
+    struct HostFree { uint32_t *p; ~HostFree() { if (p) cudaFreeHost(p); } } hf{h_cnt};
+
+    // counts of the root depth
+    AIWCRF_CUDA(cudaMemcpyAsync(h_cnt, d_counters, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    AIWCRF_CUDA(cudaMemcpyAsync(h_cnt + 2, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    AIWCRF_CUDA(cudaStreamSynchronize(s));
+    if ((rc = check_err_flags(h_cnt[2])) != AIWCRF_OK) return rc;
+    uint32_t n_small = h_cnt[0], n_big = h_cnt[1];
+    int64_t C = T;
+
+    const int bin_cap = 3072;
+    const int big_smem = bin_cap * 16;
+    AIWCRF_CUDA(cudaFuncSetAttribute(level_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem));
+
+    LevelArgs la;
+    la.row_cap = row_cap; la.R = d_R; la.vals = d_vals; la.card = d_card; la.N = N; la.y = dy;
+    la.tree_rng = d_rng; la.F = F; la.mtry = p.mtry; la.min_node = p.min_node_size;
+    la.max_depth = p.max_depth; la.seed_lo = (uint32_t)p.seed; la.seed_hi = (uint32_t)(p.seed >> 32);
+
+    uint32_t *rin = rows_a, *rout = rows_b;
+    int depth = 0;
+    for (; C > 0; ++depth) {
+        // capacity for this depth's results and the next depth's nodes
+        if ((size_t)C > res_cap) {
+            sc.drop(res);
+            res_cap = (size_t)C * 2;
+            res = sc.get<SplitRes>(res_cap, &rc); if (rc) return rc;
+        }
+        if ((size_t)C + 1 > excl_cap) {
+            sc.drop(excl);
+            excl_cap = (size_t)C * 2 + 1;
+            excl = sc.get<uint32_t>(excl_cap, &rc); if (rc) return rc;
+        }
+        const int nblocks = (int)((C + kScanTile - 1) / kScanTile);
+        if ((size_t)nblocks + 1 > bs_cap) {
+            sc.drop(block_sums);
+            bs_cap = (size_t)nblocks * 2 + 2;
+            block_sums = sc.get<uint32_t>(bs_cap, &rc); if (rc) return rc;
+        }
+        if ((size_t)(2 * C) > nxt_cap) {
+            sc.drop(nodes_nxt);
+            nxt_cap = (size_t)C * 4;
+            nodes_nxt = sc.get<NodeRec>(nxt_cap, &rc); if (rc) return rc;
+        }
+        if ((size_t)(2 * C) > list_cap) {
+            // lists are read by this depth's kernels and rewritten by its finalize: keep both
+            int32_t *ns = sc.get<int32_t>((size_t)C * 4, &rc); if (rc) return rc;
+            int32_t *nb = sc.get<int32_t>((size_t)C * 4, &rc); if (rc) return rc;
+            AIWCRF_CUDA(cudaMemcpyAsync(ns, small_list, sizeof(int32_t) * n_small, cudaMemcpyDeviceToDevice, s));
+            AIWCRF_CUDA(cudaMemcpyAsync(nb, big_list, sizeof(int32_t) * n_big, cudaMemcpyDeviceToDevice, s));
+            sc.drop(small_list); sc.drop(big_list);
+            small_list = ns; big_list = nb;
+            list_cap = (size_t)C * 4;
+        }
+        if (packed_n + (size_t)C > packed_cap) {
+            size_t ncap = std::max(packed_cap * 2, packed_n + (size_t)C);
+            PackedRec *np = sc.get<PackedRec>(ncap, &rc); if (rc) return rc;
+            AIWCRF_CUDA(cudaMemcpyAsync(np, packed, sizeof(PackedRec) * packed_n, cudaMemcpyDeviceToDevice, s));
+            sc.drop(packed);
+            packed = np;
+            packed_cap = ncap;
+        }
+
+        la.nodes = nodes_cur; la.rows_in = rin; la.rows_out = rout; la.depth = depth; la.res = res;
+        if (n_big > 0) {
+            la.list = big_list; la.list_n = (int32_t)n_big;
+            prof_begin(s, kProfLevelBig);
+            level_big_kernel<<<n_big, kBigThreads, big_smem, s>>>(la, bin_cap);
+            AIWCRF_LAUNCH_CHECK("level_big_kernel");
+            prof_end(s, kProfLevelBig);
+        }
+        if (n_small > 0) {
+            la.list = small_list; la.list_n = (int32_t)n_small;
+            const unsigned grid = (n_small + kSmallThreads / 32 - 1) / (kSmallThreads / 32);
+            prof_begin(s, kProfLevelSmall);
+            level_small_kernel<<<grid, kSmallThreads, 0, s>>>(la);
+            AIWCRF_LAUNCH_CHECK("level_small_kernel");
+            prof_end(s, kProfLevelSmall);
+        }
+
+        prof_begin(s, kProfScan);
+        scan_reduce_kernel<<<nblocks, kScanThreads, 0, s>>>(res, (int)C, block_sums);
+        scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(block_sums, nblocks);
+        scan_write_kernel<<<nblocks, kScanThreads, 0, s>>>(res, (int)C, block_sums, nblocks, excl);
+        count_launches(2);
+        AIWCRF_LAUNCH_CHECK("scan kernels");
+        prof_end(s, kProfScan);
+
+        AIWCRF_CUDA(cudaMemsetAsync(d_counters, 0, 2 * sizeof(uint32_t), s));
+        FinalArgs fa;
+        fa.nodes = nodes_cur; fa.res = res; fa.excl = excl; fa.tree_off = tree_off; fa.tree_base = tree_base;
+        fa.n = (int)C; fa.next = nodes_nxt; fa.small_list = small_list; fa.big_list = big_list;
+        fa.counters = d_counters; fa.packed = packed + packed_n; fa.stats = d_stats;
+        prof_begin(s, kProfFinalize);
+        finalize_kernel<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(fa);
+        AIWCRF_LAUNCH_CHECK("finalize_kernel");
+        tree_update_kernel<<<(unsigned)((T + 256) / 256), 256, 0, s>>>(tree_off, tree_base, excl, tree_off_nxt, (int)T);
+        AIWCRF_LAUNCH_CHECK("tree_update_kernel");
+        prof_end(s, kProfFinalize);
+        packed_n += (size_t)C;
+
+        AIWCRF_CUDA(cudaMemcpyAsync(h_cnt, d_counters, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        AIWCRF_CUDA(cudaMemcpyAsync(h_cnt + 2, excl + C, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        AIWCRF_CUDA(cudaStreamSynchronize(s));
+        n_small = h_cnt[0];
+        n_big = h_cnt[1];
+        C = 2 * (int64_t)h_cnt[2];
+
+        std::swap(nodes_cur, nodes_nxt);
+        std::swap(node_cap, nxt_cap);
+        std::swap(rin, rout);
+        std::swap(tree_off, tree_off_nxt);
+    }
+
+    AIWCRF_CUDA(cudaMemcpyAsync(h_cnt, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    std::vector<uint32_t> h_tot((size_t)T);
+    AIWCRF_CUDA(cudaMemcpyAsync(h_tot.data(), tree_base, sizeof(uint32_t) * (size_t)T, cudaMemcpyDeviceToHost, s));
+    GrowStats hs;
+    AIWCRF_CUDA(cudaMemcpyAsync(&hs, d_stats, sizeof(GrowStats), cudaMemcpyDeviceToHost, s));
+    AIWCRF_CUDA(cudaStreamSynchronize(s));
+    if ((rc = check_err_flags(h_cnt[0])) != AIWCRF_OK) return rc;
+
+    // pack: one buffer per forest, trees padded to an even node count (16-byte aligned)
+    std::vector<aiwcrf_forest *> forests((size_t)G, nullptr);
+    struct Guard {
+        std::vector<aiwcrf_forest *> *v;
+        bool keep = false;
+        ~Guard() {
+            if (keep) return;
+            for (auto f : *v) {
+                if (!f) continue;
+                cudaFree(f->d_nodes); cudaFree(f->d_tree_off);
+                delete f;
+            }
+        }
+    } guard{&forests};
+    std::vector<uint64_t *> h_dst((size_t)T);
+    for (int32_t g = 0; g < G; ++g) {
+        aiwcrf_forest *fr = new aiwcrf_forest();
+        forests[(size_t)g] = fr;
+        fr->F = F; fr->T = Tper; fr->device = device;
+        fr->tree_off.assign((size_t)Tper + 1, 0);
+        for (int64_t k = 0; k < Tper; ++k) {
+            const int64_t cnt = h_tot[(size_t)(g * Tper + k)];
+            fr->tree_off[(size_t)k + 1] = fr->tree_off[(size_t)k] + ((cnt + 1) & ~(int64_t)1);
+            fr->max_tree_nodes = std::max(fr->max_tree_nodes, (cnt + 1) & ~(int64_t)1);
+        }
+        fr->num_nodes = fr->tree_off[(size_t)Tper];
+        AIWCRF_CUDA(cudaMalloc(&fr->d_nodes, sizeof(uint64_t) * (size_t)std::max<int64_t>(fr->num_nodes, 2)));
+        AIWCRF_CUDA(cudaMalloc(&fr->d_tree_off, sizeof(int64_t) * (size_t)(Tper + 1)));
+        AIWCRF_CUDA(cudaMemcpyAsync(fr->d_tree_off, fr->tree_off.data(), sizeof(int64_t) * (size_t)(Tper + 1),
+                                    cudaMemcpyHostToDevice, s));
+        for (int64_t k = 0; k < Tper; ++k) h_dst[(size_t)(g * Tper + k)] = fr->d_nodes + fr->tree_off[(size_t)k];
+        fr->stats.num_trees = Tper;
+        fr->stats.total_nodes = 0;
+        for (int64_t k = 0; k < Tper; ++k) fr->stats.total_nodes += h_tot[(size_t)(g * Tper + k)];
+        fr->stats.levels = depth;
+        fr->stats.n_features = F;
+        fr->stats.mtry = p.mtry;
+        if (G == 1) {
+            fr->stats.rows_evaluated = (int64_t)hs.rows_evaluated;
+            fr->stats.rows_partitioned = (int64_t)hs.rows_partitioned;
+            fr->stats.nodes_evaluated = (int64_t)hs.nodes_evaluated;
+            fr->stats.nodes_small = (int64_t)hs.nodes_small;
+            fr->stats.rows_evaluated_small = (int64_t)hs.rows_evaluated_small;
+            fr->stats.rows_partitioned_small = (int64_t)hs.rows_partitioned_small;
+        }
+    }
+    uint64_t **d_dst = sc.get<uint64_t *>((size_t)T, &rc); if (rc) return rc;
+    AIWCRF_CUDA(cudaMemcpyAsync(d_dst, h_dst.data(), sizeof(uint64_t *) * (size_t)T, cudaMemcpyHostToDevice, s));
+    prof_begin(s, kProfPack);
+    pack_kernel<<<(unsigned)((packed_n + 255) / 256), 256, 0, s>>>(packed, (int64_t)packed_n, d_dst);
+    AIWCRF_LAUNCH_CHECK("pack_kernel");
+    pad_kernel<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(tree_base, T, d_dst);
+    AIWCRF_LAUNCH_CHECK("pad_kernel");
+    prof_end(s, kProfPack);
+    sc.release();
+    AIWCRF_CUDA(cudaStreamSynchronize(s));
+    guard.keep = true;
+    out = forests;
+    return AIWCRF_OK;
+}
+
+}  // namespace aiwcrf

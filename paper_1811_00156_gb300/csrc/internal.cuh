@@ -1,0 +1,302 @@
+// internal.cuh -- types and device helpers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/aiwcrf.h"
+
+namespace aiwcrf {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr int kSmallNodeRows = 32;          // nodes with <= 32 distinct rows are searched by a warp
+constexpr uint32_t kRankSentinel = 65536;   // larger than any rank (ranks are < 65536)
+constexpr uint32_t kRowBits = 24;           // row entry = row | (w << 24)
+constexpr uint32_t kRowMask = (1u << kRowBits) - 1;
+constexpr uint32_t kDomBoot = 0xB007u;      // Philox counter domain of bootstrap draws
+constexpr uint32_t kDomMtry = 0x3779u;      // Philox counter domain of mtry keys
+
+// device error flag bits (aggregated with atomicOr)
+constexpr uint32_t kErrNaN = 1u;
+constexpr uint32_t kErrCard = 2u;           // more than 65,536 distinct values in a column
+constexpr uint32_t kErrBootOverflow = 4u;   // a bootstrap multiplicity above 255
+constexpr uint32_t kErrTimeout = 8u;        // a bounded mbarrier wait gave up
+constexpr uint32_t kErrY = 16u;             // |y| > 2^40
+constexpr uint32_t kErrTree = 32u;          // malformed tree met during a walk
+
+// ------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds; each round multiplies counter
+// words 0 and 2 by the two round multipliers, XORs the high halves into words 1 and 3 with
+// the round key and swaps; the key advances by the Weyl constants between rounds.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t a = c.x, b = c.z;
+        const uint32_t hx = __umulhi(0xD2511F53u, a), lx = 0xD2511F53u * a;
+        const uint32_t hz = __umulhi(0xCD9E8D57u, b), lz = 0xCD9E8D57u * b;
+        c = make_uint4(hz ^ c.y ^ k0, lz, hx ^ c.w ^ k1, lx);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t uint4_word(uint4 v, int w)
+{
+    return w == 0 ? v.x : (w == 1 ? v.y : (w == 2 ? v.z : v.w));
+}
+
+// ------------------------------------------------------------------------------------------
+// Split candidates. Within a node (n = sum w, S = sum w*y) the CART gain of "left = ranks <= r"
+// is G = S_L^2/n_L + S_R^2/n_R = S^2/n + delta^2 / (n n_L n_R), delta = n S_L - n_L S.
+// So the search maximises D = delta^2 / (n_L n_R), exactly: a float estimate h = |delta| /
+// sqrt(n_L n_R) (relative error < 2^-20) decides whenever two candidates differ by more than
+// 2^-16, and 256-bit integer cross products decide the rest. Ties: lower feature, then lower
+// rank. A split needs delta != 0 (strict gain over the parent).
+// ------------------------------------------------------------------------------------------
+struct Cand {
+    float h;          // < 0: no candidate
+    int32_t f;
+    uint32_t r;
+    uint32_t nL;      // sum w on the left
+    uint32_t lenL;    // distinct rows on the left
+    int64_t SL;       // sum w*y on the left
+};
+
+__device__ __forceinline__ Cand cand_none()
+{
+    Cand c;
+    c.h = -1.0f; c.f = 0x7FFFFFFF; c.r = 0xFFFFFFFFu; c.nL = 0; c.lenL = 0; c.SL = 0;
+    return c;
+}
+
+typedef unsigned __int128 u128_t;
+typedef __int128 i128_t;
+
+__device__ __forceinline__ i128_t cand_delta(uint32_t n, int64_t S, uint32_t nL, int64_t SL)
+{
+    return (i128_t)n * (i128_t)SL - (i128_t)nL * (i128_t)S;
+}
+
+__device__ __forceinline__ float cand_h(i128_t delta, uint32_t n, uint32_t nL)
+{
+    const u128_t a = delta < 0 ? (u128_t)(-delta) : (u128_t)delta;
+    const uint64_t hi = (uint64_t)(a >> 64), lo = (uint64_t)a;
+    const float fa = __fadd_rn(__fmul_rn(__ull2float_rn(hi), 18446744073709551616.0f), __ull2float_rn(lo));
+    const uint64_t den = (uint64_t)nL * (uint64_t)(n - nL);
+    return __fdiv_rn(fa, __fsqrt_rn(__ull2float_rn(den)));
+}
+
+// 256-bit value as four 64-bit limbs, least significant first
+struct U256 { uint64_t w[4]; };
+
+__device__ __forceinline__ U256 mul_128x128(u128_t a, u128_t b)
+{
+    const uint64_t a0 = (uint64_t)a, a1 = (uint64_t)(a >> 64);
+    const uint64_t b0 = (uint64_t)b, b1 = (uint64_t)(b >> 64);
+    const u128_t p00 = (u128_t)a0 * b0, p01 = (u128_t)a0 * b1;
+    const u128_t p10 = (u128_t)a1 * b0, p11 = (u128_t)a1 * b1;
+    U256 r;
+    r.w[0] = (uint64_t)p00;
+    u128_t mid = (p00 >> 64) + (uint64_t)p01 + (uint64_t)p10;          // < 3 * 2^64
+    r.w[1] = (uint64_t)mid;
+    u128_t hi = (mid >> 64) + (p01 >> 64) + (p10 >> 64) + (uint64_t)p11;
+    r.w[2] = (uint64_t)hi;
+    r.w[3] = (uint64_t)(hi >> 64) + (uint64_t)(p11 >> 64);
+    return r;
+}
+
+__device__ __forceinline__ U256 mul_256x64(U256 a, uint64_t b)
+{
+    U256 r;
+    u128_t carry = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const u128_t cur = (u128_t)a.w[i] * b + carry;
+        r.w[i] = (uint64_t)cur;
+        carry = cur >> 64;
+    }
+    return r;    // the callers' products are below 2^220
+}
+
+__device__ __forceinline__ int cmp_256(const U256 &a, const U256 &b)
+{
+#pragma unroll
+    for (int i = 3; i >= 0; --i) {
+        if (a.w[i] != b.w[i]) return a.w[i] < b.w[i] ? -1 : 1;
+    }
+    return 0;
+}
+
+// true if a is the better candidate: larger D, then lower feature, then lower rank
+static __device__ __noinline__ bool cand_better_exact(const Cand &a, const Cand &b, uint32_t n, int64_t S)
+{
+    if (!(a.nL == b.nL && a.SL == b.SL)) {
+        const i128_t da = cand_delta(n, S, a.nL, a.SL), db = cand_delta(n, S, b.nL, b.SL);
+        const u128_t ua = da < 0 ? (u128_t)(-da) : (u128_t)da;
+        const u128_t ub = db < 0 ? (u128_t)(-db) : (u128_t)db;
+        const uint64_t den_a = (uint64_t)a.nL * (uint64_t)(n - a.nL);
+        const uint64_t den_b = (uint64_t)b.nL * (uint64_t)(n - b.nL);
+        const int c = cmp_256(mul_256x64(mul_128x128(ua, ua), den_b), mul_256x64(mul_128x128(ub, ub), den_a));
+        if (c != 0) return c > 0;
+    }
+    if (a.f != b.f) return a.f < b.f;
+    return a.r < b.r;
+}
+
+constexpr float kFilterHi = 1.0f + 1.0f / 65536.0f;
+constexpr float kFilterLo = 1.0f - 1.0f / 65536.0f;
+
+__device__ __forceinline__ bool cand_better(const Cand &a, const Cand &b, uint32_t n, int64_t S)
+{
+    if (a.h < 0.0f) return false;
+    if (b.h < 0.0f) return true;
+    if (a.h > b.h * kFilterHi) return true;
+    if (a.h < b.h * kFilterLo) return false;
+    return cand_better_exact(a, b, n, S);
+}
+
+__device__ __forceinline__ Cand shfl_cand(const Cand &c, int src)
+{
+    Cand o;
+    o.h = __shfl_sync(kFull, c.h, src);
+    o.f = __shfl_sync(kFull, c.f, src);
+    o.r = __shfl_sync(kFull, c.r, src);
+    o.nL = __shfl_sync(kFull, c.nL, src);
+    o.lenL = __shfl_sync(kFull, c.lenL, src);
+    o.SL = (int64_t)__shfl_sync(kFull, (long long)c.SL, src);
+    return o;
+}
+
+// Warp argmax under cand_better, the same result in every lane. Float max first; every lane
+// whose estimate is within the filter margin of it is a contender (the true best always is);
+// contenders are then compared exactly, in lane order.
+__device__ __forceinline__ Cand warp_best(const Cand &mine, uint32_t n, int64_t S)
+{
+    float hm = mine.h;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) hm = fmaxf(hm, __shfl_xor_sync(kFull, hm, off));
+    if (hm < 0.0f) return cand_none();
+    const uint32_t cont = __ballot_sync(kFull, mine.h >= 0.0f && mine.h >= hm * kFilterLo);
+    int src = __ffs(cont) - 1;
+    Cand best = shfl_cand(mine, src);
+    uint32_t rest = cont & (cont - 1);
+    while (rest) {
+        src = __ffs(rest) - 1;
+        rest &= rest - 1;
+        const Cand o = shfl_cand(mine, src);
+        if (cand_better_exact(o, best, n, S)) best = o;
+    }
+    return best;
+}
+
+// Leaf value round(S/n), half up: floor((2S + n) / (2n)).
+__device__ __forceinline__ int64_t round_mean(int64_t S, uint32_t n)
+{
+    const i128_t a = (i128_t)2 * S + n, b = (i128_t)2 * n;
+    i128_t q = a / b;
+    if (a % b != 0 && a < 0) q -= 1;
+    return (int64_t)q;
+}
+
+// ------------------------------------------------------------------------------------------
+// Level-synchronous growth state
+// ------------------------------------------------------------------------------------------
+struct NodeRec {          // an active node of the current depth
+    uint32_t tree;        // forest-batch tree index
+    uint32_t idx;         // BFS index within the depth, within its tree
+    uint32_t start;       // segment start in the tree's row buffer
+    uint32_t len;         // distinct in-bag rows
+    uint32_t n;           // sum of multiplicities
+    uint32_t pad;
+    int64_t S;            // sum of w*y
+};
+
+struct SplitRes {         // outcome of one active node
+    int32_t feature;      // >= 0 split; -1 leaf after a search; -2 leaf without a search
+    uint32_t rank;
+    uint32_t thr_bits;
+    uint32_t nL;
+    uint32_t lenL;
+    uint32_t pad;
+    int64_t v;            // S_L for a split, the leaf value for a leaf
+};
+
+struct PackedRec {        // a finished node waiting for the final packing
+    uint64_t node;        // encoded node (see aiwcrf.h), child index relative to its tree
+    uint32_t tree;
+    uint32_t pos;         // BFS position within the tree
+};
+
+__device__ __forceinline__ uint64_t encode_split(int f, uint32_t left, uint32_t thr_bits)
+{
+    return ((uint64_t)(uint32_t)f << 56) | ((uint64_t)left << 32) | (uint64_t)thr_bits;
+}
+
+__device__ __forceinline__ uint64_t encode_leaf(int64_t v)
+{
+    return (1ull << 63) | ((uint64_t)v & 0x7FFFFFFFFFFFFFFFull);
+}
+
+struct GrowStats {        // device counters of one fit
+    unsigned long long rows_evaluated;
+    unsigned long long rows_partitioned;
+    unsigned long long nodes_evaluated;
+    unsigned long long nodes_small;
+    unsigned long long rows_evaluated_small;
+    unsigned long long rows_partitioned_small;
+};
+
+// ------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------
+enum ProfClass {
+    kProfRank = 0, kProfBoot, kProfLevelBig, kProfLevelSmall, kProfScan, kProfFinalize,
+    kProfPack, kProfPredict, kProfSelect, kProfNum
+};
+
+void prof_begin(cudaStream_t s, int cls);
+void count_launches(int n);      // kernels launched (for aiwcrf_launch_count)
+void prof_end(cudaStream_t s, int cls);
+
+struct Error {
+    int code;
+    std::string msg;
+};
+
+void set_error(int code, const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+}  // namespace aiwcrf
+
+struct aiwcrf_forest {
+    int32_t F = 0;
+    int64_t T = 0;
+    int64_t num_nodes = 0;
+    int64_t max_tree_nodes = 0;
+    int device = 0;
+    uint64_t *d_nodes = nullptr;          // packed nodes
+    int64_t *d_tree_off = nullptr;        // T + 1 offsets (in nodes)
+    std::vector<int64_t> tree_off;        // host copy
+    aiwcrf_fit_stats stats = {};
+};
+
+namespace aiwcrf {
+// implemented in fit.cu / predict.cu
+int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, int64_t N, int32_t F,
+              const std::vector<int64_t> &sub_off, const int32_t *d_sub_rows, int32_t G,
+              cudaStream_t s, std::vector<aiwcrf_forest *> &out);
+int predict_launch(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum,
+                   int64_t *d_pred, uint64_t *d_var, int64_t total_trees, cudaStream_t s);
+int round_mean_launch(const int64_t *d_sum, int64_t Q, int64_t total_trees, int64_t *d_out,
+                      cudaStream_t s);
+int select_launch(const aiwcrf_forest *f, const float *d_kfeat, int32_t K, int32_t size_class,
+                  const int32_t *d_dev, int32_t D, int32_t *d_best, int64_t *d_pred,
+                  float *d_scratch_q, int64_t *d_scratch_p, cudaStream_t s);
+}  // namespace aiwcrf

@@ -1,0 +1,267 @@
+"""GPU path vs the CPU oracle, bit for bit, through the C ABI.
+
+Trees are compared node by node in the packed encoding (feature, threshold bits, child index,
+leaf value); predictions, variance numerators and device choices element by element.
+"""
+import concurrent.futures as cf
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1811_00156_gb300 import synth
+from tests.forest_util import assert_tree_equal, gpu_tree, walk_packed
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_1811_00156_gb300 import aiwcrf as A
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def gpu_fit(wl, T, mtry, min_node, max_depth=0, seed=156, bootstrap=True, first_tree=0):
+    return A.aiwcrf_fit(A.params(T, mtry, min_node, max_depth, seed, bootstrap, first_tree), dev(wl.X), dev(wl.y))
+
+
+def gpu_predict(forest, Xq, var=False):
+    Q = Xq.shape[1]
+    out = torch.empty(Q, dtype=torch.int64, device="cuda")
+    ov = torch.empty(2 * Q, dtype=torch.int64, device="cuda") if var else None
+    A.aiwcrf_predict(forest, dev(Xq), out, ov)
+    torch.cuda.synchronize()
+    if var:
+        v = ov.cpu().numpy().view(np.uint64)
+        return out.cpu().numpy(), [int(v[2 * q]) | (int(v[2 * q + 1]) << 64) for q in range(Q)]
+    return out.cpu().numpy()
+
+
+def compare_forest(forest, ref, T, tree_ids=None):
+    dec = A.decode_forest(forest.serialize())
+    assert dec["T"] == T
+    for k in (range(T) if tree_ids is None else tree_ids):
+        assert_tree_equal(gpu_tree(dec, k), ref.tree(k), where=f"tree {k}")
+    return dec
+
+
+def test_aiwc_2220_forest_bit_exact():
+    """2,220 rows, 128 trees, mtry 10, min_node 5: every tree, prediction and variance."""
+    wl = synth.plain_forest_workload()
+    T = 128
+    f = gpu_fit(wl, T, 10, 5)
+    ref = O.fit(wl.X, wl.y, T, 10, 5, seed=156)
+    compare_forest(f, ref, T)
+    p, v = gpu_predict(f, wl.X, var=True)
+    rp, _, rv = ref.predict(wl.X, want_var=True)
+    assert np.array_equal(p, rp)
+    assert v == rv
+    st = f.stats()
+    exp_eval = sum(int(ref.tree(k).nrows[ref.tree(k).evaluated == 1].sum()) for k in range(T))
+    assert st["rows_evaluated"] == exp_eval
+    assert st["total_nodes"] == sum(ref.tree(k).num_nodes for k in range(T))
+
+
+CASES = [
+    # n, F, card, T, mtry, min_node, max_depth, bootstrap, y_levels
+    (1, 4, None, 3, 2, 1, 0, True, None),
+    (2, 3, None, 3, 3, 1, 0, False, None),
+    (32, 5, None, 4, 3, 1, 0, False, None),
+    (33, 5, None, 4, 3, 1, 0, False, None),
+    (257, 7, 9, 6, 3, 2, 0, True, 3),
+    (1000, 32, None, 8, 10, 5, 0, True, None),
+    (1000, 32, 40, 8, 32, 1, 0, True, None),
+    (1500, 1, None, 5, 1, 3, 0, True, None),
+    (777, 3, 5, 5, 1, 2, 3, True, 2),
+    (1200, 40, 30, 5, 17, 4, 0, True, None),
+    (600, 128, 12, 3, 50, 5, 0, True, None),
+    (900, 6, None, 4, 6, 1, 1, False, None),
+    (900, 6, None, 4, 6, 1, 2, True, None),
+    (5000, 12, None, 3, 12, 20, 0, True, None),       # > 3,072 bins: grouped histograms
+    (3000, 4, 2, 6, 2, 1, 0, True, 1),                # binary features, many exact ties
+    (400, 8, 6, 5, 4, 500, 0, True, None),            # min_node above n: every root is a leaf
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "n{}_F{}_c{}_T{}_m{}_mn{}_d{}_b{}_y{}".format(*c))
+def test_small_cases_bit_exact(case):
+    n, F, card, T, mtry, min_node, max_depth, boot, ylev = case
+    wl = synth.small_case(100 + n + F, n, F, card=card, y_levels=ylev)
+    f = gpu_fit(wl, T, mtry, min_node, max_depth, seed=11, bootstrap=boot)
+    ref = O.fit(wl.X, wl.y, T, mtry, min_node, max_depth, seed=11, bootstrap=boot)
+    compare_forest(f, ref, T)
+    Xq = synth.small_case(5 + n, 300, F, card=card).X
+    assert np.array_equal(gpu_predict(f, Xq), ref.predict(Xq)[0])
+
+
+def test_degenerate_inputs():
+    rng = np.random.default_rng(3)
+    # constant features: no candidate anywhere, one leaf per tree
+    X = np.ones((5, 300), np.float32)
+    y = rng.integers(-1 << 40, 1 << 40, 300).astype(np.int64)
+    wl = synth.Workload(X=X, y=y, name="const-x")
+    f = gpu_fit(wl, 4, 3, 1)
+    compare_forest(f, O.fit(X, y, 4, 3, 1, seed=156), 4)
+    # constant target: pure root
+    wl2 = synth.Workload(X=rng.normal(size=(5, 300)).astype(np.float32), y=np.full(300, 12345, np.int64), name="const-y")
+    f2 = gpu_fit(wl2, 4, 3, 1)
+    compare_forest(f2, O.fit(wl2.X, wl2.y, 4, 3, 1, seed=156), 4)
+    # signed zeros and extreme targets
+    X3 = rng.integers(-2, 3, (3, 500)).astype(np.float32)
+    X3[X3 == 0] = np.where(rng.random((X3 == 0).sum()) < 0.5, -0.0, 0.0)
+    y3 = np.where(rng.random(500) < 0.5, 1 << 40, -(1 << 40)).astype(np.int64)
+    wl3 = synth.Workload(X=X3, y=y3, name="zeros")
+    f3 = gpu_fit(wl3, 5, 2, 1)
+    compare_forest(f3, O.fit(X3, y3, 5, 2, 1, seed=156), 5)
+
+
+@pytest.mark.parametrize("Q", [1, 511, 512, 513, 10007])
+def test_predict_ragged_query_counts(Q):
+    wl = synth.plain_forest_workload()
+    f = gpu_fit(wl, 20, 10, 5)
+    ref = O.fit(wl.X, wl.y, 20, 10, 5, seed=156)
+    Xq = synth.queries(Q, seed=Q)
+    p, v = gpu_predict(f, Xq, var=True)
+    rp, _, rv = ref.predict(Xq, want_var=True)
+    assert np.array_equal(p, rp) and v == rv
+
+
+def test_select_device_matches_oracle():
+    wl = synth.plain_forest_workload()
+    f = gpu_fit(wl, 32, 10, 5)
+    ref = O.fit(wl.X, wl.y, 32, 10, 5, seed=156)
+    kfeat = np.ascontiguousarray(synth.queries(64, seed=9)[:30])
+    for size in range(4):
+        best = torch.empty(64, dtype=torch.int32, device="cuda")
+        pred = torch.empty(64 * 15, dtype=torch.int64, device="cuda")
+        A.aiwcrf_select_device(f, dev(kfeat), size, list(range(15)), best, pred)
+        rb, rp = ref.select_device(kfeat, size, list(range(15)))
+        assert np.array_equal(best.cpu().numpy(), rb)
+        assert np.array_equal(pred.cpu().numpy().reshape(64, 15), rp)
+    # a device subset in a shuffled order, host outputs
+    ids = [11, 3, 7, 0]
+    hb = np.zeros(64, np.int32)
+    A.aiwcrf_select_device(f, kfeat, 2, ids, hb)
+    assert np.array_equal(hb, ref.select_device(kfeat, 2, ids)[0])
+
+
+def test_host_buffers_and_serialization_roundtrip():
+    wl = synth.small_case(5, 800, 9, card=20)
+    f_dev = gpu_fit(wl, 6, 4, 2)
+    f_host = A.aiwcrf_fit(A.params(6, 4, 2), wl.X, wl.y)        # numpy host arrays
+    assert f_dev.serialize() == f_host.serialize()
+    g = A.aiwcrf_forest_deserialize(f_dev.serialize())
+    Xq = synth.small_case(6, 999, 9, card=20).X
+    out = np.zeros(999, np.int64)
+    A.aiwcrf_predict(g, Xq, out)                                 # host in, host out
+    assert np.array_equal(out, gpu_predict(f_dev, Xq))
+
+
+def test_tree_sharding_and_partial_sums():
+    wl = synth.small_case(8, 1500, 32, card=50)
+    T = 12
+    full = gpu_fit(wl, T, 10, 5)
+    a = gpu_fit(wl, 5, 10, 5, first_tree=0)
+    b = gpu_fit(wl, T - 5, 10, 5, first_tree=5)
+    da, db, df = (A.decode_forest(x.serialize()) for x in (a, b, full))
+    for k in range(T):
+        src, kk = (da, k) if k < 5 else (db, k - 5)
+        assert np.array_equal(gpu_tree(src, kk), gpu_tree(df, k))
+    Xq = synth.small_case(9, 4000, 32, card=50).X
+    sa = torch.empty(4000, dtype=torch.int64, device="cuda")
+    sb = torch.empty(4000, dtype=torch.int64, device="cuda")
+    A.aiwcrf_predict_sum(a, dev(Xq), sa)
+    A.aiwcrf_predict_sum(b, dev(Xq), sb)
+    out = torch.empty(4000, dtype=torch.int64, device="cuda")
+    A.aiwcrf_round_mean(sa + sb, T, out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), gpu_predict(full, Xq))
+
+
+def test_fit_subsets_equals_per_subset_fits():
+    wl, folds = synth.loko_folds()
+    folds = folds[:5]
+    offs = np.cumsum([0] + [len(tr) for tr, _ in folds]).astype(np.int64)
+    rows = np.concatenate([tr for tr, _ in folds]).astype(np.int32)
+    T = 16
+    forests = A.aiwcrf_fit_subsets(A.params(T, 10, 5), dev(wl.X), dev(wl.y), offs, dev(rows))
+    for g, (tr, te) in enumerate(folds):
+        Xs = np.ascontiguousarray(wl.X[:, tr])
+        ref = O.fit(Xs, wl.y[tr], T, 10, 5, seed=156)
+        compare_forest(forests[g], ref, T)
+        Xt = np.ascontiguousarray(wl.X[:, te])
+        assert np.array_equal(gpu_predict(forests[g], Xt), ref.predict(Xt)[0])
+
+
+def test_error_codes():
+    wl = synth.small_case(1, 100, 4)
+    X = wl.X.copy()
+    X[2, 7] = np.nan
+    with pytest.raises(A.AiwcrfError) as e:
+        A.aiwcrf_fit(A.params(2, 2, 1), dev(X), dev(wl.y))
+    assert e.value.code == -2
+    y = wl.y.copy()
+    y[3] = (1 << 40) + 1
+    with pytest.raises(A.AiwcrfError) as e:
+        A.aiwcrf_fit(A.params(2, 2, 1), dev(wl.X), dev(y))
+    assert e.value.code == -1
+    big = synth.small_case(2, 70000, 1)                 # 70,000 distinct values in one column
+    with pytest.raises(A.AiwcrfError) as e:
+        A.aiwcrf_fit(A.params(1, 1, 1), dev(big.X), dev(big.y))
+    assert e.value.code == -8
+    # the library stays usable after errors
+    f = gpu_fit(wl, 2, 2, 1)
+    assert f.info()["num_trees"] == 2
+
+
+def _oracle_trees_parallel(X, y, T, mtry, min_node, seed, workers=16):
+    chunks = [(t0, min(T, t0 + 8)) for t0 in range(0, T, 8)]
+    with cf.ThreadPoolExecutor(workers) as ex:
+        parts = list(ex.map(lambda c: O.fit(X, y, T, mtry, min_node, seed=seed, t0=c[0], t1=c[1]), chunks))
+    return parts
+
+
+def test_aiwc_111000_full_size():
+    """111,000 rows x 500 trees and 1,000,000 queries, the benchmark's launch configuration.
+    Trees 0, 1, 255, 499 are grown alone by the oracle and compared node by node; the full
+    forest's predictions are checked on a query sample by walking the packed trees, and the
+    variance numerators of the sample by their definition."""
+    wl = synth.scaled_forest_workload()
+    T = 500
+    f = gpu_fit(wl, T, 10, 5)
+    dec = A.decode_forest(f.serialize())
+    for t in (0, 1, 255, 499):
+        ref = O.fit(wl.X, wl.y, T, 10, 5, seed=156, t0=t, t1=t + 1)
+        assert_tree_equal(gpu_tree(dec, t), ref.tree(0), where=f"tree {t}")
+    Q = 1_000_000
+    Xq = synth.queries(Q)
+    p, v = gpu_predict(f, Xq, var=True)
+    rng = np.random.default_rng(0)
+    for q in rng.choice(Q, 40, replace=False):
+        leaves = [walk_packed(gpu_tree(dec, t), Xq[:, q]) for t in range(T)]
+        P = sum(leaves)
+        assert p[q] == (2 * P + T) // (2 * T)
+        assert v[q] == T * sum(x * x for x in leaves) - P * P
+
+
+def test_aiwc_111000_full_forest_predictions_vs_oracle():
+    """The whole 500-tree oracle forest (grown tree-parallel on the host cores) against the GPU
+    forest on a 20,000-query sample of the 1,000,000-query workload."""
+    wl = synth.scaled_forest_workload()
+    T = 500
+    f = gpu_fit(wl, T, 10, 5)
+    parts = _oracle_trees_parallel(wl.X, wl.y, T, 10, 5, 156)
+    Xq = np.ascontiguousarray(synth.queries(1_000_000)[:, ::50])
+    P = sum(part.predict(Xq, total_trees=T)[1].astype(object) for part in parts)
+    exp = np.array([(2 * int(s) + T) // (2 * T) for s in P], np.int64)
+    assert np.array_equal(gpu_predict(f, Xq), exp)

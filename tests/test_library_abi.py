@@ -1,0 +1,86 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads, it exports every function
+include/aiwcrf.h declares, and argument validation that runs before any CUDA call rejects bad
+input with the documented codes."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1811_00156_gb300 import aiwcrf as A
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "aiwcrf.h")
+
+
+def _lib():
+    if not os.path.exists(A.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    return A.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(aiwcrf_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("aiwcrf_fit", "aiwcrf_predict", "aiwcrf_select_device"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = _lib()
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+    assert sorted(A.EXPORTS) == declared_functions()
+
+
+def test_struct_layouts_match_header():
+    assert C.sizeof(A.FitParams) == 40
+    assert A.FitParams.first_tree.offset == 32
+    assert C.sizeof(A.FitStats) == 9 * 8 + 8
+
+
+def test_param_validation_without_gpu():
+    L = _lib()
+    X = np.zeros((4, 10), np.float32)
+    y = np.zeros(10, np.int64)
+    h = C.c_void_p()
+    bad = [A.params(0, 2, 1), A.params(3, 0, 1), A.params(3, 2, 0), A.params(3, 2, 1, max_depth=-1)]
+    for p in bad:
+        rc = L.aiwcrf_fit(C.byref(p), X.ctypes.data, y.ctypes.data, 10, 4, None, C.byref(h))
+        assert rc == -1, rc
+        assert b"aiwcrf error -1" in L.aiwcrf_last_error()
+    p = A.params(3, 2, 1)
+    assert L.aiwcrf_fit(C.byref(p), X.ctypes.data, y.ctypes.data, 0, 4, None, C.byref(h)) == -1
+    assert L.aiwcrf_fit(C.byref(p), X.ctypes.data, y.ctypes.data, 1 << 22, 4, None, C.byref(h)) == -8
+    assert L.aiwcrf_fit(C.byref(p), X.ctypes.data, y.ctypes.data, 10, 129, None, C.byref(h)) == -1
+    assert L.aiwcrf_fit(C.byref(p), None, y.ctypes.data, 10, 4, None, C.byref(h)) == -1
+
+
+def test_deserialize_rejects_corrupt_blobs_without_gpu():
+    L = _lib()
+    h = C.c_void_p()
+    for blob in [b"", b"NOTAFOREST" + b"\0" * 40, b"AIWCRF01" + b"\0" * 24]:
+        buf = C.create_string_buffer(blob, max(len(blob), 1))
+        assert L.aiwcrf_forest_deserialize(buf, len(blob), C.byref(h)) == -7
+    # a split pointing backwards is rejected
+    hdr = b"AIWCRF01" + np.array([1, 2], np.uint32).tobytes() + np.array([1, 2], np.int64).tobytes()
+    off = np.array([0, 2], np.int64).tobytes()
+    nodes = np.array([(0 << 56) | (0 << 32), 0], np.uint64).tobytes()
+    blob = hdr + off + nodes
+    buf = C.create_string_buffer(blob, len(blob))
+    assert L.aiwcrf_forest_deserialize(buf, len(blob), C.byref(h)) == -7
+
+
+def test_profile_names():
+    L = _lib()
+    n = L.aiwcrf_profile_num_classes()
+    names = [L.aiwcrf_profile_name(k).decode() for k in range(n)]
+    assert "level_big" in names and "predict" in names
+    assert L.aiwcrf_profile_name(n) == b""

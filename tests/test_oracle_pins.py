@@ -302,3 +302,16 @@ def test_select_device_is_argmin():
         assert np.array_equal(pred[k], p)
         m = p.min()
         assert best[k] == min(d for d in devs if p[d] == m)
+
+
+def test_oracle_trees_grown_on_threads_match_serial():
+    """The benchmark's CPU baseline grows trees on several host threads: same trees."""
+    import concurrent.futures as cf
+    wl = synth.small_case(74, 600, 8, card=20)
+    with cf.ThreadPoolExecutor(4) as ex:
+        parts = list(ex.map(lambda t: O.fit(wl.X, wl.y, 12, 3, 2, seed=5, t0=t, t1=t + 1), range(12)))
+    full = O.fit(wl.X, wl.y, 12, 3, 2, seed=5)
+    for k in range(12):
+        a, b = parts[k].tree(0), full.tree(k)
+        assert np.array_equal(a.feature, b.feature) and np.array_equal(a.thr, b.thr)
+        assert np.array_equal(a.value, b.value) and np.array_equal(a.left, b.left)
