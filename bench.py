@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--trees", type=int, default=T_TREES,
+                    help="forest size per GPU; smaller values are for profiler captures only")
+    ap.add_argument("--queries", type=int, default=N_QUERIES,
+                    help="query count; smaller values are for profiler captures only")
     return ap.parse_args()
 
 
@@ -194,20 +198,21 @@ def run_ours(args):
     dev = torch.device("cuda", local_rank)
     wl = synth.scaled_forest_workload()
     N, F = wl.n_rows, wl.n_features
-    Xq_h = synth.queries(N_QUERIES)
+    n_trees, n_queries = args.trees, args.queries
+    Xq_h = synth.queries(n_queries)
     kfeat_h = np.ascontiguousarray(synth.queries(SEL_KERNELS, seed=99)[:30])
     X = torch.from_numpy(wl.X).to(dev)
     y = torch.from_numpy(wl.y).to(dev)
     Xq = torch.from_numpy(Xq_h).to(dev)
     kfeat = torch.from_numpy(kfeat_h).to(dev)
-    psum = torch.empty(N_QUERIES, dtype=torch.int64, device=dev)
-    pred = torch.empty(N_QUERIES, dtype=torch.int64, device=dev)
+    psum = torch.empty(n_queries, dtype=torch.int64, device=dev)
+    pred = torch.empty(n_queries, dtype=torch.int64, device=dev)
     best = torch.empty(SEL_KERNELS, dtype=torch.int32, device=dev)
     selp = torch.empty(SEL_KERNELS * SEL_DEVICES, dtype=torch.int64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     devices = list(range(SEL_DEVICES))
-    T_total = T_TREES * world
-    params = A.params(T_TREES, MTRY, MIN_NODE, seed=synth.FOREST_SEED, first_tree=rank * T_TREES)
+    T_total = n_trees * world
+    params = A.params(n_trees, MTRY, MIN_NODE, seed=synth.FOREST_SEED, first_tree=rank * n_trees)
     stream = torch.cuda.current_stream()
 
     def step(ev=None):
@@ -261,18 +266,18 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     fit_ms, pred_ms, sel_ms, step_ms = t.tolist()
     K = args.steps
-    value = N * T_TREES * world * K / (fit_ms / 1e3)
+    value = N * n_trees * world * K / (fit_ms / 1e3)
 
     # roofline of the dominant kernel class, from the events recorded around each launch
     peak, peak_kind = measured_peaks()
     big_rows = stats["rows_evaluated"] - stats["rows_evaluated_small"]
     big_part = stats["rows_partitioned"] - stats["rows_partitioned_small"]
-    per_eval = 4 + 8 + 2 * MTRY                   # row entry + target + mtry ranks
-    per_part = 4 + 2 + 4                          # row entry + chosen rank, entry written
+    per_eval = 4 + 8 + stats["rank_bytes"] * MTRY  # row entry + target + mtry ranks
+    per_part = 4 + stats["rank_bytes"] + 4         # row entry + chosen rank, entry written
     alg = {
         "level_big": K * (big_rows * per_eval + big_part * per_part),
         "level_small": K * (stats["rows_evaluated_small"] * per_eval + stats["rows_partitioned_small"] * per_part),
-        "predict": K * N_QUERIES * (F * 4 + 8),
+        "predict": K * n_queries * (F * 4 + 8),
     }
     sha = source_sha()
     kernels = {}
@@ -299,12 +304,13 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": ROWS_TREES_UNIT, "n_gpus": world, "steps": K,
            "warmup": args.warmup, "ms_per_step": step_ms / K, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "rows": N, "features": F, "trees_per_gpu": T_TREES,
-                      "queries": N_QUERIES, "select": f"{SEL_KERNELS}x{SEL_DEVICES}",
+           "config": {"workload": WORKLOAD if (n_trees, n_queries) == (T_TREES, N_QUERIES) else
+                      f"profiling case: {n_trees} trees, {n_queries} queries", "rows": N, "features": F,
+                      "trees_per_gpu": n_trees, "queries": n_queries, "select": f"{SEL_KERNELS}x{SEL_DEVICES}",
                       "seeds": {"data": synth.DATA_SEED, "forest": synth.FOREST_SEED, "queries": synth.QUERY_SEED},
                       "l2": "flushed between steps (256 MB write); fit working set and queries exceed L2",
                       "parallelism": f"tree-sharded x{world}" if world > 1 else "1 GPU"},
-           "predict": {"value": N_QUERIES * K / (pred_ms / 1e3), "unit": "queries/s", "ms": pred_ms / K,
+           "predict": {"value": n_queries * K / (pred_ms / 1e3), "unit": "queries/s", "ms": pred_ms / K,
                        "trees": T_total},
            "select": {"ms": sel_ms / K, "kernels": SEL_KERNELS, "devices": SEL_DEVICES},
            "fit_ms": fit_ms / K, "fit_stats": stats, "roofline": roofline, "kernels": kernels,

@@ -83,6 +83,8 @@ typedef struct {
     int64_t rows_partitioned_small;  /* rows_partitioned of the warp-searched nodes */
     int32_t n_features;
     int32_t mtry;
+    int32_t rank_bytes;          /* bytes per stored rank: 1 if every column has <= 256 values */
+    int32_t reserved;
 } aiwcrf_fit_stats;
 
 /* Fit a forest (Sec. III-B). X: F x N column-major float32 (no NaN); y: N int64 Q32.32.

@@ -37,7 +37,8 @@ class FitStats(C.Structure):
                 ("rows_evaluated", C.c_int64), ("rows_partitioned", C.c_int64),
                 ("nodes_evaluated", C.c_int64), ("nodes_small", C.c_int64),
                 ("rows_evaluated_small", C.c_int64), ("rows_partitioned_small", C.c_int64),
-                ("n_features", C.c_int32), ("mtry", C.c_int32)]
+                ("n_features", C.c_int32), ("mtry", C.c_int32), ("rank_bytes", C.c_int32),
+                ("reserved", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

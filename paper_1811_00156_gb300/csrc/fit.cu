@@ -197,6 +197,15 @@ __global__ void __launch_bounds__(kRankThreads) rank_kernel(
     if (tid == 0) card[f] = running;
 }
 
+// Row-major copy of the ranks: the tried features of one row share one 32- or 64-byte record.
+template <typename RT>
+__global__ void rank_rows_kernel(const uint16_t *__restrict__ Rcol, int64_t N, int F, RT *__restrict__ Rr)
+{
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= N) return;
+    for (int f = 0; f < F; ++f) Rr[(size_t)row * (size_t)F + f] = (RT)Rcol[(size_t)f * (size_t)N + row];
+}
+
 // ------------------------------------------------------------------------------------------
 // a2: bootstrap, one CTA per tree. Multiplicities are byte counters packed four to a word,
 // in shared memory when they fit, else in a per-tree global scratch.
@@ -309,7 +318,7 @@ struct LevelArgs {
     const uint32_t *rows_in;
     uint32_t *rows_out;
     int64_t row_cap;
-    const uint16_t *R;
+    const void *Rr;             // row-major ranks [N][F], uint8_t or uint16_t
     const float *vals;
     const uint32_t *card;
     int64_t N;
@@ -389,8 +398,10 @@ __device__ __forceinline__ void write_leaf(SplitRes *res, int j, int kind, int64
 constexpr int kSmallThreads = 256;
 
 // one warp per node with at most 32 distinct rows
+template <typename RT>
 __global__ void __launch_bounds__(kSmallThreads) level_small_kernel(LevelArgs a)
 {
+    const RT *__restrict__ Rr = static_cast<const RT *>(a.Rr);
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * (kSmallThreads / 32) + (threadIdx.x >> 5);
     if (gw >= a.list_n) return;                      // whole warp
@@ -416,7 +427,7 @@ __global__ void __launch_bounds__(kSmallThreads) level_small_kernel(LevelArgs a)
         while (m) {
             const int f = c * 32 + __ffs(m) - 1;
             m &= m - 1;
-            const uint32_t rank = valid ? (uint32_t)a.R[(size_t)f * (size_t)a.N + row] : kRankSentinel;
+            const uint32_t rank = valid ? (uint32_t)__ldg(&Rr[(size_t)row * (size_t)a.F + f]) : kRankSentinel;
             uint32_t key = (rank << 13) | (w << 5) | (uint32_t)lane;    // unique per lane
             long long v = wy;
             // bitonic sort of (key, v) across the warp, ascending key
@@ -448,7 +459,7 @@ __global__ void __launch_bounds__(kSmallThreads) level_small_kernel(LevelArgs a)
                 if (delta != 0) {
                     Cand cd;
                     cd.h = cand_h(delta, nd.n, cw);
-                    cd.f = f; cd.r = r; cd.nL = cw; cd.lenL = (uint32_t)lane + 1u; cd.SL = cs;
+                    cd.f = f; cd.r = r; cd.nL = cw; cd.SL = cs;
                     if (cand_better(cd, best, nd.n, nd.S)) best = cd;
                 }
             }
@@ -459,7 +470,7 @@ __global__ void __launch_bounds__(kSmallThreads) level_small_kernel(LevelArgs a)
         if (lane == 0) write_leaf(a.res, j, -1, round_mean(nd.S, nd.n));
         return;
     }
-    const uint32_t rk = valid ? (uint32_t)a.R[(size_t)best.f * (size_t)a.N + row] : kRankSentinel;
+    const uint32_t rk = valid ? (uint32_t)__ldg(&Rr[(size_t)row * (size_t)a.F + best.f]) : kRankSentinel;
     const bool left = valid && rk <= best.r;
     const uint32_t bl = __ballot_sync(kFull, left), bv = __ballot_sync(kFull, valid);
     const uint32_t lenL = __popc(bl), lt = lanemask_lt();
@@ -477,17 +488,25 @@ __global__ void __launch_bounds__(kSmallThreads) level_small_kernel(LevelArgs a)
 constexpr int kBigThreads = 256;
 constexpr int kBigWarps = kBigThreads / 32;
 
-// one CTA per node with more than 32 distinct rows; bin_cap bins of (u64 count, i64 sum)
-__global__ void __launch_bounds__(kBigThreads) level_big_kernel(LevelArgs a, int bin_cap)
+constexpr int kRowsPerIter = 4;   // rows per thread per pass: independent gathers in flight
+constexpr int kFeatChunk = 8;     // tried features whose ranks are loaded before their atomics
+
+// One CTA per node with more than 32 distinct rows. Shared bins, bin_cap of them, hold per rank
+// of every tried feature: sum w (u32) and sum w*y as an exact (low u32, high i32) pair. All
+// updates are native 32-bit shared atomics; a wrap of the low word carries into the high word.
+template <typename RT>
+__global__ void __launch_bounds__(kBigThreads, 3) level_big_kernel(LevelArgs a, int bin_cap)
 {
-    extern __shared__ unsigned long long sm_bins[];
-    unsigned long long *cntb = sm_bins;                               // (distinct << 32) | sum w
-    long long *sumb = reinterpret_cast<long long *>(sm_bins + bin_cap);
+    const RT *__restrict__ Rr = static_cast<const RT *>(a.Rr);
+    extern __shared__ uint32_t sm_bins[];
+    uint32_t *bw = sm_bins;                                       // sum w, then its prefix
+    uint32_t *blo = sm_bins + bin_cap;                            // sum w*y: low word
+    int32_t *bhi = reinterpret_cast<int32_t *>(sm_bins + 2 * bin_cap);   // high word
     __shared__ int feats[AIWCRF_MAX_FEATURES];
     __shared__ uint32_t fbase[AIWCRF_MAX_FEATURES + 1];
-    __shared__ unsigned long long carry_c[AIWCRF_MAX_FEATURES];
+    __shared__ uint32_t carry_w[AIWCRF_MAX_FEATURES];
     __shared__ long long carry_s[AIWCRF_MAX_FEATURES];
-    __shared__ unsigned long long tot_c[kBigThreads];
+    __shared__ uint32_t tot_w[kBigThreads];
     __shared__ long long tot_s[kBigThreads];
     __shared__ int m_sh;
     __shared__ Cand wbest[kBigWarps];
@@ -507,25 +526,32 @@ __global__ void __launch_bounds__(kBigThreads) level_big_kernel(LevelArgs a, int
     if (warp == 0) {
         uint32_t mask[4];
         warp_mtry(a, a.tree_rng[nd.tree], nd.idx, mask);
-        if (lane == 0) {
-            int m = 0;
-            uint32_t b = 0;
-            for (int c = 0; c < 4; ++c) {
-                uint32_t mm = mask[c];
-                while (mm) {
-                    const int f = c * 32 + __ffs(mm) - 1;
-                    mm &= mm - 1;
-                    feats[m] = f;
-                    fbase[m] = b;
-                    carry_c[m] = 0ull;
-                    carry_s[m] = 0ll;
-                    b += a.card[f];
-                    ++m;
-                }
-            }
-            fbase[m] = b;
-            m_sh = m;
+        // tried features in increasing order and the first bin of each
+        int m = 0;
+        for (int c = 0; c < 4; ++c) {
+            const uint32_t mm = mask[c];
+            const int f = c * 32 + lane;
+            const bool sel = (mm >> lane) & 1u;
+            const int pos = m + __popc(mm & ((1u << lane) - 1u));
+            if (sel) { feats[pos] = f; carry_w[pos] = 0u; carry_s[pos] = 0ll; }
+            m += __popc(mm);
         }
+        __syncwarp();
+        // exclusive prefix of the tried features' cardinalities
+        uint32_t run = 0;
+        for (int k0 = 0; k0 < m; k0 += 32) {
+            const int k = k0 + lane;
+            const uint32_t c = k < m ? a.card[feats[k]] : 0u;
+            uint32_t x = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, x, o);
+                if (lane >= o) x += t;
+            }
+            if (k < m) fbase[k] = run + x - c;
+            run += __shfl_sync(kFull, x, 31);
+        }
+        if (lane == 0) { fbase[m] = run; m_sh = m; }
     }
     __syncthreads();
     const int m = m_sh;
@@ -535,24 +561,56 @@ __global__ void __launch_bounds__(kBigThreads) level_big_kernel(LevelArgs a, int
     for (uint32_t g0 = 0; g0 < total_bins; g0 += (uint32_t)bin_cap) {
         const uint32_t g1 = min(total_bins, g0 + (uint32_t)bin_cap);
         const int nb = (int)(g1 - g0);
-        for (int b = tid; b < nb; b += kBigThreads) { cntb[b] = 0ull; sumb[b] = 0ll; }
+        for (int b = tid; b < nb; b += kBigThreads) { bw[b] = 0u; blo[b] = 0u; bhi[b] = 0; }
         int k_lo = 0;
         while (fbase[k_lo + 1] <= g0) ++k_lo;
         int k_hi = k_lo;
         while (k_hi + 1 < m && fbase[k_hi + 1] < g1) ++k_hi;
         __syncthreads();
 
-        // histogram of this group's bins
-        for (uint32_t i = tid; i < nd.len; i += kBigThreads) {
-            const uint32_t e = rin[i];
-            const uint32_t row = e & kRowMask, w = e >> kRowBits;
-            const long long wy = (long long)w * a.y[row];
-            const unsigned long long inc = (1ull << 32) | w;
-            for (int k = k_lo; k <= k_hi; ++k) {
-                const uint32_t b = fbase[k] + (uint32_t)a.R[(size_t)feats[k] * (size_t)a.N + row];
-                if (b >= g0 && b < g1) {
-                    atomicAdd(&cntb[b - g0], inc);
-                    atomicAdd(reinterpret_cast<unsigned long long *>(&sumb[b - g0]), (unsigned long long)wy);
+        // histogram: per pass a thread gathers the targets and the tried features' ranks of
+        // kRowsPerIter rows, then adds them to the shared bins
+        for (uint32_t base = 0; base < nd.len; base += kBigThreads * kRowsPerIter) {
+            uint32_t rowv[kRowsPerIter], wv[kRowsPerIter], lov[kRowsPerIter];
+            int32_t hiv[kRowsPerIter];
+#pragma unroll
+            for (int u = 0; u < kRowsPerIter; ++u) {
+                const uint32_t i = base + (uint32_t)(u * kBigThreads + tid);
+                const uint32_t e = i < nd.len ? rin[i] : 0u;              // w = 0: no row
+                rowv[u] = e & kRowMask;
+                wv[u] = e >> kRowBits;
+            }
+#pragma unroll
+            for (int u = 0; u < kRowsPerIter; ++u) {
+                const long long wy = wv[u] ? (long long)wv[u] * __ldg(&a.y[rowv[u]]) : 0ll;
+                lov[u] = (uint32_t)(unsigned long long)wy;
+                hiv[u] = (int32_t)(wy >> 32);
+            }
+            for (int k0 = k_lo; k0 <= k_hi; k0 += kFeatChunk) {
+                uint32_t rk[kRowsPerIter][kFeatChunk];
+#pragma unroll
+                for (int c = 0; c < kFeatChunk; ++c) {
+                    const bool kv = k0 + c <= k_hi;
+                    const int fk = kv ? feats[k0 + c] : 0;
+#pragma unroll
+                    for (int u = 0; u < kRowsPerIter; ++u)
+                        rk[u][c] = (kv && wv[u]) ? (uint32_t)__ldg(&Rr[(size_t)rowv[u] * (size_t)a.F + fk]) : 0u;
+                }
+#pragma unroll
+                for (int c = 0; c < kFeatChunk; ++c) {
+                    if (k0 + c > k_hi) break;
+                    const uint32_t fb = fbase[k0 + c];
+#pragma unroll
+                    for (int u = 0; u < kRowsPerIter; ++u) {
+                        const uint32_t b = fb + rk[u][c];
+                        if (wv[u] && b >= g0 && b < g1) {
+                            const uint32_t q = b - g0;
+                            atomicAdd(&bw[q], wv[u]);
+                            const uint32_t old = atomicAdd(&blo[q], lov[u]);
+                            const int32_t carry = (old + lov[u] < old) ? 1 : 0;
+                            if (hiv[u] + carry != 0) atomicAdd(&bhi[q], hiv[u] + carry);
+                        }
+                    }
                 }
             }
         }
@@ -561,39 +619,45 @@ __global__ void __launch_bounds__(kBigThreads) level_big_kernel(LevelArgs a, int
         // block inclusive prefix over the group's bins (unsegmented), in place
         const int per = (nb + kBigThreads - 1) / kBigThreads;
         const int lo = min(nb, tid * per), hi = min(nb, lo + per);
-        unsigned long long lc = 0;
+        uint32_t lw = 0;
         long long ls = 0;
-        for (int b = lo; b < hi; ++b) { lc += cntb[b]; ls += sumb[b]; }
-        tot_c[tid] = lc;
+        for (int b = lo; b < hi; ++b) {
+            lw += bw[b];
+            ls += ((long long)bhi[b] << 32) + (long long)blo[b];
+        }
+        tot_w[tid] = lw;
         tot_s[tid] = ls;
         __syncthreads();
         if (warp == 0) {            // exclusive scan of the 256 thread totals by one warp
-            unsigned long long c8[8];
+            uint32_t w8[8];
             long long s8[8];
-            unsigned long long cs = 0;
+            uint32_t ws = 0;
             long long ss = 0;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) { c8[k] = cs; s8[k] = ss; cs += tot_c[lane * 8 + k]; ss += tot_s[lane * 8 + k]; }
-            unsigned long long xc = cs;
+            for (int k = 0; k < 8; ++k) { w8[k] = ws; s8[k] = ss; ws += tot_w[lane * 8 + k]; ss += tot_s[lane * 8 + k]; }
+            uint32_t xw = ws;
             long long xs = ss;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long tc = __shfl_up_sync(kFull, xc, o);
+                const uint32_t tw = __shfl_up_sync(kFull, xw, o);
                 const long long ts = __shfl_up_sync(kFull, xs, o);
-                if (lane >= o) { xc += tc; xs += ts; }
+                if (lane >= o) { xw += tw; xs += ts; }
             }
-            xc -= cs;
+            xw -= ws;
             xs -= ss;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) { tot_c[lane * 8 + k] = xc + c8[k]; tot_s[lane * 8 + k] = xs + s8[k]; }
+            for (int k = 0; k < 8; ++k) { tot_w[lane * 8 + k] = xw + w8[k]; tot_s[lane * 8 + k] = xs + s8[k]; }
         }
         __syncthreads();
         {
-            unsigned long long rc = tot_c[tid];
+            uint32_t rw = tot_w[tid];
             long long rs = tot_s[tid];
             for (int b = lo; b < hi; ++b) {
-                rc += cntb[b]; rs += sumb[b];
-                cntb[b] = rc; sumb[b] = rs;
+                rw += bw[b];
+                rs += ((long long)bhi[b] << 32) + (long long)blo[b];
+                bw[b] = rw;
+                blo[b] = (uint32_t)(unsigned long long)rs;
+                bhi[b] = (int32_t)(rs >> 32);
             }
         }
         __syncthreads();
@@ -605,29 +669,28 @@ __global__ void __launch_bounds__(kBigThreads) level_big_kernel(LevelArgs a, int
             for (int b = lo; b < hi; ++b) {
                 const uint32_t gb = g0 + (uint32_t)b;
                 while (fbase[k + 1] <= gb) ++k;
-                const unsigned long long pc = cntb[b];
-                const unsigned long long prev = b > 0 ? cntb[b - 1] : 0ull;
-                if ((uint32_t)(pc - prev) == 0u) continue;             // rank not present
+                const uint32_t pw = bw[b];
+                if (pw == (b > 0 ? bw[b - 1] : 0u)) continue;          // rank not present
                 const int fs = (int)(max(fbase[k], g0) - g0);          // feature's first bin here
-                const unsigned long long base_c = fs > 0 ? cntb[fs - 1] : 0ull;
-                const long long base_s = fs > 0 ? sumb[fs - 1] : 0ll;
-                const unsigned long long cw = pc - base_c + carry_c[k];
-                const uint32_t nL = (uint32_t)cw;
+                const uint32_t nL = pw - (fs > 0 ? bw[fs - 1] : 0u) + carry_w[k];
                 if (nL >= nd.n) continue;                               // last present rank
-                const long long SL = sumb[b] - base_s + carry_s[k];
+                const long long pS = ((long long)bhi[b] << 32) + (long long)blo[b];
+                const long long baseS = fs > 0 ? ((long long)bhi[fs - 1] << 32) + (long long)blo[fs - 1] : 0ll;
+                const long long SL = pS - baseS + carry_s[k];
                 const i128_t delta = cand_delta(nd.n, nd.S, nL, SL);
                 if (delta == 0) continue;
                 Cand cd;
                 cd.h = cand_h(delta, nd.n, nL);
-                cd.f = feats[k]; cd.r = gb - fbase[k]; cd.nL = nL; cd.lenL = (uint32_t)(cw >> 32); cd.SL = SL;
+                cd.f = feats[k]; cd.r = gb - fbase[k]; cd.nL = nL; cd.SL = SL;
                 if (cand_better(cd, best, nd.n, nd.S)) best = cd;
             }
         }
         __syncthreads();
         if (tid == 0 && fbase[k_hi + 1] > g1) {                        // feature continues
             const int fs = (int)(max(fbase[k_hi], g0) - g0);
-            carry_c[k_hi] += cntb[nb - 1] - (fs > 0 ? cntb[fs - 1] : 0ull);
-            carry_s[k_hi] += sumb[nb - 1] - (fs > 0 ? sumb[fs - 1] : 0ll);
+            carry_w[k_hi] += bw[nb - 1] - (fs > 0 ? bw[fs - 1] : 0u);
+            const long long lastS = ((long long)bhi[nb - 1] << 32) + (long long)blo[nb - 1];
+            carry_s[k_hi] += lastS - (fs > 0 ? ((long long)bhi[fs - 1] << 32) + (long long)blo[fs - 1] : 0ll);
         }
         __syncthreads();
     }
@@ -647,21 +710,28 @@ __global__ void __launch_bounds__(kBigThreads) level_big_kernel(LevelArgs a, int
         return;
     }
 
-    // a5: stable partition of the node's rows into [left | right] at the same offsets
+    // a5: stable partition of the node's rows into [left | right] at the same offsets; a first
+    // pass counts the rows that go left
+    uint32_t cnt = 0;
+    for (uint32_t i = tid; i < nd.len; i += kBigThreads) {
+        const uint32_t e = rin[i];
+        cnt += (uint32_t)__ldg(&Rr[(size_t)(e & kRowMask) * (size_t)a.F + win.f]) <= win.r ? 1u : 0u;
+    }
+    uint32_t lenL;
+    block_incl_scan(cnt, warp_tmp, lenL);
     uint32_t run_l = 0u, run_r = 0u;           // block-uniform running counts
     uint32_t *rout = a.rows_out + tb;
-    const uint16_t *rcol = a.R + (size_t)win.f * (size_t)a.N;
     for (uint32_t b0 = 0; b0 < nd.len; b0 += kBigThreads) {
         const uint32_t i = b0 + tid;
         const bool valid = i < nd.len;
         const uint32_t e = valid ? rin[i] : 0u;
-        const bool left = valid && (uint32_t)rcol[e & kRowMask] <= win.r;
+        const bool left = valid && (uint32_t)__ldg(&Rr[(size_t)(e & kRowMask) * (size_t)a.F + win.f]) <= win.r;
         uint32_t tot;
         const uint32_t incl = block_incl_scan(left ? 1u : 0u, warp_tmp, tot);
         if (valid) {
             const uint32_t before_l = incl - (left ? 1u : 0u);
             if (left) rout[run_l + before_l] = e;
-            else rout[win.lenL + run_r + ((uint32_t)tid - before_l)] = e;
+            else rout[lenL + run_r + ((uint32_t)tid - before_l)] = e;
         }
         run_l += tot;
         run_r += min((uint32_t)kBigThreads, nd.len - b0) - tot;
@@ -670,7 +740,7 @@ __global__ void __launch_bounds__(kBigThreads) level_big_kernel(LevelArgs a, int
         SplitRes sr;
         sr.feature = win.f; sr.rank = win.r;
         sr.thr_bits = __float_as_uint(a.vals[(size_t)win.f * (size_t)a.N + win.r]);
-        sr.nL = win.nL; sr.lenL = win.lenL; sr.pad = 0u; sr.v = win.SL;
+        sr.nL = win.nL; sr.lenL = lenL; sr.pad = 0u; sr.v = win.SL;
         a.res[j] = sr;
     }
 }
@@ -976,6 +1046,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     uint16_t *d_R = sc.get<uint16_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
     float *d_vals = sc.get<float>((size_t)F * (size_t)N, &rc); if (rc) return rc;
     uint32_t *d_card = sc.get<uint32_t>((size_t)F, &rc); if (rc) return rc;
+    uint32_t max_card = 0;
     {
         uint32_t *kA = sc.get<uint32_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
         uint32_t *iA = sc.get<uint32_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
@@ -990,6 +1061,24 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         prof_end(s, kProfRank);
         sc.drop(kA); sc.drop(iA); sc.drop(kB); sc.drop(iB);
     }
+    {
+        std::vector<uint32_t> h_card((size_t)F);
+        uint32_t h_err = 0;
+        AIWCRF_CUDA(cudaMemcpyAsync(h_card.data(), d_card, sizeof(uint32_t) * (size_t)F, cudaMemcpyDeviceToHost, s));
+        AIWCRF_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        AIWCRF_CUDA(cudaStreamSynchronize(s));
+        if ((rc = check_err_flags(h_err)) != AIWCRF_OK) return rc;
+        max_card = *std::max_element(h_card.begin(), h_card.end());
+    }
+    const bool rank8 = max_card <= 256;
+    void *d_Rr = rank8 ? (void *)sc.get<uint8_t>((size_t)F * (size_t)N, &rc) : (void *)sc.get<uint16_t>((size_t)F * (size_t)N, &rc);
+    if (rc) return rc;
+    prof_begin(s, kProfRank);
+    if (rank8) rank_rows_kernel<uint8_t><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(d_R, N, F, (uint8_t *)d_Rr);
+    else rank_rows_kernel<uint16_t><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(d_R, N, F, (uint16_t *)d_Rr);
+    AIWCRF_LAUNCH_CHECK("rank_rows_kernel");
+    prof_end(s, kProfRank);
+    sc.drop(d_R);
 
     // a2: bootstrap
     int64_t *d_pool_off = sc.get<int64_t>((size_t)T, &rc); if (rc) return rc;
@@ -1066,12 +1155,13 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     uint32_t n_small = h_cnt[0], n_big = h_cnt[1];
     int64_t C = T;
 
-    const int bin_cap = 3072;
-    const int big_smem = bin_cap * 16;
-    AIWCRF_CUDA(cudaFuncSetAttribute(level_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem));
+    const int bin_cap = 4096;
+    const int big_smem = bin_cap * 12;
+    AIWCRF_CUDA(cudaFuncSetAttribute(level_big_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem));
+    AIWCRF_CUDA(cudaFuncSetAttribute(level_big_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem));
 
     LevelArgs la;
-    la.row_cap = row_cap; la.R = d_R; la.vals = d_vals; la.card = d_card; la.N = N; la.y = dy;
+    la.row_cap = row_cap; la.Rr = d_Rr; la.vals = d_vals; la.card = d_card; la.N = N; la.y = dy;
     la.tree_rng = d_rng; la.F = F; la.mtry = p.mtry; la.min_node = p.min_node_size;
     la.max_depth = p.max_depth; la.seed_lo = (uint32_t)p.seed; la.seed_hi = (uint32_t)(p.seed >> 32);
 
@@ -1123,7 +1213,8 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         if (n_big > 0) {
             la.list = big_list; la.list_n = (int32_t)n_big;
             prof_begin(s, kProfLevelBig);
-            level_big_kernel<<<n_big, kBigThreads, big_smem, s>>>(la, bin_cap);
+            if (rank8) level_big_kernel<uint8_t><<<n_big, kBigThreads, big_smem, s>>>(la, bin_cap);
+            else level_big_kernel<uint16_t><<<n_big, kBigThreads, big_smem, s>>>(la, bin_cap);
             AIWCRF_LAUNCH_CHECK("level_big_kernel");
             prof_end(s, kProfLevelBig);
         }
@@ -1131,7 +1222,8 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
             la.list = small_list; la.list_n = (int32_t)n_small;
             const unsigned grid = (n_small + kSmallThreads / 32 - 1) / (kSmallThreads / 32);
             prof_begin(s, kProfLevelSmall);
-            level_small_kernel<<<grid, kSmallThreads, 0, s>>>(la);
+            if (rank8) level_small_kernel<uint8_t><<<grid, kSmallThreads, 0, s>>>(la);
+            else level_small_kernel<uint16_t><<<grid, kSmallThreads, 0, s>>>(la);
             AIWCRF_LAUNCH_CHECK("level_small_kernel");
             prof_end(s, kProfLevelSmall);
         }
@@ -1215,6 +1307,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         fr->stats.levels = depth;
         fr->stats.n_features = F;
         fr->stats.mtry = p.mtry;
+        fr->stats.rank_bytes = rank8 ? 1 : 2;
         if (G == 1) {
             fr->stats.rows_evaluated = (int64_t)hs.rows_evaluated;
             fr->stats.rows_partitioned = (int64_t)hs.rows_partitioned;

@@ -64,14 +64,13 @@ struct Cand {
     int32_t f;
     uint32_t r;
     uint32_t nL;      // sum w on the left
-    uint32_t lenL;    // distinct rows on the left
     int64_t SL;       // sum w*y on the left
 };
 
 __device__ __forceinline__ Cand cand_none()
 {
     Cand c;
-    c.h = -1.0f; c.f = 0x7FFFFFFF; c.r = 0xFFFFFFFFu; c.nL = 0; c.lenL = 0; c.SL = 0;
+    c.h = -1.0f; c.f = 0x7FFFFFFF; c.r = 0xFFFFFFFFu; c.nL = 0; c.SL = 0;
     return c;
 }
 
@@ -168,7 +167,6 @@ __device__ __forceinline__ Cand shfl_cand(const Cand &c, int src)
     o.f = __shfl_sync(kFull, c.f, src);
     o.r = __shfl_sync(kFull, c.r, src);
     o.nL = __shfl_sync(kFull, c.nL, src);
-    o.lenL = __shfl_sync(kFull, c.lenL, src);
     o.SL = (int64_t)__shfl_sync(kFull, (long long)c.SL, src);
     return o;
 }
