@@ -270,13 +270,13 @@ def run_ours(args):
 
     # roofline of the dominant kernel class, from the events recorded around each launch
     peak, peak_kind = measured_peaks()
-    big_rows = stats["rows_evaluated"] - stats["rows_evaluated_small"]
-    big_part = stats["rows_partitioned"] - stats["rows_partitioned_small"]
-    per_eval = 4 + 8 + stats["rank_bytes"] * MTRY  # row entry + target + mtry ranks
-    per_part = 4 + stats["rank_bytes"] + 4         # row entry + chosen rank, entry written
+    big_rows = stats["entries_evaluated"] - stats["entries_evaluated_small"]
+    big_part = stats["entries_partitioned"] - stats["entries_partitioned_small"]
+    per_eval = 16 + stats["rank_bytes"] * MTRY     # 16-byte entry + the tried features' ranks
+    per_part = 16 + stats["rank_bytes"] + 16       # entry and chosen rank read, entry written
     alg = {
         "level_big": K * (big_rows * per_eval + big_part * per_part),
-        "level_small": K * (stats["rows_evaluated_small"] * per_eval + stats["rows_partitioned_small"] * per_part),
+        "level_small": K * (stats["entries_evaluated_small"] * per_eval + stats["entries_partitioned_small"] * per_part),
         "predict": K * n_queries * (F * 4 + 8),
     }
     sha = source_sha()

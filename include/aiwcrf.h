@@ -70,17 +70,20 @@ typedef struct {
                                tree t uses random counters of tree first_tree + t). >= 0 */
 } aiwcrf_fit_params;
 
-/* Per-fit counters, for byte accounting and tests. */
+/* Per-fit counters, for byte accounting and tests. Rows with identical feature vectors form
+ * one group; a tree carries one entry per group that holds in-bag rows (its summed
+ * multiplicity and summed w*y), since such rows fall on the same side of every split. */
 typedef struct {
     int64_t num_trees;
     int64_t total_nodes;
-    int64_t levels;              /* depth of the deepest tree + 1 */
-    int64_t rows_evaluated;      /* sum over searched nodes of their distinct in-bag rows */
-    int64_t rows_partitioned;    /* sum over split nodes of their distinct in-bag rows */
-    int64_t nodes_evaluated;     /* nodes whose split was searched */
-    int64_t nodes_small;         /* of those, searched by one warp (<= 32 distinct rows) */
-    int64_t rows_evaluated_small;    /* rows_evaluated of the warp-searched nodes */
-    int64_t rows_partitioned_small;  /* rows_partitioned of the warp-searched nodes */
+    int64_t levels;                     /* depth of the deepest tree + 1 */
+    int64_t groups;                     /* distinct feature vectors among the rows */
+    int64_t entries_evaluated;          /* sum over searched nodes of their entries */
+    int64_t entries_partitioned;        /* sum over split nodes of their entries */
+    int64_t nodes_evaluated;            /* nodes whose split was searched */
+    int64_t nodes_small;                /* of those, searched by one warp (<= 32 entries) */
+    int64_t entries_evaluated_small;    /* entries_evaluated of the warp-searched nodes */
+    int64_t entries_partitioned_small;  /* entries_partitioned of the warp-searched nodes */
     int32_t n_features;
     int32_t mtry;
     int32_t rank_bytes;          /* bytes per stored rank: 1 if every column has <= 256 values */

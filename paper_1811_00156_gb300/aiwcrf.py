@@ -34,9 +34,9 @@ class FitParams(C.Structure):
 
 class FitStats(C.Structure):
     _fields_ = [("num_trees", C.c_int64), ("total_nodes", C.c_int64), ("levels", C.c_int64),
-                ("rows_evaluated", C.c_int64), ("rows_partitioned", C.c_int64),
+                ("groups", C.c_int64), ("entries_evaluated", C.c_int64), ("entries_partitioned", C.c_int64),
                 ("nodes_evaluated", C.c_int64), ("nodes_small", C.c_int64),
-                ("rows_evaluated_small", C.c_int64), ("rows_partitioned_small", C.c_int64),
+                ("entries_evaluated_small", C.c_int64), ("entries_partitioned_small", C.c_int64),
                 ("n_features", C.c_int32), ("mtry", C.c_int32), ("rank_bytes", C.c_int32),
                 ("reserved", C.c_int32)]
 

@@ -1,15 +1,21 @@
 // fit.cu -- random-forest growth on the GPU (the model of Sec. III-B, fitted breadth first).
 //
 // Pipeline of one fit (all trees of all forests of the batch grow together, level by level):
-//   rank_kernel        one-time stable LSD radix sort of every column; dense ranks (u16) and
-//                      the rank -> value table
-//   bootstrap_kernel   Philox draws per tree -> multiplicities -> in-bag row list (row | w<<24)
+//   presort            every column's float keys sorted by the segmented radix sort (sort.cu);
+//                      dense ranks and the rank -> value table; ranks copied to row-major
+//                      records of F bytes (u8 when every column has <= 256 values, else u16)
+//   grouping           rows with identical rank records (identical feature vectors) form a
+//                      group: such rows fall on the same side of every threshold, so a tree
+//                      can carry one entry per group with the summed multiplicity and target.
+//                      Groups are ordered by a hash of their record.
+//   bootstrap_kernel   Philox draws per tree -> per-row multiplicities -> one entry
+//                      {row, sum w, sum w*y} per group that has an in-bag row
 //   per depth d:
-//     level_big_kernel   one CTA per node with > 32 distinct rows: mtry draw, shared-memory
-//                        histogram of (sum w | distinct rows, sum w*y) per rank for every tried
-//                        feature, block scan, exact argmax of the gain, stable partition
-//     level_small_kernel one warp per node with <= 32 distinct rows: the same search with a
-//                        register bitonic sort per feature instead of a histogram
+//     level_big_kernel   one CTA per node with > 32 entries: mtry draw, shared-memory histogram
+//                        (sum w, sum w*y) per rank of every tried feature, block scan, exact
+//                        argmax of the gain, stable partition of the entries
+//     level_small_kernel one warp per node with <= 32 entries: the same search with a register
+//                        bitonic sort per feature instead of a histogram
 //     scan_*             exclusive scan of the split flags over the depth's nodes
 //     finalize_kernel    encodes each node, numbers the children breadth first, writes the
 //                        next depth's node table and its warp/CTA work lists
@@ -26,178 +32,73 @@
 
 namespace aiwcrf {
 
-// ------------------------------------------------------------------------------------------
-// small device utilities
-// ------------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t lanemask_lt()
+struct Entry {            // one group of identical in-bag rows of one tree
+    uint32_t row;         // a row of the group (all its rows have the same features)
+    uint32_t w;           // summed bootstrap multiplicity
+    int64_t wy;           // summed w * y
+};
+static_assert(sizeof(Entry) == 16, "Entry is one 16-byte vector");
+
+__device__ __forceinline__ Entry load_entry(const Entry *p)
 {
-    uint32_t m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
+    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+    Entry e;
+    e.row = v.x; e.w = v.y; e.wy = (int64_t)(((uint64_t)v.w << 32) | v.z);
+    return e;
 }
 
-__device__ __forceinline__ uint32_t float_key(float x)
+__device__ __forceinline__ void store_entry(Entry *p, const Entry &e)
 {
-    uint32_t b = __float_as_uint(x);
-    if (b == 0x80000000u) b = 0u;                      // -0 and +0 are one value
-    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);  // order-preserving unsigned key
-}
-
-__device__ __forceinline__ float key_float(uint32_t k)
-{
-    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
-}
-
-// inclusive block scan of one u32 per thread (blockDim multiple of 32, <= 1024)
-__device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t *warp_tmp, uint32_t &total)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(kFull, x, o);
-        if (lane >= o) x += t;
-    }
-    if (lane == 31) warp_tmp[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = lane < nw ? warp_tmp[lane] : 0u;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(kFull, w, o);
-            if (lane >= o) w += t;
-        }
-        if (lane < nw) warp_tmp[lane] = w;             // inclusive warp prefix
-    }
-    __syncthreads();
-    const uint32_t off = warp > 0 ? warp_tmp[warp - 1] : 0u;
-    total = warp_tmp[nw - 1];
-    __syncthreads();
-    return x + off;
+    *reinterpret_cast<uint4 *>(p) = make_uint4(e.row, e.w, (uint32_t)(uint64_t)e.wy, (uint32_t)((uint64_t)e.wy >> 32));
 }
 
 // ------------------------------------------------------------------------------------------
-// a1: presort and rank, one CTA of 1024 threads per column
+// a1: presort and rank
 // ------------------------------------------------------------------------------------------
-constexpr int kRankThreads = 1024;
-
-__global__ void __launch_bounds__(kRankThreads) rank_kernel(
-    const float *__restrict__ X, int64_t N, uint32_t *keyA, uint32_t *idxA, uint32_t *keyB,
-    uint32_t *idxB, uint16_t *__restrict__ R, float *__restrict__ vals, uint32_t *__restrict__ card,
-    uint32_t *err)
+__global__ void key_init_kernel(const float *__restrict__ X, int64_t N, uint32_t *keys, uint32_t *vals, uint32_t *err)
 {
-    __shared__ uint32_t hist[256];
-    __shared__ uint32_t base[256];
-    __shared__ uint32_t wcnt[32][256];
-    __shared__ uint32_t tile_tot[256];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int f = blockIdx.y;
+    if (i >= N) return;
+    const float x = X[(size_t)f * (size_t)N + i];
+    if (x != x) atomicOr(err, kErrNaN);
+    keys[(size_t)f * (size_t)N + i] = float_key(x);
+    vals[(size_t)f * (size_t)N + i] = (uint32_t)i;
+}
+
+// dense ranks of one sorted column per CTA: equal keys share a rank
+__global__ void __launch_bounds__(1024) dense_rank_kernel(const uint32_t *__restrict__ keys,
+                                                          const uint32_t *__restrict__ idx, int64_t N,
+                                                          uint16_t *__restrict__ Rcol, float *__restrict__ vals,
+                                                          uint32_t *__restrict__ card, uint32_t *err)
+{
     __shared__ uint32_t warp_tmp[32];
-    __shared__ uint32_t running;
-
-    const int f = blockIdx.x;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int f = blockIdx.x, tid = threadIdx.x;
     const size_t off = (size_t)f * (size_t)N;
-    uint32_t *kin = keyA + off, *iin = idxA + off, *kout = keyB + off, *iout = idxB + off;
-
-    int nan = 0;
-    for (int64_t i = tid; i < N; i += kRankThreads) {
-        const float x = X[off + i];
-        if (x != x) nan = 1;
-        kin[i] = float_key(x);
-        iin[i] = (uint32_t)i;
-    }
-    if (__syncthreads_or(nan)) {
-        if (tid == 0) atomicOr(err, kErrNaN);
-        return;
-    }
-    for (int k = tid; k < 32 * 256; k += kRankThreads) (&wcnt[0][0])[k] = 0u;
-
-    for (int pass = 0; pass < 4; ++pass) {
-        const int shift = 8 * pass;
-        if (tid < 256) hist[tid] = 0u;
-        __syncthreads();
-        for (int64_t i = tid; i < N; i += kRankThreads) atomicAdd(&hist[(kin[i] >> shift) & 255u], 1u);
-        __syncthreads();
-        // one digit holds every key: the pass is the identity permutation
-        if (__syncthreads_or(tid < 256 && hist[tid] == (uint32_t)N)) continue;
-        if (warp == 0) {                                         // exclusive scan of 256 counts
-            uint32_t loc[8], s = 0;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) { loc[k] = s; s += hist[lane * 8 + k]; }
-            uint32_t x = s;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(kFull, x, o);
-                if (lane >= o) x += t;
-            }
-            const uint32_t ex = x - s;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) base[lane * 8 + k] = ex + loc[k];
-        }
-        __syncthreads();
-        for (int64_t t0 = 0; t0 < N; t0 += kRankThreads) {
-            const int64_t i = t0 + tid;
-            const bool valid = i < N;
-            const uint32_t k = valid ? kin[i] : 0u;
-            const uint32_t id = valid ? iin[i] : 0u;
-            const uint32_t d = (k >> shift) & 255u;
-            const uint32_t peers = __match_any_sync(kFull, valid ? d : (256u + lane));
-            const uint32_t rk = __popc(peers & lanemask_lt());
-            if (valid && rk == 0) wcnt[warp][d] = __popc(peers);
-            __syncthreads();
-            if (tid < 256) {
-                uint32_t run = 0;
-                for (int w = 0; w < 32; ++w) {
-                    const uint32_t c = wcnt[w][tid];
-                    wcnt[w][tid] = run;
-                    run += c;
-                }
-                tile_tot[tid] = run;
-            }
-            __syncthreads();
-            if (valid) {
-                const uint32_t pos = base[d] + wcnt[warp][d] + rk;
-                kout[pos] = k;
-                iout[pos] = id;
-            }
-            __syncthreads();
-            if (tid < 256) {
-                base[tid] += tile_tot[tid];
-                for (int w = 0; w < 32; ++w) wcnt[w][tid] = 0u;
-            }
-            __syncthreads();
-        }
-        uint32_t *t;
-        t = kin; kin = kout; kout = t;
-        t = iin; iin = iout; iout = t;
-    }
-
-    if (tid == 0) running = 0u;
-    __syncthreads();
+    uint32_t running = 0;
     int over = 0;
-    for (int64_t t0 = 0; t0 < N; t0 += kRankThreads) {
+    for (int64_t t0 = 0; t0 < N; t0 += 1024) {
         const int64_t i = t0 + tid;
         const bool valid = i < N;
-        const uint32_t k = valid ? kin[i] : 0u;
-        const uint32_t flag = (valid && (i == 0 || kin[i - 1] != k)) ? 1u : 0u;
+        const uint32_t k = valid ? keys[off + i] : 0u;
+        const uint32_t flag = (valid && (i == 0 || keys[off + i - 1] != k)) ? 1u : 0u;
         uint32_t tot;
         const uint32_t incl = block_incl_scan(flag, warp_tmp, tot);
         if (valid) {
             const uint32_t r = running + incl - 1u;
             if (r >= 65536u) over = 1;
             else {
-                R[off + iin[i]] = (uint16_t)r;
+                Rcol[off + idx[off + i]] = (uint16_t)r;
                 if (flag) vals[off + r] = key_float(k);
             }
         }
-        __syncthreads();
-        if (tid == 0) running += tot;
-        __syncthreads();
+        running += tot;
     }
     if (over) atomicOr(err, kErrCard);
     if (tid == 0) card[f] = running;
 }
 
-// Row-major copy of the ranks: the tried features of one row share one 32- or 64-byte record.
+// Row-major copy of the ranks: the tried features of one row share one record.
 template <typename RT>
 __global__ void rank_rows_kernel(const uint16_t *__restrict__ Rcol, int64_t N, int F, RT *__restrict__ Rr)
 {
@@ -207,8 +108,65 @@ __global__ void rank_rows_kernel(const uint16_t *__restrict__ Rcol, int64_t N, i
 }
 
 // ------------------------------------------------------------------------------------------
-// a2: bootstrap, one CTA per tree. Multiplicities are byte counters packed four to a word,
-// in shared memory when they fit, else in a per-tree global scratch.
+// grouping of rows with identical rank records
+// ------------------------------------------------------------------------------------------
+template <typename RT>
+__global__ void hash_rows_kernel(const RT *__restrict__ Rr, int64_t N, int F, uint32_t *keys, uint32_t *vals)
+{
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= N) return;
+    const RT *r = Rr + (size_t)row * (size_t)F;
+    uint32_t h = 0x811C9DC5u;
+    for (int f = 0; f < F; ++f) {
+        h ^= (uint32_t)r[f];
+        h *= 0x01000193u;
+        h ^= h >> 13;
+    }
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    keys[row] = h;
+    vals[row] = (uint32_t)row;
+}
+
+template <typename RT>
+__device__ __forceinline__ bool same_record(const RT *Rr, int F, uint32_t a, uint32_t b)
+{
+    const RT *ra = Rr + (size_t)a * (size_t)F, *rb = Rr + (size_t)b * (size_t)F;
+    for (int f = 0; f < F; ++f)
+        if (ra[f] != rb[f]) return false;
+    return true;
+}
+
+// rows sorted by hash -> groups of adjacent rows with the same hash and the same record.
+// grp_off[g] = first sorted position of group g (grp_off[G] = N); G is written to *n_groups.
+template <typename RT>
+__global__ void __launch_bounds__(1024) group_kernel(const RT *__restrict__ Rr, int64_t N, int F,
+                                                     const uint32_t *__restrict__ hkeys,
+                                                     const uint32_t *__restrict__ rows, uint32_t *grp_off,
+                                                     uint32_t *n_groups)
+{
+    __shared__ uint32_t warp_tmp[32];
+    uint32_t running = 0;
+    for (int64_t t0 = 0; t0 < N; t0 += 1024) {
+        const int64_t i = t0 + threadIdx.x;
+        bool flag = false;
+        if (i < N) flag = i == 0 || hkeys[i] != hkeys[i - 1] || !same_record(Rr, F, rows[i], rows[i - 1]);
+        uint32_t tot;
+        const uint32_t incl = block_incl_scan(flag ? 1u : 0u, warp_tmp, tot);
+        if (flag) grp_off[running + incl - 1u] = (uint32_t)i;
+        running += tot;
+    }
+    if (threadIdx.x == 0) {
+        grp_off[running] = (uint32_t)N;
+        *n_groups = running;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// a2: bootstrap, one CTA per tree. Multiplicities are byte counters per row, packed four to a
+// word, in shared memory when they fit, else in a per-tree global scratch. Entries are then
+// formed group by group, in group order.
 // ------------------------------------------------------------------------------------------
 constexpr int kBootThreads = 1024;
 
@@ -218,12 +176,16 @@ struct BootArgs {
     const uint32_t *tree_rng;       // per tree: global tree index used as Philox counter word 0
     const int32_t *sub_rows;
     const int64_t *y;
+    int64_t N;
+    const uint32_t *grp_off;        // G + 1
+    const uint32_t *grp_rows;       // rows in group order
+    uint32_t G;
     uint32_t seed_lo, seed_hi;
     int bootstrap;
     uint32_t *gcnt;                 // global byte counters (may be null)
     int64_t gcnt_stride;            // words per tree
     int smem_words;
-    uint32_t *rows_out;
+    Entry *rows_out;
     int64_t row_cap;
     NodeRec *root;
     int32_t *small_list, *big_list;
@@ -237,56 +199,71 @@ __global__ void __launch_bounds__(kBootThreads) bootstrap_kernel(BootArgs a)
     __shared__ uint32_t warp_tmp[32];
     __shared__ unsigned long long red_n[32];
     __shared__ long long red_s[32];
-    __shared__ uint32_t running;
 
     const int t = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t n = a.tree_pool_len[t];
     const int64_t poff = a.tree_pool_off[t];
-    const uint32_t words = (n + 3u) / 4u;
+    const uint32_t words = (uint32_t)((a.N + 3) / 4);
     uint32_t *cnt = ((int)words <= a.smem_words) ? sm_cnt : a.gcnt + (size_t)t * (size_t)a.gcnt_stride;
 
+    for (uint32_t k = tid; k < words; k += kBootThreads) cnt[k] = 0u;
+    __syncthreads();
     if (a.bootstrap) {
-        for (uint32_t k = tid; k < words; k += kBootThreads) cnt[k] = 0u;
-        __syncthreads();
         const uint32_t tg = a.tree_rng[t];
         int overflow = 0;
-        for (uint32_t b = tid; b < words; b += kBootThreads) {
+        for (uint32_t b = tid; b < (n + 3u) / 4u; b += kBootThreads) {
             const uint4 u = philox10(make_uint4(tg, b, kDomBoot, 0u), a.seed_lo, a.seed_hi);
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
                 const uint32_t k = 4u * b + (uint32_t)w;
                 if (k < n) {
                     const uint32_t j = __umulhi(uint4_word(u, w), n);
-                    const uint32_t sh = 8u * (j & 3u);
-                    const uint32_t old = atomicAdd(&cnt[j >> 2], 1u << sh);
+                    const uint32_t row = poff < 0 ? j : (uint32_t)a.sub_rows[poff + j];
+                    const uint32_t sh = 8u * (row & 3u);
+                    const uint32_t old = atomicAdd(&cnt[row >> 2], 1u << sh);
                     if (((old >> sh) & 255u) == 255u) overflow = 1;
                 }
             }
         }
         if (overflow) atomicOr(a.err, kErrBootOverflow);
-        __syncthreads();
+    } else {
+        for (uint32_t j = tid; j < n; j += kBootThreads) {
+            const uint32_t row = poff < 0 ? j : (uint32_t)a.sub_rows[poff + j];
+            atomicOr(&cnt[row >> 2], 1u << (8u * (row & 3u)));
+        }
     }
-
-    if (tid == 0) running = 0u;
     __syncthreads();
+
+    uint32_t running = 0;
     unsigned long long acc_n = 0;
     long long acc_s = 0;
-    uint32_t *out = a.rows_out + (size_t)t * (size_t)a.row_cap;
-    for (uint32_t b0 = 0; b0 < n; b0 += kBootThreads) {
-        const uint32_t j = b0 + tid;
-        uint32_t w = 0;
-        if (j < n) w = a.bootstrap ? ((cnt[j >> 2] >> (8u * (j & 3u))) & 255u) : 1u;
-        uint32_t tot;
-        const uint32_t incl = block_incl_scan(w > 0 ? 1u : 0u, warp_tmp, tot);
-        if (w > 0) {
-            const uint32_t row = poff < 0 ? j : (uint32_t)a.sub_rows[poff + j];
-            out[running + incl - 1u] = row | (w << kRowBits);
-            acc_n += w;
-            acc_s += (long long)w * a.y[row];
+    Entry *out = a.rows_out + (size_t)t * (size_t)a.row_cap;
+    for (uint32_t g0 = 0; g0 < a.G; g0 += kBootThreads) {
+        const uint32_t g = g0 + tid;
+        uint32_t sw = 0, rep = 0;
+        long long swy = 0;
+        if (g < a.G) {
+            const uint32_t e = a.grp_off[g + 1];
+            rep = a.grp_rows[a.grp_off[g]];
+            for (uint32_t k = a.grp_off[g]; k < e; ++k) {
+                const uint32_t row = a.grp_rows[k];
+                const uint32_t w = (cnt[row >> 2] >> (8u * (row & 3u))) & 255u;
+                if (w) {
+                    sw += w;
+                    swy += (long long)w * a.y[row];
+                }
+            }
         }
-        __syncthreads();
-        if (tid == 0) running += tot;
-        __syncthreads();
+        uint32_t tot;
+        const uint32_t incl = block_incl_scan(sw > 0 ? 1u : 0u, warp_tmp, tot);
+        if (sw > 0) {
+            Entry en;
+            en.row = rep; en.w = sw; en.wy = swy;
+            store_entry(&out[running + incl - 1u], en);
+            acc_n += sw;
+            acc_s += swy;
+        }
+        running += tot;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -315,14 +292,13 @@ struct LevelArgs {
     const NodeRec *nodes;
     const int32_t *list;
     int32_t list_n;
-    const uint32_t *rows_in;
-    uint32_t *rows_out;
+    const Entry *rows_in;
+    Entry *rows_out;
     int64_t row_cap;
     const void *Rr;             // row-major ranks [N][F], uint8_t or uint16_t
     const float *vals;
     const uint32_t *card;
     int64_t N;
-    const int64_t *y;
     const uint32_t *tree_rng;
     int32_t F, mtry, min_node, max_depth, depth;
     uint32_t seed_lo, seed_hi;
@@ -395,9 +371,10 @@ __device__ __forceinline__ void write_leaf(SplitRes *res, int j, int kind, int64
     res[j] = r;
 }
 
+
 constexpr int kSmallThreads = 256;
 
-// one warp per node with at most 32 distinct rows
+// one warp per node with at most 32 entries
 template <typename RT>
 __global__ void __launch_bounds__(kSmallThreads) level_small_kernel(LevelArgs a)
 {
@@ -413,10 +390,10 @@ __global__ void __launch_bounds__(kSmallThreads) level_small_kernel(LevelArgs a)
     }
     const size_t tb = (size_t)nd.tree * (size_t)a.row_cap + nd.start;
     const bool valid = lane < (int)nd.len;
-    const uint32_t e = valid ? a.rows_in[tb + lane] : 0u;
-    const uint32_t row = e & kRowMask;
-    const uint32_t w = valid ? (e >> kRowBits) : 0u;
-    const long long wy = valid ? (long long)w * a.y[row] : 0ll;
+    Entry e;
+    e.row = 0u; e.w = 0u; e.wy = 0;
+    if (valid) e = load_entry(a.rows_in + tb + lane);
+    const size_t rec = (size_t)e.row * (size_t)a.F;
 
     uint32_t mask[4];
     warp_mtry(a, a.tree_rng[nd.tree], nd.idx, mask);
@@ -427,29 +404,31 @@ __global__ void __launch_bounds__(kSmallThreads) level_small_kernel(LevelArgs a)
         while (m) {
             const int f = c * 32 + __ffs(m) - 1;
             m &= m - 1;
-            const uint32_t rank = valid ? (uint32_t)__ldg(&Rr[(size_t)row * (size_t)a.F + f]) : kRankSentinel;
-            uint32_t key = (rank << 13) | (w << 5) | (uint32_t)lane;    // unique per lane
-            long long v = wy;
-            // bitonic sort of (key, v) across the warp, ascending key
+            const uint32_t rank = valid ? (uint32_t)__ldg(&Rr[rec + f]) : kRankSentinel;
+            uint32_t key = (rank << 5) | (uint32_t)lane;                 // unique per lane
+            uint32_t w = e.w;
+            long long v = e.wy;
+            // bitonic sort of (key, w, v) across the warp, ascending key
 #pragma unroll
             for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
                 for (int jj = k >> 1; jj > 0; jj >>= 1) {
                     const uint32_t ok = __shfl_xor_sync(kFull, key, jj);
-                    const long long ov = shfl_xor_ll(v, jj);
+                    const uint32_t ow = __shfl_xor_sync(kFull, w, jj);
+                    const long long ov = __shfl_xor_sync(kFull, v, jj);
                     const bool asc = (lane & k) == 0;
                     const bool lower = (lane & jj) == 0;
                     const bool take = (lower == asc) ? (ok < key) : (ok > key);
-                    if (take) { key = ok; v = ov; }
+                    if (take) { key = ok; w = ow; v = ov; }
                 }
             }
-            const uint32_t r = key >> 13;
-            uint32_t cw = (key >> 5) & 255u;
+            const uint32_t r = key >> 5;
+            uint32_t cw = w;
             long long cs = v;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t tw = __shfl_up_sync(kFull, cw, o);
-                const long long ts = shfl_up_ll(cs, o);
+                const long long ts = __shfl_up_sync(kFull, cs, o);
                 if (lane >= o) { cw += tw; cs += ts; }
             }
             uint32_t nr = __shfl_down_sync(kFull, r, 1);
@@ -470,12 +449,12 @@ __global__ void __launch_bounds__(kSmallThreads) level_small_kernel(LevelArgs a)
         if (lane == 0) write_leaf(a.res, j, -1, round_mean(nd.S, nd.n));
         return;
     }
-    const uint32_t rk = valid ? (uint32_t)__ldg(&Rr[(size_t)row * (size_t)a.F + best.f]) : kRankSentinel;
+    const uint32_t rk = valid ? (uint32_t)__ldg(&Rr[rec + best.f]) : kRankSentinel;
     const bool left = valid && rk <= best.r;
     const uint32_t bl = __ballot_sync(kFull, left), bv = __ballot_sync(kFull, valid);
     const uint32_t lenL = __popc(bl), lt = lanemask_lt();
     const uint32_t pos = left ? __popc(bl & lt) : lenL + __popc(bv & ~bl & lt);
-    if (valid) a.rows_out[tb + pos] = e;
+    if (valid) store_entry(a.rows_out + tb + pos, e);
     if (lane == 0) {
         SplitRes sr;
         sr.feature = best.f; sr.rank = best.r;
@@ -487,11 +466,10 @@ __global__ void __launch_bounds__(kSmallThreads) level_small_kernel(LevelArgs a)
 
 constexpr int kBigThreads = 256;
 constexpr int kBigWarps = kBigThreads / 32;
-
 constexpr int kRowsPerIter = 4;   // rows per thread per pass: independent gathers in flight
 constexpr int kFeatChunk = 8;     // tried features whose ranks are loaded before their atomics
 
-// One CTA per node with more than 32 distinct rows. Shared bins, bin_cap of them, hold per rank
+// One CTA per node with more than 32 entries. Shared bins, bin_cap of them, hold per rank
 // of every tried feature: sum w (u32) and sum w*y as an exact (low u32, high i32) pair. All
 // updates are native 32-bit shared atomics; a wrap of the low word carries into the high word.
 template <typename RT>
@@ -521,7 +499,7 @@ __global__ void __launch_bounds__(kBigThreads, 3) level_big_kernel(LevelArgs a, 
         return;
     }
     const size_t tb = (size_t)nd.tree * (size_t)a.row_cap + nd.start;
-    const uint32_t *rin = a.rows_in + tb;
+    const Entry *rin = a.rows_in + tb;
 
     if (warp == 0) {
         uint32_t mask[4];
@@ -568,23 +546,21 @@ __global__ void __launch_bounds__(kBigThreads, 3) level_big_kernel(LevelArgs a, 
         while (k_hi + 1 < m && fbase[k_hi + 1] < g1) ++k_hi;
         __syncthreads();
 
-        // histogram: per pass a thread gathers the targets and the tried features' ranks of
-        // kRowsPerIter rows, then adds them to the shared bins
+        // histogram: per pass a thread loads kRowsPerIter entries and gathers the tried
+        // features' ranks of their rows, then adds them to the shared bins
         for (uint32_t base = 0; base < nd.len; base += kBigThreads * kRowsPerIter) {
             uint32_t rowv[kRowsPerIter], wv[kRowsPerIter], lov[kRowsPerIter];
             int32_t hiv[kRowsPerIter];
 #pragma unroll
             for (int u = 0; u < kRowsPerIter; ++u) {
                 const uint32_t i = base + (uint32_t)(u * kBigThreads + tid);
-                const uint32_t e = i < nd.len ? rin[i] : 0u;              // w = 0: no row
-                rowv[u] = e & kRowMask;
-                wv[u] = e >> kRowBits;
-            }
-#pragma unroll
-            for (int u = 0; u < kRowsPerIter; ++u) {
-                const long long wy = wv[u] ? (long long)wv[u] * __ldg(&a.y[rowv[u]]) : 0ll;
-                lov[u] = (uint32_t)(unsigned long long)wy;
-                hiv[u] = (int32_t)(wy >> 32);
+                Entry e;
+                e.row = 0u; e.w = 0u; e.wy = 0;                           // w = 0: no entry
+                if (i < nd.len) e = load_entry(rin + i);
+                rowv[u] = e.row;
+                wv[u] = e.w;
+                lov[u] = (uint32_t)(uint64_t)e.wy;
+                hiv[u] = (int32_t)(e.wy >> 32);
             }
             for (int k0 = k_lo; k0 <= k_hi; k0 += kFeatChunk) {
                 uint32_t rk[kRowsPerIter][kFeatChunk];
@@ -710,28 +686,29 @@ __global__ void __launch_bounds__(kBigThreads, 3) level_big_kernel(LevelArgs a, 
         return;
     }
 
-    // a5: stable partition of the node's rows into [left | right] at the same offsets; a first
-    // pass counts the rows that go left
+    // a5: stable partition of the node's entries into [left | right] at the same offsets; a
+    // first pass counts the entries that go left
     uint32_t cnt = 0;
     for (uint32_t i = tid; i < nd.len; i += kBigThreads) {
-        const uint32_t e = rin[i];
-        cnt += (uint32_t)__ldg(&Rr[(size_t)(e & kRowMask) * (size_t)a.F + win.f]) <= win.r ? 1u : 0u;
+        const uint32_t row = __ldg(&rin[i].row);
+        cnt += (uint32_t)__ldg(&Rr[(size_t)row * (size_t)a.F + win.f]) <= win.r ? 1u : 0u;
     }
     uint32_t lenL;
     block_incl_scan(cnt, warp_tmp, lenL);
     uint32_t run_l = 0u, run_r = 0u;           // block-uniform running counts
-    uint32_t *rout = a.rows_out + tb;
+    Entry *rout = a.rows_out + tb;
     for (uint32_t b0 = 0; b0 < nd.len; b0 += kBigThreads) {
         const uint32_t i = b0 + tid;
         const bool valid = i < nd.len;
-        const uint32_t e = valid ? rin[i] : 0u;
-        const bool left = valid && (uint32_t)__ldg(&Rr[(size_t)(e & kRowMask) * (size_t)a.F + win.f]) <= win.r;
+        Entry e;
+        e.row = 0u; e.w = 0u; e.wy = 0;
+        if (valid) e = load_entry(rin + i);
+        const bool left = valid && (uint32_t)__ldg(&Rr[(size_t)e.row * (size_t)a.F + win.f]) <= win.r;
         uint32_t tot;
         const uint32_t incl = block_incl_scan(left ? 1u : 0u, warp_tmp, tot);
         if (valid) {
             const uint32_t before_l = incl - (left ? 1u : 0u);
-            if (left) rout[run_l + before_l] = e;
-            else rout[lenL + run_r + ((uint32_t)tid - before_l)] = e;
+            store_entry(left ? &rout[run_l + before_l] : &rout[lenL + run_r + ((uint32_t)tid - before_l)], e);
         }
         run_l += tot;
         run_r += min((uint32_t)kBigThreads, nd.len - b0) - tot;
@@ -889,7 +866,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinalArgs a)
     if (threadIdx.x < 6) {
         unsigned long long s = 0;
         for (int w = 0; w < 8; ++w) s += red[threadIdx.x][w];
-        if (s) atomicAdd(&a.stats->rows_evaluated + threadIdx.x, s);   // GrowStats field order
+        if (s) atomicAdd(&a.stats->entries_evaluated + threadIdx.x, s);   // GrowStats field order
     }
 }
 
@@ -1042,26 +1019,27 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     AIWCRF_CUDA(cudaMemsetAsync(d_stats, 0, sizeof(GrowStats), s));
     AIWCRF_CUDA(cudaMemsetAsync(d_counters, 0, 4 * sizeof(uint32_t), s));
 
-    // a1: rank
+    // a1: presort and rank
     uint16_t *d_R = sc.get<uint16_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
     float *d_vals = sc.get<float>((size_t)F * (size_t)N, &rc); if (rc) return rc;
     uint32_t *d_card = sc.get<uint32_t>((size_t)F, &rc); if (rc) return rc;
+    uint32_t *kA = sc.get<uint32_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
+    uint32_t *vA = sc.get<uint32_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
+    uint32_t *kB = sc.get<uint32_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
+    uint32_t *vB = sc.get<uint32_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
+    uint32_t *hist = sc.get<uint32_t>(radix_sort_hist_words(N, F), &rc); if (rc) return rc;
     uint32_t max_card = 0;
     {
-        uint32_t *kA = sc.get<uint32_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
-        uint32_t *iA = sc.get<uint32_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
-        uint32_t *kB = sc.get<uint32_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
-        uint32_t *iB = sc.get<uint32_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
-        const int64_t yblocks = (N + 255) / 256;
-        check_y_kernel<<<(unsigned)yblocks, 256, 0, s>>>(dy, N, d_err);
+        const unsigned yblocks = (unsigned)((N + 255) / 256);
+        check_y_kernel<<<yblocks, 256, 0, s>>>(dy, N, d_err);
         AIWCRF_LAUNCH_CHECK("check_y_kernel");
         prof_begin(s, kProfRank);
-        rank_kernel<<<F, kRankThreads, 0, s>>>(dX, N, kA, iA, kB, iB, d_R, d_vals, d_card, d_err);
-        AIWCRF_LAUNCH_CHECK("rank_kernel");
+        key_init_kernel<<<dim3(yblocks, (unsigned)F), 256, 0, s>>>(dX, N, kA, vA, d_err);
+        AIWCRF_LAUNCH_CHECK("key_init_kernel");
+        if ((rc = radix_sort_segments(kA, vA, kB, vB, N, F, N, hist, s)) != AIWCRF_OK) return rc;
+        dense_rank_kernel<<<F, 1024, 0, s>>>(kA, vA, N, d_R, d_vals, d_card, d_err);
+        AIWCRF_LAUNCH_CHECK("dense_rank_kernel");
         prof_end(s, kProfRank);
-        sc.drop(kA); sc.drop(iA); sc.drop(kB); sc.drop(iB);
-    }
-    {
         std::vector<uint32_t> h_card((size_t)F);
         uint32_t h_err = 0;
         AIWCRF_CUDA(cudaMemcpyAsync(h_card.data(), d_card, sizeof(uint32_t) * (size_t)F, cudaMemcpyDeviceToHost, s));
@@ -1073,12 +1051,33 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     const bool rank8 = max_card <= 256;
     void *d_Rr = rank8 ? (void *)sc.get<uint8_t>((size_t)F * (size_t)N, &rc) : (void *)sc.get<uint16_t>((size_t)F * (size_t)N, &rc);
     if (rc) return rc;
-    prof_begin(s, kProfRank);
-    if (rank8) rank_rows_kernel<uint8_t><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(d_R, N, F, (uint8_t *)d_Rr);
-    else rank_rows_kernel<uint16_t><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(d_R, N, F, (uint16_t *)d_Rr);
-    AIWCRF_LAUNCH_CHECK("rank_rows_kernel");
-    prof_end(s, kProfRank);
-    sc.drop(d_R);
+
+    // grouping of identical feature vectors
+    uint32_t *grp_off = sc.get<uint32_t>((size_t)N + 1, &rc); if (rc) return rc;
+    uint32_t n_groups = 0;
+    {
+        const unsigned rb = (unsigned)((N + 255) / 256);
+        prof_begin(s, kProfRank);
+        if (rank8) {
+            rank_rows_kernel<uint8_t><<<rb, 256, 0, s>>>(d_R, N, F, (uint8_t *)d_Rr);
+            hash_rows_kernel<uint8_t><<<rb, 256, 0, s>>>((const uint8_t *)d_Rr, N, F, kA, vA);
+        } else {
+            rank_rows_kernel<uint16_t><<<rb, 256, 0, s>>>(d_R, N, F, (uint16_t *)d_Rr);
+            hash_rows_kernel<uint16_t><<<rb, 256, 0, s>>>((const uint16_t *)d_Rr, N, F, kA, vA);
+        }
+        count_launches(1);
+        AIWCRF_LAUNCH_CHECK("rank_rows / hash_rows");
+        if ((rc = radix_sort_segments(kA, vA, kB, vB, N, 1, N, hist, s)) != AIWCRF_OK) return rc;
+        if (rank8) group_kernel<uint8_t><<<1, 1024, 0, s>>>((const uint8_t *)d_Rr, N, F, kA, vA, grp_off, d_counters + 2);
+        else group_kernel<uint16_t><<<1, 1024, 0, s>>>((const uint16_t *)d_Rr, N, F, kA, vA, grp_off, d_counters + 2);
+        AIWCRF_LAUNCH_CHECK("group_kernel");
+        prof_end(s, kProfRank);
+        AIWCRF_CUDA(cudaMemcpyAsync(&n_groups, d_counters + 2, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        AIWCRF_CUDA(cudaStreamSynchronize(s));
+    }
+    const uint32_t *grp_rows = vA;            // rows in group order
+    sc.drop(d_R); sc.drop(kA); sc.drop(kB); sc.drop(vB); sc.drop(hist);
+    row_cap = std::min<int64_t>(row_cap, (int64_t)n_groups);
 
     // a2: bootstrap
     int64_t *d_pool_off = sc.get<int64_t>((size_t)T, &rc); if (rc) return rc;
@@ -1088,8 +1087,8 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     AIWCRF_CUDA(cudaMemcpyAsync(d_pool_len, h_pool_len.data(), sizeof(uint32_t) * (size_t)T, cudaMemcpyHostToDevice, s));
     AIWCRF_CUDA(cudaMemcpyAsync(d_rng, h_rng.data(), sizeof(uint32_t) * (size_t)T, cudaMemcpyHostToDevice, s));
 
-    uint32_t *rows_a = sc.get<uint32_t>((size_t)T * (size_t)row_cap, &rc); if (rc) return rc;
-    uint32_t *rows_b = sc.get<uint32_t>((size_t)T * (size_t)row_cap, &rc); if (rc) return rc;
+    Entry *rows_a = sc.get<Entry>((size_t)T * (size_t)row_cap, &rc); if (rc) return rc;
+    Entry *rows_b = sc.get<Entry>((size_t)T * (size_t)row_cap, &rc); if (rc) return rc;
 
     size_t node_cap = (size_t)std::max<int64_t>(T, 1024);
     NodeRec *nodes_cur = sc.get<NodeRec>(node_cap, &rc); if (rc) return rc;
@@ -1100,22 +1099,23 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     size_t list_cap = node_cap;
 
     {
-        const int boot_smem_words = std::min<int>((max_smem_optin - 1024) / 4, 56 * 1024);
-        const uint32_t words = (uint32_t)((row_cap + 3) / 4);
+        const int boot_smem_words = std::min<int>((max_smem_optin - 2048) / 4, 56 * 1024);
+        const uint32_t words = (uint32_t)((N + 3) / 4);
         uint32_t *gcnt = nullptr;
         int64_t gstride = 0;
-        if (p.bootstrap && (int)words > boot_smem_words) {
+        if ((int)words > boot_smem_words) {
             gstride = words;
             gcnt = sc.get<uint32_t>((size_t)T * (size_t)words, &rc); if (rc) return rc;
         }
-        const int smem_bytes = p.bootstrap ? (int)std::min<int64_t>((int64_t)words, boot_smem_words) * 4 : 0;
+        const int smem_bytes = gcnt ? 0 : (int)words * 4;
         AIWCRF_CUDA(cudaFuncSetAttribute(bootstrap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          std::max(smem_bytes, 1)));
         BootArgs ba;
         ba.tree_pool_off = d_pool_off; ba.tree_pool_len = d_pool_len; ba.tree_rng = d_rng;
-        ba.sub_rows = d_sub_rows; ba.y = dy; ba.seed_lo = (uint32_t)p.seed; ba.seed_hi = (uint32_t)(p.seed >> 32);
+        ba.sub_rows = d_sub_rows; ba.y = dy; ba.N = N; ba.grp_off = grp_off; ba.grp_rows = grp_rows; ba.G = n_groups;
+        ba.seed_lo = (uint32_t)p.seed; ba.seed_hi = (uint32_t)(p.seed >> 32);
         ba.bootstrap = p.bootstrap; ba.gcnt = gcnt; ba.gcnt_stride = gstride;
-        ba.smem_words = (gcnt != nullptr) ? 0 : boot_smem_words;
+        ba.smem_words = gcnt ? 0 : (int)words;
         ba.rows_out = rows_a; ba.row_cap = row_cap; ba.root = nodes_cur;
         ba.small_list = small_list; ba.big_list = big_list; ba.counters = d_counters; ba.err = d_err;
         prof_begin(s, kProfBoot);
@@ -1161,11 +1161,11 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     AIWCRF_CUDA(cudaFuncSetAttribute(level_big_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem));
 
     LevelArgs la;
-    la.row_cap = row_cap; la.Rr = d_Rr; la.vals = d_vals; la.card = d_card; la.N = N; la.y = dy;
+    la.row_cap = row_cap; la.Rr = d_Rr; la.vals = d_vals; la.card = d_card; la.N = N;
     la.tree_rng = d_rng; la.F = F; la.mtry = p.mtry; la.min_node = p.min_node_size;
     la.max_depth = p.max_depth; la.seed_lo = (uint32_t)p.seed; la.seed_hi = (uint32_t)(p.seed >> 32);
 
-    uint32_t *rin = rows_a, *rout = rows_b;
+    Entry *rin = rows_a, *rout = rows_b;
     int depth = 0;
     for (; C > 0; ++depth) {
         // capacity for this depth's results and the next depth's nodes
@@ -1308,13 +1308,14 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         fr->stats.n_features = F;
         fr->stats.mtry = p.mtry;
         fr->stats.rank_bytes = rank8 ? 1 : 2;
+        fr->stats.groups = n_groups;
         if (G == 1) {
-            fr->stats.rows_evaluated = (int64_t)hs.rows_evaluated;
-            fr->stats.rows_partitioned = (int64_t)hs.rows_partitioned;
+            fr->stats.entries_evaluated = (int64_t)hs.entries_evaluated;
+            fr->stats.entries_partitioned = (int64_t)hs.entries_partitioned;
             fr->stats.nodes_evaluated = (int64_t)hs.nodes_evaluated;
             fr->stats.nodes_small = (int64_t)hs.nodes_small;
-            fr->stats.rows_evaluated_small = (int64_t)hs.rows_evaluated_small;
-            fr->stats.rows_partitioned_small = (int64_t)hs.rows_partitioned_small;
+            fr->stats.entries_evaluated_small = (int64_t)hs.entries_evaluated_small;
+            fr->stats.entries_partitioned_small = (int64_t)hs.entries_partitioned_small;
         }
     }
     uint64_t **d_dst = sc.get<uint64_t *>((size_t)T, &rc); if (rc) return rc;

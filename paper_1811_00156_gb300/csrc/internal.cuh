@@ -52,6 +52,56 @@ __device__ __forceinline__ uint32_t uint4_word(uint4 v, int w)
 }
 
 // ------------------------------------------------------------------------------------------
+// small device utilities
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint32_t float_key(float x)
+{
+    uint32_t b = __float_as_uint(x);
+    if (b == 0x80000000u) b = 0u;                      // -0 and +0 are one value
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);  // order-preserving unsigned key
+}
+
+__device__ __forceinline__ float key_float(uint32_t k)
+{
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+// inclusive block scan of one u32 per thread (blockDim multiple of 32, <= 1024)
+__device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t *warp_tmp, uint32_t &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) warp_tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < nw ? warp_tmp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += t;
+        }
+        if (lane < nw) warp_tmp[lane] = w;             // inclusive warp prefix
+    }
+    __syncthreads();
+    const uint32_t off = warp > 0 ? warp_tmp[warp - 1] : 0u;
+    total = warp_tmp[nw - 1];
+    __syncthreads();
+    return x + off;
+}
+
+// ------------------------------------------------------------------------------------------
 // Split candidates. Within a node (n = sum w, S = sum w*y) the CART gain of "left = ranks <= r"
 // is G = S_L^2/n_L + S_R^2/n_R = S^2/n + delta^2 / (n n_L n_R), delta = n S_L - n_L S.
 // So the search maximises D = delta^2 / (n_L n_R), exactly: a float estimate h = |delta| /
@@ -241,18 +291,25 @@ __device__ __forceinline__ uint64_t encode_leaf(int64_t v)
     return (1ull << 63) | ((uint64_t)v & 0x7FFFFFFFFFFFFFFFull);
 }
 
-struct GrowStats {        // device counters of one fit
-    unsigned long long rows_evaluated;
-    unsigned long long rows_partitioned;
+struct GrowStats {        // device counters of one fit (field order is used by finalize_kernel)
+    unsigned long long entries_evaluated;
+    unsigned long long entries_partitioned;
     unsigned long long nodes_evaluated;
     unsigned long long nodes_small;
-    unsigned long long rows_evaluated_small;
-    unsigned long long rows_partitioned_small;
+    unsigned long long entries_evaluated_small;
+    unsigned long long entries_partitioned_small;
 };
 
 // ------------------------------------------------------------------------------------------
 // host side
 // ------------------------------------------------------------------------------------------
+// Stable LSD radix sort (four 8-bit passes) of S segments of n (key, value) u32 pairs, segment s
+// at offset s * stride. The result ends in (keys_a, vals_a); (keys_b, vals_b) is scratch.
+// hist needs S * 256 * ceil(n / 4096) + 1 words.
+int radix_sort_segments(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b, int64_t n,
+                        int S, int64_t stride, uint32_t *hist, cudaStream_t s);
+size_t radix_sort_hist_words(int64_t n, int S);
+
 enum ProfClass {
     kProfRank = 0, kProfBoot, kProfLevelBig, kProfLevelSmall, kProfScan, kProfFinalize,
     kProfPack, kProfPredict, kProfSelect, kProfNum

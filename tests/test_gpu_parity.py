@@ -67,9 +67,9 @@ def test_aiwc_2220_forest_bit_exact():
     assert np.array_equal(p, rp)
     assert v == rv
     st = f.stats()
-    exp_eval = sum(int(ref.tree(k).nrows[ref.tree(k).evaluated == 1].sum()) for k in range(T))
-    assert st["rows_evaluated"] == exp_eval
     assert st["total_nodes"] == sum(ref.tree(k).num_nodes for k in range(T))
+    assert st["groups"] == len({tuple(c) for c in wl.X.T.tolist()})
+    assert st["nodes_evaluated"] == sum(int(ref.tree(k).evaluated.sum()) for k in range(T))
 
 
 CASES = [

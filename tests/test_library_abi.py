@@ -43,7 +43,7 @@ def test_library_exports_every_declared_symbol():
 def test_struct_layouts_match_header():
     assert C.sizeof(A.FitParams) == 40
     assert A.FitParams.first_tree.offset == 32
-    assert C.sizeof(A.FitStats) == 9 * 8 + 16
+    assert C.sizeof(A.FitStats) == 10 * 8 + 16
 
 
 def test_param_validation_without_gpu():
