@@ -1,6 +1,7 @@
 // api.cu -- the extern "C" boundary declared in include/aiwcrf.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstring>
 #include <mutex>
@@ -28,6 +29,17 @@ int cuda_fail(cudaError_t e, const char *what)
 {
     cudaGetLastError();   // clear a sticky launch error where possible
     return fail(AIWCRF_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void forest_release(aiwcrf_forest *f)
+{
+    if (!f) return;
+    cudaFree(f->d_nodes);
+    cudaFree(f->d_cnodes);
+    cudaFree(f->d_tree_off);
+    cudaFree(f->d_fvals);
+    cudaFree(f->d_fcard);
+    delete f;
 }
 
 static std::atomic<long long> g_launches{0};
@@ -451,18 +463,66 @@ int aiwcrf_forest_deserialize(const void *buf, size_t len, aiwcrf_forest **out)
             if (fe >= F || (int64_t)lc <= j || (int64_t)lc + 1 >= m) return fail(AIWCRF_E_CORRUPT, "bad node");
         }
     }
+    // value tables: per feature the sorted distinct thresholds (-0 read as +0); coded copy of
+    // every split holds its threshold's index in that table
+    std::vector<std::vector<float>> tab((size_t)F);
+    std::vector<uint64_t> cnodes((size_t)nn);
+    for (int64_t j = 0; j < nn; ++j) {
+        uint64_t nd;
+        std::memcpy(&nd, nodes + j, 8);
+        if (nd >> 63) continue;
+        uint32_t b = (uint32_t)nd;
+        if (b == 0x80000000u) b = 0u;
+        float x;
+        std::memcpy(&x, &b, 4);
+        if (x != x) return fail(AIWCRF_E_CORRUPT, "NaN threshold");
+        tab[(size_t)((nd >> 56) & 0x7F)].push_back(x);
+    }
+    uint32_t max_card = 0;
+    for (auto &v : tab) {
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+        if (v.size() >= (1u << 24)) return fail(AIWCRF_E_LIMIT, "more than 2^24 - 1 thresholds for one feature");
+        max_card = std::max<uint32_t>(max_card, (uint32_t)v.size());
+    }
+    for (int64_t j = 0; j < nn; ++j) {
+        uint64_t nd;
+        std::memcpy(&nd, nodes + j, 8);
+        if (nd >> 63) { cnodes[(size_t)j] = nd; continue; }
+        uint32_t b = (uint32_t)nd;
+        if (b == 0x80000000u) b = 0u;
+        float x;
+        std::memcpy(&x, &b, 4);
+        const auto &v = tab[(size_t)((nd >> 56) & 0x7F)];
+        const uint32_t code = (uint32_t)(std::lower_bound(v.begin(), v.end(), x) - v.begin());
+        cnodes[(size_t)j] = (nd & 0xFFFFFFFF00000000ull) | code;
+    }
+    const int64_t fstride = std::max<uint32_t>(max_card, 1u);
+    std::vector<float> fv((size_t)F * (size_t)fstride, 0.0f);
+    std::vector<uint32_t> fc((size_t)F);
+    for (uint32_t f = 0; f < F; ++f) {
+        fc[f] = (uint32_t)tab[f].size();
+        std::copy(tab[f].begin(), tab[f].end(), fv.begin() + (size_t)f * (size_t)fstride);
+    }
     int dev, rc;
     if ((rc = current_device(&dev))) return rc;
     aiwcrf_forest *f = new aiwcrf_forest();
     f->F = (int32_t)F; f->T = T; f->num_nodes = nn; f->max_tree_nodes = max_tree; f->device = dev;
     f->tree_off = off;
+    f->max_card = max_card;
+    f->fstride = fstride;
     cudaError_t e = cudaMalloc(&f->d_nodes, 8 * (size_t)nn);
+    if (e == cudaSuccess) e = cudaMalloc(&f->d_cnodes, 8 * (size_t)nn);
     if (e == cudaSuccess) e = cudaMalloc(&f->d_tree_off, 8 * (size_t)(T + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&f->d_fvals, sizeof(float) * fv.size());
+    if (e == cudaSuccess) e = cudaMalloc(&f->d_fcard, sizeof(uint32_t) * fc.size());
     if (e == cudaSuccess) e = cudaMemcpy(f->d_nodes, nodes, 8 * (size_t)nn, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(f->d_cnodes, cnodes.data(), 8 * (size_t)nn, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(f->d_tree_off, off.data(), 8 * (size_t)(T + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(f->d_fvals, fv.data(), sizeof(float) * fv.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(f->d_fcard, fc.data(), sizeof(uint32_t) * fc.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        cudaFree(f->d_nodes); cudaFree(f->d_tree_off);
-        delete f;
+        forest_release(f);
         return cuda_fail(e, "uploading forest");
     }
     *out = f;
@@ -472,10 +532,7 @@ int aiwcrf_forest_deserialize(const void *buf, size_t len, aiwcrf_forest **out)
 int aiwcrf_forest_free(aiwcrf_forest *forest)
 {
     g_last_error.clear();
-    if (!forest) return AIWCRF_OK;
-    cudaFree(forest->d_nodes);
-    cudaFree(forest->d_tree_off);
-    delete forest;
+    forest_release(forest);
     return AIWCRF_OK;
 }
 

@@ -833,6 +833,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinalArgs a)
         pr.tree = t;
         pr.pos = base_t + nd.idx;
         pr.node = split ? encode_split(r.feature, base_t + cnt_t + 2u * local, r.thr_bits) : encode_leaf(r.v);
+        pr.cnode = split ? encode_split_coded(r.feature, base_t + cnt_t + 2u * local, r.rank) : pr.node;
         a.packed[j] = pr;
     }
     if (split) {
@@ -885,21 +886,22 @@ __global__ void iota_kernel(uint32_t *v, int n)
     if (i <= n) v[i] = (uint32_t)i;
 }
 
-__global__ void pack_kernel(const PackedRec *packed, int64_t n, uint64_t *const *tree_dst)
+__global__ void pack_kernel(const PackedRec *packed, int64_t n, uint64_t *const *tree_dst, uint64_t *const *tree_cdst)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const PackedRec p = packed[i];
     tree_dst[p.tree][p.pos] = p.node;
+    tree_cdst[p.tree][p.pos] = p.cnode;
 }
 
 // a tree with an odd node count is padded by one never-reached leaf of value 0
-__global__ void pad_kernel(const uint32_t *counts, int64_t T, uint64_t *const *tree_dst)
+__global__ void pad_kernel(const uint32_t *counts, int64_t T, uint64_t *const *tree_dst, uint64_t *const *tree_cdst)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     const uint32_t c = counts[t];
-    if (c & 1u) tree_dst[t][c] = 1ull << 63;
+    if (c & 1u) { tree_dst[t][c] = 1ull << 63; tree_cdst[t][c] = 1ull << 63; }
 }
 
 __global__ void check_y_kernel(const int64_t *y, int64_t n, uint32_t *err)
@@ -1277,14 +1279,10 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         bool keep = false;
         ~Guard() {
             if (keep) return;
-            for (auto f : *v) {
-                if (!f) continue;
-                cudaFree(f->d_nodes); cudaFree(f->d_tree_off);
-                delete f;
-            }
+            for (auto f : *v) forest_release(f);
         }
     } guard{&forests};
-    std::vector<uint64_t *> h_dst((size_t)T);
+    std::vector<uint64_t *> h_dst((size_t)T), h_cdst((size_t)T);
     for (int32_t g = 0; g < G; ++g) {
         aiwcrf_forest *fr = new aiwcrf_forest();
         forests[(size_t)g] = fr;
@@ -1297,10 +1295,22 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         }
         fr->num_nodes = fr->tree_off[(size_t)Tper];
         AIWCRF_CUDA(cudaMalloc(&fr->d_nodes, sizeof(uint64_t) * (size_t)std::max<int64_t>(fr->num_nodes, 2)));
+        AIWCRF_CUDA(cudaMalloc(&fr->d_cnodes, sizeof(uint64_t) * (size_t)std::max<int64_t>(fr->num_nodes, 2)));
         AIWCRF_CUDA(cudaMalloc(&fr->d_tree_off, sizeof(int64_t) * (size_t)(Tper + 1)));
+        // the training value tables code the queries at predict time
+        fr->max_card = max_card;
+        fr->fstride = std::max<int64_t>(max_card, 1);
+        AIWCRF_CUDA(cudaMalloc(&fr->d_fvals, sizeof(float) * (size_t)F * (size_t)fr->fstride));
+        AIWCRF_CUDA(cudaMalloc(&fr->d_fcard, sizeof(uint32_t) * (size_t)F));
+        AIWCRF_CUDA(cudaMemcpy2DAsync(fr->d_fvals, sizeof(float) * (size_t)fr->fstride, d_vals, sizeof(float) * (size_t)N,
+                                      sizeof(float) * (size_t)max_card, (size_t)F, cudaMemcpyDeviceToDevice, s));
+        AIWCRF_CUDA(cudaMemcpyAsync(fr->d_fcard, d_card, sizeof(uint32_t) * (size_t)F, cudaMemcpyDeviceToDevice, s));
         AIWCRF_CUDA(cudaMemcpyAsync(fr->d_tree_off, fr->tree_off.data(), sizeof(int64_t) * (size_t)(Tper + 1),
                                     cudaMemcpyHostToDevice, s));
-        for (int64_t k = 0; k < Tper; ++k) h_dst[(size_t)(g * Tper + k)] = fr->d_nodes + fr->tree_off[(size_t)k];
+        for (int64_t k = 0; k < Tper; ++k) {
+            h_dst[(size_t)(g * Tper + k)] = fr->d_nodes + fr->tree_off[(size_t)k];
+            h_cdst[(size_t)(g * Tper + k)] = fr->d_cnodes + fr->tree_off[(size_t)k];
+        }
         fr->stats.num_trees = Tper;
         fr->stats.total_nodes = 0;
         for (int64_t k = 0; k < Tper; ++k) fr->stats.total_nodes += h_tot[(size_t)(g * Tper + k)];
@@ -1318,12 +1328,13 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
             fr->stats.entries_partitioned_small = (int64_t)hs.entries_partitioned_small;
         }
     }
-    uint64_t **d_dst = sc.get<uint64_t *>((size_t)T, &rc); if (rc) return rc;
+    uint64_t **d_dst = sc.get<uint64_t *>(2 * (size_t)T, &rc); if (rc) return rc;
     AIWCRF_CUDA(cudaMemcpyAsync(d_dst, h_dst.data(), sizeof(uint64_t *) * (size_t)T, cudaMemcpyHostToDevice, s));
+    AIWCRF_CUDA(cudaMemcpyAsync(d_dst + T, h_cdst.data(), sizeof(uint64_t *) * (size_t)T, cudaMemcpyHostToDevice, s));
     prof_begin(s, kProfPack);
-    pack_kernel<<<(unsigned)((packed_n + 255) / 256), 256, 0, s>>>(packed, (int64_t)packed_n, d_dst);
+    pack_kernel<<<(unsigned)((packed_n + 255) / 256), 256, 0, s>>>(packed, (int64_t)packed_n, d_dst, d_dst + T);
     AIWCRF_LAUNCH_CHECK("pack_kernel");
-    pad_kernel<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(tree_base, T, d_dst);
+    pad_kernel<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(tree_base, T, d_dst, d_dst + T);
     AIWCRF_LAUNCH_CHECK("pad_kernel");
     prof_end(s, kProfPack);
     sc.release();

@@ -277,9 +277,19 @@ struct SplitRes {         // outcome of one active node
 
 struct PackedRec {        // a finished node waiting for the final packing
     uint64_t node;        // encoded node (see aiwcrf.h), child index relative to its tree
+    uint64_t cnode;       // the same node with its threshold replaced by its rank code
     uint32_t tree;
     uint32_t pos;         // BFS position within the tree
 };
+
+// Rank-coded copy of a split used by predict: bits 0..23 the threshold's index in the
+// feature's sorted value table, bits 32..55 left child, bits 56..62 feature; leaves unchanged.
+// A query value x is coded as c(x) = #{table values < x} (NaN: the table size), and
+// x <= table[r]  <=>  c(x) <= r, so the coded walk takes exactly the float walk's path.
+__device__ __forceinline__ uint64_t encode_split_coded(int f, uint32_t left, uint32_t code)
+{
+    return ((uint64_t)(uint32_t)f << 56) | ((uint64_t)left << 32) | (uint64_t)code;
+}
 
 __device__ __forceinline__ uint64_t encode_split(int f, uint32_t left, uint32_t thr_bits)
 {
@@ -337,10 +347,19 @@ struct aiwcrf_forest {
     int64_t max_tree_nodes = 0;
     int device = 0;
     uint64_t *d_nodes = nullptr;          // packed nodes
+    uint64_t *d_cnodes = nullptr;         // the same nodes, thresholds as rank codes
     int64_t *d_tree_off = nullptr;        // T + 1 offsets (in nodes)
+    float *d_fvals = nullptr;             // per feature sorted value table [F][fstride]
+    uint32_t *d_fcard = nullptr;          // per feature table size
+    int64_t fstride = 0;
+    uint32_t max_card = 0;
     std::vector<int64_t> tree_off;        // host copy
     aiwcrf_fit_stats stats = {};
 };
+
+namespace aiwcrf {
+void forest_release(aiwcrf_forest *f);
+}
 
 namespace aiwcrf {
 // implemented in fit.cu / predict.cu

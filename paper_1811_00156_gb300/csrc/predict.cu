@@ -1,12 +1,15 @@
 // predict.cu -- forest queries (Sec. I, Sec. V) and device selection (Sec. VI).
 //
-// predict_kernel: one CTA owns 256 * QPT queries, whose features it stages once in shared
-// memory ([query][F + 1] floats, conflict-free across queries). It then walks every tree of
-// the forest for all its queries. Trees stream through two shared-memory slots with 1-D bulk
-// asynchronous copies (cp.async.bulk, completion counted on an mbarrier): while the CTA walks
-// tree t from one slot, tree t + 1 is landing in the other. A tree larger than a slot is
-// walked straight from global memory. Per-query sums are exact int64 (plus an exact 128-bit
-// sum of squares for the variance), so the result does not depend on any ordering.
+// code_queries_kernel turns every query feature into its rank code c(x) = #{training values of
+// the feature < x}; the forest keeps a copy of its nodes whose thresholds are the ranks of the
+// training values they are, and x <= threshold  <=>  c(x) <= rank, so the walk is exact.
+// predict_kernel: one CTA owns 256 * QPT queries whose codes (one byte per feature when every
+// column has at most 255 values) it stages once in shared memory. It then walks every tree for
+// all its queries, QPT independent walks per thread. Trees stream through two shared-memory
+// slots with 1-D bulk asynchronous copies (cp.async.bulk, completion counted on an mbarrier):
+// while the CTA walks tree t from one slot, tree t + 1 is landing in the other. A tree larger
+// than a slot is walked straight from global memory. Per-query sums are exact int64 (plus an
+// exact 128-bit sum of squares for the variance), so the result does not depend on any order.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -92,26 +95,76 @@ __device__ __forceinline__ int64_t leaf_value(uint64_t nd)
     return ((int64_t)(nd << 1)) >> 1;
 }
 
-__device__ __forceinline__ uint32_t next_node(uint64_t nd, const float *x)
+// c(x) = #{table values < x}; NaN goes right of every threshold (c = table size)
+template <typename CT>
+__global__ void code_queries_kernel(const float *__restrict__ Xq, int64_t Q, int F, const float *__restrict__ fvals,
+                                    int64_t fstride, const uint32_t *__restrict__ fcard, CT *__restrict__ codes,
+                                    int ld)
 {
-    const uint32_t f = (uint32_t)(nd >> 56) & 0x7Fu;
-    const uint32_t lc = (uint32_t)(nd >> 32) & 0xFFFFFFu;
-    return lc + (x[f] <= __uint_as_float((uint32_t)nd) ? 0u : 1u);
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int f = blockIdx.y;
+    if (q >= Q) return;
+    const float x = Xq[(size_t)f * (size_t)Q + q];
+    const float *V = fvals + (size_t)f * (size_t)fstride;
+    uint32_t lo = 0, hi = fcard[f];
+    if (x != x) {
+        lo = hi;
+    } else {
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (__ldg(&V[mid]) < x) lo = mid + 1;
+            else hi = mid;
+        }
+    }
+    codes[(size_t)q * (size_t)ld + f] = (CT)lo;
 }
 
-template <int QPT, bool VAR>
+// One step of QPT independent walks through one tree (coded thresholds).
+template <typename CT, int QPT, typename NodePtr>
+__device__ __forceinline__ void walk_tree(NodePtr tn, const CT *const (&xr)[QPT], int64_t (&acc)[QPT],
+                                          u128_t (&sq)[QPT], bool var)
+{
+    uint32_t j[QPT];
+#pragma unroll
+    for (int i = 0; i < QPT; ++i) j[i] = 0u;
+    for (;;) {
+        bool more = false;
+#pragma unroll
+        for (int i = 0; i < QPT; ++i) {
+            const uint64_t nd = tn[j[i]];
+            const uint32_t hi = (uint32_t)(nd >> 32);
+            const bool leaf = (int32_t)hi < 0;
+            const uint32_t f = leaf ? 0u : ((hi >> 24) & 0x7Fu);
+            const uint32_t c = (uint32_t)xr[i][f];
+            const uint32_t nxt = (hi & 0xFFFFFFu) + (c > ((uint32_t)nd & 0xFFFFFFu) ? 1u : 0u);
+            j[i] = leaf ? j[i] : nxt;
+            more |= !leaf;
+        }
+        if (!more) break;
+    }
+#pragma unroll
+    for (int i = 0; i < QPT; ++i) {
+        const int64_t v = leaf_value(tn[j[i]]);
+        acc[i] += v;
+        if (var) sq[i] += (u128_t)((i128_t)v * (i128_t)v);
+    }
+}
+
+// Coded walk. The CTA's 256 * QPT query codes sit in shared memory as rows of ld_words
+// 32-bit words (an odd count, so neighbouring queries hit different banks).
+template <typename CT, int QPT, bool VAR>
 __global__ void __launch_bounds__(kPredThreads) predict_kernel(
-    const uint64_t *__restrict__ nodes, const int64_t *__restrict__ tree_off, int T, const float *__restrict__ Xq,
-    int64_t Q, int F, int64_t total_trees, int tree_cap, int64_t *out_sum, int64_t *out_pred, uint64_t *out_var,
-    uint32_t *err)
+    const uint64_t *__restrict__ nodes, const int64_t *__restrict__ tree_off, int T, const CT *__restrict__ codes,
+    int64_t Q, int ld_words, int64_t total_trees, int tree_cap, int64_t *out_sum, int64_t *out_pred,
+    uint64_t *out_var, uint32_t *err)
 {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     __shared__ __align__(8) uint64_t bar[2];
     uint64_t *slot0 = reinterpret_cast<uint64_t *>(sm_raw);
     uint64_t *slot1 = slot0 + tree_cap;
-    float *xs = reinterpret_cast<float *>(slot1 + tree_cap);
+    uint32_t *xw = reinterpret_cast<uint32_t *>(slot1 + tree_cap);
     const int tid = threadIdx.x;
-    const int QT = kPredThreads * QPT, ld = F + 1;
+    const int QT = kPredThreads * QPT;
     const int64_t q0 = (int64_t)blockIdx.x * QT;
 
     if (tid == 0) {
@@ -119,12 +172,13 @@ __global__ void __launch_bounds__(kPredThreads) predict_kernel(
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
-    for (int f = 0; f < F; ++f) {
-        const float *col = Xq + (size_t)f * (size_t)Q;
-        for (int k = tid; k < QT; k += kPredThreads) {
-            const int64_t q = q0 + k;
-            xs[k * ld + f] = q < Q ? col[q] : 0.0f;
-        }
+    // stage the tile's codes: global rows of ld_words words -> shared rows of ld_words words
+    {
+        const uint32_t *gw = reinterpret_cast<const uint32_t *>(codes);
+        const int64_t nq = min((int64_t)QT, Q - q0);
+        const int64_t words = nq * ld_words;
+        const uint32_t *src = gw + (size_t)q0 * (size_t)ld_words;
+        for (int64_t k = tid; k < words; k += kPredThreads) xw[k] = src[k];
     }
     __syncthreads();
     if (tid == 0) {
@@ -132,6 +186,10 @@ __global__ void __launch_bounds__(kPredThreads) predict_kernel(
         if (T > 1) issue_tree(nodes, tree_off, 1, tree_cap, slot1, &bar[1]);
     }
 
+    const CT *xr[QPT];
+#pragma unroll
+    for (int i = 0; i < QPT; ++i)
+        xr[i] = reinterpret_cast<const CT *>(xw + (size_t)(tid + i * kPredThreads) * (size_t)ld_words);
     int64_t acc[QPT];
     u128_t sq[QPT];
 #pragma unroll
@@ -140,45 +198,25 @@ __global__ void __launch_bounds__(kPredThreads) predict_kernel(
     for (int t = 0; t < T; ++t) {
         const int s = t & 1;
         const uint32_t parity = (uint32_t)((t >> 1) & 1);
-        uint64_t *slot = s ? slot1 : slot0;
         bool ok = false;
         for (uint32_t it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(&bar[s], parity);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicOr(err, kErrTimeout);
-            // give the other slot's copy a bounded chance to land before the CTA exits
-            for (uint32_t it = 0; it < kWaitLimit; ++it)
-                if (mbar_try_wait(&bar[s ^ 1], parity ^ (uint32_t)(s == 1))) break;
+            // give the other slot's copy (tree t + 1) a bounded chance to land before exiting
+            if (t + 1 < T)
+                for (uint32_t it = 0; it < kWaitLimit; ++it)
+                    if (mbar_try_wait(&bar[s ^ 1], (uint32_t)(((t + 1) >> 1) & 1))) break;
             return;
         }
         const int64_t a = tree_off[t];
-        const bool fits = tree_off[t + 1] - a <= tree_cap;
-        const uint64_t *tn = fits ? slot : nodes + a;
-
-        uint32_t j[QPT];
-        bool done[QPT];
-#pragma unroll
-        for (int i = 0; i < QPT; ++i) { j[i] = 0u; done[i] = false; }
-        bool all = false;
-        while (!all) {
-            all = true;
-#pragma unroll
-            for (int i = 0; i < QPT; ++i) {
-                if (!done[i]) {
-                    const uint64_t nd = tn[j[i]];
-                    if ((int64_t)nd < 0) {
-                        const int64_t v = leaf_value(nd);
-                        acc[i] += v;
-                        if (VAR) sq[i] += (u128_t)((i128_t)v * (i128_t)v);
-                        done[i] = true;
-                    } else {
-                        j[i] = next_node(nd, xs + (tid + i * kPredThreads) * ld);
-                        all = false;
-                    }
-                }
-            }
+        if (tree_off[t + 1] - a <= tree_cap) {
+            if (s) walk_tree<CT, QPT>(slot1, xr, acc, sq, VAR);
+            else walk_tree<CT, QPT>(slot0, xr, acc, sq, VAR);
+        } else {
+            walk_tree<CT, QPT>(nodes + a, xr, acc, sq, VAR);
         }
         __syncthreads();
-        if (tid == 0 && t + 2 < T) issue_tree(nodes, tree_off, t + 2, tree_cap, slot, &bar[s]);
+        if (tid == 0 && t + 2 < T) issue_tree(nodes, tree_off, t + 2, tree_cap, s ? slot1 : slot0, &bar[s]);
     }
 
 #pragma unroll
@@ -241,31 +279,50 @@ __global__ void argmin_kernel(const int64_t *pred, const int32_t *dev, int32_t K
 
 namespace {
 
-template <int QPT, bool VAR>
+constexpr int kQPT = 4;
+
+template <typename CT, bool VAR>
 int launch_predict(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum, int64_t *d_pred,
                    uint64_t *d_var, int64_t total_trees, cudaStream_t s, uint32_t *d_err)
 {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const int xs_bytes = kPredThreads * QPT * (f->F + 1) * 4;
-    int budget = optin - xs_bytes - 1024;
-    // two slots, each a whole number of 16-byte units, capped at 48 KB
-    int tree_cap = std::min<int>(budget / 16, 6144);
+    int ld_words = (int)((f->F * (int)sizeof(CT) + 3) / 4);
+    if ((ld_words & 1) == 0) ++ld_words;                       // odd: conflict-free rows
+    const int ld = ld_words * 4 / (int)sizeof(CT);
+    CT *d_codes = nullptr;
+    cudaError_t e = cudaMallocAsync(&d_codes, (size_t)Q * (size_t)ld_words * 4, s);
+    if (e != cudaSuccess) return fail(AIWCRF_E_OOM, "device allocation of the query codes failed");
+    struct Free { CT *p; cudaStream_t s; ~Free() { cudaFreeAsync(p, s); } } fr{d_codes, s};
+    code_queries_kernel<CT><<<dim3((unsigned)((Q + 255) / 256), (unsigned)f->F), 256, 0, s>>>(
+        dXq, Q, f->F, f->d_fvals, f->fstride, f->d_fcard, d_codes, ld);
+    count_launches(1);
+    const int xs_bytes = kPredThreads * kQPT * ld_words * 4;
+    // two tree slots, sized to the largest tree up to 48 KB each
+    int tree_cap = std::min<int>((optin - xs_bytes - 1024) / 16, 6144);
+    if ((int64_t)tree_cap > f->max_tree_nodes) tree_cap = (int)f->max_tree_nodes;
     tree_cap &= ~1;
-    if ((int64_t)tree_cap > f->max_tree_nodes) tree_cap = (int)((f->max_tree_nodes + 1) & ~(int64_t)1);
     if (tree_cap < 2) tree_cap = 2;
     const int smem = 2 * tree_cap * 8 + xs_bytes;
-    auto kern = predict_kernel<QPT, VAR>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    auto kern = predict_kernel<CT, kQPT, VAR>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(predict_kernel)");
-    const int64_t grid = (Q + (int64_t)kPredThreads * QPT - 1) / ((int64_t)kPredThreads * QPT);
-    kern<<<(unsigned)grid, kPredThreads, smem, s>>>(f->d_nodes, f->d_tree_off, (int)f->T, dXq, Q, f->F,
+    const int64_t grid = (Q + (int64_t)kPredThreads * kQPT - 1) / ((int64_t)kPredThreads * kQPT);
+    kern<<<(unsigned)grid, kPredThreads, smem, s>>>(f->d_cnodes, f->d_tree_off, (int)f->T, d_codes, Q, ld_words,
                                                     total_trees, tree_cap, d_sum, d_pred, d_var, d_err);
     count_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "predict_kernel launch");
     return AIWCRF_OK;
+}
+
+template <typename CT>
+int launch_predict_ct(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum, int64_t *d_pred,
+                      uint64_t *d_var, int64_t total_trees, cudaStream_t s, uint32_t *d_err)
+{
+    return d_var ? launch_predict<CT, true>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err)
+                 : launch_predict<CT, false>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err);
 }
 
 }  // namespace
@@ -280,13 +337,9 @@ int predict_launch(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t 
     cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s);
     prof_begin(s, kProfPredict);
     int rc;
-    if (f->F <= 48) {
-        rc = d_var ? launch_predict<2, true>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err)
-                   : launch_predict<2, false>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err);
-    } else {
-        rc = d_var ? launch_predict<1, true>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err)
-                   : launch_predict<1, false>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err);
-    }
+    if (f->max_card <= 255u) rc = launch_predict_ct<uint8_t>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err);
+    else if (f->max_card <= 65535u) rc = launch_predict_ct<uint16_t>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err);
+    else rc = launch_predict_ct<uint32_t>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err);
     prof_end(s, kProfPredict);
     uint32_t h_err = 0;
     if (rc == AIWCRF_OK) {

@@ -265,3 +265,24 @@ def test_aiwc_111000_full_forest_predictions_vs_oracle():
     P = sum(part.predict(Xq, total_trees=T)[1].astype(object) for part in parts)
     exp = np.array([(2 * int(s) + T) // (2 * T) for s in P], np.int64)
     assert np.array_equal(gpu_predict(f, Xq), exp)
+
+
+def test_predict_special_query_values():
+    """Coded walks must take the float walk's path for NaN, signed zeros, infinities, training
+    values themselves and values between or beyond them."""
+    rng = np.random.default_rng(12)
+    X = rng.integers(-3, 4, (4, 900)).astype(np.float32) * np.float32(0.5)
+    X[X == 0] = np.where(rng.random((X == 0).sum()) < 0.5, -0.0, 0.0)
+    y = rng.integers(-1 << 36, 1 << 36, 900).astype(np.int64)
+    wl = synth.Workload(X=X, y=y, name="special")
+    f = gpu_fit(wl, 9, 2, 1)
+    ref = O.fit(X, y, 9, 2, 1, seed=156)
+    specials = np.array([np.nan, -0.0, 0.0, np.inf, -np.inf, -1.5, -1.25, 1.5, 1.75, 99.0, -99.0, 0.25],
+                        np.float32)
+    Xq = rng.choice(specials, size=(4, 5000)).astype(np.float32)
+    assert np.array_equal(gpu_predict(f, Xq), ref.predict(Xq)[0])
+    g = A.aiwcrf_forest_deserialize(f.serialize())          # thresholds-only value tables
+    out = torch.empty(5000, dtype=torch.int64, device="cuda")
+    A.aiwcrf_predict(g, dev(Xq), out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), ref.predict(Xq)[0])
