@@ -398,6 +398,9 @@ __global__ void __launch_bounds__(kSmallThreads) level_small_kernel(LevelArgs a)
     uint32_t mask[4];
     warp_mtry(a, a.tree_rng[nd.tree], nd.idx, mask);
 
+    // sorting network width: the smallest power of two >= the node's entries; lanes at or
+    // above it hold no entry and only ever exchange among themselves
+    const int K = nd.len <= 2 ? 2 : (int)(1u << (32 - __clz((int)nd.len - 1)));
     Cand best = cand_none();
     for (int c = 0; c < 4; ++c) {
         uint32_t m = mask[c];
@@ -405,13 +408,15 @@ __global__ void __launch_bounds__(kSmallThreads) level_small_kernel(LevelArgs a)
             const int f = c * 32 + __ffs(m) - 1;
             m &= m - 1;
             const uint32_t rank = valid ? (uint32_t)__ldg(&Rr[rec + f]) : kRankSentinel;
+            // a feature constant over the node has no boundary (lane 0 always holds an entry;
+            // the shuffle runs in every lane before the vote)
+            const uint32_t rank0 = __shfl_sync(kFull, rank, 0);
+            if (__all_sync(kFull, !valid || rank == rank0)) continue;
             uint32_t key = (rank << 5) | (uint32_t)lane;                 // unique per lane
             uint32_t w = e.w;
             long long v = e.wy;
-            // bitonic sort of (key, w, v) across the warp, ascending key
-#pragma unroll
-            for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
+            // bitonic sort of (key, w, v) over lanes [0, K), ascending key
+            for (int k = 2; k <= K; k <<= 1) {
                 for (int jj = k >> 1; jj > 0; jj >>= 1) {
                     const uint32_t ok = __shfl_xor_sync(kFull, key, jj);
                     const uint32_t ow = __shfl_xor_sync(kFull, w, jj);
@@ -425,8 +430,7 @@ __global__ void __launch_bounds__(kSmallThreads) level_small_kernel(LevelArgs a)
             const uint32_t r = key >> 5;
             uint32_t cw = w;
             long long cs = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
+            for (int o = 1; o < K; o <<= 1) {
                 const uint32_t tw = __shfl_up_sync(kFull, cw, o);
                 const long long ts = __shfl_up_sync(kFull, cs, o);
                 if (lane >= o) { cw += tw; cs += ts; }
