@@ -133,6 +133,27 @@ int aiwcrf_select_device(const aiwcrf_forest *forest, const float *kfeat, int32_
                          int32_t size_class, const int32_t *device_ids, int32_t n_devices,
                          int32_t *out_best, int64_t *out_pred, void *cuda_stream);
 
+/* Device selection that allocates no device memory (the paper has no counterpart; this is for
+ * callers that cannot allocate). aiwcrf_select_device allocates scratch on the stream; a
+ * caller such as a scheduler hook living inside another application, whose device memory is
+ * owned by that application's allocator and which must not trigger the device-wide
+ * synchronisation a cudaMalloc/cudaFree can cause, uses this variant instead. Same inputs,
+ * outputs and results as aiwcrf_select_device, except:
+ *  - kfeat, out_best and out_pred (or NULL) must be memory of the current device
+ *    (AIWCRF_E_BAD_POINTER otherwise); device_ids is a host array as before.
+ *  - Scratch is one static device array of AIWCRF_NOALLOC_SCRATCH_BYTES that every GPU loading
+ *    the library holds until the process exits. A request needs about
+ *    (4F + 8 + 4 * code words) bytes per (kernel, device) pair (F = 32: 172 bytes, so about
+ *    6,000 pairs fit); a larger request fails with AIWCRF_E_LIMIT before launching anything.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ *    make that first call before any stream capture.
+ *  - Every call reuses the same array: calls that overlap on the GPU (other streams, other
+ *    host threads) race on it. The call synchronises its stream before returning. */
+#define AIWCRF_NOALLOC_SCRATCH_BYTES (1 << 20)
+int aiwcrf_select_device_noalloc(const aiwcrf_forest *forest, const float *kfeat, int32_t n_kernels,
+                                 int32_t size_class, const int32_t *device_ids, int32_t n_devices,
+                                 int32_t *out_best, int64_t *out_pred, void *cuda_stream);
+
 /* Counters of the fit that produced the forest (zeros for a deserialized forest). */
 int aiwcrf_forest_stats(const aiwcrf_forest *forest, aiwcrf_fit_stats *out);
 

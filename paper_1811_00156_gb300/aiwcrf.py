@@ -48,7 +48,8 @@ EXPORTS = ["aiwcrf_fit", "aiwcrf_fit_subsets", "aiwcrf_predict", "aiwcrf_predict
            "aiwcrf_round_mean", "aiwcrf_select_device", "aiwcrf_forest_stats", "aiwcrf_forest_info",
            "aiwcrf_forest_serialize", "aiwcrf_forest_deserialize", "aiwcrf_forest_free",
            "aiwcrf_last_error", "aiwcrf_profile_enable", "aiwcrf_profile_read",
-           "aiwcrf_profile_name", "aiwcrf_profile_num_classes", "aiwcrf_launch_count"]
+           "aiwcrf_profile_name", "aiwcrf_profile_num_classes", "aiwcrf_launch_count",
+           "aiwcrf_select_device_noalloc"]
 
 _lib = None
 _lock = threading.Lock()
@@ -72,6 +73,7 @@ def load():
         L.aiwcrf_predict_sum.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
         L.aiwcrf_round_mean.argtypes = [_vp, C.c_int64, C.c_int64, _vp, _vp]
         L.aiwcrf_select_device.argtypes = [_vp, _vp, C.c_int32, C.c_int32, _vp, C.c_int32, _vp, _vp, _vp]
+        L.aiwcrf_select_device_noalloc.argtypes = [_vp, _vp, C.c_int32, C.c_int32, _vp, C.c_int32, _vp, _vp, _vp]
         L.aiwcrf_forest_stats.argtypes = [_vp, C.POINTER(FitStats)]
         L.aiwcrf_forest_info.argtypes = [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
         L.aiwcrf_forest_serialize.argtypes = [_vp, _vp, C.c_size_t, C.POINTER(C.c_size_t)]
@@ -199,6 +201,17 @@ def aiwcrf_select_device(forest: Forest, kfeat, size_class: int, device_ids, out
     dev = np.ascontiguousarray(device_ids, dtype=np.int32)
     _check(load().aiwcrf_select_device(forest.handle, _ptr(kfeat), K, int(size_class), dev.ctypes.data,
                                        int(dev.size), _ptr(out_best), _ptr(out_pred), _stream(stream)))
+    return out_best
+
+
+def aiwcrf_select_device_noalloc(forest: Forest, kfeat, size_class: int, device_ids, out_best, out_pred=None,
+                                 stream=None):
+    """Same as aiwcrf_select_device without any device allocation: kfeat and the outputs must be
+    device tensors; the library's static scratch array limits the request size."""
+    Fm2, K = _shape(kfeat)
+    dev = np.ascontiguousarray(device_ids, dtype=np.int32)
+    _check(load().aiwcrf_select_device_noalloc(forest.handle, _ptr(kfeat), K, int(size_class), dev.ctypes.data,
+                                               int(dev.size), _ptr(out_best), _ptr(out_pred), _stream(stream)))
     return out_best
 
 

@@ -373,4 +373,8 @@ int round_mean_launch(const int64_t *d_sum, int64_t Q, int64_t total_trees, int6
 int select_launch(const aiwcrf_forest *f, const float *d_kfeat, int32_t K, int32_t size_class,
                   const int32_t *d_dev, int32_t D, int32_t *d_best, int64_t *d_pred,
                   float *d_scratch_q, int64_t *d_scratch_p, cudaStream_t s);
+size_t select_noalloc_bytes(const aiwcrf_forest *f, int32_t K, int32_t D);
+int select_launch_noalloc(const aiwcrf_forest *f, const float *d_kfeat, int32_t K, int32_t size_class,
+                          const int32_t *h_dev, int32_t D, int32_t *d_best, int64_t *d_pred, unsigned char *scratch,
+                          cudaStream_t s);
 }  // namespace aiwcrf

@@ -384,4 +384,101 @@ int select_launch(const aiwcrf_forest *f, const float *d_kfeat, int32_t K, int32
     return AIWCRF_OK;
 }
 
+// ------------------------------------------------------------------------------------------
+// Device selection inside caller-provided scratch (no allocation). Scratch layout, each part
+// 256-byte aligned: device ids (D int32), expanded queries (F x K*D float), query codes
+// (K*D rows of ld_words words), predictions (K*D int64), error flag (u32).
+// ------------------------------------------------------------------------------------------
+namespace {
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+int code_ld_words(const aiwcrf_forest *f)
+{
+    const int cb = f->max_card <= 255u ? 1 : (f->max_card <= 65535u ? 2 : 4);
+    int ld_words = (f->F * cb + 3) / 4;
+    if ((ld_words & 1) == 0) ++ld_words;
+    return ld_words;
+}
+
+template <typename CT>
+int select_noalloc_ct(const aiwcrf_forest *f, const float *d_kfeat, int32_t K, int32_t size_class, int32_t D,
+                      int32_t *d_best, int64_t *d_pred, const int32_t *d_dev, float *d_q, uint32_t *d_codes,
+                      int64_t *d_p, uint32_t *d_err, cudaStream_t s)
+{
+    const int64_t Qn = (int64_t)K * D;
+    const int ld_words = code_ld_words(f);
+    const int ld = ld_words * 4 / (int)sizeof(CT);
+    expand_queries_kernel<<<(unsigned)((Qn + 255) / 256), 256, 0, s>>>(d_kfeat, K, size_class, d_dev, D, f->F, d_q);
+    code_queries_kernel<CT><<<dim3((unsigned)((Qn + 255) / 256), (unsigned)f->F), 256, 0, s>>>(
+        d_q, Qn, f->F, f->d_fvals, f->fstride, f->d_fcard, reinterpret_cast<CT *>(d_codes), ld);
+    count_launches(2);
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int xs_bytes = kPredThreads * kQPT * ld_words * 4;
+    int tree_cap = std::min<int>((optin - xs_bytes - 1024) / 16, 6144);
+    if ((int64_t)tree_cap > f->max_tree_nodes) tree_cap = (int)f->max_tree_nodes;
+    tree_cap &= ~1;
+    if (tree_cap < 2) tree_cap = 2;
+    const int smem = 2 * tree_cap * 8 + xs_bytes;
+    auto kern = predict_kernel<CT, kQPT, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(predict_kernel)");
+    const int64_t grid = (Qn + (int64_t)kPredThreads * kQPT - 1) / ((int64_t)kPredThreads * kQPT);
+    kern<<<(unsigned)grid, kPredThreads, smem, s>>>(f->d_cnodes, f->d_tree_off, (int)f->T,
+                                                    reinterpret_cast<const CT *>(d_codes), Qn, ld_words, f->T,
+                                                    tree_cap, nullptr, d_p, nullptr, d_err);
+    argmin_kernel<<<(unsigned)((K + 127) / 128), 128, 0, s>>>(d_p, d_dev, K, D, d_best, d_pred);
+    count_launches(2);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "select_device launch");
+    return AIWCRF_OK;
+}
+
+}  // namespace
+
+size_t select_noalloc_bytes(const aiwcrf_forest *f, int32_t K, int32_t D)
+{
+    const size_t Qn = (size_t)K * (size_t)D;
+    return align256(sizeof(int32_t) * (size_t)D) + align256(sizeof(float) * (size_t)f->F * Qn) +
+           align256(Qn * (size_t)code_ld_words(f) * 4) + align256(sizeof(int64_t) * Qn) + align256(sizeof(uint32_t));
+}
+
+int select_launch_noalloc(const aiwcrf_forest *f, const float *d_kfeat, int32_t K, int32_t size_class,
+                          const int32_t *h_dev, int32_t D, int32_t *d_best, int64_t *d_pred, unsigned char *scratch,
+                          cudaStream_t s)
+{
+    const size_t Qn = (size_t)K * (size_t)D;
+    unsigned char *p = scratch;
+    int32_t *d_dev = reinterpret_cast<int32_t *>(p);
+    p += align256(sizeof(int32_t) * (size_t)D);
+    float *d_q = reinterpret_cast<float *>(p);
+    p += align256(sizeof(float) * (size_t)f->F * Qn);
+    uint32_t *d_codes = reinterpret_cast<uint32_t *>(p);
+    p += align256(Qn * (size_t)code_ld_words(f) * 4);
+    int64_t *d_p = reinterpret_cast<int64_t *>(p);
+    p += align256(sizeof(int64_t) * Qn);
+    uint32_t *d_err = reinterpret_cast<uint32_t *>(p);
+    cudaError_t e = cudaMemcpyAsync(d_dev, h_dev, sizeof(int32_t) * (size_t)D, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s);    // the flag must start at 0
+    if (e != cudaSuccess) return cuda_fail(e, "select_device scratch set-up");
+    prof_begin(s, kProfSelect);
+    int rc;
+    if (f->max_card <= 255u)
+        rc = select_noalloc_ct<uint8_t>(f, d_kfeat, K, size_class, D, d_best, d_pred, d_dev, d_q, d_codes, d_p, d_err, s);
+    else if (f->max_card <= 65535u)
+        rc = select_noalloc_ct<uint16_t>(f, d_kfeat, K, size_class, D, d_best, d_pred, d_dev, d_q, d_codes, d_p, d_err, s);
+    else
+        rc = select_noalloc_ct<uint32_t>(f, d_kfeat, K, size_class, D, d_best, d_pred, d_dev, d_q, d_codes, d_p, d_err, s);
+    prof_end(s, kProfSelect);
+    if (rc != AIWCRF_OK) return rc;
+    uint32_t h_err = 0;
+    e = cudaMemcpyAsync(&h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "select_device");
+    if (h_err & kErrTimeout) return fail(AIWCRF_E_TIMEOUT, "a bounded device wait gave up");
+    return AIWCRF_OK;
+}
+
 }  // namespace aiwcrf
