@@ -34,12 +34,56 @@ int cuda_fail(cudaError_t e, const char *what)
 void forest_release(aiwcrf_forest *f)
 {
     if (!f) return;
-    cudaFree(f->d_nodes);
-    cudaFree(f->d_cnodes);
-    cudaFree(f->d_tree_off);
-    cudaFree(f->d_fvals);
-    cudaFree(f->d_fcard);
+    cudaFree(f->d_block);
     delete f;
+}
+
+cudaError_t forest_alloc(aiwcrf_forest *f)
+{
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t nn = (size_t)std::max<int64_t>(f->num_nodes, 2);
+    const size_t b_nodes = up(8 * nn), b_off = up(8 * (size_t)(f->T + 1));
+    const size_t b_vals = up(sizeof(float) * (size_t)f->F * (size_t)f->fstride), b_card = up(4 * (size_t)f->F);
+    void *p = nullptr;
+    const cudaError_t e = cudaMalloc(&p, 2 * b_nodes + b_off + b_vals + b_card);
+    if (e != cudaSuccess) return e;
+    unsigned char *c = static_cast<unsigned char *>(p);
+    f->d_block = p;
+    f->d_nodes = reinterpret_cast<uint64_t *>(c);
+    f->d_cnodes = reinterpret_cast<uint64_t *>(c + b_nodes);
+    f->d_tree_off = reinterpret_cast<int64_t *>(c + 2 * b_nodes);
+    f->d_fvals = reinterpret_cast<float *>(c + 2 * b_nodes + b_off);
+    f->d_fcard = reinterpret_cast<uint32_t *>(c + 2 * b_nodes + b_off + b_vals);
+    return cudaSuccess;
+}
+
+void keep_pool_memory(int device)
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    std::lock_guard<std::mutex> lk(mu);
+    if (device < 0 || device >= 64 || done[device]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done[device] = true;
+}
+
+void *pinned_scratch()
+{
+    struct Buf {
+        void *p = nullptr;
+        ~Buf() { if (p) cudaFreeHost(p); }
+    };
+    static thread_local Buf b;
+    if (!b.p && cudaMallocHost(&b.p, 4096) != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+    }
+    return b.p;
 }
 
 static std::atomic<long long> g_launches{0};
@@ -511,11 +555,7 @@ int aiwcrf_forest_deserialize(const void *buf, size_t len, aiwcrf_forest **out)
     f->tree_off = off;
     f->max_card = max_card;
     f->fstride = fstride;
-    cudaError_t e = cudaMalloc(&f->d_nodes, 8 * (size_t)nn);
-    if (e == cudaSuccess) e = cudaMalloc(&f->d_cnodes, 8 * (size_t)nn);
-    if (e == cudaSuccess) e = cudaMalloc(&f->d_tree_off, 8 * (size_t)(T + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&f->d_fvals, sizeof(float) * fv.size());
-    if (e == cudaSuccess) e = cudaMalloc(&f->d_fcard, sizeof(uint32_t) * fc.size());
+    cudaError_t e = forest_alloc(f);
     if (e == cudaSuccess) e = cudaMemcpy(f->d_nodes, nodes, 8 * (size_t)nn, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(f->d_cnodes, cnodes.data(), 8 * (size_t)nn, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(f->d_tree_off, off.data(), 8 * (size_t)(T + 1), cudaMemcpyHostToDevice);

@@ -138,28 +138,26 @@ __device__ __forceinline__ bool same_record(const RT *Rr, int F, uint32_t a, uin
     return true;
 }
 
-// rows sorted by hash -> groups of adjacent rows with the same hash and the same record.
-// grp_off[g] = first sorted position of group g (grp_off[G] = N); G is written to *n_groups.
+// rows sorted by hash -> groups of adjacent rows with the same hash and the same record:
+// flag[i] = 1 where sorted position i starts a group
 template <typename RT>
-__global__ void __launch_bounds__(1024) group_kernel(const RT *__restrict__ Rr, int64_t N, int F,
-                                                     const uint32_t *__restrict__ hkeys,
-                                                     const uint32_t *__restrict__ rows, uint32_t *grp_off,
-                                                     uint32_t *n_groups)
+__global__ void group_flags_kernel(const RT *__restrict__ Rr, int64_t N, int F, const uint32_t *__restrict__ hkeys,
+                                   const uint32_t *__restrict__ rows, uint32_t *__restrict__ flags)
 {
-    __shared__ uint32_t warp_tmp[32];
-    uint32_t running = 0;
-    for (int64_t t0 = 0; t0 < N; t0 += 1024) {
-        const int64_t i = t0 + threadIdx.x;
-        bool flag = false;
-        if (i < N) flag = i == 0 || hkeys[i] != hkeys[i - 1] || !same_record(Rr, F, rows[i], rows[i - 1]);
-        uint32_t tot;
-        const uint32_t incl = block_incl_scan(flag ? 1u : 0u, warp_tmp, tot);
-        if (flag) grp_off[running + incl - 1u] = (uint32_t)i;
-        running += tot;
-    }
-    if (threadIdx.x == 0) {
-        grp_off[running] = (uint32_t)N;
-        *n_groups = running;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    flags[i] = (i == 0 || hkeys[i] != hkeys[i - 1] || !same_record(Rr, F, rows[i], rows[i - 1])) ? 1u : 0u;
+}
+
+// grp_off[g] = first sorted position of group g, grp_off[G] = N, *n_groups = G
+__global__ void group_offsets_kernel(const uint32_t *__restrict__ flags, const uint32_t *__restrict__ excl, int64_t N,
+                                     uint32_t *__restrict__ grp_off, uint32_t *n_groups)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N && flags[i]) grp_off[excl[i]] = (uint32_t)i;
+    if (i == 0) {
+        grp_off[excl[N]] = (uint32_t)N;
+        *n_groups = excl[N];
     }
 }
 
@@ -286,12 +284,21 @@ __global__ void __launch_bounds__(kBootThreads) bootstrap_kernel(BootArgs a)
 }
 
 // ------------------------------------------------------------------------------------------
-// a3/a4/a5: one depth of growth
+// a3/a4/a5: one depth of growth. Every per-depth kernel reads its sizes from LevelCounts in
+// device memory, so the host can enqueue several depths without waiting for their results.
 // ------------------------------------------------------------------------------------------
+struct LevelCounts {
+    uint32_t n_small;             // nodes of the current depth searched by a warp
+    uint32_t n_big;               // nodes of the current depth searched by a CTA
+    uint32_t C;                   // nodes of the current depth
+    uint32_t levels;              // depths that held nodes so far
+    unsigned long long packed_off;    // finished nodes of the earlier depths
+};
+
 struct LevelArgs {
     const NodeRec *nodes;
     const int32_t *list;
-    int32_t list_n;
+    const uint32_t *list_n;       // n_small or n_big in LevelCounts
     const Entry *rows_in;
     Entry *rows_out;
     int64_t row_cap;
@@ -374,15 +381,9 @@ __device__ __forceinline__ void write_leaf(SplitRes *res, int j, int kind, int64
 
 constexpr int kSmallThreads = 256;
 
-// one warp per node with at most 32 entries
 template <typename RT>
-__global__ void __launch_bounds__(kSmallThreads) level_small_kernel(LevelArgs a)
+__device__ __forceinline__ void small_node(const LevelArgs &a, const RT *__restrict__ Rr, int j, int lane)
 {
-    const RT *__restrict__ Rr = static_cast<const RT *>(a.Rr);
-    const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * (kSmallThreads / 32) + (threadIdx.x >> 5);
-    if (gw >= a.list_n) return;                      // whole warp
-    const int j = a.list[gw];
     const NodeRec nd = a.nodes[j];
     if (node_stops(a, nd)) {
         if (lane == 0) write_leaf(a.res, j, -2, round_mean(nd.S, nd.n));
@@ -468,6 +469,20 @@ __global__ void __launch_bounds__(kSmallThreads) level_small_kernel(LevelArgs a)
     }
 }
 
+// one warp per node with at most 32 entries
+template <typename RT>
+__global__ void __launch_bounds__(kSmallThreads) level_small_kernel(LevelArgs a)
+{
+    const RT *__restrict__ Rr = static_cast<const RT *>(a.Rr);
+    const int lane = threadIdx.x & 31;
+    const uint32_t list_n = *a.list_n;
+    const uint32_t wstride = gridDim.x * (kSmallThreads / 32);
+    for (uint32_t gw = blockIdx.x * (kSmallThreads / 32) + (threadIdx.x >> 5); gw < list_n; gw += wstride) {
+        small_node(a, Rr, a.list[gw], lane);         // warp-uniform trip count
+    }
+}
+
+
 constexpr int kBigThreads = 256;
 constexpr int kBigWarps = kBigThreads / 32;
 constexpr int kRowsPerIter = 4;   // rows per thread per pass: independent gathers in flight
@@ -477,7 +492,7 @@ constexpr int kFeatChunk = 8;     // tried features whose ranks are loaded befor
 // of every tried feature: sum w (u32) and sum w*y as an exact (low u32, high i32) pair. All
 // updates are native 32-bit shared atomics; a wrap of the low word carries into the high word.
 template <typename RT>
-__global__ void __launch_bounds__(kBigThreads, 3) level_big_kernel(LevelArgs a, int bin_cap)
+__device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
 {
     const RT *__restrict__ Rr = static_cast<const RT *>(a.Rr);
     extern __shared__ uint32_t sm_bins[];
@@ -496,7 +511,6 @@ __global__ void __launch_bounds__(kBigThreads, 3) level_big_kernel(LevelArgs a, 
     __shared__ uint32_t warp_tmp[32];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int j = a.list[blockIdx.x];
     const NodeRec nd = a.nodes[j];
     if (node_stops(a, nd)) {
         if (tid == 0) write_leaf(a.res, j, -2, round_mean(nd.S, nd.n));
@@ -726,6 +740,17 @@ __global__ void __launch_bounds__(kBigThreads, 3) level_big_kernel(LevelArgs a, 
     }
 }
 
+// one CTA per node with more than 32 entries, strided over the depth's CTA list
+template <typename RT>
+__global__ void __launch_bounds__(kBigThreads, 3) level_big_kernel(LevelArgs a, int bin_cap)
+{
+    const uint32_t list_n = *a.list_n;
+    for (uint32_t k = blockIdx.x; k < list_n; k += gridDim.x) {
+        __syncthreads();                 // the previous node's shared state is no longer read
+        big_node<RT>(a, bin_cap, a.list[k]);
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // exclusive scan of the split flags (three passes, 4096 flags per block)
 // ------------------------------------------------------------------------------------------
@@ -733,47 +758,90 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanPer = 4;
 constexpr int kScanTile = kScanThreads * kScanPer;
 
-__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const SplitRes *res, int n, uint32_t *block_sums)
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const SplitRes *res, const LevelCounts *cnt,
+                                                                   uint32_t *block_sums)
 {
     __shared__ uint32_t warp_tmp[32];
-    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanPer;
-    uint32_t c = 0;
+    const int n = (int)cnt->C;
+    const int ntiles = (n + kScanTile - 1) / kScanTile;
+    for (int b = blockIdx.x; b < ntiles; b += gridDim.x) {
+        const int base = b * kScanTile + threadIdx.x * kScanPer;
+        uint32_t c = 0;
 #pragma unroll
-    for (int k = 0; k < kScanPer; ++k) c += (base + k < n && res[base + k].feature >= 0) ? 1u : 0u;
-    uint32_t tot;
-    block_incl_scan(c, warp_tmp, tot);
-    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+        for (int k = 0; k < kScanPer; ++k) c += (base + k < n && res[base + k].feature >= 0) ? 1u : 0u;
+        uint32_t tot;
+        block_incl_scan(c, warp_tmp, tot);
+        if (threadIdx.x == 0) block_sums[b] = tot;
+    }
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(uint32_t *block_sums, int nblocks)
+// exclusive scan of nblocks block sums (nblocks from the count, or given when cnt is null)
+__global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(uint32_t *block_sums, int nblocks,
+                                                                   const LevelCounts *cnt = nullptr)
 {
     __shared__ uint32_t warp_tmp[32];
-    __shared__ uint32_t carry;
-    if (threadIdx.x == 0) carry = 0u;
-    __syncthreads();
+    if (cnt) nblocks = (int)((cnt->C + kScanTile - 1) / kScanTile);
+    uint32_t carry = 0;
     for (int b0 = 0; b0 < nblocks; b0 += kScanThreads) {
         const int b = b0 + threadIdx.x;
         const uint32_t v = b < nblocks ? block_sums[b] : 0u;
         uint32_t tot;
         const uint32_t incl = block_incl_scan(v, warp_tmp, tot);
         if (b < nblocks) block_sums[b] = carry + incl - v;
-        __syncthreads();
-        if (threadIdx.x == 0) carry += tot;
-        __syncthreads();
+        carry += tot;
     }
     if (threadIdx.x == 0) block_sums[nblocks] = carry;
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_write_kernel(const SplitRes *res, int n,
-                                                                  const uint32_t *block_sums, int nblocks,
-                                                                  uint32_t *excl)
+__global__ void __launch_bounds__(kScanThreads) scan_write_kernel(const SplitRes *res, const LevelCounts *cnt,
+                                                                  const uint32_t *block_sums, uint32_t *excl)
 {
     __shared__ uint32_t warp_tmp[32];
-    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanPer;
+    const int n = (int)cnt->C;
+    const int ntiles = (n + kScanTile - 1) / kScanTile;
+    for (int b = blockIdx.x; b < ntiles; b += gridDim.x) {
+        const int base = b * kScanTile + threadIdx.x * kScanPer;
+        uint32_t fl[kScanPer], c = 0;
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) {
+            fl[k] = (base + k < n && res[base + k].feature >= 0) ? 1u : 0u;
+            c += fl[k];
+        }
+        uint32_t tot;
+        const uint32_t incl = block_incl_scan(c, warp_tmp, tot);
+        uint32_t run = block_sums[b] + incl - c;
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) {
+            if (base + k < n) excl[base + k] = run;
+            run += fl[k];
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) excl[n] = block_sums[ntiles];
+}
+
+// the same three passes over a u32 flag array
+__global__ void __launch_bounds__(kScanThreads) flag_scan_reduce_kernel(const uint32_t *flags, int64_t n, uint32_t *block_sums)
+{
+    __shared__ uint32_t warp_tmp[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) c += base + k < n ? flags[base + k] : 0u;
+    uint32_t tot;
+    block_incl_scan(c, warp_tmp, tot);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) flag_scan_write_kernel(const uint32_t *flags, int64_t n,
+                                                                       const uint32_t *block_sums, int nblocks,
+                                                                       uint32_t *excl)
+{
+    __shared__ uint32_t warp_tmp[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
     uint32_t fl[kScanPer], c = 0;
 #pragma unroll
     for (int k = 0; k < kScanPer; ++k) {
-        fl[k] = (base + k < n && res[base + k].feature >= 0) ? 1u : 0u;
+        fl[k] = base + k < n ? flags[base + k] : 0u;
         c += fl[k];
     }
     uint32_t tot;
@@ -796,11 +864,10 @@ struct FinalArgs {
     const uint32_t *excl;          // n + 1
     const uint32_t *tree_off;      // T + 1: first node of each tree at this depth
     const uint32_t *tree_base;     // T: nodes of each tree at lower depths
-    int n;
+    LevelCounts *cnt;              // C and packed_off of this depth; n_small / n_big of the next
     NodeRec *next;
     int32_t *small_list, *big_list;
-    uint32_t *counters;            // [0] small, [1] big
-    PackedRec *packed;             // this depth's slice
+    PackedRec *packed;             // all finished nodes; this depth starts at cnt->packed_off
     GrowStats *stats;
 };
 
@@ -819,44 +886,52 @@ __device__ __forceinline__ void push_list(int32_t *list, uint32_t *counter, bool
 __global__ void __launch_bounds__(256) finalize_kernel(FinalArgs a)
 {
     __shared__ unsigned long long red[6][8];
-    const int jj = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = jj < a.n;
-    const int j = active ? jj : 0;
-    const NodeRec nd = a.nodes[j];
-    const SplitRes r = a.res[j];
-    const bool split = active && r.feature >= 0;
-    const uint32_t t = nd.tree;
-    const uint32_t first = a.tree_off[t];
-    const uint32_t cnt_t = a.tree_off[t + 1] - first;
-    const uint32_t g = a.excl[j];
-    const uint32_t local = g - a.excl[first];
-    const uint32_t base_t = a.tree_base[t];
-    NodeRec L, Rn;
-    if (active) {
-        PackedRec pr;
-        pr.tree = t;
-        pr.pos = base_t + nd.idx;
-        pr.node = split ? encode_split(r.feature, base_t + cnt_t + 2u * local, r.thr_bits) : encode_leaf(r.v);
-        pr.cnode = split ? encode_split_coded(r.feature, base_t + cnt_t + 2u * local, r.rank) : pr.node;
-        a.packed[j] = pr;
-    }
-    if (split) {
-        L.tree = t; L.idx = 2u * local; L.start = nd.start; L.len = r.lenL; L.n = r.nL; L.pad = 0u; L.S = r.v;
-        Rn.tree = t; Rn.idx = 2u * local + 1u; Rn.start = nd.start + r.lenL; Rn.len = nd.len - r.lenL;
-        Rn.n = nd.n - r.nL; Rn.pad = 0u; Rn.S = nd.S - r.v;
-        a.next[2u * g] = L;
-        a.next[2u * g + 1u] = Rn;
-    }
-    push_list(a.small_list, &a.counters[0], split && L.len <= (uint32_t)kSmallNodeRows, (int32_t)(2u * g));
-    push_list(a.big_list, &a.counters[1], split && L.len > (uint32_t)kSmallNodeRows, (int32_t)(2u * g));
-    push_list(a.small_list, &a.counters[0], split && Rn.len <= (uint32_t)kSmallNodeRows, (int32_t)(2u * g + 1u));
-    push_list(a.big_list, &a.counters[1], split && Rn.len > (uint32_t)kSmallNodeRows, (int32_t)(2u * g + 1u));
+    const uint32_t n = a.cnt->C;
+    PackedRec *packed = a.packed + a.cnt->packed_off;
+    unsigned long long v[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {   // block-uniform
+        const uint32_t jj = base + threadIdx.x;
+        const bool active = jj < n;
+        const uint32_t j = active ? jj : 0u;
+        const NodeRec nd = a.nodes[j];
+        const SplitRes r = a.res[j];
+        const bool split = active && r.feature >= 0;
+        const uint32_t t = nd.tree;
+        const uint32_t first = a.tree_off[t];
+        const uint32_t cnt_t = a.tree_off[t + 1] - first;
+        const uint32_t g = a.excl[j];
+        const uint32_t local = g - a.excl[first];
+        const uint32_t base_t = a.tree_base[t];
+        NodeRec L, Rn;
+        if (active) {
+            PackedRec pr;
+            pr.tree = t;
+            pr.pos = base_t + nd.idx;
+            pr.node = split ? encode_split(r.feature, base_t + cnt_t + 2u * local, r.thr_bits) : encode_leaf(r.v);
+            pr.cnode = split ? encode_split_coded(r.feature, base_t + cnt_t + 2u * local, r.rank) : pr.node;
+            packed[j] = pr;
+        }
+        if (split) {
+            L.tree = t; L.idx = 2u * local; L.start = nd.start; L.len = r.lenL; L.n = r.nL; L.pad = 0u; L.S = r.v;
+            Rn.tree = t; Rn.idx = 2u * local + 1u; Rn.start = nd.start + r.lenL; Rn.len = nd.len - r.lenL;
+            Rn.n = nd.n - r.nL; Rn.pad = 0u; Rn.S = nd.S - r.v;
+            a.next[2u * g] = L;
+            a.next[2u * g + 1u] = Rn;
+        }
+        push_list(a.small_list, &a.cnt->n_small, split && L.len <= (uint32_t)kSmallNodeRows, (int32_t)(2u * g));
+        push_list(a.big_list, &a.cnt->n_big, split && L.len > (uint32_t)kSmallNodeRows, (int32_t)(2u * g));
+        push_list(a.small_list, &a.cnt->n_small, split && Rn.len <= (uint32_t)kSmallNodeRows, (int32_t)(2u * g + 1u));
+        push_list(a.big_list, &a.cnt->n_big, split && Rn.len > (uint32_t)kSmallNodeRows, (int32_t)(2u * g + 1u));
 
-    const bool evald = active && r.feature != -2;
-    const bool small = nd.len <= (uint32_t)kSmallNodeRows;
-    unsigned long long v[6] = {evald ? nd.len : 0ull, split ? nd.len : 0ull, evald ? 1ull : 0ull,
-                               (evald && small) ? 1ull : 0ull, (evald && small) ? nd.len : 0ull,
-                               (split && small) ? nd.len : 0ull};
+        const bool evald = active && r.feature != -2;
+        const bool small = nd.len <= (uint32_t)kSmallNodeRows;
+        v[0] += evald ? nd.len : 0u;
+        v[1] += split ? nd.len : 0u;
+        v[2] += evald ? 1u : 0u;
+        v[3] += (evald && small) ? 1u : 0u;
+        v[4] += (evald && small) ? nd.len : 0u;
+        v[5] += (split && small) ? nd.len : 0u;
+    }
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
 #pragma unroll
@@ -869,19 +944,28 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinalArgs a)
     }
     __syncthreads();
     if (threadIdx.x < 6) {
-        unsigned long long s = 0;
-        for (int w = 0; w < 8; ++w) s += red[threadIdx.x][w];
-        if (s) atomicAdd(&a.stats->entries_evaluated + threadIdx.x, s);   // GrowStats field order
+        unsigned long long sum = 0;
+        for (int w = 0; w < 8; ++w) sum += red[threadIdx.x][w];
+        if (sum) atomicAdd(&a.stats->entries_evaluated + threadIdx.x, sum);   // GrowStats field order
     }
 }
 
+// per tree: nodes below the next depth and where the tree's nodes start in the next depth's
+// table; thread 0 then advances the depth counters (after every reader of them has finished)
 __global__ void tree_update_kernel(const uint32_t *tree_off, uint32_t *tree_base, const uint32_t *excl,
-                                   uint32_t *next_tree_off, int T)
+                                   uint32_t *next_tree_off, int T, LevelCounts *cnt)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t > T) return;
-    if (t < T) tree_base[t] += tree_off[t + 1] - tree_off[t];
-    next_tree_off[t] = 2u * excl[tree_off[t]];
+    if (t <= T) {
+        if (t < T) tree_base[t] += tree_off[t + 1] - tree_off[t];
+        next_tree_off[t] = 2u * excl[tree_off[t]];
+    }
+    if (t == 0) {
+        const uint32_t c = cnt->C;
+        cnt->packed_off += c;
+        cnt->levels += c > 0 ? 1u : 0u;
+        cnt->C = 2u * excl[c];
+    }
 }
 
 __global__ void iota_kernel(uint32_t *v, int n)
@@ -999,6 +1083,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
 
     int device = 0;
     AIWCRF_CUDA(cudaGetDevice(&device));
+    keep_pool_memory(device);
     int max_smem_optin = 0;
     AIWCRF_CUDA(cudaDeviceGetAttribute(&max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
 
@@ -1029,10 +1114,11 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     uint16_t *d_R = sc.get<uint16_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
     float *d_vals = sc.get<float>((size_t)F * (size_t)N, &rc); if (rc) return rc;
     uint32_t *d_card = sc.get<uint32_t>((size_t)F, &rc); if (rc) return rc;
-    uint32_t *kA = sc.get<uint32_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
-    uint32_t *vA = sc.get<uint32_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
-    uint32_t *kB = sc.get<uint32_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
-    uint32_t *vB = sc.get<uint32_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
+    // sort buffers (one spare word: the grouping's scan writes its total at [N])
+    uint32_t *kA = sc.get<uint32_t>((size_t)F * (size_t)N + 1, &rc); if (rc) return rc;
+    uint32_t *vA = sc.get<uint32_t>((size_t)F * (size_t)N + 1, &rc); if (rc) return rc;
+    uint32_t *kB = sc.get<uint32_t>((size_t)F * (size_t)N + 1, &rc); if (rc) return rc;
+    uint32_t *vB = sc.get<uint32_t>((size_t)F * (size_t)N + 1, &rc); if (rc) return rc;
     uint32_t *hist = sc.get<uint32_t>(radix_sort_hist_words(N, F), &rc); if (rc) return rc;
     uint32_t max_card = 0;
     {
@@ -1074,9 +1160,16 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         count_launches(1);
         AIWCRF_LAUNCH_CHECK("rank_rows / hash_rows");
         if ((rc = radix_sort_segments(kA, vA, kB, vB, N, 1, N, hist, s)) != AIWCRF_OK) return rc;
-        if (rank8) group_kernel<uint8_t><<<1, 1024, 0, s>>>((const uint8_t *)d_Rr, N, F, kA, vA, grp_off, d_counters + 2);
-        else group_kernel<uint16_t><<<1, 1024, 0, s>>>((const uint16_t *)d_Rr, N, F, kA, vA, grp_off, d_counters + 2);
-        AIWCRF_LAUNCH_CHECK("group_kernel");
+        // group starts (flags in kB), their exclusive scan (in vB), offsets
+        if (rank8) group_flags_kernel<uint8_t><<<rb, 256, 0, s>>>((const uint8_t *)d_Rr, N, F, kA, vA, kB);
+        else group_flags_kernel<uint16_t><<<rb, 256, 0, s>>>((const uint16_t *)d_Rr, N, F, kA, vA, kB);
+        const int gblocks = (int)((N + kScanTile - 1) / kScanTile);
+        flag_scan_reduce_kernel<<<gblocks, kScanThreads, 0, s>>>(kB, N, hist);
+        scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(hist, gblocks);
+        flag_scan_write_kernel<<<gblocks, kScanThreads, 0, s>>>(kB, N, hist, gblocks, vB);
+        group_offsets_kernel<<<rb, 256, 0, s>>>(kB, vB, N, grp_off, d_counters + 2);
+        count_launches(4);
+        AIWCRF_LAUNCH_CHECK("grouping kernels");
         prof_end(s, kProfRank);
         AIWCRF_CUDA(cudaMemcpyAsync(&n_groups, d_counters + 2, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         AIWCRF_CUDA(cudaStreamSynchronize(s));
@@ -1096,13 +1189,69 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     Entry *rows_a = sc.get<Entry>((size_t)T * (size_t)row_cap, &rc); if (rc) return rc;
     Entry *rows_b = sc.get<Entry>((size_t)T * (size_t)row_cap, &rc); if (rc) return rc;
 
-    size_t node_cap = (size_t)std::max<int64_t>(T, 1024);
-    NodeRec *nodes_cur = sc.get<NodeRec>(node_cap, &rc); if (rc) return rc;
-    NodeRec *nodes_nxt = sc.get<NodeRec>(2 * node_cap, &rc); if (rc) return rc;
-    size_t nxt_cap = 2 * node_cap;
-    int32_t *small_list = sc.get<int32_t>(node_cap, &rc); if (rc) return rc;
-    int32_t *big_list = sc.get<int32_t>(node_cap, &rc); if (rc) return rc;
-    size_t list_cap = node_cap;
+    // Level-loop capacities. A depth holds at most C_max = T * row_cap nodes (each holds an
+    // entry) and a tree at most 2 * row_cap - 1 nodes. Depths are enqueued in chunks without
+    // waiting; after each chunk the host reads the node count and grows the buffers so that
+    // they hold the next chunk whatever its growth (at most doubling per depth).
+    const int64_t C_max = T * row_cap;
+    const int64_t nodes_max = T * (2 * row_cap - 1);
+    const size_t per_node_bytes = 2 * sizeof(NodeRec) + sizeof(SplitRes) + 4 * sizeof(int32_t) + 8;
+    const size_t budget = (size_t)4 << 30;                      // level-table budget per fit
+    int dev_sms = 0;
+    AIWCRF_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, device));
+
+    size_t node_cap = 0, packed_cap = 0;
+    NodeRec *nodes_cur = nullptr, *nodes_nxt = nullptr;
+    SplitRes *res = nullptr;
+    uint32_t *excl = nullptr, *block_sums = nullptr;
+    int32_t *small_a = nullptr, *big_a = nullptr;
+    PackedRec *packed = nullptr;
+    // (re)allocate the per-depth tables for up to cap nodes per depth; the current depth's
+    // nodes and lists are carried over
+    auto grow_tables = [&](size_t cap, uint32_t carry_nodes) -> int {
+        if (cap <= node_cap) return AIWCRF_OK;
+        int rc2 = AIWCRF_OK;
+        NodeRec *nc = sc.get<NodeRec>(cap, &rc2); if (rc2) return rc2;
+        NodeRec *nn = sc.get<NodeRec>(2 * cap, &rc2); if (rc2) return rc2;
+        SplitRes *nr = sc.get<SplitRes>(cap, &rc2); if (rc2) return rc2;
+        uint32_t *ne = sc.get<uint32_t>(cap + 1, &rc2); if (rc2) return rc2;
+        uint32_t *nbs = sc.get<uint32_t>(cap / kScanTile + 2, &rc2); if (rc2) return rc2;
+        int32_t *ns = sc.get<int32_t>(2 * cap, &rc2); if (rc2) return rc2;
+        int32_t *nb = sc.get<int32_t>(2 * cap, &rc2); if (rc2) return rc2;
+        if (nodes_cur) {
+            cudaError_t e1 = cudaMemcpyAsync(nc, nodes_cur, sizeof(NodeRec) * carry_nodes, cudaMemcpyDeviceToDevice, s);
+            if (e1 == cudaSuccess) e1 = cudaMemcpyAsync(ns, small_a, sizeof(int32_t) * carry_nodes, cudaMemcpyDeviceToDevice, s);
+            if (e1 == cudaSuccess) e1 = cudaMemcpyAsync(nb, big_a, sizeof(int32_t) * carry_nodes, cudaMemcpyDeviceToDevice, s);
+            if (e1 != cudaSuccess) return cuda_fail(e1, "growing level tables");
+            sc.drop(nodes_cur); sc.drop(nodes_nxt); sc.drop(res); sc.drop(excl); sc.drop(block_sums);
+            sc.drop(small_a); sc.drop(big_a);
+        }
+        nodes_cur = nc; nodes_nxt = nn; res = nr; excl = ne; block_sums = nbs; small_a = ns; big_a = nb;
+        node_cap = cap;
+        return AIWCRF_OK;
+    };
+    if ((rc = grow_tables((size_t)std::max<int64_t>(T, 1024), 0)) != AIWCRF_OK) return rc;
+    auto grow_packed = [&](size_t need, size_t keep) -> int {
+        if (need <= packed_cap) return AIWCRF_OK;
+        int rc2 = AIWCRF_OK;
+        const size_t ncap = std::max(need, packed_cap * 2);
+        PackedRec *np = sc.get<PackedRec>(ncap, &rc2); if (rc2) return rc2;
+        if (packed && keep) {
+            cudaError_t e1 = cudaMemcpyAsync(np, packed, sizeof(PackedRec) * keep, cudaMemcpyDeviceToDevice, s);
+            if (e1 != cudaSuccess) return cuda_fail(e1, "growing node records");
+        }
+        if (packed) sc.drop(packed);
+        packed = np;
+        packed_cap = ncap;
+        return AIWCRF_OK;
+    };
+
+    LevelCounts *d_cnt = sc.get<LevelCounts>(1, &rc); if (rc) return rc;
+    {
+        LevelCounts c0;
+        c0.n_small = 0u; c0.n_big = 0u; c0.C = (uint32_t)T; c0.levels = 0u; c0.packed_off = 0ull;
+        AIWCRF_CUDA(cudaMemcpyAsync(d_cnt, &c0, sizeof(LevelCounts), cudaMemcpyHostToDevice, s));
+    }
 
     {
         const int boot_smem_words = std::min<int>((max_smem_optin - 2048) / 4, 56 * 1024);
@@ -1123,7 +1272,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         ba.bootstrap = p.bootstrap; ba.gcnt = gcnt; ba.gcnt_stride = gstride;
         ba.smem_words = gcnt ? 0 : (int)words;
         ba.rows_out = rows_a; ba.row_cap = row_cap; ba.root = nodes_cur;
-        ba.small_list = small_list; ba.big_list = big_list; ba.counters = d_counters; ba.err = d_err;
+        ba.small_list = small_a; ba.big_list = big_a; ba.counters = &d_cnt->n_small; ba.err = d_err;
         prof_begin(s, kProfBoot);
         bootstrap_kernel<<<(unsigned)T, kBootThreads, smem_bytes, s>>>(ba);
         AIWCRF_LAUNCH_CHECK("bootstrap_kernel");
@@ -1138,28 +1287,9 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     AIWCRF_LAUNCH_CHECK("iota_kernel");
     AIWCRF_CUDA(cudaMemsetAsync(tree_base, 0, sizeof(uint32_t) * (size_t)T, s));
 
-    size_t packed_cap = (size_t)std::max<int64_t>(4 * T, 4096);
-    PackedRec *packed = sc.get<PackedRec>(packed_cap, &rc); if (rc) return rc;
-    size_t packed_n = 0;
-
-    SplitRes *res = sc.get<SplitRes>(node_cap, &rc); if (rc) return rc;
-    size_t res_cap = node_cap;
-    uint32_t *excl = sc.get<uint32_t>(node_cap + 1, &rc); if (rc) return rc;
-    size_t excl_cap = node_cap + 1;
-    uint32_t *block_sums = sc.get<uint32_t>(node_cap / kScanTile + 2, &rc); if (rc) return rc;
-    size_t bs_cap = node_cap / kScanTile + 2;
-
-    uint32_t *h_cnt = nullptr;
-    AIWCRF_CUDA(cudaMallocHost(&h_cnt, 8 * sizeof(uint32_t)));
-    struct HostFree { uint32_t *p; ~HostFree() { if (p) cudaFreeHost(p); } } hf{h_cnt};
-
-    // counts of the root depth
-    AIWCRF_CUDA(cudaMemcpyAsync(h_cnt, d_counters, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    AIWCRF_CUDA(cudaMemcpyAsync(h_cnt + 2, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    AIWCRF_CUDA(cudaStreamSynchronize(s));
-    if ((rc = check_err_flags(h_cnt[2])) != AIWCRF_OK) return rc;
-    uint32_t n_small = h_cnt[0], n_big = h_cnt[1];
-    int64_t C = T;
+    LevelCounts *h_cnt = static_cast<LevelCounts *>(pinned_scratch());
+    if (!h_cnt) return fail(AIWCRF_E_OOM, "pinned host buffer");
+    uint32_t *h_err = reinterpret_cast<uint32_t *>(h_cnt + 1);
 
     const int bin_cap = 4096;
     const int big_smem = bin_cap * 12;
@@ -1173,108 +1303,83 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
 
     Entry *rin = rows_a, *rout = rows_b;
     int depth = 0;
-    for (; C > 0; ++depth) {
-        // capacity for this depth's results and the next depth's nodes
-        if ((size_t)C > res_cap) {
-            sc.drop(res);
-            res_cap = (size_t)C * 2;
-            res = sc.get<SplitRes>(res_cap, &rc); if (rc) return rc;
-        }
-        if ((size_t)C + 1 > excl_cap) {
-            sc.drop(excl);
-            excl_cap = (size_t)C * 2 + 1;
-            excl = sc.get<uint32_t>(excl_cap, &rc); if (rc) return rc;
-        }
-        const int nblocks = (int)((C + kScanTile - 1) / kScanTile);
-        if ((size_t)nblocks + 1 > bs_cap) {
-            sc.drop(block_sums);
-            bs_cap = (size_t)nblocks * 2 + 2;
-            block_sums = sc.get<uint32_t>(bs_cap, &rc); if (rc) return rc;
-        }
-        if ((size_t)(2 * C) > nxt_cap) {
-            sc.drop(nodes_nxt);
-            nxt_cap = (size_t)C * 4;
-            nodes_nxt = sc.get<NodeRec>(nxt_cap, &rc); if (rc) return rc;
-        }
-        if ((size_t)(2 * C) > list_cap) {
-            // lists are read by this depth's kernels and rewritten by its finalize: keep both
-            int32_t *ns = sc.get<int32_t>((size_t)C * 4, &rc); if (rc) return rc;
-            int32_t *nb = sc.get<int32_t>((size_t)C * 4, &rc); if (rc) return rc;
-            AIWCRF_CUDA(cudaMemcpyAsync(ns, small_list, sizeof(int32_t) * n_small, cudaMemcpyDeviceToDevice, s));
-            AIWCRF_CUDA(cudaMemcpyAsync(nb, big_list, sizeof(int32_t) * n_big, cudaMemcpyDeviceToDevice, s));
-            sc.drop(small_list); sc.drop(big_list);
-            small_list = ns; big_list = nb;
-            list_cap = (size_t)C * 4;
-        }
-        if (packed_n + (size_t)C > packed_cap) {
-            size_t ncap = std::max(packed_cap * 2, packed_n + (size_t)C);
-            PackedRec *np = sc.get<PackedRec>(ncap, &rc); if (rc) return rc;
-            AIWCRF_CUDA(cudaMemcpyAsync(np, packed, sizeof(PackedRec) * packed_n, cudaMemcpyDeviceToDevice, s));
-            sc.drop(packed);
-            packed = np;
-            packed_cap = ncap;
-        }
+    int64_t C_known = T;                 // node count at the start of the next chunk (exact)
+    uint64_t packed_known = 0;           // finished nodes before it (exact)
+    while (C_known > 0) {
+        // largest chunk whose bound fits the budget
+        int chunk = 8;
+        auto bound = [&](int k) { return std::min<int64_t>(C_known << k, C_max); };
+        while (chunk > 1 && (size_t)bound(chunk) * per_node_bytes > budget) chunk >>= 1;
+        if ((rc = grow_tables((size_t)bound(chunk), (uint32_t)C_known)) != AIWCRF_OK) return rc;
+        int64_t packed_need = (int64_t)packed_known;
+        for (int k = 0; k < chunk; ++k) packed_need += bound(k);
+        packed_need = std::min<int64_t>(packed_need, nodes_max + T);
+        if ((rc = grow_packed((size_t)packed_need, (size_t)packed_known)) != AIWCRF_OK) return rc;
 
-        la.nodes = nodes_cur; la.rows_in = rin; la.rows_out = rout; la.depth = depth; la.res = res;
-        if (n_big > 0) {
-            la.list = big_list; la.list_n = (int32_t)n_big;
-            prof_begin(s, kProfLevelBig);
-            if (rank8) level_big_kernel<uint8_t><<<n_big, kBigThreads, big_smem, s>>>(la, bin_cap);
-            else level_big_kernel<uint16_t><<<n_big, kBigThreads, big_smem, s>>>(la, bin_cap);
-            AIWCRF_LAUNCH_CHECK("level_big_kernel");
-            prof_end(s, kProfLevelBig);
+        for (int k = 0; k < chunk; ++k, ++depth) {
+            const int64_t Cb = bound(k);                        // bound on this depth's nodes
+            la.nodes = nodes_cur; la.rows_in = rin; la.rows_out = rout; la.depth = depth; la.res = res;
+            {
+                la.list = big_a; la.list_n = &d_cnt->n_big;
+                const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(Cb, 3 * dev_sms));
+                prof_begin(s, kProfLevelBig);
+                if (rank8) level_big_kernel<uint8_t><<<grid, kBigThreads, big_smem, s>>>(la, bin_cap);
+                else level_big_kernel<uint16_t><<<grid, kBigThreads, big_smem, s>>>(la, bin_cap);
+                AIWCRF_LAUNCH_CHECK("level_big_kernel");
+                prof_end(s, kProfLevelBig);
+            }
+            {
+                la.list = small_a; la.list_n = &d_cnt->n_small;
+                const int64_t wpb = kSmallThreads / 32;
+                const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + wpb - 1) / wpb, 3 * dev_sms));
+                prof_begin(s, kProfLevelSmall);
+                if (rank8) level_small_kernel<uint8_t><<<grid, kSmallThreads, 0, s>>>(la);
+                else level_small_kernel<uint16_t><<<grid, kSmallThreads, 0, s>>>(la);
+                AIWCRF_LAUNCH_CHECK("level_small_kernel");
+                prof_end(s, kProfLevelSmall);
+            }
+            const unsigned sgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + kScanTile - 1) / kScanTile, 2 * dev_sms));
+            prof_begin(s, kProfScan);
+            scan_reduce_kernel<<<sgrid, kScanThreads, 0, s>>>(res, d_cnt, block_sums);
+            scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(block_sums, 0, d_cnt);
+            scan_write_kernel<<<sgrid, kScanThreads, 0, s>>>(res, d_cnt, block_sums, excl);
+            count_launches(2);
+            AIWCRF_LAUNCH_CHECK("scan kernels");
+            prof_end(s, kProfScan);
+
+            AIWCRF_CUDA(cudaMemsetAsync(d_cnt, 0, 2 * sizeof(uint32_t), s));     // next depth's list counts
+            FinalArgs fa;
+            fa.nodes = nodes_cur; fa.res = res; fa.excl = excl; fa.tree_off = tree_off; fa.tree_base = tree_base;
+            fa.cnt = d_cnt; fa.next = nodes_nxt; fa.small_list = small_a; fa.big_list = big_a;
+            fa.packed = packed; fa.stats = d_stats;
+            const unsigned fgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + 255) / 256, 8 * dev_sms));
+            prof_begin(s, kProfFinalize);
+            finalize_kernel<<<fgrid, 256, 0, s>>>(fa);
+            AIWCRF_LAUNCH_CHECK("finalize_kernel");
+            tree_update_kernel<<<(unsigned)((T + 256) / 256), 256, 0, s>>>(tree_off, tree_base, excl, tree_off_nxt,
+                                                                            (int)T, d_cnt);
+            AIWCRF_LAUNCH_CHECK("tree_update_kernel");
+            prof_end(s, kProfFinalize);
+
+            std::swap(nodes_cur, nodes_nxt);
+            std::swap(rin, rout);
+            std::swap(tree_off, tree_off_nxt);
         }
-        if (n_small > 0) {
-            la.list = small_list; la.list_n = (int32_t)n_small;
-            const unsigned grid = (n_small + kSmallThreads / 32 - 1) / (kSmallThreads / 32);
-            prof_begin(s, kProfLevelSmall);
-            if (rank8) level_small_kernel<uint8_t><<<grid, kSmallThreads, 0, s>>>(la);
-            else level_small_kernel<uint16_t><<<grid, kSmallThreads, 0, s>>>(la);
-            AIWCRF_LAUNCH_CHECK("level_small_kernel");
-            prof_end(s, kProfLevelSmall);
-        }
-
-        prof_begin(s, kProfScan);
-        scan_reduce_kernel<<<nblocks, kScanThreads, 0, s>>>(res, (int)C, block_sums);
-        scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(block_sums, nblocks);
-        scan_write_kernel<<<nblocks, kScanThreads, 0, s>>>(res, (int)C, block_sums, nblocks, excl);
-        count_launches(2);
-        AIWCRF_LAUNCH_CHECK("scan kernels");
-        prof_end(s, kProfScan);
-
-        AIWCRF_CUDA(cudaMemsetAsync(d_counters, 0, 2 * sizeof(uint32_t), s));
-        FinalArgs fa;
-        fa.nodes = nodes_cur; fa.res = res; fa.excl = excl; fa.tree_off = tree_off; fa.tree_base = tree_base;
-        fa.n = (int)C; fa.next = nodes_nxt; fa.small_list = small_list; fa.big_list = big_list;
-        fa.counters = d_counters; fa.packed = packed + packed_n; fa.stats = d_stats;
-        prof_begin(s, kProfFinalize);
-        finalize_kernel<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(fa);
-        AIWCRF_LAUNCH_CHECK("finalize_kernel");
-        tree_update_kernel<<<(unsigned)((T + 256) / 256), 256, 0, s>>>(tree_off, tree_base, excl, tree_off_nxt, (int)T);
-        AIWCRF_LAUNCH_CHECK("tree_update_kernel");
-        prof_end(s, kProfFinalize);
-        packed_n += (size_t)C;
-
-        AIWCRF_CUDA(cudaMemcpyAsync(h_cnt, d_counters, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-        AIWCRF_CUDA(cudaMemcpyAsync(h_cnt + 2, excl + C, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        AIWCRF_CUDA(cudaMemcpyAsync(h_cnt, d_cnt, sizeof(LevelCounts), cudaMemcpyDeviceToHost, s));
+        AIWCRF_CUDA(cudaMemcpyAsync(h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         AIWCRF_CUDA(cudaStreamSynchronize(s));
-        n_small = h_cnt[0];
-        n_big = h_cnt[1];
-        C = 2 * (int64_t)h_cnt[2];
-
-        std::swap(nodes_cur, nodes_nxt);
-        std::swap(node_cap, nxt_cap);
-        std::swap(rin, rout);
-        std::swap(tree_off, tree_off_nxt);
+        if ((rc = check_err_flags(*h_err)) != AIWCRF_OK) return rc;
+        C_known = h_cnt->C;
+        packed_known = h_cnt->packed_off;
     }
+    const size_t packed_n = (size_t)packed_known;
+    depth = (int)h_cnt->levels;
 
-    AIWCRF_CUDA(cudaMemcpyAsync(h_cnt, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     std::vector<uint32_t> h_tot((size_t)T);
     AIWCRF_CUDA(cudaMemcpyAsync(h_tot.data(), tree_base, sizeof(uint32_t) * (size_t)T, cudaMemcpyDeviceToHost, s));
     GrowStats hs;
     AIWCRF_CUDA(cudaMemcpyAsync(&hs, d_stats, sizeof(GrowStats), cudaMemcpyDeviceToHost, s));
     AIWCRF_CUDA(cudaStreamSynchronize(s));
-    if ((rc = check_err_flags(h_cnt[0])) != AIWCRF_OK) return rc;
 
     // pack: one buffer per forest, trees padded to an even node count (16-byte aligned)
     std::vector<aiwcrf_forest *> forests((size_t)G, nullptr);
@@ -1298,14 +1403,10 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
             fr->max_tree_nodes = std::max(fr->max_tree_nodes, (cnt + 1) & ~(int64_t)1);
         }
         fr->num_nodes = fr->tree_off[(size_t)Tper];
-        AIWCRF_CUDA(cudaMalloc(&fr->d_nodes, sizeof(uint64_t) * (size_t)std::max<int64_t>(fr->num_nodes, 2)));
-        AIWCRF_CUDA(cudaMalloc(&fr->d_cnodes, sizeof(uint64_t) * (size_t)std::max<int64_t>(fr->num_nodes, 2)));
-        AIWCRF_CUDA(cudaMalloc(&fr->d_tree_off, sizeof(int64_t) * (size_t)(Tper + 1)));
         // the training value tables code the queries at predict time
         fr->max_card = max_card;
         fr->fstride = std::max<int64_t>(max_card, 1);
-        AIWCRF_CUDA(cudaMalloc(&fr->d_fvals, sizeof(float) * (size_t)F * (size_t)fr->fstride));
-        AIWCRF_CUDA(cudaMalloc(&fr->d_fcard, sizeof(uint32_t) * (size_t)F));
+        AIWCRF_CUDA(forest_alloc(fr));
         AIWCRF_CUDA(cudaMemcpy2DAsync(fr->d_fvals, sizeof(float) * (size_t)fr->fstride, d_vals, sizeof(float) * (size_t)N,
                                       sizeof(float) * (size_t)max_card, (size_t)F, cudaMemcpyDeviceToDevice, s));
         AIWCRF_CUDA(cudaMemcpyAsync(fr->d_fcard, d_card, sizeof(uint32_t) * (size_t)F, cudaMemcpyDeviceToDevice, s));

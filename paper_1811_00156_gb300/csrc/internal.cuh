@@ -346,6 +346,7 @@ struct aiwcrf_forest {
     int64_t num_nodes = 0;
     int64_t max_tree_nodes = 0;
     int device = 0;
+    void *d_block = nullptr;              // one device allocation holding every array below
     uint64_t *d_nodes = nullptr;          // packed nodes
     uint64_t *d_cnodes = nullptr;         // the same nodes, thresholds as rank codes
     int64_t *d_tree_off = nullptr;        // T + 1 offsets (in nodes)
@@ -359,6 +360,12 @@ struct aiwcrf_forest {
 
 namespace aiwcrf {
 void forest_release(aiwcrf_forest *f);
+// one device allocation for the forest's arrays (nodes, coded nodes, tree offsets, value tables)
+cudaError_t forest_alloc(aiwcrf_forest *f);
+// keep freed stream-ordered allocations cached in the device's default pool (once per device)
+void keep_pool_memory(int device);
+// a small pinned host buffer reused by the calling thread (at least 64 bytes)
+void *pinned_scratch();
 }
 
 namespace aiwcrf {

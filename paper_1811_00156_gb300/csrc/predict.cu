@@ -331,6 +331,7 @@ int predict_launch(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t 
                    uint64_t *d_var, int64_t total_trees, cudaStream_t s)
 {
     if (Q == 0) return AIWCRF_OK;
+    keep_pool_memory(f->device);
     uint32_t *d_err = nullptr;
     cudaError_t e = cudaMallocAsync(&d_err, sizeof(uint32_t), s);
     if (e != cudaSuccess) return fail(AIWCRF_E_OOM, "device allocation failed");
