@@ -41,11 +41,23 @@ void forest_release(aiwcrf_forest *f)
 cudaError_t forest_alloc(aiwcrf_forest *f)
 {
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    // compact layout: trees padded to a multiple of four nodes
+    std::vector<int64_t> off4((size_t)f->T + 1, 0);
+    f->max_tree4 = 0;
+    for (int64_t t = 0; t < f->T; ++t) {
+        const int64_t m = f->tree_off[(size_t)t + 1] - f->tree_off[(size_t)t];
+        const int64_t m4 = (m + 3) & ~(int64_t)3;
+        off4[(size_t)t + 1] = off4[(size_t)t] + m4;
+        f->max_tree4 = std::max(f->max_tree4, m4);
+    }
+    f->compact = f->max_card <= 255u && f->max_tree_nodes <= 65536 && f->F <= 128;
+    f->num_c32 = f->compact ? off4[(size_t)f->T] : 0;
     const size_t nn = (size_t)std::max<int64_t>(f->num_nodes, 2);
     const size_t b_nodes = up(8 * nn), b_off = up(8 * (size_t)(f->T + 1));
     const size_t b_vals = up(sizeof(float) * (size_t)f->F * (size_t)f->fstride), b_card = up(4 * (size_t)f->F);
+    const size_t b_c32 = f->compact ? up(4 * (size_t)f->num_c32) + b_off : 0;
     void *p = nullptr;
-    const cudaError_t e = cudaMalloc(&p, 2 * b_nodes + b_off + b_vals + b_card);
+    cudaError_t e = cudaMalloc(&p, 2 * b_nodes + b_off + b_vals + b_card + b_c32);
     if (e != cudaSuccess) return e;
     unsigned char *c = static_cast<unsigned char *>(p);
     f->d_block = p;
@@ -54,7 +66,13 @@ cudaError_t forest_alloc(aiwcrf_forest *f)
     f->d_tree_off = reinterpret_cast<int64_t *>(c + 2 * b_nodes);
     f->d_fvals = reinterpret_cast<float *>(c + 2 * b_nodes + b_off);
     f->d_fcard = reinterpret_cast<uint32_t *>(c + 2 * b_nodes + b_off + b_vals);
-    return cudaSuccess;
+    if (f->compact) {
+        unsigned char *q = c + 2 * b_nodes + b_off + b_vals + b_card;
+        f->d_tree_off4 = reinterpret_cast<int64_t *>(q);
+        f->d_c32 = reinterpret_cast<uint32_t *>(q + b_off);
+        e = cudaMemcpy(f->d_tree_off4, off4.data(), 8 * (size_t)(f->T + 1), cudaMemcpyHostToDevice);
+    }
+    return e;
 }
 
 void keep_pool_memory(int device)
@@ -564,6 +582,10 @@ int aiwcrf_forest_deserialize(const void *buf, size_t len, aiwcrf_forest **out)
     if (e != cudaSuccess) {
         forest_release(f);
         return cuda_fail(e, "uploading forest");
+    }
+    if ((rc = forest_build_compact(f, nullptr)) != AIWCRF_OK || (rc = (cudaDeviceSynchronize() == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "compact nodes"))) != AIWCRF_OK) {
+        forest_release(f);
+        return rc;
     }
     *out = f;
     return AIWCRF_OK;

@@ -1442,6 +1442,8 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     pad_kernel<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(tree_base, T, d_dst, d_dst + T);
     AIWCRF_LAUNCH_CHECK("pad_kernel");
     prof_end(s, kProfPack);
+    for (auto fr : forests)
+        if ((rc = forest_build_compact(fr, s)) != AIWCRF_OK) return rc;
     sc.release();
     AIWCRF_CUDA(cudaStreamSynchronize(s));
     guard.keep = true;

@@ -354,14 +354,26 @@ struct aiwcrf_forest {
     uint32_t *d_fcard = nullptr;          // per feature table size
     int64_t fstride = 0;
     uint32_t max_card = 0;
+    // 4-byte coded nodes for the shared-memory walk, when every code fits a byte and every tree
+    // 65,536 nodes: bit 31 leaf; else bits 24..30 feature, 16..23 code, 0..15 left child.
+    // Trees padded to a multiple of four nodes (16-byte aligned copies); leaf values are read
+    // from d_nodes at the same tree-relative index.
+    bool compact = false;
+    uint32_t *d_c32 = nullptr;
+    int64_t *d_tree_off4 = nullptr;       // T + 1 offsets into d_c32
+    int64_t num_c32 = 0;
+    int64_t max_tree4 = 0;
     std::vector<int64_t> tree_off;        // host copy
     aiwcrf_fit_stats stats = {};
 };
 
 namespace aiwcrf {
 void forest_release(aiwcrf_forest *f);
-// one device allocation for the forest's arrays (nodes, coded nodes, tree offsets, value tables)
+// one device allocation for the forest's arrays (nodes, coded nodes, tree offsets, value tables,
+// compact nodes); sets the compact layout's host fields from tree_off and max_card
 cudaError_t forest_alloc(aiwcrf_forest *f);
+// fills the compact 4-byte node array from d_cnodes (after d_cnodes and d_tree_off are written)
+int forest_build_compact(aiwcrf_forest *f, cudaStream_t s);
 // keep freed stream-ordered allocations cached in the device's default pool (once per device)
 void keep_pool_memory(int device);
 // a small pinned host buffer reused by the calling thread (at least 64 bytes)

@@ -238,6 +238,166 @@ __global__ void __launch_bounds__(kPredThreads) predict_kernel(
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// compact 4-byte coded nodes (one CTA per tree)
+// ------------------------------------------------------------------------------------------
+__global__ void compact_nodes_kernel(const uint64_t *__restrict__ cnodes, const int64_t *__restrict__ tree_off,
+                                     const int64_t *__restrict__ tree_off4, uint32_t *__restrict__ c32)
+{
+    const int t = blockIdx.x;
+    const int64_t a = tree_off[t], m = tree_off[t + 1] - a;
+    const int64_t a4 = tree_off4[t], m4 = tree_off4[t + 1] - a4;
+    for (int64_t j = threadIdx.x; j < m4; j += blockDim.x) {
+        uint32_t v = 0x80000000u;
+        if (j < m) {
+            const uint64_t nd = cnodes[a + j];
+            if (!(nd >> 63)) {
+                const uint32_t f = (uint32_t)(nd >> 56) & 0x7Fu;
+                const uint32_t lc = (uint32_t)(nd >> 32) & 0xFFFFFFu;
+                const uint32_t code = (uint32_t)nd & 0xFFFFFFu;
+                v = (f << 24) | (code << 16) | lc;
+            }
+        }
+        c32[a4 + j] = v;
+    }
+}
+
+__device__ __forceinline__ void issue_tree4(const uint32_t *c32, const int64_t *tree_off4, int t, int tree_cap,
+                                            uint32_t *slot, uint64_t *bar)
+{
+    const int64_t a = tree_off4[t], nn = tree_off4[t + 1] - a;
+    if (nn <= tree_cap) {
+        const uint32_t bytes = (uint32_t)nn * 4u;
+        fence_proxy_async();
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_g2s(slot, c32 + a, bytes, bar);
+    } else {
+        mbar_arrive(bar);
+    }
+}
+
+// Walk of compact nodes; returns each chain's leaf index within the tree.
+template <int QPT, typename NodePtr>
+__device__ __forceinline__ void walk_tree4(NodePtr tn, const uint8_t *const (&xr)[QPT], uint32_t (&j)[QPT])
+{
+#pragma unroll
+    for (int i = 0; i < QPT; ++i) j[i] = 0u;
+    for (;;) {
+        bool more = false;
+#pragma unroll
+        for (int i = 0; i < QPT; ++i) {
+            const uint32_t nd = tn[j[i]];
+            const bool leaf = (int32_t)nd < 0;
+            const uint32_t f = leaf ? 0u : (nd >> 24);
+            const uint32_t c = (uint32_t)xr[i][f];
+            const uint32_t nxt = (nd & 0xFFFFu) + (c > ((nd >> 16) & 0xFFu) ? 1u : 0u);
+            j[i] = leaf ? j[i] : nxt;
+            more |= !leaf;
+        }
+        if (!more) break;
+    }
+}
+
+// The byte-code walk over compact trees. Leaf values are loaded from the 8-byte node array
+// (L2-resident) and added one tree later, so their latency overlaps the next walk.
+template <int QPT, bool VAR>
+__global__ void __launch_bounds__(kPredThreads) predict4_kernel(
+    const uint32_t *__restrict__ c32, const int64_t *__restrict__ tree_off4, const uint64_t *__restrict__ nodes,
+    const int64_t *__restrict__ tree_off, int T, const uint8_t *__restrict__ codes, int64_t Q, int ld_words,
+    int64_t total_trees, int tree_cap, int64_t *out_sum, int64_t *out_pred, uint64_t *out_var, uint32_t *err)
+{
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    uint32_t *slot0 = reinterpret_cast<uint32_t *>(sm_raw);
+    uint32_t *slot1 = slot0 + tree_cap;
+    uint32_t *xw = slot1 + tree_cap;
+    const int tid = threadIdx.x;
+    const int QT = kPredThreads * QPT;
+    const int64_t q0 = (int64_t)blockIdx.x * QT;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    {
+        const uint32_t *gw = reinterpret_cast<const uint32_t *>(codes);
+        const int64_t nq = min((int64_t)QT, Q - q0);
+        const int64_t words = nq * ld_words;
+        const uint32_t *src = gw + (size_t)q0 * (size_t)ld_words;
+        for (int64_t k = tid; k < words; k += kPredThreads) xw[k] = src[k];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        issue_tree4(c32, tree_off4, 0, tree_cap, slot0, &bar[0]);
+        if (T > 1) issue_tree4(c32, tree_off4, 1, tree_cap, slot1, &bar[1]);
+    }
+
+    const uint8_t *xr[QPT];
+#pragma unroll
+    for (int i = 0; i < QPT; ++i)
+        xr[i] = reinterpret_cast<const uint8_t *>(xw + (size_t)(tid + i * kPredThreads) * (size_t)ld_words);
+    int64_t acc[QPT], pend[QPT];
+    u128_t sq[QPT];
+#pragma unroll
+    for (int i = 0; i < QPT; ++i) { acc[i] = 0; pend[i] = 0; sq[i] = 0; }
+
+    for (int t = 0; t < T; ++t) {
+        const int s = t & 1;
+        const uint32_t parity = (uint32_t)((t >> 1) & 1);
+        bool ok = false;
+        for (uint32_t it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(&bar[s], parity);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicOr(err, kErrTimeout);
+            if (t + 1 < T)
+                for (uint32_t it = 0; it < kWaitLimit; ++it)
+                    if (mbar_try_wait(&bar[s ^ 1], (uint32_t)(((t + 1) >> 1) & 1))) break;
+            return;
+        }
+        uint32_t j[QPT];
+        const int64_t a4 = tree_off4[t];
+        if (tree_off4[t + 1] - a4 <= tree_cap) {
+            if (s) walk_tree4<QPT>(slot1, xr, j);
+            else walk_tree4<QPT>(slot0, xr, j);
+        } else {
+            walk_tree4<QPT>(c32 + a4, xr, j);
+        }
+        // add the previous tree's leaves, then start loading this tree's
+        const uint64_t *tn = nodes + tree_off[t];
+#pragma unroll
+        for (int i = 0; i < QPT; ++i) {
+            acc[i] += pend[i];
+            if (VAR) sq[i] += (u128_t)((i128_t)pend[i] * (i128_t)pend[i]);
+            pend[i] = leaf_value(__ldg(&tn[j[i]]));
+        }
+        __syncthreads();
+        if (tid == 0 && t + 2 < T) issue_tree4(c32, tree_off4, t + 2, tree_cap, s ? slot1 : slot0, &bar[s]);
+    }
+#pragma unroll
+    for (int i = 0; i < QPT; ++i) {
+        acc[i] += pend[i];
+        if (VAR) sq[i] += (u128_t)((i128_t)pend[i] * (i128_t)pend[i]);
+    }
+
+#pragma unroll
+    for (int i = 0; i < QPT; ++i) {
+        const int64_t q = q0 + tid + i * kPredThreads;
+        if (q >= Q) continue;
+        if (out_sum) out_sum[q] = acc[i];
+        if (out_pred) {
+            const i128_t num = (i128_t)2 * acc[i] + total_trees, den = (i128_t)2 * total_trees;
+            i128_t d = num / den;
+            if (num % den != 0 && num < 0) d -= 1;
+            out_pred[q] = (int64_t)d;
+        }
+        if (VAR) {
+            const u128_t V = (u128_t)total_trees * sq[i] - (u128_t)((i128_t)acc[i] * (i128_t)acc[i]);
+            out_var[2 * q] = (uint64_t)V;
+            out_var[2 * q + 1] = (uint64_t)(V >> 64);
+        }
+    }
+}
+
 __global__ void round_mean_kernel(const int64_t *sums, int64_t n, int64_t T, int64_t *out)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -317,10 +477,49 @@ int launch_predict(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t 
     return AIWCRF_OK;
 }
 
+template <bool VAR>
+int launch_predict4(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum, int64_t *d_pred,
+                    uint64_t *d_var, int64_t total_trees, cudaStream_t s, uint32_t *d_err)
+{
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int ld_words = (f->F + 3) / 4;
+    if ((ld_words & 1) == 0) ++ld_words;                       // odd: conflict-free rows
+    uint8_t *d_codes = nullptr;
+    cudaError_t e = cudaMallocAsync(&d_codes, (size_t)Q * (size_t)ld_words * 4, s);
+    if (e != cudaSuccess) return fail(AIWCRF_E_OOM, "device allocation of the query codes failed");
+    struct Free { uint8_t *p; cudaStream_t s; ~Free() { cudaFreeAsync(p, s); } } fr{d_codes, s};
+    code_queries_kernel<uint8_t><<<dim3((unsigned)((Q + 255) / 256), (unsigned)f->F), 256, 0, s>>>(
+        dXq, Q, f->F, f->d_fvals, f->fstride, f->d_fcard, d_codes, ld_words * 4);
+    count_launches(1);
+    const int xs_bytes = kPredThreads * kQPT * ld_words * 4;
+    // two tree slots of 4-byte nodes, sized to the largest tree up to 48 KB each
+    int tree_cap = std::min<int>((optin - xs_bytes - 1024) / 8, 12288);
+    if ((int64_t)tree_cap > f->max_tree4) tree_cap = (int)f->max_tree4;
+    tree_cap &= ~3;
+    if (tree_cap < 4) tree_cap = 4;
+    const int smem = 2 * tree_cap * 4 + xs_bytes;
+    auto kern = predict4_kernel<kQPT, VAR>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(predict4_kernel)");
+    const int64_t grid = (Q + (int64_t)kPredThreads * kQPT - 1) / ((int64_t)kPredThreads * kQPT);
+    kern<<<(unsigned)grid, kPredThreads, smem, s>>>(f->d_c32, f->d_tree_off4, f->d_nodes, f->d_tree_off, (int)f->T,
+                                                    d_codes, Q, ld_words, total_trees, tree_cap, d_sum, d_pred, d_var,
+                                                    d_err);
+    count_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "predict4_kernel launch");
+    return AIWCRF_OK;
+}
+
 template <typename CT>
 int launch_predict_ct(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum, int64_t *d_pred,
                       uint64_t *d_var, int64_t total_trees, cudaStream_t s, uint32_t *d_err)
 {
+    if (f->compact)
+        return d_var ? launch_predict4<true>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err)
+                     : launch_predict4<false>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err);
     return d_var ? launch_predict<CT, true>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err)
                  : launch_predict<CT, false>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err);
 }
@@ -351,6 +550,16 @@ int predict_launch(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t 
     cudaFreeAsync(d_err, s);
     if (rc == AIWCRF_OK && (h_err & kErrTimeout)) rc = fail(AIWCRF_E_TIMEOUT, "a bounded device wait gave up");
     return rc;
+}
+
+int forest_build_compact(aiwcrf_forest *f, cudaStream_t s)
+{
+    if (!f->compact) return AIWCRF_OK;
+    compact_nodes_kernel<<<(unsigned)f->T, 256, 0, s>>>(f->d_cnodes, f->d_tree_off, f->d_tree_off4, f->d_c32);
+    count_launches(1);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "compact_nodes_kernel launch");
+    return AIWCRF_OK;
 }
 
 int round_mean_launch(const int64_t *d_sum, int64_t Q, int64_t total_trees, int64_t *d_out, cudaStream_t s)
