@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the OOB and LOKO reports")
     ap.add_argument("--trees", type=int, default=T_TREES,
                     help="forest size per GPU; smaller values are for profiler captures only")
     ap.add_argument("--queries", type=int, default=N_QUERIES,
@@ -318,6 +319,11 @@ def run_ours(args):
 
     if not args.no_e2e:
         out["e2e"] = e2e(A, wl, Xq_h, kfeat_h, params, devices, world, dev, max(1, min(K, 3)))
+    if rank == 0 and not args.no_extras:
+        f = A.aiwcrf_fit(params, X, y)
+        out["oob"] = oob_report(A, wl, X, f)
+        del f
+        out["loko"] = loko_report(A, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
@@ -349,6 +355,57 @@ def e2e(A, wl, Xq_h, kfeat_h, params, devices, world, dev, steps):
     return {"value": wl.n_rows * params.num_trees * world * steps / secs, "unit": ROWS_TREES_UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * secs / steps,
             "steps": steps, "note": "host clock around fit + predict + select with pinned host arrays"}
+
+
+def loko_report(A, dev, steps: int = 2):
+    """Leave-one-kernel-out cross-validation (Alg. 1 / Table III, here without the simulated-
+    annealing re-tuning): 37 forests x 256 trees grown together by one batched fit; per-fold
+    mean absolute percentage error of the predicted runtime (10^log10 t) on the held-out rows
+    (Sec. V reports the same relative error)."""
+    import torch
+    wl, folds = synth.loko_folds()
+    X, y = torch.from_numpy(wl.X).to(dev), torch.from_numpy(wl.y).to(dev)
+    offs = np.cumsum([0] + [len(tr) for tr, _ in folds]).astype(np.int64)
+    rows = torch.from_numpy(np.concatenate([tr for tr, _ in folds]).astype(np.int32)).to(dev)
+    params = A.params(256, MTRY, MIN_NODE, seed=synth.FOREST_SEED)
+    forests = A.aiwcrf_fit_subsets(params, X, y, offs, rows)          # warm-up
+    ms = []
+    for _ in range(steps):
+        del forests
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        forests = A.aiwcrf_fit_subsets(params, X, y, offs, rows)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    mape = []
+    for g, (tr, te) in enumerate(folds):
+        Xt = torch.from_numpy(np.ascontiguousarray(wl.X[:, te])).to(dev)
+        out = torch.empty(len(te), dtype=torch.int64, device=dev)
+        A.aiwcrf_predict(forests[g], Xt, out)
+        pred = out.cpu().numpy() / 2.0 ** 32
+        truth = wl.y[te] / 2.0 ** 32
+        mape.append(float(np.mean(np.abs(10.0 ** pred - 10.0 ** truth) / 10.0 ** truth)))
+    rows_trees = int(sum(len(tr) for tr, _ in folds)) * 256
+    return {"folds": len(folds), "trees_per_fold": 256, "train_rows": [int(min(len(t) for t, _ in folds)),
+                                                                      int(max(len(t) for t, _ in folds))],
+            "fit_ms": min(ms), "rows_trees_per_s": rows_trees / (min(ms) / 1e3),
+            "mape_mean": float(np.mean(mape)), "mape_median": float(np.median(mape)),
+            "mape_max": float(np.max(mape)), "batched": "one aiwcrf_fit_subsets call for all folds"}
+
+
+def oob_report(A, wl, X, forest):
+    import torch
+    s = torch.empty(wl.n_rows, dtype=torch.int64, device=X.device)
+    c = torch.empty(wl.n_rows, dtype=torch.int32, device=X.device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    A.aiwcrf_oob(forest, X, s, c)
+    e1.record()
+    torch.cuda.synchronize()
+    sn, cn = s.cpu().numpy(), c.cpu().numpy()
+    return {"mse_log10_s2": A.oob_error(sn, cn, wl.y), "rows_out_of_bag": float((cn > 0).mean()),
+            "ms": e0.elapsed_time(e1)}
 
 
 def main():

@@ -120,6 +120,14 @@ int aiwcrf_predict(const aiwcrf_forest *forest, const float *Xq, int64_t n_queri
 int aiwcrf_predict_sum(const aiwcrf_forest *forest, const float *Xq, int64_t n_queries,
                        int64_t *out_sum, void *cuda_stream);
 
+/* Out-of-bag evaluation (Sec. III-B: the tuning minimises the out-of-bag prediction error).
+ * X: the F x n_rows training matrix the forest was fitted on by aiwcrf_fit in this process
+ * (AIWCRF_E_INVALID_ARG otherwise). For each row r: out_sum[r] = exact sum of the leaf values
+ * reached in the trees whose bootstrap did not draw r, out_count[r] = their number. The
+ * out-of-bag prediction is floor((2 out_sum + c) / (2 c)) for c = out_count > 0. */
+int aiwcrf_oob(const aiwcrf_forest *forest, const float *X, int64_t n_rows, int64_t *out_sum,
+               int32_t *out_count, void *cuda_stream);
+
 /* out[q] = floor((2 sums[q] + total_trees) / (2 total_trees)). */
 int aiwcrf_round_mean(const int64_t *sums, int64_t n, int64_t total_trees, int64_t *out,
                       void *cuda_stream);

@@ -65,6 +65,8 @@ def lib():
             L.orc_predict.argtypes = [C.c_void_p, _P_F32, C.c_int64, C.c_int64, _P_I64, _P_I64,
                                       _P_U64]
             L.orc_predict.restype = C.c_int
+            L.orc_oob.argtypes = [C.c_void_p, _P_F32, C.c_int64, _P_I64, _P_I32]
+            L.orc_oob.restype = C.c_int
             L.orc_select_device.argtypes = [C.c_void_p, _P_F32, C.c_int32, C.c_int32, _P_I32,
                                             C.c_int32, _P_I32, _P_I64]
             L.orc_select_device.restype = C.c_int
@@ -177,6 +179,16 @@ class Forest:
             var = [int(v[2 * q]) | (int(v[2 * q + 1]) << 64) for q in range(Q)]
             return p, s, var
         return p, s
+
+    def oob(self, X: np.ndarray):
+        """(out_sum, out_count) of every training row over the trees that did not draw it."""
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        N = int(X.shape[1])
+        s = np.zeros(N, np.int64)
+        c = np.zeros(N, np.int32)
+        if lib().orc_oob(self._h, _ptr(X, _P_F32), N, _ptr(s, _P_I64), _ptr(c, _P_I32)) != 0:
+            raise ValueError("X is not the training matrix")
+        return s, c
 
     def select_device(self, kfeat: np.ndarray, size_class: int, device_ids):
         kfeat = np.ascontiguousarray(kfeat, dtype=np.float32)

@@ -252,6 +252,9 @@ struct orc_forest {
     int64_t t0, t1;      /* global tree indices [t0, t1) */
     int32_t F;
     otree *trees;
+    uint64_t seed;       /* the fit's bootstrap, kept for out-of-bag evaluation */
+    int32_t bootstrap;
+    int64_t N;
 };
 typedef struct orc_forest orc_forest;
 
@@ -386,6 +389,7 @@ int orc_fit(const float *X, const int64_t *y, int64_t N, int32_t F,
         return -1;
     orc_forest *fr = (orc_forest *)calloc(1, sizeof(orc_forest));
     fr->t0 = t0; fr->t1 = t1; fr->F = F;
+    fr->seed = seed; fr->bootstrap = bootstrap; fr->N = N;
     fr->trees = (otree *)calloc((size_t)(t1 - t0), sizeof(otree));
     for (int64_t t = t0; t < t1; ++t)
         grow_tree(&fr->trees[t - t0], X, y, N, F, t, mtry, min_node, max_depth, seed, bootstrap);
@@ -458,6 +462,27 @@ int orc_predict(const orc_forest *fr, const float *Xq, int64_t Q, int64_t total_
             out_var[2 * q + 1] = (uint64_t)(V >> 64);
         }
     }
+    return 0;
+}
+
+/* Out-of-bag evaluation (Sec. III-B: the tuning objective). For each training row r of the
+ * fit's X: out_sum[r] = sum of the leaf values of the trees whose bootstrap did not draw r,
+ * out_count[r] = their number. Without bootstrap every row is in every tree's sample. */
+int orc_oob(const orc_forest *fr, const float *X, int64_t N, int64_t *out_sum, int32_t *out_count)
+{
+    if (N != fr->N) return -1;
+    uint32_t *w = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)N);
+    for (int64_t r = 0; r < N; ++r) { out_sum[r] = 0; out_count[r] = 0; }
+    for (int64_t k = 0; k < fr->t1 - fr->t0; ++k) {
+        if (!fr->bootstrap) break;
+        orc_bootstrap_counts(fr->seed, fr->t0 + k, N, w);
+        for (int64_t r = 0; r < N; ++r) {
+            if (w[r] > 0) continue;
+            out_sum[r] += tree_leaf(&fr->trees[k], X, N, r);
+            out_count[r] += 1;
+        }
+    }
+    free(w);
     return 0;
 }
 

@@ -44,7 +44,7 @@ class FitStats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-EXPORTS = ["aiwcrf_fit", "aiwcrf_fit_subsets", "aiwcrf_predict", "aiwcrf_predict_sum",
+EXPORTS = ["aiwcrf_fit", "aiwcrf_fit_subsets", "aiwcrf_predict", "aiwcrf_predict_sum", "aiwcrf_oob",
            "aiwcrf_round_mean", "aiwcrf_select_device", "aiwcrf_forest_stats", "aiwcrf_forest_info",
            "aiwcrf_forest_serialize", "aiwcrf_forest_deserialize", "aiwcrf_forest_free",
            "aiwcrf_last_error", "aiwcrf_profile_enable", "aiwcrf_profile_read",
@@ -72,6 +72,7 @@ def load():
         L.aiwcrf_predict.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp]
         L.aiwcrf_predict_sum.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
         L.aiwcrf_round_mean.argtypes = [_vp, C.c_int64, C.c_int64, _vp, _vp]
+        L.aiwcrf_oob.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp]
         L.aiwcrf_select_device.argtypes = [_vp, _vp, C.c_int32, C.c_int32, _vp, C.c_int32, _vp, _vp, _vp]
         L.aiwcrf_select_device_noalloc.argtypes = [_vp, _vp, C.c_int32, C.c_int32, _vp, C.c_int32, _vp, _vp, _vp]
         L.aiwcrf_forest_stats.argtypes = [_vp, C.POINTER(FitStats)]
@@ -187,6 +188,21 @@ def aiwcrf_predict_sum(forest: Forest, Xq, out_sum, stream=None):
     F, Q = _shape(Xq)
     _check(load().aiwcrf_predict_sum(forest.handle, _ptr(Xq), Q, _ptr(out_sum), _stream(stream)))
     return out_sum
+
+
+def aiwcrf_oob(forest: Forest, X, out_sum, out_count, stream=None):
+    F, N = _shape(X)
+    _check(load().aiwcrf_oob(forest.handle, _ptr(X), N, _ptr(out_sum), _ptr(out_count), _stream(stream)))
+    return out_sum, out_count
+
+
+def oob_error(sums: np.ndarray, counts: np.ndarray, y: np.ndarray) -> float:
+    """Out-of-bag mean squared error in the target's units (rows never out of bag are skipped).
+    The out-of-bag prediction of a row is the rounded mean of its out-of-bag leaf values."""
+    m = counts > 0
+    s, c = sums[m].astype(object), counts[m].astype(object)
+    pred = np.array([(2 * int(a) + int(b)) // (2 * int(b)) for a, b in zip(s, c)], dtype=np.float64)
+    return float(np.mean(((pred - y[m].astype(np.float64)) / 2.0 ** 32) ** 2))
 
 
 def aiwcrf_round_mean(sums, total_trees: int, out, stream=None):

@@ -56,8 +56,9 @@ cudaError_t forest_alloc(aiwcrf_forest *f)
     const size_t b_nodes = up(8 * nn), b_off = up(8 * (size_t)(f->T + 1));
     const size_t b_vals = up(sizeof(float) * (size_t)f->F * (size_t)f->fstride), b_card = up(4 * (size_t)f->F);
     const size_t b_c32 = f->compact ? up(4 * (size_t)f->num_c32) + b_off : 0;
+    const size_t b_inbag = up(4 * (size_t)f->T * (size_t)f->inbag_words);
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, 2 * b_nodes + b_off + b_vals + b_card + b_c32);
+    cudaError_t e = cudaMalloc(&p, 2 * b_nodes + b_off + b_vals + b_card + b_c32 + b_inbag);
     if (e != cudaSuccess) return e;
     unsigned char *c = static_cast<unsigned char *>(p);
     f->d_block = p;
@@ -66,6 +67,7 @@ cudaError_t forest_alloc(aiwcrf_forest *f)
     f->d_tree_off = reinterpret_cast<int64_t *>(c + 2 * b_nodes);
     f->d_fvals = reinterpret_cast<float *>(c + 2 * b_nodes + b_off);
     f->d_fcard = reinterpret_cast<uint32_t *>(c + 2 * b_nodes + b_off + b_vals);
+    if (f->inbag_words) f->d_inbag = reinterpret_cast<uint32_t *>(c + 2 * b_nodes + b_off + b_vals + b_card + b_c32);
     if (f->compact) {
         unsigned char *q = c + 2 * b_nodes + b_off + b_vals + b_card;
         f->d_tree_off4 = reinterpret_cast<int64_t *>(q);
@@ -391,6 +393,28 @@ int aiwcrf_predict_sum(const aiwcrf_forest *forest, const float *Xq, int64_t n_q
     g_last_error.clear();
     if (!out_sum) return fail(AIWCRF_E_INVALID_ARG, "out_sum is NULL");
     return predict_common(forest, Xq, n_queries, out_sum, nullptr, nullptr, cuda_stream);
+}
+
+int aiwcrf_oob(const aiwcrf_forest *forest, const float *X, int64_t n_rows, int64_t *out_sum, int32_t *out_count,
+               void *cuda_stream)
+{
+    g_last_error.clear();
+    if (!forest || !X || !out_sum || !out_count) return fail(AIWCRF_E_INVALID_ARG, "arguments must not be NULL");
+    if (forest->oob_rows == 0)
+        return fail(AIWCRF_E_INVALID_ARG, "out-of-bag evaluation needs a forest fitted by aiwcrf_fit in this process");
+    if (n_rows != forest->oob_rows) return fail(AIWCRF_E_INVALID_ARG, "n_rows differs from the training matrix");
+    int dev, rc;
+    if ((rc = current_device(&dev))) return rc;
+    if (dev != forest->device) return fail(AIWCRF_E_BAD_POINTER, "the forest lives on another device");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    InArg ax;
+    OutArg os, oc;
+    if ((rc = stage_in(ax, X, sizeof(float) * (size_t)forest->F * (size_t)n_rows, dev, s, "X"))) return rc;
+    if ((rc = stage_out(os, out_sum, sizeof(int64_t) * (size_t)n_rows, dev, s, "out_sum"))) return rc;
+    if ((rc = stage_out(oc, out_count, sizeof(int32_t) * (size_t)n_rows, dev, s, "out_count"))) return rc;
+    if ((rc = oob_launch(forest, (const float *)ax.dev, n_rows, (int64_t *)os.dev, (int32_t *)oc.dev, s))) return rc;
+    if ((rc = finish_out(os)) || (rc = finish_out(oc))) return rc;
+    return sync_if(os.host || oc.host, s);
 }
 
 int aiwcrf_round_mean(const int64_t *sums, int64_t n, int64_t total_trees, int64_t *out, void *cuda_stream)

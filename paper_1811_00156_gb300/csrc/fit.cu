@@ -189,6 +189,8 @@ struct BootArgs {
     int32_t *small_list, *big_list;
     uint32_t *counters;             // [0] small count, [1] big count
     uint32_t *err;
+    uint32_t *inbag;                // per tree ceil(N / 32) words: bit r set = row r drawn (or null)
+    int64_t inbag_words;
 };
 
 __global__ void __launch_bounds__(kBootThreads) bootstrap_kernel(BootArgs a)
@@ -231,6 +233,18 @@ __global__ void __launch_bounds__(kBootThreads) bootstrap_kernel(BootArgs a)
         }
     }
     __syncthreads();
+
+    if (a.inbag) {                  // in-bag bitmap for out-of-bag evaluation
+        uint32_t *bits = a.inbag + (size_t)t * (size_t)a.inbag_words;
+        for (int64_t wd = tid; wd < a.inbag_words; wd += kBootThreads) {
+            uint32_t v = 0;
+            for (int b = 0; b < 32; ++b) {
+                const int64_t row = wd * 32 + b;
+                if (row < a.N && ((cnt[row >> 2] >> (8u * (uint32_t)(row & 3))) & 255u)) v |= 1u << b;
+            }
+            bits[wd] = v;
+        }
+    }
 
     uint32_t running = 0;
     unsigned long long acc_n = 0;
@@ -1247,6 +1261,12 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     };
 
     LevelCounts *d_cnt = sc.get<LevelCounts>(1, &rc); if (rc) return rc;
+    // in-bag bitmaps (forests fitted on all rows keep them for out-of-bag evaluation)
+    const int64_t inbag_words = (N + 31) / 32;
+    uint32_t *d_inbag = nullptr;
+    if (!d_sub_rows) {
+        d_inbag = sc.get<uint32_t>((size_t)T * (size_t)inbag_words, &rc); if (rc) return rc;
+    }
     {
         LevelCounts c0;
         c0.n_small = 0u; c0.n_big = 0u; c0.C = (uint32_t)T; c0.levels = 0u; c0.packed_off = 0ull;
@@ -1273,6 +1293,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         ba.smem_words = gcnt ? 0 : (int)words;
         ba.rows_out = rows_a; ba.row_cap = row_cap; ba.root = nodes_cur;
         ba.small_list = small_a; ba.big_list = big_a; ba.counters = &d_cnt->n_small; ba.err = d_err;
+        ba.inbag = d_inbag; ba.inbag_words = inbag_words;
         prof_begin(s, kProfBoot);
         bootstrap_kernel<<<(unsigned)T, kBootThreads, smem_bytes, s>>>(ba);
         AIWCRF_LAUNCH_CHECK("bootstrap_kernel");
@@ -1406,7 +1427,11 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         // the training value tables code the queries at predict time
         fr->max_card = max_card;
         fr->fstride = std::max<int64_t>(max_card, 1);
+        if (d_inbag) { fr->oob_rows = N; fr->inbag_words = inbag_words; }
         AIWCRF_CUDA(forest_alloc(fr));
+        if (d_inbag)
+            AIWCRF_CUDA(cudaMemcpyAsync(fr->d_inbag, d_inbag + (size_t)g * (size_t)Tper * (size_t)inbag_words,
+                                        sizeof(uint32_t) * (size_t)Tper * (size_t)inbag_words, cudaMemcpyDeviceToDevice, s));
         AIWCRF_CUDA(cudaMemcpy2DAsync(fr->d_fvals, sizeof(float) * (size_t)fr->fstride, d_vals, sizeof(float) * (size_t)N,
                                       sizeof(float) * (size_t)max_card, (size_t)F, cudaMemcpyDeviceToDevice, s));
         AIWCRF_CUDA(cudaMemcpyAsync(fr->d_fcard, d_card, sizeof(uint32_t) * (size_t)F, cudaMemcpyDeviceToDevice, s));

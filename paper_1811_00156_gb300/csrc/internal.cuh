@@ -358,6 +358,10 @@ struct aiwcrf_forest {
     // 65,536 nodes: bit 31 leaf; else bits 24..30 feature, 16..23 code, 0..15 left child.
     // Trees padded to a multiple of four nodes (16-byte aligned copies); leaf values are read
     // from d_nodes at the same tree-relative index.
+    // out-of-bag evaluation: per tree ceil(oob_rows / 32) words, bit r = training row r in-bag
+    int64_t oob_rows = 0;                 // 0: not available (deserialized or subset forests)
+    int64_t inbag_words = 0;
+    uint32_t *d_inbag = nullptr;
     bool compact = false;
     uint32_t *d_c32 = nullptr;
     int64_t *d_tree_off4 = nullptr;       // T + 1 offsets into d_c32
@@ -385,6 +389,7 @@ namespace aiwcrf {
 int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, int64_t N, int32_t F,
               const std::vector<int64_t> &sub_off, const int32_t *d_sub_rows, int32_t G,
               cudaStream_t s, std::vector<aiwcrf_forest *> &out);
+int oob_launch(const aiwcrf_forest *f, const float *dX, int64_t N, int64_t *d_sum, int32_t *d_count, cudaStream_t s);
 int predict_launch(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum,
                    int64_t *d_pred, uint64_t *d_var, int64_t total_trees, cudaStream_t s);
 int round_mean_launch(const int64_t *d_sum, int64_t Q, int64_t total_trees, int64_t *d_out,

@@ -398,6 +398,36 @@ __global__ void __launch_bounds__(kPredThreads) predict4_kernel(
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// out-of-bag evaluation (the tuning objective of Sec. III-B): per training row, the exact sum of
+// the leaf values of the trees whose bootstrap did not draw it, and their number
+// ------------------------------------------------------------------------------------------
+template <typename CT>
+__global__ void oob_kernel(const uint64_t *__restrict__ cnodes, const int64_t *__restrict__ tree_off, int T,
+                           const CT *__restrict__ codes, int ld, int64_t N, const uint32_t *__restrict__ inbag,
+                           int64_t words, int64_t *__restrict__ out_sum, int32_t *__restrict__ out_count)
+{
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= N) return;
+    const CT *x = codes + (size_t)row * (size_t)ld;
+    int64_t sum = 0;
+    int32_t cnt = 0;
+    for (int t = 0; t < T; ++t) {
+        if ((__ldg(&inbag[(size_t)t * (size_t)words + (size_t)(row >> 5)]) >> (row & 31)) & 1u) continue;
+        const uint64_t *tn = cnodes + tree_off[t];
+        uint32_t j = 0;
+        for (;;) {
+            const uint64_t nd = __ldg(&tn[j]);
+            if (nd >> 63) { sum += leaf_value(nd); break; }
+            const uint32_t f = (uint32_t)(nd >> 56) & 0x7Fu;
+            j = ((uint32_t)(nd >> 32) & 0xFFFFFFu) + ((uint32_t)x[f] > ((uint32_t)nd & 0xFFFFFFu) ? 1u : 0u);
+        }
+        ++cnt;
+    }
+    out_sum[row] = sum;
+    out_count[row] = cnt;
+}
+
 __global__ void round_mean_kernel(const int64_t *sums, int64_t n, int64_t T, int64_t *out)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -550,6 +580,35 @@ int predict_launch(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t 
     cudaFreeAsync(d_err, s);
     if (rc == AIWCRF_OK && (h_err & kErrTimeout)) rc = fail(AIWCRF_E_TIMEOUT, "a bounded device wait gave up");
     return rc;
+}
+
+namespace {
+template <typename CT>
+int oob_ct(const aiwcrf_forest *f, const float *dX, int64_t N, int64_t *d_sum, int32_t *d_count, cudaStream_t s)
+{
+    const int ld = f->F;
+    CT *d_codes = nullptr;
+    cudaError_t e = cudaMallocAsync(&d_codes, sizeof(CT) * (size_t)N * (size_t)ld, s);
+    if (e != cudaSuccess) return fail(AIWCRF_E_OOM, "device allocation of the row codes failed");
+    struct Free { CT *p; cudaStream_t s; ~Free() { cudaFreeAsync(p, s); } } fr{d_codes, s};
+    code_queries_kernel<CT><<<dim3((unsigned)((N + 255) / 256), (unsigned)f->F), 256, 0, s>>>(
+        dX, N, f->F, f->d_fvals, f->fstride, f->d_fcard, d_codes, ld);
+    oob_kernel<CT><<<(unsigned)((N + 127) / 128), 128, 0, s>>>(f->d_cnodes, f->d_tree_off, (int)f->T, d_codes, ld, N,
+                                                              f->d_inbag, f->inbag_words, d_sum, d_count);
+    count_launches(2);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "oob launch");
+    return AIWCRF_OK;
+}
+}  // namespace
+
+int oob_launch(const aiwcrf_forest *f, const float *dX, int64_t N, int64_t *d_sum, int32_t *d_count, cudaStream_t s)
+{
+    if (N == 0) return AIWCRF_OK;
+    keep_pool_memory(f->device);
+    if (f->max_card <= 255u) return oob_ct<uint8_t>(f, dX, N, d_sum, d_count, s);
+    if (f->max_card <= 65535u) return oob_ct<uint16_t>(f, dX, N, d_sum, d_count, s);
+    return oob_ct<uint32_t>(f, dX, N, d_sum, d_count, s);
 }
 
 int forest_build_compact(aiwcrf_forest *f, cudaStream_t s)

@@ -286,3 +286,23 @@ def test_predict_special_query_values():
     A.aiwcrf_predict(g, dev(Xq), out)
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy(), ref.predict(Xq)[0])
+
+
+def test_oob_matches_oracle():
+    wl = synth.plain_forest_workload()
+    T = 64
+    f = gpu_fit(wl, T, 10, 5)
+    ref = O.fit(wl.X, wl.y, T, 10, 5, seed=156)
+    s = torch.empty(wl.n_rows, dtype=torch.int64, device="cuda")
+    c = torch.empty(wl.n_rows, dtype=torch.int32, device="cuda")
+    A.aiwcrf_oob(f, dev(wl.X), s, c)
+    torch.cuda.synchronize()
+    rs, rc = ref.oob(wl.X)
+    assert np.array_equal(s.cpu().numpy(), rs) and np.array_equal(c.cpu().numpy(), rc)
+    err = A.oob_error(rs, rc, wl.y)
+    assert 0.0 < err < 1.0                                   # log10-seconds squared
+    # subset forests keep no bitmaps
+    fs = A.aiwcrf_fit_subsets(A.params(4, 10, 5), dev(wl.X), dev(wl.y), np.array([0, 100], np.int64),
+                              dev(np.arange(100, dtype=np.int32)))
+    with pytest.raises(A.AiwcrfError):
+        A.aiwcrf_oob(fs[0], dev(wl.X), s, c)

@@ -315,3 +315,24 @@ def test_oracle_trees_grown_on_threads_match_serial():
         a, b = parts[k].tree(0), full.tree(k)
         assert np.array_equal(a.feature, b.feature) and np.array_equal(a.thr, b.thr)
         assert np.array_equal(a.value, b.value) and np.array_equal(a.left, b.left)
+
+
+def test_oob_sums_are_the_out_of_bag_trees():
+    """Out-of-bag sums equal the sum over exactly the trees whose bootstrap skipped the row,
+    each tree evaluated as a single-tree forest; rows drawn by every tree have count 0."""
+    wl = synth.small_case(75, 250, 5, card=9)
+    T = 9
+    fr = O.fit(wl.X, wl.y, T, 3, 2, seed=12)
+    s, c = fr.oob(wl.X)
+    exp_s = np.zeros(wl.n_rows, object)
+    exp_c = np.zeros(wl.n_rows, np.int64)
+    for t in range(T):
+        w = O.bootstrap_counts(12, t, wl.n_rows)
+        _, leaf = O.fit(wl.X, wl.y, 1, 3, 2, seed=12, t0=t).predict(wl.X)
+        out = w == 0
+        exp_s[out] += leaf[out].astype(object)
+        exp_c[out] += 1
+    assert np.array_equal(s.astype(object), exp_s) and np.array_equal(c, exp_c)
+    assert 0.2 < (c > 0).mean() <= 1.0                       # about 1 - 0.632^9 of the rows
+    nb = O.fit(wl.X, wl.y, 3, 3, 2, seed=12, bootstrap=False)
+    assert not nb.oob(wl.X)[1].any()
