@@ -162,6 +162,16 @@ int aiwcrf_select_device_noalloc(const aiwcrf_forest *forest, const float *kfeat
                                  int32_t size_class, const int32_t *device_ids, int32_t n_devices,
                                  int32_t *out_best, int64_t *out_pred, void *cuda_stream);
 
+/* Tensor-core primitive of the learned surrogate (the paper has no surrogate; the model queried
+ * in Sec. VI is the forest): C (M x N, FP32, row-major, device) = A * B^T for BF16 A (M x K)
+ * and B (N x K), on tcgen05 with an FP32 accumulator in tensor memory. Element (m, k) of A is
+ * A[m * lda + k], or A[k * lda + m] with a_trans; likewise B with b_trans. N is a multiple of 16
+ * in [16, 256]; lda and ldb are multiples of 8; device pointers, 16-byte aligned. ksplit > 1
+ * spreads K over that many CTAs per 128-row slab and sums their FP32 partials in a fixed order. */
+int aiwcrf_tc_gemm_bf16(const void *A, int32_t lda, int32_t a_trans, const void *B, int32_t ldb,
+                        int32_t b_trans, float *C, int32_t M, int32_t N, int32_t K, int32_t ksplit,
+                        void *cuda_stream);
+
 /* Counters of the fit that produced the forest (zeros for a deserialized forest). */
 int aiwcrf_forest_stats(const aiwcrf_forest *forest, aiwcrf_fit_stats *out);
 

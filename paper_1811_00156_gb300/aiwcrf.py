@@ -49,7 +49,7 @@ EXPORTS = ["aiwcrf_fit", "aiwcrf_fit_subsets", "aiwcrf_predict", "aiwcrf_predict
            "aiwcrf_forest_serialize", "aiwcrf_forest_deserialize", "aiwcrf_forest_free",
            "aiwcrf_last_error", "aiwcrf_profile_enable", "aiwcrf_profile_read",
            "aiwcrf_profile_name", "aiwcrf_profile_num_classes", "aiwcrf_launch_count",
-           "aiwcrf_select_device_noalloc"]
+           "aiwcrf_select_device_noalloc", "aiwcrf_tc_gemm_bf16"]
 
 _lib = None
 _lock = threading.Lock()
@@ -73,6 +73,8 @@ def load():
         L.aiwcrf_predict_sum.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
         L.aiwcrf_round_mean.argtypes = [_vp, C.c_int64, C.c_int64, _vp, _vp]
         L.aiwcrf_oob.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp]
+        L.aiwcrf_tc_gemm_bf16.argtypes = [_vp, C.c_int32, C.c_int32, _vp, C.c_int32, C.c_int32, _vp, C.c_int32,
+                                          C.c_int32, C.c_int32, C.c_int32, _vp]
         L.aiwcrf_select_device.argtypes = [_vp, _vp, C.c_int32, C.c_int32, _vp, C.c_int32, _vp, _vp, _vp]
         L.aiwcrf_select_device_noalloc.argtypes = [_vp, _vp, C.c_int32, C.c_int32, _vp, C.c_int32, _vp, _vp, _vp]
         L.aiwcrf_forest_stats.argtypes = [_vp, C.POINTER(FitStats)]
@@ -203,6 +205,16 @@ def oob_error(sums: np.ndarray, counts: np.ndarray, y: np.ndarray) -> float:
     s, c = sums[m].astype(object), counts[m].astype(object)
     pred = np.array([(2 * int(a) + int(b)) // (2 * int(b)) for a, b in zip(s, c)], dtype=np.float64)
     return float(np.mean(((pred - y[m].astype(np.float64)) / 2.0 ** 32) ** 2))
+
+
+def aiwcrf_tc_gemm_bf16(A, B, C, a_trans=False, b_trans=False, ksplit=1, stream=None):
+    """C = A @ B^T on the tensor cores (BF16 in, FP32 out). A: (M, K) or, with a_trans, (K, M)."""
+    M = A.shape[1] if a_trans else A.shape[0]
+    K = A.shape[0] if a_trans else A.shape[1]
+    N = B.shape[1] if b_trans else B.shape[0]
+    _check(load().aiwcrf_tc_gemm_bf16(_ptr(A), A.shape[1], int(a_trans), _ptr(B), B.shape[1], int(b_trans), _ptr(C),
+                                      M, N, K, int(ksplit), _stream(stream)))
+    return C
 
 
 def aiwcrf_round_mean(sums, total_trees: int, out, stream=None):

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libaiwcrf.so")
-SOURCES = ["fit.cu", "sort.cu", "predict.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["fit.cu", "sort.cu", "predict.cu", "api.cu", "noalloc.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -34,7 +34,8 @@ def _flags(extra=()):
 def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
-    deps = [src, os.path.join(CSRC, "internal.cuh"), os.path.join(ROOT, "include", "aiwcrf.h")]
+    deps = [src, os.path.join(CSRC, "internal.cuh"), os.path.join(CSRC, "tc.cuh"),
+            os.path.join(ROOT, "include", "aiwcrf.h")]
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps)
 
 
