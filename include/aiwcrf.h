@@ -172,6 +172,65 @@ int aiwcrf_tc_gemm_bf16(const void *A, int32_t lda, int32_t a_trans, const void 
                         int32_t b_trans, float *C, int32_t M, int32_t N, int32_t K, int32_t ksplit,
                         void *cuda_stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Learned surrogate (not in the paper: its model is the forest of Sec. III-B). A small MLP
+ * distilled from a forest's own predictions, for cheaper queries: inputs are the first F-2
+ * (AIWC) columns standardised -- after log2 for columns of values >= 1 that span three orders
+ * of magnitude -- then one-hot device (column F-2) and size class (column F-1), zero-padded to
+ * 64; layers 64 -> 256 -> 256 -> 1 with GELU; BF16 weights and activations, FP32 accumulation
+ * on the tensor cores (tcgen05); output log10 seconds as float. Trained with Adam on the mean
+ * squared error against the forest's predictions.
+ * Parameter vector (float32, aiwcrf_surrogate_num_params() of them): W1[256][64], b1[256],
+ * W2[256][256], b2[256], w3[256], b3. */
+typedef struct aiwcrf_surrogate aiwcrf_surrogate;
+
+typedef struct {
+    int32_t epochs;      /* passes over the samples (20) */
+    int32_t batch;       /* samples per Adam step, a multiple of 128 (4096) */
+    float lr;            /* Adam step size (1e-3) */
+    float beta1;         /* 0.9 */
+    float beta2;         /* 0.999 */
+    float eps;           /* 1e-8 */
+    uint64_t seed;       /* weight initialisation and shuffling */
+    int32_t n_devices;   /* one-hot width of the device column (15) */
+    int32_t n_sizes;     /* one-hot width of the size-class column (4) */
+} aiwcrf_surrogate_params;
+
+typedef struct {
+    int64_t steps;
+    float first_batch_loss;   /* mean of (out - y)^2 / 2 over the first batch */
+    float last_batch_loss;    /* ... over the last batch */
+} aiwcrf_surrogate_fit_stats;
+
+/* Distil: label X (device, F x n column-major) with the teacher forest's predictions and train. */
+int aiwcrf_surrogate_fit(const aiwcrf_surrogate_params *params, const aiwcrf_forest *teacher,
+                         const float *X, int64_t n, int32_t n_features, void *cuda_stream,
+                         aiwcrf_surrogate **out);
+
+/* out[q] = surrogate prediction of log10 seconds for query q (device pointers). One fused
+ * persistent kernel: weights resident in shared memory, both layers on the tensor cores. */
+int aiwcrf_surrogate_predict(const aiwcrf_surrogate *surrogate, const float *Xq, int64_t n,
+                             float *out, void *cuda_stream);
+
+/* Loss (sum over the batch of (out - y)^2 / 2) and its gradient with respect to every
+ * parameter divided by n (the training step's gradient), for X (F x n) and float targets y;
+ * n a multiple of 128; device pointers; grad has aiwcrf_surrogate_num_params() floats. */
+int aiwcrf_surrogate_grad(const aiwcrf_surrogate *surrogate, const float *X, const float *y,
+                          int32_t n, float *grad, float *loss, void *cuda_stream);
+
+/* Build a surrogate from a host parameter vector and feature transform (mean, standard
+ * deviation and log2 flag of each of the F-2 AIWC columns). */
+int aiwcrf_surrogate_create(int32_t n_features, int32_t n_devices, int32_t n_sizes,
+                            const float *params, const float *mu, const float *sd,
+                            const uint8_t *log2_cols, aiwcrf_surrogate **out);
+
+/* Copy out parameters and feature transform (host arrays; any may be NULL). */
+int aiwcrf_surrogate_export(const aiwcrf_surrogate *surrogate, float *params, float *mu,
+                            float *sd, uint8_t *log2_cols);
+int aiwcrf_surrogate_stats(const aiwcrf_surrogate *surrogate, aiwcrf_surrogate_fit_stats *out);
+int32_t aiwcrf_surrogate_num_params(void);
+int aiwcrf_surrogate_free(aiwcrf_surrogate *surrogate);
+
 /* Counters of the fit that produced the forest (zeros for a deserialized forest). */
 int aiwcrf_forest_stats(const aiwcrf_forest *forest, aiwcrf_fit_stats *out);
 

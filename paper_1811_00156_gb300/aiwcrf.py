@@ -32,6 +32,16 @@ class FitParams(C.Structure):
                 ("reserved", C.c_int32), ("first_tree", C.c_int64)]
 
 
+class SurrogateParams(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("seed", C.c_uint64), ("n_devices", C.c_int32),
+                ("n_sizes", C.c_int32)]
+
+
+class SurrogateStats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("first_batch_loss", C.c_float), ("last_batch_loss", C.c_float)]
+
+
 class FitStats(C.Structure):
     _fields_ = [("num_trees", C.c_int64), ("total_nodes", C.c_int64), ("levels", C.c_int64),
                 ("groups", C.c_int64), ("entries_evaluated", C.c_int64), ("entries_partitioned", C.c_int64),
@@ -49,7 +59,9 @@ EXPORTS = ["aiwcrf_fit", "aiwcrf_fit_subsets", "aiwcrf_predict", "aiwcrf_predict
            "aiwcrf_forest_serialize", "aiwcrf_forest_deserialize", "aiwcrf_forest_free",
            "aiwcrf_last_error", "aiwcrf_profile_enable", "aiwcrf_profile_read",
            "aiwcrf_profile_name", "aiwcrf_profile_num_classes", "aiwcrf_launch_count",
-           "aiwcrf_select_device_noalloc", "aiwcrf_tc_gemm_bf16"]
+           "aiwcrf_select_device_noalloc", "aiwcrf_tc_gemm_bf16", "aiwcrf_surrogate_fit",
+           "aiwcrf_surrogate_predict", "aiwcrf_surrogate_grad", "aiwcrf_surrogate_create", "aiwcrf_surrogate_export",
+           "aiwcrf_surrogate_stats", "aiwcrf_surrogate_num_params", "aiwcrf_surrogate_free"]
 
 _lib = None
 _lock = threading.Lock()
@@ -73,6 +85,15 @@ def load():
         L.aiwcrf_predict_sum.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
         L.aiwcrf_round_mean.argtypes = [_vp, C.c_int64, C.c_int64, _vp, _vp]
         L.aiwcrf_oob.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp]
+        L.aiwcrf_surrogate_fit.argtypes = [C.POINTER(SurrogateParams), _vp, _vp, C.c_int64, C.c_int32, _vp,
+                                           C.POINTER(_vp)]
+        L.aiwcrf_surrogate_predict.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
+        L.aiwcrf_surrogate_grad.argtypes = [_vp, _vp, _vp, C.c_int32, _vp, _vp, _vp]
+        L.aiwcrf_surrogate_create.argtypes = [C.c_int32, C.c_int32, C.c_int32, _vp, _vp, _vp, _vp, C.POINTER(_vp)]
+        L.aiwcrf_surrogate_export.argtypes = [_vp, _vp, _vp, _vp, _vp]
+        L.aiwcrf_surrogate_stats.argtypes = [_vp, C.POINTER(SurrogateStats)]
+        L.aiwcrf_surrogate_num_params.restype = C.c_int32
+        L.aiwcrf_surrogate_free.argtypes = [_vp]
         L.aiwcrf_tc_gemm_bf16.argtypes = [_vp, C.c_int32, C.c_int32, _vp, C.c_int32, C.c_int32, _vp, C.c_int32,
                                           C.c_int32, C.c_int32, C.c_int32, _vp]
         L.aiwcrf_select_device.argtypes = [_vp, _vp, C.c_int32, C.c_int32, _vp, C.c_int32, _vp, _vp, _vp]
@@ -91,7 +112,7 @@ def load():
         L.aiwcrf_launch_count.restype = C.c_int64
         for name in EXPORTS:
             if name not in ("aiwcrf_last_error", "aiwcrf_profile_name", "aiwcrf_profile_num_classes",
-                            "aiwcrf_launch_count"):
+                            "aiwcrf_launch_count", "aiwcrf_surrogate_num_params"):
                 getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -205,6 +226,67 @@ def oob_error(sums: np.ndarray, counts: np.ndarray, y: np.ndarray) -> float:
     s, c = sums[m].astype(object), counts[m].astype(object)
     pred = np.array([(2 * int(a) + int(b)) // (2 * int(b)) for a, b in zip(s, c)], dtype=np.float64)
     return float(np.mean(((pred - y[m].astype(np.float64)) / 2.0 ** 32) ** 2))
+
+
+class Surrogate:
+    """A trained surrogate owned by the library."""
+
+    def __init__(self, handle: int, F: int):
+        self._h = _vp(handle)
+        self.F = F
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().aiwcrf_surrogate_free(self._h)
+        self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def predict(self, Xq, out, stream=None):
+        F, Q = _shape(Xq)
+        _check(load().aiwcrf_surrogate_predict(self._h, _ptr(Xq), Q, _ptr(out), _stream(stream)))
+        return out
+
+    def grad(self, X, y, grad, loss, stream=None):
+        F, n = _shape(X)
+        _check(load().aiwcrf_surrogate_grad(self._h, _ptr(X), _ptr(y), n, _ptr(grad), _ptr(loss), _stream(stream)))
+        return grad, loss
+
+    def export(self):
+        P = np.zeros(int(load().aiwcrf_surrogate_num_params()), np.float32)
+        mu = np.zeros(self.F - 2, np.float32)
+        sd = np.zeros(self.F - 2, np.float32)
+        lg = np.zeros(self.F - 2, np.uint8)
+        _check(load().aiwcrf_surrogate_export(self._h, P.ctypes.data, mu.ctypes.data, sd.ctypes.data, lg.ctypes.data))
+        return P, mu, sd, lg
+
+    def stats(self) -> dict:
+        st = SurrogateStats()
+        _check(load().aiwcrf_surrogate_stats(self._h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+
+def surrogate_params(epochs=20, batch=4096, lr=1e-3, seed=156, n_devices=15, n_sizes=4) -> SurrogateParams:
+    return SurrogateParams(epochs, batch, lr, 0.9, 0.999, 1e-8, seed, n_devices, n_sizes)
+
+
+def aiwcrf_surrogate_fit(params: SurrogateParams, teacher: Forest, X, stream=None) -> Surrogate:
+    F, n = _shape(X)
+    h = _vp()
+    _check(load().aiwcrf_surrogate_fit(C.byref(params), teacher.handle, _ptr(X), n, F, _stream(stream), C.byref(h)))
+    return Surrogate(h.value, F)
+
+
+def aiwcrf_surrogate_create(F, n_devices, n_sizes, P, mu, sd, log2_cols) -> Surrogate:
+    P = np.ascontiguousarray(P, np.float32)
+    mu, sd = np.ascontiguousarray(mu, np.float32), np.ascontiguousarray(sd, np.float32)
+    lg = np.ascontiguousarray(log2_cols, np.uint8)
+    h = _vp()
+    _check(load().aiwcrf_surrogate_create(F, n_devices, n_sizes, P.ctypes.data, mu.ctypes.data, sd.ctypes.data,
+                                          lg.ctypes.data, C.byref(h)))
+    return Surrogate(h.value, F)
 
 
 def aiwcrf_tc_gemm_bf16(A, B, C, a_trans=False, b_trans=False, ksplit=1, stream=None):

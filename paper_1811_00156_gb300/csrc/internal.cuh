@@ -1,6 +1,7 @@
 // internal.cuh -- types and device helpers shared by the library's translation units.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -389,6 +390,8 @@ namespace aiwcrf {
 int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, int64_t N, int32_t F,
               const std::vector<int64_t> &sub_off, const int32_t *d_sub_rows, int32_t G,
               cudaStream_t s, std::vector<aiwcrf_forest *> &out);
+int tc_gemm(const __nv_bfloat16 *A, int lda, bool a_trans, const __nv_bfloat16 *B, int ldb, bool b_trans, float *C,
+            int M, int N, int K, int ksplit, float *part, uint32_t *d_err, cudaStream_t s);
 int oob_launch(const aiwcrf_forest *f, const float *dX, int64_t N, int64_t *d_sum, int32_t *d_count, cudaStream_t s);
 int predict_launch(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum,
                    int64_t *d_pred, uint64_t *d_var, int64_t total_trees, cudaStream_t s);
