@@ -324,6 +324,11 @@ def run_ours(args):
         out["oob"] = oob_report(A, wl, X, f)
         del f
         out["loko"] = loko_report(A, dev)
+        f = A.aiwcrf_fit(params, X, y)
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        out["surrogate"] = surrogate_report(A, f, Xq, bf16_peak_tflops=peaks.get("bf16_tflops"))
+        del f
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
@@ -392,6 +397,52 @@ def loko_report(A, dev, steps: int = 2):
             "fit_ms": min(ms), "rows_trees_per_s": rows_trees / (min(ms) / 1e3),
             "mape_mean": float(np.mean(mape)), "mape_median": float(np.median(mape)),
             "mape_max": float(np.max(mape)), "batched": "one aiwcrf_fit_subsets call for all folds"}
+
+
+def surrogate_report(A, forest, Xq, n_train=4_000_000, epochs=20, bf16_peak_tflops=None):
+    """The learned surrogate distilled from the benchmark forest: 4,000,000 samples of the query
+    distribution labelled by the forest, Adam (lr 1e-3, batch 4096, 20 epochs); then both models
+    predict the benchmark's 1,000,000 queries. Error against the forest for the BF16 tensor-core
+    network and, on a 20,000-query sample, for the same weights evaluated in FP64 by the oracle."""
+    import torch
+    from oracle import mlp as M
+    dev = Xq.device
+    Xs = torch.from_numpy(synth.queries(n_train, seed=4242)).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sg = A.aiwcrf_surrogate_fit(A.surrogate_params(epochs=epochs, batch=4096), forest, Xs)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del Xs
+    Q = Xq.shape[1]
+    ref = torch.empty(Q, dtype=torch.int64, device=dev)
+    out = torch.empty(Q, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        A.aiwcrf_predict(forest, Xq, ref)
+        sg.predict(Xq, out)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record(); A.aiwcrf_predict(forest, Xq, ref); e[1].record()
+    e[2].record(); sg.predict(Xq, out); e[3].record()
+    torch.cuda.synchronize()
+    f_ms, s_ms = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
+    f = ref.cpu().numpy() / 2.0 ** 32
+    s = out.cpu().numpy().astype(np.float64)
+    err = np.abs(s - f)
+    P, mu, sd, lg = sg.export()
+    idx = np.arange(0, Q, max(1, Q // 20000))
+    Xh = Xq[:, idx].cpu().numpy()
+    r64, _ = M.forward(P.astype(np.float64), M.encode(Xh, mu, sd, lg, 15, 4), rounding=False)
+    flops = 2.0 * Q * (64 * 256 + 256 * 256 + 256)
+    rep = {"train_samples": n_train, "epochs": epochs, "train_s": train_s, "stats": sg.stats(),
+           "queries_per_s": Q / (s_ms / 1e3), "forest_queries_per_s": Q / (f_ms / 1e3),
+           "speedup_vs_forest": f_ms / s_ms, "mae_vs_forest_log10": float(err.mean()),
+           "p99_abs_err_log10": float(np.percentile(err, 99)),
+           "mae_vs_forest_fp64_oracle_log10": float(np.abs(r64 - f[idx]).mean()),
+           "mae_of_mean_predictor_log10": float(np.abs(f - f.mean()).mean()),
+           "tensor_tflops": flops / (s_ms / 1e3) / 1e12}
+    if bf16_peak_tflops:
+        rep["tensor_frac_of_measured_bf16"] = rep["tensor_tflops"] / bf16_peak_tflops
+    return rep
 
 
 def oob_report(A, wl, X, forest):
