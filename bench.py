@@ -329,6 +329,7 @@ def run_ours(args):
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
         out["surrogate"] = surrogate_report(A, f, Xq, bf16_peak_tflops=peaks.get("bf16_tflops"))
         del f
+        out["serving"] = serving_report(A, wl)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
@@ -443,6 +444,62 @@ def surrogate_report(A, forest, Xq, n_train=4_000_000, epochs=20, bf16_peak_tflo
     if bf16_peak_tflops:
         rep["tensor_frac_of_measured_bf16"] = rep["tensor_tflops"] / bf16_peak_tflops
     return rep
+
+
+def serving_report(A, wl, rates=(5000.0, 20000.0, 50000.0), n_requests=20000, refit_every=10000):
+    """The device-selection server under open-loop Poisson load: a 500-tree forest of the
+    111,000-row workload resident, requests of 1-64 kernels (uniform) x 15 devices x one size
+    class (uniform), a refit every 10,000 requests on 2,220 appended rows. Latency runs from the
+    scheduled arrival to the completed batch being seen on the host. A sample of the answers is
+    checked against aiwcrf_select_device on the creation forest."""
+    rng = np.random.default_rng(2024)
+    pool = np.ascontiguousarray(synth.queries(4096, seed=77)[:synth.N_AIWC])
+    devices = np.arange(SEL_DEVICES, dtype=np.int32)
+    fp = A.params(T_TREES, MTRY, MIN_NODE, seed=synth.FOREST_SEED)
+    sp = A.server_params(n_streams=4, max_request_kernels=64, batch_kernels=1024, arena_bytes=64 << 20,
+                         refit_every=refit_every, refit_rows=synth.N_KERNELS * SEL_DEVICES * synth.N_SIZES)
+    out = {"trees": T_TREES, "train_rows": wl.n_rows, "devices": SEL_DEVICES, "kernels_per_request": "1-64",
+           "refit_every": refit_every, "refit_rows": sp.refit_rows, "streams": sp.n_streams,
+           "batch_kernels": sp.batch_kernels, "arena_bytes": sp.arena_bytes, "runs": []}
+    with A.Server(sp, fp, wl.X, wl.y, devices) as srv:
+        # a lone request at a time: the latency floor
+        lat = []
+        for i in range(200):
+            t0 = time.perf_counter()
+            srv.wait(srv.submit(np.ascontiguousarray(pool[:, i:i + 64]), i % synth.N_SIZES))
+            lat.append((time.perf_counter() - t0) * 1e6)
+        out["lone_64_kernel_request_us"] = {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))}
+        # answers checked against the forest fitted at creation
+        ref = {}
+        f0 = A.aiwcrf_fit(fp, wl.X, wl.y)
+        for s_ in range(synth.N_SIZES):
+            b = np.zeros(pool.shape[1], np.int32)
+            A.aiwcrf_select_device(f0, pool, s_, devices, b)
+            ref[s_] = b
+        del f0
+        blk = 0
+        for rate in rates:
+            n_refit = n_requests // refit_every + 1
+            for _ in range(n_refit):
+                e = synth.plain_forest_workload(seed=synth.DATA_SEED + 100 + blk)
+                blk += 1
+                srv.append(e.X, e.y)
+            k = rng.integers(1, 65, n_requests).astype(np.int32)
+            first = (rng.integers(0, pool.shape[1] - 64, n_requests)).astype(np.int64)
+            size = rng.integers(0, synth.N_SIZES, n_requests).astype(np.int32)
+            rep, best, gen, _ = srv.run_load(pool, first, k, size, rate_per_s=rate, seed=int(rate), timeout_ms=600000)
+            checked = mism = 0
+            off = 0
+            for i in range(n_requests):
+                if gen[i] == 0:
+                    checked += 1
+                    mism += int((best[off:off + k[i]] != ref[int(size[i])][first[i]:first[i] + k[i]]).any())
+                off += k[i]
+            rep["generation_0_requests_checked"] = checked
+            rep["generation_0_mismatches"] = mism
+            out["runs"].append(rep)
+        out["counters"] = srv.stats()
+    return out
 
 
 def oob_report(A, wl, X, forest):

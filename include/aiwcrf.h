@@ -231,6 +231,126 @@ int aiwcrf_surrogate_stats(const aiwcrf_surrogate *surrogate, aiwcrf_surrogate_f
 int32_t aiwcrf_surrogate_num_params(void);
 int aiwcrf_surrogate_free(aiwcrf_surrogate *surrogate);
 
+/* ---------------------------------------------------------------------------------------------
+ * Device-selection server. Sec. VI's use of the model is a scheduler that asks, for kernels about
+ * to run, which device will be fastest; Sec. I notes the model is retrained only when the set of
+ * devices changes. The server keeps a forest resident on the device and answers requests
+ * (1..max_request_kernels kernels of one size class, each against every server device) by
+ * continuous batching:
+ *  - A dispatcher thread owns n_streams stream slots. Whenever a slot is free it takes the
+ *    pending requests in arrival order, as many as fit in one batch (batch_kernels kernels) and
+ *    in the device arena, and launches them as one batch: a host-to-device copy of the features,
+ *    one selection kernel (trees spread over warps, exact int64 sums, argmin with ties to the
+ *    lower device id), a device-to-host copy of the results. Batches on different slots run
+ *    concurrently; requests arriving meanwhile queue for the next free slot.
+ *  - Admission by device memory: every batch's inputs and outputs live in a first-fit arena of
+ *    arena_bytes carved from one allocation made at creation. A batch takes requests only while
+ *    their bytes fit the arena's free space; the rest wait for batches to complete and release
+ *    theirs. A request that could never fit, has more than max_request_kernels kernels, or
+ *    arrives while max_pending requests wait, is refused with AIWCRF_E_LIMIT.
+ *  - Refit: rows appended with aiwcrf_server_append are held on the host. Every refit_every
+ *    completed requests (and on aiwcrf_server_refit) a refit thread moves refit_rows of them
+ *    (all when 0) into the training set, fits a new forest with the creation's fit parameters on
+ *    its own stream, and swaps it in. Each batch uses the forest current when it was formed, and
+ *    each result reports that forest's generation (0 = the forest fitted at creation). A result
+ *    equals aiwcrf_select_device on a forest fitted by aiwcrf_fit on the same rows.
+ * Host pointers throughout; the server copies what it keeps. The device is the calling thread's
+ * current device at creation. */
+typedef struct aiwcrf_server aiwcrf_server;
+
+typedef struct {
+    int32_t n_streams;            /* batches in flight at once, 1..16 (4) */
+    int32_t max_request_kernels;  /* kernels of one request, 1..4096 (64) */
+    int32_t batch_kernels;        /* kernels of one batch, max_request_kernels..65536 (1024) */
+    int32_t max_pending;          /* requests waiting for a slot, >= 1 (65536) */
+    int64_t arena_bytes;          /* device arena for batch inputs and outputs (64 MiB) */
+    int64_t refit_every;          /* completed requests between automatic refits; 0 = never */
+    int64_t refit_rows;           /* appended rows one refit consumes; 0 = all appended */
+} aiwcrf_server_params;
+
+typedef struct {
+    int64_t submitted;            /* requests accepted */
+    int64_t rejected;             /* requests refused with AIWCRF_E_LIMIT */
+    int64_t completed;
+    int64_t failed;               /* completed with an error */
+    int64_t batches;
+    int64_t batch_kernels_total;  /* sum over batches of their kernels */
+    int64_t batch_kernels_max;
+    int64_t arena_waits;          /* batches cut short because the arena was full */
+    int64_t arena_bytes;
+    int64_t arena_peak_bytes;     /* most arena bytes held at once */
+    int64_t refits;               /* forests swapped in after creation */
+    int64_t refit_failures;
+    int64_t generation;           /* generation of the current forest */
+    int64_t training_rows;        /* rows the current forest was fitted on */
+    int64_t appended_rows;        /* appended rows not yet consumed by a refit */
+    int64_t forest_bytes;         /* device bytes of the current forest */
+} aiwcrf_server_counters;
+
+typedef struct {
+    int64_t n_requests;
+    int64_t n_kernels;            /* sum of the requests' kernels */
+    double offered_rate;          /* requests per second of the Poisson arrival process */
+    double wall_s;                /* first arrival to last completion */
+    double requests_per_s;        /* n_requests / wall_s */
+    double kernels_per_s;
+    double p50_us, p99_us, mean_us, max_us;   /* arrival to completion */
+    int64_t batches;              /* batches launched during the run */
+    double mean_batch_kernels;
+    int64_t refits;               /* refits finished during the run */
+    int64_t failed;               /* requests that completed with an error or were abandoned */
+    int64_t rejected;             /* requests refused on arrival (AIWCRF_E_LIMIT) */
+} aiwcrf_load_report;
+
+/* X: host, F x n_rows column-major training matrix (columns F-2 and F-1 are the device id and
+ * the size class); y: host Q32.32 targets; device_ids: host, the n_devices (1..64) devices
+ * every request is answered for. Fits the generation-0 forest before returning. */
+int aiwcrf_server_create(const aiwcrf_server_params *params, const aiwcrf_fit_params *fit,
+                         const float *X, const int64_t *y, int64_t n_rows, int32_t n_features,
+                         const int32_t *device_ids, int32_t n_devices, aiwcrf_server **out);
+
+/* Queue one request: kfeat is a host (F-2) x n_kernels column-major matrix (copied before
+ * returning). *ticket identifies it for aiwcrf_server_wait. */
+int aiwcrf_server_submit(aiwcrf_server *server, const float *kfeat, int32_t n_kernels,
+                         int32_t size_class, int64_t *ticket);
+
+/* Wait up to timeout_ms (< 0: without limit) for a request; AIWCRF_E_TIMEOUT if it is still
+ * running (the ticket stays valid). On completion writes best (host, n_kernels device ids),
+ * pred (host n_kernels x n_devices row-major Q32.32, or NULL) and generation (or NULL), and
+ * retires the ticket; returns the request's status. */
+int aiwcrf_server_wait(aiwcrf_server *server, int64_t ticket, int32_t timeout_ms, int32_t *best,
+                       int64_t *pred, int64_t *generation);
+
+/* Append training rows (host, F x n_rows column-major, and targets) for later refits. */
+int aiwcrf_server_append(aiwcrf_server *server, const float *X, const int64_t *y, int64_t n_rows);
+
+/* Ask for a refit now; with wait != 0 return once it finished (its status). */
+int aiwcrf_server_refit(aiwcrf_server *server, int32_t wait);
+
+/* While paused != 0 the dispatcher forms no new batch (queued requests wait; batches in flight
+ * complete). */
+int aiwcrf_server_pause(aiwcrf_server *server, int32_t paused);
+
+int aiwcrf_server_stats(aiwcrf_server *server, aiwcrf_server_counters *out);
+
+/* Open-loop load generator: request i arrives at the i-th event of a Poisson process of
+ * rate_per_s (exponential gaps from a SplitMix64 stream of seed) and asks for kernels
+ * pool[:, first[i] .. first[i] + n_kernels[i]) of size class size_class[i]; pool is a host
+ * (F-2) x pool_kernels column-major matrix. Latency runs from the scheduled arrival to the
+ * dispatcher seeing the batch complete, so a late submission counts against it. Optional host
+ * outputs: best (sum of n_kernels entries, in request order), generation and latency_ns (one per
+ * request; a refused request keeps its best entries and gets latency -1). Returns the first failing request's status, or AIWCRF_E_TIMEOUT if requests were
+ * still running after timeout_ms (they are then abandoned without writing the outputs). */
+int aiwcrf_server_run_load(aiwcrf_server *server, const float *pool, int64_t pool_kernels,
+                           const int64_t *first, const int32_t *n_kernels, const int32_t *size_class,
+                           int64_t n_requests, double rate_per_s, uint64_t seed, int32_t timeout_ms,
+                           int32_t *best, int64_t *generation, int64_t *latency_ns,
+                           aiwcrf_load_report *report);
+
+/* Stop the dispatcher and refit threads (queued requests fail with AIWCRF_E_INVALID_ARG; batches
+ * in flight complete first) and free everything. */
+int aiwcrf_server_destroy(aiwcrf_server *server);
+
 /* Counters of the fit that produced the forest (zeros for a deserialized forest). */
 int aiwcrf_forest_stats(const aiwcrf_forest *forest, aiwcrf_fit_stats *out);
 

@@ -54,6 +54,33 @@ class FitStats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ServerParams(C.Structure):
+    _fields_ = [("n_streams", C.c_int32), ("max_request_kernels", C.c_int32), ("batch_kernels", C.c_int32),
+                ("max_pending", C.c_int32), ("arena_bytes", C.c_int64), ("refit_every", C.c_int64),
+                ("refit_rows", C.c_int64)]
+
+
+class ServerCounters(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in (
+        "submitted", "rejected", "completed", "failed", "batches", "batch_kernels_total", "batch_kernels_max",
+        "arena_waits", "arena_bytes", "arena_peak_bytes", "refits", "refit_failures", "generation",
+        "training_rows", "appended_rows", "forest_bytes")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class LoadReport(C.Structure):
+    _fields_ = [("n_requests", C.c_int64), ("n_kernels", C.c_int64), ("offered_rate", C.c_double),
+                ("wall_s", C.c_double), ("requests_per_s", C.c_double), ("kernels_per_s", C.c_double),
+                ("p50_us", C.c_double), ("p99_us", C.c_double), ("mean_us", C.c_double), ("max_us", C.c_double),
+                ("batches", C.c_int64), ("mean_batch_kernels", C.c_double), ("refits", C.c_int64),
+                ("failed", C.c_int64), ("rejected", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 EXPORTS = ["aiwcrf_fit", "aiwcrf_fit_subsets", "aiwcrf_predict", "aiwcrf_predict_sum", "aiwcrf_oob",
            "aiwcrf_round_mean", "aiwcrf_select_device", "aiwcrf_forest_stats", "aiwcrf_forest_info",
            "aiwcrf_forest_serialize", "aiwcrf_forest_deserialize", "aiwcrf_forest_free",
@@ -61,7 +88,10 @@ EXPORTS = ["aiwcrf_fit", "aiwcrf_fit_subsets", "aiwcrf_predict", "aiwcrf_predict
            "aiwcrf_profile_name", "aiwcrf_profile_num_classes", "aiwcrf_launch_count",
            "aiwcrf_select_device_noalloc", "aiwcrf_tc_gemm_bf16", "aiwcrf_surrogate_fit",
            "aiwcrf_surrogate_predict", "aiwcrf_surrogate_grad", "aiwcrf_surrogate_create", "aiwcrf_surrogate_export",
-           "aiwcrf_surrogate_stats", "aiwcrf_surrogate_num_params", "aiwcrf_surrogate_free"]
+           "aiwcrf_surrogate_stats", "aiwcrf_surrogate_num_params", "aiwcrf_surrogate_free",
+           "aiwcrf_server_create", "aiwcrf_server_submit", "aiwcrf_server_wait", "aiwcrf_server_append",
+           "aiwcrf_server_refit", "aiwcrf_server_pause", "aiwcrf_server_stats", "aiwcrf_server_run_load",
+           "aiwcrf_server_destroy"]
 
 _lib = None
 _lock = threading.Lock()
@@ -110,6 +140,17 @@ def load():
         L.aiwcrf_profile_name.restype = C.c_char_p
         L.aiwcrf_profile_num_classes.restype = C.c_int32
         L.aiwcrf_launch_count.restype = C.c_int64
+        L.aiwcrf_server_create.argtypes = [C.POINTER(ServerParams), C.POINTER(FitParams), _vp, _vp, C.c_int64,
+                                           C.c_int32, _vp, C.c_int32, C.POINTER(_vp)]
+        L.aiwcrf_server_submit.argtypes = [_vp, _vp, C.c_int32, C.c_int32, C.POINTER(C.c_int64)]
+        L.aiwcrf_server_wait.argtypes = [_vp, C.c_int64, C.c_int32, _vp, _vp, C.POINTER(C.c_int64)]
+        L.aiwcrf_server_append.argtypes = [_vp, _vp, _vp, C.c_int64]
+        L.aiwcrf_server_refit.argtypes = [_vp, C.c_int32]
+        L.aiwcrf_server_pause.argtypes = [_vp, C.c_int32]
+        L.aiwcrf_server_stats.argtypes = [_vp, C.POINTER(ServerCounters)]
+        L.aiwcrf_server_run_load.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp, C.c_int64, C.c_double,
+                                             C.c_uint64, C.c_int32, _vp, _vp, _vp, C.POINTER(LoadReport)]
+        L.aiwcrf_server_destroy.argtypes = [_vp]
         for name in EXPORTS:
             if name not in ("aiwcrf_last_error", "aiwcrf_profile_name", "aiwcrf_profile_num_classes",
                             "aiwcrf_launch_count", "aiwcrf_surrogate_num_params"):
@@ -323,6 +364,95 @@ def aiwcrf_select_device_noalloc(forest: Forest, kfeat, size_class: int, device_
     _check(load().aiwcrf_select_device_noalloc(forest.handle, _ptr(kfeat), K, int(size_class), dev.ctypes.data,
                                                int(dev.size), _ptr(out_best), _ptr(out_pred), _stream(stream)))
     return out_best
+
+
+def server_params(n_streams=4, max_request_kernels=64, batch_kernels=1024, max_pending=65536,
+                  arena_bytes=64 << 20, refit_every=0, refit_rows=0) -> ServerParams:
+    return ServerParams(n_streams, max_request_kernels, batch_kernels, max_pending, arena_bytes, refit_every,
+                        refit_rows)
+
+
+class Server:
+    """Device-selection server (include/aiwcrf.h): a resident forest answering requests by
+    continuous batching, with refits from appended rows. Host numpy arrays throughout."""
+
+    def __init__(self, sparams: ServerParams, fparams: FitParams, X: np.ndarray, y: np.ndarray, device_ids):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.int64)
+        self.F, N = X.shape
+        self.device_ids = np.ascontiguousarray(device_ids, dtype=np.int32)
+        self.D = int(self.device_ids.size)
+        h = _vp()
+        _check(load().aiwcrf_server_create(C.byref(sparams), C.byref(fparams), X.ctypes.data, y.ctypes.data, N,
+                                           self.F, self.device_ids.ctypes.data, self.D, C.byref(h)))
+        self.handle = h.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().aiwcrf_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, kfeat: np.ndarray, size_class: int) -> int:
+        kfeat = np.ascontiguousarray(kfeat, dtype=np.float32)
+        t = C.c_int64()
+        _check(load().aiwcrf_server_submit(self.handle, kfeat.ctypes.data, int(kfeat.shape[1]), int(size_class),
+                                           C.byref(t)))
+        self._k = getattr(self, "_k", {})
+        self._k[t.value] = int(kfeat.shape[1])
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """(best[K], pred[K, D], generation)."""
+        K = self._k[ticket]
+        best = np.zeros(K, np.int32)
+        pred = np.zeros((K, self.D), np.int64)
+        g = C.c_int64()
+        _check(load().aiwcrf_server_wait(self.handle, ticket, timeout_ms, best.ctypes.data, pred.ctypes.data,
+                                         C.byref(g)))
+        del self._k[ticket]
+        return best, pred, g.value
+
+    def append(self, X: np.ndarray, y: np.ndarray):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.int64)
+        _check(load().aiwcrf_server_append(self.handle, X.ctypes.data, y.ctypes.data, int(y.size)))
+
+    def refit(self, wait: bool = True):
+        _check(load().aiwcrf_server_refit(self.handle, 1 if wait else 0))
+
+    def pause(self, paused: bool):
+        _check(load().aiwcrf_server_pause(self.handle, 1 if paused else 0))
+
+    def stats(self) -> dict:
+        c = ServerCounters()
+        _check(load().aiwcrf_server_stats(self.handle, C.byref(c)))
+        return c.as_dict()
+
+    def run_load(self, pool: np.ndarray, first, n_kernels, size_class, rate_per_s: float, seed: int = 1,
+                 timeout_ms: int = 120000):
+        """Open-loop Poisson load. Returns (report dict, best[sum K], generation[n], latency_ns[n])."""
+        pool = np.ascontiguousarray(pool, dtype=np.float32)
+        first = np.ascontiguousarray(first, dtype=np.int64)
+        nk = np.ascontiguousarray(n_kernels, dtype=np.int32)
+        sc = np.ascontiguousarray(size_class, dtype=np.int32)
+        n = int(first.size)
+        best = np.full(int(nk.sum()), -1, np.int32)
+        gen = np.full(n, -1, np.int64)
+        lat = np.full(n, -1, np.int64)
+        rep = LoadReport()
+        _check(load().aiwcrf_server_run_load(self.handle, pool.ctypes.data, int(pool.shape[1]), first.ctypes.data,
+                                             nk.ctypes.data, sc.ctypes.data, n, float(rate_per_s), seed, timeout_ms,
+                                             best.ctypes.data, gen.ctypes.data, lat.ctypes.data, C.byref(rep)))
+        return rep.as_dict(), best, gen, lat
 
 
 def aiwcrf_forest_deserialize(blob: bytes) -> Forest:

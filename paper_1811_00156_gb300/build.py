@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libaiwcrf.so")
-SOURCES = ["fit.cu", "sort.cu", "predict.cu", "api.cu", "noalloc.cu", "mlp.cu", "surrogate.cu"]
+SOURCES = ["fit.cu", "sort.cu", "predict.cu", "api.cu", "noalloc.cu", "mlp.cu", "surrogate.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -58,7 +58,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
                 raise RuntimeError(f"nvcc failed: {' '.join(cmd)}")
     if force or jobs or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
+        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             sys.stderr.write(res.stdout + res.stderr)

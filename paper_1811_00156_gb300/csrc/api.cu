@@ -34,11 +34,21 @@ int cuda_fail(cudaError_t e, const char *what)
 void forest_release(aiwcrf_forest *f)
 {
     if (!f) return;
-    cudaFree(f->d_block);
+    // callers may still have work reading the forest in flight on any stream
+    cudaDeviceSynchronize();
+    if (f->d_block) cudaFreeAsync(f->d_block, cudaStreamPerThread);
+    cudaStreamSynchronize(cudaStreamPerThread);
     delete f;
 }
 
-cudaError_t forest_alloc(aiwcrf_forest *f)
+void forest_release_async(aiwcrf_forest *f, cudaStream_t s)
+{
+    if (!f) return;
+    if (f->d_block) cudaFreeAsync(f->d_block, s);
+    delete f;
+}
+
+cudaError_t forest_alloc(aiwcrf_forest *f, cudaStream_t s)
 {
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     // compact layout: trees padded to a multiple of four nodes
@@ -58,7 +68,9 @@ cudaError_t forest_alloc(aiwcrf_forest *f)
     const size_t b_c32 = f->compact ? up(4 * (size_t)f->num_c32) + b_off : 0;
     const size_t b_inbag = up(4 * (size_t)f->T * (size_t)f->inbag_words);
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, 2 * b_nodes + b_off + b_vals + b_card + b_c32 + b_inbag);
+    keep_pool_memory(f->device);
+    // stream-ordered, so that freeing a forest never waits for the whole device
+    cudaError_t e = cudaMallocAsync(&p, 2 * b_nodes + b_off + b_vals + b_card + b_c32 + b_inbag, s);
     if (e != cudaSuccess) return e;
     unsigned char *c = static_cast<unsigned char *>(p);
     f->d_block = p;
@@ -72,7 +84,7 @@ cudaError_t forest_alloc(aiwcrf_forest *f)
         unsigned char *q = c + 2 * b_nodes + b_off + b_vals + b_card;
         f->d_tree_off4 = reinterpret_cast<int64_t *>(q);
         f->d_c32 = reinterpret_cast<uint32_t *>(q + b_off);
-        e = cudaMemcpy(f->d_tree_off4, off4.data(), 8 * (size_t)(f->T + 1), cudaMemcpyHostToDevice);
+        e = cudaMemcpyAsync(f->d_tree_off4, off4.data(), 8 * (size_t)(f->T + 1), cudaMemcpyHostToDevice, s);
     }
     return e;
 }
@@ -597,17 +609,20 @@ int aiwcrf_forest_deserialize(const void *buf, size_t len, aiwcrf_forest **out)
     f->tree_off = off;
     f->max_card = max_card;
     f->fstride = fstride;
-    cudaError_t e = forest_alloc(f);
-    if (e == cudaSuccess) e = cudaMemcpy(f->d_nodes, nodes, 8 * (size_t)nn, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(f->d_cnodes, cnodes.data(), 8 * (size_t)nn, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(f->d_tree_off, off.data(), 8 * (size_t)(T + 1), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(f->d_fvals, fv.data(), sizeof(float) * fv.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(f->d_fcard, fc.data(), sizeof(uint32_t) * fc.size(), cudaMemcpyHostToDevice);
+    const cudaStream_t st = cudaStreamPerThread;
+    const cudaMemcpyKind h2d = cudaMemcpyHostToDevice;
+    cudaError_t e = forest_alloc(f, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f->d_nodes, nodes, 8 * (size_t)nn, h2d, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f->d_cnodes, cnodes.data(), 8 * (size_t)nn, h2d, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f->d_tree_off, off.data(), 8 * (size_t)(T + 1), h2d, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f->d_fvals, fv.data(), sizeof(float) * fv.size(), h2d, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f->d_fcard, fc.data(), sizeof(uint32_t) * fc.size(), h2d, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         forest_release(f);
         return cuda_fail(e, "uploading forest");
     }
-    if ((rc = forest_build_compact(f, nullptr)) != AIWCRF_OK || (rc = (cudaDeviceSynchronize() == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "compact nodes"))) != AIWCRF_OK) {
+    if ((rc = forest_build_compact(f, st)) != AIWCRF_OK || (rc = (cudaStreamSynchronize(st) == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "compact nodes"))) != AIWCRF_OK) {
         forest_release(f);
         return rc;
     }

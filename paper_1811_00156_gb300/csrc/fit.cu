@@ -1428,7 +1428,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         fr->max_card = max_card;
         fr->fstride = std::max<int64_t>(max_card, 1);
         if (d_inbag) { fr->oob_rows = N; fr->inbag_words = inbag_words; }
-        AIWCRF_CUDA(forest_alloc(fr));
+        AIWCRF_CUDA(forest_alloc(fr, s));
         if (d_inbag)
             AIWCRF_CUDA(cudaMemcpyAsync(fr->d_inbag, d_inbag + (size_t)g * (size_t)Tper * (size_t)inbag_words,
                                         sizeof(uint32_t) * (size_t)Tper * (size_t)inbag_words, cudaMemcpyDeviceToDevice, s));

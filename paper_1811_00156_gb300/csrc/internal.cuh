@@ -373,10 +373,14 @@ struct aiwcrf_forest {
 };
 
 namespace aiwcrf {
+// frees a forest once every stream of the device is idle
 void forest_release(aiwcrf_forest *f);
-// one device allocation for the forest's arrays (nodes, coded nodes, tree offsets, value tables,
-// compact nodes); sets the compact layout's host fields from tree_off and max_card
-cudaError_t forest_alloc(aiwcrf_forest *f);
+// frees a forest in stream order on s; the caller has seen all work reading it complete
+void forest_release_async(aiwcrf_forest *f, cudaStream_t s);
+// one stream-ordered device allocation on s for the forest's arrays (nodes, coded nodes, tree
+// offsets, value tables, compact nodes); sets the compact layout's host fields from tree_off
+// and max_card
+cudaError_t forest_alloc(aiwcrf_forest *f, cudaStream_t s);
 // fills the compact 4-byte node array from d_cnodes (after d_cnodes and d_tree_off are written)
 int forest_build_compact(aiwcrf_forest *f, cudaStream_t s);
 // keep freed stream-ordered allocations cached in the device's default pool (once per device)
@@ -392,6 +396,10 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
               cudaStream_t s, std::vector<aiwcrf_forest *> &out);
 int tc_gemm(const __nv_bfloat16 *A, int lda, bool a_trans, const __nv_bfloat16 *B, int ldb, bool b_trans, float *C,
             int M, int N, int K, int ksplit, float *part, uint32_t *d_err, cudaStream_t s);
+// predict without allocating or synchronising: codes_scratch holds predict_codes_bytes(f, Q)
+size_t predict_codes_bytes(const aiwcrf_forest *f, int64_t Q);
+int predict_enqueue(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum, int64_t *d_pred,
+                    cudaStream_t s, uint32_t *d_err, void *codes_scratch);
 int oob_launch(const aiwcrf_forest *f, const float *dX, int64_t N, int64_t *d_sum, int32_t *d_count, cudaStream_t s);
 int predict_launch(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum,
                    int64_t *d_pred, uint64_t *d_var, int64_t total_trees, cudaStream_t s);

@@ -473,7 +473,7 @@ constexpr int kQPT = 4;
 
 template <typename CT, bool VAR>
 int launch_predict(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum, int64_t *d_pred,
-                   uint64_t *d_var, int64_t total_trees, cudaStream_t s, uint32_t *d_err)
+                   uint64_t *d_var, int64_t total_trees, cudaStream_t s, uint32_t *d_err, void *codes_scratch)
 {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
@@ -481,10 +481,11 @@ int launch_predict(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t 
     int ld_words = (int)((f->F * (int)sizeof(CT) + 3) / 4);
     if ((ld_words & 1) == 0) ++ld_words;                       // odd: conflict-free rows
     const int ld = ld_words * 4 / (int)sizeof(CT);
-    CT *d_codes = nullptr;
-    cudaError_t e = cudaMallocAsync(&d_codes, (size_t)Q * (size_t)ld_words * 4, s);
-    if (e != cudaSuccess) return fail(AIWCRF_E_OOM, "device allocation of the query codes failed");
-    struct Free { CT *p; cudaStream_t s; ~Free() { cudaFreeAsync(p, s); } } fr{d_codes, s};
+    CT *d_codes = static_cast<CT *>(codes_scratch);
+    cudaError_t e = cudaSuccess;
+    if (!d_codes && cudaMallocAsync(&d_codes, (size_t)Q * (size_t)ld_words * 4, s) != cudaSuccess)
+        return fail(AIWCRF_E_OOM, "device allocation of the query codes failed");
+    struct Free { CT *p; cudaStream_t s; ~Free() { if (p) cudaFreeAsync(p, s); } } fr{codes_scratch ? nullptr : d_codes, s};
     code_queries_kernel<CT><<<dim3((unsigned)((Q + 255) / 256), (unsigned)f->F), 256, 0, s>>>(
         dXq, Q, f->F, f->d_fvals, f->fstride, f->d_fcard, d_codes, ld);
     count_launches(1);
@@ -509,17 +510,18 @@ int launch_predict(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t 
 
 template <bool VAR>
 int launch_predict4(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum, int64_t *d_pred,
-                    uint64_t *d_var, int64_t total_trees, cudaStream_t s, uint32_t *d_err)
+                    uint64_t *d_var, int64_t total_trees, cudaStream_t s, uint32_t *d_err, void *codes_scratch)
 {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     int ld_words = (f->F + 3) / 4;
     if ((ld_words & 1) == 0) ++ld_words;                       // odd: conflict-free rows
-    uint8_t *d_codes = nullptr;
-    cudaError_t e = cudaMallocAsync(&d_codes, (size_t)Q * (size_t)ld_words * 4, s);
-    if (e != cudaSuccess) return fail(AIWCRF_E_OOM, "device allocation of the query codes failed");
-    struct Free { uint8_t *p; cudaStream_t s; ~Free() { cudaFreeAsync(p, s); } } fr{d_codes, s};
+    uint8_t *d_codes = static_cast<uint8_t *>(codes_scratch);
+    cudaError_t e = cudaSuccess;
+    if (!d_codes && cudaMallocAsync(&d_codes, (size_t)Q * (size_t)ld_words * 4, s) != cudaSuccess)
+        return fail(AIWCRF_E_OOM, "device allocation of the query codes failed");
+    struct Free { uint8_t *p; cudaStream_t s; ~Free() { if (p) cudaFreeAsync(p, s); } } fr{codes_scratch ? nullptr : d_codes, s};
     code_queries_kernel<uint8_t><<<dim3((unsigned)((Q + 255) / 256), (unsigned)f->F), 256, 0, s>>>(
         dXq, Q, f->F, f->d_fvals, f->fstride, f->d_fcard, d_codes, ld_words * 4);
     count_launches(1);
@@ -545,16 +547,33 @@ int launch_predict4(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t
 
 template <typename CT>
 int launch_predict_ct(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum, int64_t *d_pred,
-                      uint64_t *d_var, int64_t total_trees, cudaStream_t s, uint32_t *d_err)
+                      uint64_t *d_var, int64_t total_trees, cudaStream_t s, uint32_t *d_err, void *scratch = nullptr)
 {
     if (f->compact)
-        return d_var ? launch_predict4<true>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err)
-                     : launch_predict4<false>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err);
-    return d_var ? launch_predict<CT, true>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err)
-                 : launch_predict<CT, false>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err);
+        return d_var ? launch_predict4<true>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err, scratch)
+                     : launch_predict4<false>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err, scratch);
+    return d_var ? launch_predict<CT, true>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err, scratch)
+                 : launch_predict<CT, false>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err, scratch);
 }
 
 }  // namespace
+
+size_t predict_codes_bytes(const aiwcrf_forest *f, int64_t Q)
+{
+    const int cb = f->max_card <= 255u ? 1 : (f->max_card <= 65535u ? 2 : 4);
+    int ld_words = (f->F * cb + 3) / 4;
+    if ((ld_words & 1) == 0) ++ld_words;
+    return (size_t)Q * (size_t)ld_words * 4;
+}
+
+int predict_enqueue(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum, int64_t *d_pred,
+                    cudaStream_t s, uint32_t *d_err, void *codes_scratch)
+{
+    if (Q == 0) return AIWCRF_OK;
+    if (f->max_card <= 255u) return launch_predict_ct<uint8_t>(f, dXq, Q, d_sum, d_pred, nullptr, f->T, s, d_err, codes_scratch);
+    if (f->max_card <= 65535u) return launch_predict_ct<uint16_t>(f, dXq, Q, d_sum, d_pred, nullptr, f->T, s, d_err, codes_scratch);
+    return launch_predict_ct<uint32_t>(f, dXq, Q, d_sum, d_pred, nullptr, f->T, s, d_err, codes_scratch);
+}
 
 int predict_launch(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum, int64_t *d_pred,
                    uint64_t *d_var, int64_t total_trees, cudaStream_t s)

@@ -1,0 +1,1032 @@
+// serve.cu -- the device-selection server: the scheduler of Sec. VI (pick the fastest device
+// for each kernel about to run) as a resident service, with the retraining of Sec. I (refit
+// when the training data changes) running beside it.
+//
+// Runtime (host C++):
+//  - a dispatcher thread owns n_streams stream slots. It forms a batch from the pending
+//    requests in arrival order whenever a slot is free (continuous batching: whatever arrived
+//    while the other slots were busy goes into the next batch), stages the batch's features in
+//    the slot's pinned buffer, and enqueues copy in, one selection kernel, copy out and an
+//    event. It polls the events and completes the requests of finished batches;
+//  - every batch's device inputs and outputs come from a first-fit arena carved out of one
+//    allocation: a request is admitted into a batch only while its bytes fit the arena's free
+//    space, so the server's device footprint is fixed at creation;
+//  - a refit thread fits new forests from the training rows plus appended rows on its own
+//    stream and swaps them in; each batch holds a reference to the forest it was formed with,
+//    and a forest is freed (stream-ordered) only after the last batch using it completed.
+//
+// Selection kernel (serve_select_kernel): one warp per (query, group of 64 trees), a query
+// being one (kernel, device) pair. The warp's lanes first code the query's features as ranks
+// in the forest's value tables (c(x) = #{training values < x}; NaN past every value), then each
+// lane walks two trees, and the warp's exact int64 leaf sum is added atomically to the query's
+// sum. The warp that completes a kernel's last query group (a per-kernel counter) rounds the
+// kernel's sums to predictions, takes the argmin over devices (ties to the lower device id)
+// and resets the sums and the counter for the slot's next batch. Integer sums make the result
+// independent of the order in which warps finish: a request gets the same answer alone or
+// batched with any others.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace aiwcrf {
+
+struct ServeForest {
+    const uint32_t *c32;
+    const int64_t *tree_off4;
+    const uint64_t *nodes;
+    const uint64_t *cnodes;
+    const int64_t *tree_off;
+    const float *fvals;
+    const uint32_t *fcard;
+    int64_t fstride;
+    int T;
+    int F;
+};
+
+constexpr int kServeThreads = 256;
+constexpr int kServeWarps = kServeThreads / 32;
+constexpr int kTreesPerWarp = 64;
+constexpr int kServeMaxDevices = 64;
+
+__device__ __forceinline__ int64_t serve_leaf(uint64_t nd)
+{
+    return ((int64_t)(nd << 1)) >> 1;
+}
+
+// Two independent walks (trees t0, t1; -1 = none) with the query's codes in shared memory.
+template <bool COMPACT>
+__device__ __forceinline__ int64_t serve_walk2(const ServeForest &sf, int t0, int t1, const uint32_t *code)
+{
+    int64_t v = 0;
+    if (COMPACT) {
+        const uint32_t *n0 = sf.c32 + (t0 >= 0 ? sf.tree_off4[t0] : 0);
+        const uint32_t *n1 = sf.c32 + (t1 >= 0 ? sf.tree_off4[t1] : 0);
+        uint32_t j0 = 0, j1 = 0;
+        bool l0 = t0 < 0, l1 = t1 < 0;
+        while (!(l0 && l1)) {
+            const uint32_t a = __ldg(n0 + j0), b = __ldg(n1 + j1);
+            const bool la = l0 || (int32_t)a < 0, lb = l1 || (int32_t)b < 0;
+            const uint32_t ca = code[la ? 0u : (a >> 24)], cb = code[lb ? 0u : (b >> 24)];
+            j0 = la ? j0 : (a & 0xFFFFu) + (ca > ((a >> 16) & 0xFFu) ? 1u : 0u);
+            j1 = lb ? j1 : (b & 0xFFFFu) + (cb > ((b >> 16) & 0xFFu) ? 1u : 0u);
+            l0 = la;
+            l1 = lb;
+        }
+        if (t0 >= 0) v += serve_leaf(__ldg(sf.nodes + sf.tree_off[t0] + j0));
+        if (t1 >= 0) v += serve_leaf(__ldg(sf.nodes + sf.tree_off[t1] + j1));
+    } else {
+        const uint64_t *n0 = sf.cnodes + (t0 >= 0 ? sf.tree_off[t0] : 0);
+        const uint64_t *n1 = sf.cnodes + (t1 >= 0 ? sf.tree_off[t1] : 0);
+        uint32_t j0 = 0, j1 = 0;
+        bool l0 = t0 < 0, l1 = t1 < 0;
+        uint64_t a = 0, b = 0;
+        while (!(l0 && l1)) {
+            a = __ldg(n0 + j0);
+            b = __ldg(n1 + j1);
+            const bool la = l0 || (a >> 63), lb = l1 || (b >> 63);
+            const uint32_t ca = code[la ? 0u : (uint32_t)(a >> 56) & 0x7Fu];
+            const uint32_t cb = code[lb ? 0u : (uint32_t)(b >> 56) & 0x7Fu];
+            j0 = la ? j0 : ((uint32_t)(a >> 32) & 0xFFFFFFu) + (ca > ((uint32_t)a & 0xFFFFFFu) ? 1u : 0u);
+            j1 = lb ? j1 : ((uint32_t)(b >> 32) & 0xFFFFFFu) + (cb > ((uint32_t)b & 0xFFFFFFu) ? 1u : 0u);
+            l0 = la;
+            l1 = lb;
+        }
+        if (t0 >= 0) v += serve_leaf(__ldg(n0 + j0));
+        if (t1 >= 0) v += serve_leaf(__ldg(n1 + j1));
+    }
+    return v;
+}
+
+// kq: F x Kb column-major batch features (row F-2 unused: the device id comes from dev[]; row
+// F-1 the size class). sums (Kb * D) and cnt (Kb) are zero on entry and left zero.
+// pred: Kb x D row-major predictions; best: Kb device ids.
+template <bool COMPACT>
+__global__ void __launch_bounds__(kServeThreads) serve_select_kernel(ServeForest sf, const float *__restrict__ kq,
+                                                                     int Kb, const int32_t *__restrict__ dev, int D,
+                                                                     int G, unsigned long long *sums, uint32_t *cnt,
+                                                                     int64_t *pred, int32_t *best)
+{
+    __shared__ uint32_t code[kServeWarps][AIWCRF_MAX_FEATURES];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t Qn = (int64_t)Kb * D;
+    const int64_t w = (int64_t)blockIdx.x * kServeWarps + warp;
+    const int64_t q = w / G;
+    const int g = (int)(w % G);
+    if (q >= Qn) return;                       // warp-uniform
+    const int k = (int)(q / D), jd = (int)(q % D);
+    for (int f = lane; f < sf.F; f += 32) {
+        const float x = (f == sf.F - 2) ? (float)dev[jd] : kq[(size_t)f * (size_t)Kb + (size_t)k];
+        const float *V = sf.fvals + (size_t)f * (size_t)sf.fstride;
+        uint32_t lo = 0, hi = sf.fcard[f];
+        if (x != x) {
+            lo = hi;
+        } else {
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (__ldg(&V[mid]) < x) lo = mid + 1;
+                else hi = mid;
+            }
+        }
+        code[warp][f] = lo;
+    }
+    __syncwarp();
+    const int t0 = g * kTreesPerWarp + lane, t1 = t0 + 32;
+    int64_t v = serve_walk2<COMPACT>(sf, t0 < sf.T ? t0 : -1, t1 < sf.T ? t1 : -1, code[warp]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    uint32_t prev = 0;
+    if (lane == 0) {
+        atomicAdd(&sums[q], (unsigned long long)v);
+        __threadfence();
+        prev = atomicAdd(&cnt[k], 1u);
+    }
+    prev = __shfl_sync(0xFFFFFFFFu, prev, 0);
+    if (prev != (uint32_t)(D * G) - 1u) return;  // warp-uniform
+    // this warp finishes kernel k: every group of every device has added its sum
+    __threadfence();
+    int64_t bp = LLONG_MAX;
+    int32_t bd = INT_MAX;
+    for (int j = lane; j < D; j += 32) {
+        const int64_t s = (int64_t)atomicExch(&sums[(size_t)k * (size_t)D + (size_t)j], 0ull);
+        const i128_t num = (i128_t)2 * s + sf.T, den = (i128_t)2 * sf.T;
+        i128_t d = num / den;
+        if (num % den != 0 && num < 0) d -= 1;
+        const int64_t p = (int64_t)d;
+        pred[(size_t)k * (size_t)D + (size_t)j] = p;
+        const int32_t id = dev[j];
+        if (p < bp || (p == bp && id < bd)) { bp = p; bd = id; }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const int64_t op = __shfl_xor_sync(0xFFFFFFFFu, bp, o);
+        const int32_t od = __shfl_xor_sync(0xFFFFFFFFu, bd, o);
+        if (op < bp || (op == bp && od < bd)) { bp = op; bd = od; }
+    }
+    if (lane == 0) {
+        best[k] = bd;
+        cnt[k] = 0u;
+    }
+}
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+int64_t now_ns()
+{
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now().time_since_epoch()).count();
+}
+
+size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int serve_launch(const aiwcrf_forest *f, const float *d_kq, int Kb, const int32_t *d_dev, int D,
+                 unsigned long long *d_sum, uint32_t *d_cnt, int64_t *d_pred, int32_t *d_best, cudaStream_t s)
+{
+    ServeForest sf;
+    sf.c32 = f->d_c32;
+    sf.tree_off4 = f->d_tree_off4;
+    sf.nodes = f->d_nodes;
+    sf.cnodes = f->d_cnodes;
+    sf.tree_off = f->d_tree_off;
+    sf.fvals = f->d_fvals;
+    sf.fcard = f->d_fcard;
+    sf.fstride = f->fstride;
+    sf.T = (int)f->T;
+    sf.F = f->F;
+    const int G = (int)((f->T + kTreesPerWarp - 1) / kTreesPerWarp);
+    const int64_t warps = (int64_t)Kb * D * G;
+    const unsigned grid = (unsigned)((warps + kServeWarps - 1) / kServeWarps);
+    if (f->compact)
+        serve_select_kernel<true><<<grid, kServeThreads, 0, s>>>(sf, d_kq, Kb, d_dev, D, G, d_sum, d_cnt, d_pred, d_best);
+    else
+        serve_select_kernel<false><<<grid, kServeThreads, 0, s>>>(sf, d_kq, Kb, d_dev, D, G, d_sum, d_cnt, d_pred, d_best);
+    count_launches(1);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "serve_select_kernel launch");
+    return AIWCRF_OK;
+}
+
+// First-fit allocator over [0, cap) in 256-byte granules; free neighbours merge.
+struct Arena {
+    int64_t cap = 0, used = 0, peak = 0;
+    std::map<int64_t, int64_t> free_;    // offset -> bytes
+
+    void init(int64_t c)
+    {
+        cap = c;
+        used = peak = 0;
+        free_.clear();
+        if (c > 0) free_[0] = c;
+    }
+    int64_t largest() const
+    {
+        int64_t m = 0;
+        for (auto &kv : free_) m = std::max(m, kv.second);
+        return m;
+    }
+    int64_t alloc(int64_t bytes)
+    {
+        bytes = (int64_t)up256((size_t)bytes);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < bytes) continue;
+            const int64_t off = it->first, rest = it->second - bytes;
+            free_.erase(it);
+            if (rest) free_[off + bytes] = rest;
+            used += bytes;
+            peak = std::max(peak, used);
+            return off;
+        }
+        return -1;
+    }
+    void release(int64_t off, int64_t bytes)
+    {
+        bytes = (int64_t)up256((size_t)bytes);
+        used -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+struct LoadRun {
+    std::mutex mu;
+    std::condition_variable cv;
+    bool abandoned = false;
+    int64_t remaining = 0;
+    int first_error = AIWCRF_OK;
+    int32_t *best = nullptr;              // caller's, may be null
+    int64_t *gen = nullptr;               // caller's, may be null
+    std::vector<int64_t> lat;             // -1: not served
+};
+
+struct Request {
+    int64_t ticket = -1;
+    int32_t K = 0, size = 0;
+    const float *src = nullptr;           // feature (f, k) at src[f * ld + k]
+    int64_t ld = 0;
+    std::vector<float> own;
+    int64_t t_arrive = 0;
+    // completion of a submitted request
+    bool done = false;
+    int32_t status = AIWCRF_OK;
+    std::string msg;
+    int64_t generation = -1;
+    std::vector<int32_t> best;
+    std::vector<int64_t> pred;
+    // load-generator request
+    std::shared_ptr<LoadRun> run;
+    int64_t run_index = 0, run_best_off = 0;
+};
+
+struct Model {
+    aiwcrf_forest *f = nullptr;
+    int64_t gen = 0;
+    int64_t rows = 0;
+    int64_t bytes = 0;
+};
+
+struct Slot {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    float *h_in = nullptr;                // pinned F x batch_kernels
+    unsigned char *h_out = nullptr;       // pinned batch_kernels x (8 D + 4)
+    unsigned long long *d_sum = nullptr;  // batch_kernels x D, kept zero between batches
+    uint32_t *d_cnt = nullptr;            // batch_kernels, kept zero between batches
+    bool busy = false;
+    int64_t off = -1, bytes = 0;
+    int32_t Kb = 0;
+    std::shared_ptr<Model> model;
+    std::vector<std::shared_ptr<Request>> reqs;
+};
+
+struct SplitMix64 {
+    uint64_t x;
+    uint64_t next()
+    {
+        uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+};
+
+}  // namespace
+}  // namespace aiwcrf
+
+using namespace aiwcrf;
+
+struct aiwcrf_server {
+    aiwcrf_server_params sp{};
+    aiwcrf_fit_params fp{};
+    int32_t F = 0, D = 0;
+    int device = 0;
+    std::vector<int32_t> dev_ids;
+    int32_t *d_dev = nullptr;
+    unsigned char *d_arena = nullptr;
+    Arena arena;
+    std::vector<Slot> slots;
+
+    std::mutex mu;                        // queue, tickets, arena, current model, counters
+    std::condition_variable cv_disp, cv_done;
+    std::deque<std::shared_ptr<Request>> pending;
+    std::unordered_map<int64_t, std::shared_ptr<Request>> tickets;
+    int64_t next_ticket = 1;
+    bool stop = false, paused = false;
+    std::shared_ptr<Model> current;
+    aiwcrf_server_counters st{};
+    int64_t refit_mark = 0;
+
+    std::mutex rmu;                       // training rows and refit requests
+    std::condition_variable rcv, rcv_done;
+    bool refit_req = false, refit_stop = false, refit_running = false;
+    std::string last_refit_msg;
+    int64_t refits_finished = 0;
+    int last_refit_status = AIWCRF_OK;
+    std::vector<std::vector<float>> xcols, acols;   // training / appended rows, per feature
+    std::vector<int64_t> ytrain, yapp;
+    cudaStream_t refit_stream = nullptr;
+
+    std::mutex gmu;                       // forests waiting to be freed
+    std::vector<aiwcrf_forest *> graveyard;
+    cudaStream_t free_stream = nullptr;
+
+    std::thread disp, refitter;
+
+    int64_t req_bytes(int64_t K) const
+    {
+        return (int64_t)(up256(sizeof(float) * (size_t)F * (size_t)K) +
+                         up256((size_t)K * ((size_t)D * 8 + 4)));
+    }
+
+    std::shared_ptr<Model> wrap(aiwcrf_forest *f, int64_t gen, int64_t rows)
+    {
+        Model *m = new Model();
+        m->f = f;
+        m->gen = gen;
+        m->rows = rows;
+        m->bytes = 16 * f->num_nodes + 4 * f->num_c32 + 16 * (f->T + 1) + 4 * (int64_t)f->F * f->fstride +
+                   4 * f->T * f->inbag_words;
+        return std::shared_ptr<Model>(m, [this](Model *p) {
+            {
+                std::lock_guard<std::mutex> lk(gmu);
+                graveyard.push_back(p->f);
+            }
+            delete p;
+        });
+    }
+
+    void drain_graveyard()
+    {
+        std::vector<aiwcrf_forest *> g;
+        {
+            std::lock_guard<std::mutex> lk(gmu);
+            g.swap(graveyard);
+        }
+        for (auto f : g) forest_release_async(f, free_stream);
+    }
+
+    // fit a forest on the current training rows (refit thread or creation)
+    int fit_training(aiwcrf_forest **out, int64_t *rows)
+    {
+        const int64_t N = (int64_t)ytrain.size();
+        std::vector<float> X((size_t)F * (size_t)N);
+        for (int32_t f = 0; f < F; ++f) std::copy(xcols[(size_t)f].begin(), xcols[(size_t)f].end(), X.begin() + (size_t)f * (size_t)N);
+        float *dX = nullptr;
+        int64_t *dy = nullptr;
+        cudaError_t e = cudaMallocAsync(&dX, sizeof(float) * X.size(), refit_stream);
+        if (e == cudaSuccess) e = cudaMallocAsync(&dy, sizeof(int64_t) * (size_t)N, refit_stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dX, X.data(), sizeof(float) * X.size(), cudaMemcpyHostToDevice, refit_stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dy, ytrain.data(), sizeof(int64_t) * (size_t)N, cudaMemcpyHostToDevice, refit_stream);
+        int rc = e == cudaSuccess ? AIWCRF_OK : cuda_fail(e, "staging the training rows");
+        if (rc == AIWCRF_OK) rc = aiwcrf_fit(&fp, dX, dy, N, F, refit_stream, out);
+        if (dX) cudaFreeAsync(dX, refit_stream);
+        if (dy) cudaFreeAsync(dy, refit_stream);
+        cudaStreamSynchronize(refit_stream);
+        *rows = N;
+        return rc;
+    }
+
+    void finish(const std::shared_ptr<Request> &r, int status, const std::string &msg, int64_t gen,
+                const int32_t *best, const int64_t *pred, int64_t t_done)
+    {
+        if (r->run) {
+            LoadRun &run = *r->run;
+            std::lock_guard<std::mutex> lk(run.mu);
+            if (!run.abandoned) {
+                if (status == AIWCRF_OK) {
+                    if (run.best && best) std::memcpy(run.best + r->run_best_off, best, sizeof(int32_t) * (size_t)r->K);
+                    if (run.gen) run.gen[r->run_index] = gen;
+                    run.lat[(size_t)r->run_index] = t_done - r->t_arrive;
+                } else if (run.first_error == AIWCRF_OK) {
+                    run.first_error = status;
+                }
+            }
+            --run.remaining;
+            run.cv.notify_all();
+            return;
+        }
+        std::lock_guard<std::mutex> lk(mu);
+        r->status = status;
+        r->msg = msg;
+        r->generation = gen;
+        if (status == AIWCRF_OK) {
+            r->best.assign(best, best + r->K);
+            r->pred.assign(pred, pred + (size_t)r->K * (size_t)D);
+        }
+        r->done = true;
+        cv_done.notify_all();
+    }
+
+    void complete(Slot &sl, cudaError_t e)
+    {
+        const int64_t t = now_ns();
+        const int status = e == cudaSuccess ? AIWCRF_OK : AIWCRF_E_CUDA;
+        const std::string msg = e == cudaSuccess ? std::string() : std::string("selection batch: ") + cudaGetErrorString(e);
+        const int64_t *hp = reinterpret_cast<const int64_t *>(sl.h_out);
+        const int32_t *hb = reinterpret_cast<const int32_t *>(sl.h_out + (size_t)sl.Kb * (size_t)D * 8);
+        int64_t off = 0;
+        const int64_t gen = sl.model ? sl.model->gen : -1;
+        for (auto &r : sl.reqs) {
+            finish(r, status, msg, gen, hb + off, hp + off * D, t);
+            off += r->K;
+        }
+        bool want_refit = false;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            arena.release(sl.off, sl.bytes);
+            st.completed += (int64_t)sl.reqs.size();
+            if (status != AIWCRF_OK) st.failed += (int64_t)sl.reqs.size();
+            if (sp.refit_every > 0 && st.completed - refit_mark >= sp.refit_every) {
+                refit_mark = st.completed;
+                want_refit = true;
+            }
+        }
+        sl.busy = false;
+        sl.off = -1;
+        sl.reqs.clear();
+        sl.model.reset();
+        if (want_refit) {
+            std::lock_guard<std::mutex> lk(rmu);
+            refit_req = true;
+            rcv.notify_all();
+        }
+    }
+
+    // Takes the batch (popped under mu, features staged in sl.h_in) to the GPU.
+    void launch(Slot &sl)
+    {
+        const size_t in_bytes = sizeof(float) * (size_t)F * (size_t)sl.Kb;
+        unsigned char *base = d_arena + sl.off;
+        float *d_in = reinterpret_cast<float *>(base);
+        int64_t *d_pred = reinterpret_cast<int64_t *>(base + up256(in_bytes));
+        int32_t *d_best = reinterpret_cast<int32_t *>(d_pred + (size_t)sl.Kb * (size_t)D);
+        const size_t out_bytes = (size_t)sl.Kb * ((size_t)D * 8 + 4);
+        cudaError_t e = cudaMemcpyAsync(d_in, sl.h_in, in_bytes, cudaMemcpyHostToDevice, sl.s);
+        if (e == cudaSuccess &&
+            serve_launch(sl.model->f, d_in, sl.Kb, d_dev, D, sl.d_sum, sl.d_cnt, d_pred, d_best, sl.s) != AIWCRF_OK)
+            e = cudaErrorLaunchFailure;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_out, d_pred, out_bytes, cudaMemcpyDeviceToHost, sl.s);
+        if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.s);
+        sl.busy = true;
+        if (e != cudaSuccess) {
+            cudaStreamSynchronize(sl.s);
+            complete(sl, e);
+        }
+    }
+
+    void dispatcher()
+    {
+        cudaSetDevice(device);
+        for (;;) {
+            bool progressed = false;
+            bool any_busy = false;
+            for (auto &sl : slots) {
+                if (!sl.busy) continue;
+                const cudaError_t e = cudaEventQuery(sl.ev);
+                if (e == cudaErrorNotReady) { any_busy = true; continue; }
+                complete(sl, e);
+                progressed = true;
+            }
+            drain_graveyard();
+            Slot *free_slot = nullptr;
+            for (auto &sl : slots)
+                if (!sl.busy) { free_slot = &sl; break; }
+
+            std::unique_lock<std::mutex> lk(mu);
+            if (stop) {
+                std::deque<std::shared_ptr<Request>> drop;
+                drop.swap(pending);
+                lk.unlock();
+                for (auto &r : drop) finish(r, AIWCRF_E_INVALID_ARG, "server shut down", -1, nullptr, nullptr, now_ns());
+                if (!any_busy) {
+                    bool busy = false;
+                    for (auto &sl : slots) busy |= sl.busy;
+                    if (!busy) break;
+                }
+                std::this_thread::yield();
+                continue;
+            }
+            if (free_slot && !paused && !pending.empty()) {
+                // form a batch: arrival order, within the batch size and the arena's free space
+                const int64_t room = arena.largest();
+                int64_t Kb = 0;
+                size_t n = 0;
+                bool cut = false;
+                while (n < pending.size()) {
+                    const int64_t K2 = Kb + pending[n]->K;
+                    if (K2 > sp.batch_kernels) break;
+                    if (req_bytes(K2) > room) { cut = true; break; }
+                    Kb = K2;
+                    ++n;
+                }
+                if (n > 0) {
+                    if (cut) ++st.arena_waits;
+                    Slot &sl = *free_slot;
+                    sl.Kb = (int32_t)Kb;
+                    sl.bytes = req_bytes(Kb);
+                    sl.off = arena.alloc(sl.bytes);
+                    sl.reqs.assign(pending.begin(), pending.begin() + (std::ptrdiff_t)n);
+                    pending.erase(pending.begin(), pending.begin() + (std::ptrdiff_t)n);
+                    sl.model = current;
+                    ++st.batches;
+                    st.batch_kernels_total += Kb;
+                    st.batch_kernels_max = std::max(st.batch_kernels_max, Kb);
+                    st.arena_peak_bytes = std::max(st.arena_peak_bytes, arena.peak);
+                    // stage features while the requests' sources are guaranteed alive
+                    int64_t k0 = 0;
+                    for (auto &r : sl.reqs) {
+                        for (int32_t f = 0; f < F; ++f) {
+                            float *dst = sl.h_in + (size_t)f * (size_t)Kb + (size_t)k0;
+                            if (f < F - 2) {
+                                const float *src = r->src + (size_t)f * (size_t)r->ld;
+                                std::memcpy(dst, src, sizeof(float) * (size_t)r->K);
+                            } else {
+                                const float val = f == F - 2 ? 0.0f : (float)r->size;
+                                std::fill(dst, dst + r->K, val);
+                            }
+                        }
+                        k0 += r->K;
+                    }
+                    lk.unlock();
+                    launch(sl);
+                    continue;
+                }
+            }
+            if (!progressed) {
+                if (any_busy) {
+                    lk.unlock();
+                    std::this_thread::yield();
+                } else {
+                    cv_disp.wait_for(lk, std::chrono::milliseconds(2));
+                }
+            }
+        }
+    }
+
+    void refit_loop()
+    {
+        cudaSetDevice(device);
+        for (;;) {
+            std::unique_lock<std::mutex> lk(rmu);
+            rcv.wait(lk, [&] { return refit_stop || refit_req; });
+            if (refit_stop) break;
+            refit_req = false;
+            refit_running = true;
+            const int64_t avail = (int64_t)yapp.size();
+            const int64_t take = sp.refit_rows > 0 ? std::min<int64_t>(sp.refit_rows, avail) : avail;
+            for (int32_t f = 0; f < F; ++f) {
+                auto &a = acols[(size_t)f];
+                xcols[(size_t)f].insert(xcols[(size_t)f].end(), a.begin(), a.begin() + take);
+                a.erase(a.begin(), a.begin() + take);
+            }
+            ytrain.insert(ytrain.end(), yapp.begin(), yapp.begin() + take);
+            yapp.erase(yapp.begin(), yapp.begin() + take);
+            lk.unlock();
+
+            aiwcrf_forest *f = nullptr;
+            int64_t rows = 0;
+            const int rc = fit_training(&f, &rows);
+            if (rc == AIWCRF_OK) {
+                std::shared_ptr<Model> old;
+                {
+                    std::lock_guard<std::mutex> g(mu);
+                    const int64_t gen = current ? current->gen + 1 : 0;
+                    old = current;
+                    current = wrap(f, gen, rows);
+                    st.generation = gen;
+                    st.training_rows = rows;
+                    st.forest_bytes = current->bytes;
+                    ++st.refits;
+                }
+                old.reset();
+            } else {
+                std::lock_guard<std::mutex> g(mu);
+                ++st.refit_failures;
+            }
+            const std::string msg = rc == AIWCRF_OK ? std::string() : std::string(aiwcrf_last_error());
+            lk.lock();
+            last_refit_status = rc;
+            last_refit_msg = msg;
+            refit_running = false;
+            ++refits_finished;
+            rcv_done.notify_all();
+        }
+    }
+
+    int enqueue(const std::shared_ptr<Request> &r)
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (stop) return fail(AIWCRF_E_INVALID_ARG, "server is shutting down");
+        if ((int64_t)pending.size() >= sp.max_pending) {
+            ++st.rejected;
+            return fail(AIWCRF_E_LIMIT, "request refused: max_pending requests are waiting");
+        }
+        if (r->run == nullptr) {
+            r->ticket = next_ticket++;
+            tickets[r->ticket] = r;
+        }
+        pending.push_back(r);
+        ++st.submitted;
+        cv_disp.notify_one();
+        return AIWCRF_OK;
+    }
+
+    void shutdown()
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            stop = true;
+            cv_disp.notify_all();
+        }
+        if (disp.joinable()) disp.join();
+        {
+            std::lock_guard<std::mutex> lk(rmu);
+            refit_stop = true;
+            rcv.notify_all();
+        }
+        if (refitter.joinable()) refitter.join();
+        current.reset();
+        drain_graveyard();
+        if (free_stream) cudaStreamSynchronize(free_stream);
+        for (auto &sl : slots) {
+            if (sl.s) cudaStreamDestroy(sl.s);
+            if (sl.ev) cudaEventDestroy(sl.ev);
+            if (sl.h_in) cudaFreeHost(sl.h_in);
+            if (sl.h_out) cudaFreeHost(sl.h_out);
+            if (sl.d_sum) cudaFree(sl.d_sum);
+            if (sl.d_cnt) cudaFree(sl.d_cnt);
+        }
+        if (d_arena) cudaFree(d_arena);
+        if (d_dev) cudaFree(d_dev);
+        if (refit_stream) cudaStreamDestroy(refit_stream);
+        if (free_stream) cudaStreamDestroy(free_stream);
+    }
+};
+
+namespace {
+
+int check_rows(const float *X, const int64_t *y, int64_t n, int32_t F)
+{
+    for (int64_t i = 0; i < (int64_t)F * n; ++i)
+        if (X[i] != X[i]) return fail(AIWCRF_E_NAN_INPUT, "NaN in the training features");
+    for (int64_t i = 0; i < n; ++i)
+        if (y[i] > AIWCRF_MAX_ABS_Y || y[i] < -AIWCRF_MAX_ABS_Y) return fail(AIWCRF_E_LIMIT, "|y| above 2^40");
+    return AIWCRF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int aiwcrf_server_create(const aiwcrf_server_params *params, const aiwcrf_fit_params *fit, const float *X,
+                         const int64_t *y, int64_t n_rows, int32_t n_features, const int32_t *device_ids,
+                         int32_t n_devices, aiwcrf_server **out)
+{
+    if (!params || !fit || !X || !y || !device_ids || !out) return fail(AIWCRF_E_INVALID_ARG, "null argument");
+    *out = nullptr;
+    const aiwcrf_server_params &p = *params;
+    if (n_features < 3 || n_features > AIWCRF_MAX_FEATURES || n_rows < 1 || n_rows > AIWCRF_MAX_ROWS)
+        return fail(AIWCRF_E_INVALID_ARG, "n_features must be 3..128 and n_rows 1..2^22-1");
+    if (n_devices < 1 || n_devices > kServeMaxDevices) return fail(AIWCRF_E_INVALID_ARG, "n_devices must be 1..64");
+    if (p.n_streams < 1 || p.n_streams > 16 || p.max_request_kernels < 1 || p.max_request_kernels > 4096 ||
+        p.batch_kernels < p.max_request_kernels || p.batch_kernels > 65536 || p.max_pending < 1 ||
+        p.arena_bytes < 1 || p.refit_every < 0 || p.refit_rows < 0)
+        return fail(AIWCRF_E_INVALID_ARG, "server parameters out of range");
+    const int64_t one_request = (int64_t)(up256(sizeof(float) * (size_t)n_features * (size_t)p.max_request_kernels) +
+                                          up256((size_t)p.max_request_kernels * ((size_t)n_devices * 8 + 4)));
+    if (one_request > p.arena_bytes)
+        return fail(AIWCRF_E_INVALID_ARG, "arena_bytes cannot hold one request of max_request_kernels kernels");
+    int rc = check_rows(X, y, n_rows, n_features);
+    if (rc) return rc;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "no usable CUDA device");
+
+    auto *s = new aiwcrf_server();
+    s->sp = p;
+    s->fp = *fit;
+    s->F = n_features;
+    s->D = n_devices;
+    s->device = dev;
+    s->dev_ids.assign(device_ids, device_ids + n_devices);
+    s->xcols.resize((size_t)n_features);
+    s->acols.resize((size_t)n_features);
+    for (int32_t f = 0; f < n_features; ++f)
+        s->xcols[(size_t)f].assign(X + (size_t)f * (size_t)n_rows, X + (size_t)(f + 1) * (size_t)n_rows);
+    s->ytrain.assign(y, y + n_rows);
+
+    auto bail = [&](int code) {
+        s->shutdown();
+        delete s;
+        return code;
+    };
+    const size_t KB = (size_t)p.batch_kernels, D = (size_t)n_devices;
+    e = cudaStreamCreateWithFlags(&s->refit_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->free_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_dev, sizeof(int32_t) * D);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_dev, device_ids, sizeof(int32_t) * D, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_arena, (size_t)p.arena_bytes);
+    s->slots.resize((size_t)p.n_streams);
+    for (auto &sl : s->slots) {
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMallocHost(&sl.h_in, sizeof(float) * (size_t)n_features * KB);
+        if (e == cudaSuccess) e = cudaMallocHost(&sl.h_out, KB * (D * 8 + 4));
+        if (e == cudaSuccess) e = cudaMalloc(&sl.d_sum, sizeof(unsigned long long) * KB * D);
+        if (e == cudaSuccess) e = cudaMalloc(&sl.d_cnt, sizeof(uint32_t) * KB);
+        if (e == cudaSuccess) e = cudaMemset(sl.d_sum, 0, sizeof(unsigned long long) * KB * D);
+        if (e == cudaSuccess) e = cudaMemset(sl.d_cnt, 0, sizeof(uint32_t) * KB);
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cuda_fail(e, "server set-up");
+        return bail(e == cudaErrorMemoryAllocation ? AIWCRF_E_OOM : AIWCRF_E_CUDA);
+    }
+    s->arena.init(p.arena_bytes);
+    s->st.arena_bytes = p.arena_bytes;
+
+    aiwcrf_forest *f = nullptr;
+    int64_t rows = 0;
+    rc = s->fit_training(&f, &rows);
+    if (rc) return bail(rc);
+    s->current = s->wrap(f, 0, rows);
+    s->st.generation = 0;
+    s->st.training_rows = rows;
+    s->st.forest_bytes = s->current->bytes;
+    s->disp = std::thread([s] { s->dispatcher(); });
+    s->refitter = std::thread([s] { s->refit_loop(); });
+    *out = s;
+    return AIWCRF_OK;
+}
+
+int aiwcrf_server_submit(aiwcrf_server *server, const float *kfeat, int32_t n_kernels, int32_t size_class,
+                         int64_t *ticket)
+{
+    if (!server || !kfeat || !ticket) return fail(AIWCRF_E_INVALID_ARG, "null argument");
+    if (n_kernels < 1) return fail(AIWCRF_E_INVALID_ARG, "n_kernels must be >= 1");
+    if (n_kernels > server->sp.max_request_kernels) {
+        std::lock_guard<std::mutex> lk(server->mu);
+        ++server->st.rejected;
+        return fail(AIWCRF_E_LIMIT, "request has more than max_request_kernels kernels");
+    }
+    auto r = std::make_shared<Request>();
+    r->K = n_kernels;
+    r->size = size_class;
+    r->own.assign(kfeat, kfeat + (size_t)(server->F - 2) * (size_t)n_kernels);
+    r->src = r->own.data();
+    r->ld = n_kernels;
+    r->t_arrive = now_ns();
+    const int rc = server->enqueue(r);
+    if (rc == AIWCRF_OK) *ticket = r->ticket;
+    return rc;
+}
+
+int aiwcrf_server_wait(aiwcrf_server *server, int64_t ticket, int32_t timeout_ms, int32_t *best, int64_t *pred,
+                       int64_t *generation)
+{
+    if (!server) return fail(AIWCRF_E_INVALID_ARG, "null server");
+    std::unique_lock<std::mutex> lk(server->mu);
+    auto it = server->tickets.find(ticket);
+    if (it == server->tickets.end()) return fail(AIWCRF_E_INVALID_ARG, "unknown ticket");
+    std::shared_ptr<Request> r = it->second;
+    auto ready = [&] { return r->done; };
+    if (timeout_ms < 0) server->cv_done.wait(lk, ready);
+    else if (!server->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+        return fail(AIWCRF_E_TIMEOUT, "request still running");
+    server->tickets.erase(ticket);
+    if (r->status != AIWCRF_OK) return fail(r->status, r->msg);
+    if (best) std::copy(r->best.begin(), r->best.end(), best);
+    if (pred) std::copy(r->pred.begin(), r->pred.end(), pred);
+    if (generation) *generation = r->generation;
+    return AIWCRF_OK;
+}
+
+int aiwcrf_server_append(aiwcrf_server *server, const float *X, const int64_t *y, int64_t n_rows)
+{
+    if (!server || !X || !y) return fail(AIWCRF_E_INVALID_ARG, "null argument");
+    if (n_rows < 0) return fail(AIWCRF_E_INVALID_ARG, "n_rows < 0");
+    int rc = check_rows(X, y, n_rows, server->F);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(server->rmu);
+    if ((int64_t)server->ytrain.size() + (int64_t)server->yapp.size() + n_rows > AIWCRF_MAX_ROWS)
+        return fail(AIWCRF_E_LIMIT, "training rows would exceed 2^22-1");
+    for (int32_t f = 0; f < server->F; ++f)
+        server->acols[(size_t)f].insert(server->acols[(size_t)f].end(), X + (size_t)f * (size_t)n_rows,
+                                        X + (size_t)(f + 1) * (size_t)n_rows);
+    server->yapp.insert(server->yapp.end(), y, y + n_rows);
+    return AIWCRF_OK;
+}
+
+int aiwcrf_server_refit(aiwcrf_server *server, int32_t wait)
+{
+    if (!server) return fail(AIWCRF_E_INVALID_ARG, "null server");
+    std::unique_lock<std::mutex> lk(server->rmu);
+    // a refit already running read its rows before this call: wait for the one after it
+    const int64_t target = server->refits_finished + 1 + (server->refit_running ? 1 : 0);
+    server->refit_req = true;
+    server->rcv.notify_all();
+    if (!wait) return AIWCRF_OK;
+    server->rcv_done.wait(lk, [&] { return server->refits_finished >= target || server->refit_stop; });
+    if (server->last_refit_status != AIWCRF_OK) return fail(server->last_refit_status, "refit failed: " + server->last_refit_msg);
+    return AIWCRF_OK;
+}
+
+int aiwcrf_server_pause(aiwcrf_server *server, int32_t paused)
+{
+    if (!server) return fail(AIWCRF_E_INVALID_ARG, "null server");
+    std::lock_guard<std::mutex> lk(server->mu);
+    server->paused = paused != 0;
+    server->cv_disp.notify_all();
+    return AIWCRF_OK;
+}
+
+int aiwcrf_server_stats(aiwcrf_server *server, aiwcrf_server_counters *out)
+{
+    if (!server || !out) return fail(AIWCRF_E_INVALID_ARG, "null argument");
+    {
+        std::lock_guard<std::mutex> lk(server->mu);
+        *out = server->st;
+        out->arena_peak_bytes = server->arena.peak;
+    }
+    std::lock_guard<std::mutex> lk(server->rmu);
+    out->appended_rows = (int64_t)server->yapp.size();
+    return AIWCRF_OK;
+}
+
+int aiwcrf_server_run_load(aiwcrf_server *server, const float *pool, int64_t pool_kernels, const int64_t *first,
+                           const int32_t *n_kernels, const int32_t *size_class, int64_t n_requests, double rate_per_s,
+                           uint64_t seed, int32_t timeout_ms, int32_t *best, int64_t *generation, int64_t *latency_ns,
+                           aiwcrf_load_report *report)
+{
+    if (!server || !pool || !first || !n_kernels || !size_class || !report)
+        return fail(AIWCRF_E_INVALID_ARG, "null argument");
+    if (n_requests < 1 || !(rate_per_s > 0.0) || pool_kernels < 1)
+        return fail(AIWCRF_E_INVALID_ARG, "n_requests, rate and pool size must be positive");
+    std::vector<int64_t> best_off((size_t)n_requests);
+    int64_t total_k = 0;
+    for (int64_t i = 0; i < n_requests; ++i) {
+        if (n_kernels[i] < 1 || first[i] < 0 || first[i] + n_kernels[i] > pool_kernels)
+            return fail(AIWCRF_E_INVALID_ARG, "request outside the kernel pool");
+        best_off[(size_t)i] = total_k;
+        total_k += n_kernels[i];
+    }
+    auto run = std::make_shared<LoadRun>();
+    run->remaining = n_requests;
+    run->best = best;
+    run->gen = generation;
+    run->lat.assign((size_t)n_requests, -1);
+    aiwcrf_server_counters s0;
+    aiwcrf_server_stats(server, &s0);
+
+    // arrival times of a Poisson process: exponential gaps by inversion of SplitMix64 uniforms
+    SplitMix64 rng{seed};
+    std::vector<int64_t> arrive((size_t)n_requests);
+    const int64_t t0 = now_ns() + 1000000;
+    double t = 0.0;
+    for (int64_t i = 0; i < n_requests; ++i) {
+        const double u = (double)(rng.next() >> 11) * 0x1.0p-53;
+        t += -std::log1p(-u) / rate_per_s;
+        arrive[(size_t)i] = t0 + (int64_t)(t * 1e9);
+    }
+    int64_t rejected = 0;
+    for (int64_t i = 0; i < n_requests; ++i) {
+        for (;;) {
+            const int64_t d = arrive[(size_t)i] - now_ns();
+            if (d <= 0) break;
+            if (d > 300000) std::this_thread::sleep_for(std::chrono::nanoseconds(d - 200000));
+            else std::this_thread::yield();
+        }
+        auto r = std::make_shared<Request>();
+        r->K = n_kernels[i];
+        r->size = size_class[i];
+        r->src = pool + first[i];
+        r->ld = pool_kernels;
+        r->t_arrive = arrive[(size_t)i];
+        r->run = run;
+        r->run_index = i;
+        r->run_best_off = best_off[(size_t)i];
+        int rc = r->K > server->sp.max_request_kernels ? AIWCRF_E_LIMIT : server->enqueue(r);
+        if (rc != AIWCRF_OK) {
+            std::lock_guard<std::mutex> lk(run->mu);
+            --run->remaining;
+            ++rejected;
+        }
+    }
+    bool timed_out = false;
+    {
+        std::unique_lock<std::mutex> lk(run->mu);
+        auto done = [&] { return run->remaining == 0; };
+        if (timeout_ms < 0) run->cv.wait(lk, done);
+        else timed_out = !run->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), done);
+    }
+    if (timed_out) {
+        // stop reading the caller's pool and writing its outputs
+        {
+            std::lock_guard<std::mutex> lk(server->mu);
+            std::deque<std::shared_ptr<Request>> keep;
+            for (auto &r : server->pending)
+                if (r->run != run) keep.push_back(r);
+            server->pending.swap(keep);
+        }
+        std::lock_guard<std::mutex> lk(run->mu);
+        run->abandoned = true;
+    }
+    aiwcrf_server_counters s1;
+    aiwcrf_server_stats(server, &s1);
+
+    std::vector<int64_t> lat;
+    int64_t t_last = 0;
+    for (int64_t i = 0; i < n_requests; ++i) {
+        const int64_t l = run->lat[(size_t)i];
+        if (latency_ns) latency_ns[i] = l;
+        if (l >= 0) {
+            lat.push_back(l);
+            t_last = std::max(t_last, arrive[(size_t)i] + l);
+        }
+    }
+    std::sort(lat.begin(), lat.end());
+    auto pct = [&](double p) {
+        if (lat.empty()) return 0.0;
+        size_t r = (size_t)std::ceil(p * (double)lat.size());
+        r = std::min(std::max<size_t>(r, 1), lat.size());
+        return (double)lat[r - 1] * 1e-3;
+    };
+    std::memset(report, 0, sizeof(*report));
+    report->n_requests = (int64_t)lat.size();
+    report->n_kernels = total_k;
+    report->offered_rate = rate_per_s;
+    report->wall_s = lat.empty() ? 0.0 : (double)(t_last - arrive[0]) * 1e-9;
+    report->requests_per_s = report->wall_s > 0 ? (double)lat.size() / report->wall_s : 0.0;
+    report->kernels_per_s = report->wall_s > 0 ? (double)total_k / report->wall_s : 0.0;
+    report->p50_us = pct(0.50);
+    report->p99_us = pct(0.99);
+    double sum = 0.0;
+    for (auto l : lat) sum += (double)l;
+    report->mean_us = lat.empty() ? 0.0 : sum / (double)lat.size() * 1e-3;
+    report->max_us = lat.empty() ? 0.0 : (double)lat.back() * 1e-3;
+    report->batches = s1.batches - s0.batches;
+    report->mean_batch_kernels =
+        report->batches ? (double)(s1.batch_kernels_total - s0.batch_kernels_total) / (double)report->batches : 0.0;
+    report->refits = s1.refits - s0.refits;
+    report->failed = n_requests - (int64_t)lat.size() - rejected;
+    report->rejected = rejected;
+    if (timed_out) return fail(AIWCRF_E_TIMEOUT, "requests still running at the time limit");
+    if (run->first_error != AIWCRF_OK) return fail(run->first_error, "a request failed");
+    return AIWCRF_OK;
+}
+
+int aiwcrf_server_destroy(aiwcrf_server *server)
+{
+    if (!server) return AIWCRF_OK;
+    server->shutdown();
+    delete server;
+    return AIWCRF_OK;
+}
+
+}  // extern "C"

@@ -84,3 +84,34 @@ def test_profile_names():
     names = [L.aiwcrf_profile_name(k).decode() for k in range(n)]
     assert "level_big" in names and "predict" in names
     assert L.aiwcrf_profile_name(n) == b""
+
+
+def test_server_layouts_and_validation_without_gpu():
+    assert C.sizeof(A.ServerParams) == 40
+    assert C.sizeof(A.ServerCounters) == 16 * 8
+    assert C.sizeof(A.LoadReport) == 15 * 8
+    L = _lib()
+    F, N, D = 4, 10, 3
+    X = np.zeros((F, N), np.float32)
+    y = np.zeros(N, np.int64)
+    dev = np.arange(D, dtype=np.int32)
+    fp = A.params(3, 2, 1)
+    h = C.c_void_p()
+
+    def create(sp, X=X, y=y, F=F, N=N, D=D):
+        return L.aiwcrf_server_create(C.byref(sp), C.byref(fp), X.ctypes.data, y.ctypes.data, N, F,
+                                      dev.ctypes.data, D, C.byref(h))
+
+    for sp in [A.server_params(n_streams=0), A.server_params(n_streams=17), A.server_params(max_request_kernels=0),
+               A.server_params(max_request_kernels=128, batch_kernels=64), A.server_params(max_pending=0),
+               A.server_params(refit_every=-1), A.server_params(arena_bytes=1024)]:
+        assert create(sp) == -1, sp
+    assert create(A.server_params(), F=2) == -1
+    assert create(A.server_params(), D=0) == -1
+    Xn = X.copy()
+    Xn[1, 3] = np.nan
+    assert create(A.server_params(), X=Xn) == -2
+    yb = y.copy()
+    yb[0] = (1 << 40) + 1
+    assert create(A.server_params(), y=yb) == -8
+    assert L.aiwcrf_server_destroy(None) == 0
