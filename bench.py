@@ -487,7 +487,13 @@ def serving_report(A, wl, rates=(5000.0, 20000.0, 50000.0), n_requests=20000, re
             k = rng.integers(1, 65, n_requests).astype(np.int32)
             first = (rng.integers(0, pool.shape[1] - 64, n_requests)).astype(np.int64)
             size = rng.integers(0, synth.N_SIZES, n_requests).astype(np.int32)
-            rep, best, gen, _ = srv.run_load(pool, first, k, size, rate_per_s=rate, seed=int(rate), timeout_ms=600000)
+            c0 = srv.stats()
+            rep, best, gen, lat = srv.run_load(pool, first, k, size, rate_per_s=rate, seed=int(rate),
+                                               timeout_ms=600000)
+            c1 = srv.stats()
+            rep["refit_ms"] = (c1["refit_us_total"] - c0["refit_us_total"]) / 1e3
+            rep["requests_over_1ms"] = int((lat > 1_000_000).sum())
+            rep["requests_over_10ms"] = int((lat > 10_000_000).sum())
             checked = mism = 0
             off = 0
             for i in range(n_requests):
@@ -498,6 +504,25 @@ def serving_report(A, wl, rates=(5000.0, 20000.0, 50000.0), n_requests=20000, re
             rep["generation_0_requests_checked"] = checked
             rep["generation_0_mismatches"] = mism
             out["runs"].append(rep)
+        # the selection kernel alone, from events around its launches: lone 64-kernel requests,
+        # then 1,024-kernel batches (16 requests queued while the dispatcher is paused)
+        A.aiwcrf_profile_enable(True)
+        A.aiwcrf_profile_read()
+        for i in range(100):
+            srv.wait(srv.submit(np.ascontiguousarray(pool[:, i:i + 64]), 1))
+        n64, ms64 = A.aiwcrf_profile_read()["serve"]
+        for r in range(20):
+            srv.pause(True)
+            ts = [srv.submit(np.ascontiguousarray(pool[:, 64 * j:64 * j + 64]), r % 4) for j in range(16)]
+            srv.pause(False)
+            for t in ts:
+                srv.wait(t)
+        n1k, ms1k = A.aiwcrf_profile_read()["serve"]
+        A.aiwcrf_profile_enable(False)
+        out["kernel"] = {
+            "batch_64_us": 1e3 * ms64 / max(n64, 1), "batch_64_launches": n64,
+            "batch_1024_us": 1e3 * ms1k / max(n1k, 1), "batch_1024_launches": n1k,
+            "batch_1024_queries_per_s": 1024 * SEL_DEVICES * n1k / (ms1k / 1e3) if ms1k else None}
         out["counters"] = srv.stats()
     return out
 

@@ -285,6 +285,8 @@ typedef struct {
     int64_t training_rows;        /* rows the current forest was fitted on */
     int64_t appended_rows;        /* appended rows not yet consumed by a refit */
     int64_t forest_bytes;         /* device bytes of the current forest */
+    int64_t refit_us_total;       /* wall time of all refits (rows staged, fit, swap) */
+    int64_t refit_us_max;
 } aiwcrf_server_counters;
 
 typedef struct {

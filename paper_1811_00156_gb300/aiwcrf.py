@@ -64,7 +64,7 @@ class ServerCounters(C.Structure):
     _fields_ = [(k, C.c_int64) for k in (
         "submitted", "rejected", "completed", "failed", "batches", "batch_kernels_total", "batch_kernels_max",
         "arena_waits", "arena_bytes", "arena_peak_bytes", "refits", "refit_failures", "generation",
-        "training_rows", "appended_rows", "forest_bytes")]
+        "training_rows", "appended_rows", "forest_bytes", "refit_us_total", "refit_us_max")]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -147,7 +147,7 @@ cudaEvent_t take_event()
 }
 
 const char *kProfNames[kProfNum] = {"rank",    "bootstrap", "level_big", "level_small", "scan",
-                                    "finalize", "pack",      "predict",   "select"};
+                                    "finalize", "pack",      "predict",   "select", "serve"};
 }  // namespace
 
 void prof_begin(cudaStream_t s, int cls)

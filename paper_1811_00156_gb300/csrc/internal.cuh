@@ -323,7 +323,7 @@ size_t radix_sort_hist_words(int64_t n, int S);
 
 enum ProfClass {
     kProfRank = 0, kProfBoot, kProfLevelBig, kProfLevelSmall, kProfScan, kProfFinalize,
-    kProfPack, kProfPredict, kProfSelect, kProfNum
+    kProfPack, kProfPredict, kProfSelect, kProfServe, kProfNum
 };
 
 void prof_begin(cudaStream_t s, int cls);

@@ -15,15 +15,16 @@
 //    stream and swaps them in; each batch holds a reference to the forest it was formed with,
 //    and a forest is freed (stream-ordered) only after the last batch using it completed.
 //
-// Selection kernel (serve_select_kernel): one warp per (query, group of 64 trees), a query
-// being one (kernel, device) pair. The warp's lanes first code the query's features as ranks
-// in the forest's value tables (c(x) = #{training values < x}; NaN past every value), then each
-// lane walks two trees, and the warp's exact int64 leaf sum is added atomically to the query's
-// sum. The warp that completes a kernel's last query group (a per-kernel counter) rounds the
-// kernel's sums to predictions, takes the argmin over devices (ties to the lower device id)
-// and resets the sums and the counter for the slot's next batch. Integer sums make the result
-// independent of the order in which warps finish: a request gets the same answer alone or
-// batched with any others.
+// Selection kernel (serve_select_kernel): one CTA per (kernel, chunk of 32 trees). It codes the
+// kernel's features once as ranks in the forest's value tables (c(x) = #{training values < x};
+// NaN past every value) plus one code per device, then its threads walk (tree, device) pairs,
+// the threads of one tree side by side so that their paths, identical until a split on the
+// device column, read the same nodes. Exact int64 sums per (kernel, device) are added
+// atomically; the CTA that completes a kernel's last chunk (a per-kernel counter) rounds the
+// sums to predictions, takes the argmin over devices (ties to the lower device id) and resets
+// the sums and the counter for the slot's next batch. Integer sums make the result independent
+// of the order in which CTAs finish: a request gets the same answer alone or batched with any
+// others.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -60,8 +61,9 @@ struct ServeForest {
 };
 
 constexpr int kServeThreads = 256;
-constexpr int kServeWarps = kServeThreads / 32;
-constexpr int kTreesPerWarp = 64;
+constexpr int kDevSlots = 16;                             // threads of one tree slot: devices
+constexpr int kTreeSlots = kServeThreads / kDevSlots;    // 16 tree slots
+constexpr int kTreesPerBlock = 2 * kTreeSlots;            // each thread walks two trees
 constexpr int kServeMaxDevices = 64;
 
 __device__ __forceinline__ int64_t serve_leaf(uint64_t nd)
@@ -69,9 +71,17 @@ __device__ __forceinline__ int64_t serve_leaf(uint64_t nd)
     return ((int64_t)(nd << 1)) >> 1;
 }
 
-// Two independent walks (trees t0, t1; -1 = none) with the query's codes in shared memory.
+// The rank code of feature f for this thread's query: the kernel's codes are shared by the
+// block, the device column's code is the thread's own.
+__device__ __forceinline__ uint32_t serve_code(const uint32_t *kcode, uint32_t f, uint32_t fd, uint32_t dc)
+{
+    return f == fd ? dc : kcode[f];
+}
+
+// Two independent walks (trees t0, t1; -1 = none).
 template <bool COMPACT>
-__device__ __forceinline__ int64_t serve_walk2(const ServeForest &sf, int t0, int t1, const uint32_t *code)
+__device__ __forceinline__ int64_t serve_walk2(const ServeForest &sf, int t0, int t1, const uint32_t *kcode,
+                                               uint32_t fd, uint32_t dc)
 {
     int64_t v = 0;
     if (COMPACT) {
@@ -82,7 +92,8 @@ __device__ __forceinline__ int64_t serve_walk2(const ServeForest &sf, int t0, in
         while (!(l0 && l1)) {
             const uint32_t a = __ldg(n0 + j0), b = __ldg(n1 + j1);
             const bool la = l0 || (int32_t)a < 0, lb = l1 || (int32_t)b < 0;
-            const uint32_t ca = code[la ? 0u : (a >> 24)], cb = code[lb ? 0u : (b >> 24)];
+            const uint32_t ca = serve_code(kcode, la ? 0u : (a >> 24), fd, dc);
+            const uint32_t cb = serve_code(kcode, lb ? 0u : (b >> 24), fd, dc);
             j0 = la ? j0 : (a & 0xFFFFu) + (ca > ((a >> 16) & 0xFFu) ? 1u : 0u);
             j1 = lb ? j1 : (b & 0xFFFFu) + (cb > ((b >> 16) & 0xFFu) ? 1u : 0u);
             l0 = la;
@@ -95,13 +106,11 @@ __device__ __forceinline__ int64_t serve_walk2(const ServeForest &sf, int t0, in
         const uint64_t *n1 = sf.cnodes + (t1 >= 0 ? sf.tree_off[t1] : 0);
         uint32_t j0 = 0, j1 = 0;
         bool l0 = t0 < 0, l1 = t1 < 0;
-        uint64_t a = 0, b = 0;
         while (!(l0 && l1)) {
-            a = __ldg(n0 + j0);
-            b = __ldg(n1 + j1);
+            const uint64_t a = __ldg(n0 + j0), b = __ldg(n1 + j1);
             const bool la = l0 || (a >> 63), lb = l1 || (b >> 63);
-            const uint32_t ca = code[la ? 0u : (uint32_t)(a >> 56) & 0x7Fu];
-            const uint32_t cb = code[lb ? 0u : (uint32_t)(b >> 56) & 0x7Fu];
+            const uint32_t ca = serve_code(kcode, la ? 0u : (uint32_t)(a >> 56) & 0x7Fu, fd, dc);
+            const uint32_t cb = serve_code(kcode, lb ? 0u : (uint32_t)(b >> 56) & 0x7Fu, fd, dc);
             j0 = la ? j0 : ((uint32_t)(a >> 32) & 0xFFFFFFu) + (ca > ((uint32_t)a & 0xFFFFFFu) ? 1u : 0u);
             j1 = lb ? j1 : ((uint32_t)(b >> 32) & 0xFFFFFFu) + (cb > ((uint32_t)b & 0xFFFFFFu) ? 1u : 0u);
             l0 = la;
@@ -113,52 +122,66 @@ __device__ __forceinline__ int64_t serve_walk2(const ServeForest &sf, int t0, in
     return v;
 }
 
-// kq: F x Kb column-major batch features (row F-2 unused: the device id comes from dev[]; row
-// F-1 the size class). sums (Kb * D) and cnt (Kb) are zero on entry and left zero.
+__device__ __forceinline__ uint32_t rank_code(const float *V, uint32_t card, float x)
+{
+    if (x != x) return card;
+    uint32_t lo = 0, hi = card;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(&V[mid]) < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Block (kernel k, chunk g of 32 trees). Thread (tree slot ts, device slot jl) walks trees
+// 32g + ts and 32g + ts + 16 for device jb + jl, for each pass jb = 0, 16, .. < D: the threads of
+// one tree follow the same path until a split on the device column, so their node loads
+// coincide. kq: F x Kb column-major batch features (row F-2 unused: the device id comes from
+// dev[]; row F-1 the size class). sums (Kb * D) and cnt (Kb) are zero on entry and left zero.
 // pred: Kb x D row-major predictions; best: Kb device ids.
 template <bool COMPACT>
 __global__ void __launch_bounds__(kServeThreads) serve_select_kernel(ServeForest sf, const float *__restrict__ kq,
                                                                      int Kb, const int32_t *__restrict__ dev, int D,
-                                                                     int G, unsigned long long *sums, uint32_t *cnt,
+                                                                     unsigned long long *sums, uint32_t *cnt,
                                                                      int64_t *pred, int32_t *best)
 {
-    __shared__ uint32_t code[kServeWarps][AIWCRF_MAX_FEATURES];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t Qn = (int64_t)Kb * D;
-    const int64_t w = (int64_t)blockIdx.x * kServeWarps + warp;
-    const int64_t q = w / G;
-    const int g = (int)(w % G);
-    if (q >= Qn) return;                       // warp-uniform
-    const int k = (int)(q / D), jd = (int)(q % D);
-    for (int f = lane; f < sf.F; f += 32) {
-        const float x = (f == sf.F - 2) ? (float)dev[jd] : kq[(size_t)f * (size_t)Kb + (size_t)k];
-        const float *V = sf.fvals + (size_t)f * (size_t)sf.fstride;
-        uint32_t lo = 0, hi = sf.fcard[f];
-        if (x != x) {
-            lo = hi;
-        } else {
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (__ldg(&V[mid]) < x) lo = mid + 1;
-                else hi = mid;
-            }
-        }
-        code[warp][f] = lo;
-    }
-    __syncwarp();
-    const int t0 = g * kTreesPerWarp + lane, t1 = t0 + 32;
-    int64_t v = serve_walk2<COMPACT>(sf, t0 < sf.T ? t0 : -1, t1 < sf.T ? t1 : -1, code[warp]);
+    __shared__ uint32_t kcode[AIWCRF_MAX_FEATURES];
+    __shared__ uint32_t dcode[kServeMaxDevices];
+    __shared__ int64_t red[kServeThreads / 32][kDevSlots];
+    __shared__ int last;
+    const int k = blockIdx.x, g = blockIdx.y;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ts = tid / kDevSlots, jl = tid % kDevSlots;
+    const uint32_t fd = (uint32_t)sf.F - 2u;
+    for (int f = tid; f < sf.F; f += kServeThreads)
+        if (f != (int)fd)
+            kcode[f] = rank_code(sf.fvals + (size_t)f * (size_t)sf.fstride, sf.fcard[f],
+                                 kq[(size_t)f * (size_t)Kb + (size_t)k]);
+    for (int j = tid; j < D; j += kServeThreads)
+        dcode[j] = rank_code(sf.fvals + (size_t)fd * (size_t)sf.fstride, sf.fcard[fd], (float)dev[j]);
+    __syncthreads();
+    const int t0 = g * kTreesPerBlock + ts, t1 = t0 + kTreeSlots;
+    for (int jb = 0; jb < D; jb += kDevSlots) {
+        const int j = jb + jl;
+        int64_t v = 0;
+        if (j < D) v = serve_walk2<COMPACT>(sf, t0 < sf.T ? t0 : -1, t1 < sf.T ? t1 : -1, kcode, fd, dcode[j]);
+        v += __shfl_xor_sync(0xFFFFFFFFu, v, 16);             // the warp's two tree slots
+        if (lane < kDevSlots) red[warp][lane] = v;
+        __syncthreads();
+        if (tid < kDevSlots && j < D) {
+            int64_t sum = 0;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    uint32_t prev = 0;
-    if (lane == 0) {
-        atomicAdd(&sums[q], (unsigned long long)v);
-        __threadfence();
-        prev = atomicAdd(&cnt[k], 1u);
+            for (int w = 0; w < kServeThreads / 32; ++w) sum += red[w][tid];
+            atomicAdd(&sums[(size_t)k * (size_t)D + (size_t)j], (unsigned long long)sum);
+            __threadfence();
+        }
+        __syncthreads();
     }
-    prev = __shfl_sync(0xFFFFFFFFu, prev, 0);
-    if (prev != (uint32_t)(D * G) - 1u) return;  // warp-uniform
-    // this warp finishes kernel k: every group of every device has added its sum
+    if (tid == 0) last = atomicAdd(&cnt[k], 1u) == gridDim.y - 1u;
+    __syncthreads();
+    if (!last || warp != 0) return;
+    // the last chunk of kernel k: every tree has been added for every device
     __threadfence();
     int64_t bp = LLONG_MAX;
     int32_t bd = INT_MAX;
@@ -195,6 +218,8 @@ int64_t now_ns()
 
 size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+constexpr int64_t kIdlePollNs = 200000;   // the dispatcher polls this long before sleeping
+
 int serve_launch(const aiwcrf_forest *f, const float *d_kq, int Kb, const int32_t *d_dev, int D,
                  unsigned long long *d_sum, uint32_t *d_cnt, int64_t *d_pred, int32_t *d_best, cudaStream_t s)
 {
@@ -209,13 +234,13 @@ int serve_launch(const aiwcrf_forest *f, const float *d_kq, int Kb, const int32_
     sf.fstride = f->fstride;
     sf.T = (int)f->T;
     sf.F = f->F;
-    const int G = (int)((f->T + kTreesPerWarp - 1) / kTreesPerWarp);
-    const int64_t warps = (int64_t)Kb * D * G;
-    const unsigned grid = (unsigned)((warps + kServeWarps - 1) / kServeWarps);
+    const dim3 grid((unsigned)Kb, (unsigned)((f->T + kTreesPerBlock - 1) / kTreesPerBlock));
+    prof_begin(s, kProfServe);
     if (f->compact)
-        serve_select_kernel<true><<<grid, kServeThreads, 0, s>>>(sf, d_kq, Kb, d_dev, D, G, d_sum, d_cnt, d_pred, d_best);
+        serve_select_kernel<true><<<grid, kServeThreads, 0, s>>>(sf, d_kq, Kb, d_dev, D, d_sum, d_cnt, d_pred, d_best);
     else
-        serve_select_kernel<false><<<grid, kServeThreads, 0, s>>>(sf, d_kq, Kb, d_dev, D, G, d_sum, d_cnt, d_pred, d_best);
+        serve_select_kernel<false><<<grid, kServeThreads, 0, s>>>(sf, d_kq, Kb, d_dev, D, d_sum, d_cnt, d_pred, d_best);
+    prof_end(s, kProfServe);
     count_launches(1);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "serve_select_kernel launch");
@@ -355,6 +380,7 @@ struct aiwcrf_server {
     std::mutex mu;                        // queue, tickets, arena, current model, counters
     std::condition_variable cv_disp, cv_done;
     std::deque<std::shared_ptr<Request>> pending;
+    std::atomic<int64_t> n_pending{0};    // pending.size(), readable without the lock
     std::unordered_map<int64_t, std::shared_ptr<Request>> tickets;
     int64_t next_ticket = 1;
     bool stop = false, paused = false;
@@ -542,6 +568,7 @@ struct aiwcrf_server {
             if (stop) {
                 std::deque<std::shared_ptr<Request>> drop;
                 drop.swap(pending);
+                n_pending.store(0);
                 lk.unlock();
                 for (auto &r : drop) finish(r, AIWCRF_E_INVALID_ARG, "server shut down", -1, nullptr, nullptr, now_ns());
                 if (!any_busy) {
@@ -573,6 +600,7 @@ struct aiwcrf_server {
                     sl.off = arena.alloc(sl.bytes);
                     sl.reqs.assign(pending.begin(), pending.begin() + (std::ptrdiff_t)n);
                     pending.erase(pending.begin(), pending.begin() + (std::ptrdiff_t)n);
+                    n_pending.store((int64_t)pending.size());
                     sl.model = current;
                     ++st.batches;
                     st.batch_kernels_total += Kb;
@@ -602,8 +630,16 @@ struct aiwcrf_server {
                 if (any_busy) {
                     lk.unlock();
                     std::this_thread::yield();
-                } else {
-                    cv_disp.wait_for(lk, std::chrono::milliseconds(2));
+                } else if (paused || pending.empty()) {
+                    // idle: poll for a new request a little while before sleeping on the queue
+                    if (!paused) {
+                        lk.unlock();
+                        const int64_t t_end = now_ns() + kIdlePollNs;
+                        while (n_pending.load(std::memory_order_relaxed) == 0 && now_ns() < t_end)
+                            std::this_thread::yield();
+                        lk.lock();
+                    }
+                    if (!stop && (paused || pending.empty())) cv_disp.wait_for(lk, std::chrono::milliseconds(2));
                 }
             }
         }
@@ -631,7 +667,14 @@ struct aiwcrf_server {
 
             aiwcrf_forest *f = nullptr;
             int64_t rows = 0;
+            const int64_t t_fit = now_ns();
             const int rc = fit_training(&f, &rows);
+            const int64_t us = (now_ns() - t_fit) / 1000;
+            {
+                std::lock_guard<std::mutex> g(mu);
+                st.refit_us_total += us;
+                st.refit_us_max = std::max(st.refit_us_max, us);
+            }
             if (rc == AIWCRF_OK) {
                 std::shared_ptr<Model> old;
                 {
@@ -672,6 +715,7 @@ struct aiwcrf_server {
             tickets[r->ticket] = r;
         }
         pending.push_back(r);
+        n_pending.store((int64_t)pending.size());
         ++st.submitted;
         cv_disp.notify_one();
         return AIWCRF_OK;
@@ -767,14 +811,17 @@ int aiwcrf_server_create(const aiwcrf_server_params *params, const aiwcrf_fit_pa
         return code;
     };
     const size_t KB = (size_t)p.batch_kernels, D = (size_t)n_devices;
-    e = cudaStreamCreateWithFlags(&s->refit_stream, cudaStreamNonBlocking);
+    // selection batches go first: a refit's many small launches yield the SMs to them
+    int prio_low = 0, prio_high = 0;
+    e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->refit_stream, cudaStreamNonBlocking, prio_low);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->free_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_dev, sizeof(int32_t) * D);
     if (e == cudaSuccess) e = cudaMemcpy(s->d_dev, device_ids, sizeof(int32_t) * D, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_arena, (size_t)p.arena_bytes);
     s->slots.resize((size_t)p.n_streams);
     for (auto &sl : s->slots) {
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&sl.s, cudaStreamNonBlocking, prio_high);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_in, sizeof(float) * (size_t)n_features * KB);
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_out, KB * (D * 8 + 4));
@@ -973,6 +1020,7 @@ int aiwcrf_server_run_load(aiwcrf_server *server, const float *pool, int64_t poo
             for (auto &r : server->pending)
                 if (r->run != run) keep.push_back(r);
             server->pending.swap(keep);
+            server->n_pending.store((int64_t)server->pending.size());
         }
         std::lock_guard<std::mutex> lk(run->mu);
         run->abandoned = true;

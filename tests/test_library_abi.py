@@ -88,7 +88,7 @@ def test_profile_names():
 
 def test_server_layouts_and_validation_without_gpu():
     assert C.sizeof(A.ServerParams) == 40
-    assert C.sizeof(A.ServerCounters) == 16 * 8
+    assert C.sizeof(A.ServerCounters) == 18 * 8
     assert C.sizeof(A.LoadReport) == 15 * 8
     L = _lib()
     F, N, D = 4, 10, 3
