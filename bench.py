@@ -28,6 +28,8 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# one hardware queue per stream for the selection server's streams (read when CUDA initialises)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 from paper_1811_00156_gb300 import synth  # noqa: E402
 
@@ -469,6 +471,25 @@ def serving_report(A, wl, rates=(5000.0, 20000.0, 50000.0), n_requests=20000, re
             srv.wait(srv.submit(np.ascontiguousarray(pool[:, i:i + 64]), i % synth.N_SIZES))
             lat.append((time.perf_counter() - t0) * 1e6)
         out["lone_64_kernel_request_us"] = {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))}
+        # the selection kernel alone, from events around its launches: lone 64-kernel requests,
+        # then 1,024-kernel batches (16 requests queued while the dispatcher is paused)
+        A.aiwcrf_profile_enable(True)
+        A.aiwcrf_profile_read()
+        for i in range(100):
+            srv.wait(srv.submit(np.ascontiguousarray(pool[:, i:i + 64]), 1))
+        n64, ms64 = A.aiwcrf_profile_read()["serve"]
+        for r in range(20):
+            srv.pause(True)
+            ts = [srv.submit(np.ascontiguousarray(pool[:, 64 * j:64 * j + 64]), r % 4) for j in range(16)]
+            srv.pause(False)
+            for t in ts:
+                srv.wait(t)
+        n1k, ms1k = A.aiwcrf_profile_read()["serve"]
+        A.aiwcrf_profile_enable(False)
+        out["kernel"] = {
+            "batch_64_us": 1e3 * ms64 / max(n64, 1), "batch_64_launches": n64,
+            "batch_1024_us": 1e3 * ms1k / max(n1k, 1), "batch_1024_launches": n1k,
+            "batch_1024_queries_per_s": 1024 * SEL_DEVICES * n1k / (ms1k / 1e3) if ms1k else None}
         # answers checked against the forest fitted at creation
         ref = {}
         f0 = A.aiwcrf_fit(fp, wl.X, wl.y)
@@ -504,25 +525,6 @@ def serving_report(A, wl, rates=(5000.0, 20000.0, 50000.0), n_requests=20000, re
             rep["generation_0_requests_checked"] = checked
             rep["generation_0_mismatches"] = mism
             out["runs"].append(rep)
-        # the selection kernel alone, from events around its launches: lone 64-kernel requests,
-        # then 1,024-kernel batches (16 requests queued while the dispatcher is paused)
-        A.aiwcrf_profile_enable(True)
-        A.aiwcrf_profile_read()
-        for i in range(100):
-            srv.wait(srv.submit(np.ascontiguousarray(pool[:, i:i + 64]), 1))
-        n64, ms64 = A.aiwcrf_profile_read()["serve"]
-        for r in range(20):
-            srv.pause(True)
-            ts = [srv.submit(np.ascontiguousarray(pool[:, 64 * j:64 * j + 64]), r % 4) for j in range(16)]
-            srv.pause(False)
-            for t in ts:
-                srv.wait(t)
-        n1k, ms1k = A.aiwcrf_profile_read()["serve"]
-        A.aiwcrf_profile_enable(False)
-        out["kernel"] = {
-            "batch_64_us": 1e3 * ms64 / max(n64, 1), "batch_64_launches": n64,
-            "batch_1024_us": 1e3 * ms1k / max(n1k, 1), "batch_1024_launches": n1k,
-            "batch_1024_queries_per_s": 1024 * SEL_DEVICES * n1k / (ms1k / 1e3) if ms1k else None}
         out["counters"] = srv.stats()
     return out
 

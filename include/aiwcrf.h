@@ -65,7 +65,10 @@ typedef struct {
     int32_t max_depth;      /* 0 = unlimited; else nodes at this depth are leaves */
     uint64_t seed;          /* Philox4x32-10 key */
     int32_t bootstrap;      /* 1: n_rows draws with replacement per tree; 0: every row once */
-    int32_t reserved;       /* must be 0 */
+    int32_t ctas_per_sm;    /* 0: the level kernels may fill every SM (3 CTAs each); 1..3: at most
+                               that many of their CTAs per SM, leaving registers on every SM for
+                               concurrent work (a background fit). The forest does not depend on
+                               it. */
     int64_t first_tree;     /* global index of this forest's tree 0 (for tree-sharded fits;
                                tree t uses random counters of tree first_tree + t). >= 0 */
 } aiwcrf_fit_params;
@@ -251,11 +254,18 @@ int aiwcrf_surrogate_free(aiwcrf_surrogate *surrogate);
  *  - Refit: rows appended with aiwcrf_server_append are held on the host. Every refit_every
  *    completed requests (and on aiwcrf_server_refit) a refit thread moves refit_rows of them
  *    (all when 0) into the training set, fits a new forest with the creation's fit parameters on
- *    its own stream, and swaps it in. Each batch uses the forest current when it was formed, and
+ *    its own low-priority stream as a background fit (ctas_per_sm = 1, the same forest), and
+ *    swaps it in. Each batch uses the forest current when it was formed, and
  *    each result reports that forest's generation (0 = the forest fitted at creation). A result
  *    equals aiwcrf_select_device on a forest fitted by aiwcrf_fit on the same rows.
  * Host pointers throughout; the server copies what it keeps. The device is the calling thread's
- * current device at creation. */
+ * current device at creation.
+ * The GPU runs the server's n_streams + 1 streams, and any other stream of the process, on a
+ * fixed number of hardware queues (CUDA_DEVICE_MAX_CONNECTIONS, 8 unless set in the process
+ * environment before CUDA initialises). A selection stream that shares a queue with the refit
+ * stream waits in order behind the refit's queued kernels; a refit enqueues one tree level at a
+ * time to bound that wait, and a process that serves while refitting should set
+ * CUDA_DEVICE_MAX_CONNECTIONS=32. */
 typedef struct aiwcrf_server aiwcrf_server;
 
 typedef struct {
@@ -348,6 +358,26 @@ int aiwcrf_server_run_load(aiwcrf_server *server, const float *pool, int64_t poo
                            int64_t n_requests, double rate_per_s, uint64_t seed, int32_t timeout_ms,
                            int32_t *best, int64_t *generation, int64_t *latency_ns,
                            aiwcrf_load_report *report);
+
+/* Trace of the most recent batches and refits (steady-clock nanoseconds, oldest first): the
+ * server keeps the last 65,536 batches and 256 refits. A batch was formed (requests taken from
+ * the queue), enqueued (its copies and kernel handed to the stream) and done (completion seen by
+ * the dispatcher). A refit started (rows taken), staged its rows on the device, finished the fit
+ * and swapped the forest in. */
+typedef struct {
+    int64_t t_formed_ns, t_enqueued_ns, t_done_ns;
+    int32_t kernels, generation;
+} aiwcrf_batch_trace;
+
+typedef struct {
+    int64_t t_start_ns, t_staged_ns, t_fitted_ns, t_swapped_ns;
+    int64_t rows, generation;
+} aiwcrf_refit_trace;
+
+/* Copies up to cap batch records into batches and up to rcap refit records into refits (either
+ * may be NULL with cap 0); *n and *rn receive the numbers copied. */
+int aiwcrf_server_trace(aiwcrf_server *server, aiwcrf_batch_trace *batches, int64_t cap, int64_t *n,
+                        aiwcrf_refit_trace *refits, int64_t rcap, int64_t *rn);
 
 /* Stop the dispatcher and refit threads (queued requests fail with AIWCRF_E_INVALID_ARG; batches
  * in flight complete first) and free everything. */

@@ -29,7 +29,7 @@ class AiwcrfError(RuntimeError):
 class FitParams(C.Structure):
     _fields_ = [("num_trees", C.c_int32), ("mtry", C.c_int32), ("min_node_size", C.c_int32),
                 ("max_depth", C.c_int32), ("seed", C.c_uint64), ("bootstrap", C.c_int32),
-                ("reserved", C.c_int32), ("first_tree", C.c_int64)]
+                ("ctas_per_sm", C.c_int32), ("first_tree", C.c_int64)]
 
 
 class SurrogateParams(C.Structure):
@@ -81,6 +81,16 @@ class LoadReport(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BatchTrace(C.Structure):
+    _fields_ = [("t_formed_ns", C.c_int64), ("t_enqueued_ns", C.c_int64), ("t_done_ns", C.c_int64),
+                ("kernels", C.c_int32), ("generation", C.c_int32)]
+
+
+class RefitTrace(C.Structure):
+    _fields_ = [("t_start_ns", C.c_int64), ("t_staged_ns", C.c_int64), ("t_fitted_ns", C.c_int64),
+                ("t_swapped_ns", C.c_int64), ("rows", C.c_int64), ("generation", C.c_int64)]
+
+
 EXPORTS = ["aiwcrf_fit", "aiwcrf_fit_subsets", "aiwcrf_predict", "aiwcrf_predict_sum", "aiwcrf_oob",
            "aiwcrf_round_mean", "aiwcrf_select_device", "aiwcrf_forest_stats", "aiwcrf_forest_info",
            "aiwcrf_forest_serialize", "aiwcrf_forest_deserialize", "aiwcrf_forest_free",
@@ -91,7 +101,7 @@ EXPORTS = ["aiwcrf_fit", "aiwcrf_fit_subsets", "aiwcrf_predict", "aiwcrf_predict
            "aiwcrf_surrogate_stats", "aiwcrf_surrogate_num_params", "aiwcrf_surrogate_free",
            "aiwcrf_server_create", "aiwcrf_server_submit", "aiwcrf_server_wait", "aiwcrf_server_append",
            "aiwcrf_server_refit", "aiwcrf_server_pause", "aiwcrf_server_stats", "aiwcrf_server_run_load",
-           "aiwcrf_server_destroy"]
+           "aiwcrf_server_trace", "aiwcrf_server_destroy"]
 
 _lib = None
 _lock = threading.Lock()
@@ -151,6 +161,8 @@ def load():
         L.aiwcrf_server_run_load.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp, C.c_int64, C.c_double,
                                              C.c_uint64, C.c_int32, _vp, _vp, _vp, C.POINTER(LoadReport)]
         L.aiwcrf_server_destroy.argtypes = [_vp]
+        L.aiwcrf_server_trace.argtypes = [_vp, _vp, C.c_int64, C.POINTER(C.c_int64), _vp, C.c_int64,
+                                          C.POINTER(C.c_int64)]
         for name in EXPORTS:
             if name not in ("aiwcrf_last_error", "aiwcrf_profile_name", "aiwcrf_profile_num_classes",
                             "aiwcrf_launch_count", "aiwcrf_surrogate_num_params"):
@@ -437,6 +449,16 @@ class Server:
         _check(load().aiwcrf_server_stats(self.handle, C.byref(c)))
         return c.as_dict()
 
+    def trace(self):
+        """(batches, refits) as numpy structured arrays, oldest first."""
+        bt = (BatchTrace * 65536)()
+        rt = (RefitTrace * 256)()
+        n, rn = C.c_int64(), C.c_int64()
+        _check(load().aiwcrf_server_trace(self.handle, bt, 65536, C.byref(n), rt, 256, C.byref(rn)))
+        b = np.ctypeslib.as_array(bt)[:n.value].copy()
+        r = np.ctypeslib.as_array(rt)[:rn.value].copy()
+        return b, r
+
     def run_load(self, pool: np.ndarray, first, n_kernels, size_class, rate_per_s: float, seed: int = 1,
                  timeout_ms: int = 120000):
         """Open-loop Poisson load. Returns (report dict, best[sum K], generation[n], latency_ns[n])."""
@@ -480,8 +502,8 @@ def aiwcrf_launch_count() -> int:
 
 
 def params(num_trees: int, mtry: int, min_node_size: int, max_depth: int = 0, seed: int = 156,
-           bootstrap: bool = True, first_tree: int = 0) -> FitParams:
-    return FitParams(num_trees, mtry, min_node_size, max_depth, seed, 1 if bootstrap else 0, 0, first_tree)
+           bootstrap: bool = True, first_tree: int = 0, ctas_per_sm: int = 0) -> FitParams:
+    return FitParams(num_trees, mtry, min_node_size, max_depth, seed, 1 if bootstrap else 0, ctas_per_sm, first_tree)
 
 
 def decode_forest(blob: bytes) -> dict:

@@ -282,7 +282,7 @@ int check_params(const aiwcrf_fit_params *p, int64_t n_rows, int32_t n_features)
     if (p->min_node_size < 1) return fail(AIWCRF_E_INVALID_ARG, "min_node_size must be >= 1");
     if (p->max_depth < 0) return fail(AIWCRF_E_INVALID_ARG, "max_depth must be >= 0");
     if (p->bootstrap != 0 && p->bootstrap != 1) return fail(AIWCRF_E_INVALID_ARG, "bootstrap must be 0 or 1");
-    if (p->reserved != 0) return fail(AIWCRF_E_INVALID_ARG, "reserved must be 0");
+    if (p->ctas_per_sm < 0 || p->ctas_per_sm > 3) return fail(AIWCRF_E_INVALID_ARG, "ctas_per_sm must be 0..3");
     if (p->first_tree < 0 || p->first_tree + p->num_trees > 0xFFFFFFFFll)
         return fail(AIWCRF_E_INVALID_ARG, "first_tree out of range");
     if (n_rows < 1) return fail(AIWCRF_E_INVALID_ARG, "n_rows must be >= 1");

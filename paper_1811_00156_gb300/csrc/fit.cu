@@ -1213,6 +1213,8 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     const size_t budget = (size_t)4 << 30;                      // level-table budget per fit
     int dev_sms = 0;
     AIWCRF_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, device));
+    // CTAs per SM of the grid-stride level, scan and finalize kernels (a background fit takes fewer)
+    const int64_t cps = p.ctas_per_sm > 0 ? p.ctas_per_sm : 3;
 
     size_t node_cap = 0, packed_cap = 0;
     NodeRec *nodes_cur = nullptr, *nodes_nxt = nullptr;
@@ -1327,8 +1329,10 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     int64_t C_known = T;                 // node count at the start of the next chunk (exact)
     uint64_t packed_known = 0;           // finished nodes before it (exact)
     while (C_known > 0) {
-        // largest chunk whose bound fits the budget
-        int chunk = 8;
+        // largest chunk whose bound fits the budget; a background fit enqueues one level at a
+        // time, so that work of other streams sharing a hardware queue with it waits at most
+        // one level behind it
+        int chunk = p.ctas_per_sm > 0 ? 1 : 8;
         auto bound = [&](int k) { return std::min<int64_t>(C_known << k, C_max); };
         while (chunk > 1 && (size_t)bound(chunk) * per_node_bytes > budget) chunk >>= 1;
         if ((rc = grow_tables((size_t)bound(chunk), (uint32_t)C_known)) != AIWCRF_OK) return rc;
@@ -1342,7 +1346,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
             la.nodes = nodes_cur; la.rows_in = rin; la.rows_out = rout; la.depth = depth; la.res = res;
             {
                 la.list = big_a; la.list_n = &d_cnt->n_big;
-                const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(Cb, 3 * dev_sms));
+                const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(Cb, cps * dev_sms));
                 prof_begin(s, kProfLevelBig);
                 if (rank8) level_big_kernel<uint8_t><<<grid, kBigThreads, big_smem, s>>>(la, bin_cap);
                 else level_big_kernel<uint16_t><<<grid, kBigThreads, big_smem, s>>>(la, bin_cap);
@@ -1352,14 +1356,14 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
             {
                 la.list = small_a; la.list_n = &d_cnt->n_small;
                 const int64_t wpb = kSmallThreads / 32;
-                const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + wpb - 1) / wpb, 3 * dev_sms));
+                const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + wpb - 1) / wpb, cps * dev_sms));
                 prof_begin(s, kProfLevelSmall);
                 if (rank8) level_small_kernel<uint8_t><<<grid, kSmallThreads, 0, s>>>(la);
                 else level_small_kernel<uint16_t><<<grid, kSmallThreads, 0, s>>>(la);
                 AIWCRF_LAUNCH_CHECK("level_small_kernel");
                 prof_end(s, kProfLevelSmall);
             }
-            const unsigned sgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + kScanTile - 1) / kScanTile, 2 * dev_sms));
+            const unsigned sgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + kScanTile - 1) / kScanTile, std::min<int64_t>(2, cps) * dev_sms));
             prof_begin(s, kProfScan);
             scan_reduce_kernel<<<sgrid, kScanThreads, 0, s>>>(res, d_cnt, block_sums);
             scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(block_sums, 0, d_cnt);
@@ -1373,7 +1377,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
             fa.nodes = nodes_cur; fa.res = res; fa.excl = excl; fa.tree_off = tree_off; fa.tree_base = tree_base;
             fa.cnt = d_cnt; fa.next = nodes_nxt; fa.small_list = small_a; fa.big_list = big_a;
             fa.packed = packed; fa.stats = d_stats;
-            const unsigned fgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + 255) / 256, 8 * dev_sms));
+            const unsigned fgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + 255) / 256, (cps == 3 ? 8 : cps) * dev_sms));
             prof_begin(s, kProfFinalize);
             finalize_kernel<<<fgrid, 256, 0, s>>>(fa);
             AIWCRF_LAUNCH_CHECK("finalize_kernel");

@@ -12,7 +12,8 @@
 //    allocation: a request is admitted into a batch only while its bytes fit the arena's free
 //    space, so the server's device footprint is fixed at creation;
 //  - a refit thread fits new forests from the training rows plus appended rows on its own
-//    stream and swaps them in; each batch holds a reference to the forest it was formed with,
+//    low-priority stream, as a background fit (one level-kernel CTA per SM, so that selection
+//    CTAs always find registers on every SM), and swaps them in; each batch holds a reference to the forest it was formed with,
 //    and a forest is freed (stream-ordered) only after the last batch using it completed.
 //
 // Selection kernel (serve_select_kernel): one CTA per (kernel, chunk of 32 trees). It codes the
@@ -346,6 +347,7 @@ struct Slot {
     bool busy = false;
     int64_t off = -1, bytes = 0;
     int32_t Kb = 0;
+    int64_t t_formed = 0, t_enqueued = 0;
     std::shared_ptr<Model> model;
     std::vector<std::shared_ptr<Request>> reqs;
 };
@@ -398,11 +400,16 @@ struct aiwcrf_server {
     std::vector<int64_t> ytrain, yapp;
     cudaStream_t refit_stream = nullptr;
 
-    std::mutex gmu;                       // forests waiting to be freed
+    std::mutex gmu;                       // forests waiting to be freed (on the refit stream)
     std::vector<aiwcrf_forest *> graveyard;
-    cudaStream_t free_stream = nullptr;
 
     std::thread disp, refitter;
+
+    // traces (under mu)
+    static constexpr int64_t kBatchRing = 65536, kRefitRing = 256;
+    std::vector<aiwcrf_batch_trace> btrace = std::vector<aiwcrf_batch_trace>((size_t)kBatchRing);
+    std::vector<aiwcrf_refit_trace> rtrace = std::vector<aiwcrf_refit_trace>((size_t)kRefitRing);
+    int64_t n_btrace = 0, n_rtrace = 0;
 
     int64_t req_bytes(int64_t K) const
     {
@@ -434,12 +441,14 @@ struct aiwcrf_server {
             std::lock_guard<std::mutex> lk(gmu);
             g.swap(graveyard);
         }
-        for (auto f : g) forest_release_async(f, free_stream);
+        for (auto f : g) forest_release_async(f, refit_stream);
     }
 
     // fit a forest on the current training rows (refit thread or creation)
-    int fit_training(aiwcrf_forest **out, int64_t *rows)
+    int fit_training(aiwcrf_forest **out, int64_t *rows, bool background, int64_t *t_staged = nullptr)
     {
+        aiwcrf_fit_params fp_bg = fp;
+        fp_bg.ctas_per_sm = 1;            // refits leave every SM room for selection batches
         const int64_t N = (int64_t)ytrain.size();
         std::vector<float> X((size_t)F * (size_t)N);
         for (int32_t f = 0; f < F; ++f) std::copy(xcols[(size_t)f].begin(), xcols[(size_t)f].end(), X.begin() + (size_t)f * (size_t)N);
@@ -450,7 +459,11 @@ struct aiwcrf_server {
         if (e == cudaSuccess) e = cudaMemcpyAsync(dX, X.data(), sizeof(float) * X.size(), cudaMemcpyHostToDevice, refit_stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dy, ytrain.data(), sizeof(int64_t) * (size_t)N, cudaMemcpyHostToDevice, refit_stream);
         int rc = e == cudaSuccess ? AIWCRF_OK : cuda_fail(e, "staging the training rows");
-        if (rc == AIWCRF_OK) rc = aiwcrf_fit(&fp, dX, dy, N, F, refit_stream, out);
+        if (t_staged) {
+            cudaStreamSynchronize(refit_stream);
+            *t_staged = now_ns();
+        }
+        if (rc == AIWCRF_OK) rc = aiwcrf_fit(background ? &fp_bg : &fp, dX, dy, N, F, refit_stream, out);
         if (dX) cudaFreeAsync(dX, refit_stream);
         if (dy) cudaFreeAsync(dy, refit_stream);
         cudaStreamSynchronize(refit_stream);
@@ -505,6 +518,12 @@ struct aiwcrf_server {
         bool want_refit = false;
         {
             std::lock_guard<std::mutex> lk(mu);
+            aiwcrf_batch_trace &tr = btrace[(size_t)(n_btrace++ % kBatchRing)];
+            tr.t_formed_ns = sl.t_formed;
+            tr.t_enqueued_ns = sl.t_enqueued;
+            tr.t_done_ns = t;
+            tr.kernels = sl.Kb;
+            tr.generation = (int32_t)gen;
             arena.release(sl.off, sl.bytes);
             st.completed += (int64_t)sl.reqs.size();
             if (status != AIWCRF_OK) st.failed += (int64_t)sl.reqs.size();
@@ -539,6 +558,7 @@ struct aiwcrf_server {
             e = cudaErrorLaunchFailure;
         if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_out, d_pred, out_bytes, cudaMemcpyDeviceToHost, sl.s);
         if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.s);
+        sl.t_enqueued = now_ns();
         sl.busy = true;
         if (e != cudaSuccess) {
             cudaStreamSynchronize(sl.s);
@@ -595,6 +615,7 @@ struct aiwcrf_server {
                 if (n > 0) {
                     if (cut) ++st.arena_waits;
                     Slot &sl = *free_slot;
+                    sl.t_formed = now_ns();
                     sl.Kb = (int32_t)Kb;
                     sl.bytes = req_bytes(Kb);
                     sl.off = arena.alloc(sl.bytes);
@@ -668,8 +689,10 @@ struct aiwcrf_server {
             aiwcrf_forest *f = nullptr;
             int64_t rows = 0;
             const int64_t t_fit = now_ns();
-            const int rc = fit_training(&f, &rows);
-            const int64_t us = (now_ns() - t_fit) / 1000;
+            int64_t t_staged = 0;
+            const int rc = fit_training(&f, &rows, true, &t_staged);
+            const int64_t t_fitted = now_ns();
+            const int64_t us = (t_fitted - t_fit) / 1000;
             {
                 std::lock_guard<std::mutex> g(mu);
                 st.refit_us_total += us;
@@ -686,6 +709,13 @@ struct aiwcrf_server {
                     st.training_rows = rows;
                     st.forest_bytes = current->bytes;
                     ++st.refits;
+                    aiwcrf_refit_trace &tr = rtrace[(size_t)(n_rtrace++ % kRefitRing)];
+                    tr.t_start_ns = t_fit;
+                    tr.t_staged_ns = t_staged;
+                    tr.t_fitted_ns = t_fitted;
+                    tr.t_swapped_ns = now_ns();
+                    tr.rows = rows;
+                    tr.generation = gen;
                 }
                 old.reset();
             } else {
@@ -737,7 +767,7 @@ struct aiwcrf_server {
         if (refitter.joinable()) refitter.join();
         current.reset();
         drain_graveyard();
-        if (free_stream) cudaStreamSynchronize(free_stream);
+        if (refit_stream) cudaStreamSynchronize(refit_stream);
         for (auto &sl : slots) {
             if (sl.s) cudaStreamDestroy(sl.s);
             if (sl.ev) cudaEventDestroy(sl.ev);
@@ -749,7 +779,6 @@ struct aiwcrf_server {
         if (d_arena) cudaFree(d_arena);
         if (d_dev) cudaFree(d_dev);
         if (refit_stream) cudaStreamDestroy(refit_stream);
-        if (free_stream) cudaStreamDestroy(free_stream);
     }
 };
 
@@ -815,7 +844,6 @@ int aiwcrf_server_create(const aiwcrf_server_params *params, const aiwcrf_fit_pa
     int prio_low = 0, prio_high = 0;
     e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->refit_stream, cudaStreamNonBlocking, prio_low);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->free_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_dev, sizeof(int32_t) * D);
     if (e == cudaSuccess) e = cudaMemcpy(s->d_dev, device_ids, sizeof(int32_t) * D, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_arena, (size_t)p.arena_bytes);
@@ -837,10 +865,19 @@ int aiwcrf_server_create(const aiwcrf_server_params *params, const aiwcrf_fit_pa
     }
     s->arena.init(p.arena_bytes);
     s->st.arena_bytes = p.arena_bytes;
+    // load both walk variants now: a refit can switch between them, and a kernel's first
+    // launch would otherwise load its code in the middle of serving
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, serve_select_kernel<true>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, serve_select_kernel<false>);
+    if (e != cudaSuccess) {
+        cuda_fail(e, "loading the selection kernels");
+        return bail(AIWCRF_E_CUDA);
+    }
 
     aiwcrf_forest *f = nullptr;
     int64_t rows = 0;
-    rc = s->fit_training(&f, &rows);
+    rc = s->fit_training(&f, &rows, false);
     if (rc) return bail(rc);
     s->current = s->wrap(f, 0, rows);
     s->st.generation = 0;
@@ -1066,6 +1103,23 @@ int aiwcrf_server_run_load(aiwcrf_server *server, const float *pool, int64_t poo
     report->rejected = rejected;
     if (timed_out) return fail(AIWCRF_E_TIMEOUT, "requests still running at the time limit");
     if (run->first_error != AIWCRF_OK) return fail(run->first_error, "a request failed");
+    return AIWCRF_OK;
+}
+
+int aiwcrf_server_trace(aiwcrf_server *server, aiwcrf_batch_trace *batches, int64_t cap, int64_t *n,
+                        aiwcrf_refit_trace *refits, int64_t rcap, int64_t *rn)
+{
+    if (!server || !n || !rn || cap < 0 || rcap < 0 || (cap && !batches) || (rcap && !refits))
+        return fail(AIWCRF_E_INVALID_ARG, "bad trace arguments");
+    std::lock_guard<std::mutex> lk(server->mu);
+    auto copy = [](const auto &ring, int64_t total, int64_t ring_n, auto *dst, int64_t want) {
+        const int64_t have = std::min(total, ring_n);
+        const int64_t m = std::min(have, want);
+        for (int64_t i = 0; i < m; ++i) dst[i] = ring[(size_t)((total - m + i) % ring_n)];
+        return m;
+    };
+    *n = copy(server->btrace, server->n_btrace, aiwcrf_server::kBatchRing, batches, cap);
+    *rn = copy(server->rtrace, server->n_rtrace, aiwcrf_server::kRefitRing, refits, rcap);
     return AIWCRF_OK;
 }
 

@@ -167,6 +167,17 @@ def test_host_buffers_and_serialization_roundtrip():
     assert np.array_equal(out, gpu_predict(f_dev, Xq))
 
 
+def test_background_fit_grids_give_the_same_forest():
+    # the level kernels' grid only decides which CTA takes which node: fewer CTAs per SM (a
+    # background fit) must give the same bytes, on the big-node and the small-node paths
+    wl = synth.scaled_forest_workload(replicates=4)
+    full = A.aiwcrf_fit(A.params(24, 10, 5), dev(wl.X), dev(wl.y)).serialize()
+    for cps in (1, 2, 3):
+        assert A.aiwcrf_fit(A.params(24, 10, 5, ctas_per_sm=cps), dev(wl.X), dev(wl.y)).serialize() == full
+    with pytest.raises(A.AiwcrfError):
+        A.aiwcrf_fit(A.params(4, 10, 5, ctas_per_sm=4), dev(wl.X), dev(wl.y))
+
+
 def test_tree_sharding_and_partial_sums():
     wl = synth.small_case(8, 1500, 32, card=50)
     T = 12
