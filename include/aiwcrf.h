@@ -383,6 +383,41 @@ int aiwcrf_server_trace(aiwcrf_server *server, aiwcrf_batch_trace *batches, int6
  * in flight complete first) and free everything. */
 int aiwcrf_server_destroy(aiwcrf_server *server);
 
+/* Device selection through the surrogate with the forest as fallback and judge (the paper has no
+ * surrogate; its selection of Sec. VI queries the forest). For each kernel k the D queries
+ * (k, device_ids[j]) are predicted by the surrogate; the kernel falls back to the forest when
+ * any of its queries
+ *  - has a feature outside [smallest, largest] of the forest's training values of that column,
+ *    or NaN (with gate->ood = 1), or
+ *  - has a high ensemble variance over the forest's first var_trees trees: with v_t the leaf
+ *    values (Q32.32) and P = sum v_t, V = var_trees * sum v_t^2 - P^2 (exact), the test is
+ *    V > floor(var_threshold * 2^64) * var_trees^2, i.e. the variance of the prefix's
+ *    predictions exceeds var_threshold (log10 s)^2.
+ * A kernel that falls back gets exactly aiwcrf_select_device's device and the forest's
+ * predictions (converted to float log10 s); the others get the argmin of the surrogate's
+ * predictions (ties: lower device id). kfeat ((F-2) x K), out_best (K), out_pred (K x D float,
+ * or NULL) and out_fallback (K bytes, 1 = forest, or NULL) are device memory; device_ids and
+ * stats (or NULL) are host memory. The call synchronises its stream. */
+typedef struct {
+    int32_t var_trees;      /* 1..num_trees (32) */
+    float var_threshold;    /* (log10 s)^2, 0 <= var_threshold < 2^20 (0.01) */
+    int32_t ood;            /* 1: out-of-range features fall back (1) */
+    int32_t reserved;       /* must be 0 */
+} aiwcrf_gate_params;
+
+typedef struct {
+    int64_t kernels;
+    int64_t fallback;       /* kernels answered by the forest */
+    int64_t fallback_ood;   /* ... with an out-of-range feature */
+    int64_t fallback_var;   /* ... with a high prefix variance */
+} aiwcrf_gate_stats;
+
+int aiwcrf_select_device_gated(const aiwcrf_forest *forest, const aiwcrf_surrogate *surrogate,
+                               const aiwcrf_gate_params *gate, const float *kfeat, int32_t n_kernels,
+                               int32_t size_class, const int32_t *device_ids, int32_t n_devices,
+                               int32_t *out_best, float *out_pred, uint8_t *out_fallback,
+                               aiwcrf_gate_stats *stats, void *cuda_stream);
+
 /* Counters of the fit that produced the forest (zeros for a deserialized forest). */
 int aiwcrf_forest_stats(const aiwcrf_forest *forest, aiwcrf_fit_stats *out);
 

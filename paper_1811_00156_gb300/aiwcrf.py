@@ -81,6 +81,18 @@ class LoadReport(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class GateParams(C.Structure):
+    _fields_ = [("var_trees", C.c_int32), ("var_threshold", C.c_float), ("ood", C.c_int32), ("reserved", C.c_int32)]
+
+
+class GateStats(C.Structure):
+    _fields_ = [("kernels", C.c_int64), ("fallback", C.c_int64), ("fallback_ood", C.c_int64),
+                ("fallback_var", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class BatchTrace(C.Structure):
     _fields_ = [("t_formed_ns", C.c_int64), ("t_enqueued_ns", C.c_int64), ("t_done_ns", C.c_int64),
                 ("kernels", C.c_int32), ("generation", C.c_int32)]
@@ -101,7 +113,7 @@ EXPORTS = ["aiwcrf_fit", "aiwcrf_fit_subsets", "aiwcrf_predict", "aiwcrf_predict
            "aiwcrf_surrogate_stats", "aiwcrf_surrogate_num_params", "aiwcrf_surrogate_free",
            "aiwcrf_server_create", "aiwcrf_server_submit", "aiwcrf_server_wait", "aiwcrf_server_append",
            "aiwcrf_server_refit", "aiwcrf_server_pause", "aiwcrf_server_stats", "aiwcrf_server_run_load",
-           "aiwcrf_server_trace", "aiwcrf_server_destroy"]
+           "aiwcrf_server_trace", "aiwcrf_server_destroy", "aiwcrf_select_device_gated"]
 
 _lib = None
 _lock = threading.Lock()
@@ -161,6 +173,8 @@ def load():
         L.aiwcrf_server_run_load.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp, C.c_int64, C.c_double,
                                              C.c_uint64, C.c_int32, _vp, _vp, _vp, C.POINTER(LoadReport)]
         L.aiwcrf_server_destroy.argtypes = [_vp]
+        L.aiwcrf_select_device_gated.argtypes = [_vp, _vp, C.POINTER(GateParams), _vp, C.c_int32, C.c_int32, _vp,
+                                                 C.c_int32, _vp, _vp, _vp, C.POINTER(GateStats), _vp]
         L.aiwcrf_server_trace.argtypes = [_vp, _vp, C.c_int64, C.POINTER(C.c_int64), _vp, C.c_int64,
                                           C.POINTER(C.c_int64)]
         for name in EXPORTS:
@@ -475,6 +489,22 @@ class Server:
                                              nk.ctypes.data, sc.ctypes.data, n, float(rate_per_s), seed, timeout_ms,
                                              best.ctypes.data, gen.ctypes.data, lat.ctypes.data, C.byref(rep)))
         return rep.as_dict(), best, gen, lat
+
+
+def gate_params(var_trees: int = 32, var_threshold: float = 0.01, ood: bool = True) -> GateParams:
+    return GateParams(var_trees, var_threshold, 1 if ood else 0, 0)
+
+
+def aiwcrf_select_device_gated(forest: Forest, surrogate, gate: GateParams, kfeat, size_class: int, device_ids,
+                               out_best, out_pred=None, out_fallback=None, stream=None) -> dict:
+    """Surrogate device selection with forest fallback (device tensors); returns the gate counters."""
+    Fm2, K = _shape(kfeat)
+    dev = np.ascontiguousarray(device_ids, dtype=np.int32)
+    st = GateStats()
+    _check(load().aiwcrf_select_device_gated(forest.handle, surrogate.handle, C.byref(gate), _ptr(kfeat), K,
+                                             int(size_class), dev.ctypes.data, int(dev.size), _ptr(out_best),
+                                             _ptr(out_pred), _ptr(out_fallback), C.byref(st), _stream(stream)))
+    return st.as_dict()
 
 
 def aiwcrf_forest_deserialize(blob: bytes) -> Forest:

@@ -1,0 +1,225 @@
+// gate.cu -- device selection through the learned surrogate, with the forest as fallback and as
+// the judge of its answers (the selection of Sec. VI, made cheaper; the paper's model is the
+// forest alone).
+//
+// Pipeline on the caller's stream:
+//  1. expand the K kernels into K x D queries (kernel features, device id, size class);
+//  2. surrogate inference (fused tcgen05 kernel) for every query;
+//  3. exact ensemble-variance numerators over the forest's first var_trees trees;
+//  4. gate_kernel, one warp per kernel: out-of-range test of every feature of its D queries
+//     against the forest's value tables, the variance test, the surrogate argmin, and the
+//     kernels that fall back appended to a list;
+//  5. the fallback kernels' queries gathered, predicted by the whole forest, and their device
+//     chosen from the exact int64 predictions (fix_kernel).
+// Which kernel lands where in the fallback list depends on the order of the atomics, but every
+// kernel's result depends only on its own queries.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace aiwcrf {
+
+__global__ void gate_kernel(const float *__restrict__ q, int64_t Qn, int F, int D, const float *__restrict__ fvals,
+                            int64_t fstride, const uint32_t *__restrict__ fcard, const uint64_t *__restrict__ var,
+                            uint64_t thr_lo, uint64_t thr_hi, int ood, const float *__restrict__ sur,
+                            const int32_t *__restrict__ dev, int K, uint8_t *flag, int32_t *best, float *pred,
+                            int32_t *list, unsigned long long *counts)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (k >= K) return;                        // warp-uniform
+    const u128_t thr = ((u128_t)thr_hi << 64) | thr_lo;
+    bool o = false, v = false;
+    float bs = INFINITY;
+    int32_t bd = INT_MAX;
+    for (int j = lane; j < D; j += 32) {
+        const int64_t i = k * D + j;
+        if (ood) {
+            for (int f = 0; f < F; ++f) {
+                const float x = q[(size_t)f * (size_t)Qn + (size_t)i];
+                const float *V = fvals + (size_t)f * (size_t)fstride;
+                const uint32_t c = fcard[f];
+                if (c == 0 || !(x >= V[0] && x <= V[c - 1])) o = true;
+            }
+        }
+        const u128_t Vn = ((u128_t)var[2 * i + 1] << 64) | var[2 * i];
+        if (Vn > thr) v = true;
+        const float sv = sur[i];
+        if (pred) pred[i] = sv;
+        const int32_t id = dev[j];
+        if (sv < bs || (sv == bs && id < bd) || bd == INT_MAX) { bs = sv; bd = id; }
+    }
+#pragma unroll
+    for (int w = 16; w; w >>= 1) {
+        const float os = __shfl_xor_sync(0xFFFFFFFFu, bs, w);
+        const int32_t od = __shfl_xor_sync(0xFFFFFFFFu, bd, w);
+        if (od != INT_MAX && (bd == INT_MAX || os < bs || (os == bs && od < bd))) { bs = os; bd = od; }
+    }
+    const bool any_o = __any_sync(0xFFFFFFFFu, o), any_v = __any_sync(0xFFFFFFFFu, v);
+    if (lane == 0) {
+        const bool fb = any_o || any_v;
+        flag[k] = fb ? 1 : 0;
+        best[k] = bd;
+        if (fb) {
+            const unsigned long long slot = atomicAdd(&counts[0], 1ull);
+            list[slot] = (int32_t)k;
+            if (any_o) atomicAdd(&counts[1], 1ull);
+            if (any_v) atomicAdd(&counts[2], 1ull);
+        }
+    }
+}
+
+// fq (F x n*D): the queries of the listed kernels
+__global__ void gather_kernel(const float *__restrict__ q, int64_t Qn, int F, int D, const int32_t *__restrict__ list,
+                              int64_t n, float *__restrict__ fq)
+{
+    const int64_t Qf = n * D;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int f = blockIdx.y;
+    if (i >= Qf || f >= F) return;
+    const int64_t k = list[i / D];
+    const int j = (int)(i % D);
+    fq[(size_t)f * (size_t)Qf + (size_t)i] = q[(size_t)f * (size_t)Qn + (size_t)(k * D + j)];
+}
+
+// one warp per listed kernel: the forest's exact choice and predictions
+__global__ void fix_kernel(const int64_t *__restrict__ fpred, const int32_t *__restrict__ list, int64_t n, int D,
+                           const int32_t *__restrict__ dev, int32_t *best, float *pred)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    const int64_t k = list[i];
+    int64_t bp = LLONG_MAX;
+    int32_t bd = INT_MAX;
+    for (int j = lane; j < D; j += 32) {
+        const int64_t p = fpred[i * D + j];
+        if (pred) pred[k * D + j] = (float)((double)p * 0x1p-32);
+        const int32_t id = dev[j];
+        if (p < bp || (p == bp && id < bd)) { bp = p; bd = id; }
+    }
+#pragma unroll
+    for (int w = 16; w; w >>= 1) {
+        const int64_t op = __shfl_xor_sync(0xFFFFFFFFu, bp, w);
+        const int32_t od = __shfl_xor_sync(0xFFFFFFFFu, bd, w);
+        if (op < bp || (op == bp && od < bd)) { bp = op; bd = od; }
+    }
+    if (lane == 0) best[k] = bd;
+}
+
+namespace {
+
+size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+bool on_device(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice;
+}
+
+}  // namespace
+}  // namespace aiwcrf
+
+using namespace aiwcrf;
+
+extern "C" int aiwcrf_select_device_gated(const aiwcrf_forest *forest, const aiwcrf_surrogate *surrogate,
+                                          const aiwcrf_gate_params *gate, const float *kfeat, int32_t n_kernels,
+                                          int32_t size_class, const int32_t *device_ids, int32_t n_devices,
+                                          int32_t *out_best, float *out_pred, uint8_t *out_fallback,
+                                          aiwcrf_gate_stats *stats, void *cuda_stream)
+{
+    if (!forest || !surrogate || !gate || !device_ids)
+        return fail(AIWCRF_E_INVALID_ARG, "forest, surrogate, gate and device_ids must not be NULL");
+    if (n_kernels < 0 || n_devices < 1) return fail(AIWCRF_E_INVALID_ARG, "n_kernels >= 0 and n_devices >= 1");
+    if (gate->var_trees < 1 || gate->var_trees > forest->T || !(gate->var_threshold >= 0.0f) ||
+        !(gate->var_threshold < 1048576.0f) || (gate->ood != 0 && gate->ood != 1) || gate->reserved != 0)
+        return fail(AIWCRF_E_INVALID_ARG, "gate parameters out of range");
+    if (stats) *stats = aiwcrf_gate_stats{n_kernels, 0, 0, 0};
+    if (n_kernels == 0) return AIWCRF_OK;
+    if (!kfeat || !out_best) return fail(AIWCRF_E_INVALID_ARG, "kfeat and out_best must not be NULL");
+    if (!on_device(kfeat) || !on_device(out_best) || (out_pred && !on_device(out_pred)) ||
+        (out_fallback && !on_device(out_fallback)))
+        return fail(AIWCRF_E_BAD_POINTER, "kfeat and the outputs must be device memory");
+    const cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int F = forest->F, D = n_devices, K = n_kernels;
+    const int64_t Qn = (int64_t)K * D;
+    keep_pool_memory(forest->device);
+
+    // threshold numerator floor(thr * 2^64) * var_trees^2, exact: thr = m * 2^(ex - 24) with a
+    // 24-bit integer m, and thr < 2^20 keeps the product below 2^124
+    int ex = 0;
+    const float mf = std::frexp(gate->var_threshold, &ex);
+    const uint64_t m = (uint64_t)std::ldexp(mf, 24);
+    const int sh = ex - 24 + 64;
+    const u128_t thr_q = sh >= 0 ? (u128_t)m << sh : (sh > -64 ? (u128_t)(m >> -sh) : (u128_t)0);
+    const u128_t thr = thr_q * (u128_t)gate->var_trees * (u128_t)gate->var_trees;
+
+    // scratch: device ids, queries, surrogate outputs, variance numerators, query codes, flags,
+    // list, counters, error flag; then the fallback's gathered queries and predictions
+    const size_t b_dev = a256(4 * (size_t)D), b_q = a256(4 * (size_t)F * (size_t)Qn), b_sur = a256(4 * (size_t)Qn);
+    const size_t b_var = a256(16 * (size_t)Qn), b_codes = a256(predict_codes_bytes(forest, Qn));
+    const size_t b_flag = a256((size_t)K), b_list = a256(4 * (size_t)K), b_cnt = a256(8 * 4);
+    const size_t b_fp = a256(8 * (size_t)Qn);
+    const size_t total = b_dev + b_q + b_sur + b_var + b_codes + b_flag + b_list + b_cnt + b_q + b_fp;
+    unsigned char *blk = nullptr;
+    if (cudaMallocAsync(&blk, total, s) != cudaSuccess) return fail(AIWCRF_E_OOM, "gated selection scratch");
+    struct Free { unsigned char *p; cudaStream_t s; ~Free() { cudaFreeAsync(p, s); } } fr{blk, s};
+    unsigned char *c = blk;
+    int32_t *d_dev = reinterpret_cast<int32_t *>(c); c += b_dev;
+    float *d_q = reinterpret_cast<float *>(c); c += b_q;
+    float *d_sur = reinterpret_cast<float *>(c); c += b_sur;
+    uint64_t *d_var = reinterpret_cast<uint64_t *>(c); c += b_var;
+    void *d_codes = c; c += b_codes;
+    uint8_t *d_flag = out_fallback ? out_fallback : reinterpret_cast<uint8_t *>(c); c += b_flag;
+    int32_t *d_list = reinterpret_cast<int32_t *>(c); c += b_list;
+    unsigned long long *d_cnt = reinterpret_cast<unsigned long long *>(c);
+    uint32_t *d_err = reinterpret_cast<uint32_t *>(d_cnt + 3); c += b_cnt;
+    float *d_fq = reinterpret_cast<float *>(c); c += b_q;
+    int64_t *d_fpred = reinterpret_cast<int64_t *>(c);
+
+    cudaError_t e = cudaMemcpyAsync(d_dev, device_ids, 4 * (size_t)D, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, 32, s);
+    if (e != cudaSuccess) return cuda_fail(e, "gated selection set-up");
+    int rc;
+    prof_begin(s, kProfSelect);
+    if ((rc = expand_launch(kfeat, K, size_class, d_dev, D, F, d_q, s))) return rc;
+    if ((rc = surrogate_predict_enqueue(surrogate, d_q, Qn, d_sur, d_err, s))) return rc;
+    if ((rc = predict_prefix_var_enqueue(forest, d_q, Qn, gate->var_trees, d_var, s, d_err, d_codes))) return rc;
+    const unsigned gblocks = (unsigned)(((int64_t)K * 32 + 255) / 256);
+    gate_kernel<<<gblocks, 256, 0, s>>>(d_q, Qn, F, D, forest->d_fvals, forest->fstride, forest->d_fcard, d_var,
+                                        (uint64_t)thr, (uint64_t)(thr >> 64), gate->ood, d_sur, d_dev, K, d_flag,
+                                        out_best, out_pred, d_list, d_cnt);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gate_kernel launch");
+    unsigned long long h_cnt[4] = {0, 0, 0, 0};
+    e = cudaMemcpyAsync(h_cnt, d_cnt, 32, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "gated selection");
+    const int64_t n = (int64_t)h_cnt[0];
+    if (n > 0) {
+        const int64_t Qf = n * D;
+        gather_kernel<<<dim3((unsigned)((Qf + 255) / 256), (unsigned)F), 256, 0, s>>>(d_q, Qn, F, D, d_list, n, d_fq);
+        count_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gather_kernel launch");
+        if ((rc = predict_enqueue(forest, d_fq, Qf, nullptr, d_fpred, s, d_err, d_codes))) return rc;
+        fix_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(d_fpred, d_list, n, D, d_dev, out_best, out_pred);
+        count_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "fix_kernel launch");
+    }
+    prof_end(s, kProfSelect);
+    uint32_t h_err = 0;
+    e = cudaMemcpyAsync(&h_err, d_err, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "gated selection");
+    if (h_err & kErrTimeout) return fail(AIWCRF_E_TIMEOUT, "a bounded device wait gave up");
+    if (stats) *stats = aiwcrf_gate_stats{K, n, (int64_t)h_cnt[1], (int64_t)h_cnt[2]};
+    return AIWCRF_OK;
+}

@@ -400,6 +400,15 @@ int tc_gemm(const __nv_bfloat16 *A, int lda, bool a_trans, const __nv_bfloat16 *
 size_t predict_codes_bytes(const aiwcrf_forest *f, int64_t Q);
 int predict_enqueue(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum, int64_t *d_pred,
                     cudaStream_t s, uint32_t *d_err, void *codes_scratch);
+// fused surrogate inference on the stream, timeouts flagged in d_err (no allocation, no sync)
+int surrogate_predict_enqueue(const aiwcrf_surrogate *sg, const float *dXq, int64_t Q, float *d_out, uint32_t *d_err,
+                              cudaStream_t s);
+// exact ensemble variance numerators of the first n_trees trees (2 u64 words per query)
+int predict_prefix_var_enqueue(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t n_trees,
+                               uint64_t *d_var, cudaStream_t s, uint32_t *d_err, void *codes_scratch);
+// F x (K * D) queries: kernel k's F-2 features, device d_dev[j], size class (query k * D + j)
+int expand_launch(const float *d_kfeat, int32_t K, int32_t size_class, const int32_t *d_dev, int32_t D, int32_t F,
+                  float *d_q, cudaStream_t s);
 int oob_launch(const aiwcrf_forest *f, const float *dX, int64_t N, int64_t *d_sum, int32_t *d_count, cudaStream_t s);
 int predict_launch(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum,
                    int64_t *d_pred, uint64_t *d_var, int64_t total_trees, cudaStream_t s);

@@ -473,7 +473,8 @@ constexpr int kQPT = 4;
 
 template <typename CT, bool VAR>
 int launch_predict(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum, int64_t *d_pred,
-                   uint64_t *d_var, int64_t total_trees, cudaStream_t s, uint32_t *d_err, void *codes_scratch)
+                   uint64_t *d_var, int64_t total_trees, cudaStream_t s, uint32_t *d_err, void *codes_scratch,
+                   int64_t walk_T)
 {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
@@ -500,7 +501,7 @@ int launch_predict(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t 
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(predict_kernel)");
     const int64_t grid = (Q + (int64_t)kPredThreads * kQPT - 1) / ((int64_t)kPredThreads * kQPT);
-    kern<<<(unsigned)grid, kPredThreads, smem, s>>>(f->d_cnodes, f->d_tree_off, (int)f->T, d_codes, Q, ld_words,
+    kern<<<(unsigned)grid, kPredThreads, smem, s>>>(f->d_cnodes, f->d_tree_off, (int)walk_T, d_codes, Q, ld_words,
                                                     total_trees, tree_cap, d_sum, d_pred, d_var, d_err);
     count_launches(1);
     e = cudaGetLastError();
@@ -510,7 +511,8 @@ int launch_predict(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t 
 
 template <bool VAR>
 int launch_predict4(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum, int64_t *d_pred,
-                    uint64_t *d_var, int64_t total_trees, cudaStream_t s, uint32_t *d_err, void *codes_scratch)
+                    uint64_t *d_var, int64_t total_trees, cudaStream_t s, uint32_t *d_err, void *codes_scratch,
+                    int64_t walk_T)
 {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
@@ -536,7 +538,7 @@ int launch_predict4(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(predict4_kernel)");
     const int64_t grid = (Q + (int64_t)kPredThreads * kQPT - 1) / ((int64_t)kPredThreads * kQPT);
-    kern<<<(unsigned)grid, kPredThreads, smem, s>>>(f->d_c32, f->d_tree_off4, f->d_nodes, f->d_tree_off, (int)f->T,
+    kern<<<(unsigned)grid, kPredThreads, smem, s>>>(f->d_c32, f->d_tree_off4, f->d_nodes, f->d_tree_off, (int)walk_T,
                                                     d_codes, Q, ld_words, total_trees, tree_cap, d_sum, d_pred, d_var,
                                                     d_err);
     count_launches(1);
@@ -547,13 +549,15 @@ int launch_predict4(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t
 
 template <typename CT>
 int launch_predict_ct(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum, int64_t *d_pred,
-                      uint64_t *d_var, int64_t total_trees, cudaStream_t s, uint32_t *d_err, void *scratch = nullptr)
+                      uint64_t *d_var, int64_t total_trees, cudaStream_t s, uint32_t *d_err, void *scratch = nullptr,
+                      int64_t walk_T = -1)
 {
+    if (walk_T < 0) walk_T = f->T;
     if (f->compact)
-        return d_var ? launch_predict4<true>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err, scratch)
-                     : launch_predict4<false>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err, scratch);
-    return d_var ? launch_predict<CT, true>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err, scratch)
-                 : launch_predict<CT, false>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err, scratch);
+        return d_var ? launch_predict4<true>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err, scratch, walk_T)
+                     : launch_predict4<false>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err, scratch, walk_T);
+    return d_var ? launch_predict<CT, true>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err, scratch, walk_T)
+                 : launch_predict<CT, false>(f, dXq, Q, d_sum, d_pred, d_var, total_trees, s, d_err, scratch, walk_T);
 }
 
 }  // namespace
@@ -573,6 +577,29 @@ int predict_enqueue(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t
     if (f->max_card <= 255u) return launch_predict_ct<uint8_t>(f, dXq, Q, d_sum, d_pred, nullptr, f->T, s, d_err, codes_scratch);
     if (f->max_card <= 65535u) return launch_predict_ct<uint16_t>(f, dXq, Q, d_sum, d_pred, nullptr, f->T, s, d_err, codes_scratch);
     return launch_predict_ct<uint32_t>(f, dXq, Q, d_sum, d_pred, nullptr, f->T, s, d_err, codes_scratch);
+}
+
+int predict_prefix_var_enqueue(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t n_trees,
+                               uint64_t *d_var, cudaStream_t s, uint32_t *d_err, void *codes_scratch)
+{
+    if (Q == 0) return AIWCRF_OK;
+    if (f->max_card <= 255u)
+        return launch_predict_ct<uint8_t>(f, dXq, Q, nullptr, nullptr, d_var, n_trees, s, d_err, codes_scratch, n_trees);
+    if (f->max_card <= 65535u)
+        return launch_predict_ct<uint16_t>(f, dXq, Q, nullptr, nullptr, d_var, n_trees, s, d_err, codes_scratch, n_trees);
+    return launch_predict_ct<uint32_t>(f, dXq, Q, nullptr, nullptr, d_var, n_trees, s, d_err, codes_scratch, n_trees);
+}
+
+int expand_launch(const float *d_kfeat, int32_t K, int32_t size_class, const int32_t *d_dev, int32_t D, int32_t F,
+                  float *d_q, cudaStream_t s)
+{
+    const int64_t Qn = (int64_t)K * D;
+    if (Qn == 0) return AIWCRF_OK;
+    expand_queries_kernel<<<(unsigned)((Qn + 255) / 256), 256, 0, s>>>(d_kfeat, K, size_class, d_dev, D, F, d_q);
+    count_launches(1);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "expand_queries_kernel launch");
+    return AIWCRF_OK;
 }
 
 int predict_launch(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum, int64_t *d_pred,

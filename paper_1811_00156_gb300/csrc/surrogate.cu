@@ -543,17 +543,15 @@ int new_surrogate(int32_t F, int32_t n_dev, int32_t n_size, aiwcrf_surrogate **o
 
 }  // namespace
 
-int surrogate_predict_launch(const aiwcrf_surrogate *sg, const float *dXq, int64_t Q, float *d_out, cudaStream_t s)
+int surrogate_predict_enqueue(const aiwcrf_surrogate *sg, const float *dXq, int64_t Q, float *d_out, uint32_t *d_err,
+                              cudaStream_t s)
 {
     if (Q == 0) return AIWCRF_OK;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    uint32_t *d_err = nullptr;
-    if (cudaMallocAsync(&d_err, 4, s) != cudaSuccess) return fail(AIWCRF_E_OOM, "surrogate error flag");
-    cudaMemsetAsync(d_err, 0, 4, s);
     cudaError_t e = cudaFuncSetAttribute(surrogate_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kInferSmem);
-    if (e != cudaSuccess) { cudaFreeAsync(d_err, s); return cuda_fail(e, "surrogate kernel attribute"); }
+    if (e != cudaSuccess) return cuda_fail(e, "surrogate kernel attribute");
     const int64_t tiles = (Q + 127) / 128;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, sms));
     surrogate_infer_kernel<<<grid, kInferThreads, kInferSmem, s>>>(encoder_of(sg), dXq, Q, sg->d_W1b, sg->d_W2b,
@@ -561,6 +559,19 @@ int surrogate_predict_launch(const aiwcrf_surrogate *sg, const float *dXq, int64
                                                                      sg->d_param + ow3, sg->d_param + ob3, d_out, d_err);
     count_launches(1);
     e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "surrogate_infer_kernel launch");
+    return AIWCRF_OK;
+}
+
+int surrogate_predict_launch(const aiwcrf_surrogate *sg, const float *dXq, int64_t Q, float *d_out, cudaStream_t s)
+{
+    if (Q == 0) return AIWCRF_OK;
+    uint32_t *d_err = nullptr;
+    if (cudaMallocAsync(&d_err, 4, s) != cudaSuccess) return fail(AIWCRF_E_OOM, "surrogate error flag");
+    cudaMemsetAsync(d_err, 0, 4, s);
+    int rc = surrogate_predict_enqueue(sg, dXq, Q, d_out, d_err, s);
+    if (rc) { cudaFreeAsync(d_err, s); return rc; }
+    cudaError_t e = cudaSuccess;
     uint32_t h = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_err, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
