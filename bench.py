@@ -445,6 +445,51 @@ def surrogate_report(A, forest, Xq, n_train=4_000_000, epochs=20, bf16_peak_tflo
            "tensor_tflops": flops / (s_ms / 1e3) / 1e12}
     if bf16_peak_tflops:
         rep["tensor_frac_of_measured_bf16"] = rep["tensor_tflops"] / bf16_peak_tflops
+    rep["gated_selection"] = gated_selection_report(A, forest, sg)
+    return rep
+
+
+def gated_selection_report(A, forest, sg, K=65536, var_trees=32, thresholds=(0.0005, 0.002, 0.01, None)):
+    """Device selection for K kernels x 15 devices: the forest alone, and the surrogate gated by
+    out-of-range features and the exact ensemble variance of the forest's first 32 trees (None:
+    the surrogate alone). Agreement and regret are judged by the forest's own predictions."""
+    import torch
+    dev = torch.device("cuda")
+    kf = torch.from_numpy(np.ascontiguousarray(synth.queries(K, seed=555)[:synth.N_AIWC])).to(dev)
+    devices = list(range(SEL_DEVICES))
+    fb_best = torch.empty(K, dtype=torch.int32, device=dev)
+    fb_pred = torch.empty(K * SEL_DEVICES, dtype=torch.int64, device=dev)
+    best = torch.empty(K, dtype=torch.int32, device=dev)
+    flags = torch.empty(K, dtype=torch.uint8, device=dev)
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            out = fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        return statistics.median(ts), out
+
+    t_forest, _ = timed(lambda: A.aiwcrf_select_device(forest, kf, 2, devices, fb_best, fb_pred))
+    fp = fb_pred.view(K, SEL_DEVICES).cpu().numpy().astype(np.float64) / 2.0 ** 32
+    fbest = fb_best.cpu().numpy()
+    rep = {"kernels": K, "devices": SEL_DEVICES, "var_trees": var_trees,
+           "forest": {"ms": 1e3 * t_forest, "queries_per_s": K * SEL_DEVICES / t_forest}, "gated": []}
+    for thr in thresholds:
+        g = A.gate_params(var_trees, thr if thr is not None else 0.0, ood=thr is not None)
+        if thr is None:
+            g = A.gate_params(1, 1048575.0, ood=False)
+        t, st = timed(lambda: A.aiwcrf_select_device_gated(forest, sg, g, kf, 2, devices, best, None, flags))
+        b = best.cpu().numpy()
+        regret = fp[np.arange(K), b] - fp[np.arange(K), fbest]
+        rep["gated"].append({"var_threshold": thr, "ms": 1e3 * t, "queries_per_s": K * SEL_DEVICES / t,
+                             "speedup_vs_forest": t_forest / t, "fallback_frac": st["fallback"] / K,
+                             "fallback_ood": st["fallback_ood"], "fallback_var": st["fallback_var"],
+                             "agreement_with_forest": float((b == fbest).mean()),
+                             "mean_regret_log10": float(regret.mean()), "p99_regret_log10": float(np.percentile(regret, 99))})
     return rep
 
 
@@ -513,6 +558,24 @@ def serving_report(A, wl, rates=(5000.0, 20000.0, 50000.0), n_requests=20000, re
                                                timeout_ms=600000)
             c1 = srv.stats()
             rep["refit_ms"] = (c1["refit_us_total"] - c0["refit_us_total"]) / 1e3
+            # where the tail comes from: host enqueue time and GPU (copies + kernel) time per batch
+            bt, rt = srv.trace()
+            nb = int(rep["batches"])
+            bt = bt[-nb:] if nb else bt[:0]
+            if nb:
+                gpu = (bt["t_done_ns"] - bt["t_enqueued_ns"]) / 1e3
+                enq = (bt["t_enqueued_ns"] - bt["t_formed_ns"]) / 1e3
+                form = np.sort(bt["t_formed_ns"])
+                rep["batch_gpu_us"] = {"p50": float(np.median(gpu)), "p99": float(np.percentile(gpu, 99)),
+                                       "max": float(gpu.max())}
+                rep["batch_enqueue_us"] = {"p50": float(np.median(enq)), "max": float(enq.max())}
+                rep["max_gap_between_batches_ms"] = float(np.diff(form).max() / 1e6) if nb > 1 else 0.0
+                slow = bt[gpu > 5000]
+                rep["slow_batches"] = [{"t_ms": float((b["t_formed_ns"] - form[0]) / 1e6),
+                                        "gpu_ms": float((b["t_done_ns"] - b["t_enqueued_ns"]) / 1e6)} for b in slow[:8]]
+                rep["refit_windows_ms"] = [[float((r["t_start_ns"] - form[0]) / 1e6),
+                                            float((r["t_swapped_ns"] - form[0]) / 1e6)]
+                                           for r in rt if r["t_start_ns"] >= form[0]]
             rep["requests_over_1ms"] = int((lat > 1_000_000).sum())
             rep["requests_over_10ms"] = int((lat > 10_000_000).sum())
             checked = mism = 0

@@ -83,11 +83,21 @@ def expected(A, models, kf, size, thr, ood):
     return fb, ood_fb, var_fb, best, pred
 
 
-@pytest.mark.parametrize("thr,ood", [(0.002, True), (0.0, False), (1000.0, False), (0.02, True)])
+def median_kernel_variance(models, kf, size):
+    """Median over kernels of the largest prefix variance among the kernel's devices, (log10 s)^2."""
+    wl, f, sg, of, op = models
+    _, _, V = op.predict(expand(kf, size), want_var=True)
+    v = np.array([float(x) for x in V]).reshape(kf.shape[1], -1) / (VAR_TREES ** 2 * 2.0 ** 64)
+    return float(np.float32(np.median(v.max(axis=1))))
+
+
+@pytest.mark.parametrize("thr,ood", [("median", True), (0.0, False), (1000.0, False), ("median", False)])
 def test_gate_matches_oracle(A, models, thr, ood):
     wl, f, sg, of, op = models
     K, size = 300, 2
     kf = kernels(K, seed=41)
+    if thr == "median":
+        thr = median_kernel_variance(models, kf, size)
     fb, ood_fb, var_fb, best, pred = expected(A, models, kf, size, thr, ood)
     ob = torch.empty(K, dtype=torch.int32, device="cuda")
     opr = torch.empty(K * DEV.size, dtype=torch.float32, device="cuda")
@@ -104,8 +114,8 @@ def test_gate_matches_oracle(A, models, thr, ood):
         assert st["fallback"] == 0
     if ood:
         assert ood_fb[[3, 5, 7]].all()
-    if thr == 0.002:
-        assert 0 < st["fallback"] < K         # both paths taken
+    if thr not in (0.0, 1000.0):
+        assert K // 4 < st["fallback"] < 3 * K // 4         # both paths taken
 
 
 def test_gate_everything_falls_back_equals_select_device(A, models):
