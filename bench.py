@@ -449,13 +449,25 @@ def surrogate_report(A, forest, Xq, n_train=4_000_000, epochs=20, bf16_peak_tflo
     return rep
 
 
-def gated_selection_report(A, forest, sg, K=65536, var_trees=32, thresholds=(0.0005, 0.002, 0.01, None)):
-    """Device selection for K kernels x 15 devices: the forest alone, and the surrogate gated by
-    out-of-range features and the exact ensemble variance of the forest's first 32 trees (None:
-    the surrogate alone). Agreement and regret are judged by the forest's own predictions."""
+def gated_selection_report(A, forest, sg, K=65536, var_trees=32, zs=(0.1, 0.25, 0.5, 1.0, 2.0, None)):
+    """The gated selection on two kernel populations: fresh draws of the feature distributions
+    (far from the 37 training kernels) and neighbours of the training kernels."""
+    far = np.ascontiguousarray(synth.queries(K, seed=555)[:synth.N_AIWC])
+    near = synth.kernel_neighbours(K, 2, jitter=0.05, seed=556)
+    return {"random_kernels": gated_selection_case(A, forest, sg, far, var_trees, zs),
+            "training_neighbours": gated_selection_case(A, forest, sg, near, var_trees, zs)}
+
+
+def gated_selection_case(A, forest, sg, kf_h, var_trees, zs):
+    """Device selection for K kernels x 15 devices: the forest alone, and the surrogate whose
+    choice falls back to the forest on out-of-range features or when its margin between the two
+    best devices is within z standard deviations of their ensemble spread over the forest's first
+    32 trees (None: the surrogate alone). Agreement and regret are judged by the forest's own
+    predictions."""
     import torch
     dev = torch.device("cuda")
-    kf = torch.from_numpy(np.ascontiguousarray(synth.queries(K, seed=555)[:synth.N_AIWC])).to(dev)
+    K = kf_h.shape[1]
+    kf = torch.from_numpy(kf_h).to(dev)
     devices = list(range(SEL_DEVICES))
     fb_best = torch.empty(K, dtype=torch.int32, device=dev)
     fb_pred = torch.empty(K * SEL_DEVICES, dtype=torch.int64, device=dev)
@@ -478,14 +490,12 @@ def gated_selection_report(A, forest, sg, K=65536, var_trees=32, thresholds=(0.0
     fbest = fb_best.cpu().numpy()
     rep = {"kernels": K, "devices": SEL_DEVICES, "var_trees": var_trees,
            "forest": {"ms": 1e3 * t_forest, "queries_per_s": K * SEL_DEVICES / t_forest}, "gated": []}
-    for thr in thresholds:
-        g = A.gate_params(var_trees, thr if thr is not None else 0.0, ood=thr is not None)
-        if thr is None:
-            g = A.gate_params(1, 1048575.0, ood=False)
+    for z in zs:
+        g = A.gate_params(var_trees, z, ood=True) if z is not None else A.gate_params(1, 0.0, ood=False)
         t, st = timed(lambda: A.aiwcrf_select_device_gated(forest, sg, g, kf, 2, devices, best, None, flags))
         b = best.cpu().numpy()
         regret = fp[np.arange(K), b] - fp[np.arange(K), fbest]
-        rep["gated"].append({"var_threshold": thr, "ms": 1e3 * t, "queries_per_s": K * SEL_DEVICES / t,
+        rep["gated"].append({"z": z, "ms": 1e3 * t, "queries_per_s": K * SEL_DEVICES / t,
                              "speedup_vs_forest": t_forest / t, "fallback_frac": st["fallback"] / K,
                              "fallback_ood": st["fallback_ood"], "fallback_var": st["fallback_var"],
                              "agreement_with_forest": float((b == fbest).mean()),

@@ -385,22 +385,25 @@ int aiwcrf_server_destroy(aiwcrf_server *server);
 
 /* Device selection through the surrogate with the forest as fallback and judge (the paper has no
  * surrogate; its selection of Sec. VI queries the forest). For each kernel k the D queries
- * (k, device_ids[j]) are predicted by the surrogate; the kernel falls back to the forest when
- * any of its queries
- *  - has a feature outside [smallest, largest] of the forest's training values of that column,
- *    or NaN (with gate->ood = 1), or
- *  - has a high ensemble variance over the forest's first var_trees trees: with v_t the leaf
- *    values (Q32.32) and P = sum v_t, V = var_trees * sum v_t^2 - P^2 (exact), the test is
- *    V > floor(var_threshold * 2^64) * var_trees^2, i.e. the variance of the prefix's
- *    predictions exceeds var_threshold (log10 s)^2.
+ * (k, device_ids[j]) are predicted by the surrogate, s_j (NaN counts as +infinity); b is the
+ * argmin and r the runner-up (ties: lower device id). The kernel falls back to the forest when
+ *  - gate->ood = 1 and a feature of one of its queries lies outside [smallest, largest] of the
+ *    forest's training values of that column, or is NaN; or
+ *  - the surrogate's margin is within z standard deviations of the ensemble spread of the two
+ *    contenders: with V_j = var_trees * sum_t v_t^2 - (sum_t v_t)^2 over the forest's first
+ *    var_trees trees' leaf values v_t (Q32.32, exact), the test is
+ *        ((s_r - s_b)^2 * var_trees^2) * 2^64  <=  (z * z) * (V_b + V_r)
+ *    evaluated in IEEE double with round-to-nearest in exactly this order, V_b + V_r converted
+ *    as double(high 64 bits) * 2^64 + double(low 64 bits). With one device there is no
+ *    runner-up and only the range test applies.
  * A kernel that falls back gets exactly aiwcrf_select_device's device and the forest's
- * predictions (converted to float log10 s); the others get the argmin of the surrogate's
- * predictions (ties: lower device id). kfeat ((F-2) x K), out_best (K), out_pred (K x D float,
- * or NULL) and out_fallback (K bytes, 1 = forest, or NULL) are device memory; device_ids and
- * stats (or NULL) are host memory. The call synchronises its stream. */
+ * predictions (converted to float log10 s); the others get b and the surrogate's predictions.
+ * kfeat ((F-2) x K), out_best (K), out_pred (K x D float, or NULL) and out_fallback (K bytes,
+ * 1 = forest, or NULL) are device memory; device_ids and stats (or NULL) are host memory. The
+ * call synchronises its stream. */
 typedef struct {
     int32_t var_trees;      /* 1..num_trees (32) */
-    float var_threshold;    /* (log10 s)^2, 0 <= var_threshold < 2^20 (0.01) */
+    float z;                /* margin in ensemble standard deviations, 0 <= z < 2^20 (1) */
     int32_t ood;            /* 1: out-of-range features fall back (1) */
     int32_t reserved;       /* must be 0 */
 } aiwcrf_gate_params;
@@ -409,7 +412,7 @@ typedef struct {
     int64_t kernels;
     int64_t fallback;       /* kernels answered by the forest */
     int64_t fallback_ood;   /* ... with an out-of-range feature */
-    int64_t fallback_var;   /* ... with a high prefix variance */
+    int64_t fallback_var;   /* ... whose surrogate margin was within z deviations */
 } aiwcrf_gate_stats;
 
 int aiwcrf_select_device_gated(const aiwcrf_forest *forest, const aiwcrf_surrogate *surrogate,

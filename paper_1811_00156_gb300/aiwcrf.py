@@ -82,7 +82,7 @@ class LoadReport(C.Structure):
 
 
 class GateParams(C.Structure):
-    _fields_ = [("var_trees", C.c_int32), ("var_threshold", C.c_float), ("ood", C.c_int32), ("reserved", C.c_int32)]
+    _fields_ = [("var_trees", C.c_int32), ("z", C.c_float), ("ood", C.c_int32), ("reserved", C.c_int32)]
 
 
 class GateStats(C.Structure):
@@ -491,8 +491,8 @@ class Server:
         return rep.as_dict(), best, gen, lat
 
 
-def gate_params(var_trees: int = 32, var_threshold: float = 0.01, ood: bool = True) -> GateParams:
-    return GateParams(var_trees, var_threshold, 1 if ood else 0, 0)
+def gate_params(var_trees: int = 32, z: float = 1.0, ood: bool = True) -> GateParams:
+    return GateParams(var_trees, z, 1 if ood else 0, 0)
 
 
 def aiwcrf_select_device_gated(forest: Forest, surrogate, gate: GateParams, kfeat, size_class: int, device_ids,

@@ -7,8 +7,9 @@
 //  2. surrogate inference (fused tcgen05 kernel) for every query;
 //  3. exact ensemble-variance numerators over the forest's first var_trees trees;
 //  4. gate_kernel, one warp per kernel: out-of-range test of every feature of its D queries
-//     against the forest's value tables, the variance test, the surrogate argmin, and the
-//     kernels that fall back appended to a list;
+//     against the forest's value tables, the surrogate's best and runner-up devices, the test of
+//     their margin against the two contenders' ensemble spread, and the kernels that fall back
+//     appended to a list;
 //  5. the fallback kernels' queries gathered, predicted by the whole forest, and their device
 //     chosen from the exact int64 predictions (fix_kernel).
 // Which kernel lands where in the fallback list depends on the order of the atomics, but every
@@ -23,19 +24,36 @@
 
 namespace aiwcrf {
 
+// argmin step over (value, device id): smaller value, then lower id; id INT_MAX = empty
+__device__ __forceinline__ void take_min(float &bs, int32_t &bd, float os, int32_t od)
+{
+    if (od != INT_MAX && (bd == INT_MAX || os < bs || (os == bs && od < bd))) { bs = os; bd = od; }
+}
+
+__device__ __forceinline__ void warp_min(float &bs, int32_t &bd)
+{
+#pragma unroll
+    for (int w = 16; w; w >>= 1) {
+        const float os = __shfl_xor_sync(0xFFFFFFFFu, bs, w);
+        const int32_t od = __shfl_xor_sync(0xFFFFFFFFu, bd, w);
+        take_min(bs, bd, os, od);
+    }
+}
+
+// One warp per kernel: range test of every feature of its D queries, the surrogate's best and
+// runner-up devices, and the margin test against the two contenders' prefix variances.
 __global__ void gate_kernel(const float *__restrict__ q, int64_t Qn, int F, int D, const float *__restrict__ fvals,
                             int64_t fstride, const uint32_t *__restrict__ fcard, const uint64_t *__restrict__ var,
-                            uint64_t thr_lo, uint64_t thr_hi, int ood, const float *__restrict__ sur,
+                            double z2, double scale, int ood, const float *__restrict__ sur,
                             const int32_t *__restrict__ dev, int K, uint8_t *flag, int32_t *best, float *pred,
                             int32_t *list, unsigned long long *counts)
 {
     const int lane = threadIdx.x & 31;
     const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (k >= K) return;                        // warp-uniform
-    const u128_t thr = ((u128_t)thr_hi << 64) | thr_lo;
-    bool o = false, v = false;
-    float bs = INFINITY;
-    int32_t bd = INT_MAX;
+    bool o = false;
+    float bs = INFINITY, rs = INFINITY;
+    int32_t bd = INT_MAX, rd = INT_MAX;
     for (int j = lane; j < D; j += 32) {
         const int64_t i = k * D + j;
         if (ood) {
@@ -46,29 +64,52 @@ __global__ void gate_kernel(const float *__restrict__ q, int64_t Qn, int F, int 
                 if (c == 0 || !(x >= V[0] && x <= V[c - 1])) o = true;
             }
         }
-        const u128_t Vn = ((u128_t)var[2 * i + 1] << 64) | var[2 * i];
-        if (Vn > thr) v = true;
-        const float sv = sur[i];
+        float sv = sur[i];
         if (pred) pred[i] = sv;
-        const int32_t id = dev[j];
-        if (sv < bs || (sv == bs && id < bd) || bd == INT_MAX) { bs = sv; bd = id; }
+        if (sv != sv) sv = INFINITY;
+        take_min(bs, bd, sv, dev[j]);
     }
-#pragma unroll
+    warp_min(bs, bd);                          // every lane now holds the best (bs, bd)
+    // runner-up: the best among the devices other than bd
+    int jb = -1;
+    for (int j = lane; j < D; j += 32) {
+        float sv = sur[k * D + j];
+        if (sv != sv) sv = INFINITY;
+        if (dev[j] == bd) { jb = j; continue; }
+        take_min(rs, rd, sv, dev[j]);
+    }
+    warp_min(rs, rd);
+    int jr = -1;
+    for (int j = lane; j < D; j += 32)
+        if (rd != INT_MAX && dev[j] == rd) jr = j;
+    // the lanes holding b and r publish their queries' index; max over lanes
     for (int w = 16; w; w >>= 1) {
-        const float os = __shfl_xor_sync(0xFFFFFFFFu, bs, w);
-        const int32_t od = __shfl_xor_sync(0xFFFFFFFFu, bd, w);
-        if (od != INT_MAX && (bd == INT_MAX || os < bs || (os == bs && od < bd))) { bs = os; bd = od; }
+        jb = max(jb, __shfl_xor_sync(0xFFFFFFFFu, jb, w));
+        jr = max(jr, __shfl_xor_sync(0xFFFFFFFFu, jr, w));
     }
-    const bool any_o = __any_sync(0xFFFFFFFFu, o), any_v = __any_sync(0xFFFFFFFFu, v);
+    const bool any_o = __any_sync(0xFFFFFFFFu, o);
     if (lane == 0) {
-        const bool fb = any_o || any_v;
+        bool v = false;
+        if (jr >= 0) {
+            const int64_t ib = k * D + jb, ir = k * D + jr;
+            const u128_t Vb = ((u128_t)var[2 * ib + 1] << 64) | var[2 * ib];
+            const u128_t Vr = ((u128_t)var[2 * ir + 1] << 64) | var[2 * ir];
+            const u128_t Vs = Vb + Vr;
+            const double vs = __dadd_rn(__dmul_rn(__ull2double_rn((unsigned long long)(Vs >> 64)), 0x1p64),
+                                        __ull2double_rn((unsigned long long)Vs));
+            const double m = __dsub_rn((double)rs, (double)bs);
+            const double lhs = __dmul_rn(__dmul_rn(m, m), scale);
+            const double rhs = __dmul_rn(z2, vs);
+            v = lhs <= rhs;
+        }
+        const bool fb = any_o || v;
         flag[k] = fb ? 1 : 0;
         best[k] = bd;
         if (fb) {
             const unsigned long long slot = atomicAdd(&counts[0], 1ull);
             list[slot] = (int32_t)k;
             if (any_o) atomicAdd(&counts[1], 1ull);
-            if (any_v) atomicAdd(&counts[2], 1ull);
+            if (v) atomicAdd(&counts[2], 1ull);
         }
     }
 }
@@ -139,8 +180,8 @@ extern "C" int aiwcrf_select_device_gated(const aiwcrf_forest *forest, const aiw
     if (!forest || !surrogate || !gate || !device_ids)
         return fail(AIWCRF_E_INVALID_ARG, "forest, surrogate, gate and device_ids must not be NULL");
     if (n_kernels < 0 || n_devices < 1) return fail(AIWCRF_E_INVALID_ARG, "n_kernels >= 0 and n_devices >= 1");
-    if (gate->var_trees < 1 || gate->var_trees > forest->T || !(gate->var_threshold >= 0.0f) ||
-        !(gate->var_threshold < 1048576.0f) || (gate->ood != 0 && gate->ood != 1) || gate->reserved != 0)
+    if (gate->var_trees < 1 || gate->var_trees > forest->T || !(gate->z >= 0.0f) || !(gate->z < 1048576.0f) ||
+        (gate->ood != 0 && gate->ood != 1) || gate->reserved != 0)
         return fail(AIWCRF_E_INVALID_ARG, "gate parameters out of range");
     if (stats) *stats = aiwcrf_gate_stats{n_kernels, 0, 0, 0};
     if (n_kernels == 0) return AIWCRF_OK;
@@ -153,14 +194,9 @@ extern "C" int aiwcrf_select_device_gated(const aiwcrf_forest *forest, const aiw
     const int64_t Qn = (int64_t)K * D;
     keep_pool_memory(forest->device);
 
-    // threshold numerator floor(thr * 2^64) * var_trees^2, exact: thr = m * 2^(ex - 24) with a
-    // 24-bit integer m, and thr < 2^20 keeps the product below 2^124
-    int ex = 0;
-    const float mf = std::frexp(gate->var_threshold, &ex);
-    const uint64_t m = (uint64_t)std::ldexp(mf, 24);
-    const int sh = ex - 24 + 64;
-    const u128_t thr_q = sh >= 0 ? (u128_t)m << sh : (sh > -64 ? (u128_t)(m >> -sh) : (u128_t)0);
-    const u128_t thr = thr_q * (u128_t)gate->var_trees * (u128_t)gate->var_trees;
+    // the margin test's constants: (z * z) and var_trees^2 * 2^64 (exact in double)
+    const double z2 = (double)gate->z * (double)gate->z;
+    const double scale = (double)gate->var_trees * (double)gate->var_trees * 0x1p64;
 
     // scratch: device ids, queries, surrogate outputs, variance numerators, query codes, flags,
     // list, counters, error flag; then the fallback's gathered queries and predictions
@@ -195,7 +231,7 @@ extern "C" int aiwcrf_select_device_gated(const aiwcrf_forest *forest, const aiw
     if ((rc = predict_prefix_var_enqueue(forest, d_q, Qn, gate->var_trees, d_var, s, d_err, d_codes))) return rc;
     const unsigned gblocks = (unsigned)(((int64_t)K * 32 + 255) / 256);
     gate_kernel<<<gblocks, 256, 0, s>>>(d_q, Qn, F, D, forest->d_fvals, forest->fstride, forest->d_fcard, d_var,
-                                        (uint64_t)thr, (uint64_t)(thr >> 64), gate->ood, d_sur, d_dev, K, d_flag,
+                                        z2, scale, gate->ood, d_sur, d_dev, K, d_flag,
                                         out_best, out_pred, d_list, d_cnt);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gate_kernel launch");

@@ -161,6 +161,23 @@ def queries(q: int, seed: int = QUERY_SEED) -> np.ndarray:
     return Xq
 
 
+def kernel_neighbours(K: int, size: int, jitter: float = 0.05, seed: int = QUERY_SEED,
+                      data_seed: int = DATA_SEED) -> np.ndarray:
+    """K kernels near the training kernels: the AIWC vector of a random training kernel at this
+    size class, each count column scaled by exp(N(0, jitter)), each entropy and ratio column moved
+    by N(0, jitter) times its range and kept inside it. float32 [30][K]."""
+    _, pop, _ = _population(data_seed)
+    rng = np.random.default_rng(seed)
+    k = rng.integers(0, N_KERNELS, size=K)
+    out = pop[:, k * N_SIZES + size].astype(np.float64)
+    out[_COUNT_COLS] *= np.exp(rng.normal(0.0, jitter, size=(len(_COUNT_COLS), K)))
+    ent = list(range(10, 18))
+    out[ent] = np.clip(out[ent] + rng.normal(0.0, 32.0 * jitter, size=(len(ent), K)), 0.0, 32.0)
+    rat = list(range(18, 24))
+    out[rat] = np.clip(out[rat] + rng.normal(0.0, jitter, size=(len(rat), K)), 0.0, 1.0)
+    return np.ascontiguousarray(out.astype(np.float32))
+
+
 def loko_folds(seed: int = DATA_SEED):
     """Leave-one-kernel-out folds over the 2,220-row workload.
 
