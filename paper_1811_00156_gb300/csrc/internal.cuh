@@ -403,6 +403,12 @@ int predict_enqueue(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t
 // fused surrogate inference on the stream, timeouts flagged in d_err (no allocation, no sync)
 int surrogate_predict_enqueue(const aiwcrf_surrogate *sg, const float *dXq, int64_t Q, float *d_out, uint32_t *d_err,
                               cudaStream_t s);
+// Device selection by the tree-parallel kernel (one CTA per kernel and 32 trees): d_kfeat is
+// (F-2) x K, d_sum (K * D) and d_cnt (K) zero on entry and left zero, d_pred K x D; needs
+// D <= 64 and size_class >= 0. Same integer results as predict + argmin.
+int select_small_launch(const aiwcrf_forest *f, const float *d_kfeat, int32_t K, int32_t size_class,
+                        const int32_t *d_dev, int32_t D, int32_t *d_best, int64_t *d_pred, unsigned long long *d_sum,
+                        uint32_t *d_cnt, cudaStream_t s);
 // exact ensemble variance numerators of the first n_trees trees (2 u64 words per query)
 int predict_prefix_var_enqueue(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t n_trees,
                                uint64_t *d_var, cudaStream_t s, uint32_t *d_err, void *codes_scratch);

@@ -73,6 +73,8 @@ __device__ __forceinline__ void fence_mbar_init()
 }
 
 constexpr int kPredThreads = 256;
+// device selections with at most this many queries use the tree-parallel kernel
+constexpr int64_t kTreeParallelMaxQueries = 1 << 18;
 constexpr uint32_t kWaitLimit = 1u << 24;     // try_wait polls before giving up
 
 // stage tree t into slot (or just complete the phase if it does not fit)
@@ -682,6 +684,19 @@ int select_launch(const aiwcrf_forest *f, const float *d_kfeat, int32_t K, int32
                   int64_t *d_p, cudaStream_t s)
 {
     const int64_t Qn = (int64_t)K * D;
+    if (D <= 64 && Qn <= kTreeParallelMaxQueries && size_class >= 0) {
+        // few queries: spread the trees over CTAs instead of the queries; the query scratch
+        // (F * Qn floats) holds the kernel's zeroed sums and counters
+        unsigned long long *d_sum = reinterpret_cast<unsigned long long *>(d_q);
+        uint32_t *d_cnt = reinterpret_cast<uint32_t *>(d_sum + Qn);
+        const cudaError_t e = cudaMemsetAsync(d_sum, 0, 8 * (size_t)Qn + 4 * (size_t)K, s);
+        if (e != cudaSuccess) return cuda_fail(e, "select scratch");
+        prof_begin(s, kProfSelect);
+        const int rc = select_small_launch(f, d_kfeat, K, size_class, d_dev, D, d_best, d_pred ? d_pred : d_p, d_sum,
+                                           d_cnt, s);
+        prof_end(s, kProfSelect);
+        return rc;
+    }
     prof_begin(s, kProfSelect);
     expand_queries_kernel<<<(unsigned)((Qn + 255) / 256), 256, 0, s>>>(d_kfeat, K, size_class, d_dev, D, f->F, d_q);
     count_launches(1);

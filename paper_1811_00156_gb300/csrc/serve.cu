@@ -139,13 +139,14 @@ __device__ __forceinline__ uint32_t rank_code(const float *V, uint32_t card, flo
 // 32g + ts and 32g + ts + 16 for device jb + jl, for each pass jb = 0, 16, .. < D: the threads of
 // one tree follow the same path until a split on the device column, so their node loads
 // coincide. kq: F x Kb column-major batch features (row F-2 unused: the device id comes from
-// dev[]; row F-1 the size class). sums (Kb * D) and cnt (Kb) are zero on entry and left zero.
+// dev[]; row F-1 the size class, unless size_override >= 0 gives it for every kernel, and then kq
+// may have only F-2 rows). sums (Kb * D) and cnt (Kb) are zero on entry and left zero.
 // pred: Kb x D row-major predictions; best: Kb device ids.
 template <bool COMPACT>
 __global__ void __launch_bounds__(kServeThreads) serve_select_kernel(ServeForest sf, const float *__restrict__ kq,
                                                                      int Kb, const int32_t *__restrict__ dev, int D,
-                                                                     unsigned long long *sums, uint32_t *cnt,
-                                                                     int64_t *pred, int32_t *best)
+                                                                     int size_override, unsigned long long *sums,
+                                                                     uint32_t *cnt, int64_t *pred, int32_t *best)
 {
     __shared__ uint32_t kcode[AIWCRF_MAX_FEATURES];
     __shared__ uint32_t dcode[kServeMaxDevices];
@@ -158,7 +159,8 @@ __global__ void __launch_bounds__(kServeThreads) serve_select_kernel(ServeForest
     for (int f = tid; f < sf.F; f += kServeThreads)
         if (f != (int)fd)
             kcode[f] = rank_code(sf.fvals + (size_t)f * (size_t)sf.fstride, sf.fcard[f],
-                                 kq[(size_t)f * (size_t)Kb + (size_t)k]);
+                                 (f == sf.F - 1 && size_override >= 0) ? (float)size_override
+                                                                       : kq[(size_t)f * (size_t)Kb + (size_t)k]);
     for (int j = tid; j < D; j += kServeThreads)
         dcode[j] = rank_code(sf.fvals + (size_t)fd * (size_t)sf.fstride, sf.fcard[fd], (float)dev[j]);
     __syncthreads();
@@ -221,7 +223,7 @@ size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 constexpr int64_t kIdlePollNs = 200000;   // the dispatcher polls this long before sleeping
 
-int serve_launch(const aiwcrf_forest *f, const float *d_kq, int Kb, const int32_t *d_dev, int D,
+int serve_launch(const aiwcrf_forest *f, const float *d_kq, int Kb, const int32_t *d_dev, int D, int size_override,
                  unsigned long long *d_sum, uint32_t *d_cnt, int64_t *d_pred, int32_t *d_best, cudaStream_t s)
 {
     ServeForest sf;
@@ -238,15 +240,30 @@ int serve_launch(const aiwcrf_forest *f, const float *d_kq, int Kb, const int32_
     const dim3 grid((unsigned)Kb, (unsigned)((f->T + kTreesPerBlock - 1) / kTreesPerBlock));
     prof_begin(s, kProfServe);
     if (f->compact)
-        serve_select_kernel<true><<<grid, kServeThreads, 0, s>>>(sf, d_kq, Kb, d_dev, D, d_sum, d_cnt, d_pred, d_best);
+        serve_select_kernel<true><<<grid, kServeThreads, 0, s>>>(sf, d_kq, Kb, d_dev, D, size_override, d_sum, d_cnt,
+                                                                 d_pred, d_best);
     else
-        serve_select_kernel<false><<<grid, kServeThreads, 0, s>>>(sf, d_kq, Kb, d_dev, D, d_sum, d_cnt, d_pred, d_best);
+        serve_select_kernel<false><<<grid, kServeThreads, 0, s>>>(sf, d_kq, Kb, d_dev, D, size_override, d_sum, d_cnt,
+                                                                  d_pred, d_best);
     prof_end(s, kProfServe);
     count_launches(1);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "serve_select_kernel launch");
     return AIWCRF_OK;
 }
+
+}  // namespace
+
+int select_small_launch(const aiwcrf_forest *f, const float *d_kfeat, int32_t K, int32_t size_class,
+                        const int32_t *d_dev, int32_t D, int32_t *d_best, int64_t *d_pred, unsigned long long *d_sum,
+                        uint32_t *d_cnt, cudaStream_t s)
+{
+    if (D > kServeMaxDevices || f->F > AIWCRF_MAX_FEATURES || size_class < 0)
+        return fail(AIWCRF_E_INVALID_ARG, "select_small_launch: unsupported shape");
+    return serve_launch(f, d_kfeat, K, d_dev, D, size_class, d_sum, d_cnt, d_pred, d_best, s);
+}
+
+namespace {
 
 // First-fit allocator over [0, cap) in 256-byte granules; free neighbours merge.
 struct Arena {
@@ -554,7 +571,7 @@ struct aiwcrf_server {
         const size_t out_bytes = (size_t)sl.Kb * ((size_t)D * 8 + 4);
         cudaError_t e = cudaMemcpyAsync(d_in, sl.h_in, in_bytes, cudaMemcpyHostToDevice, sl.s);
         if (e == cudaSuccess &&
-            serve_launch(sl.model->f, d_in, sl.Kb, d_dev, D, sl.d_sum, sl.d_cnt, d_pred, d_best, sl.s) != AIWCRF_OK)
+            serve_launch(sl.model->f, d_in, sl.Kb, d_dev, D, -1, sl.d_sum, sl.d_cnt, d_pred, d_best, sl.s) != AIWCRF_OK)
             e = cudaErrorLaunchFailure;
         if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_out, d_pred, out_bytes, cudaMemcpyDeviceToHost, sl.s);
         if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.s);
