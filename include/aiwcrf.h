@@ -5,7 +5,7 @@
  * plus a device id and a problem-size class, are the predictors of a random-forest regression
  * (Sec. III-B: ranger, num.trees / mtry / min.node.size) whose response is the kernel's
  * execution time, here log10 seconds in Q32.32 fixed point. The fitted model is queried to
- * predict times (Sec. I: "querying the model is computationally inexpensive"; Sec. V) and to
+ * predict times (Sec. I notes that a query of the fitted model is cheap; Sec. V) and to
  * pick the fastest device for a kernel (Sec. VI).
  *
  * Conventions for every call:
