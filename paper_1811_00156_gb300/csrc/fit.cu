@@ -394,7 +394,30 @@ __device__ __forceinline__ void write_leaf(SplitRes *res, int j, int kind, int64
 
 
 constexpr int kSmallThreads = 256;
+constexpr int kSmallCtasPerSm = 4;     // resident CTAs per SM the small-node kernel is compiled for
 
+// the n-th (from 0) set bit of the 128-bit feature mask, or -1
+__device__ __forceinline__ int nth_feature(const uint32_t (&mask)[4], int n)
+{
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int pc = __popc(mask[c]);
+        if (n < pc) {
+            uint32_t m = mask[c];
+            for (int i = 0; i < n; ++i) m &= m - 1;
+            return c * 32 + __ffs(m) - 1;
+        }
+        n -= pc;
+    }
+    return -1;
+}
+
+// One warp per node of at most 32 entries. The node's entries are sorted by each tried feature's
+// rank with a bitonic network of width K (the smallest power of two >= the entry count), and
+// 32 / K features are sorted side by side in K-lane segments: segment s of pass q takes the
+// (q * 32 / K + s)-th tried feature, lane p of a segment entry p. The best candidate is kept
+// per lane and reduced over the warp at the end; ties resolve on (gain, feature, rank), so the
+// order in which features are visited does not matter.
 template <typename RT>
 __device__ __forceinline__ void small_node(const LevelArgs &a, const RT *__restrict__ Rr, int j, int lane)
 {
@@ -404,62 +427,60 @@ __device__ __forceinline__ void small_node(const LevelArgs &a, const RT *__restr
         return;
     }
     const size_t tb = (size_t)nd.tree * (size_t)a.row_cap + nd.start;
-    const bool valid = lane < (int)nd.len;
+    const int K = nd.len <= 2 ? 2 : (int)(1u << (32 - __clz((int)nd.len - 1)));
+    const int P = 32 / K;                                        // features per pass
+    const int pos = lane & (K - 1), seg = lane / K;
+    const bool valid = pos < (int)nd.len;
     Entry e;
     e.row = 0u; e.w = 0u; e.wy = 0;
-    if (valid) e = load_entry(a.rows_in + tb + lane);
+    if (valid) e = load_entry(a.rows_in + tb + pos);
     const size_t rec = (size_t)e.row * (size_t)a.F;
 
     uint32_t mask[4];
     warp_mtry(a, a.tree_rng[nd.tree], nd.idx, mask);
+    const int n_tried = __popc(mask[0]) + __popc(mask[1]) + __popc(mask[2]) + __popc(mask[3]);
 
-    // sorting network width: the smallest power of two >= the node's entries; lanes at or
-    // above it hold no entry and only ever exchange among themselves
-    const int K = nd.len <= 2 ? 2 : (int)(1u << (32 - __clz((int)nd.len - 1)));
     Cand best = cand_none();
-    for (int c = 0; c < 4; ++c) {
-        uint32_t m = mask[c];
-        while (m) {
-            const int f = c * 32 + __ffs(m) - 1;
-            m &= m - 1;
-            const uint32_t rank = valid ? (uint32_t)__ldg(&Rr[rec + f]) : kRankSentinel;
-            // a feature constant over the node has no boundary (lane 0 always holds an entry;
-            // the shuffle runs in every lane before the vote)
-            const uint32_t rank0 = __shfl_sync(kFull, rank, 0);
-            if (__all_sync(kFull, !valid || rank == rank0)) continue;
-            uint32_t key = (rank << 5) | (uint32_t)lane;                 // unique per lane
-            uint32_t w = e.w;
-            long long v = e.wy;
-            // bitonic sort of (key, w, v) over lanes [0, K), ascending key
-            for (int k = 2; k <= K; k <<= 1) {
-                for (int jj = k >> 1; jj > 0; jj >>= 1) {
-                    const uint32_t ok = __shfl_xor_sync(kFull, key, jj);
-                    const uint32_t ow = __shfl_xor_sync(kFull, w, jj);
-                    const long long ov = __shfl_xor_sync(kFull, v, jj);
-                    const bool asc = (lane & k) == 0;
-                    const bool lower = (lane & jj) == 0;
-                    const bool take = (lower == asc) ? (ok < key) : (ok > key);
-                    if (take) { key = ok; w = ow; v = ov; }
-                }
+    for (int q0 = 0; q0 < n_tried; q0 += P) {
+        const int f = (q0 + seg < n_tried) ? nth_feature(mask, q0 + seg) : -1;
+        const bool live = valid && f >= 0;
+        const uint32_t rank = live ? (uint32_t)__ldg(&Rr[rec + f]) : kRankSentinel;
+        // a pass whose features are all constant over the node has no boundary (lane seg*K
+        // always holds an entry; the shuffle runs in every lane before the vote)
+        const uint32_t rank0 = __shfl_sync(kFull, rank, lane & ~(K - 1));
+        if (__all_sync(kFull, !live || rank == rank0)) continue;
+        uint32_t key = (rank << 5) | (uint32_t)pos;                  // unique within a segment
+        uint32_t w = live ? e.w : 0u;
+        long long v = live ? e.wy : 0;
+        // bitonic sort of (key, w, v) within each segment, ascending key
+        for (int k = 2; k <= K; k <<= 1) {
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                const uint32_t ok = __shfl_xor_sync(kFull, key, jj);
+                const uint32_t ow = __shfl_xor_sync(kFull, w, jj);
+                const long long ov = __shfl_xor_sync(kFull, v, jj);
+                const bool asc = (pos & k) == 0;
+                const bool lower = (pos & jj) == 0;
+                const bool take = (lower == asc) ? (ok < key) : (ok > key);
+                if (take) { key = ok; w = ow; v = ov; }
             }
-            const uint32_t r = key >> 5;
-            uint32_t cw = w;
-            long long cs = v;
-            for (int o = 1; o < K; o <<= 1) {
-                const uint32_t tw = __shfl_up_sync(kFull, cw, o);
-                const long long ts = __shfl_up_sync(kFull, cs, o);
-                if (lane >= o) { cw += tw; cs += ts; }
-            }
-            uint32_t nr = __shfl_down_sync(kFull, r, 1);
-            if (lane == 31) nr = kRankSentinel;
-            if (r != kRankSentinel && nr != kRankSentinel && r != nr) {
-                const i128_t delta = cand_delta(nd.n, nd.S, cw, cs);
-                if (delta != 0) {
-                    Cand cd;
-                    cd.h = cand_h(delta, nd.n, cw);
-                    cd.f = f; cd.r = r; cd.nL = cw; cd.SL = cs;
-                    if (cand_better(cd, best, nd.n, nd.S)) best = cd;
-                }
+        }
+        const uint32_t r = key >> 5;
+        uint32_t cw = w;
+        long long cs = v;
+        for (int o = 1; o < K; o <<= 1) {
+            const uint32_t tw = __shfl_up_sync(kFull, cw, o);
+            const long long ts = __shfl_up_sync(kFull, cs, o);
+            if (pos >= o) { cw += tw; cs += ts; }
+        }
+        uint32_t nr = __shfl_down_sync(kFull, r, 1);
+        if (pos == K - 1) nr = kRankSentinel;
+        if (f >= 0 && r != kRankSentinel && nr != kRankSentinel && r != nr) {
+            const i128_t delta = cand_delta(nd.n, nd.S, cw, cs);
+            if (delta != 0) {
+                Cand cd;
+                cd.h = cand_h(delta, nd.n, cw);
+                cd.f = f; cd.r = r; cd.nL = cw; cd.SL = cs;
+                if (cand_better(cd, best, nd.n, nd.S)) best = cd;
             }
         }
     }
@@ -468,12 +489,19 @@ __device__ __forceinline__ void small_node(const LevelArgs &a, const RT *__restr
         if (lane == 0) write_leaf(a.res, j, -1, round_mean(nd.S, nd.n));
         return;
     }
-    const uint32_t rk = valid ? (uint32_t)__ldg(&Rr[rec + best.f]) : kRankSentinel;
-    const bool left = valid && rk <= best.r;
-    const uint32_t bl = __ballot_sync(kFull, left), bv = __ballot_sync(kFull, valid);
+    // partition: entry i on lane i
+    const bool lv = lane < (int)nd.len;
+    Entry el = e;
+    if (K != 32) {
+        el.row = 0u; el.w = 0u; el.wy = 0;
+        if (lv) el = load_entry(a.rows_in + tb + lane);
+    }
+    const uint32_t rk = lv ? (uint32_t)__ldg(&Rr[(size_t)el.row * (size_t)a.F + best.f]) : kRankSentinel;
+    const bool left = lv && rk <= best.r;
+    const uint32_t bl = __ballot_sync(kFull, left), bv = __ballot_sync(kFull, lv);
     const uint32_t lenL = __popc(bl), lt = lanemask_lt();
-    const uint32_t pos = left ? __popc(bl & lt) : lenL + __popc(bv & ~bl & lt);
-    if (valid) store_entry(a.rows_out + tb + pos, e);
+    const uint32_t pos_out = left ? __popc(bl & lt) : lenL + __popc(bv & ~bl & lt);
+    if (lv) store_entry(a.rows_out + tb + pos_out, el);
     if (lane == 0) {
         SplitRes sr;
         sr.feature = best.f; sr.rank = best.r;
@@ -485,7 +513,7 @@ __device__ __forceinline__ void small_node(const LevelArgs &a, const RT *__restr
 
 // one warp per node with at most 32 entries
 template <typename RT>
-__global__ void __launch_bounds__(kSmallThreads) level_small_kernel(LevelArgs a)
+__global__ void __launch_bounds__(kSmallThreads, kSmallCtasPerSm) level_small_kernel(LevelArgs a)
 {
     const RT *__restrict__ Rr = static_cast<const RT *>(a.Rr);
     const int lane = threadIdx.x & 31;
@@ -1356,7 +1384,8 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
             {
                 la.list = small_a; la.list_n = &d_cnt->n_small;
                 const int64_t wpb = kSmallThreads / 32;
-                const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + wpb - 1) / wpb, cps * dev_sms));
+                const int64_t cps_small = p.ctas_per_sm > 0 ? p.ctas_per_sm : kSmallCtasPerSm;
+                const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + wpb - 1) / wpb, cps_small * dev_sms));
                 prof_begin(s, kProfLevelSmall);
                 if (rank8) level_small_kernel<uint8_t><<<grid, kSmallThreads, 0, s>>>(la);
                 else level_small_kernel<uint16_t><<<grid, kSmallThreads, 0, s>>>(la);
