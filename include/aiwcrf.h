@@ -421,6 +421,46 @@ int aiwcrf_select_device_gated(const aiwcrf_forest *forest, const aiwcrf_surroga
                                int32_t *out_best, float *out_pred, uint8_t *out_fallback,
                                aiwcrf_gate_stats *stats, void *cuda_stream);
 
+/* Fit plan: the whole fit of aiwcrf_fit / aiwcrf_fit_subsets captured once as a CUDA graph and
+ * replayed (the batched leave-one-kernel-out fits of Alg. 1 run as one graph launch). The graph
+ * holds the presort, ranks and groups, the bootstrap, and a device-side loop over the tree
+ * levels (a conditional WHILE node whose body grows two levels; a kernel ends it when no node
+ * is left), so no host synchronisation happens inside the fit; the host then packs the forests.
+ * X ((n_features x n_rows), y and subset_rows (or NULL for one forest on all rows) are device
+ * memory bound to the plan and read at every run: a run fits the data they hold then. The plan
+ * sizes its tables from the data at creation (rank width, number of distinct feature vectors);
+ * a run on data that outgrows them fails with AIWCRF_E_LIMIT. subset_offsets is a host array.
+ * Results equal aiwcrf_fit / aiwcrf_fit_subsets on the same data, bit for bit, for every
+ * schedule. The plan owns its device tables (about 150 bytes per (tree, distinct row) pair)
+ * until aiwcrf_fit_plan_free. */
+typedef struct aiwcrf_fit_plan aiwcrf_fit_plan;
+
+/* A launch schedule of the level loop: resident CTAs per SM of the grid-stride level kernels. */
+typedef struct {
+    int32_t level_big_ctas_per_sm;     /* 1..3 */
+    int32_t level_small_ctas_per_sm;   /* 1..4 */
+    float ms;                          /* median wall time of a run with this schedule (tuning) */
+    int32_t reserved;
+} aiwcrf_fit_schedule;
+
+int aiwcrf_fit_plan_create(const aiwcrf_fit_params *params, const float *X, const int64_t *y, int64_t n_rows,
+                           int32_t n_features, const int64_t *subset_offsets, const int32_t *subset_rows,
+                           int32_t n_subsets, void *cuda_stream, aiwcrf_fit_plan **out);
+
+/* Replay the fit; out receives n_subsets forests (1 without subsets). Synchronises the stream. */
+int aiwcrf_fit_plan_run(aiwcrf_fit_plan *plan, void *cuda_stream, aiwcrf_forest **out);
+
+/* Autotuner: times every schedule (reps runs each, median) on the plan's data, keeps the
+ * fastest, and reports them (tried: host array of cap entries or NULL; *n_tried the number
+ * tried; chosen or NULL). */
+int aiwcrf_fit_plan_tune(aiwcrf_fit_plan *plan, int32_t reps, void *cuda_stream, aiwcrf_fit_schedule *tried,
+                         int32_t cap, int32_t *n_tried, aiwcrf_fit_schedule *chosen);
+
+/* Set a schedule explicitly (the graph is captured again). */
+int aiwcrf_fit_plan_set_schedule(aiwcrf_fit_plan *plan, const aiwcrf_fit_schedule *schedule);
+
+int aiwcrf_fit_plan_free(aiwcrf_fit_plan *plan);
+
 /* Counters of the fit that produced the forest (zeros for a deserialized forest). */
 int aiwcrf_forest_stats(const aiwcrf_forest *forest, aiwcrf_fit_stats *out);
 

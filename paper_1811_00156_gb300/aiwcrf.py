@@ -93,6 +93,14 @@ class GateStats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class FitSchedule(C.Structure):
+    _fields_ = [("level_big_ctas_per_sm", C.c_int32), ("level_small_ctas_per_sm", C.c_int32), ("ms", C.c_float),
+                ("reserved", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 class BatchTrace(C.Structure):
     _fields_ = [("t_formed_ns", C.c_int64), ("t_enqueued_ns", C.c_int64), ("t_done_ns", C.c_int64),
                 ("kernels", C.c_int32), ("generation", C.c_int32)]
@@ -113,7 +121,9 @@ EXPORTS = ["aiwcrf_fit", "aiwcrf_fit_subsets", "aiwcrf_predict", "aiwcrf_predict
            "aiwcrf_surrogate_stats", "aiwcrf_surrogate_num_params", "aiwcrf_surrogate_free",
            "aiwcrf_server_create", "aiwcrf_server_submit", "aiwcrf_server_wait", "aiwcrf_server_append",
            "aiwcrf_server_refit", "aiwcrf_server_pause", "aiwcrf_server_stats", "aiwcrf_server_run_load",
-           "aiwcrf_server_trace", "aiwcrf_server_destroy", "aiwcrf_select_device_gated"]
+           "aiwcrf_server_trace", "aiwcrf_server_destroy", "aiwcrf_select_device_gated",
+           "aiwcrf_fit_plan_create", "aiwcrf_fit_plan_run", "aiwcrf_fit_plan_tune", "aiwcrf_fit_plan_set_schedule",
+           "aiwcrf_fit_plan_free"]
 
 _lib = None
 _lock = threading.Lock()
@@ -173,6 +183,13 @@ def load():
         L.aiwcrf_server_run_load.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp, C.c_int64, C.c_double,
                                              C.c_uint64, C.c_int32, _vp, _vp, _vp, C.POINTER(LoadReport)]
         L.aiwcrf_server_destroy.argtypes = [_vp]
+        L.aiwcrf_fit_plan_create.argtypes = [C.POINTER(FitParams), _vp, _vp, C.c_int64, C.c_int32, _vp, _vp,
+                                             C.c_int32, _vp, C.POINTER(_vp)]
+        L.aiwcrf_fit_plan_run.argtypes = [_vp, _vp, _vp]
+        L.aiwcrf_fit_plan_tune.argtypes = [_vp, C.c_int32, _vp, _vp, C.c_int32, C.POINTER(C.c_int32),
+                                           C.POINTER(FitSchedule)]
+        L.aiwcrf_fit_plan_set_schedule.argtypes = [_vp, C.POINTER(FitSchedule)]
+        L.aiwcrf_fit_plan_free.argtypes = [_vp]
         L.aiwcrf_select_device_gated.argtypes = [_vp, _vp, C.POINTER(GateParams), _vp, C.c_int32, C.c_int32, _vp,
                                                  C.c_int32, _vp, _vp, _vp, C.POINTER(GateStats), _vp]
         L.aiwcrf_server_trace.argtypes = [_vp, _vp, C.c_int64, C.POINTER(C.c_int64), _vp, C.c_int64,
@@ -489,6 +506,47 @@ class Server:
                                              nk.ctypes.data, sc.ctypes.data, n, float(rate_per_s), seed, timeout_ms,
                                              best.ctypes.data, gen.ctypes.data, lat.ctypes.data, C.byref(rep)))
         return rep.as_dict(), best, gen, lat
+
+
+class FitPlan:
+    """A fit captured once as a CUDA graph and replayed (include/aiwcrf.h). X, y and subset_rows are
+    device tensors the plan reads at every run; keep them alive while the plan lives."""
+
+    def __init__(self, params: FitParams, X, y, subset_offsets=None, subset_rows=None, stream=None):
+        F, N = _shape(X)
+        self._keep = (X, y, subset_rows)
+        off = None if subset_offsets is None else np.ascontiguousarray(subset_offsets, dtype=np.int64)
+        G = 0 if off is None else int(off.size - 1)
+        h = _vp()
+        _check(load().aiwcrf_fit_plan_create(C.byref(params), _ptr(X), _ptr(y), N, F,
+                                             None if off is None else off.ctypes.data, _ptr(subset_rows), G,
+                                             _stream(stream), C.byref(h)))
+        self.handle = h.value
+        self.n_forests = max(G, 1)
+
+    def run(self, stream=None) -> list:
+        arr = (_vp * self.n_forests)()
+        _check(load().aiwcrf_fit_plan_run(self.handle, _stream(stream), arr))
+        return [Forest(arr[i]) for i in range(self.n_forests)]
+
+    def tune(self, reps: int = 3, stream=None):
+        """(chosen schedule dict, list of every schedule tried)."""
+        tried = (FitSchedule * 16)()
+        n = C.c_int32()
+        chosen = FitSchedule()
+        _check(load().aiwcrf_fit_plan_tune(self.handle, reps, _stream(stream), tried, 16, C.byref(n), C.byref(chosen)))
+        return chosen.as_dict(), [tried[i].as_dict() for i in range(min(n.value, 16))]
+
+    def set_schedule(self, level_big: int, level_small: int):
+        _check(load().aiwcrf_fit_plan_set_schedule(self.handle, C.byref(FitSchedule(level_big, level_small, 0.0, 0))))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().aiwcrf_fit_plan_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
 
 
 def gate_params(var_trees: int = 32, z: float = 1.0, ood: bool = True) -> GateParams:

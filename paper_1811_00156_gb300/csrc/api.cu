@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -364,6 +365,126 @@ int aiwcrf_fit_subsets(const aiwcrf_fit_params *params, const float *X, const in
     if (rc) return rc;
     for (int32_t g = 0; g < n_subsets; ++g) out[g] = fs[(size_t)g];
     cudaStreamSynchronize(s);   // the staged host copy of the rows must outlive its transfer
+    return AIWCRF_OK;
+}
+
+struct aiwcrf_fit_plan {
+    aiwcrf::FitPlan *impl = nullptr;
+    int32_t n_forests = 1;
+};
+
+int aiwcrf_fit_plan_create(const aiwcrf_fit_params *params, const float *X, const int64_t *y, int64_t n_rows,
+                           int32_t n_features, const int64_t *subset_offsets, const int32_t *subset_rows,
+                           int32_t n_subsets, void *cuda_stream, aiwcrf_fit_plan **out)
+{
+    g_last_error.clear();
+    int rc = check_params(params, n_rows, n_features);
+    if (rc) return rc;
+    if (!X || !y || !out) return fail(AIWCRF_E_INVALID_ARG, "X, y and out must not be NULL");
+    *out = nullptr;
+    int dev;
+    if ((rc = current_device(&dev))) return rc;
+    if (classify(X, dev) != kPtrDevice || classify(y, dev) != kPtrDevice ||
+        (subset_rows && classify(subset_rows, dev) != kPtrDevice))
+        return fail(AIWCRF_E_BAD_POINTER, "a fit plan binds device memory: X, y and subset_rows must be on the device");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    std::vector<int64_t> off;
+    int32_t G = 1;
+    if (subset_rows) {
+        if (!subset_offsets || n_subsets < 1) return fail(AIWCRF_E_INVALID_ARG, "subset_offsets and n_subsets >= 1 needed");
+        if ((int64_t)n_subsets * params->num_trees > (int64_t)AIWCRF_MAX_TREES * 16)
+            return fail(AIWCRF_E_LIMIT, "too many trees in one batch");
+        off.assign(subset_offsets, subset_offsets + n_subsets + 1);
+        if (off[0] != 0) return fail(AIWCRF_E_INVALID_ARG, "subset_offsets[0] must be 0");
+        for (int32_t g = 0; g < n_subsets; ++g)
+            if (off[(size_t)g + 1] <= off[(size_t)g]) return fail(AIWCRF_E_INVALID_ARG, "every subset needs >= 1 row");
+        const int64_t total = off[(size_t)n_subsets];
+        std::vector<int32_t> rows((size_t)total);
+        cudaError_t e = cudaMemcpyAsync(rows.data(), subset_rows, sizeof(int32_t) * (size_t)total, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "reading subset_rows");
+        for (int32_t g = 0; g < n_subsets; ++g)
+            for (int64_t k = off[(size_t)g]; k < off[(size_t)g + 1]; ++k)
+                if (rows[(size_t)k] < 0 || rows[(size_t)k] >= n_rows ||
+                    (k > off[(size_t)g] && rows[(size_t)k] <= rows[(size_t)k - 1]))
+                    return fail(AIWCRF_E_INVALID_ARG, "subset rows must be strictly increasing row indices");
+        G = n_subsets;
+    }
+    aiwcrf::FitPlan *impl = nullptr;
+    if ((rc = aiwcrf::fit_plan_create(*params, X, y, n_rows, n_features, off, subset_rows, G, s, &impl))) return rc;
+    auto *pl = new aiwcrf_fit_plan();
+    pl->impl = impl;
+    pl->n_forests = G;
+    *out = pl;
+    return AIWCRF_OK;
+}
+
+int aiwcrf_fit_plan_run(aiwcrf_fit_plan *plan, void *cuda_stream, aiwcrf_forest **out)
+{
+    g_last_error.clear();
+    if (!plan || !out) return fail(AIWCRF_E_INVALID_ARG, "plan and out must not be NULL");
+    std::vector<aiwcrf_forest *> fs;
+    const int rc = aiwcrf::fit_plan_run(plan->impl, (cudaStream_t)cuda_stream, fs);
+    if (rc) return rc;
+    for (size_t g = 0; g < fs.size(); ++g) out[g] = fs[g];
+    return AIWCRF_OK;
+}
+
+int aiwcrf_fit_plan_set_schedule(aiwcrf_fit_plan *plan, const aiwcrf_fit_schedule *schedule)
+{
+    g_last_error.clear();
+    if (!plan || !schedule) return fail(AIWCRF_E_INVALID_ARG, "plan and schedule must not be NULL");
+    return aiwcrf::fit_plan_set_schedule(plan->impl, schedule->level_big_ctas_per_sm, schedule->level_small_ctas_per_sm);
+}
+
+int aiwcrf_fit_plan_tune(aiwcrf_fit_plan *plan, int32_t reps, void *cuda_stream, aiwcrf_fit_schedule *tried,
+                         int32_t cap, int32_t *n_tried, aiwcrf_fit_schedule *chosen)
+{
+    g_last_error.clear();
+    if (!plan || reps < 1 || cap < 0 || (cap > 0 && !tried))
+        return fail(AIWCRF_E_INVALID_ARG, "plan, reps >= 1 and a tried array of cap entries are needed");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    std::vector<aiwcrf_fit_schedule> all;
+    for (int big = 1; big <= 3; ++big)
+        for (int small = 1; small <= 4; ++small) {
+            int rc = aiwcrf::fit_plan_set_schedule(plan->impl, big, small);
+            if (rc) return rc;
+            std::vector<double> ts;
+            for (int r = 0; r <= reps; ++r) {              // one warm-up run
+                std::vector<aiwcrf_forest *> fs;
+                const auto t0 = std::chrono::steady_clock::now();
+                rc = aiwcrf::fit_plan_run(plan->impl, s, fs);
+                const auto t1 = std::chrono::steady_clock::now();
+                for (auto f : fs) forest_release(f);
+                if (rc) return rc;
+                if (r > 0) ts.push_back(std::chrono::duration<double, std::milli>(t1 - t0).count());
+            }
+            std::sort(ts.begin(), ts.end());
+            aiwcrf_fit_schedule sc;
+            sc.level_big_ctas_per_sm = big;
+            sc.level_small_ctas_per_sm = small;
+            sc.ms = (float)ts[ts.size() / 2];
+            sc.reserved = 0;
+            all.push_back(sc);
+        }
+    size_t bi = 0;
+    for (size_t i = 1; i < all.size(); ++i)
+        if (all[i].ms < all[bi].ms) bi = i;
+    int rc = aiwcrf::fit_plan_set_schedule(plan->impl, all[bi].level_big_ctas_per_sm, all[bi].level_small_ctas_per_sm);
+    if (rc) return rc;
+    for (int32_t i = 0; i < cap && (size_t)i < all.size(); ++i) tried[i] = all[(size_t)i];
+    if (n_tried) *n_tried = (int32_t)all.size();
+    if (chosen) *chosen = all[bi];
+    return AIWCRF_OK;
+}
+
+int aiwcrf_fit_plan_free(aiwcrf_fit_plan *plan)
+{
+    g_last_error.clear();
+    if (!plan) return AIWCRF_OK;
+    cudaDeviceSynchronize();
+    aiwcrf::fit_plan_free(plan->impl);
+    delete plan;
     return AIWCRF_OK;
 }
 

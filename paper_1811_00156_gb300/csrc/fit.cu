@@ -25,6 +25,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -178,6 +179,7 @@ struct BootArgs {
     const uint32_t *grp_off;        // G + 1
     const uint32_t *grp_rows;       // rows in group order
     uint32_t G;
+    const uint32_t *G_ptr;          // when set, the group count is read here
     uint32_t seed_lo, seed_hi;
     int bootstrap;
     uint32_t *gcnt;                 // global byte counters (may be null)
@@ -250,11 +252,12 @@ __global__ void __launch_bounds__(kBootThreads) bootstrap_kernel(BootArgs a)
     unsigned long long acc_n = 0;
     long long acc_s = 0;
     Entry *out = a.rows_out + (size_t)t * (size_t)a.row_cap;
-    for (uint32_t g0 = 0; g0 < a.G; g0 += kBootThreads) {
+    const uint32_t G = a.G_ptr ? *a.G_ptr : a.G;
+    for (uint32_t g0 = 0; g0 < G; g0 += kBootThreads) {
         const uint32_t g = g0 + tid;
         uint32_t sw = 0, rep = 0;
         long long swy = 0;
-        if (g < a.G) {
+        if (g < G) {
             const uint32_t e = a.grp_off[g + 1];
             rep = a.grp_rows[a.grp_off[g]];
             for (uint32_t k = a.grp_off[g]; k < e; ++k) {
@@ -271,7 +274,10 @@ __global__ void __launch_bounds__(kBootThreads) bootstrap_kernel(BootArgs a)
         if (sw > 0) {
             Entry en;
             en.row = rep; en.w = sw; en.wy = swy;
-            store_entry(&out[running + incl - 1u], en);
+            // entries never outnumber the row capacity when it was sized from this data; a
+            // replayed plan on data with more groups than it was built for flags it instead
+            if ((int64_t)(running + incl - 1u) < a.row_cap) store_entry(&out[running + incl - 1u], en);
+            else atomicOr(a.err, kErrCapacity);
             acc_n += sw;
             acc_s += swy;
         }
@@ -289,7 +295,9 @@ __global__ void __launch_bounds__(kBootThreads) bootstrap_kernel(BootArgs a)
         long long ss = 0;
         for (int w = 0; w < kBootThreads / 32; ++w) { sn += red_n[w]; ss += red_s[w]; }
         NodeRec r;
-        r.tree = (uint32_t)t; r.idx = 0u; r.start = 0u; r.len = running; r.n = (uint32_t)sn;
+        // (a flagged overflow keeps the node inside its tree's slice; the fit then fails)
+        r.tree = (uint32_t)t; r.idx = 0u; r.start = 0u; r.len = (uint32_t)min((int64_t)running, a.row_cap);
+        r.n = (uint32_t)sn;
         r.pad = 0u; r.S = ss;
         a.root[t] = r;
         if (running <= (uint32_t)kSmallNodeRows) a.small_list[atomicAdd(&a.counters[0], 1u)] = t;
@@ -324,11 +332,17 @@ struct LevelArgs {
     int32_t F, mtry, min_node, max_depth, depth;
     uint32_t seed_lo, seed_hi;
     SplitRes *res;
+    const uint32_t *depth_ptr;  // when set, the depth is read here (a graph replays one level body)
 };
+
+__device__ __forceinline__ int level_depth(const LevelArgs &a)
+{
+    return a.depth_ptr ? (int)*a.depth_ptr : a.depth;
+}
 
 __device__ __forceinline__ bool node_stops(const LevelArgs &a, const NodeRec &nd)
 {
-    return nd.n <= (uint32_t)a.min_node || (a.max_depth > 0 && a.depth >= a.max_depth);
+    return nd.n <= (uint32_t)a.min_node || (a.max_depth > 0 && level_depth(a) >= a.max_depth);
 }
 
 // a3: the tried features of node (tree, depth, idx). Lane l of the warp evaluates the keys of
@@ -345,7 +359,7 @@ __device__ __forceinline__ void warp_mtry(const LevelArgs &a, uint32_t tg, uint3
         mask[c] = 0u;
         const int f = c * 32 + lane;
         if (c < nch && f < F) {
-            const uint4 u = philox10(make_uint4(tg, (uint32_t)a.depth, idx, (kDomMtry << 16) | (uint32_t)(f >> 2)),
+            const uint4 u = philox10(make_uint4(tg, (uint32_t)level_depth(a), idx, (kDomMtry << 16) | (uint32_t)(f >> 2)),
                                      a.seed_lo, a.seed_hi);
             key[c] = uint4_word(u, f & 3);
         }
@@ -1107,6 +1121,117 @@ int check_err_flags(uint32_t err)
     if (err & kErrCard) return fail(AIWCRF_E_LIMIT, "a feature column has more than 65,536 distinct values");
     if (err & kErrBootOverflow) return fail(AIWCRF_E_LIMIT, "a bootstrap multiplicity exceeded 255");
     if (err & kErrTimeout) return fail(AIWCRF_E_TIMEOUT, "a bounded device wait gave up");
+    if (err & kErrCapacity)
+        return fail(AIWCRF_E_LIMIT, "the data outgrew the fit plan (more groups, wider ranks or deeper trees)");
+    return AIWCRF_OK;
+}
+
+// what the level loop leaves behind, for packing into forests
+struct PackIn {
+    const aiwcrf_fit_params *p;
+    int64_t T, Tper;
+    int32_t G;
+    int64_t N;
+    int32_t F;
+    int device;
+    const uint32_t *tree_base;     // nodes per tree
+    const GrowStats *d_stats;
+    const PackedRec *packed;
+    size_t packed_n;
+    int levels;
+    const uint32_t *d_inbag;       // or null
+    int64_t inbag_words;
+    const float *d_vals;
+    const uint32_t *d_card;
+    uint32_t max_card;
+    bool rank8;
+    uint32_t n_groups;
+};
+
+// One forest per tree group, trees padded to an even node count (16-byte aligned); nodes placed
+// by pack_kernel, padding by pad_kernel, compact copies built. Enqueued on s; the caller
+// synchronises before using the forests.
+int package_forests(const PackIn &in, cudaStream_t s, std::vector<aiwcrf_forest *> &out)
+{
+    int rc = AIWCRF_OK;
+    const int64_t T = in.T, Tper = in.Tper;
+    const int32_t G = in.G, F = in.F;
+    std::vector<uint32_t> h_tot((size_t)T);
+    AIWCRF_CUDA(cudaMemcpyAsync(h_tot.data(), in.tree_base, sizeof(uint32_t) * (size_t)T, cudaMemcpyDeviceToHost, s));
+    GrowStats hs;
+    AIWCRF_CUDA(cudaMemcpyAsync(&hs, in.d_stats, sizeof(GrowStats), cudaMemcpyDeviceToHost, s));
+    AIWCRF_CUDA(cudaStreamSynchronize(s));
+
+    std::vector<aiwcrf_forest *> forests((size_t)G, nullptr);
+    struct Guard {
+        std::vector<aiwcrf_forest *> *v;
+        bool keep = false;
+        ~Guard() {
+            if (keep) return;
+            for (auto f : *v) forest_release(f);
+        }
+    } guard{&forests};
+    std::vector<uint64_t *> h_dst((size_t)T), h_cdst((size_t)T);
+    for (int32_t g = 0; g < G; ++g) {
+        aiwcrf_forest *fr = new aiwcrf_forest();
+        forests[(size_t)g] = fr;
+        fr->F = F; fr->T = Tper; fr->device = in.device;
+        fr->tree_off.assign((size_t)Tper + 1, 0);
+        for (int64_t k = 0; k < Tper; ++k) {
+            const int64_t cnt = h_tot[(size_t)(g * Tper + k)];
+            fr->tree_off[(size_t)k + 1] = fr->tree_off[(size_t)k] + ((cnt + 1) & ~(int64_t)1);
+            fr->max_tree_nodes = std::max(fr->max_tree_nodes, (cnt + 1) & ~(int64_t)1);
+        }
+        fr->num_nodes = fr->tree_off[(size_t)Tper];
+        // the training value tables code the queries at predict time
+        fr->max_card = in.max_card;
+        fr->fstride = std::max<int64_t>(in.max_card, 1);
+        if (in.d_inbag) { fr->oob_rows = in.N; fr->inbag_words = in.inbag_words; }
+        AIWCRF_CUDA(forest_alloc(fr, s));
+        if (in.d_inbag)
+            AIWCRF_CUDA(cudaMemcpyAsync(fr->d_inbag, in.d_inbag + (size_t)g * (size_t)Tper * (size_t)in.inbag_words,
+                                        sizeof(uint32_t) * (size_t)Tper * (size_t)in.inbag_words, cudaMemcpyDeviceToDevice, s));
+        AIWCRF_CUDA(cudaMemcpy2DAsync(fr->d_fvals, sizeof(float) * (size_t)fr->fstride, in.d_vals,
+                                      sizeof(float) * (size_t)in.N, sizeof(float) * (size_t)in.max_card, (size_t)F,
+                                      cudaMemcpyDeviceToDevice, s));
+        AIWCRF_CUDA(cudaMemcpyAsync(fr->d_fcard, in.d_card, sizeof(uint32_t) * (size_t)F, cudaMemcpyDeviceToDevice, s));
+        AIWCRF_CUDA(cudaMemcpyAsync(fr->d_tree_off, fr->tree_off.data(), sizeof(int64_t) * (size_t)(Tper + 1),
+                                    cudaMemcpyHostToDevice, s));
+        for (int64_t k = 0; k < Tper; ++k) {
+            h_dst[(size_t)(g * Tper + k)] = fr->d_nodes + fr->tree_off[(size_t)k];
+            h_cdst[(size_t)(g * Tper + k)] = fr->d_cnodes + fr->tree_off[(size_t)k];
+        }
+        fr->stats.num_trees = Tper;
+        fr->stats.total_nodes = 0;
+        for (int64_t k = 0; k < Tper; ++k) fr->stats.total_nodes += h_tot[(size_t)(g * Tper + k)];
+        fr->stats.levels = in.levels;
+        fr->stats.n_features = F;
+        fr->stats.mtry = in.p->mtry;
+        fr->stats.rank_bytes = in.rank8 ? 1 : 2;
+        fr->stats.groups = in.n_groups;
+        if (G == 1) {
+            fr->stats.entries_evaluated = (int64_t)hs.entries_evaluated;
+            fr->stats.entries_partitioned = (int64_t)hs.entries_partitioned;
+            fr->stats.nodes_evaluated = (int64_t)hs.nodes_evaluated;
+            fr->stats.nodes_small = (int64_t)hs.nodes_small;
+            fr->stats.entries_evaluated_small = (int64_t)hs.entries_evaluated_small;
+            fr->stats.entries_partitioned_small = (int64_t)hs.entries_partitioned_small;
+        }
+    }
+    Scratch sc(s);
+    uint64_t **d_dst = sc.get<uint64_t *>(2 * (size_t)T, &rc); if (rc) return rc;
+    AIWCRF_CUDA(cudaMemcpyAsync(d_dst, h_dst.data(), sizeof(uint64_t *) * (size_t)T, cudaMemcpyHostToDevice, s));
+    AIWCRF_CUDA(cudaMemcpyAsync(d_dst + T, h_cdst.data(), sizeof(uint64_t *) * (size_t)T, cudaMemcpyHostToDevice, s));
+    prof_begin(s, kProfPack);
+    pack_kernel<<<(unsigned)((in.packed_n + 255) / 256), 256, 0, s>>>(in.packed, (int64_t)in.packed_n, d_dst, d_dst + T);
+    AIWCRF_LAUNCH_CHECK("pack_kernel");
+    pad_kernel<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(in.tree_base, T, d_dst, d_dst + T);
+    AIWCRF_LAUNCH_CHECK("pad_kernel");
+    prof_end(s, kProfPack);
+    for (auto fr : forests)
+        if ((rc = forest_build_compact(fr, s)) != AIWCRF_OK) return rc;
+    guard.keep = true;
+    out = forests;
     return AIWCRF_OK;
 }
 
@@ -1324,6 +1449,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         ba.rows_out = rows_a; ba.row_cap = row_cap; ba.root = nodes_cur;
         ba.small_list = small_a; ba.big_list = big_a; ba.counters = &d_cnt->n_small; ba.err = d_err;
         ba.inbag = d_inbag; ba.inbag_words = inbag_words;
+        ba.G_ptr = nullptr;
         prof_begin(s, kProfBoot);
         bootstrap_kernel<<<(unsigned)T, kBootThreads, smem_bytes, s>>>(ba);
         AIWCRF_LAUNCH_CHECK("bootstrap_kernel");
@@ -1351,6 +1477,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     la.row_cap = row_cap; la.Rr = d_Rr; la.vals = d_vals; la.card = d_card; la.N = N;
     la.tree_rng = d_rng; la.F = F; la.mtry = p.mtry; la.min_node = p.min_node_size;
     la.max_depth = p.max_depth; la.seed_lo = (uint32_t)p.seed; la.seed_hi = (uint32_t)(p.seed >> 32);
+    la.depth_ptr = nullptr;
 
     Entry *rin = rows_a, *rout = rows_b;
     int depth = 0;
@@ -1426,87 +1553,416 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         C_known = h_cnt->C;
         packed_known = h_cnt->packed_off;
     }
-    const size_t packed_n = (size_t)packed_known;
-    depth = (int)h_cnt->levels;
+    PackIn pin;
+    pin.p = &p; pin.T = T; pin.Tper = Tper; pin.G = G; pin.N = N; pin.F = F; pin.device = device;
+    pin.tree_base = tree_base; pin.d_stats = d_stats; pin.packed = packed; pin.packed_n = (size_t)packed_known;
+    pin.levels = (int)h_cnt->levels; pin.d_inbag = d_inbag; pin.inbag_words = inbag_words;
+    pin.d_vals = d_vals; pin.d_card = d_card; pin.max_card = max_card; pin.rank8 = rank8; pin.n_groups = n_groups;
+    rc = package_forests(pin, s, out);
+    sc.release();
+    if (rc == AIWCRF_OK) AIWCRF_CUDA(cudaStreamSynchronize(s));
+    return rc;
+}
 
-    std::vector<uint32_t> h_tot((size_t)T);
-    AIWCRF_CUDA(cudaMemcpyAsync(h_tot.data(), tree_base, sizeof(uint32_t) * (size_t)T, cudaMemcpyDeviceToHost, s));
-    GrowStats hs;
-    AIWCRF_CUDA(cudaMemcpyAsync(&hs, d_stats, sizeof(GrowStats), cudaMemcpyDeviceToHost, s));
-    AIWCRF_CUDA(cudaStreamSynchronize(s));
 
-    // pack: one buffer per forest, trees padded to an even node count (16-byte aligned)
-    std::vector<aiwcrf_forest *> forests((size_t)G, nullptr);
-    struct Guard {
-        std::vector<aiwcrf_forest *> *v;
-        bool keep = false;
-        ~Guard() {
-            if (keep) return;
-            for (auto f : *v) forest_release(f);
-        }
-    } guard{&forests};
-    std::vector<uint64_t *> h_dst((size_t)T), h_cdst((size_t)T);
-    for (int32_t g = 0; g < G; ++g) {
-        aiwcrf_forest *fr = new aiwcrf_forest();
-        forests[(size_t)g] = fr;
-        fr->F = F; fr->T = Tper; fr->device = device;
-        fr->tree_off.assign((size_t)Tper + 1, 0);
-        for (int64_t k = 0; k < Tper; ++k) {
-            const int64_t cnt = h_tot[(size_t)(g * Tper + k)];
-            fr->tree_off[(size_t)k + 1] = fr->tree_off[(size_t)k] + ((cnt + 1) & ~(int64_t)1);
-            fr->max_tree_nodes = std::max(fr->max_tree_nodes, (cnt + 1) & ~(int64_t)1);
-        }
-        fr->num_nodes = fr->tree_off[(size_t)Tper];
-        // the training value tables code the queries at predict time
-        fr->max_card = max_card;
-        fr->fstride = std::max<int64_t>(max_card, 1);
-        if (d_inbag) { fr->oob_rows = N; fr->inbag_words = inbag_words; }
-        AIWCRF_CUDA(forest_alloc(fr, s));
-        if (d_inbag)
-            AIWCRF_CUDA(cudaMemcpyAsync(fr->d_inbag, d_inbag + (size_t)g * (size_t)Tper * (size_t)inbag_words,
-                                        sizeof(uint32_t) * (size_t)Tper * (size_t)inbag_words, cudaMemcpyDeviceToDevice, s));
-        AIWCRF_CUDA(cudaMemcpy2DAsync(fr->d_fvals, sizeof(float) * (size_t)fr->fstride, d_vals, sizeof(float) * (size_t)N,
-                                      sizeof(float) * (size_t)max_card, (size_t)F, cudaMemcpyDeviceToDevice, s));
-        AIWCRF_CUDA(cudaMemcpyAsync(fr->d_fcard, d_card, sizeof(uint32_t) * (size_t)F, cudaMemcpyDeviceToDevice, s));
-        AIWCRF_CUDA(cudaMemcpyAsync(fr->d_tree_off, fr->tree_off.data(), sizeof(int64_t) * (size_t)(Tper + 1),
-                                    cudaMemcpyHostToDevice, s));
-        for (int64_t k = 0; k < Tper; ++k) {
-            h_dst[(size_t)(g * Tper + k)] = fr->d_nodes + fr->tree_off[(size_t)k];
-            h_cdst[(size_t)(g * Tper + k)] = fr->d_cnodes + fr->tree_off[(size_t)k];
-        }
-        fr->stats.num_trees = Tper;
-        fr->stats.total_nodes = 0;
-        for (int64_t k = 0; k < Tper; ++k) fr->stats.total_nodes += h_tot[(size_t)(g * Tper + k)];
-        fr->stats.levels = depth;
-        fr->stats.n_features = F;
-        fr->stats.mtry = p.mtry;
-        fr->stats.rank_bytes = rank8 ? 1 : 2;
-        fr->stats.groups = n_groups;
-        if (G == 1) {
-            fr->stats.entries_evaluated = (int64_t)hs.entries_evaluated;
-            fr->stats.entries_partitioned = (int64_t)hs.entries_partitioned;
-            fr->stats.nodes_evaluated = (int64_t)hs.nodes_evaluated;
-            fr->stats.nodes_small = (int64_t)hs.nodes_small;
-            fr->stats.entries_evaluated_small = (int64_t)hs.entries_evaluated_small;
-            fr->stats.entries_partitioned_small = (int64_t)hs.entries_partitioned_small;
+// ------------------------------------------------------------------------------------------
+// Fit plan: the whole fit as one CUDA graph. The presort, ranks and groups, the bootstrap and a
+// device-side WHILE loop whose body grows two tree levels (even and odd halves of the ping-pong
+// buffers) and then lets a one-thread kernel decide, from the device's node count, whether the
+// loop continues. No host synchronisation happens between the first kernel and the last level;
+// the host then reads the counts and packs the forests. Sizes the graph cannot learn without
+// the host (one- or two-byte ranks, the number of groups) are taken from a probe of the data at
+// creation; a replay on data that outgrows them sets kErrCapacity instead of writing out of
+// bounds, and the tables are sized for the worst case of that capacity.
+// ------------------------------------------------------------------------------------------
+// the plan's value tables (and one-byte ranks) hold max_card values per column
+__global__ void plan_check_kernel(const uint32_t *card, int F, uint32_t max_card, uint32_t *err)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f < F && card[f] > max_card) atomicOr(err, kErrCapacity);
+}
+
+__global__ void level_counts_init_kernel(LevelCounts *cnt, uint32_t T)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        cnt->n_small = 0u; cnt->n_big = 0u; cnt->C = T; cnt->levels = 0u; cnt->packed_off = 0ull;
+    }
+}
+
+__global__ void level_loop_cond_kernel(cudaGraphConditionalHandle h, const LevelCounts *cnt, uint32_t limit,
+                                       uint32_t *err)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const bool more = cnt->C > 0u;
+    if (more && cnt->levels >= limit) atomicOr(err, kErrCapacity);
+    if (!more || cnt->levels >= limit) cudaGraphSetConditional(h, 0u);
+}
+
+struct FitPlan {
+    aiwcrf_fit_params p{};
+    const float *dX = nullptr;
+    const int64_t *dy = nullptr;
+    int64_t N = 0;
+    int32_t F = 0, G = 1;
+    std::vector<int64_t> sub_off;
+    const int32_t *d_sub_rows = nullptr;
+    int device = 0, sms = 0;
+    int64_t T = 0, Tper = 0, row_cap = 0, C_max = 0, packed_cap = 0, inbag_words = 0;
+    bool rank8 = true;
+    uint32_t max_card = 0, probe_groups = 0;
+    int boot_smem = 0;
+    int64_t gstride = 0;
+    std::vector<void *> bufs;
+    // device buffers
+    uint32_t *d_err = nullptr, *d_counters = nullptr, *d_card = nullptr;
+    GrowStats *d_stats = nullptr;
+    uint16_t *d_R = nullptr;
+    float *d_vals = nullptr;
+    uint32_t *kA = nullptr, *vA = nullptr, *kB = nullptr, *vB = nullptr, *hist = nullptr;
+    void *d_Rr = nullptr;
+    uint32_t *grp_off = nullptr;
+    int64_t *d_pool_off = nullptr;
+    uint32_t *d_pool_len = nullptr, *d_rng = nullptr;
+    Entry *rows_a = nullptr, *rows_b = nullptr;
+    NodeRec *nodes_a = nullptr, *nodes_b = nullptr;
+    SplitRes *res = nullptr;
+    uint32_t *excl = nullptr, *block_sums = nullptr;
+    int32_t *small_l = nullptr, *big_l = nullptr;
+    PackedRec *packed = nullptr;
+    LevelCounts *d_cnt = nullptr;
+    uint32_t *d_inbag = nullptr, *gcnt = nullptr;
+    uint32_t *toff_a = nullptr, *toff_b = nullptr, *tree_base = nullptr;
+    // schedule and graph
+    int cps_big = 3, cps_small = kSmallCtasPerSm;
+    cudaGraphExec_t exec = nullptr;
+    int64_t prefix_launches = 0;
+
+    template <class U>
+    int alloc(U **ptr, size_t count)
+    {
+        void *q = nullptr;
+        const cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(U));
+        if (e != cudaSuccess)
+            return fail(AIWCRF_E_OOM, std::string("fit plan: device allocation of ") +
+                                          std::to_string(count * sizeof(U)) + " bytes failed");
+        bufs.push_back(q);
+        *ptr = static_cast<U *>(q);
+        return AIWCRF_OK;
+    }
+    ~FitPlan()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        for (auto b : bufs) cudaFree(b);
+    }
+};
+
+namespace {
+
+// phase A (presort, ranks, groups) on s; with `probe` the host reads back what sizes the rest
+int plan_phase_a(FitPlan &P, cudaStream_t s, bool probe)
+{
+    const int64_t N = P.N;
+    const int32_t F = P.F;
+    const unsigned yblocks = (unsigned)((N + 255) / 256);
+    AIWCRF_CUDA(cudaMemsetAsync(P.d_err, 0, sizeof(uint32_t), s));
+    AIWCRF_CUDA(cudaMemsetAsync(P.d_stats, 0, sizeof(GrowStats), s));
+    AIWCRF_CUDA(cudaMemsetAsync(P.d_counters, 0, 4 * sizeof(uint32_t), s));
+    check_y_kernel<<<yblocks, 256, 0, s>>>(P.dy, N, P.d_err);
+    AIWCRF_LAUNCH_CHECK("check_y_kernel");
+    key_init_kernel<<<dim3(yblocks, (unsigned)F), 256, 0, s>>>(P.dX, N, P.kA, P.vA, P.d_err);
+    AIWCRF_LAUNCH_CHECK("key_init_kernel");
+    int rc;
+    if ((rc = radix_sort_segments(P.kA, P.vA, P.kB, P.vB, N, F, N, P.hist, s)) != AIWCRF_OK) return rc;
+    dense_rank_kernel<<<F, 1024, 0, s>>>(P.kA, P.vA, N, P.d_R, P.d_vals, P.d_card, P.d_err);
+    AIWCRF_LAUNCH_CHECK("dense_rank_kernel");
+    if (probe) {
+        std::vector<uint32_t> h_card((size_t)F);
+        uint32_t h_err = 0;
+        AIWCRF_CUDA(cudaMemcpyAsync(h_card.data(), P.d_card, sizeof(uint32_t) * (size_t)F, cudaMemcpyDeviceToHost, s));
+        AIWCRF_CUDA(cudaMemcpyAsync(&h_err, P.d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        AIWCRF_CUDA(cudaStreamSynchronize(s));
+        if ((rc = check_err_flags(h_err)) != AIWCRF_OK) return rc;
+        P.max_card = *std::max_element(h_card.begin(), h_card.end());
+        P.rank8 = P.max_card <= 256;
+        if (P.rank8) { if ((rc = P.alloc(reinterpret_cast<uint8_t **>(&P.d_Rr), (size_t)F * (size_t)N))) return rc; }
+        else if ((rc = P.alloc(reinterpret_cast<uint16_t **>(&P.d_Rr), (size_t)F * (size_t)N))) return rc;
+    } else {
+        plan_check_kernel<<<(unsigned)((F + 127) / 128), 128, 0, s>>>(P.d_card, F, P.max_card, P.d_err);
+        AIWCRF_LAUNCH_CHECK("plan_check_kernel");
+    }
+    const unsigned rb = (unsigned)((N + 255) / 256);
+    if (P.rank8) {
+        rank_rows_kernel<uint8_t><<<rb, 256, 0, s>>>(P.d_R, N, F, (uint8_t *)P.d_Rr);
+        hash_rows_kernel<uint8_t><<<rb, 256, 0, s>>>((const uint8_t *)P.d_Rr, N, F, P.kA, P.vA);
+    } else {
+        rank_rows_kernel<uint16_t><<<rb, 256, 0, s>>>(P.d_R, N, F, (uint16_t *)P.d_Rr);
+        hash_rows_kernel<uint16_t><<<rb, 256, 0, s>>>((const uint16_t *)P.d_Rr, N, F, P.kA, P.vA);
+    }
+    count_launches(1);
+    AIWCRF_LAUNCH_CHECK("rank_rows / hash_rows");
+    if ((rc = radix_sort_segments(P.kA, P.vA, P.kB, P.vB, N, 1, N, P.hist, s)) != AIWCRF_OK) return rc;
+    if (P.rank8) group_flags_kernel<uint8_t><<<rb, 256, 0, s>>>((const uint8_t *)P.d_Rr, N, F, P.kA, P.vA, P.kB);
+    else group_flags_kernel<uint16_t><<<rb, 256, 0, s>>>((const uint16_t *)P.d_Rr, N, F, P.kA, P.vA, P.kB);
+    const int gblocks = (int)((N + kScanTile - 1) / kScanTile);
+    flag_scan_reduce_kernel<<<gblocks, kScanThreads, 0, s>>>(P.kB, N, P.hist);
+    scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(P.hist, gblocks);
+    flag_scan_write_kernel<<<gblocks, kScanThreads, 0, s>>>(P.kB, N, P.hist, gblocks, P.vB);
+    group_offsets_kernel<<<rb, 256, 0, s>>>(P.kB, P.vB, N, P.grp_off, P.d_counters + 2);
+    count_launches(4);
+    AIWCRF_LAUNCH_CHECK("grouping kernels");
+    if (probe) {
+        AIWCRF_CUDA(cudaMemcpyAsync(&P.probe_groups, P.d_counters + 2, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        AIWCRF_CUDA(cudaStreamSynchronize(s));
+    }
+    return AIWCRF_OK;
+}
+
+// the bootstrap and the per-tree bookkeeping (captured)
+int plan_bootstrap(FitPlan &P, cudaStream_t s)
+{
+    level_counts_init_kernel<<<1, 32, 0, s>>>(P.d_cnt, (uint32_t)P.T);
+    AIWCRF_LAUNCH_CHECK("level_counts_init_kernel");
+    BootArgs ba;
+    ba.tree_pool_off = P.d_pool_off; ba.tree_pool_len = P.d_pool_len; ba.tree_rng = P.d_rng;
+    ba.sub_rows = P.d_sub_rows; ba.y = P.dy; ba.N = P.N; ba.grp_off = P.grp_off; ba.grp_rows = P.vA;
+    ba.G = 0u; ba.G_ptr = P.d_counters + 2;
+    ba.seed_lo = (uint32_t)P.p.seed; ba.seed_hi = (uint32_t)(P.p.seed >> 32);
+    ba.bootstrap = P.p.bootstrap; ba.gcnt = P.gcnt; ba.gcnt_stride = P.gstride;
+    ba.smem_words = P.gcnt ? 0 : (int)((P.N + 3) / 4);
+    ba.rows_out = P.rows_a; ba.row_cap = P.row_cap; ba.root = P.nodes_a;
+    ba.small_list = P.small_l; ba.big_list = P.big_l; ba.counters = &P.d_cnt->n_small; ba.err = P.d_err;
+    ba.inbag = P.d_inbag; ba.inbag_words = P.inbag_words;
+    bootstrap_kernel<<<(unsigned)P.T, kBootThreads, P.boot_smem, s>>>(ba);
+    AIWCRF_LAUNCH_CHECK("bootstrap_kernel");
+    iota_kernel<<<(unsigned)((P.T + 256) / 256), 256, 0, s>>>(P.toff_a, (int)P.T);
+    AIWCRF_LAUNCH_CHECK("iota_kernel");
+    AIWCRF_CUDA(cudaMemsetAsync(P.tree_base, 0, sizeof(uint32_t) * (size_t)P.T, s));
+    return AIWCRF_OK;
+}
+
+// one level from (nodes_in, rin, toff_in) to (nodes_out, rout, toff_out), at the depth the
+// device's level counter holds; fixed grids (the kernels stride over the device's counts)
+int plan_level(FitPlan &P, cudaStream_t s, NodeRec *nodes_in, NodeRec *nodes_out, Entry *rin, Entry *rout,
+               uint32_t *toff_in, uint32_t *toff_out)
+{
+    LevelArgs la;
+    la.row_cap = P.row_cap; la.Rr = P.d_Rr; la.vals = P.d_vals; la.card = P.d_card; la.N = P.N;
+    la.tree_rng = P.d_rng; la.F = P.F; la.mtry = P.p.mtry; la.min_node = P.p.min_node_size;
+    la.max_depth = P.p.max_depth; la.seed_lo = (uint32_t)P.p.seed; la.seed_hi = (uint32_t)(P.p.seed >> 32);
+    la.depth = 0; la.depth_ptr = &P.d_cnt->levels;
+    la.nodes = nodes_in; la.rows_in = rin; la.rows_out = rout; la.res = P.res;
+    const int big_smem = 4096 * 12;
+    la.list = P.big_l; la.list_n = &P.d_cnt->n_big;
+    const unsigned gbig = (unsigned)(P.cps_big * P.sms), gsmall = (unsigned)(P.cps_small * P.sms);
+    if (P.rank8) level_big_kernel<uint8_t><<<gbig, kBigThreads, big_smem, s>>>(la, 4096);
+    else level_big_kernel<uint16_t><<<gbig, kBigThreads, big_smem, s>>>(la, 4096);
+    AIWCRF_LAUNCH_CHECK("level_big_kernel");
+    la.list = P.small_l; la.list_n = &P.d_cnt->n_small;
+    if (P.rank8) level_small_kernel<uint8_t><<<gsmall, kSmallThreads, 0, s>>>(la);
+    else level_small_kernel<uint16_t><<<gsmall, kSmallThreads, 0, s>>>(la);
+    AIWCRF_LAUNCH_CHECK("level_small_kernel");
+    const unsigned sgrid = (unsigned)(2 * P.sms);
+    scan_reduce_kernel<<<sgrid, kScanThreads, 0, s>>>(P.res, P.d_cnt, P.block_sums);
+    scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(P.block_sums, 0, P.d_cnt);
+    scan_write_kernel<<<sgrid, kScanThreads, 0, s>>>(P.res, P.d_cnt, P.block_sums, P.excl);
+    count_launches(2);
+    AIWCRF_LAUNCH_CHECK("scan kernels");
+    AIWCRF_CUDA(cudaMemsetAsync(P.d_cnt, 0, 2 * sizeof(uint32_t), s));
+    FinalArgs fa;
+    fa.nodes = nodes_in; fa.res = P.res; fa.excl = P.excl; fa.tree_off = toff_in; fa.tree_base = P.tree_base;
+    fa.cnt = P.d_cnt; fa.next = nodes_out; fa.small_list = P.small_l; fa.big_list = P.big_l;
+    fa.packed = P.packed; fa.stats = P.d_stats;
+    finalize_kernel<<<(unsigned)(8 * P.sms), 256, 0, s>>>(fa);
+    AIWCRF_LAUNCH_CHECK("finalize_kernel");
+    tree_update_kernel<<<(unsigned)((P.T + 256) / 256), 256, 0, s>>>(toff_in, P.tree_base, P.excl, toff_out, (int)P.T,
+                                                                     P.d_cnt);
+    AIWCRF_LAUNCH_CHECK("tree_update_kernel");
+    return AIWCRF_OK;
+}
+
+// capture the graph for the plan's current schedule and instantiate it
+int plan_capture(FitPlan &P)
+{
+    cudaStream_t cs = nullptr, bs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+    struct Streams { cudaStream_t a, b; ~Streams() { if (a) cudaStreamDestroy(a); if (b) cudaStreamDestroy(b); } } st{cs, bs};
+    if (e != cudaSuccess) return cuda_fail(e, "fit plan: streams");
+    cudaGraph_t g = nullptr;
+    struct G { cudaGraph_t *g; ~G() { if (*g) cudaGraphDestroy(*g); } } gg{&g};
+    const int64_t l0 = aiwcrf_launch_count();
+    AIWCRF_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int rc = plan_phase_a(P, cs, false);
+    if (rc == AIWCRF_OK) rc = plan_bootstrap(P, cs);
+    cudaGraphConditionalHandle h = 0;
+    if (rc == AIWCRF_OK) {
+        cudaStreamCaptureStatus cst;
+        cudaGraph_t cg = nullptr;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps);
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, cg, 1u, cudaGraphCondAssignDefault);
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t cn = nullptr;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&cn, cg, deps, nullptr, ndeps, &np);
+        if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (e == cudaSuccess)
+            e = cudaStreamBeginCaptureToGraph(bs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "fit plan: level loop node");
+        } else {
+            rc = plan_level(P, bs, P.nodes_a, P.nodes_b, P.rows_a, P.rows_b, P.toff_a, P.toff_b);
+            if (rc == AIWCRF_OK) rc = plan_level(P, bs, P.nodes_b, P.nodes_a, P.rows_b, P.rows_a, P.toff_b, P.toff_a);
+            if (rc == AIWCRF_OK) {
+                level_loop_cond_kernel<<<1, 32, 0, bs>>>(h, P.d_cnt, (uint32_t)(P.row_cap + 2), P.d_err);
+                count_launches(1);
+                const cudaError_t e2 = cudaGetLastError();
+                if (e2 != cudaSuccess) rc = cuda_fail(e2, "level_loop_cond_kernel launch");
+            }
+            cudaGraph_t body = nullptr;
+            const cudaError_t e3 = cudaStreamEndCapture(bs, &body);
+            if (rc == AIWCRF_OK && e3 != cudaSuccess) rc = cuda_fail(e3, "fit plan: level body capture");
         }
     }
-    uint64_t **d_dst = sc.get<uint64_t *>(2 * (size_t)T, &rc); if (rc) return rc;
-    AIWCRF_CUDA(cudaMemcpyAsync(d_dst, h_dst.data(), sizeof(uint64_t *) * (size_t)T, cudaMemcpyHostToDevice, s));
-    AIWCRF_CUDA(cudaMemcpyAsync(d_dst + T, h_cdst.data(), sizeof(uint64_t *) * (size_t)T, cudaMemcpyHostToDevice, s));
-    prof_begin(s, kProfPack);
-    pack_kernel<<<(unsigned)((packed_n + 255) / 256), 256, 0, s>>>(packed, (int64_t)packed_n, d_dst, d_dst + T);
-    AIWCRF_LAUNCH_CHECK("pack_kernel");
-    pad_kernel<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(tree_base, T, d_dst, d_dst + T);
-    AIWCRF_LAUNCH_CHECK("pad_kernel");
-    prof_end(s, kProfPack);
-    for (auto fr : forests)
-        if ((rc = forest_build_compact(fr, s)) != AIWCRF_OK) return rc;
-    sc.release();
-    AIWCRF_CUDA(cudaStreamSynchronize(s));
-    guard.keep = true;
-    out = forests;
+    const cudaError_t e4 = cudaStreamEndCapture(cs, &g);
+    if (rc != AIWCRF_OK) return rc;
+    if (e4 != cudaSuccess) return cuda_fail(e4, "fit plan: capture");
+    P.prefix_launches = aiwcrf_launch_count() - l0;
+    count_launches(-(int)P.prefix_launches);          // captured, not run
+    if (P.exec) { cudaGraphExecDestroy(P.exec); P.exec = nullptr; }
+    AIWCRF_CUDA(cudaGraphInstantiate(&P.exec, g, 0));
     return AIWCRF_OK;
+}
+
+}  // namespace
+
+int fit_plan_create(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, int64_t N, int32_t F,
+                    const std::vector<int64_t> &sub_off, const int32_t *d_sub_rows, int32_t G, cudaStream_t s,
+                    FitPlan **out)
+{
+    std::unique_ptr<FitPlan> P(new FitPlan());
+    P->p = p; P->dX = dX; P->dy = dy; P->N = N; P->F = F; P->G = G; P->sub_off = sub_off; P->d_sub_rows = d_sub_rows;
+    P->Tper = p.num_trees;
+    P->T = P->Tper * (int64_t)G;
+    if (P->T > (int64_t)AIWCRF_MAX_TREES * 16) return fail(AIWCRF_E_LIMIT, "too many trees in one batch");
+    AIWCRF_CUDA(cudaGetDevice(&P->device));
+    AIWCRF_CUDA(cudaDeviceGetAttribute(&P->sms, cudaDevAttrMultiProcessorCount, P->device));
+    keep_pool_memory(P->device);
+    int rc;
+    FitPlan &Q = *P;
+    if ((rc = Q.alloc(&Q.d_err, 1)) || (rc = Q.alloc(&Q.d_stats, 1)) || (rc = Q.alloc(&Q.d_counters, 4)) ||
+        (rc = Q.alloc(&Q.d_R, (size_t)F * (size_t)N)) || (rc = Q.alloc(&Q.d_vals, (size_t)F * (size_t)N)) ||
+        (rc = Q.alloc(&Q.d_card, (size_t)F)) || (rc = Q.alloc(&Q.kA, (size_t)F * (size_t)N + 1)) ||
+        (rc = Q.alloc(&Q.vA, (size_t)F * (size_t)N + 1)) || (rc = Q.alloc(&Q.kB, (size_t)F * (size_t)N + 1)) ||
+        (rc = Q.alloc(&Q.vB, (size_t)F * (size_t)N + 1)) || (rc = Q.alloc(&Q.hist, radix_sort_hist_words(N, F))) ||
+        (rc = Q.alloc(&Q.grp_off, (size_t)N + 1)))
+        return rc;
+    // probe: the sizes the graph is built for
+    if ((rc = plan_phase_a(Q, s, true))) return rc;
+
+    std::vector<int64_t> h_pool_off((size_t)Q.T);
+    std::vector<uint32_t> h_pool_len((size_t)Q.T), h_rng((size_t)Q.T);
+    int64_t max_pool = 1;
+    for (int32_t g = 0; g < G; ++g) {
+        const int64_t off = d_sub_rows ? sub_off[(size_t)g] : -1;
+        const int64_t len = d_sub_rows ? sub_off[(size_t)g + 1] - sub_off[(size_t)g] : N;
+        max_pool = std::max(max_pool, len);
+        for (int64_t k = 0; k < Q.Tper; ++k) {
+            const size_t t = (size_t)(g * Q.Tper + k);
+            h_pool_off[t] = off;
+            h_pool_len[t] = (uint32_t)len;
+            h_rng[t] = (uint32_t)(p.first_tree + k);
+        }
+    }
+    Q.row_cap = std::min<int64_t>(max_pool, (int64_t)Q.probe_groups);
+    Q.C_max = Q.T * Q.row_cap;
+    Q.packed_cap = Q.T * (2 * Q.row_cap - 1) + Q.T;
+    const size_t table_bytes = (size_t)Q.C_max * (2 * sizeof(NodeRec) + sizeof(SplitRes) + 4 * sizeof(int32_t) + 8) +
+                               (size_t)Q.packed_cap * sizeof(PackedRec) + 2 * (size_t)Q.C_max * sizeof(Entry);
+    if (table_bytes > ((size_t)16 << 30))
+        return fail(AIWCRF_E_LIMIT, "fit plan: worst-case level tables exceed 16 GiB; use aiwcrf_fit");
+    if ((rc = Q.alloc(&Q.d_pool_off, (size_t)Q.T)) || (rc = Q.alloc(&Q.d_pool_len, (size_t)Q.T)) ||
+        (rc = Q.alloc(&Q.d_rng, (size_t)Q.T)) || (rc = Q.alloc(&Q.rows_a, (size_t)Q.C_max)) ||
+        (rc = Q.alloc(&Q.rows_b, (size_t)Q.C_max)) || (rc = Q.alloc(&Q.nodes_a, (size_t)Q.C_max)) ||
+        (rc = Q.alloc(&Q.nodes_b, (size_t)Q.C_max)) || (rc = Q.alloc(&Q.res, (size_t)Q.C_max)) ||
+        (rc = Q.alloc(&Q.excl, (size_t)Q.C_max + 1)) || (rc = Q.alloc(&Q.block_sums, (size_t)Q.C_max / kScanTile + 2)) ||
+        (rc = Q.alloc(&Q.small_l, (size_t)Q.C_max)) || (rc = Q.alloc(&Q.big_l, (size_t)Q.C_max)) ||
+        (rc = Q.alloc(&Q.packed, (size_t)Q.packed_cap)) || (rc = Q.alloc(&Q.d_cnt, 1)) ||
+        (rc = Q.alloc(&Q.toff_a, (size_t)Q.T + 1)) || (rc = Q.alloc(&Q.toff_b, (size_t)Q.T + 1)) ||
+        (rc = Q.alloc(&Q.tree_base, (size_t)Q.T)))
+        return rc;
+    Q.inbag_words = (N + 31) / 32;
+    if (!d_sub_rows && (rc = Q.alloc(&Q.d_inbag, (size_t)Q.T * (size_t)Q.inbag_words))) return rc;
+    int optin = 0;
+    AIWCRF_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, Q.device));
+    const int boot_smem_words = std::min<int>((optin - 2048) / 4, 56 * 1024);
+    const uint32_t words = (uint32_t)((N + 3) / 4);
+    if ((int)words > boot_smem_words) {
+        Q.gstride = words;
+        if ((rc = Q.alloc(&Q.gcnt, (size_t)Q.T * (size_t)words))) return rc;
+    }
+    Q.boot_smem = Q.gcnt ? 0 : (int)words * 4;
+    AIWCRF_CUDA(cudaMemcpyAsync(Q.d_pool_off, h_pool_off.data(), sizeof(int64_t) * (size_t)Q.T, cudaMemcpyHostToDevice, s));
+    AIWCRF_CUDA(cudaMemcpyAsync(Q.d_pool_len, h_pool_len.data(), sizeof(uint32_t) * (size_t)Q.T, cudaMemcpyHostToDevice, s));
+    AIWCRF_CUDA(cudaMemcpyAsync(Q.d_rng, h_rng.data(), sizeof(uint32_t) * (size_t)Q.T, cudaMemcpyHostToDevice, s));
+    AIWCRF_CUDA(cudaStreamSynchronize(s));
+    AIWCRF_CUDA(cudaFuncSetAttribute(bootstrap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, std::max(Q.boot_smem, 1)));
+    AIWCRF_CUDA(cudaFuncSetAttribute(level_big_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4096 * 12));
+    AIWCRF_CUDA(cudaFuncSetAttribute(level_big_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4096 * 12));
+    if ((rc = plan_capture(Q))) return rc;
+    *out = P.release();
+    return AIWCRF_OK;
+}
+
+int fit_plan_run(FitPlan *P, cudaStream_t s, std::vector<aiwcrf_forest *> &out)
+{
+    AIWCRF_CUDA(cudaGraphLaunch(P->exec, s));
+    LevelCounts *h_cnt = static_cast<LevelCounts *>(pinned_scratch());
+    if (!h_cnt) return fail(AIWCRF_E_OOM, "pinned host buffer");
+    uint32_t *h_err = reinterpret_cast<uint32_t *>(h_cnt + 1);
+    AIWCRF_CUDA(cudaMemcpyAsync(h_cnt, P->d_cnt, sizeof(LevelCounts), cudaMemcpyDeviceToHost, s));
+    AIWCRF_CUDA(cudaMemcpyAsync(h_err, P->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    AIWCRF_CUDA(cudaMemcpyAsync(h_err + 1, P->d_counters + 2, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    AIWCRF_CUDA(cudaStreamSynchronize(s));
+    int rc = check_err_flags(*h_err);
+    if (rc) return rc;
+    const uint32_t n_groups = h_err[1];
+    const int64_t iters = ((int64_t)h_cnt->levels + 1) / 2;
+    count_launches((int)(P->prefix_launches - 15 + 15 * iters));    // the captured body ran iters times
+    PackIn pin;
+    pin.p = &P->p; pin.T = P->T; pin.Tper = P->Tper; pin.G = P->G; pin.N = P->N; pin.F = P->F; pin.device = P->device;
+    pin.tree_base = P->tree_base; pin.d_stats = P->d_stats; pin.packed = P->packed; pin.packed_n = (size_t)h_cnt->packed_off;
+    pin.levels = (int)h_cnt->levels; pin.d_inbag = P->d_inbag; pin.inbag_words = P->inbag_words;
+    pin.d_vals = P->d_vals; pin.d_card = P->d_card; pin.max_card = P->max_card; pin.rank8 = P->rank8;
+    pin.n_groups = n_groups;
+    rc = package_forests(pin, s, out);
+    if (rc == AIWCRF_OK) AIWCRF_CUDA(cudaStreamSynchronize(s));
+    return rc;
+}
+
+int fit_plan_set_schedule(FitPlan *P, int cps_big, int cps_small)
+{
+    if (cps_big < 1 || cps_big > 3 || cps_small < 1 || cps_small > kSmallCtasPerSm)
+        return fail(AIWCRF_E_INVALID_ARG, "schedule: level_big 1..3, level_small 1..4 CTAs per SM");
+    P->cps_big = cps_big;
+    P->cps_small = cps_small;
+    return plan_capture(*P);
+}
+
+void fit_plan_schedule(const FitPlan *P, int *cps_big, int *cps_small)
+{
+    *cps_big = P->cps_big;
+    *cps_small = P->cps_small;
+}
+
+void fit_plan_free(FitPlan *P)
+{
+    delete P;
 }
 
 }  // namespace aiwcrf

@@ -26,6 +26,7 @@ constexpr uint32_t kErrCard = 2u;           // more than 65,536 distinct values 
 constexpr uint32_t kErrBootOverflow = 4u;   // a bootstrap multiplicity above 255
 constexpr uint32_t kErrTimeout = 8u;        // a bounded mbarrier wait gave up
 constexpr uint32_t kErrY = 16u;             // |y| > 2^40
+constexpr uint32_t kErrCapacity = 32u;      // a fit plan's capacity (groups, ranks, levels) was exceeded
 constexpr uint32_t kErrTree = 32u;          // malformed tree met during a walk
 
 // ------------------------------------------------------------------------------------------
@@ -373,6 +374,16 @@ struct aiwcrf_forest {
 };
 
 namespace aiwcrf {
+// fit plans (fit.cu): the fit captured once as a CUDA graph and replayed
+struct FitPlan;
+int fit_plan_create(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, int64_t N, int32_t F,
+                    const std::vector<int64_t> &sub_off, const int32_t *d_sub_rows, int32_t G, cudaStream_t s,
+                    FitPlan **out);
+int fit_plan_run(FitPlan *P, cudaStream_t s, std::vector<aiwcrf_forest *> &out);
+int fit_plan_set_schedule(FitPlan *P, int cps_big, int cps_small);
+void fit_plan_schedule(const FitPlan *P, int *cps_big, int *cps_small);
+void fit_plan_free(FitPlan *P);
+
 // frees a forest once every stream of the device is idle
 void forest_release(aiwcrf_forest *f);
 // frees a forest in stream order on s; the caller has seen all work reading it complete

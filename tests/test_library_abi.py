@@ -86,6 +86,12 @@ def test_profile_names():
     assert L.aiwcrf_profile_name(n) == b""
 
 
+def test_plan_and_gate_layouts():
+    assert C.sizeof(A.FitSchedule) == 16
+    assert C.sizeof(A.GateParams) == 16
+    assert C.sizeof(A.GateStats) == 32
+
+
 def test_server_layouts_and_validation_without_gpu():
     assert C.sizeof(A.ServerParams) == 40
     assert C.sizeof(A.ServerCounters) == 18 * 8
