@@ -322,6 +322,7 @@ def run_ours(args):
     if not args.no_e2e:
         out["e2e"] = e2e(A, wl, Xq_h, kfeat_h, params, devices, world, dev, max(1, min(K, 3)))
     if rank == 0 and not args.no_extras:
+        out["fit_graph"] = fit_graph_report(A, params, X, y, stats)
         f = A.aiwcrf_fit(params, X, y)
         out["oob"] = oob_report(A, wl, X, f)
         del f
@@ -365,6 +366,36 @@ def e2e(A, wl, Xq_h, kfeat_h, params, devices, world, dev, steps):
             "steps": steps, "note": "host clock around fit + predict + select with pinned host arrays"}
 
 
+def fit_graph_report(A, params, X, y, stats, steps: int = 5):
+    """The benchmark fit as a fit plan: one captured CUDA graph (presort, groups, bootstrap and a
+    device-side loop over the tree levels) replayed, launch schedule from the autotuner; checked
+    byte for byte against aiwcrf_fit."""
+    import torch
+    t0 = time.perf_counter()
+    plan = A.FitPlan(params, X, y)
+    build_s = time.perf_counter() - t0
+    chosen, tried = plan.tune(reps=2)
+    ref = A.aiwcrf_fit(params, X, y).serialize()
+    ms, same = [], True
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=X.device)
+    for k in range(steps + 1):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        f = plan.run()[0]
+        e1.record()
+        torch.cuda.synchronize()
+        if k > 0:
+            ms.append(e0.elapsed_time(e1))
+        same = same and f.serialize() == ref
+        del f
+    plan.close()
+    fit_ms = statistics.median(ms)
+    return {"fit_ms": fit_ms, "rows_trees_per_s": int(X.shape[1]) * params.num_trees / (fit_ms / 1e3),
+            "forest_identical_to_aiwcrf_fit": same, "schedule": chosen, "schedules_tried": tried,
+            "build_s": build_s}
+
+
 def loko_report(A, dev, steps: int = 2):
     """Leave-one-kernel-out cross-validation (Alg. 1 / Table III, here without the simulated-
     annealing re-tuning): 37 forests x 256 trees grown together by one batched fit; per-fold
@@ -395,11 +426,36 @@ def loko_report(A, dev, steps: int = 2):
         truth = wl.y[te] / 2.0 ** 32
         mape.append(float(np.mean(np.abs(10.0 ** pred - 10.0 ** truth) / 10.0 ** truth)))
     rows_trees = int(sum(len(tr) for tr, _ in folds)) * 256
+    # the same 37 fits as one captured graph (device-side level loop), schedule from the autotuner
+    t0 = time.perf_counter()
+    plan = A.FitPlan(params, X, y, offs, rows)
+    build_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    chosen, tried = plan.tune(reps=2)
+    tune_s = time.perf_counter() - t0
+    pms = []
+    same = True
+    ref = [f.serialize() for f in forests]
+    for k in range(steps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pf = plan.run()
+        e1.record()
+        torch.cuda.synchronize()
+        if k > 0:
+            pms.append(e0.elapsed_time(e1))
+        same = same and [f.serialize() for f in pf] == ref
+        del pf
+    plan.close()
     return {"folds": len(folds), "trees_per_fold": 256, "train_rows": [int(min(len(t) for t, _ in folds)),
                                                                       int(max(len(t) for t, _ in folds))],
             "fit_ms": min(ms), "rows_trees_per_s": rows_trees / (min(ms) / 1e3),
+            "graph": {"fit_ms": min(pms), "rows_trees_per_s": rows_trees / (min(pms) / 1e3),
+                      "speedup_vs_batched_fit": min(ms) / min(pms), "forests_identical": same,
+                      "schedule": chosen, "schedules_tried": tried, "build_s": build_s, "tune_s": tune_s},
             "mape_mean": float(np.mean(mape)), "mape_median": float(np.median(mape)),
-            "mape_max": float(np.max(mape)), "batched": "one aiwcrf_fit_subsets call for all folds"}
+            "mape_max": float(np.max(mape)), "batched": "one aiwcrf_fit_subsets call for all folds; "
+            "graph: one aiwcrf_fit_plan_run (captured CUDA graph, autotuned schedule)"}
 
 
 def surrogate_report(A, forest, Xq, n_train=4_000_000, epochs=20, bf16_peak_tflops=None):
