@@ -201,7 +201,9 @@ __global__ void sum_kernel(const float *__restrict__ v, int n, float *__restrict
 // ------------------------------------------------------------------------------------------
 // fused inference
 // ------------------------------------------------------------------------------------------
-constexpr int kInferThreads = 256;
+constexpr int kInferThreads = 512;
+constexpr int kInferColGroups = kInferThreads / 128;          // warps sharing one TMEM lane quarter
+constexpr int kInferCols = 256 / kInferColGroups;              // accumulator columns per warp
 constexpr int kInferSmem = 32768 + 4 * 32768 + 4 * 16384;     // W1, W2 (4 K-chunks), H1 (4 K-chunks)
 
 __global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(
@@ -215,9 +217,9 @@ __global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(
     unsigned char *sH = sm + 32768 + 4 * 32768; // 4 chunks of 128 x 64; chunk 0 holds the input tile first
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tmem_base;
-    __shared__ float part[2][128];
+    __shared__ float part[kInferColGroups][128];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int q4 = warp & 3, half = warp >> 2;
+    const int q4 = warp & 3, half = warp >> 2;          // TMEM lane quarter, column group
 
     // weights, once per CTA, in the operand layout
     for (int p = tid; p < 256 * 8; p += kInferThreads) {
@@ -247,9 +249,11 @@ __global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(
 
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const int64_t q0 = tile * 128;
-        if (tid < 128) {                                    // encode the query tile
-            const int64_t q = q0 + tid;
-            for (int kk = 0; kk < kIn; kk += 8) {
+        {   // encode the query tile: thread (row, part) encodes inputs [part * kIn / G, ...) of one row
+            const int row = tid & 127, kpart = tid >> 7;
+            const int64_t q = q0 + row;
+            constexpr int kPer = kIn / kInferColGroups;
+            for (int kk = kpart * kPer; kk < (kpart + 1) * kPer; kk += 8) {
                 uint32_t w[4];
                 for (int i = 0; i < 4; ++i) {
                     const float v0 = q < Q ? encode_value(e, Xq, Q, q, kk + 2 * i) : 0.0f;
@@ -257,7 +261,7 @@ __global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(
                     w[i] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v0)) |
                            ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v1)) << 16);
                 }
-                *reinterpret_cast<uint4 *>(sH + tc::core_offset(tid, kk)) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4 *>(sH + tc::core_offset(row, kk)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
         tc::fence_smem_to_async();
@@ -277,8 +281,8 @@ __global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(
         tc::fence_after_sync();
         {   // epilogue 1: bias, GELU, BF16 into the layer-2 operand tile
             const int r = 32 * q4 + lane;
-            for (int c = 0; c < 4; ++c) {
-                const int col0 = 128 * half + 32 * c;
+            for (int c = 0; c < kInferCols / 32; ++c) {
+                const int col0 = kInferCols * half + 32 * c;
                 float v[32];
                 tc::tmem_ld32(tbase + ((uint32_t)(32 * q4) << 16) + (uint32_t)col0, v);
                 for (int g8 = 0; g8 < 32; g8 += 8) {
@@ -317,8 +321,8 @@ __global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(
         {   // epilogue 2: bias, GELU, dot with w3
             const int r = 32 * q4 + lane;
             float dot = 0.0f;
-            for (int c = 0; c < 4; ++c) {
-                const int col0 = 128 * half + 32 * c;
+            for (int c = 0; c < kInferCols / 32; ++c) {
+                const int col0 = kInferCols * half + 32 * c;
                 float v[32];
                 tc::tmem_ld32(tbase + ((uint32_t)(32 * q4) << 16) + 256u + (uint32_t)col0, v);
                 for (int i = 0; i < 32; ++i) dot += gelu(v[i] + __ldg(&b2[col0 + i])) * __ldg(&w3[col0 + i]);
@@ -327,7 +331,12 @@ __global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(
         }
         tc::fence_before_sync();
         __syncthreads();
-        if (tid < 128 && q0 + tid < Q) out[q0 + tid] = part[0][tid] + part[1][tid] + __ldg(&b3[0]);
+        if (tid < 128 && q0 + tid < Q) {
+            float o = __ldg(&b3[0]);
+#pragma unroll
+            for (int g = 0; g < kInferColGroups; ++g) o += part[g][tid];
+            out[q0 + tid] = o;
+        }
     }
     if (!ok && tid == 0) atomicOr(err, kErrTimeout);
     tc::fence_before_sync();
