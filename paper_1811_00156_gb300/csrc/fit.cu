@@ -409,6 +409,7 @@ __device__ __forceinline__ void write_leaf(SplitRes *res, int j, int kind, int64
 
 constexpr int kSmallThreads = 256;
 constexpr int kSmallCtasPerSm = 4;     // resident CTAs per SM the small-node kernel is compiled for
+constexpr int kLevelChunk = 32;        // depths enqueued between two host reads of the node count
 
 // the n-th (from 0) set bit of the 128-bit feature mask, or -1
 __device__ __forceinline__ int nth_feature(const uint32_t (&mask)[4], int n)
@@ -1487,7 +1488,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         // largest chunk whose bound fits the budget; a background fit enqueues one level at a
         // time, so that work of other streams sharing a hardware queue with it waits at most
         // one level behind it
-        int chunk = p.ctas_per_sm > 0 ? 1 : 8;
+        int chunk = p.ctas_per_sm > 0 ? 1 : kLevelChunk;
         auto bound = [&](int k) { return std::min<int64_t>(C_known << k, C_max); };
         while (chunk > 1 && (size_t)bound(chunk) * per_node_bytes > budget) chunk >>= 1;
         if ((rc = grow_tables((size_t)bound(chunk), (uint32_t)C_known)) != AIWCRF_OK) return rc;
