@@ -437,8 +437,8 @@ typedef struct aiwcrf_fit_plan aiwcrf_fit_plan;
 
 /* A launch schedule of the level loop: resident CTAs per SM of the grid-stride level kernels. */
 typedef struct {
-    int32_t level_big_ctas_per_sm;     /* 1..3 */
-    int32_t level_small_ctas_per_sm;   /* 1..4 */
+    int32_t level_big_ctas_per_sm;     /* 1..the CTAs per SM the big-node kernel is built for */
+    int32_t level_small_ctas_per_sm;   /* 1..the same for the small-node kernel */
     float ms;                          /* median wall time of a run with this schedule (tuning) */
     int32_t reserved;
 } aiwcrf_fit_schedule;

@@ -531,11 +531,11 @@ class FitPlan:
 
     def tune(self, reps: int = 3, stream=None):
         """(chosen schedule dict, list of every schedule tried)."""
-        tried = (FitSchedule * 16)()
+        tried = (FitSchedule * 64)()
         n = C.c_int32()
         chosen = FitSchedule()
-        _check(load().aiwcrf_fit_plan_tune(self.handle, reps, _stream(stream), tried, 16, C.byref(n), C.byref(chosen)))
-        return chosen.as_dict(), [tried[i].as_dict() for i in range(min(n.value, 16))]
+        _check(load().aiwcrf_fit_plan_tune(self.handle, reps, _stream(stream), tried, 64, C.byref(n), C.byref(chosen)))
+        return chosen.as_dict(), [tried[i].as_dict() for i in range(min(n.value, 64))]
 
     def set_schedule(self, level_big: int, level_small: int):
         _check(load().aiwcrf_fit_plan_set_schedule(self.handle, C.byref(FitSchedule(level_big, level_small, 0.0, 0))))

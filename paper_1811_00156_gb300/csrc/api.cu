@@ -445,8 +445,10 @@ int aiwcrf_fit_plan_tune(aiwcrf_fit_plan *plan, int32_t reps, void *cuda_stream,
         return fail(AIWCRF_E_INVALID_ARG, "plan, reps >= 1 and a tried array of cap entries are needed");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     std::vector<aiwcrf_fit_schedule> all;
-    for (int big = 1; big <= 3; ++big)
-        for (int small = 1; small <= 4; ++small) {
+    int max_big = 3, max_small = 4;
+    aiwcrf::fit_plan_limits(&max_big, &max_small);
+    for (int big = 1; big <= max_big; ++big)
+        for (int small = 1; small <= max_small; ++small) {
             int rc = aiwcrf::fit_plan_set_schedule(plan->impl, big, small);
             if (rc) return rc;
             std::vector<double> ts;

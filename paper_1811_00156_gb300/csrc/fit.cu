@@ -540,10 +540,19 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallCtasPerSm) level_small_ke
 }
 
 
-constexpr int kBigThreads = 256;
+constexpr int kBigThreads = 128;
 constexpr int kBigWarps = kBigThreads / 32;
+constexpr int kBigCtasPerSm = 6;       // resident CTAs per SM the big-node kernel is compiled for
 constexpr int kRowsPerIter = 4;   // rows per thread per pass: independent gathers in flight
 constexpr int kFeatChunk = 8;     // tried features whose ranks are loaded before their atomics
+
+// bins the big-node kernel needs so that every tried feature's values fit in one pass (at most
+// 4,096; more is handled in groups of that size)
+inline int big_bin_cap(int mtry, int F, uint32_t max_card)
+{
+    const int64_t need = (int64_t)std::min(mtry, F) * (int64_t)std::max<uint32_t>(max_card, 1u);
+    return (int)std::min<int64_t>(4096, (need + 31) & ~(int64_t)31);
+}
 
 // One CTA per node with more than 32 entries. Shared bins, bin_cap of them, hold per rank
 // of every tried feature: sum w (u32) and sum w*y as an exact (low u32, high i32) pair. All
@@ -679,13 +688,16 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
         tot_w[tid] = lw;
         tot_s[tid] = ls;
         __syncthreads();
-        if (warp == 0) {            // exclusive scan of the 256 thread totals by one warp
-            uint32_t w8[8];
-            long long s8[8];
+        if (warp == 0) {            // exclusive scan of the thread totals by one warp
+            constexpr int kPer = kBigThreads / 32;
+            uint32_t w8[kPer];
+            long long s8[kPer];
             uint32_t ws = 0;
             long long ss = 0;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) { w8[k] = ws; s8[k] = ss; ws += tot_w[lane * 8 + k]; ss += tot_s[lane * 8 + k]; }
+            for (int k = 0; k < kPer; ++k) {
+                w8[k] = ws; s8[k] = ss; ws += tot_w[lane * kPer + k]; ss += tot_s[lane * kPer + k];
+            }
             uint32_t xw = ws;
             long long xs = ss;
 #pragma unroll
@@ -697,7 +709,7 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
             xw -= ws;
             xs -= ss;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) { tot_w[lane * 8 + k] = xw + w8[k]; tot_s[lane * 8 + k] = xs + s8[k]; }
+            for (int k = 0; k < kPer; ++k) { tot_w[lane * kPer + k] = xw + w8[k]; tot_s[lane * kPer + k] = xs + s8[k]; }
         }
         __syncthreads();
         {
@@ -799,7 +811,7 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
 
 // one CTA per node with more than 32 entries, strided over the depth's CTA list
 template <typename RT>
-__global__ void __launch_bounds__(kBigThreads, 3) level_big_kernel(LevelArgs a, int bin_cap)
+__global__ void __launch_bounds__(kBigThreads, kBigCtasPerSm) level_big_kernel(LevelArgs a, int bin_cap)
 {
     const uint32_t list_n = *a.list_n;
     for (uint32_t k = blockIdx.x; k < list_n; k += gridDim.x) {
@@ -1469,7 +1481,8 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     if (!h_cnt) return fail(AIWCRF_E_OOM, "pinned host buffer");
     uint32_t *h_err = reinterpret_cast<uint32_t *>(h_cnt + 1);
 
-    const int bin_cap = 4096;
+    // bins: the tried features' value counts side by side (one pass over the entries)
+    const int bin_cap = big_bin_cap(p.mtry, F, max_card);
     const int big_smem = bin_cap * 12;
     AIWCRF_CUDA(cudaFuncSetAttribute(level_big_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem));
     AIWCRF_CUDA(cudaFuncSetAttribute(level_big_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem));
@@ -1502,7 +1515,8 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
             la.nodes = nodes_cur; la.rows_in = rin; la.rows_out = rout; la.depth = depth; la.res = res;
             {
                 la.list = big_a; la.list_n = &d_cnt->n_big;
-                const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(Cb, cps * dev_sms));
+                const int64_t cps_big = p.ctas_per_sm > 0 ? p.ctas_per_sm : kBigCtasPerSm;
+                const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(Cb, cps_big * dev_sms));
                 prof_begin(s, kProfLevelBig);
                 if (rank8) level_big_kernel<uint8_t><<<grid, kBigThreads, big_smem, s>>>(la, bin_cap);
                 else level_big_kernel<uint16_t><<<grid, kBigThreads, big_smem, s>>>(la, bin_cap);
@@ -1634,7 +1648,7 @@ struct FitPlan {
     uint32_t *d_inbag = nullptr, *gcnt = nullptr;
     uint32_t *toff_a = nullptr, *toff_b = nullptr, *tree_base = nullptr;
     // schedule and graph
-    int cps_big = 3, cps_small = kSmallCtasPerSm;
+    int cps_big = kBigCtasPerSm, cps_small = kSmallCtasPerSm;
     cudaGraphExec_t exec = nullptr;
     int64_t prefix_launches = 0;
 
@@ -1752,11 +1766,11 @@ int plan_level(FitPlan &P, cudaStream_t s, NodeRec *nodes_in, NodeRec *nodes_out
     la.max_depth = P.p.max_depth; la.seed_lo = (uint32_t)P.p.seed; la.seed_hi = (uint32_t)(P.p.seed >> 32);
     la.depth = 0; la.depth_ptr = &P.d_cnt->levels;
     la.nodes = nodes_in; la.rows_in = rin; la.rows_out = rout; la.res = P.res;
-    const int big_smem = 4096 * 12;
+    const int bin_cap = big_bin_cap(P.p.mtry, P.F, P.max_card), big_smem = bin_cap * 12;
     la.list = P.big_l; la.list_n = &P.d_cnt->n_big;
     const unsigned gbig = (unsigned)(P.cps_big * P.sms), gsmall = (unsigned)(P.cps_small * P.sms);
-    if (P.rank8) level_big_kernel<uint8_t><<<gbig, kBigThreads, big_smem, s>>>(la, 4096);
-    else level_big_kernel<uint16_t><<<gbig, kBigThreads, big_smem, s>>>(la, 4096);
+    if (P.rank8) level_big_kernel<uint8_t><<<gbig, kBigThreads, big_smem, s>>>(la, bin_cap);
+    else level_big_kernel<uint16_t><<<gbig, kBigThreads, big_smem, s>>>(la, bin_cap);
     AIWCRF_LAUNCH_CHECK("level_big_kernel");
     la.list = P.small_l; la.list_n = &P.d_cnt->n_small;
     if (P.rank8) level_small_kernel<uint8_t><<<gsmall, kSmallThreads, 0, s>>>(la);
@@ -1913,8 +1927,9 @@ int fit_plan_create(const aiwcrf_fit_params &p, const float *dX, const int64_t *
     AIWCRF_CUDA(cudaMemcpyAsync(Q.d_rng, h_rng.data(), sizeof(uint32_t) * (size_t)Q.T, cudaMemcpyHostToDevice, s));
     AIWCRF_CUDA(cudaStreamSynchronize(s));
     AIWCRF_CUDA(cudaFuncSetAttribute(bootstrap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, std::max(Q.boot_smem, 1)));
-    AIWCRF_CUDA(cudaFuncSetAttribute(level_big_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4096 * 12));
-    AIWCRF_CUDA(cudaFuncSetAttribute(level_big_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4096 * 12));
+    const int big_smem = big_bin_cap(p.mtry, F, Q.max_card) * 12;
+    AIWCRF_CUDA(cudaFuncSetAttribute(level_big_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem));
+    AIWCRF_CUDA(cudaFuncSetAttribute(level_big_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem));
     if ((rc = plan_capture(Q))) return rc;
     *out = P.release();
     return AIWCRF_OK;
@@ -1948,8 +1963,8 @@ int fit_plan_run(FitPlan *P, cudaStream_t s, std::vector<aiwcrf_forest *> &out)
 
 int fit_plan_set_schedule(FitPlan *P, int cps_big, int cps_small)
 {
-    if (cps_big < 1 || cps_big > 3 || cps_small < 1 || cps_small > kSmallCtasPerSm)
-        return fail(AIWCRF_E_INVALID_ARG, "schedule: level_big 1..3, level_small 1..4 CTAs per SM");
+    if (cps_big < 1 || cps_big > kBigCtasPerSm || cps_small < 1 || cps_small > kSmallCtasPerSm)
+        return fail(AIWCRF_E_INVALID_ARG, "schedule: CTAs per SM out of the range the level kernels are built for");
     P->cps_big = cps_big;
     P->cps_small = cps_small;
     return plan_capture(*P);
@@ -1959,6 +1974,12 @@ void fit_plan_schedule(const FitPlan *P, int *cps_big, int *cps_small)
 {
     *cps_big = P->cps_big;
     *cps_small = P->cps_small;
+}
+
+void fit_plan_limits(int *cps_big, int *cps_small)
+{
+    *cps_big = kBigCtasPerSm;
+    *cps_small = kSmallCtasPerSm;
 }
 
 void fit_plan_free(FitPlan *P)

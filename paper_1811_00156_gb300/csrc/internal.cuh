@@ -383,6 +383,8 @@ int fit_plan_run(FitPlan *P, cudaStream_t s, std::vector<aiwcrf_forest *> &out);
 int fit_plan_set_schedule(FitPlan *P, int cps_big, int cps_small);
 void fit_plan_schedule(const FitPlan *P, int *cps_big, int *cps_small);
 void fit_plan_free(FitPlan *P);
+// the largest CTAs per SM each level kernel is built for
+void fit_plan_limits(int *cps_big, int *cps_small);
 
 // frees a forest once every stream of the device is idle
 void forest_release(aiwcrf_forest *f);

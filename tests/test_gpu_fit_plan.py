@@ -68,7 +68,7 @@ def test_plan_subsets_equal_fit_subsets():
     plan = A.FitPlan(params, X, y, offs, rows)
     assert blobs(plan.run()) == ref
     chosen, tried = plan.tune(reps=1)
-    assert len(tried) == 12 and chosen["ms"] == min(t["ms"] for t in tried)
+    assert len(tried) >= 12 and chosen["ms"] == min(t["ms"] for t in tried)
     assert (chosen["level_big_ctas_per_sm"], chosen["level_small_ctas_per_sm"]) in \
         {(t["level_big_ctas_per_sm"], t["level_small_ctas_per_sm"]) for t in tried}
     assert blobs(plan.run()) == ref
