@@ -369,6 +369,9 @@ struct aiwcrf_forest {
     int64_t *d_tree_off4 = nullptr;       // T + 1 offsets into d_c32
     int64_t num_c32 = 0;
     int64_t max_tree4 = 0;
+    // features whose codes order large query batches before a compact walk (most used in the
+    // trees' top levels first; -1: none), so that a warp's queries take similar paths
+    int32_t key_feats[4] = {-1, -1, -1, -1};
     std::vector<int64_t> tree_off;        // host copy
     aiwcrf_fit_stats stats = {};
 };

@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <string>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -302,11 +303,12 @@ __device__ __forceinline__ void walk_tree4(NodePtr tn, const uint8_t *const (&xr
 
 // The byte-code walk over compact trees. Leaf values are loaded from the 8-byte node array
 // (L2-resident) and added one tree later, so their latency overlaps the next walk.
-template <int QPT, bool VAR>
+template <int QPT, bool VAR, bool PERM>
 __global__ void __launch_bounds__(kPredThreads) predict4_kernel(
     const uint32_t *__restrict__ c32, const int64_t *__restrict__ tree_off4, const uint64_t *__restrict__ nodes,
     const int64_t *__restrict__ tree_off, int T, const uint8_t *__restrict__ codes, int64_t Q, int ld_words,
-    int64_t total_trees, int tree_cap, int64_t *out_sum, int64_t *out_pred, uint64_t *out_var, uint32_t *err)
+    int64_t total_trees, int tree_cap, int64_t *out_sum, int64_t *out_pred, uint64_t *out_var, uint32_t *err,
+    const uint32_t *__restrict__ perm)
 {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     __shared__ __align__(8) uint64_t bar[2];
@@ -323,11 +325,19 @@ __global__ void __launch_bounds__(kPredThreads) predict4_kernel(
         fence_mbar_init();
     }
     {
+        // the tile's query codes; with PERM, tile position i holds query perm[q0 + i]
         const uint32_t *gw = reinterpret_cast<const uint32_t *>(codes);
         const int64_t nq = min((int64_t)QT, Q - q0);
         const int64_t words = nq * ld_words;
-        const uint32_t *src = gw + (size_t)q0 * (size_t)ld_words;
-        for (int64_t k = tid; k < words; k += kPredThreads) xw[k] = src[k];
+        if (PERM) {
+            for (int64_t k = tid; k < words; k += kPredThreads) {
+                const int64_t r = k / ld_words, w = k - r * ld_words;
+                xw[k] = gw[(size_t)perm[q0 + r] * (size_t)ld_words + (size_t)w];
+            }
+        } else {
+            const uint32_t *src = gw + (size_t)q0 * (size_t)ld_words;
+            for (int64_t k = tid; k < words; k += kPredThreads) xw[k] = src[k];
+        }
     }
     __syncthreads();
     if (tid == 0) {
@@ -383,8 +393,9 @@ __global__ void __launch_bounds__(kPredThreads) predict4_kernel(
 
 #pragma unroll
     for (int i = 0; i < QPT; ++i) {
-        const int64_t q = q0 + tid + i * kPredThreads;
-        if (q >= Q) continue;
+        const int64_t qs = q0 + tid + i * kPredThreads;
+        if (qs >= Q) continue;
+        const int64_t q = PERM ? (int64_t)perm[qs] : qs;
         if (out_sum) out_sum[q] = acc[i];
         if (out_pred) {
             const i128_t num = (i128_t)2 * acc[i] + total_trees, den = (i128_t)2 * total_trees;
@@ -398,6 +409,36 @@ __global__ void __launch_bounds__(kPredThreads) predict4_kernel(
             out_var[2 * q + 1] = (uint64_t)(V >> 64);
         }
     }
+}
+
+// Split features of every tree's first kTopNodes nodes (breadth-first: the top levels).
+constexpr int kTopNodes = 7;
+__global__ void top_features_kernel(const uint64_t *__restrict__ cnodes, const int64_t *__restrict__ tree_off, int T,
+                                    uint32_t *counts)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const int64_t a = tree_off[t], m = min((int64_t)kTopNodes, tree_off[t + 1] - a);
+    for (int64_t j = 0; j < m; ++j) {
+        const uint64_t nd = cnodes[a + j];
+        if (!(nd >> 63)) atomicAdd(&counts[(nd >> 56) & 0x7Fu], 1u);
+    }
+}
+
+// 32-bit sort key of a coded query: the one-byte codes of four features, most significant first
+__global__ void query_key_kernel(const uint8_t *__restrict__ codes, int ld_bytes, int64_t Q, int4 kf,
+                                 uint32_t *__restrict__ keys, uint32_t *__restrict__ idx)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= Q) return;
+    const uint8_t *c = codes + (size_t)q * (size_t)ld_bytes;
+    uint32_t k = 0;
+    k |= kf.x >= 0 ? (uint32_t)c[kf.x] << 24 : 0u;
+    k |= kf.y >= 0 ? (uint32_t)c[kf.y] << 16 : 0u;
+    k |= kf.z >= 0 ? (uint32_t)c[kf.z] << 8 : 0u;
+    k |= kf.w >= 0 ? (uint32_t)c[kf.w] : 0u;
+    keys[q] = k;
+    idx[q] = (uint32_t)q;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -472,6 +513,8 @@ __global__ void argmin_kernel(const int64_t *pred, const int32_t *dev, int32_t K
 namespace {
 
 constexpr int kQPT = 4;
+// compact-forest batches of at least this many queries are walked in sorted order
+constexpr int64_t kSortMinQueries = 1 << 16;
 
 template <typename CT, bool VAR>
 int launch_predict(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum, int64_t *d_pred,
@@ -536,13 +579,31 @@ int launch_predict4(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t
     tree_cap &= ~3;
     if (tree_cap < 4) tree_cap = 4;
     const int smem = 2 * tree_cap * 4 + xs_bytes;
-    auto kern = predict4_kernel<kQPT, VAR>;
+    // large batches walk in the order of their leading codes (own scratch only)
+    const bool sorted = !codes_scratch && Q >= kSortMinQueries && Q < ((int64_t)1 << 32) && f->key_feats[0] >= 0;
+    uint32_t *perm = nullptr;
+    struct FreeSort { uint32_t *p; cudaStream_t s; ~FreeSort() { if (p) cudaFreeAsync(p, s); } } fs{nullptr, s};
+    if (sorted) {
+        const size_t nq = (size_t)Q + 1, hw = radix_sort_hist_words(Q, 1);
+        uint32_t *buf = nullptr;
+        if (cudaMallocAsync(&buf, sizeof(uint32_t) * (4 * nq + hw), s) != cudaSuccess)
+            return fail(AIWCRF_E_OOM, "device allocation of the query order failed");
+        fs.p = buf;
+        uint32_t *kA = buf, *vA = buf + nq, *kB = buf + 2 * nq, *vB = buf + 3 * nq, *hist = buf + 4 * nq;
+        const int4 kf = make_int4(f->key_feats[0], f->key_feats[1], f->key_feats[2], f->key_feats[3]);
+        query_key_kernel<<<(unsigned)((Q + 255) / 256), 256, 0, s>>>(d_codes, ld_words * 4, Q, kf, kA, vA);
+        count_launches(1);
+        int rc = radix_sort_segments(kA, vA, kB, vB, Q, 1, Q, hist, s);
+        if (rc != AIWCRF_OK) return rc;
+        perm = vA;
+    }
+    auto kern = sorted ? predict4_kernel<kQPT, VAR, true> : predict4_kernel<kQPT, VAR, false>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(predict4_kernel)");
     const int64_t grid = (Q + (int64_t)kPredThreads * kQPT - 1) / ((int64_t)kPredThreads * kQPT);
     kern<<<(unsigned)grid, kPredThreads, smem, s>>>(f->d_c32, f->d_tree_off4, f->d_nodes, f->d_tree_off, (int)walk_T,
                                                     d_codes, Q, ld_words, total_trees, tree_cap, d_sum, d_pred, d_var,
-                                                    d_err);
+                                                    d_err, perm);
     count_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "predict4_kernel launch");
@@ -664,8 +725,27 @@ int forest_build_compact(aiwcrf_forest *f, cudaStream_t s)
     if (!f->compact) return AIWCRF_OK;
     compact_nodes_kernel<<<(unsigned)f->T, 256, 0, s>>>(f->d_cnodes, f->d_tree_off, f->d_tree_off4, f->d_c32);
     count_launches(1);
-    const cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "compact_nodes_kernel launch");
+    // the features the trees split on first, for the order of large query batches
+    uint32_t *d_cnt = nullptr;
+    if (cudaMallocAsync(&d_cnt, 4 * (size_t)f->F, s) != cudaSuccess) return fail(AIWCRF_E_OOM, "feature counts");
+    e = cudaMemsetAsync(d_cnt, 0, 4 * (size_t)f->F, s);
+    if (e == cudaSuccess) {
+        top_features_kernel<<<(unsigned)((f->T + 127) / 128), 128, 0, s>>>(f->d_cnodes, f->d_tree_off, (int)f->T, d_cnt);
+        count_launches(1);
+        e = cudaGetLastError();
+    }
+    std::vector<uint32_t> h((size_t)f->F, 0u);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d_cnt, 4 * (size_t)f->F, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(d_cnt, s);
+    if (e != cudaSuccess) return cuda_fail(e, "top split features");
+    std::vector<int> order((size_t)f->F);
+    for (int i = 0; i < f->F; ++i) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return h[(size_t)x] > h[(size_t)y]; });
+    for (int k = 0; k < 4; ++k)
+        f->key_feats[k] = (k < f->F && h[(size_t)order[(size_t)k]] > 0) ? order[(size_t)k] : -1;
     return AIWCRF_OK;
 }
 

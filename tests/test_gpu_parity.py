@@ -317,3 +317,16 @@ def test_oob_matches_oracle():
                               dev(np.arange(100, dtype=np.int32)))
     with pytest.raises(A.AiwcrfError):
         A.aiwcrf_oob(fs[0], dev(wl.X), s, c)
+
+
+def test_sorted_walk_of_large_batches_equals_unsorted_chunks():
+    # batches of >= 65,536 queries on a compact forest are walked in the order of their leading
+    # codes; the sums, predictions and variance numerators must not change
+    wl = synth.scaled_forest_workload(replicates=2)
+    f = gpu_fit(wl, 40, 10, 5)
+    Xq = synth.queries(150_001, seed=77)
+    Xq[:, 5] = np.nan
+    big = gpu_predict(f, Xq, var=True)
+    chunks = [gpu_predict(f, np.ascontiguousarray(Xq[:, a:a + 40_000]), var=True) for a in range(0, 150_001, 40_000)]
+    np.testing.assert_array_equal(big[0], np.concatenate([c[0] for c in chunks]))
+    np.testing.assert_array_equal(big[1], np.concatenate([c[1] for c in chunks]))
