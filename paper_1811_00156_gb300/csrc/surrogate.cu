@@ -201,6 +201,13 @@ __global__ void sum_kernel(const float *__restrict__ v, int n, float *__restrict
 // ------------------------------------------------------------------------------------------
 // fused inference
 // ------------------------------------------------------------------------------------------
+// two floats as BF16 (round to nearest even) in one word, the first in the low half
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
 constexpr int kInferThreads = 512;
 constexpr int kInferColGroups = kInferThreads / 128;          // warps sharing one TMEM lane quarter
 constexpr int kInferCols = 256 / kInferColGroups;              // accumulator columns per warp
@@ -258,8 +265,7 @@ __global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(
                 for (int i = 0; i < 4; ++i) {
                     const float v0 = q < Q ? encode_value(e, Xq, Q, q, kk + 2 * i) : 0.0f;
                     const float v1 = q < Q ? encode_value(e, Xq, Q, q, kk + 2 * i + 1) : 0.0f;
-                    w[i] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v0)) |
-                           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v1)) << 16);
+                    w[i] = pack_bf16x2(v0, v1);
                 }
                 *reinterpret_cast<uint4 *>(sH + tc::core_offset(row, kk)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
@@ -291,8 +297,7 @@ __global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(
                         const int j0 = col0 + g8 + 2 * i;
                         const float h0 = gelu(v[g8 + 2 * i] + __ldg(&b1[j0]));
                         const float h1 = gelu(v[g8 + 2 * i + 1] + __ldg(&b1[j0 + 1]));
-                        w[i] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(h0)) |
-                               ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(h1)) << 16);
+                        w[i] = pack_bf16x2(h0, h1);
                     }
                     const int k = col0 + g8;
                     *reinterpret_cast<uint4 *>(sH + (k >> 6) * 16384 + tc::core_offset(r, k & 63)) =
