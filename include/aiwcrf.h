@@ -490,6 +490,9 @@ const char *aiwcrf_last_error(void);
  * returns, per kernel class k < n (names via aiwcrf_profile_name), the launch count and the
  * summed duration in milliseconds; it then clears the record. */
 int aiwcrf_profile_enable(int32_t on);
+/* Restrict the timing to the kernel classes whose bit k is set in mask (all by default): each
+ * recorded pair of events costs the stream a little time. */
+int aiwcrf_profile_classes(uint32_t mask);
 int aiwcrf_profile_read(int32_t n, int64_t *launches, double *total_ms);
 const char *aiwcrf_profile_name(int32_t k);
 int32_t aiwcrf_profile_num_classes(void);

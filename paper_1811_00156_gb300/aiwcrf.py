@@ -123,7 +123,7 @@ EXPORTS = ["aiwcrf_fit", "aiwcrf_fit_subsets", "aiwcrf_predict", "aiwcrf_predict
            "aiwcrf_server_refit", "aiwcrf_server_pause", "aiwcrf_server_stats", "aiwcrf_server_run_load",
            "aiwcrf_server_trace", "aiwcrf_server_destroy", "aiwcrf_select_device_gated",
            "aiwcrf_fit_plan_create", "aiwcrf_fit_plan_run", "aiwcrf_fit_plan_tune", "aiwcrf_fit_plan_set_schedule",
-           "aiwcrf_fit_plan_free"]
+           "aiwcrf_fit_plan_free", "aiwcrf_profile_classes"]
 
 _lib = None
 _lock = threading.Lock()
@@ -167,6 +167,7 @@ def load():
         L.aiwcrf_forest_free.argtypes = [_vp]
         L.aiwcrf_last_error.restype = C.c_char_p
         L.aiwcrf_profile_enable.argtypes = [C.c_int32]
+        L.aiwcrf_profile_classes.argtypes = [C.c_uint32]
         L.aiwcrf_profile_read.argtypes = [C.c_int32, _vp, _vp]
         L.aiwcrf_profile_name.argtypes = [C.c_int32]
         L.aiwcrf_profile_name.restype = C.c_char_p
@@ -574,6 +575,19 @@ def aiwcrf_forest_deserialize(blob: bytes) -> Forest:
 
 def aiwcrf_profile_enable(on: bool):
     _check(load().aiwcrf_profile_enable(1 if on else 0))
+
+
+def aiwcrf_profile_classes(names=None):
+    """Time only the named kernel classes (None: all)."""
+    L = load()
+    if names is None:
+        mask = 0xFFFFFFFF
+    else:
+        idx = {L.aiwcrf_profile_name(k).decode(): k for k in range(int(L.aiwcrf_profile_num_classes()))}
+        mask = 0
+        for n in names:
+            mask |= 1 << idx[n]
+    _check(L.aiwcrf_profile_classes(mask))
 
 
 def aiwcrf_profile_read() -> dict:

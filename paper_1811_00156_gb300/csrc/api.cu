@@ -131,6 +131,7 @@ struct ProfRec {
 };
 std::mutex g_prof_mu;
 bool g_prof_on = false;
+uint32_t g_prof_mask = ~0u;       // kernel classes that record events while profiling is on
 std::vector<ProfRec> g_prof;
 std::vector<cudaEvent_t> g_event_pool;
 thread_local std::vector<std::pair<int, cudaEvent_t>> t_open;
@@ -154,7 +155,7 @@ const char *kProfNames[kProfNum] = {"rank",    "bootstrap", "level_big", "level_
 void prof_begin(cudaStream_t s, int cls)
 {
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    if (!g_prof_on) return;
+    if (!g_prof_on || !((g_prof_mask >> cls) & 1u)) return;
     cudaEvent_t e = take_event();
     cudaEventRecord(e, s);
     t_open.push_back({cls, e});
@@ -163,7 +164,7 @@ void prof_begin(cudaStream_t s, int cls)
 void prof_end(cudaStream_t s, int cls)
 {
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    if (!g_prof_on) return;
+    if (!g_prof_on || !((g_prof_mask >> cls) & 1u)) return;
     for (size_t i = t_open.size(); i-- > 0;) {
         if (t_open[i].first == cls) {
             cudaEvent_t b = take_event();
@@ -764,6 +765,13 @@ int aiwcrf_profile_enable(int32_t on)
 {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     g_prof_on = on != 0;
+    return AIWCRF_OK;
+}
+
+int aiwcrf_profile_classes(uint32_t mask)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_mask = mask;
     return AIWCRF_OK;
 }
 
