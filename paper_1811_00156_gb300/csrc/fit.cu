@@ -18,8 +18,8 @@
 //                        bitonic sort per feature instead of a histogram
 //     scan_*             exclusive scan of the split flags over the depth's nodes
 //     finalize_kernel    encodes each node, numbers the children breadth first, writes the
-//                        next depth's node table and its warp/CTA work lists
-//     tree_update_kernel per-tree node counts and next-depth offsets
+//                        next depth's node table and its warp/CTA work lists; its last CTA
+//                        advances the per-tree node counts, next-depth offsets and level counts
 //   pack_kernel        scatters every finished node to its forest / tree / BFS position
 #include <cuda_runtime.h>
 
@@ -862,13 +862,21 @@ __global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(uint32_t *blo
     if (threadIdx.x == 0) block_sums[nblocks] = carry;
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_write_kernel(const SplitRes *res, const LevelCounts *cnt,
+// Writes the exclusive scan of the split flags (tile totals from scan_reduce_kernel). Every CTA
+// adds up the totals of the tiles before its own (a few hundred at most per depth), CTA 0 also
+// writes the grand total at [n] and clears the list counts for the next depth (the level
+// kernels that read them have finished; finalize_kernel refills them).
+__global__ void __launch_bounds__(kScanThreads) scan_write_kernel(const SplitRes *res, LevelCounts *cnt,
                                                                   const uint32_t *block_sums, uint32_t *excl)
 {
     __shared__ uint32_t warp_tmp[32];
     const int n = (int)cnt->C;
     const int ntiles = (n + kScanTile - 1) / kScanTile;
     for (int b = blockIdx.x; b < ntiles; b += gridDim.x) {
+        uint32_t part = 0;
+        for (int i = threadIdx.x; i < b; i += kScanThreads) part += block_sums[i];
+        uint32_t prefix;
+        block_incl_scan(part, warp_tmp, prefix);
         const int base = b * kScanTile + threadIdx.x * kScanPer;
         uint32_t fl[kScanPer], c = 0;
 #pragma unroll
@@ -878,14 +886,24 @@ __global__ void __launch_bounds__(kScanThreads) scan_write_kernel(const SplitRes
         }
         uint32_t tot;
         const uint32_t incl = block_incl_scan(c, warp_tmp, tot);
-        uint32_t run = block_sums[b] + incl - c;
+        uint32_t run = prefix + incl - c;
 #pragma unroll
         for (int k = 0; k < kScanPer; ++k) {
             if (base + k < n) excl[base + k] = run;
             run += fl[k];
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) excl[n] = block_sums[ntiles];
+    if (blockIdx.x == 0) {
+        uint32_t part = 0;
+        for (int i = threadIdx.x; i < ntiles; i += kScanThreads) part += block_sums[i];
+        uint32_t total;
+        block_incl_scan(part, warp_tmp, total);
+        if (threadIdx.x == 0) {
+            excl[n] = total;
+            cnt->n_small = 0u;
+            cnt->n_big = 0u;
+        }
+    }
 }
 
 // the same three passes over a u32 flag array
@@ -932,12 +950,15 @@ struct FinalArgs {
     const SplitRes *res;
     const uint32_t *excl;          // n + 1
     const uint32_t *tree_off;      // T + 1: first node of each tree at this depth
-    const uint32_t *tree_base;     // T: nodes of each tree at lower depths
+    uint32_t *tree_base;           // T: nodes of each tree at lower depths
     LevelCounts *cnt;              // C and packed_off of this depth; n_small / n_big of the next
     NodeRec *next;
     int32_t *small_list, *big_list;
     PackedRec *packed;             // all finished nodes; this depth starts at cnt->packed_off
     GrowStats *stats;
+    uint32_t *next_tree_off;       // T + 1: first node of each tree at the next depth
+    int T;
+    uint32_t *done;                // CTAs finished (zero on entry, left zero)
 };
 
 __device__ __forceinline__ void push_list(int32_t *list, uint32_t *counter, bool want, int32_t value)
@@ -1017,26 +1038,31 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinalArgs a)
         for (int w = 0; w < 8; ++w) sum += red[threadIdx.x][w];
         if (sum) atomicAdd(&a.stats->entries_evaluated + threadIdx.x, sum);   // GrowStats field order
     }
+    // the last CTA to finish advances the per-tree bookkeeping and the level counts
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(a.done, 1u) == gridDim.x - 1u;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int t = threadIdx.x; t <= a.T; t += blockDim.x) {
+        if (t < a.T) a.tree_base[t] += a.tree_off[t + 1] - a.tree_off[t];
+        a.next_tree_off[t] = 2u * a.excl[a.tree_off[t]];
+    }
+    if (threadIdx.x == 0) {
+        const uint32_t c = a.cnt->C;
+        a.cnt->packed_off += c;
+        a.cnt->levels += c > 0 ? 1u : 0u;
+        a.cnt->C = 2u * a.excl[c];
+        *a.done = 0u;
+    }
 }
 
 // per tree: nodes below the next depth and where the tree's nodes start in the next depth's
 // table; thread 0 then advances the depth counters (after every reader of them has finished)
-__global__ void tree_update_kernel(const uint32_t *tree_off, uint32_t *tree_base, const uint32_t *excl,
-                                   uint32_t *next_tree_off, int T, LevelCounts *cnt)
-{
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t <= T) {
-        if (t < T) tree_base[t] += tree_off[t + 1] - tree_off[t];
-        next_tree_off[t] = 2u * excl[tree_off[t]];
-    }
-    if (t == 0) {
-        const uint32_t c = cnt->C;
-        cnt->packed_off += c;
-        cnt->levels += c > 0 ? 1u : 0u;
-        cnt->C = 2u * excl[c];
-    }
-}
-
 __global__ void iota_kernel(uint32_t *v, int n)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1473,9 +1499,11 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     uint32_t *tree_off = sc.get<uint32_t>((size_t)T + 1, &rc); if (rc) return rc;
     uint32_t *tree_off_nxt = sc.get<uint32_t>((size_t)T + 1, &rc); if (rc) return rc;
     uint32_t *tree_base = sc.get<uint32_t>((size_t)T, &rc); if (rc) return rc;
+    uint32_t *d_done = sc.get<uint32_t>(1, &rc); if (rc) return rc;
     iota_kernel<<<(unsigned)((T + 256) / 256), 256, 0, s>>>(tree_off, (int)T);
     AIWCRF_LAUNCH_CHECK("iota_kernel");
     AIWCRF_CUDA(cudaMemsetAsync(tree_base, 0, sizeof(uint32_t) * (size_t)T, s));
+    AIWCRF_CUDA(cudaMemsetAsync(d_done, 0, sizeof(uint32_t), s));
 
     LevelCounts *h_cnt = static_cast<LevelCounts *>(pinned_scratch());
     if (!h_cnt) return fail(AIWCRF_E_OOM, "pinned host buffer");
@@ -1537,24 +1565,20 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
             const unsigned sgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + kScanTile - 1) / kScanTile, std::min<int64_t>(2, cps) * dev_sms));
             prof_begin(s, kProfScan);
             scan_reduce_kernel<<<sgrid, kScanThreads, 0, s>>>(res, d_cnt, block_sums);
-            scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(block_sums, 0, d_cnt);
             scan_write_kernel<<<sgrid, kScanThreads, 0, s>>>(res, d_cnt, block_sums, excl);
-            count_launches(2);
+            count_launches(1);
             AIWCRF_LAUNCH_CHECK("scan kernels");
             prof_end(s, kProfScan);
 
-            AIWCRF_CUDA(cudaMemsetAsync(d_cnt, 0, 2 * sizeof(uint32_t), s));     // next depth's list counts
             FinalArgs fa;
             fa.nodes = nodes_cur; fa.res = res; fa.excl = excl; fa.tree_off = tree_off; fa.tree_base = tree_base;
             fa.cnt = d_cnt; fa.next = nodes_nxt; fa.small_list = small_a; fa.big_list = big_a;
             fa.packed = packed; fa.stats = d_stats;
+            fa.next_tree_off = tree_off_nxt; fa.T = (int)T; fa.done = d_done;
             const unsigned fgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + 255) / 256, (cps == 3 ? 8 : cps) * dev_sms));
             prof_begin(s, kProfFinalize);
             finalize_kernel<<<fgrid, 256, 0, s>>>(fa);
             AIWCRF_LAUNCH_CHECK("finalize_kernel");
-            tree_update_kernel<<<(unsigned)((T + 256) / 256), 256, 0, s>>>(tree_off, tree_base, excl, tree_off_nxt,
-                                                                            (int)T, d_cnt);
-            AIWCRF_LAUNCH_CHECK("tree_update_kernel");
             prof_end(s, kProfFinalize);
 
             std::swap(nodes_cur, nodes_nxt);
@@ -1646,11 +1670,11 @@ struct FitPlan {
     PackedRec *packed = nullptr;
     LevelCounts *d_cnt = nullptr;
     uint32_t *d_inbag = nullptr, *gcnt = nullptr;
-    uint32_t *toff_a = nullptr, *toff_b = nullptr, *tree_base = nullptr;
+    uint32_t *toff_a = nullptr, *toff_b = nullptr, *tree_base = nullptr, *d_done = nullptr;
     // schedule and graph
     int cps_big = kBigCtasPerSm, cps_small = kSmallCtasPerSm;
     cudaGraphExec_t exec = nullptr;
-    int64_t prefix_launches = 0;
+    int64_t prefix_launches = 0, body_launches = 0;
 
     template <class U>
     int alloc(U **ptr, size_t count)
@@ -1752,6 +1776,7 @@ int plan_bootstrap(FitPlan &P, cudaStream_t s)
     iota_kernel<<<(unsigned)((P.T + 256) / 256), 256, 0, s>>>(P.toff_a, (int)P.T);
     AIWCRF_LAUNCH_CHECK("iota_kernel");
     AIWCRF_CUDA(cudaMemsetAsync(P.tree_base, 0, sizeof(uint32_t) * (size_t)P.T, s));
+    AIWCRF_CUDA(cudaMemsetAsync(P.d_done, 0, sizeof(uint32_t), s));
     return AIWCRF_OK;
 }
 
@@ -1778,20 +1803,16 @@ int plan_level(FitPlan &P, cudaStream_t s, NodeRec *nodes_in, NodeRec *nodes_out
     AIWCRF_LAUNCH_CHECK("level_small_kernel");
     const unsigned sgrid = (unsigned)(2 * P.sms);
     scan_reduce_kernel<<<sgrid, kScanThreads, 0, s>>>(P.res, P.d_cnt, P.block_sums);
-    scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(P.block_sums, 0, P.d_cnt);
     scan_write_kernel<<<sgrid, kScanThreads, 0, s>>>(P.res, P.d_cnt, P.block_sums, P.excl);
-    count_launches(2);
+    count_launches(1);
     AIWCRF_LAUNCH_CHECK("scan kernels");
-    AIWCRF_CUDA(cudaMemsetAsync(P.d_cnt, 0, 2 * sizeof(uint32_t), s));
     FinalArgs fa;
     fa.nodes = nodes_in; fa.res = P.res; fa.excl = P.excl; fa.tree_off = toff_in; fa.tree_base = P.tree_base;
     fa.cnt = P.d_cnt; fa.next = nodes_out; fa.small_list = P.small_l; fa.big_list = P.big_l;
     fa.packed = P.packed; fa.stats = P.d_stats;
+    fa.next_tree_off = toff_out; fa.T = (int)P.T; fa.done = P.d_done;
     finalize_kernel<<<(unsigned)(8 * P.sms), 256, 0, s>>>(fa);
     AIWCRF_LAUNCH_CHECK("finalize_kernel");
-    tree_update_kernel<<<(unsigned)((P.T + 256) / 256), 256, 0, s>>>(toff_in, P.tree_base, P.excl, toff_out, (int)P.T,
-                                                                     P.d_cnt);
-    AIWCRF_LAUNCH_CHECK("tree_update_kernel");
     return AIWCRF_OK;
 }
 
@@ -1831,6 +1852,7 @@ int plan_capture(FitPlan &P)
         if (e != cudaSuccess) {
             rc = cuda_fail(e, "fit plan: level loop node");
         } else {
+            P.prefix_launches = aiwcrf_launch_count() - l0;
             rc = plan_level(P, bs, P.nodes_a, P.nodes_b, P.rows_a, P.rows_b, P.toff_a, P.toff_b);
             if (rc == AIWCRF_OK) rc = plan_level(P, bs, P.nodes_b, P.nodes_a, P.rows_b, P.rows_a, P.toff_b, P.toff_a);
             if (rc == AIWCRF_OK) {
@@ -1847,8 +1869,8 @@ int plan_capture(FitPlan &P)
     const cudaError_t e4 = cudaStreamEndCapture(cs, &g);
     if (rc != AIWCRF_OK) return rc;
     if (e4 != cudaSuccess) return cuda_fail(e4, "fit plan: capture");
-    P.prefix_launches = aiwcrf_launch_count() - l0;
-    count_launches(-(int)P.prefix_launches);          // captured, not run
+    P.body_launches = aiwcrf_launch_count() - l0 - P.prefix_launches;
+    count_launches(-(int)(P.prefix_launches + P.body_launches));     // captured, not run
     if (P.exec) { cudaGraphExecDestroy(P.exec); P.exec = nullptr; }
     AIWCRF_CUDA(cudaGraphInstantiate(&P.exec, g, 0));
     return AIWCRF_OK;
@@ -1909,7 +1931,7 @@ int fit_plan_create(const aiwcrf_fit_params &p, const float *dX, const int64_t *
         (rc = Q.alloc(&Q.small_l, (size_t)Q.C_max)) || (rc = Q.alloc(&Q.big_l, (size_t)Q.C_max)) ||
         (rc = Q.alloc(&Q.packed, (size_t)Q.packed_cap)) || (rc = Q.alloc(&Q.d_cnt, 1)) ||
         (rc = Q.alloc(&Q.toff_a, (size_t)Q.T + 1)) || (rc = Q.alloc(&Q.toff_b, (size_t)Q.T + 1)) ||
-        (rc = Q.alloc(&Q.tree_base, (size_t)Q.T)))
+        (rc = Q.alloc(&Q.tree_base, (size_t)Q.T)) || (rc = Q.alloc(&Q.d_done, 1)))
         return rc;
     Q.inbag_words = (N + 31) / 32;
     if (!d_sub_rows && (rc = Q.alloc(&Q.d_inbag, (size_t)Q.T * (size_t)Q.inbag_words))) return rc;
@@ -1949,7 +1971,7 @@ int fit_plan_run(FitPlan *P, cudaStream_t s, std::vector<aiwcrf_forest *> &out)
     if (rc) return rc;
     const uint32_t n_groups = h_err[1];
     const int64_t iters = ((int64_t)h_cnt->levels + 1) / 2;
-    count_launches((int)(P->prefix_launches - 15 + 15 * iters));    // the captured body ran iters times
+    count_launches((int)(P->prefix_launches + P->body_launches * iters));    // the body ran iters times
     PackIn pin;
     pin.p = &P->p; pin.T = P->T; pin.Tper = P->Tper; pin.G = P->G; pin.N = P->N; pin.F = P->F; pin.device = P->device;
     pin.tree_base = P->tree_base; pin.d_stats = P->d_stats; pin.packed = P->packed; pin.packed_n = (size_t)h_cnt->packed_off;
