@@ -369,6 +369,18 @@ __device__ __forceinline__ void warp_mtry(const LevelArgs &a, uint32_t tg, uint3
         for (int c = 0; c < 4; ++c) mask[c] = __ballot_sync(kFull, c < nch && c * 32 + lane < F);
         return;
     }
+    if (nch == 1) {
+        // F <= 32: one key per lane; lanes >= F hold 0xFFFFFFFF, which never ranks below a
+        // feature's key (on an equal key the higher index loses)
+        uint32_t cnt0 = 0u;
+#pragma unroll
+        for (int g = 0; g < 32; ++g) {
+            const uint32_t kg = __shfl_sync(kFull, key[0], g);
+            cnt0 += (kg < key[0] || (kg == key[0] && g < lane)) ? 1u : 0u;
+        }
+        mask[0] = __ballot_sync(kFull, lane < F && cnt0 < (uint32_t)a.mtry);
+        return;
+    }
     uint32_t cnt[4] = {0u, 0u, 0u, 0u};
     for (int c2 = 0; c2 < nch; ++c2) {
         for (int s = 0; s < 32; ++s) {
@@ -454,10 +466,13 @@ __device__ __forceinline__ void small_node(const LevelArgs &a, const RT *__restr
     uint32_t mask[4];
     warp_mtry(a, a.tree_rng[nd.tree], nd.idx, mask);
     const int n_tried = __popc(mask[0]) + __popc(mask[1]) + __popc(mask[2]) + __popc(mask[3]);
+    const int f_lane = lane < n_tried ? nth_feature(mask, lane) : -1;     // lane p: p-th tried feature
 
     Cand best = cand_none();
     for (int q0 = 0; q0 < n_tried; q0 += P) {
-        const int f = (q0 + seg < n_tried) ? nth_feature(mask, q0 + seg) : -1;
+        const int qf = q0 + seg;
+        const int fs = __shfl_sync(kFull, f_lane, qf & 31);
+        const int f = qf < n_tried ? (qf < 32 ? fs : nth_feature(mask, qf)) : -1;
         const bool live = valid && f >= 0;
         const uint32_t rank = live ? (uint32_t)__ldg(&Rr[rec + f]) : kRankSentinel;
         // a pass whose features are all constant over the node has no boundary (lane seg*K
@@ -565,6 +580,7 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
     uint32_t *bw = sm_bins;                                       // sum w, then its prefix
     uint32_t *blo = sm_bins + bin_cap;                            // sum w*y: low word
     int32_t *bhi = reinterpret_cast<int32_t *>(sm_bins + 2 * bin_cap);   // high word
+    uint16_t *cand_l = reinterpret_cast<uint16_t *>(sm_bins + 3 * bin_cap);  // present bins, per warp
     __shared__ int feats[AIWCRF_MAX_FEATURES];
     __shared__ uint32_t fbase[AIWCRF_MAX_FEATURES + 1];
     __shared__ uint32_t carry_w[AIWCRF_MAX_FEATURES];
@@ -725,15 +741,26 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
         }
         __syncthreads();
 
-        // candidates of this thread's bins
-        if (lo < hi) {
-            int k = k_lo;
-            while (k < k_hi && fbase[k + 1] <= g0 + (uint32_t)lo) ++k;
-            for (int b = lo; b < hi; ++b) {
+        // candidates: each warp first lists the present ranks (bins holding entries) of its
+        // threads' bins, by ballots, in its own part of cand_l (warp w's part starts at its first
+        // bin and holds at most its bins); then its lanes evaluate the listed bins one each
+        {
+            uint16_t *wl = cand_l + (size_t)warp * 32u * (size_t)per;
+            uint32_t n_w = 0u;
+            for (int i = 0; i < per; ++i) {
+                const int b = lo + i;
+                const bool pres = b < hi && bw[b] != (b > 0 ? bw[b - 1] : 0u);
+                const uint32_t bal = __ballot_sync(kFull, pres);
+                if (pres) wl[n_w + __popc(bal & lanemask_lt())] = (uint16_t)b;
+                n_w += (uint32_t)__popc(bal);
+            }
+            __syncwarp();
+            for (uint32_t ix = (uint32_t)lane; ix < n_w; ix += 32u) {
+                const int b = wl[ix];
                 const uint32_t gb = g0 + (uint32_t)b;
+                int k = k_lo;
                 while (fbase[k + 1] <= gb) ++k;
                 const uint32_t pw = bw[b];
-                if (pw == (b > 0 ? bw[b - 1] : 0u)) continue;          // rank not present
                 const int fs = (int)(max(fbase[k], g0) - g0);          // feature's first bin here
                 const uint32_t nL = pw - (fs > 0 ? bw[fs - 1] : 0u) + carry_w[k];
                 if (nL >= nd.n) continue;                               // last present rank
@@ -1511,7 +1538,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
 
     // bins: the tried features' value counts side by side (one pass over the entries)
     const int bin_cap = big_bin_cap(p.mtry, F, max_card);
-    const int big_smem = bin_cap * 12;
+    const int big_smem = bin_cap * 14;
     AIWCRF_CUDA(cudaFuncSetAttribute(level_big_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem));
     AIWCRF_CUDA(cudaFuncSetAttribute(level_big_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem));
 
@@ -1791,7 +1818,7 @@ int plan_level(FitPlan &P, cudaStream_t s, NodeRec *nodes_in, NodeRec *nodes_out
     la.max_depth = P.p.max_depth; la.seed_lo = (uint32_t)P.p.seed; la.seed_hi = (uint32_t)(P.p.seed >> 32);
     la.depth = 0; la.depth_ptr = &P.d_cnt->levels;
     la.nodes = nodes_in; la.rows_in = rin; la.rows_out = rout; la.res = P.res;
-    const int bin_cap = big_bin_cap(P.p.mtry, P.F, P.max_card), big_smem = bin_cap * 12;
+    const int bin_cap = big_bin_cap(P.p.mtry, P.F, P.max_card), big_smem = bin_cap * 14;
     la.list = P.big_l; la.list_n = &P.d_cnt->n_big;
     const unsigned gbig = (unsigned)(P.cps_big * P.sms), gsmall = (unsigned)(P.cps_small * P.sms);
     if (P.rank8) level_big_kernel<uint8_t><<<gbig, kBigThreads, big_smem, s>>>(la, bin_cap);
@@ -1949,7 +1976,7 @@ int fit_plan_create(const aiwcrf_fit_params &p, const float *dX, const int64_t *
     AIWCRF_CUDA(cudaMemcpyAsync(Q.d_rng, h_rng.data(), sizeof(uint32_t) * (size_t)Q.T, cudaMemcpyHostToDevice, s));
     AIWCRF_CUDA(cudaStreamSynchronize(s));
     AIWCRF_CUDA(cudaFuncSetAttribute(bootstrap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, std::max(Q.boot_smem, 1)));
-    const int big_smem = big_bin_cap(p.mtry, F, Q.max_card) * 12;
+    const int big_smem = big_bin_cap(p.mtry, F, Q.max_card) * 14;
     AIWCRF_CUDA(cudaFuncSetAttribute(level_big_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem));
     AIWCRF_CUDA(cudaFuncSetAttribute(level_big_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem));
     if ((rc = plan_capture(Q))) return rc;

@@ -251,7 +251,9 @@ __global__ void compact_nodes_kernel(const uint64_t *__restrict__ cnodes, const 
     const int64_t a = tree_off[t], m = tree_off[t + 1] - a;
     const int64_t a4 = tree_off4[t], m4 = tree_off4[t + 1] - a4;
     for (int64_t j = threadIdx.x; j < m4; j += blockDim.x) {
-        uint32_t v = 0x80000000u;
+        // a leaf (and a pad) is its own child: left = j, threshold 255 (no code exceeds it),
+        // feature field 255 with the top bit as the leaf flag
+        uint32_t v = 0xFFFF0000u | (uint32_t)j;
         if (j < m) {
             const uint64_t nd = cnodes[a + j];
             if (!(nd >> 63)) {
@@ -279,25 +281,32 @@ __device__ __forceinline__ void issue_tree4(const uint32_t *c32, const int64_t *
     }
 }
 
-// Walk of compact nodes; returns each chain's leaf index within the tree.
+// Walk of compact nodes; returns each chain's leaf index within the tree. A leaf is its own
+// child, so a step past it stays on it: chains step kWalkSteps nodes at a time with no per-step
+// leaf test, and the warp stops once the last node of every chain was a leaf. (A leaf's feature
+// field is 255: its code read lands in the padding after the query rows and is never above the
+// leaf's threshold 255.)
+constexpr int kWalkSteps = 2;
 template <int QPT, typename NodePtr>
 __device__ __forceinline__ void walk_tree4(NodePtr tn, const uint8_t *const (&xr)[QPT], uint32_t (&j)[QPT])
 {
+    uint32_t nd[QPT];
 #pragma unroll
     for (int i = 0; i < QPT; ++i) j[i] = 0u;
     for (;;) {
-        bool more = false;
 #pragma unroll
-        for (int i = 0; i < QPT; ++i) {
-            const uint32_t nd = tn[j[i]];
-            const bool leaf = (int32_t)nd < 0;
-            const uint32_t f = leaf ? 0u : (nd >> 24);
-            const uint32_t c = (uint32_t)xr[i][f];
-            const uint32_t nxt = (nd & 0xFFFFu) + (c > ((nd >> 16) & 0xFFu) ? 1u : 0u);
-            j[i] = leaf ? j[i] : nxt;
-            more |= !leaf;
+        for (int u = 0; u < kWalkSteps; ++u) {
+#pragma unroll
+            for (int i = 0; i < QPT; ++i) {
+                nd[i] = tn[j[i]];
+                const uint32_t c = (uint32_t)xr[i][nd[i] >> 24];
+                j[i] = (nd[i] & 0xFFFFu) + (c > ((nd[i] >> 16) & 0xFFu) ? 1u : 0u);
+            }
         }
-        if (!more) break;
+        bool done = true;
+#pragma unroll
+        for (int i = 0; i < QPT; ++i) done = done && (int32_t)nd[i] < 0;
+        if (__all_sync(kFull, done)) break;
     }
 }
 
@@ -535,7 +544,8 @@ int launch_predict(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t 
     code_queries_kernel<CT><<<dim3((unsigned)((Q + 255) / 256), (unsigned)f->F), 256, 0, s>>>(
         dXq, Q, f->F, f->d_fvals, f->fstride, f->d_fcard, d_codes, ld);
     count_launches(1);
-    const int xs_bytes = kPredThreads * kQPT * ld_words * 4;
+    // query code rows, then 256 bytes that a leaf's code read (feature field 255) may touch
+    const int xs_bytes = kPredThreads * kQPT * ld_words * 4 + 256;
     // two tree slots, sized to the largest tree up to 48 KB each
     int tree_cap = std::min<int>((optin - xs_bytes - 1024) / 16, 6144);
     if ((int64_t)tree_cap > f->max_tree_nodes) tree_cap = (int)f->max_tree_nodes;
@@ -572,7 +582,8 @@ int launch_predict4(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t
     code_queries_kernel<uint8_t><<<dim3((unsigned)((Q + 255) / 256), (unsigned)f->F), 256, 0, s>>>(
         dXq, Q, f->F, f->d_fvals, f->fstride, f->d_fcard, d_codes, ld_words * 4);
     count_launches(1);
-    const int xs_bytes = kPredThreads * kQPT * ld_words * 4;
+    // query code rows, then 256 bytes that a leaf's code read (feature field 255) may touch
+    const int xs_bytes = kPredThreads * kQPT * ld_words * 4 + 256;
     // two tree slots of 4-byte nodes, sized to the largest tree up to 48 KB each
     int tree_cap = std::min<int>((optin - xs_bytes - 1024) / 8, 12288);
     if ((int64_t)tree_cap > f->max_tree4) tree_cap = (int)f->max_tree4;
