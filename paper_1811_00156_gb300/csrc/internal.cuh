@@ -136,13 +136,16 @@ __device__ __forceinline__ i128_t cand_delta(uint32_t n, int64_t S, uint32_t nL,
 
 __device__ __forceinline__ float cand_h(i128_t delta, uint32_t n, uint32_t nL)
 {
+    // |delta| < 2^96 and den < 2^64 are converted from 32-bit limbs (32-bit conversions stay off
+    // the FP64 pipe): three limb conversions and two roundings for |delta|, two and one for den,
+    // rsqrtf (at most 2 ulp) and the product keep the relative error of h below 2^-20
     const u128_t a = delta < 0 ? (u128_t)(-delta) : (u128_t)delta;
-    const uint64_t hi = (uint64_t)(a >> 64), lo = (uint64_t)a;
-    const float fa = __fadd_rn(__fmul_rn(__ull2float_rn(hi), 18446744073709551616.0f), __ull2float_rn(lo));
+    const float fa = __fadd_rn(__fmaf_rn(__uint2float_rn((uint32_t)(a >> 64)), 18446744073709551616.0f,
+                                         __fmul_rn(__uint2float_rn((uint32_t)(a >> 32)), 4294967296.0f)),
+                               __uint2float_rn((uint32_t)a));
     const uint64_t den = (uint64_t)nL * (uint64_t)(n - nL);
-    // |delta| (3 roundings), den (1), rsqrtf (at most 2 ulp) and the product (1) keep the
-    // relative error of h below 2^-20
-    return __fmul_rn(fa, rsqrtf(__ull2float_rn(den)));
+    const float fd = __fmaf_rn(__uint2float_rn((uint32_t)(den >> 32)), 4294967296.0f, __uint2float_rn((uint32_t)den));
+    return __fmul_rn(fa, rsqrtf(fd));
 }
 
 // 256-bit value as four 64-bit limbs, least significant first
@@ -186,20 +189,28 @@ __device__ __forceinline__ int cmp_256(const U256 &a, const U256 &b)
     return 0;
 }
 
-// true if a is the better candidate: larger D, then lower feature, then lower rank
-static __device__ __noinline__ bool cand_better_exact(const Cand &a, const Cand &b, uint32_t n, int64_t S)
+// true if candidate a is better than b: larger D, then lower feature, then lower rank (plain
+// scalar arguments: nothing of the caller's candidates needs an address)
+static __device__ __noinline__ bool cand_better_exact_s(uint32_t a_nL, int64_t a_SL, int32_t a_f, uint32_t a_r,
+                                                        uint32_t b_nL, int64_t b_SL, int32_t b_f, uint32_t b_r,
+                                                        uint32_t n, int64_t S)
 {
-    if (!(a.nL == b.nL && a.SL == b.SL)) {
-        const i128_t da = cand_delta(n, S, a.nL, a.SL), db = cand_delta(n, S, b.nL, b.SL);
+    if (!(a_nL == b_nL && a_SL == b_SL)) {
+        const i128_t da = cand_delta(n, S, a_nL, a_SL), db = cand_delta(n, S, b_nL, b_SL);
         const u128_t ua = da < 0 ? (u128_t)(-da) : (u128_t)da;
         const u128_t ub = db < 0 ? (u128_t)(-db) : (u128_t)db;
-        const uint64_t den_a = (uint64_t)a.nL * (uint64_t)(n - a.nL);
-        const uint64_t den_b = (uint64_t)b.nL * (uint64_t)(n - b.nL);
+        const uint64_t den_a = (uint64_t)a_nL * (uint64_t)(n - a_nL);
+        const uint64_t den_b = (uint64_t)b_nL * (uint64_t)(n - b_nL);
         const int c = cmp_256(mul_256x64(mul_128x128(ua, ua), den_b), mul_256x64(mul_128x128(ub, ub), den_a));
         if (c != 0) return c > 0;
     }
-    if (a.f != b.f) return a.f < b.f;
-    return a.r < b.r;
+    if (a_f != b_f) return a_f < b_f;
+    return a_r < b_r;
+}
+
+__device__ __forceinline__ bool cand_better_exact(const Cand &a, const Cand &b, uint32_t n, int64_t S)
+{
+    return cand_better_exact_s(a.nL, a.SL, a.f, a.r, b.nL, b.SL, b.f, b.r, n, S);
 }
 
 constexpr float kFilterHi = 1.0f + 1.0f / 65536.0f;
