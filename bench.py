@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the OOB and LOKO reports")
+    ap.add_argument("--write-traffic", metavar="CSV", default=None,
+                    help="write profiles/traffic.json from an ncu --csv capture of dram__bytes_read.sum and "
+                         "dram__bytes_write.sum over the benchmark's launches, then exit")
+    ap.add_argument("--traffic-command", default="", help="the ncu command that made the CSV (recorded)")
     ap.add_argument("--trees", type=int, default=T_TREES,
                     help="forest size per GPU; smaller values are for profiler captures only")
     ap.add_argument("--queries", type=int, default=N_QUERIES,
@@ -233,15 +237,28 @@ def run_ours(args):
         if ev: ev[3].record(stream)
         return forest
 
-    for _ in range(args.warmup):
+    LEVEL_CLASSES = ("level_small", "level_big")
+    dom_fit, dom = "level_small", "predict"
+    for w in range(args.warmup):
+        last = w == args.warmup - 1
+        if last:               # the last warm-up step finds the dominant kernels of the fit and the step
+            A.aiwcrf_profile_classes([*LEVEL_CLASSES, "predict"])
+            A.aiwcrf_profile_enable(True)
+            A.aiwcrf_profile_read()
         step()
+        if last:
+            torch.cuda.synchronize()
+            p0 = A.aiwcrf_profile_read()
+            A.aiwcrf_profile_enable(False)
+            dom_fit = max(LEVEL_CLASSES, key=lambda c: p0[c][1])
+            dom = max((*LEVEL_CLASSES, "predict"), key=lambda c: p0[c][1])
     torch.cuda.synchronize()
 
     clocks = Clocks(local_rank)
     clocks.start()
-    # events around the classes the report needs only (each pair costs the stream a little);
-    # profiles/ holds the full launch list
-    A.aiwcrf_profile_classes(["level_small", "level_big", "predict", "select"])
+    # inside the timed steps, events bracket the dominant kernels' launches only: every pair
+    # costs the stream about 2 us, and bracketing every class would add ~5 % to the fit
+    A.aiwcrf_profile_classes(sorted({dom, dom_fit}))
     A.aiwcrf_profile_enable(True)
     A.aiwcrf_profile_read()
     launches0 = A.aiwcrf_launch_count()
@@ -259,10 +276,21 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     launches = A.aiwcrf_launch_count() - launches0
+    prof_dom = A.aiwcrf_profile_read()
+    A.aiwcrf_profile_enable(False)
+    clk = clocks.stop()
+    # the kernel classes' shares: K more (untimed) steps with every class bracketed
+    A.aiwcrf_profile_classes(["level_small", "level_big", "predict", "select"])
+    A.aiwcrf_profile_enable(True)
+    A.aiwcrf_profile_read()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        del_f = step()
+        del del_f
+    torch.cuda.synchronize()
     prof = A.aiwcrf_profile_read()
     A.aiwcrf_profile_enable(False)
     A.aiwcrf_profile_classes(None)
-    clk = clocks.stop()
 
     fit_ms = sum(e[0].elapsed_time(e[1]) for e in evs)
     pred_ms = sum(e[1].elapsed_time(e[2]) for e in evs)
@@ -299,14 +327,17 @@ def run_ours(args):
     tot_ms = sum(v["total_ms"] for v in kernels.values()) or 1.0
     for v in kernels.values():
         v["share_of_profiled"] = v["total_ms"] / tot_ms
-    dom = max((k for k in kernels if k in ("level_big", "level_small")), key=lambda k: kernels[k]["total_ms"])
-    d = kernels[dom]
-    n_l = d["launches"]
-    traffic = ncu_traffic(dom, sha)
-    roofline = {"kernel": dom, "bound": "hbm", "achieved": d["achieved_gbs"], "peak": peak, "unit": "GB/s",
-                "frac": d["achieved_gbs"] / peak, "peak_source": f"hbm_gbs of {peak_kind} peaks",
-                "traffic": traffic, "alg_bytes_per_launch": d["alg_bytes"] / n_l,
-                "ms_per_launch": d["total_ms"] / n_l}
+    # the dominant kernels' launches as timed inside the timed steps
+    def roofline_of(name):
+        n_l, ms = prof_dom[name]
+        achieved = alg[name] / (ms / 1e3) / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind} peaks",
+                "traffic": ncu_traffic(name, sha), "alg_bytes_per_launch": alg[name] / n_l,
+                "ms_per_launch": ms / n_l,
+                "timing": "CUDA events around each launch of this kernel inside the timed steps"}
+    roofline = roofline_of(dom)                  # the step's dominant kernel
+    roofline_fit = roofline_of(dom_fit)          # the fit's (the metric's) dominant kernel
 
     out = {"metric": METRIC, "value": value, "unit": ROWS_TREES_UNIT, "n_gpus": world, "steps": K,
            "warmup": args.warmup, "ms_per_step": step_ms / K, "higher_is_better": True, "scaling": "weak",
@@ -320,7 +351,9 @@ def run_ours(args):
            "predict": {"value": n_queries * K / (pred_ms / 1e3), "unit": "queries/s", "ms": pred_ms / K,
                        "trees": T_total},
            "select": {"ms": sel_ms / K, "kernels": SEL_KERNELS, "devices": SEL_DEVICES},
-           "fit_ms": fit_ms / K, "fit_stats": stats, "roofline": roofline, "kernels": kernels,
+           "fit_ms": fit_ms / K, "fit_stats": stats, "roofline": roofline, "roofline_fit": roofline_fit,
+           "kernels": {"timing": "CUDA events around every launch of these classes, in K further untimed steps",
+                       **kernels},
            "gpu_launches": launches, "clocks": clk, "parity": "bit-exact vs oracle (tests/test_gpu_parity.py)"}
 
     if not args.no_e2e:
@@ -676,8 +709,40 @@ def oob_report(A, wl, X, forest):
             "ms": e0.elapsed_time(e1)}
 
 
+TRAFFIC_CLASSES = {"predict4_kernel": "predict", "level_small_kernel": "level_small", "level_big_kernel": "level_big"}
+
+
+def write_traffic(csv_path: str, command: str):
+    """Per-launch DRAM bytes (read + write) of each kernel class in an ncu CSV, keyed by the
+    kernel source hash so that the bench reports them only while the kernels are unchanged."""
+    import csv
+    rows = list(csv.reader(open(csv_path)))
+    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    hdr = rows[hi]
+    ki, ii, mi, ui, vi = (hdr.index(c) for c in ("Kernel Name", "ID", "Metric Name", "Metric Unit", "Metric Value"))
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
+    per = {}
+    for r in rows[hi + 1:]:
+        if len(r) != len(hdr) or not r[mi].startswith("dram__bytes_"):
+            continue
+        name = r[ki].split("(")[0].split("<")[0].split("::")[-1].replace("void ", "").strip()
+        cls = TRAFFIC_CLASSES.get(name)
+        if cls:
+            per.setdefault(cls, {}).setdefault(r[ii], 0.0)
+            per[cls][r[ii]] += float(r[vi].replace(",", "")) * scale[r[ui]]
+    sha = source_sha()
+    out = {cls: {"bytes_per_launch": sum(v.values()) / len(v), "launches": len(v), "source_sha": sha,
+                 "command": command} for cls, v in per.items()}
+    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as fh:
+        json.dump(out, fh, indent=1, sort_keys=True)
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
+    if args.write_traffic:
+        write_traffic(args.write_traffic, args.traffic_command)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -480,23 +480,20 @@ __device__ __forceinline__ void small_node(const LevelArgs &a, const RT *__restr
         const uint32_t rank0 = __shfl_sync(kFull, rank, lane & ~(K - 1));
         if (__all_sync(kFull, !live || rank == rank0)) continue;
         uint32_t key = (rank << 5) | (uint32_t)pos;                  // unique within a segment
-        uint32_t w = live ? e.w : 0u;
-        long long v = live ? e.wy : 0;
-        // bitonic sort of (key, w, v) within each segment, ascending key
+        // bitonic sort of the keys within each segment, ascending; the low five bits name the
+        // entry's lane, whose w and w*y are fetched once the order is known
         for (int k = 2; k <= K; k <<= 1) {
             for (int jj = k >> 1; jj > 0; jj >>= 1) {
                 const uint32_t ok = __shfl_xor_sync(kFull, key, jj);
-                const uint32_t ow = __shfl_xor_sync(kFull, w, jj);
-                const long long ov = __shfl_xor_sync(kFull, v, jj);
                 const bool asc = (pos & k) == 0;
                 const bool lower = (pos & jj) == 0;
-                const bool take = (lower == asc) ? (ok < key) : (ok > key);
-                if (take) { key = ok; w = ow; v = ov; }
+                key = ((lower == asc) ? (ok < key) : (ok > key)) ? ok : key;
             }
         }
+        const int src = (lane & ~(K - 1)) | (int)(key & 31u);
         const uint32_t r = key >> 5;
-        uint32_t cw = w;
-        long long cs = v;
+        uint32_t cw = __shfl_sync(kFull, live ? e.w : 0u, src);
+        long long cs = __shfl_sync(kFull, live ? (long long)e.wy : 0ll, src);
         for (int o = 1; o < K; o <<= 1) {
             const uint32_t tw = __shfl_up_sync(kFull, cw, o);
             const long long ts = __shfl_up_sync(kFull, cs, o);
