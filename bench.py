@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import concurrent.futures as cf
+import gc
 import hashlib
 import json
 import os
@@ -369,6 +370,10 @@ def run_ours(args):
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
         out["surrogate"] = surrogate_report(A, f, Xq, bf16_peak_tflops=peaks.get("bf16_tflops"))
         del f
+        # the earlier reports' forests, plans and networks are freed now, not by the garbage
+        # collector in the middle of the load test
+        gc.collect()
+        torch.cuda.synchronize()
         out["serving"] = serving_report(A, wl)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl)
@@ -709,30 +714,40 @@ def oob_report(A, wl, X, forest):
             "ms": e0.elapsed_time(e1)}
 
 
-TRAFFIC_CLASSES = {"predict4_kernel": "predict", "level_small_kernel": "level_small", "level_big_kernel": "level_big"}
-
-
 def write_traffic(csv_path: str, command: str):
-    """Per-launch DRAM bytes (read + write) of each kernel class in an ncu CSV, keyed by the
-    kernel source hash so that the bench reports them only while the kernels are unchanged."""
+    """DRAM bytes (read + write) per launch of each kernel class in an ncu CSV of one step's
+    launches, keyed by the kernel source hash so that the bench reports them only while the
+    kernels are unchanged. The level classes are one kernel each; the predict class is every
+    launch from the query coding to the compact walk (coding, key sort, walk), summed."""
     import csv
     rows = list(csv.reader(open(csv_path)))
     hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
     hdr = rows[hi]
     ki, ii, mi, ui, vi = (hdr.index(c) for c in ("Kernel Name", "ID", "Metric Name", "Metric Unit", "Metric Value"))
     scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
-    per = {}
+    launches = {}                                   # launch ID -> [kernel name, bytes]
     for r in rows[hi + 1:]:
         if len(r) != len(hdr) or not r[mi].startswith("dram__bytes_"):
             continue
         name = r[ki].split("(")[0].split("<")[0].split("::")[-1].replace("void ", "").strip()
-        cls = TRAFFIC_CLASSES.get(name)
-        if cls:
-            per.setdefault(cls, {}).setdefault(r[ii], 0.0)
-            per[cls][r[ii]] += float(r[vi].replace(",", "")) * scale[r[ui]]
+        e = launches.setdefault(int(r[ii]), [name, 0.0])
+        e[1] += float(r[vi].replace(",", "")) * scale[r[ui]]
+    per = {}                                        # class -> list of per-launch (or per-call) bytes
+    in_predict, acc = False, 0.0
+    for lid in sorted(launches):
+        name, b = launches[lid]
+        if name == "code_queries_kernel":
+            in_predict, acc = True, 0.0
+        if in_predict:
+            acc += b
+            if name == "predict4_kernel":
+                per.setdefault("predict", []).append(acc)
+                in_predict = False
+        elif name in ("level_small_kernel", "level_big_kernel"):
+            per.setdefault(name.replace("_kernel", ""), []).append(b)
     sha = source_sha()
-    out = {cls: {"bytes_per_launch": sum(v.values()) / len(v), "launches": len(v), "source_sha": sha,
-                 "command": command} for cls, v in per.items()}
+    out = {cls: {"bytes_per_launch": sum(v) / len(v), "launches": len(v), "source_sha": sha, "command": command}
+           for cls, v in per.items()}
     with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as fh:
         json.dump(out, fh, indent=1, sort_keys=True)
     print(json.dumps(out))

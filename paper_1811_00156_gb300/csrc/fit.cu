@@ -1700,11 +1700,14 @@ struct FitPlan {
     cudaGraphExec_t exec = nullptr;
     int64_t prefix_launches = 0, body_launches = 0;
 
+    // buffers come from the stream-ordered pool: freeing them never waits for the whole
+    // device (a selection server may be busy on other streams)
     template <class U>
     int alloc(U **ptr, size_t count)
     {
         void *q = nullptr;
-        const cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(U));
+        cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(count, 1) * sizeof(U), cudaStreamPerThread);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamPerThread);
         if (e != cudaSuccess)
             return fail(AIWCRF_E_OOM, std::string("fit plan: device allocation of ") +
                                           std::to_string(count * sizeof(U)) + " bytes failed");
@@ -1714,8 +1717,10 @@ struct FitPlan {
     }
     ~FitPlan()
     {
+        // a run returns only after its work has finished, so nothing reads these any more
         if (exec) cudaGraphExecDestroy(exec);
-        for (auto b : bufs) cudaFree(b);
+        for (auto b : bufs) cudaFreeAsync(b, cudaStreamPerThread);
+        cudaStreamSynchronize(cudaStreamPerThread);
     }
 };
 

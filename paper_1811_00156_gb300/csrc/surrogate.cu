@@ -372,13 +372,30 @@ struct aiwcrf_surrogate {
 namespace aiwcrf {
 namespace {
 
+// work reading the network may still be in flight on any stream: wait for it, then give the
+// block back to the pool (stream-ordered, no device-wide wait inside the free)
+void surrogate_release(aiwcrf_surrogate *s)
+{
+    if (!s) return;
+    cudaDeviceSynchronize();
+    if (s->d_block) cudaFreeAsync(s->d_block, cudaStreamPerThread);
+    cudaStreamSynchronize(cudaStreamPerThread);
+    delete s;
+}
+
 int surrogate_alloc(aiwcrf_surrogate *s)
 {
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t bp = up(4 * (size_t)kParams), bf = up(4 * (size_t)s->n_aiwc), bl = up((size_t)s->n_aiwc);
     const size_t bw1 = up(2 * (size_t)kHid * kIn), bw2 = up(2 * (size_t)kHid * kHid);
+    // from the stream-ordered pool, whose frees never wait for the whole device (a
+    // selection server may be busy on other streams)
+    int dev = 0;
+    cudaGetDevice(&dev);
+    keep_pool_memory(dev);
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bp + 2 * bf + bl + bw1 + bw2);
+    cudaError_t e = cudaMallocAsync(&p, bp + 2 * bf + bl + bw1 + bw2, cudaStreamPerThread);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamPerThread);
     if (e != cudaSuccess) return fail(AIWCRF_E_OOM, "surrogate allocation");
     unsigned char *c = static_cast<unsigned char *>(p);
     s->d_block = p;
@@ -621,7 +638,7 @@ int aiwcrf_surrogate_fit(const aiwcrf_surrogate_params *p, const aiwcrf_forest *
     aiwcrf_surrogate *sg = nullptr;
     int rc = new_surrogate(n_features, p->n_devices, p->n_sizes, &sg);
     if (rc) return rc;
-    struct Guard { aiwcrf_surrogate *g; bool keep = false; ~Guard() { if (!keep && g) { cudaFree(g->d_block); delete g; } } } guard{sg};
+    struct Guard { aiwcrf_surrogate *g; bool keep = false; ~Guard() { if (!keep && g) surrogate_release(g); } } guard{sg};
 
     // labels: the teacher forest's predictions (log10 seconds)
     float *d_y = nullptr;
@@ -749,7 +766,7 @@ int aiwcrf_surrogate_create(int32_t n_features, int32_t n_devices, int32_t n_siz
     }
     if (!rc) rc = refresh_bf16(sg, nullptr);
     if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "surrogate create");
-    if (rc) { cudaFree(sg->d_block); delete sg; return rc; }
+    if (rc) { surrogate_release(sg); return rc; }
     *out = sg;
     return AIWCRF_OK;
 }
@@ -777,8 +794,7 @@ int32_t aiwcrf_surrogate_num_params(void) { return kParams; }
 int aiwcrf_surrogate_free(aiwcrf_surrogate *sg)
 {
     if (!sg) return AIWCRF_OK;
-    cudaFree(sg->d_block);
-    delete sg;
+    surrogate_release(sg);
     return AIWCRF_OK;
 }
 
