@@ -1545,6 +1545,30 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     la.max_depth = p.max_depth; la.seed_lo = (uint32_t)p.seed; la.seed_hi = (uint32_t)(p.seed >> 32);
     la.depth_ptr = nullptr;
 
+    // The two level kernels of a depth are independent (disjoint nodes, disjoint entry
+    // segments): a foreground fit runs the small-node kernel on a second stream of the same
+    // priority, forked after the previous depth's finalize and joined before the scan, so that
+    // either kernel's tail overlaps the other's work. (A background fit stays on one stream.)
+    struct Fork {
+        cudaStream_t side = nullptr;
+        cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+        ~Fork()
+        {
+            if (ev_fork) cudaEventDestroy(ev_fork);
+            if (ev_join) cudaEventDestroy(ev_join);
+            if (side) cudaStreamDestroy(side);
+        }
+    } fk;
+    const bool fork = p.ctas_per_sm == 0;
+    if (fork) {
+        int prio = 0;
+        AIWCRF_CUDA(cudaStreamGetPriority(s, &prio));
+        AIWCRF_CUDA(cudaStreamCreateWithPriority(&fk.side, cudaStreamNonBlocking, prio));
+        AIWCRF_CUDA(cudaEventCreateWithFlags(&fk.ev_fork, cudaEventDisableTiming));
+        AIWCRF_CUDA(cudaEventCreateWithFlags(&fk.ev_join, cudaEventDisableTiming));
+    }
+    cudaStream_t s_small = fork ? fk.side : s;
+
     Entry *rin = rows_a, *rout = rows_b;
     int depth = 0;
     int64_t C_known = T;                 // node count at the start of the next chunk (exact)
@@ -1565,6 +1589,10 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         for (int k = 0; k < chunk; ++k, ++depth) {
             const int64_t Cb = bound(k);                        // bound on this depth's nodes
             la.nodes = nodes_cur; la.rows_in = rin; la.rows_out = rout; la.depth = depth; la.res = res;
+            if (fork) {
+                AIWCRF_CUDA(cudaEventRecord(fk.ev_fork, s));
+                AIWCRF_CUDA(cudaStreamWaitEvent(fk.side, fk.ev_fork, 0));
+            }
             {
                 la.list = big_a; la.list_n = &d_cnt->n_big;
                 const int64_t cps_big = p.ctas_per_sm > 0 ? p.ctas_per_sm : kBigCtasPerSm;
@@ -1580,11 +1608,15 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
                 const int64_t wpb = kSmallThreads / 32;
                 const int64_t cps_small = p.ctas_per_sm > 0 ? p.ctas_per_sm : kSmallCtasPerSm;
                 const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + wpb - 1) / wpb, cps_small * dev_sms));
-                prof_begin(s, kProfLevelSmall);
-                if (rank8) level_small_kernel<uint8_t><<<grid, kSmallThreads, 0, s>>>(la);
-                else level_small_kernel<uint16_t><<<grid, kSmallThreads, 0, s>>>(la);
+                prof_begin(s_small, kProfLevelSmall);
+                if (rank8) level_small_kernel<uint8_t><<<grid, kSmallThreads, 0, s_small>>>(la);
+                else level_small_kernel<uint16_t><<<grid, kSmallThreads, 0, s_small>>>(la);
                 AIWCRF_LAUNCH_CHECK("level_small_kernel");
-                prof_end(s, kProfLevelSmall);
+                prof_end(s_small, kProfLevelSmall);
+            }
+            if (fork) {
+                AIWCRF_CUDA(cudaEventRecord(fk.ev_join, fk.side));
+                AIWCRF_CUDA(cudaStreamWaitEvent(s, fk.ev_join, 0));
             }
             const unsigned sgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + kScanTile - 1) / kScanTile, std::min<int64_t>(2, cps) * dev_sms));
             prof_begin(s, kProfScan);
