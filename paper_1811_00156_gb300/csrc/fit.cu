@@ -1843,8 +1843,10 @@ int plan_bootstrap(FitPlan &P, cudaStream_t s)
 
 // one level from (nodes_in, rin, toff_in) to (nodes_out, rout, toff_out), at the depth the
 // device's level counter holds; fixed grids (the kernels stride over the device's counts)
-int plan_level(FitPlan &P, cudaStream_t s, NodeRec *nodes_in, NodeRec *nodes_out, Entry *rin, Entry *rout,
-               uint32_t *toff_in, uint32_t *toff_out)
+// one depth; the small-node kernel is captured on `side` (forked and joined through the two
+// events), so the graph runs the depth's two level kernels as parallel branches
+int plan_level(FitPlan &P, cudaStream_t s, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join,
+               NodeRec *nodes_in, NodeRec *nodes_out, Entry *rin, Entry *rout, uint32_t *toff_in, uint32_t *toff_out)
 {
     LevelArgs la;
     la.row_cap = P.row_cap; la.Rr = P.d_Rr; la.vals = P.d_vals; la.card = P.d_card; la.N = P.N;
@@ -1855,13 +1857,17 @@ int plan_level(FitPlan &P, cudaStream_t s, NodeRec *nodes_in, NodeRec *nodes_out
     const int bin_cap = big_bin_cap(P.p.mtry, P.F, P.max_card), big_smem = bin_cap * 14;
     la.list = P.big_l; la.list_n = &P.d_cnt->n_big;
     const unsigned gbig = (unsigned)(P.cps_big * P.sms), gsmall = (unsigned)(P.cps_small * P.sms);
+    AIWCRF_CUDA(cudaEventRecord(ev_fork, s));
+    AIWCRF_CUDA(cudaStreamWaitEvent(side, ev_fork, 0));
     if (P.rank8) level_big_kernel<uint8_t><<<gbig, kBigThreads, big_smem, s>>>(la, bin_cap);
     else level_big_kernel<uint16_t><<<gbig, kBigThreads, big_smem, s>>>(la, bin_cap);
     AIWCRF_LAUNCH_CHECK("level_big_kernel");
     la.list = P.small_l; la.list_n = &P.d_cnt->n_small;
-    if (P.rank8) level_small_kernel<uint8_t><<<gsmall, kSmallThreads, 0, s>>>(la);
-    else level_small_kernel<uint16_t><<<gsmall, kSmallThreads, 0, s>>>(la);
+    if (P.rank8) level_small_kernel<uint8_t><<<gsmall, kSmallThreads, 0, side>>>(la);
+    else level_small_kernel<uint16_t><<<gsmall, kSmallThreads, 0, side>>>(la);
     AIWCRF_LAUNCH_CHECK("level_small_kernel");
+    AIWCRF_CUDA(cudaEventRecord(ev_join, side));
+    AIWCRF_CUDA(cudaStreamWaitEvent(s, ev_join, 0));
     const unsigned sgrid = (unsigned)(2 * P.sms);
     scan_reduce_kernel<<<sgrid, kScanThreads, 0, s>>>(P.res, P.d_cnt, P.block_sums);
     scan_write_kernel<<<sgrid, kScanThreads, 0, s>>>(P.res, P.d_cnt, P.block_sums, P.excl);
@@ -1880,10 +1886,25 @@ int plan_level(FitPlan &P, cudaStream_t s, NodeRec *nodes_in, NodeRec *nodes_out
 // capture the graph for the plan's current schedule and instantiate it
 int plan_capture(FitPlan &P)
 {
-    cudaStream_t cs = nullptr, bs = nullptr;
+    cudaStream_t cs = nullptr, bs = nullptr, ss = nullptr;
+    cudaEvent_t evf = nullptr, evj = nullptr;
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
-    struct Streams { cudaStream_t a, b; ~Streams() { if (a) cudaStreamDestroy(a); if (b) cudaStreamDestroy(b); } } st{cs, bs};
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&evf, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&evj, cudaEventDisableTiming);
+    struct Streams {
+        cudaStream_t a, b, c;
+        cudaEvent_t f, j;
+        ~Streams()
+        {
+            if (f) cudaEventDestroy(f);
+            if (j) cudaEventDestroy(j);
+            if (a) cudaStreamDestroy(a);
+            if (b) cudaStreamDestroy(b);
+            if (c) cudaStreamDestroy(c);
+        }
+    } st{cs, bs, ss, evf, evj};
     if (e != cudaSuccess) return cuda_fail(e, "fit plan: streams");
     cudaGraph_t g = nullptr;
     struct G { cudaGraph_t *g; ~G() { if (*g) cudaGraphDestroy(*g); } } gg{&g};
@@ -1914,8 +1935,9 @@ int plan_capture(FitPlan &P)
             rc = cuda_fail(e, "fit plan: level loop node");
         } else {
             P.prefix_launches = aiwcrf_launch_count() - l0;
-            rc = plan_level(P, bs, P.nodes_a, P.nodes_b, P.rows_a, P.rows_b, P.toff_a, P.toff_b);
-            if (rc == AIWCRF_OK) rc = plan_level(P, bs, P.nodes_b, P.nodes_a, P.rows_b, P.rows_a, P.toff_b, P.toff_a);
+            rc = plan_level(P, bs, ss, evf, evj, P.nodes_a, P.nodes_b, P.rows_a, P.rows_b, P.toff_a, P.toff_b);
+            if (rc == AIWCRF_OK)
+                rc = plan_level(P, bs, ss, evf, evj, P.nodes_b, P.nodes_a, P.rows_b, P.rows_a, P.toff_b, P.toff_a);
             if (rc == AIWCRF_OK) {
                 level_loop_cond_kernel<<<1, 32, 0, bs>>>(h, P.d_cnt, (uint32_t)(P.row_cap + 2), P.d_err);
                 count_launches(1);
