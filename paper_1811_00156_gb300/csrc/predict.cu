@@ -521,7 +521,7 @@ __global__ void argmin_kernel(const int64_t *pred, const int32_t *dev, int32_t K
 
 namespace {
 
-constexpr int kQPT = 1;
+constexpr int kQPT = 2;
 // compact-forest batches of at least this many queries are walked in sorted order
 constexpr int64_t kSortMinQueries = 1 << 16;
 

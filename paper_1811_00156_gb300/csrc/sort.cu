@@ -29,20 +29,34 @@ __global__ void __launch_bounds__(kSortThreads) sort_hist_kernel(const uint32_t 
     hist[((size_t)seg * 256 + tid) * (size_t)nb + b] = h[tid];
 }
 
-// exclusive scan of one segment's 256 * nb counts, digit-major
+// exclusive scan of one segment's 256 * nb counts, digit-major: every thread sums a contiguous
+// run of 16-byte words (independent loads), one block scan of the run sums, then every thread
+// rewrites its run from its own prefix. (A segment starts 1,024 * nb bytes after the 16-byte
+// aligned base, and 256 * nb counts are whole words.)
 __global__ void __launch_bounds__(1024) sort_scan_kernel(uint32_t *hist, int nb)
 {
     __shared__ uint32_t warp_tmp[32];
-    uint32_t *h = hist + (size_t)blockIdx.x * 256 * (size_t)nb;
-    const int64_t total = 256 * (int64_t)nb;
-    uint32_t carry = 0;
-    for (int64_t b0 = 0; b0 < total; b0 += 1024) {
-        const int64_t i = b0 + threadIdx.x;
-        const uint32_t v = i < total ? h[i] : 0u;
-        uint32_t tot;
-        const uint32_t incl = block_incl_scan(v, warp_tmp, tot);
-        if (i < total) h[i] = carry + incl - v;
-        carry += tot;
+    uint4 *h4 = reinterpret_cast<uint4 *>(hist + (size_t)blockIdx.x * 256 * (size_t)nb);
+    const int64_t total4 = 64 * (int64_t)nb;
+    const int64_t per = (total4 + 1023) / 1024;
+    const int64_t lo = min(total4, (int64_t)threadIdx.x * per), hi = min(total4, lo + per);
+    uint32_t sum = 0;
+#pragma unroll 4
+    for (int64_t i = lo; i < hi; ++i) {
+        const uint4 v = h4[i];
+        sum += v.x + v.y + v.z + v.w;
+    }
+    uint32_t tot;
+    uint32_t run = block_incl_scan(sum, warp_tmp, tot) - sum;
+#pragma unroll 4
+    for (int64_t i = lo; i < hi; ++i) {
+        const uint4 v = h4[i];
+        uint4 o;
+        o.x = run; run += v.x;
+        o.y = run; run += v.y;
+        o.z = run; run += v.z;
+        o.w = run; run += v.w;
+        h4[i] = o;
     }
 }
 
