@@ -363,9 +363,13 @@ __global__ void __launch_bounds__(kPredThreads) predict4_kernel(
 #pragma unroll
     for (int i = 0; i < QPT; ++i) { acc[i] = 0; pend[i] = 0; sq[i] = 0; }
 
+    // the tree's offsets are loaded one tree ahead, so their latency overlaps a walk
+    int64_t a4 = tree_off4[0], b4 = T > 0 ? tree_off4[1] : 0, ta = tree_off[0];
     for (int t = 0; t < T; ++t) {
         const int s = t & 1;
         const uint32_t parity = (uint32_t)((t >> 1) & 1);
+        const int tn1 = t + 1 < T ? t + 1 : t;
+        const int64_t b4n = tree_off4[tn1 + 1], tan = tree_off[tn1];
         bool ok = false;
         for (uint32_t it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(&bar[s], parity);
         if (__syncthreads_or(!ok)) {
@@ -376,15 +380,17 @@ __global__ void __launch_bounds__(kPredThreads) predict4_kernel(
             return;
         }
         uint32_t j[QPT];
-        const int64_t a4 = tree_off4[t];
-        if (tree_off4[t + 1] - a4 <= tree_cap) {
+        if (b4 - a4 <= tree_cap) {
             if (s) walk_tree4<QPT>(slot1, xr, j);
             else walk_tree4<QPT>(slot0, xr, j);
         } else {
             walk_tree4<QPT>(c32 + a4, xr, j);
         }
         // add the previous tree's leaves, then start loading this tree's
-        const uint64_t *tn = nodes + tree_off[t];
+        const uint64_t *tn = nodes + ta;
+        a4 = b4;
+        b4 = b4n;
+        ta = tan;
 #pragma unroll
         for (int i = 0; i < QPT; ++i) {
             acc[i] += pend[i];
