@@ -317,6 +317,10 @@ struct LevelCounts {
     unsigned long long packed_off;    // finished nodes of the earlier depths
 };
 
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 4;
+constexpr int kScanTile = kScanThreads * kScanPer;   // nodes per tile of the split-flag scan
+
 struct LevelArgs {
     const NodeRec *nodes;
     const int32_t *list;
@@ -332,6 +336,7 @@ struct LevelArgs {
     int32_t F, mtry, min_node, max_depth, depth;
     uint32_t seed_lo, seed_hi;
     SplitRes *res;
+    uint32_t *tile_splits;      // per tile of kScanTile nodes: nodes that split (zero on entry)
     const uint32_t *depth_ptr;  // when set, the depth is read here (a graph replays one level body)
 };
 
@@ -535,6 +540,7 @@ __device__ __forceinline__ void small_node(const LevelArgs &a, const RT *__restr
         sr.thr_bits = __float_as_uint(a.vals[(size_t)best.f * (size_t)a.N + best.r]);
         sr.nL = best.nL; sr.lenL = lenL; sr.pad = 0u; sr.v = best.SL;
         a.res[j] = sr;
+        atomicAdd(&a.tile_splits[(uint32_t)j / (uint32_t)kScanTile], 1u);
     }
 }
 
@@ -830,6 +836,7 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
         sr.thr_bits = __float_as_uint(a.vals[(size_t)win.f * (size_t)a.N + win.r]);
         sr.nL = win.nL; sr.lenL = lenL; sr.pad = 0u; sr.v = win.SL;
         a.res[j] = sr;
+        atomicAdd(&a.tile_splits[(uint32_t)j / (uint32_t)kScanTile], 1u);
     }
 }
 
@@ -845,28 +852,8 @@ __global__ void __launch_bounds__(kBigThreads, kBigCtasPerSm) level_big_kernel(L
 }
 
 // ------------------------------------------------------------------------------------------
-// exclusive scan of the split flags (three passes, 4096 flags per block)
+// exclusive scan of the split flags (tiles of kScanTile flags)
 // ------------------------------------------------------------------------------------------
-constexpr int kScanThreads = 1024;
-constexpr int kScanPer = 4;
-constexpr int kScanTile = kScanThreads * kScanPer;
-
-__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const SplitRes *res, const LevelCounts *cnt,
-                                                                   uint32_t *block_sums)
-{
-    __shared__ uint32_t warp_tmp[32];
-    const int n = (int)cnt->C;
-    const int ntiles = (n + kScanTile - 1) / kScanTile;
-    for (int b = blockIdx.x; b < ntiles; b += gridDim.x) {
-        const int base = b * kScanTile + threadIdx.x * kScanPer;
-        uint32_t c = 0;
-#pragma unroll
-        for (int k = 0; k < kScanPer; ++k) c += (base + k < n && res[base + k].feature >= 0) ? 1u : 0u;
-        uint32_t tot;
-        block_incl_scan(c, warp_tmp, tot);
-        if (threadIdx.x == 0) block_sums[b] = tot;
-    }
-}
 
 // exclusive scan of nblocks block sums (nblocks from the count, or given when cnt is null)
 __global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(uint32_t *block_sums, int nblocks,
@@ -886,7 +873,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(uint32_t *blo
     if (threadIdx.x == 0) block_sums[nblocks] = carry;
 }
 
-// Writes the exclusive scan of the split flags (tile totals from scan_reduce_kernel). Every CTA
+// Writes the exclusive scan of the split flags (tile totals counted by the level kernels). Every CTA
 // adds up the totals of the tiles before its own (a few hundred at most per depth), CTA 0 also
 // writes the grand total at [n] and clears the list counts for the next depth (the level
 // kernels that read them have finished; finalize_kernel refills them).
@@ -983,6 +970,7 @@ struct FinalArgs {
     uint32_t *next_tree_off;       // T + 1: first node of each tree at the next depth
     int T;
     uint32_t *done;                // CTAs finished (zero on entry, left zero)
+    uint32_t *tile_splits;         // the level kernels' split counts per tile, cleared for the next depth
 };
 
 __device__ __forceinline__ void push_list(int32_t *list, uint32_t *counter, bool want, int32_t value)
@@ -1076,6 +1064,13 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinalArgs a)
         if (t < a.T) a.tree_base[t] += a.tree_off[t + 1] - a.tree_off[t];
         a.next_tree_off[t] = 2u * a.excl[a.tree_off[t]];
     }
+    {
+        // this depth's tiles and the next depth's start from zero
+        const uint32_t c = a.cnt->C, cn = 2u * a.excl[c];
+        const uint32_t nt = (max(c, cn) + (uint32_t)kScanTile - 1u) / (uint32_t)kScanTile;
+        for (uint32_t b = threadIdx.x; b < nt; b += blockDim.x) a.tile_splits[b] = 0u;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         const uint32_t c = a.cnt->C;
         a.cnt->packed_off += c;
@@ -1460,6 +1455,9 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         }
         nodes_cur = nc; nodes_nxt = nn; res = nr; excl = ne; block_sums = nbs; small_a = ns; big_a = nb;
         node_cap = cap;
+        // the level kernels count splits per tile into block_sums: zero before the next depth
+        const cudaError_t e2 = cudaMemsetAsync(nbs, 0, sizeof(uint32_t) * (cap / kScanTile + 2), s);
+        if (e2 != cudaSuccess) return cuda_fail(e2, "growing level tables");
         return AIWCRF_OK;
     };
     if ((rc = grow_tables((size_t)std::max<int64_t>(T, 1024), 0)) != AIWCRF_OK) return rc;
@@ -1589,6 +1587,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         for (int k = 0; k < chunk; ++k, ++depth) {
             const int64_t Cb = bound(k);                        // bound on this depth's nodes
             la.nodes = nodes_cur; la.rows_in = rin; la.rows_out = rout; la.depth = depth; la.res = res;
+            la.tile_splits = block_sums;
             if (fork) {
                 AIWCRF_CUDA(cudaEventRecord(fk.ev_fork, s));
                 AIWCRF_CUDA(cudaStreamWaitEvent(fk.side, fk.ev_fork, 0));
@@ -1620,9 +1619,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
             }
             const unsigned sgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + kScanTile - 1) / kScanTile, std::min<int64_t>(2, cps) * dev_sms));
             prof_begin(s, kProfScan);
-            scan_reduce_kernel<<<sgrid, kScanThreads, 0, s>>>(res, d_cnt, block_sums);
             scan_write_kernel<<<sgrid, kScanThreads, 0, s>>>(res, d_cnt, block_sums, excl);
-            count_launches(1);
             AIWCRF_LAUNCH_CHECK("scan kernels");
             prof_end(s, kProfScan);
 
@@ -1630,7 +1627,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
             fa.nodes = nodes_cur; fa.res = res; fa.excl = excl; fa.tree_off = tree_off; fa.tree_base = tree_base;
             fa.cnt = d_cnt; fa.next = nodes_nxt; fa.small_list = small_a; fa.big_list = big_a;
             fa.packed = packed; fa.stats = d_stats;
-            fa.next_tree_off = tree_off_nxt; fa.T = (int)T; fa.done = d_done;
+            fa.next_tree_off = tree_off_nxt; fa.T = (int)T; fa.done = d_done; fa.tile_splits = block_sums;
             const unsigned fgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + 255) / 256, (cps == 3 ? 8 : cps) * dev_sms));
             prof_begin(s, kProfFinalize);
             finalize_kernel<<<fgrid, 256, 0, s>>>(fa);
@@ -1822,6 +1819,7 @@ int plan_bootstrap(FitPlan &P, cudaStream_t s)
 {
     level_counts_init_kernel<<<1, 32, 0, s>>>(P.d_cnt, (uint32_t)P.T);
     AIWCRF_LAUNCH_CHECK("level_counts_init_kernel");
+    AIWCRF_CUDA(cudaMemsetAsync(P.block_sums, 0, sizeof(uint32_t) * ((size_t)P.C_max / kScanTile + 2), s));
     BootArgs ba;
     ba.tree_pool_off = P.d_pool_off; ba.tree_pool_len = P.d_pool_len; ba.tree_rng = P.d_rng;
     ba.sub_rows = P.d_sub_rows; ba.y = P.dy; ba.N = P.N; ba.grp_off = P.grp_off; ba.grp_rows = P.vA;
@@ -1853,7 +1851,7 @@ int plan_level(FitPlan &P, cudaStream_t s, cudaStream_t side, cudaEvent_t ev_for
     la.tree_rng = P.d_rng; la.F = P.F; la.mtry = P.p.mtry; la.min_node = P.p.min_node_size;
     la.max_depth = P.p.max_depth; la.seed_lo = (uint32_t)P.p.seed; la.seed_hi = (uint32_t)(P.p.seed >> 32);
     la.depth = 0; la.depth_ptr = &P.d_cnt->levels;
-    la.nodes = nodes_in; la.rows_in = rin; la.rows_out = rout; la.res = P.res;
+    la.nodes = nodes_in; la.rows_in = rin; la.rows_out = rout; la.res = P.res; la.tile_splits = P.block_sums;
     const int bin_cap = big_bin_cap(P.p.mtry, P.F, P.max_card), big_smem = bin_cap * 14;
     la.list = P.big_l; la.list_n = &P.d_cnt->n_big;
     const unsigned gbig = (unsigned)(P.cps_big * P.sms), gsmall = (unsigned)(P.cps_small * P.sms);
@@ -1869,15 +1867,13 @@ int plan_level(FitPlan &P, cudaStream_t s, cudaStream_t side, cudaEvent_t ev_for
     AIWCRF_CUDA(cudaEventRecord(ev_join, side));
     AIWCRF_CUDA(cudaStreamWaitEvent(s, ev_join, 0));
     const unsigned sgrid = (unsigned)(2 * P.sms);
-    scan_reduce_kernel<<<sgrid, kScanThreads, 0, s>>>(P.res, P.d_cnt, P.block_sums);
     scan_write_kernel<<<sgrid, kScanThreads, 0, s>>>(P.res, P.d_cnt, P.block_sums, P.excl);
-    count_launches(1);
     AIWCRF_LAUNCH_CHECK("scan kernels");
     FinalArgs fa;
     fa.nodes = nodes_in; fa.res = P.res; fa.excl = P.excl; fa.tree_off = toff_in; fa.tree_base = P.tree_base;
     fa.cnt = P.d_cnt; fa.next = nodes_out; fa.small_list = P.small_l; fa.big_list = P.big_l;
     fa.packed = P.packed; fa.stats = P.d_stats;
-    fa.next_tree_off = toff_out; fa.T = (int)P.T; fa.done = P.d_done;
+    fa.next_tree_off = toff_out; fa.T = (int)P.T; fa.done = P.d_done; fa.tile_splits = P.block_sums;
     finalize_kernel<<<(unsigned)(8 * P.sms), 256, 0, s>>>(fa);
     AIWCRF_LAUNCH_CHECK("finalize_kernel");
     return AIWCRF_OK;
