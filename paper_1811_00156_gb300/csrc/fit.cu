@@ -189,7 +189,7 @@ struct BootArgs {
     int64_t row_cap;
     NodeRec *root;
     int32_t *small_list, *big_list;
-    uint32_t *counters;             // [0] small count, [1] big count
+    uint32_t *counters;             // [0] small count, [1] big count (depth 0's list counts)
     uint32_t *err;
     uint32_t *inbag;                // per tree ceil(N / 32) words: bit r set = row r drawn (or null)
     int64_t inbag_words;
@@ -310,21 +310,19 @@ __global__ void __launch_bounds__(kBootThreads) bootstrap_kernel(BootArgs a)
 // device memory, so the host can enqueue several depths without waiting for their results.
 // ------------------------------------------------------------------------------------------
 struct LevelCounts {
-    uint32_t n_small;             // nodes of the current depth searched by a warp
-    uint32_t n_big;               // nodes of the current depth searched by a CTA
+    uint32_t n_list[2][2];        // by depth parity: [0] nodes searched by a warp, [1] by a CTA
     uint32_t C;                   // nodes of the current depth
     uint32_t levels;              // depths that held nodes so far
     unsigned long long packed_off;    // finished nodes of the earlier depths
 };
 
 constexpr int kScanThreads = 1024;
-constexpr int kScanPer = 4;
-constexpr int kScanTile = kScanThreads * kScanPer;   // nodes per tile of the split-flag scan
+constexpr int kScanTile = kScanThreads;   // nodes per tile of the split-flag scan (one per thread)
 
 struct LevelArgs {
     const NodeRec *nodes;
     const int32_t *list;
-    const uint32_t *list_n;       // n_small or n_big in LevelCounts
+    const uint32_t *list_n;       // the depth's warp or CTA list count in LevelCounts
     const Entry *rows_in;
     Entry *rows_out;
     int64_t row_cap;
@@ -852,15 +850,13 @@ __global__ void __launch_bounds__(kBigThreads, kBigCtasPerSm) level_big_kernel(L
 }
 
 // ------------------------------------------------------------------------------------------
-// exclusive scan of the split flags (tiles of kScanTile flags)
+// exclusive scans of flag arrays (the grouping of identical feature vectors)
 // ------------------------------------------------------------------------------------------
 
-// exclusive scan of nblocks block sums (nblocks from the count, or given when cnt is null)
-__global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(uint32_t *block_sums, int nblocks,
-                                                                   const LevelCounts *cnt = nullptr)
+// exclusive scan of nblocks block sums, the grand total at [nblocks]
+__global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(uint32_t *block_sums, int nblocks)
 {
     __shared__ uint32_t warp_tmp[32];
-    if (cnt) nblocks = (int)((cnt->C + kScanTile - 1) / kScanTile);
     uint32_t carry = 0;
     for (int b0 = 0; b0 < nblocks; b0 += kScanThreads) {
         const int b = b0 + threadIdx.x;
@@ -873,58 +869,17 @@ __global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(uint32_t *blo
     if (threadIdx.x == 0) block_sums[nblocks] = carry;
 }
 
-// Writes the exclusive scan of the split flags (tile totals counted by the level kernels). Every CTA
-// adds up the totals of the tiles before its own (a few hundred at most per depth), CTA 0 also
-// writes the grand total at [n] and clears the list counts for the next depth (the level
-// kernels that read them have finished; finalize_kernel refills them).
-__global__ void __launch_bounds__(kScanThreads) scan_write_kernel(const SplitRes *res, LevelCounts *cnt,
-                                                                  const uint32_t *block_sums, uint32_t *excl)
-{
-    __shared__ uint32_t warp_tmp[32];
-    const int n = (int)cnt->C;
-    const int ntiles = (n + kScanTile - 1) / kScanTile;
-    for (int b = blockIdx.x; b < ntiles; b += gridDim.x) {
-        uint32_t part = 0;
-        for (int i = threadIdx.x; i < b; i += kScanThreads) part += block_sums[i];
-        uint32_t prefix;
-        block_incl_scan(part, warp_tmp, prefix);
-        const int base = b * kScanTile + threadIdx.x * kScanPer;
-        uint32_t fl[kScanPer], c = 0;
-#pragma unroll
-        for (int k = 0; k < kScanPer; ++k) {
-            fl[k] = (base + k < n && res[base + k].feature >= 0) ? 1u : 0u;
-            c += fl[k];
-        }
-        uint32_t tot;
-        const uint32_t incl = block_incl_scan(c, warp_tmp, tot);
-        uint32_t run = prefix + incl - c;
-#pragma unroll
-        for (int k = 0; k < kScanPer; ++k) {
-            if (base + k < n) excl[base + k] = run;
-            run += fl[k];
-        }
-    }
-    if (blockIdx.x == 0) {
-        uint32_t part = 0;
-        for (int i = threadIdx.x; i < ntiles; i += kScanThreads) part += block_sums[i];
-        uint32_t total;
-        block_incl_scan(part, warp_tmp, total);
-        if (threadIdx.x == 0) {
-            excl[n] = total;
-            cnt->n_small = 0u;
-            cnt->n_big = 0u;
-        }
-    }
-}
+// exclusive scan of a u32 flag array in three passes (4 flags per thread, tiles of kFlagTile)
+constexpr int kFlagPer = 4;
+constexpr int kFlagTile = kScanThreads * kFlagPer;
 
-// the same three passes over a u32 flag array
 __global__ void __launch_bounds__(kScanThreads) flag_scan_reduce_kernel(const uint32_t *flags, int64_t n, uint32_t *block_sums)
 {
     __shared__ uint32_t warp_tmp[32];
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+    const int64_t base = (int64_t)blockIdx.x * kFlagTile + (int64_t)threadIdx.x * kFlagPer;
     uint32_t c = 0;
 #pragma unroll
-    for (int k = 0; k < kScanPer; ++k) c += base + k < n ? flags[base + k] : 0u;
+    for (int k = 0; k < kFlagPer; ++k) c += base + k < n ? flags[base + k] : 0u;
     uint32_t tot;
     block_incl_scan(c, warp_tmp, tot);
     if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
@@ -935,10 +890,10 @@ __global__ void __launch_bounds__(kScanThreads) flag_scan_write_kernel(const uin
                                                                        uint32_t *excl)
 {
     __shared__ uint32_t warp_tmp[32];
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
-    uint32_t fl[kScanPer], c = 0;
+    const int64_t base = (int64_t)blockIdx.x * kFlagTile + (int64_t)threadIdx.x * kFlagPer;
+    uint32_t fl[kFlagPer], c = 0;
 #pragma unroll
-    for (int k = 0; k < kScanPer; ++k) {
+    for (int k = 0; k < kFlagPer; ++k) {
         fl[k] = base + k < n ? flags[base + k] : 0u;
         c += fl[k];
     }
@@ -946,7 +901,7 @@ __global__ void __launch_bounds__(kScanThreads) flag_scan_write_kernel(const uin
     const uint32_t incl = block_incl_scan(c, warp_tmp, tot);
     uint32_t run = block_sums[blockIdx.x] + incl - c;
 #pragma unroll
-    for (int k = 0; k < kScanPer; ++k) {
+    for (int k = 0; k < kFlagPer; ++k) {
         if (base + k < n) excl[base + k] = run;
         run += fl[k];
     }
@@ -959,10 +914,9 @@ __global__ void __launch_bounds__(kScanThreads) flag_scan_write_kernel(const uin
 struct FinalArgs {
     const NodeRec *nodes;
     const SplitRes *res;
-    const uint32_t *excl;          // n + 1
     const uint32_t *tree_off;      // T + 1: first node of each tree at this depth
     uint32_t *tree_base;           // T: nodes of each tree at lower depths
-    LevelCounts *cnt;              // C and packed_off of this depth; n_small / n_big of the next
+    LevelCounts *cnt;              // C and packed_off of this depth; list counts of the next
     NodeRec *next;
     int32_t *small_list, *big_list;
     PackedRec *packed;             // all finished nodes; this depth starts at cnt->packed_off
@@ -971,6 +925,8 @@ struct FinalArgs {
     int T;
     uint32_t *done;                // CTAs finished (zero on entry, left zero)
     uint32_t *tile_splits;         // the level kernels' split counts per tile, cleared for the next depth
+    uint32_t *excl_out;            // n + 1: exclusive split count of every node (written here)
+    int parity;                    // this depth's parity: its list counts, cleared at the end
 };
 
 __device__ __forceinline__ void push_list(int32_t *list, uint32_t *counter, bool want, int32_t value)
@@ -985,24 +941,61 @@ __device__ __forceinline__ void push_list(int32_t *list, uint32_t *counter, bool
     if (want) list[base + __popc(b & lanemask_lt())] = value;
 }
 
-__global__ void __launch_bounds__(256) finalize_kernel(FinalArgs a)
+// One depth's close, one node per thread, tiles of kScanTile nodes strided over the CTAs:
+//  - the exclusive scan of the split flags: the tile's base from the level kernels' per-tile
+//    split counts, then a block scan; written to excl_out;
+//  - every node finished: its packed record, its children and their list entries in the next
+//    depth's parity. A tree's split count before its first node comes from this tile's scan,
+//    or, for the one tree that reaches into the tile from an earlier tile, from that tile's base
+//    and a count of its flags before the tree's first node;
+//  - the last CTA (atomic counter) advances the per-tree bookkeeping and the level counts, and
+//    clears this depth's tile and list counts.
+__global__ void __launch_bounds__(kScanThreads) finalize_kernel(FinalArgs a)
 {
-    __shared__ unsigned long long red[6][8];
+    __shared__ uint32_t sx[kScanTile];
+    __shared__ uint32_t warp_tmp[32];
+    __shared__ unsigned long long red[6][kScanThreads / 32];
+    __shared__ int last;
     const uint32_t n = a.cnt->C;
-    PackedRec *packed = a.packed + a.cnt->packed_off;
+    const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t *n_next = a.cnt->n_list[a.parity ^ 1];
     unsigned long long v[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
-    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {   // block-uniform
-        const uint32_t jj = base + threadIdx.x;
+    PackedRec *packed = a.packed + a.cnt->packed_off;
+    for (uint32_t b = blockIdx.x; b < ntiles; b += gridDim.x) {     // block-uniform
+        const uint32_t t0 = b * (uint32_t)kScanTile;
+        uint32_t part = 0, base;
+        for (uint32_t i = (uint32_t)tid; i < b; i += kScanThreads) part += a.tile_splits[i];
+        block_incl_scan(part, warp_tmp, base);          // splits before the tile
+        const uint32_t jj = t0 + (uint32_t)tid;
         const bool active = jj < n;
-        const uint32_t j = active ? jj : 0u;
+        const uint32_t j = active ? jj : t0;
         const NodeRec nd = a.nodes[j];
         const SplitRes r = a.res[j];
         const bool split = active && r.feature >= 0;
+        uint32_t tot;
+        const uint32_t g = base + block_incl_scan(split ? 1u : 0u, warp_tmp, tot) - (split ? 1u : 0u);
+        sx[tid] = g;
+        if (active) a.excl_out[j] = g;
+        // the tree of the tile's first node: its split count before its first node
+        const uint32_t tf = a.nodes[t0].tree;
+        const uint32_t ff = a.tree_off[tf];
+        uint32_t span = 0u;
+        if (ff < t0) {                                  // block-uniform
+            const uint32_t fb = ff / (uint32_t)kScanTile, fs = fb * (uint32_t)kScanTile;
+            uint32_t p2 = 0, before;
+            for (uint32_t i = (uint32_t)tid; i < fb; i += kScanThreads) p2 += a.tile_splits[i];
+            block_incl_scan(p2, warp_tmp, before);
+            const uint32_t k = fs + (uint32_t)tid;
+            uint32_t cnt_k;
+            block_incl_scan((k < ff && a.res[k].feature >= 0) ? 1u : 0u, warp_tmp, cnt_k);
+            span = before + cnt_k;
+        }
+        __syncthreads();
         const uint32_t t = nd.tree;
         const uint32_t first = a.tree_off[t];
         const uint32_t cnt_t = a.tree_off[t + 1] - first;
-        const uint32_t g = a.excl[j];
-        const uint32_t local = g - a.excl[first];
+        const uint32_t local = g - (first >= t0 ? sx[first - t0] : span);
         const uint32_t base_t = a.tree_base[t];
         NodeRec L, Rn;
         if (active) {
@@ -1020,10 +1013,10 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinalArgs a)
             a.next[2u * g] = L;
             a.next[2u * g + 1u] = Rn;
         }
-        push_list(a.small_list, &a.cnt->n_small, split && L.len <= (uint32_t)kSmallNodeRows, (int32_t)(2u * g));
-        push_list(a.big_list, &a.cnt->n_big, split && L.len > (uint32_t)kSmallNodeRows, (int32_t)(2u * g));
-        push_list(a.small_list, &a.cnt->n_small, split && Rn.len <= (uint32_t)kSmallNodeRows, (int32_t)(2u * g + 1u));
-        push_list(a.big_list, &a.cnt->n_big, split && Rn.len > (uint32_t)kSmallNodeRows, (int32_t)(2u * g + 1u));
+        push_list(a.small_list, &n_next[0], split && L.len <= (uint32_t)kSmallNodeRows, (int32_t)(2u * g));
+        push_list(a.big_list, &n_next[1], split && L.len > (uint32_t)kSmallNodeRows, (int32_t)(2u * g));
+        push_list(a.small_list, &n_next[0], split && Rn.len <= (uint32_t)kSmallNodeRows, (int32_t)(2u * g + 1u));
+        push_list(a.big_list, &n_next[1], split && Rn.len > (uint32_t)kSmallNodeRows, (int32_t)(2u * g + 1u));
 
         const bool evald = active && r.feature != -2;
         const bool small = nd.len <= (uint32_t)kSmallNodeRows;
@@ -1033,49 +1026,48 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinalArgs a)
         v[3] += (evald && small) ? 1u : 0u;
         v[4] += (evald && small) ? nd.len : 0u;
         v[5] += (split && small) ? nd.len : 0u;
+        __syncthreads();                                // sx is rewritten by the next tile
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], o);
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < 6; ++k) red[k][warp] = v[k];
     }
     __syncthreads();
-    if (threadIdx.x < 6) {
+    if (tid < 6) {
         unsigned long long sum = 0;
-        for (int w = 0; w < 8; ++w) sum += red[threadIdx.x][w];
-        if (sum) atomicAdd(&a.stats->entries_evaluated + threadIdx.x, sum);   // GrowStats field order
+        for (int w = 0; w < kScanThreads / 32; ++w) sum += red[tid][w];
+        if (sum) atomicAdd(&a.stats->entries_evaluated + tid, sum);   // GrowStats field order
     }
-    // the last CTA to finish advances the per-tree bookkeeping and the level counts
-    __shared__ int last;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         __threadfence();
         last = atomicAdd(a.done, 1u) == gridDim.x - 1u;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int t = threadIdx.x; t <= a.T; t += blockDim.x) {
-        if (t < a.T) a.tree_base[t] += a.tree_off[t + 1] - a.tree_off[t];
-        a.next_tree_off[t] = 2u * a.excl[a.tree_off[t]];
+    uint32_t part = 0, total;
+    for (uint32_t i = (uint32_t)tid; i < ntiles; i += kScanThreads) part += a.tile_splits[i];
+    block_incl_scan(part, warp_tmp, total);
+    for (int t = tid; t <= a.T; t += kScanThreads) {
+        const uint32_t o = a.tree_off[t];
+        if (t < a.T) a.tree_base[t] += a.tree_off[t + 1] - o;
+        a.next_tree_off[t] = 2u * (o < n ? a.excl_out[o] : total);
     }
-    {
-        // this depth's tiles and the next depth's start from zero
-        const uint32_t c = a.cnt->C, cn = 2u * a.excl[c];
-        const uint32_t nt = (max(c, cn) + (uint32_t)kScanTile - 1u) / (uint32_t)kScanTile;
-        for (uint32_t b = threadIdx.x; b < nt; b += blockDim.x) a.tile_splits[b] = 0u;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const uint32_t c = a.cnt->C;
-        a.cnt->packed_off += c;
-        a.cnt->levels += c > 0 ? 1u : 0u;
-        a.cnt->C = 2u * a.excl[c];
+    // this depth's and the next depth's tiles, and this depth's list counts, start from zero
+    const uint32_t nt = (max(n, 2u * total) + (uint32_t)kScanTile - 1u) / (uint32_t)kScanTile;
+    for (uint32_t i = (uint32_t)tid; i < nt; i += kScanThreads) a.tile_splits[i] = 0u;
+    if (tid == 0) {
+        a.cnt->n_list[a.parity][0] = 0u;
+        a.cnt->n_list[a.parity][1] = 0u;
+        a.cnt->packed_off += n;
+        a.cnt->levels += n > 0 ? 1u : 0u;
+        a.cnt->C = 2u * total;
         *a.done = 0u;
     }
 }
@@ -1388,7 +1380,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         // group starts (flags in kB), their exclusive scan (in vB), offsets
         if (rank8) group_flags_kernel<uint8_t><<<rb, 256, 0, s>>>((const uint8_t *)d_Rr, N, F, kA, vA, kB);
         else group_flags_kernel<uint16_t><<<rb, 256, 0, s>>>((const uint16_t *)d_Rr, N, F, kA, vA, kB);
-        const int gblocks = (int)((N + kScanTile - 1) / kScanTile);
+        const int gblocks = (int)((N + kFlagTile - 1) / kFlagTile);
         flag_scan_reduce_kernel<<<gblocks, kScanThreads, 0, s>>>(kB, N, hist);
         scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(hist, gblocks);
         flag_scan_write_kernel<<<gblocks, kScanThreads, 0, s>>>(kB, N, hist, gblocks, vB);
@@ -1485,7 +1477,8 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     }
     {
         LevelCounts c0;
-        c0.n_small = 0u; c0.n_big = 0u; c0.C = (uint32_t)T; c0.levels = 0u; c0.packed_off = 0ull;
+        c0.n_list[0][0] = c0.n_list[0][1] = c0.n_list[1][0] = c0.n_list[1][1] = 0u;
+        c0.C = (uint32_t)T; c0.levels = 0u; c0.packed_off = 0ull;
         AIWCRF_CUDA(cudaMemcpyAsync(d_cnt, &c0, sizeof(LevelCounts), cudaMemcpyHostToDevice, s));
     }
 
@@ -1508,7 +1501,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         ba.bootstrap = p.bootstrap; ba.gcnt = gcnt; ba.gcnt_stride = gstride;
         ba.smem_words = gcnt ? 0 : (int)words;
         ba.rows_out = rows_a; ba.row_cap = row_cap; ba.root = nodes_cur;
-        ba.small_list = small_a; ba.big_list = big_a; ba.counters = &d_cnt->n_small; ba.err = d_err;
+        ba.small_list = small_a; ba.big_list = big_a; ba.counters = d_cnt->n_list[0]; ba.err = d_err;
         ba.inbag = d_inbag; ba.inbag_words = inbag_words;
         ba.G_ptr = nullptr;
         prof_begin(s, kProfBoot);
@@ -1593,7 +1586,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
                 AIWCRF_CUDA(cudaStreamWaitEvent(fk.side, fk.ev_fork, 0));
             }
             {
-                la.list = big_a; la.list_n = &d_cnt->n_big;
+                la.list = big_a; la.list_n = &d_cnt->n_list[depth & 1][1];
                 const int64_t cps_big = p.ctas_per_sm > 0 ? p.ctas_per_sm : kBigCtasPerSm;
                 const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(Cb, cps_big * dev_sms));
                 prof_begin(s, kProfLevelBig);
@@ -1603,7 +1596,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
                 prof_end(s, kProfLevelBig);
             }
             {
-                la.list = small_a; la.list_n = &d_cnt->n_small;
+                la.list = small_a; la.list_n = &d_cnt->n_list[depth & 1][0];
                 const int64_t wpb = kSmallThreads / 32;
                 const int64_t cps_small = p.ctas_per_sm > 0 ? p.ctas_per_sm : kSmallCtasPerSm;
                 const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + wpb - 1) / wpb, cps_small * dev_sms));
@@ -1617,20 +1610,16 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
                 AIWCRF_CUDA(cudaEventRecord(fk.ev_join, fk.side));
                 AIWCRF_CUDA(cudaStreamWaitEvent(s, fk.ev_join, 0));
             }
-            const unsigned sgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + kScanTile - 1) / kScanTile, std::min<int64_t>(2, cps) * dev_sms));
-            prof_begin(s, kProfScan);
-            scan_write_kernel<<<sgrid, kScanThreads, 0, s>>>(res, d_cnt, block_sums, excl);
-            AIWCRF_LAUNCH_CHECK("scan kernels");
-            prof_end(s, kProfScan);
-
             FinalArgs fa;
-            fa.nodes = nodes_cur; fa.res = res; fa.excl = excl; fa.tree_off = tree_off; fa.tree_base = tree_base;
+            fa.nodes = nodes_cur; fa.res = res; fa.excl_out = excl; fa.tree_off = tree_off; fa.tree_base = tree_base;
             fa.cnt = d_cnt; fa.next = nodes_nxt; fa.small_list = small_a; fa.big_list = big_a;
             fa.packed = packed; fa.stats = d_stats;
             fa.next_tree_off = tree_off_nxt; fa.T = (int)T; fa.done = d_done; fa.tile_splits = block_sums;
-            const unsigned fgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + 255) / 256, (cps == 3 ? 8 : cps) * dev_sms));
+            fa.parity = depth & 1;
+            // tiles of the depth's (bounded) node count, at most one (1,024-thread) CTA per SM
+            const unsigned fgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + kScanTile - 1) / kScanTile, (int64_t)dev_sms));
             prof_begin(s, kProfFinalize);
-            finalize_kernel<<<fgrid, 256, 0, s>>>(fa);
+            finalize_kernel<<<fgrid, kScanThreads, 0, s>>>(fa);
             AIWCRF_LAUNCH_CHECK("finalize_kernel");
             prof_end(s, kProfFinalize);
 
@@ -1677,7 +1666,8 @@ __global__ void plan_check_kernel(const uint32_t *card, int F, uint32_t max_card
 __global__ void level_counts_init_kernel(LevelCounts *cnt, uint32_t T)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
-        cnt->n_small = 0u; cnt->n_big = 0u; cnt->C = T; cnt->levels = 0u; cnt->packed_off = 0ull;
+        cnt->n_list[0][0] = cnt->n_list[0][1] = cnt->n_list[1][0] = cnt->n_list[1][1] = 0u;
+        cnt->C = T; cnt->levels = 0u; cnt->packed_off = 0ull;
     }
 }
 
@@ -1800,7 +1790,7 @@ int plan_phase_a(FitPlan &P, cudaStream_t s, bool probe)
     if ((rc = radix_sort_segments(P.kA, P.vA, P.kB, P.vB, N, 1, N, P.hist, s)) != AIWCRF_OK) return rc;
     if (P.rank8) group_flags_kernel<uint8_t><<<rb, 256, 0, s>>>((const uint8_t *)P.d_Rr, N, F, P.kA, P.vA, P.kB);
     else group_flags_kernel<uint16_t><<<rb, 256, 0, s>>>((const uint16_t *)P.d_Rr, N, F, P.kA, P.vA, P.kB);
-    const int gblocks = (int)((N + kScanTile - 1) / kScanTile);
+    const int gblocks = (int)((N + kFlagTile - 1) / kFlagTile);
     flag_scan_reduce_kernel<<<gblocks, kScanThreads, 0, s>>>(P.kB, N, P.hist);
     scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(P.hist, gblocks);
     flag_scan_write_kernel<<<gblocks, kScanThreads, 0, s>>>(P.kB, N, P.hist, gblocks, P.vB);
@@ -1828,7 +1818,7 @@ int plan_bootstrap(FitPlan &P, cudaStream_t s)
     ba.bootstrap = P.p.bootstrap; ba.gcnt = P.gcnt; ba.gcnt_stride = P.gstride;
     ba.smem_words = P.gcnt ? 0 : (int)((P.N + 3) / 4);
     ba.rows_out = P.rows_a; ba.row_cap = P.row_cap; ba.root = P.nodes_a;
-    ba.small_list = P.small_l; ba.big_list = P.big_l; ba.counters = &P.d_cnt->n_small; ba.err = P.d_err;
+    ba.small_list = P.small_l; ba.big_list = P.big_l; ba.counters = P.d_cnt->n_list[0]; ba.err = P.d_err;
     ba.inbag = P.d_inbag; ba.inbag_words = P.inbag_words;
     bootstrap_kernel<<<(unsigned)P.T, kBootThreads, P.boot_smem, s>>>(ba);
     AIWCRF_LAUNCH_CHECK("bootstrap_kernel");
@@ -1843,7 +1833,7 @@ int plan_bootstrap(FitPlan &P, cudaStream_t s)
 // device's level counter holds; fixed grids (the kernels stride over the device's counts)
 // one depth; the small-node kernel is captured on `side` (forked and joined through the two
 // events), so the graph runs the depth's two level kernels as parallel branches
-int plan_level(FitPlan &P, cudaStream_t s, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join,
+int plan_level(FitPlan &P, cudaStream_t s, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join, int parity,
                NodeRec *nodes_in, NodeRec *nodes_out, Entry *rin, Entry *rout, uint32_t *toff_in, uint32_t *toff_out)
 {
     LevelArgs la;
@@ -1853,28 +1843,26 @@ int plan_level(FitPlan &P, cudaStream_t s, cudaStream_t side, cudaEvent_t ev_for
     la.depth = 0; la.depth_ptr = &P.d_cnt->levels;
     la.nodes = nodes_in; la.rows_in = rin; la.rows_out = rout; la.res = P.res; la.tile_splits = P.block_sums;
     const int bin_cap = big_bin_cap(P.p.mtry, P.F, P.max_card), big_smem = bin_cap * 14;
-    la.list = P.big_l; la.list_n = &P.d_cnt->n_big;
+    la.list = P.big_l; la.list_n = &P.d_cnt->n_list[parity][1];
     const unsigned gbig = (unsigned)(P.cps_big * P.sms), gsmall = (unsigned)(P.cps_small * P.sms);
     AIWCRF_CUDA(cudaEventRecord(ev_fork, s));
     AIWCRF_CUDA(cudaStreamWaitEvent(side, ev_fork, 0));
     if (P.rank8) level_big_kernel<uint8_t><<<gbig, kBigThreads, big_smem, s>>>(la, bin_cap);
     else level_big_kernel<uint16_t><<<gbig, kBigThreads, big_smem, s>>>(la, bin_cap);
     AIWCRF_LAUNCH_CHECK("level_big_kernel");
-    la.list = P.small_l; la.list_n = &P.d_cnt->n_small;
+    la.list = P.small_l; la.list_n = &P.d_cnt->n_list[parity][0];
     if (P.rank8) level_small_kernel<uint8_t><<<gsmall, kSmallThreads, 0, side>>>(la);
     else level_small_kernel<uint16_t><<<gsmall, kSmallThreads, 0, side>>>(la);
     AIWCRF_LAUNCH_CHECK("level_small_kernel");
     AIWCRF_CUDA(cudaEventRecord(ev_join, side));
     AIWCRF_CUDA(cudaStreamWaitEvent(s, ev_join, 0));
-    const unsigned sgrid = (unsigned)(2 * P.sms);
-    scan_write_kernel<<<sgrid, kScanThreads, 0, s>>>(P.res, P.d_cnt, P.block_sums, P.excl);
-    AIWCRF_LAUNCH_CHECK("scan kernels");
     FinalArgs fa;
-    fa.nodes = nodes_in; fa.res = P.res; fa.excl = P.excl; fa.tree_off = toff_in; fa.tree_base = P.tree_base;
+    fa.nodes = nodes_in; fa.res = P.res; fa.excl_out = P.excl; fa.tree_off = toff_in; fa.tree_base = P.tree_base;
     fa.cnt = P.d_cnt; fa.next = nodes_out; fa.small_list = P.small_l; fa.big_list = P.big_l;
     fa.packed = P.packed; fa.stats = P.d_stats;
     fa.next_tree_off = toff_out; fa.T = (int)P.T; fa.done = P.d_done; fa.tile_splits = P.block_sums;
-    finalize_kernel<<<(unsigned)(8 * P.sms), 256, 0, s>>>(fa);
+    fa.parity = parity;
+    finalize_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((P.C_max + kScanTile - 1) / kScanTile, (int64_t)P.sms)), kScanThreads, 0, s>>>(fa);
     AIWCRF_LAUNCH_CHECK("finalize_kernel");
     return AIWCRF_OK;
 }
@@ -1931,9 +1919,10 @@ int plan_capture(FitPlan &P)
             rc = cuda_fail(e, "fit plan: level loop node");
         } else {
             P.prefix_launches = aiwcrf_launch_count() - l0;
-            rc = plan_level(P, bs, ss, evf, evj, P.nodes_a, P.nodes_b, P.rows_a, P.rows_b, P.toff_a, P.toff_b);
+            // the body grows an even and then an odd depth (the loop starts at depth 0)
+            rc = plan_level(P, bs, ss, evf, evj, 0, P.nodes_a, P.nodes_b, P.rows_a, P.rows_b, P.toff_a, P.toff_b);
             if (rc == AIWCRF_OK)
-                rc = plan_level(P, bs, ss, evf, evj, P.nodes_b, P.nodes_a, P.rows_b, P.rows_a, P.toff_b, P.toff_a);
+                rc = plan_level(P, bs, ss, evf, evj, 1, P.nodes_b, P.nodes_a, P.rows_b, P.rows_a, P.toff_b, P.toff_a);
             if (rc == AIWCRF_OK) {
                 level_loop_cond_kernel<<<1, 32, 0, bs>>>(h, P.d_cnt, (uint32_t)(P.row_cap + 2), P.d_err);
                 count_launches(1);
