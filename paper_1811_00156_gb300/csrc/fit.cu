@@ -317,7 +317,8 @@ struct LevelCounts {
 };
 
 constexpr int kScanThreads = 1024;
-constexpr int kScanTile = kScanThreads;   // nodes per tile of the split-flag scan (one per thread)
+constexpr int kFinThreads = 256;
+constexpr int kScanTile = kFinThreads;   // nodes per tile of the split-flag scan (one per thread)
 
 struct LevelArgs {
     const NodeRec *nodes;
@@ -950,11 +951,11 @@ __device__ __forceinline__ void push_list(int32_t *list, uint32_t *counter, bool
 //    and a count of its flags before the tree's first node;
 //  - the last CTA (atomic counter) advances the per-tree bookkeeping and the level counts, and
 //    clears this depth's tile and list counts.
-__global__ void __launch_bounds__(kScanThreads) finalize_kernel(FinalArgs a)
+__global__ void __launch_bounds__(kFinThreads) finalize_kernel(FinalArgs a)
 {
     __shared__ uint32_t sx[kScanTile];
     __shared__ uint32_t warp_tmp[32];
-    __shared__ unsigned long long red[6][kScanThreads / 32];
+    __shared__ unsigned long long red[6][kFinThreads / 32];
     __shared__ int last;
     const uint32_t n = a.cnt->C;
     const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
@@ -965,7 +966,7 @@ __global__ void __launch_bounds__(kScanThreads) finalize_kernel(FinalArgs a)
     for (uint32_t b = blockIdx.x; b < ntiles; b += gridDim.x) {     // block-uniform
         const uint32_t t0 = b * (uint32_t)kScanTile;
         uint32_t part = 0, base;
-        for (uint32_t i = (uint32_t)tid; i < b; i += kScanThreads) part += a.tile_splits[i];
+        for (uint32_t i = (uint32_t)tid; i < b; i += kFinThreads) part += a.tile_splits[i];
         block_incl_scan(part, warp_tmp, base);          // splits before the tile
         const uint32_t jj = t0 + (uint32_t)tid;
         const bool active = jj < n;
@@ -984,7 +985,7 @@ __global__ void __launch_bounds__(kScanThreads) finalize_kernel(FinalArgs a)
         if (ff < t0) {                                  // block-uniform
             const uint32_t fb = ff / (uint32_t)kScanTile, fs = fb * (uint32_t)kScanTile;
             uint32_t p2 = 0, before;
-            for (uint32_t i = (uint32_t)tid; i < fb; i += kScanThreads) p2 += a.tile_splits[i];
+            for (uint32_t i = (uint32_t)tid; i < fb; i += kFinThreads) p2 += a.tile_splits[i];
             block_incl_scan(p2, warp_tmp, before);
             const uint32_t k = fs + (uint32_t)tid;
             uint32_t cnt_k;
@@ -1040,7 +1041,7 @@ __global__ void __launch_bounds__(kScanThreads) finalize_kernel(FinalArgs a)
     __syncthreads();
     if (tid < 6) {
         unsigned long long sum = 0;
-        for (int w = 0; w < kScanThreads / 32; ++w) sum += red[tid][w];
+        for (int w = 0; w < kFinThreads / 32; ++w) sum += red[tid][w];
         if (sum) atomicAdd(&a.stats->entries_evaluated + tid, sum);   // GrowStats field order
     }
     __syncthreads();
@@ -1052,16 +1053,16 @@ __global__ void __launch_bounds__(kScanThreads) finalize_kernel(FinalArgs a)
     if (!last) return;
     __threadfence();
     uint32_t part = 0, total;
-    for (uint32_t i = (uint32_t)tid; i < ntiles; i += kScanThreads) part += a.tile_splits[i];
+    for (uint32_t i = (uint32_t)tid; i < ntiles; i += kFinThreads) part += a.tile_splits[i];
     block_incl_scan(part, warp_tmp, total);
-    for (int t = tid; t <= a.T; t += kScanThreads) {
+    for (int t = tid; t <= a.T; t += kFinThreads) {
         const uint32_t o = a.tree_off[t];
         if (t < a.T) a.tree_base[t] += a.tree_off[t + 1] - o;
         a.next_tree_off[t] = 2u * (o < n ? a.excl_out[o] : total);
     }
     // this depth's and the next depth's tiles, and this depth's list counts, start from zero
     const uint32_t nt = (max(n, 2u * total) + (uint32_t)kScanTile - 1u) / (uint32_t)kScanTile;
-    for (uint32_t i = (uint32_t)tid; i < nt; i += kScanThreads) a.tile_splits[i] = 0u;
+    for (uint32_t i = (uint32_t)tid; i < nt; i += kFinThreads) a.tile_splits[i] = 0u;
     if (tid == 0) {
         a.cnt->n_list[a.parity][0] = 0u;
         a.cnt->n_list[a.parity][1] = 0u;
@@ -1616,10 +1617,10 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
             fa.packed = packed; fa.stats = d_stats;
             fa.next_tree_off = tree_off_nxt; fa.T = (int)T; fa.done = d_done; fa.tile_splits = block_sums;
             fa.parity = depth & 1;
-            // tiles of the depth's (bounded) node count, at most one (1,024-thread) CTA per SM
-            const unsigned fgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + kScanTile - 1) / kScanTile, (int64_t)dev_sms));
+            // tiles of the depth's (bounded) node count, at most four (256-thread) CTAs per SM
+            const unsigned fgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + kScanTile - 1) / kScanTile, 4 * (int64_t)dev_sms));
             prof_begin(s, kProfFinalize);
-            finalize_kernel<<<fgrid, kScanThreads, 0, s>>>(fa);
+            finalize_kernel<<<fgrid, kFinThreads, 0, s>>>(fa);
             AIWCRF_LAUNCH_CHECK("finalize_kernel");
             prof_end(s, kProfFinalize);
 
@@ -1862,7 +1863,7 @@ int plan_level(FitPlan &P, cudaStream_t s, cudaStream_t side, cudaEvent_t ev_for
     fa.packed = P.packed; fa.stats = P.d_stats;
     fa.next_tree_off = toff_out; fa.T = (int)P.T; fa.done = P.d_done; fa.tile_splits = P.block_sums;
     fa.parity = parity;
-    finalize_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((P.C_max + kScanTile - 1) / kScanTile, (int64_t)P.sms)), kScanThreads, 0, s>>>(fa);
+    finalize_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((P.C_max + kScanTile - 1) / kScanTile, 4 * (int64_t)P.sms)), kFinThreads, 0, s>>>(fa);
     AIWCRF_LAUNCH_CHECK("finalize_kernel");
     return AIWCRF_OK;
 }
