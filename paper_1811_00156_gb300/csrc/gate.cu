@@ -1,6 +1,6 @@
 // gate.cu -- device selection through the learned surrogate, with the forest as fallback and as
-// the judge of its answers (the selection of Sec. VI, made cheaper; the paper's model is the
-// forest alone).
+// the arbiter of its uncertain answers (the selection of Sec. VI, made cheaper; the paper's
+// model is the forest alone).
 //
 // Pipeline on the caller's stream:
 //  1. expand the K kernels into K x D queries (kernel features, device id, size class);
