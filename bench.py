@@ -714,7 +714,7 @@ def oob_report(A, wl, X, forest):
             "ms": e0.elapsed_time(e1)}
 
 
-def write_traffic(csv_path: str, command: str):
+def write_traffic(csv_path: str, command: str, out_path: str | None = None) -> dict:
     """DRAM bytes (read + write) per launch of each kernel class in an ncu CSV of one step's
     launches, keyed by the kernel source hash so that the bench reports them only while the
     kernels are unchanged. The level classes are one kernel each; the predict class is every
@@ -748,15 +748,15 @@ def write_traffic(csv_path: str, command: str):
     sha = source_sha()
     out = {cls: {"bytes_per_launch": sum(v) / len(v), "launches": len(v), "source_sha": sha, "command": command}
            for cls, v in per.items()}
-    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as fh:
+    with open(out_path or os.path.join(ROOT, "profiles", "traffic.json"), "w") as fh:
         json.dump(out, fh, indent=1, sort_keys=True)
-    print(json.dumps(out))
+    return out
 
 
 def main():
     args = parse()
     if args.write_traffic:
-        write_traffic(args.write_traffic, args.traffic_command)
+        print(json.dumps(write_traffic(args.write_traffic, args.traffic_command)))
         return
     if args.impl == "reference":
         run_reference(args)

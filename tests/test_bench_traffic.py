@@ -1,0 +1,65 @@
+"""bench.py --write-traffic: per-launch DRAM bytes of the reported kernel classes from an ncu CSV.
+
+The level classes are one kernel each (one value per launch, averaged); the predict class is every
+launch from the query coding to the compact walk, summed per call; kernels of other classes (the
+presort's radix sort, for instance) count for nothing even when they share a name with a kernel
+inside the predict call.
+"""
+import csv
+import json
+
+import bench
+
+HDR = ["ID", "Process ID", "Process Name", "Host Name", "Kernel Name", "Context", "Stream", "Block Size",
+       "Grid Size", "Device", "CC", "Section Name", "Metric Name", "Metric Unit", "Metric Value"]
+
+
+def rows_for(lid, name, read, write, unit="byte"):
+    base = [str(lid), "1", "python3", "h", name, "1", "7", "(256, 1, 1)", "(1, 1, 1)", "0", "10.3", "Command line"]
+    return [base + ["dram__bytes_read.sum", unit, f"{read:,}"], base + ["dram__bytes_write.sum", unit, f"{write:,}"]]
+
+
+def test_classes_and_sums(tmp_path):
+    launches = [
+        ("void aiwcrf::sort_hist_kernel(const unsigned int *, long, long, int, int, unsigned int *)", 1000, 1000),
+        ("void aiwcrf::level_big_kernel<unsigned char>(aiwcrf::LevelArgs, int)", 100, 20),
+        ("void aiwcrf::level_small_kernel<unsigned char>(aiwcrf::LevelArgs)", 50, 10),
+        ("void aiwcrf::level_big_kernel<unsigned char>(aiwcrf::LevelArgs, int)", 300, 60),
+        ("void aiwcrf::level_small_kernel<unsigned char>(aiwcrf::LevelArgs)", 150, 30),
+        ("void aiwcrf::finalize_kernel(aiwcrf::FinalArgs)", 5, 5),
+        ("void aiwcrf::code_queries_kernel<unsigned char>(const float *, long, int, const float *, long, "
+         "const unsigned int *, T1 *, int)", 128_000, 36_000),
+        ("aiwcrf::query_key_kernel(const unsigned char *, int, long, int4, unsigned int *, unsigned int *)", 36, 8),
+        ("void aiwcrf::sort_hist_kernel(const unsigned int *, long, long, int, int, unsigned int *)", 8, 1),
+        ("void aiwcrf::predict4_kernel<2, 0, 1>(const unsigned int *, const long *)", 40, 8),
+        ("void aiwcrf::serve_select_kernel<1>(aiwcrf::ServeForest)", 7, 7),
+    ]
+    path = tmp_path / "t.csv"
+    with open(path, "w", newline="") as fh:
+        fh.write("==PROF== Connected to process\n")
+        w = csv.writer(fh)
+        w.writerow(HDR)
+        for i, (name, r, wr) in enumerate(launches):
+            for row in rows_for(i, name, r, wr):
+                w.writerow(row)
+    out = tmp_path / "traffic.json"
+    d = bench.write_traffic(str(path), "ncu ...", str(out))
+    assert json.load(open(out)) == d
+    assert d["level_big"]["launches"] == 2 and d["level_big"]["bytes_per_launch"] == (120 + 360) / 2
+    assert d["level_small"]["launches"] == 2 and d["level_small"]["bytes_per_launch"] == (60 + 180) / 2
+    # predict: coding + key + the key sort's kernel + the walk; not the presort's sort kernel
+    assert d["predict"]["launches"] == 1
+    assert d["predict"]["bytes_per_launch"] == 164_000 + 44 + 9 + 48
+    assert set(d) == {"level_big", "level_small", "predict"}
+    assert all(v["source_sha"] == bench.source_sha() for v in d.values())
+
+
+def test_units_scale(tmp_path):
+    path = tmp_path / "t.csv"
+    with open(path, "w", newline="") as fh:
+        w = csv.writer(fh)
+        w.writerow(HDR)
+        for row in rows_for(3, "void aiwcrf::level_small_kernel<unsigned short>(aiwcrf::LevelArgs)", 1.5, 0.5, "Mbyte"):
+            w.writerow(row)
+    d = bench.write_traffic(str(path), "", str(tmp_path / "o.json"))
+    assert d["level_small"]["bytes_per_launch"] == 2_000_000
