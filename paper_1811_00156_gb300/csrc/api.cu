@@ -148,7 +148,7 @@ cudaEvent_t take_event()
     return e;
 }
 
-const char *kProfNames[kProfNum] = {"rank",    "bootstrap", "level_big", "level_small", "scan",
+const char *kProfNames[kProfNum] = {"rank",    "bootstrap", "level_big", "level_small",
                                     "finalize", "pack",      "predict",   "select", "serve"};
 }  // namespace
 

@@ -15,11 +15,12 @@
 //                        (sum w, sum w*y) per rank of every tried feature, block scan, exact
 //                        argmax of the gain, stable partition of the entries
 //     level_small_kernel one warp per node with <= 32 entries: the same search with a register
-//                        bitonic sort per feature instead of a histogram
-//     scan_*             exclusive scan of the split flags over the depth's nodes
-//     finalize_kernel    encodes each node, numbers the children breadth first, writes the
-//                        next depth's node table and its warp/CTA work lists; its last CTA
-//                        advances the per-tree node counts, next-depth offsets and level counts
+//                        bitonic sort per feature instead of a histogram (runs concurrently with
+//                        level_big_kernel; both count each tile's splits)
+//     finalize_kernel    exclusive scan of the split flags, then encodes each node, numbers the
+//                        children breadth first, writes the next depth's node table and its
+//                        warp/CTA work lists; its last CTA advances the per-tree node counts,
+//                        next-depth offsets and level counts
 //   pack_kernel        scatters every finished node to its forest / tree / BFS position
 #include <cuda_runtime.h>
 

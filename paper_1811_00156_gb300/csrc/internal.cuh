@@ -336,7 +336,7 @@ int radix_sort_segments(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, ui
 size_t radix_sort_hist_words(int64_t n, int S);
 
 enum ProfClass {
-    kProfRank = 0, kProfBoot, kProfLevelBig, kProfLevelSmall, kProfScan, kProfFinalize,
+    kProfRank = 0, kProfBoot, kProfLevelBig, kProfLevelSmall, kProfFinalize,
     kProfPack, kProfPredict, kProfSelect, kProfServe, kProfNum
 };
 
