@@ -232,6 +232,10 @@ int aiwcrf_surrogate_export(const aiwcrf_surrogate *surrogate, float *params, fl
                             float *sd, uint8_t *log2_cols);
 int aiwcrf_surrogate_stats(const aiwcrf_surrogate *surrogate, aiwcrf_surrogate_fit_stats *out);
 int32_t aiwcrf_surrogate_num_params(void);
+
+/* Waits for the device (work reading the network may be in flight on any stream), then returns
+ * its memory to the stream-ordered pool: no cudaFree, so no device-wide wait inside the free.
+ * NULL is accepted. */
 int aiwcrf_surrogate_free(aiwcrf_surrogate *surrogate);
 
 /* ---------------------------------------------------------------------------------------------
@@ -459,6 +463,8 @@ int aiwcrf_fit_plan_tune(aiwcrf_fit_plan *plan, int32_t reps, void *cuda_stream,
 /* Set a schedule explicitly (the graph is captured again). */
 int aiwcrf_fit_plan_set_schedule(aiwcrf_fit_plan *plan, const aiwcrf_fit_schedule *schedule);
 
+/* Waits for the device, destroys the captured graph and returns the plan's tables to the
+ * stream-ordered pool (no cudaFree, so no device-wide wait inside the free). NULL is accepted. */
 int aiwcrf_fit_plan_free(aiwcrf_fit_plan *plan);
 
 /* Counters of the fit that produced the forest (zeros for a deserialized forest). */
@@ -480,6 +486,8 @@ int aiwcrf_forest_serialize(const aiwcrf_forest *forest, void *buf, size_t cap, 
 /* Rebuild a forest on the current device from a blob (validated: AIWCRF_E_CORRUPT). */
 int aiwcrf_forest_deserialize(const void *buf, size_t len, aiwcrf_forest **out);
 
+/* Waits for the device (work reading the forest may be in flight on any stream), then returns
+ * the forest's memory to the stream-ordered pool. NULL is accepted. */
 int aiwcrf_forest_free(aiwcrf_forest *forest);
 
 /* Message of the last failing call on this host thread ("" if none). */
