@@ -174,10 +174,10 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel: str, sha: str):
+def ncu_traffic(kernel: str, sha: str, path: str | None = None):
     """Per-launch DRAM traffic of `kernel` from the committed ncu summary, if it was taken on
     the current kernel source; else None."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    p = path or os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))

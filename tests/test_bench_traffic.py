@@ -63,3 +63,12 @@ def test_units_scale(tmp_path):
             w.writerow(row)
     d = bench.write_traffic(str(path), "", str(tmp_path / "o.json"))
     assert d["level_small"]["bytes_per_launch"] == 2_000_000
+
+
+def test_traffic_reported_only_for_the_captured_sources(tmp_path):
+    p = tmp_path / "traffic.json"
+    p.write_text(json.dumps({"predict": {"bytes_per_launch": 1.5e8, "source_sha": "abc", "launches": 1}}))
+    assert bench.ncu_traffic("predict", "abc", str(p)) == 1.5e8
+    assert bench.ncu_traffic("predict", "abd", str(p)) is None          # kernels changed since
+    assert bench.ncu_traffic("level_small", "abc", str(p)) is None      # not captured
+    assert bench.ncu_traffic("predict", "abc", str(tmp_path / "missing.json")) is None
