@@ -1,11 +1,16 @@
 """Pins of the oracle's counter-based generator and of the draws built on it.
 
 Philox (Salmon et al., SC'11) is defined by its round structure and constants. The 4x64 member
-is checked word for word against numpy's independent Philox4x64-10; the 4x32 member the
-library uses shares the round code with it. Bootstrap multiplicities and mtry subsets are then
-checked statistically against their exact distributions.
+is checked word for word against numpy's independent Philox4x64-10, and the 4x32 member the
+method uses against Triton's independent Philox4x32-10 (its `tl.philox`, run by Triton's CPU
+interpreter). Bootstrap multiplicities and mtry subsets are then checked statistically against
+their exact distributions.
 """
+import json
 import math
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -92,3 +97,55 @@ def test_mtry_draw_edge_cases():
     a = O.mtry_draw(1, 2, 3, 4, 40, 7)
     b = O.mtry_draw(1, 2, 3, 4, 40, 7)
     assert np.array_equal(a, b) and len(a) == 7
+
+
+_TRITON_PHILOX = r"""
+import json, os, sys
+os.environ["TRITON_INTERPRET"] = "1"
+import numpy as np
+import torch
+import triton
+import triton.language as tl
+
+@triton.jit
+def philox_kernel(seed, c0p, c1p, c2p, c3p, o0, o1, o2, o3, N: tl.constexpr):
+    i = tl.arange(0, N)
+    a, b, c, d = tl.philox(seed, tl.load(c0p + i), tl.load(c1p + i), tl.load(c2p + i), tl.load(c3p + i), 10)
+    tl.store(o0 + i, a)
+    tl.store(o1 + i, b)
+    tl.store(o2 + i, c)
+    tl.store(o3 + i, d)
+
+args = json.loads(sys.argv[1])
+out = []
+for seed, ctrs in args:
+    n = len(ctrs)
+    cols = [torch.from_numpy(np.array([c[w] for c in ctrs], dtype=np.uint32).view(np.int32)) for w in range(4)]
+    res = [torch.empty(n, dtype=torch.int32) for _ in range(4)]
+    philox_kernel[(1,)](seed, *cols, *res, N=n)
+    words = [r.numpy().view(np.uint32) for r in res]
+    out.append([[int(words[w][j]) for w in range(4)] for j in range(n)])
+print(json.dumps(out))
+"""
+
+
+def test_philox4x32_matches_triton():
+    """Word for word against Triton's Philox4x32-10 (key = the seed's low and high words)."""
+    pytest.importorskip("triton")
+    pytest.importorskip("torch")
+    rng = np.random.default_rng(2026)
+    cases = []
+    for seed in (0, 0x0123456789ABCDEF, 2 ** 64 - 1, 156):
+        ctrs = [[0, 0, 0, 0], [2 ** 32 - 1] * 4] + \
+            [[int(v) for v in rng.integers(0, 2 ** 32, 4, dtype=np.uint64)] for _ in range(14)]
+        cases.append([seed, ctrs])
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    r = subprocess.run([sys.executable, "-c", _TRITON_PHILOX, json.dumps(cases)], capture_output=True, text=True,
+                       env=env, timeout=600)
+    if r.returncode != 0:
+        pytest.skip("Triton's interpreter is not usable here: " + r.stderr.strip().splitlines()[-1][:200])
+    theirs = json.loads(r.stdout.strip().splitlines()[-1])
+    for (seed, ctrs), words in zip(cases, theirs):
+        for ctr, w in zip(ctrs, words):
+            ours = O.philox4x32(ctr, [seed & 0xFFFFFFFF, seed >> 32])
+            assert [int(v) for v in ours] == w, (seed, ctr)
