@@ -5,6 +5,7 @@ import pytest
 
 from oracle import mlp as M
 from paper_1811_00156_gb300 import synth
+from tests.mlp_cases import model, violations
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -20,49 +21,48 @@ def A():
     return aiwcrf
 
 
-def _model(A, seed=0):
-    rng = np.random.default_rng(seed)
-    P = rng.normal(0.0, 0.08, M.N_PARAMS).astype(np.float32)
-    P[M.OW1:M.OB1].reshape(M.HID, M.K_IN)[:, 49:] = 0.0
-    P[M.OB3] = -2.0
-    mu = rng.normal(0.0, 1.0, 30).astype(np.float32)
-    sd = rng.uniform(0.5, 3.0, 30).astype(np.float32)
-    lg = np.zeros(30, np.uint8)
-    lg[:10] = 1
-    lg[24:] = 1
-    return P, mu, sd, lg, A.aiwcrf_surrogate_create(32, 15, 4, P, mu, sd, lg)
+def _model(A, seed=0, n=512):
+    P, X, mu, sd, lg, y = model(seed, n)
+    return P, X, mu, sd, lg, y, A.aiwcrf_surrogate_create(32, 15, 4, P, mu, sd, lg)
 
 
 def test_gradient_matches_fp64_oracle(A):
-    P, mu, sd, lg, sg = _model(A)
-    n = 512
-    X = synth.queries(n, seed=3)
-    y = np.random.default_rng(4).normal(-3.0, 1.0, n).astype(np.float32)
+    """Every one of the 82,689 gradient entries, and the loss, lie within the oracle's
+    element-wise tolerance (oracle/mlp.py grad_tolerance). The tolerance is a running error
+    analysis of the device's arithmetic: FP32 operations err by at most u = 2^-24 relative;
+    log2f, erff and expf by at most 1, 2 and 2 ulp; a K-term FP32 accumulation of exact BF16
+    products by at most 2 K u times the sum of the absolute terms; GELU and GELU' move by their
+    Taylor bounds under an argument error; and a value known within E rounds to BF16 within
+    bf16(v + E) - bf16(v - E) of the oracle's rounded value. The bounds propagate through the
+    forward pass, the loss and the backward pass as the device computes them. The CPU tests show
+    it admits an independent float32 evaluation and rejects planted mistakes, among them a 5 %
+    error in one W2 gradient entry."""
+    P, X, mu, sd, lg, y, sg = _model(A)
+    n = X.shape[1]
     g = torch.empty(M.N_PARAMS, dtype=torch.float32, device="cuda")
     loss = torch.empty(1, dtype=torch.float32, device="cuda")
     sg.grad(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(), g, loss)
     torch.cuda.synchronize()
-    xin = M.encode(X, mu, sd, lg, 15, 4)
-    rl, rg = M.loss_and_grad(P.astype(np.float64), xin, y.astype(np.float64))
-    gg = g.cpu().numpy().astype(np.float64)
-    assert abs(float(loss.item()) - rl) <= 1e-3 * abs(rl)
-    for name, a, b in [("W1", M.OW1, M.OB1), ("b1", M.OB1, M.OW2), ("W2", M.OW2, M.OB2), ("b2", M.OB2, M.OW3),
-                       ("w3", M.OW3, M.OB3), ("b3", M.OB3, M.N_PARAMS)]:
-        rel = np.linalg.norm(gg[a:b] - rg[a:b]) / (np.linalg.norm(rg[a:b]) + 1e-30)
-        assert rel < 2e-2, (name, rel)
+    rl, rg, lb, gb = M.grad_tolerance(P.astype(np.float64), X, mu, sd, lg, 15, 4, y.astype(np.float64))
+    assert abs(float(loss.item()) - rl) <= lb, (float(loss.item()), rl, lb)
+    v = violations(g.cpu().numpy(), rg, gb)
+    assert all(c == 0 for c, _ in v.values()), v
+    assert n == 512
 
 
 def test_fused_inference_matches_oracle_forward(A):
-    P, mu, sd, lg, sg = _model(A, seed=5)
+    """Every prediction of the fused inference kernel lies within the oracle's element-wise
+    tolerance of the rounded forward pass (oracle/mlp.py forward_tolerance, the same running
+    error analysis as the gradient's)."""
+    P, _, mu, sd, lg, _, sg = _model(A, seed=5)
     for Q in (1, 127, 128, 1000, 70001):
         X = synth.queries(Q, seed=Q)
         out = torch.empty(Q, dtype=torch.float32, device="cuda")
         sg.predict(torch.from_numpy(X).cuda(), out)
         torch.cuda.synchronize()
-        ref, _ = M.forward(P.astype(np.float64), M.encode(X, mu, sd, lg, 15, 4))
-        err = np.abs(out.cpu().numpy() - ref)
-        assert err.max() <= 2e-2 * (np.abs(ref).max() + 1.0), (Q, err.max())
-        assert np.median(err) <= 2e-3 * (np.abs(ref).max() + 1.0)
+        ref, bound = M.forward_tolerance(P.astype(np.float64), X, mu, sd, lg, 15, 4)
+        err = np.abs(out.cpu().numpy().astype(np.float64) - ref)
+        assert np.all(err <= bound), (Q, int(np.sum(err > bound)), float(np.max(err / bound)))
 
 
 def test_distillation_learns_the_forest(A):
