@@ -52,10 +52,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the OOB and LOKO reports")
-    ap.add_argument("--write-traffic", metavar="CSV", default=None,
-                    help="write profiles/traffic.json from an ncu --csv capture of dram__bytes_read.sum and "
-                         "dram__bytes_write.sum over the benchmark's launches, then exit")
-    ap.add_argument("--traffic-command", default="", help="the ncu command that made the CSV (recorded)")
+    ap.add_argument("--write-counters", metavar="CSV", default=None,
+                    help="merge into profiles/counters.json the per-launch counters of an ncu --csv capture "
+                         "(dram__bytes_read.sum, dram__bytes_write.sum, smsp__inst_executed.sum, "
+                         "l1tex__data_pipe_lsu_wavefronts_mem_shared.sum) and exit")
+    ap.add_argument("--counters-command", default="", help="the ncu command that made the CSV (recorded)")
     ap.add_argument("--trees", type=int, default=T_TREES,
                     help="forest size per GPU; smaller values are for profiler captures only")
     ap.add_argument("--queries", type=int, default=N_QUERIES,
@@ -161,7 +162,7 @@ def run_reference(args):
 # ------------------------------------------------------------------------------ ours
 def source_sha():
     h = hashlib.sha256()
-    for f in ("fit.cu", "predict.cu", "internal.cuh"):
+    for f in ("fit.cu", "predict.cu", "sort.cu", "internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1811_00156_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -174,17 +175,23 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel: str, sha: str, path: str | None = None):
-    """Per-launch DRAM traffic of `kernel` from the committed ncu summary, if it was taken on
-    the current kernel source; else None."""
-    p = path or os.path.join(ROOT, "profiles", "traffic.json")
+def ncu_counter(kernel: str, metric: str, sha: str, path: str | None = None):
+    """A per-launch counter of a kernel class from the committed ncu summary
+    (profiles/counters.json: dram_bytes, inst, smem_wavefronts), if it was taken on the current
+    kernel source; else None."""
+    p = path or os.path.join(ROOT, "profiles", "counters.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     e = d.get(kernel)
     if not e or e.get("source_sha") != sha:
         return None
-    return e.get("bytes_per_launch")
+    return e.get(metric)
+
+
+def ncu_traffic(kernel: str, sha: str, path: str | None = None):
+    """Per-launch DRAM traffic (read + write bytes) of a kernel class, or None."""
+    return ncu_counter(kernel, "dram_bytes", sha, path)
 
 
 def run_ours(args):
@@ -238,12 +245,12 @@ def run_ours(args):
         if ev: ev[3].record(stream)
         return forest
 
-    LEVEL_CLASSES = ("level_small", "level_big")
-    dom_fit, dom = "level_small", "predict"
+    FIT_CLASSES = ("tree", "level_small", "level_big")
+    dom_fit, dom = "tree", "predict"
     for w in range(args.warmup):
         last = w == args.warmup - 1
         if last:               # the last warm-up step finds the dominant kernels of the fit and the step
-            A.aiwcrf_profile_classes([*LEVEL_CLASSES, "predict"])
+            A.aiwcrf_profile_classes([*FIT_CLASSES, "predict"])
             A.aiwcrf_profile_enable(True)
             A.aiwcrf_profile_read()
         step()
@@ -251,15 +258,15 @@ def run_ours(args):
             torch.cuda.synchronize()
             p0 = A.aiwcrf_profile_read()
             A.aiwcrf_profile_enable(False)
-            dom_fit = max(LEVEL_CLASSES, key=lambda c: p0[c][1])
-            dom = max((*LEVEL_CLASSES, "predict"), key=lambda c: p0[c][1])
+            dom_fit = max(FIT_CLASSES, key=lambda c: p0[c][1])
+            dom = max((*FIT_CLASSES, "predict"), key=lambda c: p0[c][1])
     torch.cuda.synchronize()
 
     clocks = Clocks(local_rank)
     clocks.start()
     # inside the timed steps, events bracket the dominant kernels' launches only: every pair
     # costs the stream about 2 us, and bracketing every class would add ~5 % to the fit
-    A.aiwcrf_profile_classes(sorted({dom, dom_fit}))
+    A.aiwcrf_profile_classes(sorted({dom, dom_fit, "walk"}))
     A.aiwcrf_profile_enable(True)
     A.aiwcrf_profile_read()
     launches0 = A.aiwcrf_launch_count()
@@ -281,7 +288,7 @@ def run_ours(args):
     A.aiwcrf_profile_enable(False)
     clk = clocks.stop()
     # the kernel classes' shares: K more (untimed) steps with every class bracketed
-    A.aiwcrf_profile_classes(["level_small", "level_big", "predict", "select"])
+    A.aiwcrf_profile_classes(["tree", "level_small", "level_big", "predict", "select"])
     A.aiwcrf_profile_enable(True)
     A.aiwcrf_profile_read()
     for k in range(args.steps):
@@ -306,6 +313,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel class, from the events recorded around each launch
     peak, peak_kind = measured_peaks()
+    sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
     big_rows = stats["entries_evaluated"] - stats["entries_evaluated_small"]
     big_part = stats["entries_partitioned"] - stats["entries_partitioned_small"]
     per_eval = 16 + stats["rank_bytes"] * MTRY     # 16-byte entry + the tried features' ranks
@@ -313,6 +321,7 @@ def run_ours(args):
     alg = {
         "level_big": K * (big_rows * per_eval + big_part * per_part),
         "level_small": K * (stats["entries_evaluated_small"] * per_eval + stats["entries_partitioned_small"] * per_part),
+        "tree": K * (stats["entries_evaluated"] * per_eval + stats["entries_partitioned"] * per_part),
         "predict": K * n_queries * (F * 4 + 8),
     }
     sha = source_sha()
@@ -328,17 +337,52 @@ def run_ours(args):
     tot_ms = sum(v["total_ms"] for v in kernels.values()) or 1.0
     for v in kernels.values():
         v["share_of_profiled"] = v["total_ms"] / tot_ms
-    # the dominant kernels' launches as timed inside the timed steps
-    def roofline_of(name):
+    timing = "CUDA events around each launch of this kernel inside the timed steps"
+
+    def hbm_roofline(name):
         n_l, ms = prof_dom[name]
         achieved = alg[name] / (ms / 1e3) / 1e9
         return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind} peaks",
                 "traffic": ncu_traffic(name, sha), "alg_bytes_per_launch": alg[name] / n_l,
-                "ms_per_launch": ms / n_l,
-                "timing": "CUDA events around each launch of this kernel inside the timed steps"}
-    roofline = roofline_of(dom)                  # the step's dominant kernel
-    roofline_fit = roofline_of(dom_fit)          # the fit's (the metric's) dominant kernel
+                "ms_per_launch": ms / n_l, "timing": timing}
+
+    def issue_roofline(name):
+        """A kernel whose working set is in shared memory and registers: bound by instruction
+        issue. achieved = warp instructions per launch (ncu smsp__inst_executed.sum, same
+        source) / event-timed duration; peak = 152 SMs x 4 schedulers x 1 warp instruction per
+        cycle at the median SM clock sampled in the timed region."""
+        n_l, ms = prof_dom[name]
+        inst = ncu_counter(name, "inst", sha)
+        pk = 152 * 4 * sm_mhz * 1e6 / 1e12                  # T warp-instructions/s
+        r = {"kernel": name, "bound": "alu", "unit": "T warp-inst/s", "peak": pk,
+             "peak_source": f"152 SMs x 4 issue slots x {sm_mhz:.0f} MHz (median sampled SM clock)",
+             "ms_per_launch": ms / n_l, "timing": timing, "traffic": ncu_traffic(name, sha),
+             "alg_bytes_per_launch": alg[name] / n_l, "inst_per_launch": inst,
+             "achieved": None, "frac": None}
+        if inst:
+            r["achieved"] = inst / (ms / n_l / 1e3) / 1e12
+            r["frac"] = r["achieved"] / pk
+        # context: the entry bytes it evaluates, as a rate against HBM (not its bound)
+        r["entry_bytes_gbs"] = alg[name] / n_l / (ms / n_l / 1e3) / 1e9
+        return r
+
+    roofline = hbm_roofline(dom) if dom in ("predict", "level_big", "level_small") else issue_roofline(dom)
+    if dom == "predict" and prof_dom.get("walk", (0, 0.0))[0]:
+        # the walk's real bound: shared-memory wavefronts (one per SM per cycle) and issue
+        n_w, ms_w = prof_dom["walk"]
+        wf = ncu_counter("walk", "smem_wavefronts", sha)
+        wi = ncu_counter("walk", "inst", sha)
+        smem_peak = 152 * sm_mhz * 1e6 / 1e9                  # G wavefronts/s
+        roofline["walk"] = {"ms_per_launch": ms_w / n_w, "smem_wavefronts_per_launch": wf,
+                            "smem_peak_gwf_s": smem_peak, "inst_per_launch": wi,
+                            "issue_peak_tinst_s": 152 * 4 * sm_mhz * 1e6 / 1e12}
+        if wf:
+            roofline["walk"]["smem_achieved_gwf_s"] = wf / (ms_w / n_w / 1e3) / 1e9
+            roofline["smem_frac"] = roofline["walk"]["smem_achieved_gwf_s"] / smem_peak
+        if wi:
+            roofline["walk"]["issue_frac"] = wi / (ms_w / n_w / 1e3) / 1e12 / roofline["walk"]["issue_peak_tinst_s"]
+    roofline_fit = (issue_roofline(dom_fit) if dom_fit == "tree" else hbm_roofline(dom_fit))
 
     out = {"metric": METRIC, "value": value, "unit": ROWS_TREES_UNIT, "n_gpus": world, "steps": K,
            "warmup": args.warmup, "ms_per_step": step_ms / K, "higher_is_better": True, "scaling": "weak",
@@ -365,6 +409,7 @@ def run_ours(args):
         out["oob"] = oob_report(A, wl, X, f)
         del f
         out["loko"] = loko_report(A, dev)
+        out["per_row"] = per_row_report(A, dev)
         f = A.aiwcrf_fit(params, X, y)
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
@@ -438,6 +483,56 @@ def fit_graph_report(A, params, X, y, stats, steps: int = 5):
             "build_s": build_s}
 
 
+def per_row_report(A, dev, n_trees: int = T_TREES, steps: int = 1):
+    """The 111,000-row, 500-tree fit on the per-row reading of the features (every row its own
+    AIWC vector: about 111,000 distinct values in 24 of the 32 columns, four-byte ranks, no two
+    rows grouped), where the histogram and scan passes stream every active in-bag row. roofline
+    on the scan passes' algorithmic bytes: 33 B per active in-bag row and level (4 B row id + 1 B
+    multiplicity + 8 B target + 10 tried ranks x 2 B) plus 10 B per partitioned row (row id and
+    multiplicity read and written), over the level kernels' event-timed time."""
+    import torch
+    wl = synth.per_row_forest_workload()
+    X, y = torch.from_numpy(wl.X).to(dev), torch.from_numpy(wl.y).to(dev)
+    params = A.params(n_trees, MTRY, MIN_NODE, seed=synth.FOREST_SEED)
+    f = A.aiwcrf_fit(params, X, y)                                     # warm-up
+    st = f.stats()
+    del f
+    A.aiwcrf_profile_classes(["level_small", "level_big", "finalize", "tree"])
+    A.aiwcrf_profile_enable(True)
+    A.aiwcrf_profile_read()
+    ms = 0.0
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        f = A.aiwcrf_fit(params, X, y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        st = f.stats()
+        del f
+    prof = A.aiwcrf_profile_read()
+    A.aiwcrf_profile_enable(False)
+    A.aiwcrf_profile_classes(None)
+    peak, peak_kind = measured_peaks()
+    scan_ms = sum(prof.get(c, (0, 0.0))[1] for c in ("level_small", "level_big", "tree")) / steps
+    alg = 33 * st["entries_evaluated"] + 10 * st["entries_partitioned"]
+    achieved = alg / (scan_ms / 1e3) / 1e9 if scan_ms else None
+    return {"workload": f"aiwc-111000 per-row features: fit {n_trees} trees (mtry 10, min_node 5) on 111,000 "
+                        "rows x 32 features, every row its own feature vector",
+            "fit_ms": ms / steps, "rows_trees_per_s": wl.n_rows * n_trees * steps / (ms / 1e3),
+            "stats": st,
+            "roofline_fit": {"kernels": "level_big + level_small (histogram, scan, argmax, partition)",
+                             "bound": "hbm", "alg_bytes_per_fit": alg,
+                             "alg_bytes": "33 B per active in-bag row-level (entries_evaluated) + 10 B per "
+                                          "partitioned row-level (entries_partitioned)",
+                             "ms_per_fit": scan_ms, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak if achieved else None,
+                             "peak_source": f"hbm_gbs of {peak_kind} peaks",
+                             "timing": "CUDA events around every level kernel launch of the fit"},
+            "kernels_ms": {c: prof[c][1] / steps for c in ("level_small", "level_big", "finalize", "tree")
+                           if c in prof and prof[c][0]}}
+
+
 def loko_report(A, dev, steps: int = 2):
     """Leave-one-kernel-out cross-validation (Alg. 1 / Table III, here without the simulated-
     annealing re-tuning): 37 forests x 256 trees grown together by one batched fit; per-fold
@@ -489,6 +584,27 @@ def loko_report(A, dev, steps: int = 2):
         same = same and [f.serialize() for f in pf] == ref
         del pf
     plan.close()
+    # strict leave-one-kernel-out (Alg. 1): each fold trains on the other 36 kernels' rows and is
+    # scored on every row of the held-out kernel
+    kern = wl.meta["kernel"]
+    strict = [(np.flatnonzero(kern != k), np.flatnonzero(kern == k)) for k in range(synth.N_KERNELS)]
+    soffs = np.cumsum([0] + [len(tr) for tr, _ in strict]).astype(np.int64)
+    srows = torch.from_numpy(np.concatenate([tr for tr, _ in strict]).astype(np.int32)).to(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    sforests = A.aiwcrf_fit_subsets(params, X, y, soffs, srows)
+    e1.record()
+    torch.cuda.synchronize()
+    strict_ms = e0.elapsed_time(e1)
+    smape = []
+    for g, (tr, te) in enumerate(strict):
+        Xt = torch.from_numpy(np.ascontiguousarray(wl.X[:, te])).to(dev)
+        out = torch.empty(len(te), dtype=torch.int64, device=dev)
+        A.aiwcrf_predict(sforests[g], Xt, out)
+        pred = out.cpu().numpy() / 2.0 ** 32
+        truth = wl.y[te] / 2.0 ** 32
+        smape.append(float(np.mean(np.abs(10.0 ** pred - 10.0 ** truth) / 10.0 ** truth)))
+    del sforests
     return {"folds": len(folds), "trees_per_fold": 256, "train_rows": [int(min(len(t) for t, _ in folds)),
                                                                       int(max(len(t) for t, _ in folds))],
             "fit_ms": min(ms), "rows_trees_per_s": rows_trees / (min(ms) / 1e3),
@@ -497,7 +613,11 @@ def loko_report(A, dev, steps: int = 2):
                       "schedule": chosen, "schedules_tried": tried, "build_s": build_s, "tune_s": tune_s},
             "mape_mean": float(np.mean(mape)), "mape_median": float(np.median(mape)),
             "mape_max": float(np.max(mape)), "batched": "one aiwcrf_fit_subsets call for all folds; "
-            "graph: one aiwcrf_fit_plan_run (captured CUDA graph, autotuned schedule)"}
+            "graph: one aiwcrf_fit_plan_run (captured CUDA graph, autotuned schedule)",
+            "strict": {"reading": "train on the other 36 kernels (2,160 rows), score every row of the held-out "
+                                  "kernel (60 rows)", "fit_ms": strict_ms,
+                       "mape_mean": float(np.mean(smape)), "mape_median": float(np.median(smape)),
+                       "mape_max": float(np.max(smape))}}
 
 
 def surrogate_report(A, forest, Xq, n_train=4_000_000, epochs=20, bf16_peak_tflops=None):
@@ -678,9 +798,16 @@ def serving_report(A, wl, rates=(5000.0, 20000.0, 50000.0), n_requests=20000, re
                                        "max": float(gpu.max())}
                 rep["batch_enqueue_us"] = {"p50": float(np.median(enq)), "max": float(enq.max())}
                 rep["max_gap_between_batches_ms"] = float(np.diff(form).max() / 1e6) if nb > 1 else 0.0
-                slow = bt[gpu > 5000]
+                slow = bt[(gpu > 5000) | (enq > 5000)]
+                # where a slow batch's time went: the dispatcher's CPU time and context switches
+                # while enqueuing, and the longest gap between its completion polls
                 rep["slow_batches"] = [{"t_ms": float((b["t_formed_ns"] - form[0]) / 1e6),
-                                        "gpu_ms": float((b["t_done_ns"] - b["t_enqueued_ns"]) / 1e6)} for b in slow[:8]]
+                                        "gpu_ms": float((b["t_done_ns"] - b["t_enqueued_ns"]) / 1e6),
+                                        "enqueue_ms": float((b["t_enqueued_ns"] - b["t_formed_ns"]) / 1e6),
+                                        "enqueue_cpu_ms": float(b["enqueue_cpu_ns"] / 1e6),
+                                        "enqueue_voluntary_switches": int(b["enqueue_voluntary_switches"]),
+                                        "enqueue_involuntary_switches": int(b["enqueue_involuntary_switches"]),
+                                        "poll_gap_max_ms": float(b["poll_gap_max_ns"] / 1e6)} for b in slow[:8]]
                 rep["refit_windows_ms"] = [[float((r["t_start_ns"] - form[0]) / 1e6),
                                             float((r["t_swapped_ns"] - form[0]) / 1e6)]
                                            for r in rt if r["t_start_ns"] >= form[0]]
@@ -702,61 +829,75 @@ def serving_report(A, wl, rates=(5000.0, 20000.0, 50000.0), n_requests=20000, re
 
 def oob_report(A, wl, X, forest):
     import torch
-    s = torch.empty(wl.n_rows, dtype=torch.int64, device=X.device)
-    c = torch.empty(wl.n_rows, dtype=torch.int32, device=X.device)
+    y = torch.from_numpy(wl.y).to(X.device)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    A.aiwcrf_oob(forest, X, s, c)
+    mse, rows = A.aiwcrf_oob_error(forest, X, y)
     e1.record()
     torch.cuda.synchronize()
-    sn, cn = s.cpu().numpy(), c.cpu().numpy()
-    return {"mse_log10_s2": A.oob_error(sn, cn, wl.y), "rows_out_of_bag": float((cn > 0).mean()),
-            "ms": e0.elapsed_time(e1)}
+    return {"mse_log10_s2": mse, "rows_out_of_bag": rows / wl.n_rows, "ms": e0.elapsed_time(e1)}
 
 
-def write_traffic(csv_path: str, command: str, out_path: str | None = None) -> dict:
-    """DRAM bytes (read + write) per launch of each kernel class in an ncu CSV of one step's
-    launches, keyed by the kernel source hash so that the bench reports them only while the
-    kernels are unchanged. The level classes are one kernel each; the predict class is every
-    launch from the query coding to the compact walk (coding, key sort, walk), summed."""
+COUNTER_METRICS = {"dram__bytes_read.sum": "dram_bytes", "dram__bytes_write.sum": "dram_bytes",
+                   "smsp__inst_executed.sum": "inst", "l1tex__data_pipe_lsu_wavefronts_mem_shared.sum": "smem_wavefronts"}
+
+
+def write_counters(csv_path: str, command: str, out_path: str | None = None) -> dict:
+    """Per-launch ncu counters of each kernel class from an ncu --csv capture (metrics of
+    COUNTER_METRICS), keyed by the kernel source hash so that the bench reports them only while
+    the kernels are unchanged. Classes: tree, level_big, level_small (one kernel each); walk
+    (the compact or 8-byte predict walk); predict (every launch from the query coding to the
+    walk, summed per call)."""
     import csv
     rows = list(csv.reader(open(csv_path)))
     hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
     hdr = rows[hi]
     ki, ii, mi, ui, vi = (hdr.index(c) for c in ("Kernel Name", "ID", "Metric Name", "Metric Unit", "Metric Value"))
-    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
-    launches = {}                                   # launch ID -> [kernel name, bytes]
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9, "": 1,
+             "inst": 1, "warp": 1}
+    launches = {}                                   # launch ID -> [kernel name, {counter: value}]
     for r in rows[hi + 1:]:
-        if len(r) != len(hdr) or not r[mi].startswith("dram__bytes_"):
+        if len(r) != len(hdr) or r[mi] not in COUNTER_METRICS:
             continue
         name = r[ki].split("(")[0].split("<")[0].split("::")[-1].replace("void ", "").strip()
-        e = launches.setdefault(int(r[ii]), [name, 0.0])
-        e[1] += float(r[vi].replace(",", "")) * scale[r[ui]]
-    per = {}                                        # class -> list of per-launch (or per-call) bytes
-    in_predict, acc = False, 0.0
+        e = launches.setdefault(int(r[ii]), [name, {}])
+        c = COUNTER_METRICS[r[mi]]
+        e[1][c] = e[1].get(c, 0.0) + float(r[vi].replace(",", "")) * scale.get(r[ui], 1)
+    per = {}                                        # class -> list of per-launch (or per-call) counters
+    in_predict, acc = False, {}
     for lid in sorted(launches):
-        name, b = launches[lid]
+        name, cnt = launches[lid]
         if name == "code_queries_kernel":
-            in_predict, acc = True, 0.0
+            in_predict, acc = True, {}
         if in_predict:
-            acc += b
-            if name == "predict4_kernel":
+            for k, v in cnt.items():
+                acc[k] = acc.get(k, 0.0) + v
+        if name in ("predict4_kernel", "predict_kernel"):
+            per.setdefault("walk", []).append(cnt)
+            if in_predict:
                 per.setdefault("predict", []).append(acc)
                 in_predict = False
-        elif name in ("level_small_kernel", "level_big_kernel"):
-            per.setdefault(name.replace("_kernel", ""), []).append(b)
+        elif name in ("level_small_kernel", "level_big_kernel", "tree_grow_kernel"):
+            cls = {"tree_grow_kernel": "tree"}.get(name, name.replace("_kernel", ""))
+            per.setdefault(cls, []).append(cnt)
     sha = source_sha()
-    out = {cls: {"bytes_per_launch": sum(v) / len(v), "launches": len(v), "source_sha": sha, "command": command}
-           for cls, v in per.items()}
-    with open(out_path or os.path.join(ROOT, "profiles", "traffic.json"), "w") as fh:
-        json.dump(out, fh, indent=1, sort_keys=True)
+    out = {}
+    for cls, v in per.items():
+        keys = sorted({k for c in v for k in c})
+        out[cls] = {k: sum(c.get(k, 0.0) for c in v) / len(v) for k in keys}
+        out[cls].update({"launches": len(v), "source_sha": sha, "command": command})
+    path = out_path or os.path.join(ROOT, "profiles", "counters.json")
+    old = json.load(open(path)) if os.path.exists(path) else {}
+    old.update(out)
+    with open(path, "w") as fh:
+        json.dump(old, fh, indent=1, sort_keys=True)
     return out
 
 
 def main():
     args = parse()
-    if args.write_traffic:
-        print(json.dumps(write_traffic(args.write_traffic, args.traffic_command)))
+    if args.write_counters:
+        print(json.dumps(write_counters(args.write_counters, args.counters_command)))
         return
     if args.impl == "reference":
         run_reference(args)

@@ -47,7 +47,8 @@ extern "C" {
 
 /* Size limits (checked; AIWCRF_E_LIMIT or AIWCRF_E_INVALID_ARG when exceeded):
  *   n_rows <= 4,194,303 (2^22 - 1); |y| <= 2^40 (|log10 t| < 256);
- *   n_features <= 128; each feature column has at most 65,536 distinct values;
+ *   n_features <= 128 (a column may hold as many distinct values as rows: ranks are stored in
+ *   1, 2 or 4 bytes as the columns need);
  *   num_trees <= 1,048,576; a bootstrap multiplicity above 255 (probability ~ 1e-500) fails. */
 #define AIWCRF_MAX_ROWS       ((1 << 22) - 1)
 #define AIWCRF_MAX_FEATURES   128
@@ -90,7 +91,7 @@ typedef struct {
     int32_t n_features;
     int32_t mtry;
     int32_t rank_bytes;          /* bytes per stored rank: 1 if every column has <= 256 values */
-    int32_t reserved;
+    int32_t grower;              /* 1: level-synchronous kernels, 2: tree-resident kernel */
 } aiwcrf_fit_stats;
 
 /* Fit a forest (Sec. III-B). X: F x N column-major float32 (no NaN); y: N int64 Q32.32.
@@ -131,6 +132,19 @@ int aiwcrf_predict_sum(const aiwcrf_forest *forest, const float *Xq, int64_t n_q
 int aiwcrf_oob(const aiwcrf_forest *forest, const float *X, int64_t n_rows, int64_t *out_sum,
                int32_t *out_count, void *cuda_stream);
 
+/* Out-of-bag error (Sec. III-B: the parameters are tuned by the out-of-bag prediction error).
+ * X and y: the F x n_rows training matrix and its int64 Q32.32 targets that the forest was
+ * fitted on by aiwcrf_fit in this process (host or device arrays; AIWCRF_E_INVALID_ARG for
+ * another forest or another row count, or a |y| above 2^40). For a row r with c_r > 0 trees
+ * whose bootstrap did not draw it and leaf sum s_r over those trees, its out-of-bag prediction
+ * is p_r = floor((2 s_r + c_r) / (2 c_r)). out_pred (or NULL): int64[n_rows], p_r, 0 where
+ * c_r = 0. *out_mse (host): the mean of (p_r - y_r)^2 over the rows with c_r > 0, in the
+ * target's units squared (Q32.32 differences divided by 2^32): the squared errors are summed
+ * exactly in 128-bit integers on the device and divided once in double precision. *out_rows
+ * (host, or NULL): the number of those rows. Synchronises the stream. */
+int aiwcrf_oob_error(const aiwcrf_forest *forest, const float *X, const int64_t *y, int64_t n_rows,
+                     int64_t *out_pred, double *out_mse, int64_t *out_rows, void *cuda_stream);
+
 /* out[q] = floor((2 sums[q] + total_trees) / (2 total_trees)). */
 int aiwcrf_round_mean(const int64_t *sums, int64_t n, int64_t total_trees, int64_t *out,
                       void *cuda_stream);
@@ -151,7 +165,7 @@ int aiwcrf_select_device(const aiwcrf_forest *forest, const float *kfeat, int32_
  * synchronisation a cudaMalloc/cudaFree can cause, uses this variant instead. Same inputs,
  * outputs and results as aiwcrf_select_device, except:
  *  - kfeat, out_best and out_pred (or NULL) must be memory of the current device
- *    (AIWCRF_E_BAD_POINTER otherwise); device_ids is a host array as before.
+ *    (AIWCRF_E_BAD_POINTER otherwise); device_ids may be a host or a device array.
  *  - Scratch is one static device array of AIWCRF_NOALLOC_SCRATCH_BYTES that every GPU loading
  *    the library holds until the process exits. A request needs about
  *    (4F + 8 + 4 * code words) bytes per (kernel, device) pair (F = 32: 172 bytes, so about
@@ -159,7 +173,8 @@ int aiwcrf_select_device(const aiwcrf_forest *forest, const float *kfeat, int32_
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress);
  *    make that first call before any stream capture.
  *  - Every call reuses the same array: calls that overlap on the GPU (other streams, other
- *    host threads) race on it. The call synchronises its stream before returning. */
+ *    host threads) race on it. The call synchronises its stream before returning, also when
+ *    it fails after enqueuing work, so that no work of a returned call still uses the array. */
 #define AIWCRF_NOALLOC_SCRATCH_BYTES (1 << 20)
 int aiwcrf_select_device_noalloc(const aiwcrf_forest *forest, const float *kfeat, int32_t n_kernels,
                                  int32_t size_class, const int32_t *device_ids, int32_t n_devices,
@@ -368,9 +383,22 @@ int aiwcrf_server_run_load(aiwcrf_server *server, const float *pool, int64_t poo
  * the queue), enqueued (its copies and kernel handed to the stream) and done (completion seen by
  * the dispatcher). A refit started (rows taken), staged its rows on the device, finished the fit
  * and swapped the forest in. */
+/* One batch: when it was formed, when its copies, kernel and event had been enqueued, and when
+ * the dispatcher saw it complete (steady-clock ns). Where a slow batch's time went:
+ *  - enqueue_cpu_ns: CPU time of the dispatcher thread while enqueuing (against the wall time
+ *    t_enqueued_ns - t_formed_ns: a large gap means the thread waited);
+ *  - enqueue_voluntary_switches / enqueue_involuntary_switches: the thread's context switches
+ *    while enqueuing (voluntary: it blocked, e.g. on a driver lock; involuntary: the operating
+ *    system preempted it for another thread or process);
+ *  - poll_gap_max_ns: the longest interval between two consecutive completion polls of the
+ *    batch by the dispatcher (a gap near the batch's time means the completion was seen late,
+ *    not that the GPU was slow). */
 typedef struct {
     int64_t t_formed_ns, t_enqueued_ns, t_done_ns;
     int32_t kernels, generation;
+    int64_t enqueue_cpu_ns;
+    int32_t enqueue_voluntary_switches, enqueue_involuntary_switches;
+    int64_t poll_gap_max_ns;
 } aiwcrf_batch_trace;
 
 typedef struct {
@@ -467,14 +495,35 @@ int aiwcrf_fit_plan_set_schedule(aiwcrf_fit_plan *plan, const aiwcrf_fit_schedul
  * stream-ordered pool (no cudaFree, so no device-wide wait inside the free). NULL is accepted. */
 int aiwcrf_fit_plan_free(aiwcrf_fit_plan *plan);
 
-/* Counters of the fit that produced the forest (zeros for a deserialized forest). */
+/* Which kernels grow the trees of the following fits in this process (the paper has no
+ * counterpart: both give the same forest, node for node, for the model of Sec. III-B).
+ *  AIWCRF_GROWER_AUTO (default): tree-resident when it fits, else level-synchronous.
+ *  AIWCRF_GROWER_LEVEL: level-synchronous, every depth of every tree as three launches
+ *    (big-node CTAs, small-node warps, a finalize pass).
+ *  AIWCRF_GROWER_TREE: tree-resident, one CTA grows a whole tree with its entries in shared
+ *    memory; a fit whose trees do not fit (ranks wider than one byte, more than 32 features,
+ *    more than 65,535 groups, or too many entries per tree for shared memory) fails with
+ *    AIWCRF_E_LIMIT. Fit plans always use the level-synchronous kernels.
+ * AIWCRF_E_INVALID_ARG for another value. The forest's aiwcrf_fit_stats.grower says which
+ * ran. */
+#define AIWCRF_GROWER_AUTO 0
+#define AIWCRF_GROWER_LEVEL 1
+#define AIWCRF_GROWER_TREE 2
+int aiwcrf_set_grower(int32_t grower);
+
+/* Counters of the fit that produced the forest (zeros for a deserialized forest). The paper has
+ * no counterpart: these count the work of the fit (Sec. III-B) for measurement. */
 int aiwcrf_forest_stats(const aiwcrf_forest *forest, aiwcrf_fit_stats *out);
 
-/* Number of trees, packed nodes (including alignment padding) and features. */
+/* Number of trees, packed nodes (including alignment padding) and features (the fitted model of
+ * Sec. III-B; its layout is this library's). */
 int aiwcrf_forest_info(const aiwcrf_forest *forest, int64_t *num_trees, int64_t *num_nodes,
                        int32_t *n_features);
 
-/* Versioned little-endian blob of the packed forest, into a host buffer. With buf == NULL or
+/* Checkpoint of a fitted forest. The paper's model is fitted once and needs refitting only when
+ * a new kind of device is added (Sec. I); keeping it between processes is this library's, with
+ * no counterpart in the paper.
+ * Versioned little-endian blob of the packed forest, into a host buffer. With buf == NULL or
  * cap too small, *needed receives the size and AIWCRF_E_INVALID_ARG is returned for a short
  * non-NULL buffer. Layout: "AIWCRF01", u32 version (1), u32 n_features, i64 num_trees,
  * i64 num_nodes, i64 tree_offset[num_trees + 1], u64 node[num_nodes]. Node encoding: bit 63
@@ -483,14 +532,17 @@ int aiwcrf_forest_info(const aiwcrf_forest *forest, int64_t *num_trees, int64_t 
  * Trees are padded to an even node count with one unreachable leaf of value 0. */
 int aiwcrf_forest_serialize(const aiwcrf_forest *forest, void *buf, size_t cap, size_t *needed);
 
-/* Rebuild a forest on the current device from a blob (validated: AIWCRF_E_CORRUPT). */
+/* Resume from a checkpoint (see aiwcrf_forest_serialize): rebuild a forest on the current device
+ * from a blob (validated: AIWCRF_E_CORRUPT). Out-of-bag evaluation is not available on it. */
 int aiwcrf_forest_deserialize(const void *buf, size_t len, aiwcrf_forest **out);
 
-/* Waits for the device (work reading the forest may be in flight on any stream), then returns
- * the forest's memory to the stream-ordered pool. NULL is accepted. */
+/* Releases a forest (library resource management; no counterpart in the paper). Waits for the
+ * device (work reading the forest may be in flight on any stream), then returns the forest's
+ * memory to the stream-ordered pool. NULL is accepted. */
 int aiwcrf_forest_free(aiwcrf_forest *forest);
 
-/* Message of the last failing call on this host thread ("" if none). */
+/* Message of the last failing call on this host thread ("" if none; every call clears it on
+ * entry). Error reporting of this library; no counterpart in the paper. */
 const char *aiwcrf_last_error(void);
 
 /* Optional per-kernel timing with CUDA events recorded on the launching stream around each

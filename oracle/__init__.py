@@ -12,6 +12,8 @@ import subprocess
 import threading
 from dataclasses import dataclass
 
+from fractions import Fraction
+
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -189,6 +191,22 @@ class Forest:
         if lib().orc_oob(self._h, _ptr(X, _P_F32), N, _ptr(s, _P_I64), _ptr(c, _P_I32)) != 0:
             raise ValueError("X is not the training matrix")
         return s, c
+
+    def oob_error(self, X: np.ndarray, y: np.ndarray):
+        """Out-of-bag predictions (0 for rows in every tree's bootstrap), the mean squared error
+        over the rows out of bag for some tree (in the target's units, from the exact rational
+        mean of the Q32.32 differences, rounded once) and their number (Sec. III-B)."""
+        s, c = self.oob(X)
+        y = np.asarray(y, np.int64)
+        pred = np.zeros(len(s), np.int64)
+        tot, rows = 0, 0
+        for r in range(len(s)):
+            if c[r] > 0:
+                pred[r] = (2 * int(s[r]) + int(c[r])) // (2 * int(c[r]))
+                tot += (int(pred[r]) - int(y[r])) ** 2
+                rows += 1
+        mse = float(Fraction(tot, rows * 2 ** 64)) if rows else 0.0
+        return pred, mse, rows
 
     def select_device(self, kfeat: np.ndarray, size_class: int, device_ids):
         kfeat = np.ascontiguousarray(kfeat, dtype=np.float32)

@@ -48,7 +48,7 @@ class FitStats(C.Structure):
                 ("nodes_evaluated", C.c_int64), ("nodes_small", C.c_int64),
                 ("entries_evaluated_small", C.c_int64), ("entries_partitioned_small", C.c_int64),
                 ("n_features", C.c_int32), ("mtry", C.c_int32), ("rank_bytes", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("grower", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -103,7 +103,9 @@ class FitSchedule(C.Structure):
 
 class BatchTrace(C.Structure):
     _fields_ = [("t_formed_ns", C.c_int64), ("t_enqueued_ns", C.c_int64), ("t_done_ns", C.c_int64),
-                ("kernels", C.c_int32), ("generation", C.c_int32)]
+                ("kernels", C.c_int32), ("generation", C.c_int32), ("enqueue_cpu_ns", C.c_int64),
+                ("enqueue_voluntary_switches", C.c_int32), ("enqueue_involuntary_switches", C.c_int32),
+                ("poll_gap_max_ns", C.c_int64)]
 
 
 class RefitTrace(C.Structure):
@@ -112,6 +114,7 @@ class RefitTrace(C.Structure):
 
 
 EXPORTS = ["aiwcrf_fit", "aiwcrf_fit_subsets", "aiwcrf_predict", "aiwcrf_predict_sum", "aiwcrf_oob",
+           "aiwcrf_oob_error",
            "aiwcrf_round_mean", "aiwcrf_select_device", "aiwcrf_forest_stats", "aiwcrf_forest_info",
            "aiwcrf_forest_serialize", "aiwcrf_forest_deserialize", "aiwcrf_forest_free",
            "aiwcrf_last_error", "aiwcrf_profile_enable", "aiwcrf_profile_read",
@@ -123,7 +126,7 @@ EXPORTS = ["aiwcrf_fit", "aiwcrf_fit_subsets", "aiwcrf_predict", "aiwcrf_predict
            "aiwcrf_server_refit", "aiwcrf_server_pause", "aiwcrf_server_stats", "aiwcrf_server_run_load",
            "aiwcrf_server_trace", "aiwcrf_server_destroy", "aiwcrf_select_device_gated",
            "aiwcrf_fit_plan_create", "aiwcrf_fit_plan_run", "aiwcrf_fit_plan_tune", "aiwcrf_fit_plan_set_schedule",
-           "aiwcrf_fit_plan_free", "aiwcrf_profile_classes"]
+           "aiwcrf_fit_plan_free", "aiwcrf_profile_classes", "aiwcrf_set_grower"]
 
 _lib = None
 _lock = threading.Lock()
@@ -147,6 +150,8 @@ def load():
         L.aiwcrf_predict_sum.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
         L.aiwcrf_round_mean.argtypes = [_vp, C.c_int64, C.c_int64, _vp, _vp]
         L.aiwcrf_oob.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp]
+        L.aiwcrf_oob_error.argtypes = [_vp, _vp, _vp, C.c_int64, _vp, C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                       _vp]
         L.aiwcrf_surrogate_fit.argtypes = [C.POINTER(SurrogateParams), _vp, _vp, C.c_int64, C.c_int32, _vp,
                                            C.POINTER(_vp)]
         L.aiwcrf_surrogate_predict.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
@@ -172,6 +177,7 @@ def load():
         L.aiwcrf_profile_name.argtypes = [C.c_int32]
         L.aiwcrf_profile_name.restype = C.c_char_p
         L.aiwcrf_profile_num_classes.restype = C.c_int32
+        L.aiwcrf_set_grower.argtypes = [C.c_int32]
         L.aiwcrf_launch_count.restype = C.c_int64
         L.aiwcrf_server_create.argtypes = [C.POINTER(ServerParams), C.POINTER(FitParams), _vp, _vp, C.c_int64,
                                            C.c_int32, _vp, C.c_int32, C.POINTER(_vp)]
@@ -304,13 +310,15 @@ def aiwcrf_oob(forest: Forest, X, out_sum, out_count, stream=None):
     return out_sum, out_count
 
 
-def oob_error(sums: np.ndarray, counts: np.ndarray, y: np.ndarray) -> float:
-    """Out-of-bag mean squared error in the target's units (rows never out of bag are skipped).
-    The out-of-bag prediction of a row is the rounded mean of its out-of-bag leaf values."""
-    m = counts > 0
-    s, c = sums[m].astype(object), counts[m].astype(object)
-    pred = np.array([(2 * int(a) + int(b)) // (2 * int(b)) for a, b in zip(s, c)], dtype=np.float64)
-    return float(np.mean(((pred - y[m].astype(np.float64)) / 2.0 ** 32) ** 2))
+def aiwcrf_oob_error(forest: Forest, X, y, out_pred=None, stream=None):
+    """(mean squared out-of-bag error in the target's units, rows out of bag); fills out_pred
+    with the out-of-bag predictions when given."""
+    F, N = _shape(X)
+    mse = C.c_double(0.0)
+    rows = C.c_int64(0)
+    _check(load().aiwcrf_oob_error(forest.handle, _ptr(X), _ptr(y), N, _ptr(out_pred),
+                                   C.byref(mse), C.byref(rows), _stream(stream)))
+    return mse.value, rows.value
 
 
 class Surrogate:
@@ -601,6 +609,14 @@ def aiwcrf_profile_read() -> dict:
 
 def aiwcrf_launch_count() -> int:
     return int(load().aiwcrf_launch_count())
+
+
+GROWER_AUTO, GROWER_LEVEL, GROWER_TREE = 0, 1, 2
+
+
+def aiwcrf_set_grower(grower: int):
+    """Kernels that grow the trees of the following fits (GROWER_AUTO, GROWER_LEVEL, GROWER_TREE)."""
+    _check(load().aiwcrf_set_grower(grower))
 
 
 def params(num_trees: int, mtry: int, min_node_size: int, max_depth: int = 0, seed: int = 156,

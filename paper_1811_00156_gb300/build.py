@@ -58,7 +58,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
                 raise RuntimeError(f"nvcc failed: {' '.join(cmd)}")
     if force or jobs or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
+        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread", "-ldl"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             sys.stderr.write(res.stdout + res.stderr)

@@ -9,11 +9,15 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.cuh"
 
 namespace aiwcrf {
 
 static thread_local std::string g_last_error;
+
+void clear_last_error() { g_last_error.clear(); }
 
 void set_error(int code, const std::string &msg)
 {
@@ -148,12 +152,16 @@ cudaEvent_t take_event()
     return e;
 }
 
-const char *kProfNames[kProfNum] = {"rank",    "bootstrap", "level_big", "level_small",
-                                    "finalize", "pack",      "predict",   "select", "serve"};
+const char *kProfNames[kProfNum] = {"rank",    "bootstrap", "level_big", "level_small", "finalize",
+                                    "pack",    "predict",   "select",    "serve",       "tree",
+                                    "walk"};
 }  // namespace
 
+// Every kernel class bracket is also an NVTX range on the launching host thread (a profiler's
+// timeline groups each pass's launches under its name); profiling by events is separate.
 void prof_begin(cudaStream_t s, int cls)
 {
+    nvtxRangePushA(kProfNames[cls]);
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (!g_prof_on || !((g_prof_mask >> cls) & 1u)) return;
     cudaEvent_t e = take_event();
@@ -163,6 +171,7 @@ void prof_begin(cudaStream_t s, int cls)
 
 void prof_end(cudaStream_t s, int cls)
 {
+    nvtxRangePop();
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (!g_prof_on || !((g_prof_mask >> cls) & 1u)) return;
     for (size_t i = t_open.size(); i-- > 0;) {
@@ -553,6 +562,53 @@ int aiwcrf_oob(const aiwcrf_forest *forest, const float *X, int64_t n_rows, int6
     return sync_if(os.host || oc.host, s);
 }
 
+int aiwcrf_oob_error(const aiwcrf_forest *forest, const float *X, const int64_t *y, int64_t n_rows, int64_t *out_pred,
+                     double *out_mse, int64_t *out_rows, void *cuda_stream)
+{
+    g_last_error.clear();
+    if (!forest || !X || !y || !out_mse) return fail(AIWCRF_E_INVALID_ARG, "forest, X, y and out_mse must not be NULL");
+    if (forest->oob_rows == 0)
+        return fail(AIWCRF_E_INVALID_ARG, "out-of-bag evaluation needs a forest fitted by aiwcrf_fit in this process");
+    if (n_rows != forest->oob_rows) return fail(AIWCRF_E_INVALID_ARG, "n_rows differs from the training matrix");
+    int dev, rc;
+    if ((rc = current_device(&dev))) return rc;
+    if (dev != forest->device) return fail(AIWCRF_E_BAD_POINTER, "the forest lives on another device");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    InArg ax, ay;
+    OutArg op;
+    if ((rc = stage_in(ax, X, sizeof(float) * (size_t)forest->F * (size_t)n_rows, dev, s, "X"))) return rc;
+    if ((rc = stage_in(ay, y, sizeof(int64_t) * (size_t)n_rows, dev, s, "y"))) return rc;
+    if ((rc = stage_out(op, out_pred, sizeof(int64_t) * (size_t)n_rows, dev, s, "out_pred"))) return rc;
+    // one scratch block: sums, counts, per-CTA partial sums, the result and an error flag
+    const size_t parts = oob_error_parts(n_rows);
+    const size_t b_sum = 8 * (size_t)n_rows, b_cnt = (4 * (size_t)n_rows + 15) & ~(size_t)15;
+    const size_t bytes = b_sum + b_cnt + sizeof(OobPart) * parts + sizeof(OobResult) + 16;
+    unsigned char *blk = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&blk), bytes, s);
+    if (e != cudaSuccess) return fail(AIWCRF_E_OOM, "out-of-bag error scratch");
+    struct Free { void *p; cudaStream_t s; ~Free() { cudaFreeAsync(p, s); } } fr{blk, s};
+    int64_t *d_sum = reinterpret_cast<int64_t *>(blk);
+    int32_t *d_cnt = reinterpret_cast<int32_t *>(blk + b_sum);
+    OobPart *d_parts = reinterpret_cast<OobPart *>(blk + b_sum + b_cnt);
+    OobResult *d_res = reinterpret_cast<OobResult *>(d_parts + parts);
+    uint32_t *d_err = reinterpret_cast<uint32_t *>(d_res + 1);
+    if ((e = cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s)) != cudaSuccess) return cuda_fail(e, "oob_error");
+    if ((rc = oob_launch(forest, (const float *)ax.dev, n_rows, d_sum, d_cnt, s))) return rc;
+    if ((rc = oob_error_launch(d_sum, d_cnt, (const int64_t *)ay.dev, n_rows, (int64_t *)op.dev, d_parts, d_res, d_err, s)))
+        return rc;
+    if ((rc = finish_out(op))) return rc;
+    OobResult res;
+    uint32_t h_err = 0;
+    if ((e = cudaMemcpyAsync(&res, d_res, sizeof(OobResult), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(e, "oob_error");
+    if (h_err & kErrY) return fail(AIWCRF_E_INVALID_ARG, "a target value exceeds |y| <= 2^40");
+    *out_mse = res.mse;
+    if (out_rows) *out_rows = res.rows;
+    return AIWCRF_OK;
+}
+
 int aiwcrf_round_mean(const int64_t *sums, int64_t n, int64_t total_trees, int64_t *out, void *cuda_stream)
 {
     g_last_error.clear();
@@ -763,6 +819,7 @@ int aiwcrf_forest_free(aiwcrf_forest *forest)
 
 int aiwcrf_profile_enable(int32_t on)
 {
+    aiwcrf::clear_last_error();
     std::lock_guard<std::mutex> lk(g_prof_mu);
     g_prof_on = on != 0;
     return AIWCRF_OK;
@@ -770,6 +827,7 @@ int aiwcrf_profile_enable(int32_t on)
 
 int aiwcrf_profile_classes(uint32_t mask)
 {
+    aiwcrf::clear_last_error();
     std::lock_guard<std::mutex> lk(g_prof_mu);
     g_prof_mask = mask;
     return AIWCRF_OK;
@@ -777,6 +835,7 @@ int aiwcrf_profile_classes(uint32_t mask)
 
 int aiwcrf_profile_read(int32_t n, int64_t *launches, double *total_ms)
 {
+    aiwcrf::clear_last_error();
     std::vector<ProfRec> recs;
     {
         std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -805,6 +864,12 @@ const char *aiwcrf_profile_name(int32_t k)
 }
 
 int32_t aiwcrf_profile_num_classes(void) { return kProfNum; }
+
+int aiwcrf_set_grower(int32_t grower)
+{
+    aiwcrf::clear_last_error();
+    return aiwcrf::set_grower_mode(grower);
+}
 
 int64_t aiwcrf_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 

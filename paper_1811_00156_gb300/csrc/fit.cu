@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -33,6 +34,19 @@
 #include "internal.cuh"
 
 namespace aiwcrf {
+
+// runs the statement with RT the rank type of rank_bytes (1, 2 or 4 bytes per stored rank)
+#define AIWCRF_BY_RANK(rank_bytes, ...)                                       \
+    switch (rank_bytes) {                                                     \
+    case 1: { using RT = uint8_t; __VA_ARGS__; } break;                       \
+    case 2: { using RT = uint16_t; __VA_ARGS__; } break;                      \
+    default: { using RT = uint32_t; __VA_ARGS__; } break;                     \
+    }
+
+inline int rank_bytes_for(uint32_t max_card)
+{
+    return max_card <= 256u ? 1 : (max_card <= 65536u ? 2 : 4);
+}
 
 struct Entry {            // one group of identical in-bag rows of one tree
     uint32_t row;         // a row of the group (all its rows have the same features)
@@ -71,14 +85,13 @@ __global__ void key_init_kernel(const float *__restrict__ X, int64_t N, uint32_t
 // dense ranks of one sorted column per CTA: equal keys share a rank
 __global__ void __launch_bounds__(1024) dense_rank_kernel(const uint32_t *__restrict__ keys,
                                                           const uint32_t *__restrict__ idx, int64_t N,
-                                                          uint16_t *__restrict__ Rcol, float *__restrict__ vals,
+                                                          uint32_t *__restrict__ Rcol, float *__restrict__ vals,
                                                           uint32_t *__restrict__ card, uint32_t *err)
 {
     __shared__ uint32_t warp_tmp[32];
     const int f = blockIdx.x, tid = threadIdx.x;
     const size_t off = (size_t)f * (size_t)N;
     uint32_t running = 0;
-    int over = 0;
     for (int64_t t0 = 0; t0 < N; t0 += 1024) {
         const int64_t i = t0 + tid;
         const bool valid = i < N;
@@ -87,22 +100,18 @@ __global__ void __launch_bounds__(1024) dense_rank_kernel(const uint32_t *__rest
         uint32_t tot;
         const uint32_t incl = block_incl_scan(flag, warp_tmp, tot);
         if (valid) {
-            const uint32_t r = running + incl - 1u;
-            if (r >= 65536u) over = 1;
-            else {
-                Rcol[off + idx[off + i]] = (uint16_t)r;
-                if (flag) vals[off + r] = key_float(k);
-            }
+            const uint32_t r = running + incl - 1u;             // < N < 2^22
+            Rcol[off + idx[off + i]] = r;
+            if (flag) vals[off + r] = key_float(k);
         }
         running += tot;
     }
-    if (over) atomicOr(err, kErrCard);
     if (tid == 0) card[f] = running;
 }
 
 // Row-major copy of the ranks: the tried features of one row share one record.
 template <typename RT>
-__global__ void rank_rows_kernel(const uint16_t *__restrict__ Rcol, int64_t N, int F, RT *__restrict__ Rr)
+__global__ void rank_rows_kernel(const uint32_t *__restrict__ Rcol, int64_t N, int F, RT *__restrict__ Rr)
 {
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= N) return;
@@ -194,6 +203,7 @@ struct BootArgs {
     uint32_t *err;
     uint32_t *inbag;                // per tree ceil(N / 32) words: bit r set = row r drawn (or null)
     int64_t inbag_words;
+    int store_group;                // entries name their group (tree-resident growth) instead of a row
 };
 
 __global__ void __launch_bounds__(kBootThreads) bootstrap_kernel(BootArgs a)
@@ -274,7 +284,7 @@ __global__ void __launch_bounds__(kBootThreads) bootstrap_kernel(BootArgs a)
         const uint32_t incl = block_incl_scan(sw > 0 ? 1u : 0u, warp_tmp, tot);
         if (sw > 0) {
             Entry en;
-            en.row = rep; en.w = sw; en.wy = swy;
+            en.row = a.store_group ? g : rep; en.w = sw; en.wy = swy;
             // entries never outnumber the row capacity when it was sized from this data; a
             // replayed plan on data with more groups than it was built for flags it instead
             if ((int64_t)(running + incl - 1u) < a.row_cap) store_entry(&out[running + incl - 1u], en);
@@ -353,10 +363,11 @@ __device__ __forceinline__ bool node_stops(const LevelArgs &a, const NodeRec &nd
 // a3: the tried features of node (tree, depth, idx). Lane l of the warp evaluates the keys of
 // features l, l+32, ...; feature f is tried iff fewer than mtry features have a smaller
 // (key, index). Result: bit (f & 31) of mask[f >> 5].
-__device__ __forceinline__ void warp_mtry(const LevelArgs &a, uint32_t tg, uint32_t idx, uint32_t mask[4])
+__device__ __forceinline__ void warp_mtry_s(int F, int mtry, uint32_t depth, uint32_t seed_lo, uint32_t seed_hi,
+                                            uint32_t tg, uint32_t idx, uint32_t mask[4])
 {
     const int lane = threadIdx.x & 31;
-    const int F = a.F, nch = (F + 31) >> 5;
+    const int nch = (F + 31) >> 5;
     uint32_t key[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -364,12 +375,11 @@ __device__ __forceinline__ void warp_mtry(const LevelArgs &a, uint32_t tg, uint3
         mask[c] = 0u;
         const int f = c * 32 + lane;
         if (c < nch && f < F) {
-            const uint4 u = philox10(make_uint4(tg, (uint32_t)level_depth(a), idx, (kDomMtry << 16) | (uint32_t)(f >> 2)),
-                                     a.seed_lo, a.seed_hi);
+            const uint4 u = philox10(make_uint4(tg, depth, idx, (kDomMtry << 16) | (uint32_t)(f >> 2)), seed_lo, seed_hi);
             key[c] = uint4_word(u, f & 3);
         }
     }
-    if (a.mtry >= F) {
+    if (mtry >= F) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) mask[c] = __ballot_sync(kFull, c < nch && c * 32 + lane < F);
         return;
@@ -383,7 +393,7 @@ __device__ __forceinline__ void warp_mtry(const LevelArgs &a, uint32_t tg, uint3
             const uint32_t kg = __shfl_sync(kFull, key[0], g);
             cnt0 += (kg < key[0] || (kg == key[0] && g < lane)) ? 1u : 0u;
         }
-        mask[0] = __ballot_sync(kFull, lane < F && cnt0 < (uint32_t)a.mtry);
+        mask[0] = __ballot_sync(kFull, lane < F && cnt0 < (uint32_t)mtry);
         return;
     }
     uint32_t cnt[4] = {0u, 0u, 0u, 0u};
@@ -402,8 +412,13 @@ __device__ __forceinline__ void warp_mtry(const LevelArgs &a, uint32_t tg, uint3
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         const int f = c * 32 + lane;
-        mask[c] = __ballot_sync(kFull, c < nch && f < F && cnt[c] < (uint32_t)a.mtry);
+        mask[c] = __ballot_sync(kFull, c < nch && f < F && cnt[c] < (uint32_t)mtry);
     }
+}
+
+__device__ __forceinline__ void warp_mtry(const LevelArgs &a, uint32_t tg, uint32_t idx, uint32_t mask[4])
+{
+    warp_mtry_s(a.F, a.mtry, (uint32_t)level_depth(a), a.seed_lo, a.seed_hi, tg, idx, mask);
 }
 
 __device__ __forceinline__ long long shfl_xor_ll(long long v, int m)
@@ -852,6 +867,500 @@ __global__ void __launch_bounds__(kBigThreads, kBigCtasPerSm) level_big_kernel(L
 }
 
 // ------------------------------------------------------------------------------------------
+// Tree-resident growth. One CTA grows a whole tree, depth after depth, with the tree's entries
+// (sum w, sum w*y, group) in shared memory and a permutation of them that each depth
+// partitions into the children's segments. Node tables of the current and the next depth,
+// split results and the big nodes' per-feature candidates live in a global scratch slot of the
+// CTA. Per depth:
+//   A  work items, taken by the warps in turn: (big node, k-th tried feature) -- a warp-private
+//      shared-memory histogram of (sum w, sum w*y) per rank of that feature, a scan and the
+//      best candidate of that feature; then every small node (<= 32 entries), searched whole
+//      by one warp with the bitonic method of level_small_kernel;
+//   B  per big node, one warp: the best of its features' candidates, and the stable partition
+//      of its entries;
+//   C  all threads: an exclusive scan of the split flags numbers the children breadth first;
+//      every node is encoded into the tree's output and the next depth's nodes and big-node
+//      list are written.
+// It is used when every tree's entries fit in shared memory (grouped rows, one-byte ranks,
+// F <= 32) and replaces the level-synchronous path's three launches per depth. Trees are the
+// same node for node: the same BFS numbering, mtry draws, exact candidate comparison,
+// tie-breaks and leaf values.
+// ------------------------------------------------------------------------------------------
+constexpr int kTreeThreads = 256;
+constexpr int kTreeWarps = kTreeThreads / 32;
+constexpr int kTreeCtasPerSm = 4;      // resident CTAs per SM the tree kernel is compiled for
+constexpr int kTreeIlp = 8;            // rank loads in flight per lane in a histogram pass
+
+struct TNode {            // an active node of a CTA's tree at the current depth
+    uint16_t start, len;  // segment of the tree's entry permutation
+    uint32_t n;           // sum of multiplicities
+    int64_t S;            // sum of w*y
+    uint32_t idx;         // BFS index within the depth
+    uint32_t pad;
+};
+static_assert(sizeof(TNode) == 24, "TNode layout");
+
+struct TreeArgs {
+    const Entry *rows;            // bootstrap entries (row = group id), tree t at t * row_cap
+    const NodeRec *root;          // bootstrap root record per tree (entry count, n, S)
+    int64_t row_cap;
+    const uint8_t *Rg;            // group-major rank records [groups][F]
+    const float *vals;            // rank -> value tables [F][N]
+    int64_t N;
+    const uint32_t *card;         // values per feature (<= bins)
+    const uint32_t *tree_rng;     // global tree index per tree (Philox counter word 0)
+    int T, F, mtry, min_node, max_depth;
+    uint32_t seed_lo, seed_hi;
+    int ecap;                     // entry capacity of the shared-memory arrays (>= row_cap)
+    int bins;                     // histogram bins per warp (>= every card)
+    int big_cap;                  // big nodes per depth at most (ecap / 33 + 1)
+    TNode *nodes;                 // per CTA: 2 * ecap
+    SplitRes *res;                // per CTA: ecap
+    Cand *cands;                  // per CTA: big_cap * 32
+    uint64_t *out_nodes, *out_cnodes;   // per tree t at t * node_cap, BFS order
+    int64_t node_cap;
+    uint32_t *out_count;          // nodes per tree
+    GrowStats *stats;
+    uint32_t *levels;             // the deepest tree's depth count (atomicMax)
+};
+
+size_t tree_smem_bytes(int ecap, int bins, int big_cap)
+{
+    const size_t e = (size_t)ecap;
+    return 8 * e + 4 * e + ((2 * e + 15) & ~(size_t)15) + 2 * ((2 * e + 15) & ~(size_t)15) + ((e + 15) & ~(size_t)15) +
+           (size_t)kTreeWarps * (size_t)bins * 12 + 2 * (((size_t)big_cap * 2 + 15) & ~(size_t)15);
+}
+
+struct TreeSmem {
+    int64_t *wy;
+    uint32_t *w;
+    uint16_t *g;
+    uint16_t *ix[2];
+    uint8_t *flag;
+    uint32_t *bins;
+    uint16_t *big[2];
+};
+
+__device__ __forceinline__ TreeSmem tree_smem(unsigned char *base, const TreeArgs &a)
+{
+    const size_t e = (size_t)a.ecap;
+    TreeSmem m;
+    unsigned char *p = base;
+    m.wy = reinterpret_cast<int64_t *>(p); p += 8 * e;
+    m.w = reinterpret_cast<uint32_t *>(p); p += 4 * e;
+    m.g = reinterpret_cast<uint16_t *>(p); p += (2 * e + 15) & ~(size_t)15;
+    m.ix[0] = reinterpret_cast<uint16_t *>(p); p += (2 * e + 15) & ~(size_t)15;
+    m.ix[1] = reinterpret_cast<uint16_t *>(p); p += (2 * e + 15) & ~(size_t)15;
+    m.flag = p; p += (e + 15) & ~(size_t)15;
+    m.bins = reinterpret_cast<uint32_t *>(p); p += (size_t)kTreeWarps * (size_t)a.bins * 12;
+    m.big[0] = reinterpret_cast<uint16_t *>(p); p += ((size_t)a.big_cap * 2 + 15) & ~(size_t)15;
+    m.big[1] = reinterpret_cast<uint16_t *>(p);
+    return m;
+}
+
+__device__ __forceinline__ bool tnode_stops(const TreeArgs &a, uint32_t n, uint32_t depth)
+{
+    return n <= (uint32_t)a.min_node || (a.max_depth > 0 && (int)depth >= a.max_depth);
+}
+
+__device__ __forceinline__ bool tnode_big(const TreeArgs &a, const TNode &nd, uint32_t depth)
+{
+    return nd.len > (uint32_t)kSmallNodeRows && !tnode_stops(a, nd.n, depth);
+}
+
+// A small node (or a node that stops) searched whole by one warp: as small_node, on the tree's
+// shared-memory entries and the group records.
+__device__ __forceinline__ void tree_small_node(const TreeArgs &a, const TreeSmem &sm, const uint16_t *ix, uint16_t *ox,
+                                                const TNode &nd, uint32_t tg, uint32_t depth, SplitRes *res_j, int lane)
+{
+    if (tnode_stops(a, nd.n, depth)) {
+        if (lane == 0) write_leaf(res_j, 0, -2, round_mean(nd.S, nd.n));
+        return;
+    }
+    const int len = nd.len;
+    const int K = len <= 2 ? 2 : (int)(1u << (32 - __clz(len - 1)));
+    const int P = 32 / K;
+    const int pos = lane & (K - 1), seg = lane / K;
+    const bool valid = pos < len;
+    uint32_t ew = 0u, eg = 0u;
+    long long ewy = 0ll;
+    if (valid) {
+        const int ei = ix[nd.start + pos];
+        ew = sm.w[ei]; ewy = sm.wy[ei]; eg = sm.g[ei];
+    }
+    const uint8_t *rec = a.Rg + (size_t)eg * (size_t)a.F;
+
+    uint32_t mask[4];
+    warp_mtry_s(a.F, a.mtry, depth, a.seed_lo, a.seed_hi, tg, nd.idx, mask);
+    const int n_tried = __popc(mask[0]);
+    const int f_lane = lane < n_tried ? nth_feature(mask, lane) : -1;
+
+    Cand best = cand_none();
+    for (int q0 = 0; q0 < n_tried; q0 += P) {
+        const int qf = q0 + seg;
+        const int fs = __shfl_sync(kFull, f_lane, qf & 31);
+        const int f = qf < n_tried ? fs : -1;
+        const bool live = valid && f >= 0;
+        const uint32_t rank = live ? (uint32_t)__ldg(&rec[f]) : kRankSentinel;
+        const uint32_t rank0 = __shfl_sync(kFull, rank, lane & ~(K - 1));
+        if (__all_sync(kFull, !live || rank == rank0)) continue;
+        uint32_t key = (rank << 5) | (uint32_t)pos;
+        for (int k = 2; k <= K; k <<= 1) {
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                const uint32_t ok = __shfl_xor_sync(kFull, key, jj);
+                const bool asc = (pos & k) == 0;
+                const bool lower = (pos & jj) == 0;
+                key = ((lower == asc) ? (ok < key) : (ok > key)) ? ok : key;
+            }
+        }
+        const int src = (lane & ~(K - 1)) | (int)(key & 31u);
+        const uint32_t r = key >> 5;
+        uint32_t cw = __shfl_sync(kFull, live ? ew : 0u, src);
+        long long cs = __shfl_sync(kFull, live ? ewy : 0ll, src);
+        for (int o = 1; o < K; o <<= 1) {
+            const uint32_t tw = __shfl_up_sync(kFull, cw, o);
+            const long long ts = __shfl_up_sync(kFull, cs, o);
+            if (pos >= o) { cw += tw; cs += ts; }
+        }
+        uint32_t nr = __shfl_down_sync(kFull, r, 1);
+        if (pos == K - 1) nr = kRankSentinel;
+        if (f >= 0 && r != kRankSentinel && nr != kRankSentinel && r != nr) {
+            const i128_t delta = cand_delta(nd.n, nd.S, cw, cs);
+            if (delta != 0) {
+                Cand cd;
+                cd.h = cand_h(delta, nd.n, cw);
+                cd.f = f; cd.r = r; cd.nL = cw; cd.SL = cs;
+                if (cand_better(cd, best, nd.n, nd.S)) best = cd;
+            }
+        }
+    }
+    best = warp_best(best, nd.n, nd.S);
+    if (best.h < 0.0f) {
+        if (lane == 0) write_leaf(res_j, 0, -1, round_mean(nd.S, nd.n));
+        return;
+    }
+    // partition: entry i on lane i
+    const bool lv = lane < len;
+    const int el = lv ? ix[nd.start + lane] : 0;
+    const uint32_t rk = lv ? (uint32_t)__ldg(&a.Rg[(size_t)sm.g[el] * (size_t)a.F + best.f]) : kRankSentinel;
+    const bool left = lv && rk <= best.r;
+    const uint32_t bl = __ballot_sync(kFull, left), bv = __ballot_sync(kFull, lv);
+    const uint32_t lenL = __popc(bl), lt = lanemask_lt();
+    const uint32_t pos_out = left ? __popc(bl & lt) : lenL + __popc(bv & ~bl & lt);
+    if (lv) ox[nd.start + pos_out] = (uint16_t)el;
+    if (lane == 0) {
+        SplitRes sr;
+        sr.feature = best.f; sr.rank = best.r;
+        sr.thr_bits = __float_as_uint(a.vals[(size_t)best.f * (size_t)a.N + best.r]);
+        sr.nL = best.nL; sr.lenL = lenL; sr.pad = 0u; sr.v = best.SL;
+        *res_j = sr;
+    }
+}
+
+// Work item (big node, k-th tried feature): a warp-private histogram over the feature's ranks,
+// its scan, and the best candidate of the feature.
+__device__ __forceinline__ void tree_big_item(const TreeArgs &a, const TreeSmem &sm, const uint16_t *ix, const TNode &nd,
+                                              uint32_t tg, uint32_t depth, int k, uint32_t *bins, Cand *out, int lane)
+{
+    uint32_t mask[4];
+    warp_mtry_s(a.F, a.mtry, depth, a.seed_lo, a.seed_hi, tg, nd.idx, mask);
+    const int f = nth_feature(mask, k);
+    const int card = (int)__ldg(&a.card[f]);
+    uint32_t *bw = bins, *blo = bins + a.bins;
+    int32_t *bhi = reinterpret_cast<int32_t *>(bins + 2 * a.bins);
+    for (int b = lane; b < card; b += 32) { bw[b] = 0u; blo[b] = 0u; bhi[b] = 0; }
+    __syncwarp();
+    const int len = nd.len;
+    const uint8_t *Rf = a.Rg + f;
+    for (int base = 0; base < len; base += 32 * kTreeIlp) {
+        uint32_t rk[kTreeIlp], wv[kTreeIlp], lov[kTreeIlp];
+        int32_t hiv[kTreeIlp];
+#pragma unroll
+        for (int u = 0; u < kTreeIlp; ++u) {
+            const int i = base + u * 32 + lane;
+            wv[u] = 0u; rk[u] = 0u; lov[u] = 0u; hiv[u] = 0;
+            if (i < len) {
+                const int e = ix[nd.start + i];
+                const int64_t y = sm.wy[e];
+                wv[u] = sm.w[e];
+                lov[u] = (uint32_t)(uint64_t)y;
+                hiv[u] = (int32_t)(y >> 32);
+                rk[u] = (uint32_t)__ldg(&Rf[(size_t)sm.g[e] * (size_t)a.F]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kTreeIlp; ++u) {
+            if (wv[u]) {
+                atomicAdd(&bw[rk[u]], wv[u]);
+                const uint32_t old = atomicAdd(&blo[rk[u]], lov[u]);
+                const int32_t carry = (old + lov[u] < old) ? 1 : 0;
+                if (hiv[u] + carry != 0) atomicAdd(&bhi[rk[u]], hiv[u] + carry);
+            }
+        }
+    }
+    __syncwarp();
+    // lane l scans bins [l * per, (l + 1) * per): its totals, a warp exclusive scan, then its
+    // present bins in order
+    const int per = (card + 31) >> 5;
+    const int b0 = min(card, lane * per), b1 = min(card, b0 + per);
+    uint32_t lw = 0u;
+    long long ls = 0ll;
+    for (int b = b0; b < b1; ++b) {
+        lw += bw[b];
+        ls += ((long long)bhi[b] << 32) + (long long)blo[b];
+    }
+    uint32_t xw = lw;
+    long long xs = ls;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t tw = __shfl_up_sync(kFull, xw, o);
+        const long long ts = __shfl_up_sync(kFull, xs, o);
+        if (lane >= o) { xw += tw; xs += ts; }
+    }
+    uint32_t nL = xw - lw;
+    long long SL = xs - ls;
+    Cand best = cand_none();
+    for (int b = b0; b < b1; ++b) {
+        const uint32_t cw = bw[b];
+        if (!cw) continue;
+        nL += cw;
+        SL += ((long long)bhi[b] << 32) + (long long)blo[b];
+        if (nL >= nd.n) continue;                               // the last present rank
+        const i128_t delta = cand_delta(nd.n, nd.S, nL, SL);
+        if (delta == 0) continue;
+        Cand cd;
+        cd.h = cand_h(delta, nd.n, nL);
+        cd.f = f; cd.r = (uint32_t)b; cd.nL = nL; cd.SL = SL;
+        if (cand_better(cd, best, nd.n, nd.S)) best = cd;
+    }
+    best = warp_best(best, nd.n, nd.S);
+    if (lane == 0) *out = best;
+    __syncwarp();                                               // the bins are reused next
+}
+
+// A big node's decision from its features' candidates, then the stable partition of its entries.
+__device__ __forceinline__ void tree_big_split(const TreeArgs &a, const TreeSmem &sm, const uint16_t *ix, uint16_t *ox,
+                                               const TNode &nd, int m, const Cand *cands, SplitRes *res_j, int lane)
+{
+    Cand c = lane < m ? cands[lane] : cand_none();
+    c = warp_best(c, nd.n, nd.S);
+    if (c.h < 0.0f) {
+        if (lane == 0) write_leaf(res_j, 0, -1, round_mean(nd.S, nd.n));
+        return;
+    }
+    const int len = nd.len;
+    const uint8_t *Rf = a.Rg + c.f;
+    uint32_t cnt = 0u;
+    for (int base = 0; base < len; base += 32 * kTreeIlp) {
+        uint32_t rk[kTreeIlp];
+#pragma unroll
+        for (int u = 0; u < kTreeIlp; ++u) {
+            const int i = base + u * 32 + lane;
+            rk[u] = i < len ? (uint32_t)__ldg(&Rf[(size_t)sm.g[ix[nd.start + i]] * (size_t)a.F]) : kRankSentinel;
+        }
+#pragma unroll
+        for (int u = 0; u < kTreeIlp; ++u) {
+            const int i = base + u * 32 + lane;
+            if (i < len) {
+                const bool l = rk[u] <= c.r;
+                sm.flag[nd.start + i] = l ? 1 : 0;
+                cnt += l ? 1u : 0u;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
+    __syncwarp();
+    const uint32_t lenL = cnt, lt = lanemask_lt();
+    uint32_t run_l = 0u, run_r = 0u;
+    for (int b0 = 0; b0 < len; b0 += 32) {
+        const int i = b0 + lane;
+        const bool v = i < len;
+        const bool l = v && sm.flag[nd.start + i];
+        const uint32_t bl = __ballot_sync(kFull, l), bv = __ballot_sync(kFull, v);
+        if (v) {
+            const uint32_t p = l ? run_l + __popc(bl & lt) : lenL + run_r + __popc(bv & ~bl & lt);
+            ox[nd.start + p] = ix[nd.start + i];
+        }
+        run_l += __popc(bl);
+        run_r += __popc(bv & ~bl);
+    }
+    if (lane == 0) {
+        SplitRes sr;
+        sr.feature = c.f; sr.rank = c.r;
+        sr.thr_bits = __float_as_uint(a.vals[(size_t)c.f * (size_t)a.N + c.r]);
+        sr.nL = c.nL; sr.lenL = lenL; sr.pad = 0u; sr.v = c.SL;
+        *res_j = sr;
+    }
+}
+
+__global__ void __launch_bounds__(kTreeThreads, kTreeCtasPerSm) tree_grow_kernel(TreeArgs a)
+{
+    extern __shared__ __align__(16) unsigned char tree_sm[];
+    __shared__ uint32_t warp_tmp[32];
+    __shared__ unsigned long long red[6][kTreeWarps];
+    __shared__ uint32_t s_nb[2];
+    const TreeSmem sm = tree_smem(tree_sm, a);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    TNode *const nodes0 = a.nodes + (size_t)blockIdx.x * 2 * (size_t)a.ecap;
+    TNode *const nodes1 = nodes0 + a.ecap;
+    SplitRes *const res = a.res + (size_t)blockIdx.x * (size_t)a.ecap;
+    Cand *const cands = a.cands + (size_t)blockIdx.x * (size_t)a.big_cap * 32;
+    uint32_t *const wbins = sm.bins + (size_t)warp * (size_t)a.bins * 3;
+    const int m = a.mtry < a.F ? a.mtry : a.F;
+    unsigned long long v[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+    uint32_t max_levels = 0u;
+
+    for (int t = blockIdx.x; t < a.T; t += gridDim.x) {
+        __syncthreads();                                        // the previous tree is done
+        const NodeRec root = a.root[t];
+        const int len0 = (int)root.len;
+        const Entry *rin = a.rows + (size_t)t * (size_t)a.row_cap;
+        for (int i = tid; i < len0; i += kTreeThreads) {
+            const Entry e = load_entry(rin + i);
+            sm.wy[i] = e.wy; sm.w[i] = e.w; sm.g[i] = (uint16_t)e.row; sm.ix[0][i] = (uint16_t)i;
+        }
+        if (tid == 0) {
+            TNode r;
+            r.start = 0; r.len = (uint16_t)len0; r.n = root.n; r.S = root.S; r.idx = 0u; r.pad = 0u;
+            nodes0[0] = r;
+            const bool big = tnode_big(a, r, 0u);
+            s_nb[0] = big ? 1u : 0u;
+            sm.big[0][0] = 0;
+        }
+        const uint32_t tg = a.tree_rng[t];
+        uint64_t *onodes = a.out_nodes + (size_t)t * (size_t)a.node_cap;
+        uint64_t *ocnodes = a.out_cnodes + (size_t)t * (size_t)a.node_cap;
+        uint32_t C = 1u, base = 0u, depth = 0u;
+        int p = 0;
+        __syncthreads();
+        while (C > 0u) {
+            const TNode *cn = p ? nodes1 : nodes0;
+            TNode *nx = p ? nodes0 : nodes1;
+            const uint16_t *ix = sm.ix[p];
+            uint16_t *ox = sm.ix[p ^ 1];
+            const uint16_t *big = sm.big[p];
+            const uint32_t nb = s_nb[p];
+            // A: big-node feature items first (they are the long ones), then the small nodes
+            const uint32_t items = nb * (uint32_t)m + C;
+            for (uint32_t j = (uint32_t)warp; j < items; j += kTreeWarps) {
+                if (j < nb * (uint32_t)m) {
+                    const uint32_t bi = j / (uint32_t)m, k = j - bi * (uint32_t)m;
+                    const TNode nd = cn[big[bi]];
+                    tree_big_item(a, sm, ix, nd, tg, depth, (int)k, wbins, &cands[(size_t)bi * 32 + k], lane);
+                } else {
+                    const uint32_t i = j - nb * (uint32_t)m;
+                    const TNode nd = cn[i];
+                    if (tnode_big(a, nd, depth)) continue;
+                    tree_small_node(a, sm, ix, ox, nd, tg, depth, &res[i], lane);
+                }
+            }
+            __syncthreads();
+            // B: big nodes' decisions and partitions
+            for (uint32_t bi = (uint32_t)warp; bi < nb; bi += kTreeWarps) {
+                const uint32_t i = big[bi];
+                tree_big_split(a, sm, ix, ox, cn[i], m, &cands[(size_t)bi * 32], &res[i], lane);
+            }
+            __syncthreads();
+            // C: number the children, encode every node, list the next depth
+            uint32_t run_split = 0u, run_big = 0u;
+            uint16_t *nbig = sm.big[p ^ 1];
+            for (uint32_t i0 = 0; i0 < C; i0 += kTreeThreads) {
+                const uint32_t i = i0 + (uint32_t)tid;
+                const bool valid = i < C;
+                SplitRes r;
+                TNode nd;
+                r.feature = -2;
+                if (valid) { r = res[i]; nd = cn[i]; }
+                const bool split = valid && r.feature >= 0;
+                uint32_t tot;
+                const uint32_t loc = run_split + block_incl_scan(split ? 1u : 0u, warp_tmp, tot) - (split ? 1u : 0u);
+                TNode L, R;
+                bool bigL = false, bigR = false;
+                if (valid) {
+                    const uint32_t pos = base + i;
+                    const uint32_t left = base + C + 2u * loc;
+                    const uint64_t node = split ? encode_split(r.feature, left, r.thr_bits) : encode_leaf(r.v);
+                    onodes[pos] = node;
+                    ocnodes[pos] = split ? encode_split_coded(r.feature, left, r.rank) : node;
+                    if (split) {
+                        L.start = nd.start; L.len = (uint16_t)r.lenL; L.n = r.nL; L.S = r.v; L.idx = 2u * loc; L.pad = 0u;
+                        R.start = (uint16_t)(nd.start + r.lenL); R.len = (uint16_t)(nd.len - r.lenL); R.n = nd.n - r.nL;
+                        R.S = nd.S - r.v; R.idx = 2u * loc + 1u; R.pad = 0u;
+                        nx[2u * loc] = L;
+                        nx[2u * loc + 1u] = R;
+                        bigL = tnode_big(a, L, depth + 1u);
+                        bigR = tnode_big(a, R, depth + 1u);
+                    }
+                    const bool evald = r.feature != -2;
+                    const bool small = nd.len <= (uint32_t)kSmallNodeRows;
+                    v[0] += evald ? nd.len : 0u;
+                    v[1] += split ? nd.len : 0u;
+                    v[2] += evald ? 1u : 0u;
+                    v[3] += (evald && small) ? 1u : 0u;
+                    v[4] += (evald && small) ? nd.len : 0u;
+                    v[5] += (split && small) ? nd.len : 0u;
+                }
+                const uint32_t nbi = (bigL ? 1u : 0u) + (bigR ? 1u : 0u);
+                uint32_t totb;
+                uint32_t bpos = run_big + block_incl_scan(nbi, warp_tmp, totb) - nbi;
+                if (bigL) nbig[bpos++] = (uint16_t)(2u * loc);
+                if (bigR) nbig[bpos] = (uint16_t)(2u * loc + 1u);
+                run_split += tot;
+                run_big += totb;
+            }
+            if (tid == 0) s_nb[p ^ 1] = run_big;
+            base += C;
+            C = 2u * run_split;
+            ++depth;
+            p ^= 1;
+            __syncthreads();
+        }
+        if (tid == 0) a.out_count[t] = base;
+        max_levels = max(max_levels, depth);
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) red[k][warp] = v[k];
+    }
+    __syncthreads();
+    if (tid < 6) {
+        unsigned long long sum = 0;
+        for (int w = 0; w < kTreeWarps; ++w) sum += red[tid][w];
+        if (sum) atomicAdd(&a.stats->entries_evaluated + tid, sum);   // GrowStats field order
+    }
+    if (tid == 0 && max_levels) atomicMax(a.levels, max_levels);
+}
+
+// Rg[g][f] = the rank record of group g (all its rows share it)
+__global__ void group_records_kernel(const uint8_t *__restrict__ Rr, int F, const uint32_t *__restrict__ grp_off,
+                                     const uint32_t *__restrict__ grp_rows, const uint32_t *n_groups, uint8_t *__restrict__ Rg)
+{
+    const uint32_t G = *n_groups;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)G * F) return;
+    const uint32_t g = (uint32_t)(i / F), f = (uint32_t)(i - (int64_t)g * F);
+    Rg[i] = Rr[(size_t)grp_rows[grp_off[g]] * (size_t)F + f];
+}
+
+// copy each tree's nodes from its output slot into the forest (and pad an odd count)
+__global__ void tree_place_kernel(const uint64_t *slot_nodes, const uint64_t *slot_cnodes, int64_t node_cap,
+                                  const uint32_t *counts, uint64_t *const *tree_dst, uint64_t *const *tree_cdst)
+{
+    const int t = blockIdx.x;
+    const uint32_t c = counts[t];
+    const uint64_t *sn = slot_nodes + (size_t)t * (size_t)node_cap, *sc = slot_cnodes + (size_t)t * (size_t)node_cap;
+    uint64_t *dn = tree_dst[t], *dc = tree_cdst[t];
+    for (uint32_t i = threadIdx.x; i < c; i += blockDim.x) { dn[i] = sn[i]; dc[i] = sc[i]; }
+    if (threadIdx.x == 0 && (c & 1u)) { dn[c] = 1ull << 63; dc[c] = 1ull << 63; }
+}
+
+// ------------------------------------------------------------------------------------------
 // exclusive scans of flag arrays (the grouping of identical feature vectors)
 // ------------------------------------------------------------------------------------------
 
@@ -1111,6 +1620,18 @@ __global__ void check_y_kernel(const int64_t *y, int64_t n, uint32_t *err)
 // ------------------------------------------------------------------------------------------
 // host driver
 // ------------------------------------------------------------------------------------------
+static std::atomic<int> g_grower{AIWCRF_GROWER_AUTO};
+
+int set_grower_mode(int mode)
+{
+    if (mode != AIWCRF_GROWER_AUTO && mode != AIWCRF_GROWER_LEVEL && mode != AIWCRF_GROWER_TREE)
+        return fail(AIWCRF_E_INVALID_ARG, "grower: 0 (automatic), 1 (level-synchronous) or 2 (tree-resident)");
+    g_grower.store(mode);
+    return AIWCRF_OK;
+}
+
+int grower_mode() { return g_grower.load(); }
+
 namespace {
 
 struct DevBuf {                // stream-ordered scratch allocation
@@ -1170,7 +1691,6 @@ int check_err_flags(uint32_t err)
 {
     if (err & kErrNaN) return fail(AIWCRF_E_NAN_INPUT, "NaN in the training features");
     if (err & kErrY) return fail(AIWCRF_E_INVALID_ARG, "a target value exceeds |y| <= 2^40");
-    if (err & kErrCard) return fail(AIWCRF_E_LIMIT, "a feature column has more than 65,536 distinct values");
     if (err & kErrBootOverflow) return fail(AIWCRF_E_LIMIT, "a bootstrap multiplicity exceeded 255");
     if (err & kErrTimeout) return fail(AIWCRF_E_TIMEOUT, "a bounded device wait gave up");
     if (err & kErrCapacity)
@@ -1196,8 +1716,13 @@ struct PackIn {
     const float *d_vals;
     const uint32_t *d_card;
     uint32_t max_card;
-    bool rank8;
+    int rank_bytes;
     uint32_t n_groups;
+    // tree-resident growth: nodes in per-tree slots of slot_cap (BFS order), counts in tree_base
+    const uint64_t *slot_nodes = nullptr, *slot_cnodes = nullptr;
+    int64_t slot_cap = 0;
+    const uint32_t *d_levels = nullptr;   // when set, the level count is read here
+    int grower = 1;                       // 1 level-synchronous, 2 tree-resident
 };
 
 // One forest per tree group, trees padded to an even node count (16-byte aligned); nodes placed
@@ -1212,6 +1737,8 @@ int package_forests(const PackIn &in, cudaStream_t s, std::vector<aiwcrf_forest 
     AIWCRF_CUDA(cudaMemcpyAsync(h_tot.data(), in.tree_base, sizeof(uint32_t) * (size_t)T, cudaMemcpyDeviceToHost, s));
     GrowStats hs;
     AIWCRF_CUDA(cudaMemcpyAsync(&hs, in.d_stats, sizeof(GrowStats), cudaMemcpyDeviceToHost, s));
+    uint32_t h_levels = (uint32_t)in.levels;
+    if (in.d_levels) AIWCRF_CUDA(cudaMemcpyAsync(&h_levels, in.d_levels, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     AIWCRF_CUDA(cudaStreamSynchronize(s));
 
     std::vector<aiwcrf_forest *> forests((size_t)G, nullptr);
@@ -1256,10 +1783,11 @@ int package_forests(const PackIn &in, cudaStream_t s, std::vector<aiwcrf_forest 
         fr->stats.num_trees = Tper;
         fr->stats.total_nodes = 0;
         for (int64_t k = 0; k < Tper; ++k) fr->stats.total_nodes += h_tot[(size_t)(g * Tper + k)];
-        fr->stats.levels = in.levels;
+        fr->stats.levels = (int64_t)h_levels;
+        fr->stats.grower = in.grower;
         fr->stats.n_features = F;
         fr->stats.mtry = in.p->mtry;
-        fr->stats.rank_bytes = in.rank8 ? 1 : 2;
+        fr->stats.rank_bytes = in.rank_bytes;
         fr->stats.groups = in.n_groups;
         if (G == 1) {
             fr->stats.entries_evaluated = (int64_t)hs.entries_evaluated;
@@ -1275,10 +1803,16 @@ int package_forests(const PackIn &in, cudaStream_t s, std::vector<aiwcrf_forest 
     AIWCRF_CUDA(cudaMemcpyAsync(d_dst, h_dst.data(), sizeof(uint64_t *) * (size_t)T, cudaMemcpyHostToDevice, s));
     AIWCRF_CUDA(cudaMemcpyAsync(d_dst + T, h_cdst.data(), sizeof(uint64_t *) * (size_t)T, cudaMemcpyHostToDevice, s));
     prof_begin(s, kProfPack);
-    pack_kernel<<<(unsigned)((in.packed_n + 255) / 256), 256, 0, s>>>(in.packed, (int64_t)in.packed_n, d_dst, d_dst + T);
-    AIWCRF_LAUNCH_CHECK("pack_kernel");
-    pad_kernel<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(in.tree_base, T, d_dst, d_dst + T);
-    AIWCRF_LAUNCH_CHECK("pad_kernel");
+    if (in.slot_nodes) {
+        tree_place_kernel<<<(unsigned)T, 256, 0, s>>>(in.slot_nodes, in.slot_cnodes, in.slot_cap, in.tree_base, d_dst,
+                                                      d_dst + T);
+        AIWCRF_LAUNCH_CHECK("tree_place_kernel");
+    } else {
+        pack_kernel<<<(unsigned)((in.packed_n + 255) / 256), 256, 0, s>>>(in.packed, (int64_t)in.packed_n, d_dst, d_dst + T);
+        AIWCRF_LAUNCH_CHECK("pack_kernel");
+        pad_kernel<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(in.tree_base, T, d_dst, d_dst + T);
+        AIWCRF_LAUNCH_CHECK("pad_kernel");
+    }
     prof_end(s, kProfPack);
     for (auto fr : forests)
         if ((rc = forest_build_compact(fr, s)) != AIWCRF_OK) return rc;
@@ -1330,7 +1864,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     AIWCRF_CUDA(cudaMemsetAsync(d_counters, 0, 4 * sizeof(uint32_t), s));
 
     // a1: presort and rank
-    uint16_t *d_R = sc.get<uint16_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
+    uint32_t *d_R = sc.get<uint32_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
     float *d_vals = sc.get<float>((size_t)F * (size_t)N, &rc); if (rc) return rc;
     uint32_t *d_card = sc.get<uint32_t>((size_t)F, &rc); if (rc) return rc;
     // sort buffers (one spare word: the grouping's scan writes its total at [N])
@@ -1359,8 +1893,9 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         if ((rc = check_err_flags(h_err)) != AIWCRF_OK) return rc;
         max_card = *std::max_element(h_card.begin(), h_card.end());
     }
-    const bool rank8 = max_card <= 256;
-    void *d_Rr = rank8 ? (void *)sc.get<uint8_t>((size_t)F * (size_t)N, &rc) : (void *)sc.get<uint16_t>((size_t)F * (size_t)N, &rc);
+    const int rank_bytes = rank_bytes_for(max_card);
+    const bool rank8 = rank_bytes == 1;
+    void *d_Rr = sc.get<uint8_t>((size_t)F * (size_t)N * (size_t)rank_bytes, &rc);
     if (rc) return rc;
 
     // grouping of identical feature vectors
@@ -1369,19 +1904,13 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     {
         const unsigned rb = (unsigned)((N + 255) / 256);
         prof_begin(s, kProfRank);
-        if (rank8) {
-            rank_rows_kernel<uint8_t><<<rb, 256, 0, s>>>(d_R, N, F, (uint8_t *)d_Rr);
-            hash_rows_kernel<uint8_t><<<rb, 256, 0, s>>>((const uint8_t *)d_Rr, N, F, kA, vA);
-        } else {
-            rank_rows_kernel<uint16_t><<<rb, 256, 0, s>>>(d_R, N, F, (uint16_t *)d_Rr);
-            hash_rows_kernel<uint16_t><<<rb, 256, 0, s>>>((const uint16_t *)d_Rr, N, F, kA, vA);
-        }
+        AIWCRF_BY_RANK(rank_bytes, rank_rows_kernel<RT><<<rb, 256, 0, s>>>(d_R, N, F, (RT *)d_Rr);
+                                   hash_rows_kernel<RT><<<rb, 256, 0, s>>>((const RT *)d_Rr, N, F, kA, vA))
         count_launches(1);
         AIWCRF_LAUNCH_CHECK("rank_rows / hash_rows");
         if ((rc = radix_sort_segments(kA, vA, kB, vB, N, 1, N, hist, s)) != AIWCRF_OK) return rc;
         // group starts (flags in kB), their exclusive scan (in vB), offsets
-        if (rank8) group_flags_kernel<uint8_t><<<rb, 256, 0, s>>>((const uint8_t *)d_Rr, N, F, kA, vA, kB);
-        else group_flags_kernel<uint16_t><<<rb, 256, 0, s>>>((const uint16_t *)d_Rr, N, F, kA, vA, kB);
+        AIWCRF_BY_RANK(rank_bytes, group_flags_kernel<RT><<<rb, 256, 0, s>>>((const RT *)d_Rr, N, F, kA, vA, kB))
         const int gblocks = (int)((N + kFlagTile - 1) / kFlagTile);
         flag_scan_reduce_kernel<<<gblocks, kScanThreads, 0, s>>>(kB, N, hist);
         scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(hist, gblocks);
@@ -1484,6 +2013,27 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         AIWCRF_CUDA(cudaMemcpyAsync(d_cnt, &c0, sizeof(LevelCounts), cudaMemcpyHostToDevice, s));
     }
 
+    // Tree-resident growth when every tree's entries fit in shared memory: one-byte ranks,
+    // F <= 32, group ids and entry offsets in 16 bits
+    const int tree_bins = (int)std::max<uint32_t>(max_card, 1u);
+    const int tree_ecap = (int)std::max<int64_t>(row_cap, 1);
+    const int tree_big_cap = tree_ecap / (kSmallNodeRows + 1) + 1;
+    const size_t tree_smem = tree_smem_bytes(tree_ecap, tree_bins, tree_big_cap);
+    const int gmode = grower_mode();
+    const bool tree_fits = rank8 && F <= 32 && n_groups <= 65535u && row_cap <= 65535 &&
+                           tree_smem + 1024 <= (size_t)max_smem_optin;
+    if (gmode == AIWCRF_GROWER_TREE && !tree_fits)
+        return fail(AIWCRF_E_LIMIT, "tree-resident growth needs one-byte ranks, F <= 32 and a tree's entries in shared memory");
+    const bool use_tree = tree_fits && gmode != AIWCRF_GROWER_LEVEL;
+    uint8_t *d_Rg = nullptr;
+    if (use_tree) {
+        d_Rg = sc.get<uint8_t>((size_t)n_groups * (size_t)F, &rc); if (rc) return rc;
+        const int64_t cells = (int64_t)n_groups * F;
+        group_records_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>((const uint8_t *)d_Rr, F, grp_off, grp_rows,
+                                                                           d_counters + 2, d_Rg);
+        AIWCRF_LAUNCH_CHECK("group_records_kernel");
+    }
+
     {
         const int boot_smem_words = std::min<int>((max_smem_optin - 2048) / 4, 56 * 1024);
         const uint32_t words = (uint32_t)((N + 3) / 4);
@@ -1506,10 +2056,58 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         ba.small_list = small_a; ba.big_list = big_a; ba.counters = d_cnt->n_list[0]; ba.err = d_err;
         ba.inbag = d_inbag; ba.inbag_words = inbag_words;
         ba.G_ptr = nullptr;
+        ba.store_group = use_tree ? 1 : 0;
         prof_begin(s, kProfBoot);
         bootstrap_kernel<<<(unsigned)T, kBootThreads, smem_bytes, s>>>(ba);
         AIWCRF_LAUNCH_CHECK("bootstrap_kernel");
         prof_end(s, kProfBoot);
+    }
+
+    if (use_tree) {
+        // one CTA per tree at a time, as many as fit (a background fit: at most ctas_per_sm per SM)
+        AIWCRF_CUDA(cudaFuncSetAttribute(tree_grow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tree_smem));
+        int occ = 0;
+        AIWCRF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tree_grow_kernel, kTreeThreads, tree_smem));
+        if (occ < 1) return fail(AIWCRF_E_LIMIT, "tree-resident growth: no CTA fits on an SM");
+        if (p.ctas_per_sm > 0) occ = std::min<int>(occ, p.ctas_per_sm);
+        const int64_t grid = std::min<int64_t>(T, (int64_t)occ * dev_sms);
+        const int64_t node_cap = 2 * (int64_t)tree_ecap;
+        TNode *t_nodes = sc.get<TNode>((size_t)grid * 2 * (size_t)tree_ecap, &rc); if (rc) return rc;
+        SplitRes *t_res = sc.get<SplitRes>((size_t)grid * (size_t)tree_ecap, &rc); if (rc) return rc;
+        Cand *t_cands = sc.get<Cand>((size_t)grid * (size_t)tree_big_cap * 32, &rc); if (rc) return rc;
+        uint64_t *slot_nodes = sc.get<uint64_t>((size_t)T * (size_t)node_cap, &rc); if (rc) return rc;
+        uint64_t *slot_cnodes = sc.get<uint64_t>((size_t)T * (size_t)node_cap, &rc); if (rc) return rc;
+        uint32_t *counts = sc.get<uint32_t>((size_t)T + 1, &rc); if (rc) return rc;
+        uint32_t *levels = counts + T;
+        AIWCRF_CUDA(cudaMemsetAsync(levels, 0, sizeof(uint32_t), s));
+        TreeArgs ta;
+        ta.rows = rows_a; ta.root = nodes_cur; ta.row_cap = row_cap; ta.Rg = d_Rg; ta.vals = d_vals; ta.N = N;
+        ta.card = d_card; ta.tree_rng = d_rng; ta.T = (int)T; ta.F = F; ta.mtry = p.mtry;
+        ta.min_node = p.min_node_size; ta.max_depth = p.max_depth;
+        ta.seed_lo = (uint32_t)p.seed; ta.seed_hi = (uint32_t)(p.seed >> 32);
+        ta.ecap = tree_ecap; ta.bins = tree_bins; ta.big_cap = tree_big_cap;
+        ta.nodes = t_nodes; ta.res = t_res; ta.cands = t_cands;
+        ta.out_nodes = slot_nodes; ta.out_cnodes = slot_cnodes; ta.node_cap = node_cap; ta.out_count = counts;
+        ta.stats = d_stats; ta.levels = levels;
+        prof_begin(s, kProfTree);
+        tree_grow_kernel<<<(unsigned)grid, kTreeThreads, tree_smem, s>>>(ta);
+        AIWCRF_LAUNCH_CHECK("tree_grow_kernel");
+        prof_end(s, kProfTree);
+        uint32_t h_err = 0;
+        AIWCRF_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        AIWCRF_CUDA(cudaStreamSynchronize(s));
+        if ((rc = check_err_flags(h_err)) != AIWCRF_OK) return rc;
+        PackIn pin;
+        pin.p = &p; pin.T = T; pin.Tper = Tper; pin.G = G; pin.N = N; pin.F = F; pin.device = device;
+        pin.tree_base = counts; pin.d_stats = d_stats; pin.packed = nullptr; pin.packed_n = 0;
+        pin.levels = 0; pin.d_inbag = d_inbag; pin.inbag_words = inbag_words;
+        pin.d_vals = d_vals; pin.d_card = d_card; pin.max_card = max_card; pin.rank_bytes = rank_bytes; pin.n_groups = n_groups;
+        pin.slot_nodes = slot_nodes; pin.slot_cnodes = slot_cnodes; pin.slot_cap = node_cap; pin.d_levels = levels;
+        pin.grower = AIWCRF_GROWER_TREE;
+        rc = package_forests(pin, s, out);
+        sc.release();
+        if (rc == AIWCRF_OK) AIWCRF_CUDA(cudaStreamSynchronize(s));
+        return rc;
     }
 
     // per-tree level bookkeeping
@@ -1529,8 +2127,12 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     // bins: the tried features' value counts side by side (one pass over the entries)
     const int bin_cap = big_bin_cap(p.mtry, F, max_card);
     const int big_smem = bin_cap * 14;
-    AIWCRF_CUDA(cudaFuncSetAttribute(level_big_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem));
-    AIWCRF_CUDA(cudaFuncSetAttribute(level_big_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem));
+    {
+        cudaError_t e_ = cudaSuccess;
+        AIWCRF_BY_RANK(rank_bytes, e_ = cudaFuncSetAttribute(level_big_kernel<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                             big_smem))
+        if (e_ != cudaSuccess) return cuda_fail(e_, "level_big_kernel attribute");
+    }
 
     LevelArgs la;
     la.row_cap = row_cap; la.Rr = d_Rr; la.vals = d_vals; la.card = d_card; la.N = N;
@@ -1592,8 +2194,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
                 const int64_t cps_big = p.ctas_per_sm > 0 ? p.ctas_per_sm : kBigCtasPerSm;
                 const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(Cb, cps_big * dev_sms));
                 prof_begin(s, kProfLevelBig);
-                if (rank8) level_big_kernel<uint8_t><<<grid, kBigThreads, big_smem, s>>>(la, bin_cap);
-                else level_big_kernel<uint16_t><<<grid, kBigThreads, big_smem, s>>>(la, bin_cap);
+                AIWCRF_BY_RANK(rank_bytes, level_big_kernel<RT><<<grid, kBigThreads, big_smem, s>>>(la, bin_cap))
                 AIWCRF_LAUNCH_CHECK("level_big_kernel");
                 prof_end(s, kProfLevelBig);
             }
@@ -1603,8 +2204,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
                 const int64_t cps_small = p.ctas_per_sm > 0 ? p.ctas_per_sm : kSmallCtasPerSm;
                 const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + wpb - 1) / wpb, cps_small * dev_sms));
                 prof_begin(s_small, kProfLevelSmall);
-                if (rank8) level_small_kernel<uint8_t><<<grid, kSmallThreads, 0, s_small>>>(la);
-                else level_small_kernel<uint16_t><<<grid, kSmallThreads, 0, s_small>>>(la);
+                AIWCRF_BY_RANK(rank_bytes, level_small_kernel<RT><<<grid, kSmallThreads, 0, s_small>>>(la))
                 AIWCRF_LAUNCH_CHECK("level_small_kernel");
                 prof_end(s_small, kProfLevelSmall);
             }
@@ -1640,7 +2240,8 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     pin.p = &p; pin.T = T; pin.Tper = Tper; pin.G = G; pin.N = N; pin.F = F; pin.device = device;
     pin.tree_base = tree_base; pin.d_stats = d_stats; pin.packed = packed; pin.packed_n = (size_t)packed_known;
     pin.levels = (int)h_cnt->levels; pin.d_inbag = d_inbag; pin.inbag_words = inbag_words;
-    pin.d_vals = d_vals; pin.d_card = d_card; pin.max_card = max_card; pin.rank8 = rank8; pin.n_groups = n_groups;
+    pin.d_vals = d_vals; pin.d_card = d_card; pin.max_card = max_card; pin.rank_bytes = rank_bytes; pin.n_groups = n_groups;
+    pin.grower = AIWCRF_GROWER_LEVEL;
     rc = package_forests(pin, s, out);
     sc.release();
     if (rc == AIWCRF_OK) AIWCRF_CUDA(cudaStreamSynchronize(s));
@@ -1692,7 +2293,7 @@ struct FitPlan {
     const int32_t *d_sub_rows = nullptr;
     int device = 0, sms = 0;
     int64_t T = 0, Tper = 0, row_cap = 0, C_max = 0, packed_cap = 0, inbag_words = 0;
-    bool rank8 = true;
+    int rank_bytes = 1;
     uint32_t max_card = 0, probe_groups = 0;
     int boot_smem = 0;
     int64_t gstride = 0;
@@ -1700,7 +2301,7 @@ struct FitPlan {
     // device buffers
     uint32_t *d_err = nullptr, *d_counters = nullptr, *d_card = nullptr;
     GrowStats *d_stats = nullptr;
-    uint16_t *d_R = nullptr;
+    uint32_t *d_R = nullptr;
     float *d_vals = nullptr;
     uint32_t *kA = nullptr, *vA = nullptr, *kB = nullptr, *vB = nullptr, *hist = nullptr;
     void *d_Rr = nullptr;
@@ -1772,26 +2373,19 @@ int plan_phase_a(FitPlan &P, cudaStream_t s, bool probe)
         AIWCRF_CUDA(cudaStreamSynchronize(s));
         if ((rc = check_err_flags(h_err)) != AIWCRF_OK) return rc;
         P.max_card = *std::max_element(h_card.begin(), h_card.end());
-        P.rank8 = P.max_card <= 256;
-        if (P.rank8) { if ((rc = P.alloc(reinterpret_cast<uint8_t **>(&P.d_Rr), (size_t)F * (size_t)N))) return rc; }
-        else if ((rc = P.alloc(reinterpret_cast<uint16_t **>(&P.d_Rr), (size_t)F * (size_t)N))) return rc;
+        P.rank_bytes = rank_bytes_for(P.max_card);
+        if ((rc = P.alloc(reinterpret_cast<uint8_t **>(&P.d_Rr), (size_t)F * (size_t)N * (size_t)P.rank_bytes))) return rc;
     } else {
         plan_check_kernel<<<(unsigned)((F + 127) / 128), 128, 0, s>>>(P.d_card, F, P.max_card, P.d_err);
         AIWCRF_LAUNCH_CHECK("plan_check_kernel");
     }
     const unsigned rb = (unsigned)((N + 255) / 256);
-    if (P.rank8) {
-        rank_rows_kernel<uint8_t><<<rb, 256, 0, s>>>(P.d_R, N, F, (uint8_t *)P.d_Rr);
-        hash_rows_kernel<uint8_t><<<rb, 256, 0, s>>>((const uint8_t *)P.d_Rr, N, F, P.kA, P.vA);
-    } else {
-        rank_rows_kernel<uint16_t><<<rb, 256, 0, s>>>(P.d_R, N, F, (uint16_t *)P.d_Rr);
-        hash_rows_kernel<uint16_t><<<rb, 256, 0, s>>>((const uint16_t *)P.d_Rr, N, F, P.kA, P.vA);
-    }
+    AIWCRF_BY_RANK(P.rank_bytes, rank_rows_kernel<RT><<<rb, 256, 0, s>>>(P.d_R, N, F, (RT *)P.d_Rr);
+                                 hash_rows_kernel<RT><<<rb, 256, 0, s>>>((const RT *)P.d_Rr, N, F, P.kA, P.vA))
     count_launches(1);
     AIWCRF_LAUNCH_CHECK("rank_rows / hash_rows");
     if ((rc = radix_sort_segments(P.kA, P.vA, P.kB, P.vB, N, 1, N, P.hist, s)) != AIWCRF_OK) return rc;
-    if (P.rank8) group_flags_kernel<uint8_t><<<rb, 256, 0, s>>>((const uint8_t *)P.d_Rr, N, F, P.kA, P.vA, P.kB);
-    else group_flags_kernel<uint16_t><<<rb, 256, 0, s>>>((const uint16_t *)P.d_Rr, N, F, P.kA, P.vA, P.kB);
+    AIWCRF_BY_RANK(P.rank_bytes, group_flags_kernel<RT><<<rb, 256, 0, s>>>((const RT *)P.d_Rr, N, F, P.kA, P.vA, P.kB))
     const int gblocks = (int)((N + kFlagTile - 1) / kFlagTile);
     flag_scan_reduce_kernel<<<gblocks, kScanThreads, 0, s>>>(P.kB, N, P.hist);
     scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(P.hist, gblocks);
@@ -1822,6 +2416,7 @@ int plan_bootstrap(FitPlan &P, cudaStream_t s)
     ba.rows_out = P.rows_a; ba.row_cap = P.row_cap; ba.root = P.nodes_a;
     ba.small_list = P.small_l; ba.big_list = P.big_l; ba.counters = P.d_cnt->n_list[0]; ba.err = P.d_err;
     ba.inbag = P.d_inbag; ba.inbag_words = P.inbag_words;
+    ba.store_group = 0;
     bootstrap_kernel<<<(unsigned)P.T, kBootThreads, P.boot_smem, s>>>(ba);
     AIWCRF_LAUNCH_CHECK("bootstrap_kernel");
     iota_kernel<<<(unsigned)((P.T + 256) / 256), 256, 0, s>>>(P.toff_a, (int)P.T);
@@ -1849,12 +2444,10 @@ int plan_level(FitPlan &P, cudaStream_t s, cudaStream_t side, cudaEvent_t ev_for
     const unsigned gbig = (unsigned)(P.cps_big * P.sms), gsmall = (unsigned)(P.cps_small * P.sms);
     AIWCRF_CUDA(cudaEventRecord(ev_fork, s));
     AIWCRF_CUDA(cudaStreamWaitEvent(side, ev_fork, 0));
-    if (P.rank8) level_big_kernel<uint8_t><<<gbig, kBigThreads, big_smem, s>>>(la, bin_cap);
-    else level_big_kernel<uint16_t><<<gbig, kBigThreads, big_smem, s>>>(la, bin_cap);
+    AIWCRF_BY_RANK(P.rank_bytes, level_big_kernel<RT><<<gbig, kBigThreads, big_smem, s>>>(la, bin_cap))
     AIWCRF_LAUNCH_CHECK("level_big_kernel");
     la.list = P.small_l; la.list_n = &P.d_cnt->n_list[parity][0];
-    if (P.rank8) level_small_kernel<uint8_t><<<gsmall, kSmallThreads, 0, side>>>(la);
-    else level_small_kernel<uint16_t><<<gsmall, kSmallThreads, 0, side>>>(la);
+    AIWCRF_BY_RANK(P.rank_bytes, level_small_kernel<RT><<<gsmall, kSmallThreads, 0, side>>>(la))
     AIWCRF_LAUNCH_CHECK("level_small_kernel");
     AIWCRF_CUDA(cudaEventRecord(ev_join, side));
     AIWCRF_CUDA(cudaStreamWaitEvent(s, ev_join, 0));
@@ -2020,8 +2613,12 @@ int fit_plan_create(const aiwcrf_fit_params &p, const float *dX, const int64_t *
     AIWCRF_CUDA(cudaStreamSynchronize(s));
     AIWCRF_CUDA(cudaFuncSetAttribute(bootstrap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, std::max(Q.boot_smem, 1)));
     const int big_smem = big_bin_cap(p.mtry, F, Q.max_card) * 14;
-    AIWCRF_CUDA(cudaFuncSetAttribute(level_big_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem));
-    AIWCRF_CUDA(cudaFuncSetAttribute(level_big_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem));
+    {
+        cudaError_t e_ = cudaSuccess;
+        AIWCRF_BY_RANK(Q.rank_bytes, e_ = cudaFuncSetAttribute(level_big_kernel<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                               big_smem))
+        if (e_ != cudaSuccess) return cuda_fail(e_, "level_big_kernel attribute");
+    }
     if ((rc = plan_capture(Q))) return rc;
     *out = P.release();
     return AIWCRF_OK;
@@ -2046,8 +2643,9 @@ int fit_plan_run(FitPlan *P, cudaStream_t s, std::vector<aiwcrf_forest *> &out)
     pin.p = &P->p; pin.T = P->T; pin.Tper = P->Tper; pin.G = P->G; pin.N = P->N; pin.F = P->F; pin.device = P->device;
     pin.tree_base = P->tree_base; pin.d_stats = P->d_stats; pin.packed = P->packed; pin.packed_n = (size_t)h_cnt->packed_off;
     pin.levels = (int)h_cnt->levels; pin.d_inbag = P->d_inbag; pin.inbag_words = P->inbag_words;
-    pin.d_vals = P->d_vals; pin.d_card = P->d_card; pin.max_card = P->max_card; pin.rank8 = P->rank8;
+    pin.d_vals = P->d_vals; pin.d_card = P->d_card; pin.max_card = P->max_card; pin.rank_bytes = P->rank_bytes;
     pin.n_groups = n_groups;
+    pin.grower = AIWCRF_GROWER_LEVEL;
     rc = package_forests(pin, s, out);
     if (rc == AIWCRF_OK) AIWCRF_CUDA(cudaStreamSynchronize(s));
     return rc;

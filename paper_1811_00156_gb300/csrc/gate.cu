@@ -177,6 +177,7 @@ extern "C" int aiwcrf_select_device_gated(const aiwcrf_forest *forest, const aiw
                                           int32_t *out_best, float *out_pred, uint8_t *out_fallback,
                                           aiwcrf_gate_stats *stats, void *cuda_stream)
 {
+    aiwcrf::clear_last_error();
     if (!forest || !surrogate || !gate || !device_ids)
         return fail(AIWCRF_E_INVALID_ARG, "forest, surrogate, gate and device_ids must not be NULL");
     if (n_kernels < 0 || n_devices < 1) return fail(AIWCRF_E_INVALID_ARG, "n_kernels >= 0 and n_devices >= 1");

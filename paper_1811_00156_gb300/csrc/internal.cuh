@@ -14,7 +14,7 @@ namespace aiwcrf {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 constexpr int kSmallNodeRows = 32;          // nodes with <= 32 distinct rows are searched by a warp
-constexpr uint32_t kRankSentinel = 65536;   // larger than any rank (ranks are < 65536)
+constexpr uint32_t kRankSentinel = 1u << 22;  // larger than any rank (ranks are < rows < 2^22)
 constexpr uint32_t kRowBits = 24;           // row entry = row | (w << 24)
 constexpr uint32_t kRowMask = (1u << kRowBits) - 1;
 constexpr uint32_t kDomBoot = 0xB007u;      // Philox counter domain of bootstrap draws
@@ -22,12 +22,51 @@ constexpr uint32_t kDomMtry = 0x3779u;      // Philox counter domain of mtry key
 
 // device error flag bits (aggregated with atomicOr)
 constexpr uint32_t kErrNaN = 1u;
-constexpr uint32_t kErrCard = 2u;           // more than 65,536 distinct values in a column
+constexpr uint32_t kErrCard = 2u;           // (unused: every column's ranks fit 32 bits)
 constexpr uint32_t kErrBootOverflow = 4u;   // a bootstrap multiplicity above 255
 constexpr uint32_t kErrTimeout = 8u;        // a bounded mbarrier wait gave up
 constexpr uint32_t kErrY = 16u;             // |y| > 2^40
 constexpr uint32_t kErrCapacity = 32u;      // a fit plan's capacity (groups, ranks, levels) was exceeded
 constexpr uint32_t kErrTree = 32u;          // malformed tree met during a walk
+
+// ------------------------------------------------------------------------------------------
+// Debug builds (-DAIWCRF_DEBUG_BOUNDS) check every gathered index and node id of the hot paths
+// against its array's extent. A violation sets the site's bit in the translation unit's device
+// flag and the access goes to index 0 instead (every checked array is non-empty), so a bug shows
+// as a flag, read by aiwcrf_debug_bounds(), rather than as an out-of-bounds access. Release
+// builds compile the checks away.
+// ------------------------------------------------------------------------------------------
+constexpr uint32_t kBoundRow = 1u;       // entry row or group id gathered for its ranks
+constexpr uint32_t kBoundNode = 2u;      // node id of a level's node table or work list
+constexpr uint32_t kBoundWalk = 4u;      // node id reached in a tree walk
+constexpr uint32_t kBoundFeature = 8u;   // feature index of a split
+constexpr uint32_t kBoundBin = 16u;      // histogram bin (rank) of a feature
+constexpr uint32_t kBoundOut = 32u;      // output position (entries, children, packed nodes)
+
+#ifdef AIWCRF_DEBUG_BOUNDS
+static __device__ unsigned int g_bounds_flag;
+
+__device__ __forceinline__ uint64_t checked_index(uint64_t i, uint64_t n, uint32_t site)
+{
+    if (i < n) return i;
+    atomicOr(&g_bounds_flag, site);
+    return 0;
+}
+#define AIWCRF_IDX(i, n, site) ((decltype(i))::aiwcrf::checked_index((uint64_t)(i), (uint64_t)(n), (site)))
+// host: this translation unit's flag, cleared by the read
+#define AIWCRF_BOUNDS_READER(fn)                                                                   \
+    uint32_t fn()                                                                                   \
+    {                                                                                               \
+        unsigned int v = 0, z = 0;                                                                  \
+        if (cudaMemcpyFromSymbol(&v, g_bounds_flag, sizeof(v)) != cudaSuccess) return 0x80000000u;  \
+        cudaMemcpyToSymbol(g_bounds_flag, &z, sizeof(z));                                           \
+        return v;                                                                                   \
+    }
+#else
+#define AIWCRF_IDX(i, n, site) (i)
+#define AIWCRF_BOUNDS_READER(fn) \
+    uint32_t fn() { return 0u; }
+#endif
 
 // ------------------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds; each round multiplies counter
@@ -337,7 +376,7 @@ size_t radix_sort_hist_words(int64_t n, int S);
 
 enum ProfClass {
     kProfRank = 0, kProfBoot, kProfLevelBig, kProfLevelSmall, kProfFinalize,
-    kProfPack, kProfPredict, kProfSelect, kProfServe, kProfNum
+    kProfPack, kProfPredict, kProfSelect, kProfServe, kProfTree, kProfWalk, kProfNum
 };
 
 void prof_begin(cudaStream_t s, int cls);
@@ -350,6 +389,14 @@ struct Error {
 };
 
 void set_error(int code, const std::string &msg);
+void clear_last_error();         // every C entry point starts with an empty message
+// bounds flags of the translation units that check (debug builds; cleared by the read)
+uint32_t bounds_flags_fit();
+uint32_t bounds_flags_predict();
+uint32_t bounds_flags_serve();
+// the grower of the next fits (AIWCRF_GROWER_*), process-wide
+int set_grower_mode(int mode);
+int grower_mode();
 int fail(int code, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
 
@@ -445,6 +492,13 @@ int predict_prefix_var_enqueue(const aiwcrf_forest *f, const float *dXq, int64_t
 int expand_launch(const float *d_kfeat, int32_t K, int32_t size_class, const int32_t *d_dev, int32_t D, int32_t F,
                   float *d_q, cudaStream_t s);
 int oob_launch(const aiwcrf_forest *f, const float *dX, int64_t N, int64_t *d_sum, int32_t *d_count, cudaStream_t s);
+// out-of-bag error from aiwcrf_oob's sums and counts (d_y: the training targets): d_pred (or
+// null) gets the out-of-bag predictions, d_res the exact sum of squared errors and the mean
+struct OobPart { unsigned long long lo, hi, rows; };
+struct OobResult { unsigned long long sq_lo, sq_hi; long long rows; double mse; };
+size_t oob_error_parts(int64_t N);
+int oob_error_launch(const int64_t *d_sum, const int32_t *d_count, const int64_t *d_y, int64_t N, int64_t *d_pred,
+                     OobPart *d_parts, OobResult *d_res, uint32_t *d_err, cudaStream_t s);
 int predict_launch(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum,
                    int64_t *d_pred, uint64_t *d_var, int64_t total_trees, cudaStream_t s);
 int round_mean_launch(const int64_t *d_sum, int64_t Q, int64_t total_trees, int64_t *d_out,

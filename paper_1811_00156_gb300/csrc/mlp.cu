@@ -203,6 +203,7 @@ extern "C" int aiwcrf_tc_gemm_bf16(const void *A, int32_t lda, int32_t a_trans, 
                                    int32_t b_trans, float *C, int32_t M, int32_t N, int32_t K, int32_t ksplit,
                                    void *cuda_stream)
 {
+    aiwcrf::clear_last_error();
     if (!A || !B || !C) return fail(AIWCRF_E_INVALID_ARG, "A, B and C must not be NULL");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const int nchunks = (K + 63) / 64;

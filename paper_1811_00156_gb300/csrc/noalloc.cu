@@ -59,6 +59,7 @@ extern "C" int aiwcrf_select_device_noalloc(const aiwcrf_forest *forest, const f
                                             int32_t size_class, const int32_t *device_ids, int32_t n_devices,
                                             int32_t *out_best, int64_t *out_pred, void *cuda_stream)
 {
+    clear_last_error();
     if (!forest || !kfeat || !device_ids || !out_best)
         return fail(AIWCRF_E_INVALID_ARG, "forest, kfeat, device_ids and out_best must not be NULL");
     if (n_kernels < 1 || n_devices < 1) return fail(AIWCRF_E_INVALID_ARG, "n_kernels and n_devices must be >= 1");

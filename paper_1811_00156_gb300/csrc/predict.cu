@@ -98,34 +98,89 @@ __device__ __forceinline__ int64_t leaf_value(uint64_t nd)
     return ((int64_t)(nd << 1)) >> 1;
 }
 
-// c(x) = #{table values < x}; NaN goes right of every threshold (c = table size)
+// Rank codes of queries: c(x) = #{table values < x}; NaN goes right of every threshold
+// (c = table size). One thread per query codes all F features (a binary search of each value
+// table) into the query's row in shared memory; the CTA then writes its rows, which are
+// contiguous in global memory, with 16-byte stores, so that every byte of the code matrix is
+// written once, whole sectors at a time. A row is row_words 4-byte words; its padding is zero.
+constexpr int kCodeThreads = 128;
+
 template <typename CT>
-__global__ void code_queries_kernel(const float *__restrict__ Xq, int64_t Q, int F, const float *__restrict__ fvals,
-                                    int64_t fstride, const uint32_t *__restrict__ fcard, CT *__restrict__ codes,
-                                    int ld)
+__global__ void __launch_bounds__(kCodeThreads) code_queries_kernel(const float *__restrict__ Xq, int64_t Q, int F,
+                                                                   const float *__restrict__ fvals, int64_t fstride,
+                                                                   const uint32_t *__restrict__ fcard,
+                                                                   CT *__restrict__ codes, int row_words)
 {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int f = blockIdx.y;
-    if (q >= Q) return;
-    const float x = Xq[(size_t)f * (size_t)Q + q];
-    const float *V = fvals + (size_t)f * (size_t)fstride;
-    uint32_t lo = 0, hi = fcard[f];
-    if (x != x) {
-        lo = hi;
-    } else {
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (__ldg(&V[mid]) < x) lo = mid + 1;
-            else hi = mid;
+    extern __shared__ __align__(16) uint32_t code_rows[];         // kCodeThreads * row_words words
+    const int tid = threadIdx.x;
+    const int64_t q0 = (int64_t)blockIdx.x * kCodeThreads, q = q0 + tid;
+    uint32_t *row = code_rows + (size_t)tid * (size_t)row_words;   // odd row_words: distinct banks
+    for (int w = 0; w < row_words; ++w) row[w] = 0u;
+    if (q < Q) {
+        CT *c = reinterpret_cast<CT *>(row);
+        for (int f = 0; f < F; ++f) {
+            const float x = __ldg(&Xq[(size_t)f * (size_t)Q + q]);
+            const float *V = fvals + (size_t)f * (size_t)fstride;
+            uint32_t lo = 0, hi = __ldg(&fcard[f]);
+            if (x != x) {
+                lo = hi;
+            } else {
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (__ldg(&V[mid]) < x) lo = mid + 1;
+                    else hi = mid;
+                }
+            }
+            c[f] = (CT)lo;
         }
     }
-    codes[(size_t)q * (size_t)ld + f] = (CT)lo;
+    __syncthreads();
+    const int64_t n = min((int64_t)kCodeThreads, Q - q0);
+    const int words = (int)n * row_words;
+    uint32_t *dst = reinterpret_cast<uint32_t *>(codes) + (size_t)q0 * (size_t)row_words;
+    const int vec = (reinterpret_cast<uintptr_t>(dst) & 15u) == 0 ? words >> 2 : 0;
+    for (int i = tid; i < vec; i += kCodeThreads)
+        reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(code_rows)[i];
+    for (int i = 4 * vec + tid; i < words; i += kCodeThreads) dst[i] = code_rows[i];
+}
+
+// bytes of one feature's code for a forest: one when every value table has at most 255 values
+__host__ __forceinline__ int code_bytes_of(const aiwcrf_forest *f)
+{
+    return f->max_card <= 255u ? 1 : (f->max_card <= 65535u ? 2 : 4);
+}
+
+// Words of one query's code row: F codes rounded up to whole words, made odd so that rows
+// staged side by side in shared memory start on distinct banks.
+__host__ __forceinline__ int code_row_words(int F, int code_bytes)
+{
+    int w = (F * code_bytes + 3) / 4;
+    if ((w & 1) == 0) ++w;
+    return w;
+}
+
+// codes of Q queries (row_words words per query) on the stream
+template <typename CT>
+cudaError_t launch_code_queries(const aiwcrf_forest *f, const float *dXq, int64_t Q, CT *d_codes, int row_words,
+                                cudaStream_t s)
+{
+    if (Q == 0) return cudaSuccess;
+    const size_t smem = (size_t)kCodeThreads * (size_t)row_words * 4;        // <= 66 KB (F <= 128)
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(code_queries_kernel<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    code_queries_kernel<CT><<<(unsigned)((Q + kCodeThreads - 1) / kCodeThreads), kCodeThreads, smem, s>>>(
+        dXq, Q, f->F, f->d_fvals, f->fstride, f->d_fcard, d_codes, row_words);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 // One step of QPT independent walks through one tree (coded thresholds).
 template <typename CT, int QPT, typename NodePtr>
 __device__ __forceinline__ void walk_tree(NodePtr tn, const CT *const (&xr)[QPT], int64_t (&acc)[QPT],
-                                          u128_t (&sq)[QPT], bool var)
+                                          u128_t (&sq)[QPT], bool var, uint32_t nn)
 {
     uint32_t j[QPT];
 #pragma unroll
@@ -140,7 +195,7 @@ __device__ __forceinline__ void walk_tree(NodePtr tn, const CT *const (&xr)[QPT]
             const uint32_t f = leaf ? 0u : ((hi >> 24) & 0x7Fu);
             const uint32_t c = (uint32_t)xr[i][f];
             const uint32_t nxt = (hi & 0xFFFFFFu) + (c > ((uint32_t)nd & 0xFFFFFFu) ? 1u : 0u);
-            j[i] = leaf ? j[i] : nxt;
+            j[i] = leaf ? j[i] : AIWCRF_IDX(nxt, nn, kBoundWalk);
             more |= !leaf;
         }
         if (!more) break;
@@ -212,11 +267,12 @@ __global__ void __launch_bounds__(kPredThreads) predict_kernel(
             return;
         }
         const int64_t a = tree_off[t];
-        if (tree_off[t + 1] - a <= tree_cap) {
-            if (s) walk_tree<CT, QPT>(slot1, xr, acc, sq, VAR);
-            else walk_tree<CT, QPT>(slot0, xr, acc, sq, VAR);
+        const uint32_t nn = (uint32_t)(tree_off[t + 1] - a);
+        if (nn <= (uint32_t)tree_cap) {
+            if (s) walk_tree<CT, QPT>(slot1, xr, acc, sq, VAR, nn);
+            else walk_tree<CT, QPT>(slot0, xr, acc, sq, VAR, nn);
         } else {
-            walk_tree<CT, QPT>(nodes + a, xr, acc, sq, VAR);
+            walk_tree<CT, QPT>(nodes + a, xr, acc, sq, VAR, nn);
         }
         __syncthreads();
         if (tid == 0 && t + 2 < T) issue_tree(nodes, tree_off, t + 2, tree_cap, s ? slot1 : slot0, &bar[s]);
@@ -288,7 +344,7 @@ __device__ __forceinline__ void issue_tree4(const uint32_t *c32, const int64_t *
 // leaf's threshold 255.)
 constexpr int kWalkSteps = 2;
 template <int QPT, typename NodePtr>
-__device__ __forceinline__ void walk_tree4(NodePtr tn, const uint8_t *const (&xr)[QPT], uint32_t (&j)[QPT])
+__device__ __forceinline__ void walk_tree4(NodePtr tn, const uint8_t *const (&xr)[QPT], uint32_t (&j)[QPT], uint32_t nn)
 {
     uint32_t nd[QPT];
 #pragma unroll
@@ -300,7 +356,7 @@ __device__ __forceinline__ void walk_tree4(NodePtr tn, const uint8_t *const (&xr
             for (int i = 0; i < QPT; ++i) {
                 nd[i] = tn[j[i]];
                 const uint32_t c = (uint32_t)xr[i][nd[i] >> 24];
-                j[i] = (nd[i] & 0xFFFFu) + (c > ((nd[i] >> 16) & 0xFFu) ? 1u : 0u);
+                j[i] = AIWCRF_IDX((nd[i] & 0xFFFFu) + (c > ((nd[i] >> 16) & 0xFFu) ? 1u : 0u), nn, kBoundWalk);
             }
         }
         bool done = true;
@@ -380,11 +436,12 @@ __global__ void __launch_bounds__(kPredThreads) predict4_kernel(
             return;
         }
         uint32_t j[QPT];
+        const uint32_t nn4 = (uint32_t)(b4 - a4);
         if (b4 - a4 <= tree_cap) {
-            if (s) walk_tree4<QPT>(slot1, xr, j);
-            else walk_tree4<QPT>(slot0, xr, j);
+            if (s) walk_tree4<QPT>(slot1, xr, j, nn4);
+            else walk_tree4<QPT>(slot0, xr, j, nn4);
         } else {
-            walk_tree4<QPT>(c32 + a4, xr, j);
+            walk_tree4<QPT>(c32 + a4, xr, j, nn4);
         }
         // add the previous tree's leaves, then start loading this tree's
         const uint64_t *tn = nodes + ta;
@@ -473,17 +530,108 @@ __global__ void oob_kernel(const uint64_t *__restrict__ cnodes, const int64_t *_
     for (int t = 0; t < T; ++t) {
         if ((__ldg(&inbag[(size_t)t * (size_t)words + (size_t)(row >> 5)]) >> (row & 31)) & 1u) continue;
         const uint64_t *tn = cnodes + tree_off[t];
+        const uint32_t nn = (uint32_t)(tree_off[t + 1] - tree_off[t]);
         uint32_t j = 0;
         for (;;) {
             const uint64_t nd = __ldg(&tn[j]);
             if (nd >> 63) { sum += leaf_value(nd); break; }
-            const uint32_t f = (uint32_t)(nd >> 56) & 0x7Fu;
-            j = ((uint32_t)(nd >> 32) & 0xFFFFFFu) + ((uint32_t)x[f] > ((uint32_t)nd & 0xFFFFFFu) ? 1u : 0u);
+            const uint32_t f = AIWCRF_IDX((uint32_t)(nd >> 56) & 0x7Fu, (uint32_t)ld, kBoundFeature);
+            j = AIWCRF_IDX(((uint32_t)(nd >> 32) & 0xFFFFFFu) + ((uint32_t)x[f] > ((uint32_t)nd & 0xFFFFFFu) ? 1u : 0u), nn,
+                           kBoundWalk);
         }
         ++cnt;
     }
     out_sum[row] = sum;
     out_count[row] = cnt;
+}
+
+// Out-of-bag error (Sec. III-B): per row with c > 0 out-of-bag trees its out-of-bag prediction
+// p = floor((2 s + c) / (2 c)) and the squared error (p - y)^2, exact in 128 bits; each CTA
+// writes the sum of its rows' squared errors and their number, oob_error_finish_kernel adds the
+// CTA sums in CTA order and divides once.
+constexpr int kOobErrThreads = 256;
+
+__global__ void __launch_bounds__(kOobErrThreads) oob_error_kernel(const int64_t *__restrict__ sum,
+                                                                   const int32_t *__restrict__ cnt,
+                                                                   const int64_t *__restrict__ y, int64_t N,
+                                                                   int64_t *__restrict__ pred, OobPart *part,
+                                                                   uint32_t *err)
+{
+    __shared__ OobPart red[kOobErrThreads / 32];
+    const int64_t row = (int64_t)blockIdx.x * kOobErrThreads + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long lo = 0ull, hi = 0ull, rows = 0ull;
+    if (row < N) {
+        const int32_t c = cnt[row];
+        int64_t p = 0;
+        if (c > 0) {
+            const long long yr = y[row];
+            if (yr > AIWCRF_MAX_ABS_Y || yr < -AIWCRF_MAX_ABS_Y) atomicOr(err, kErrY);
+            p = round_mean(sum[row], (uint32_t)c);
+            const i128_t d = (i128_t)p - (i128_t)yr;                 // |d| < 2^42
+            const u128_t a = d < 0 ? (u128_t)(-d) : (u128_t)d;
+            const u128_t sq = a * a;
+            lo = (unsigned long long)sq;
+            hi = (unsigned long long)(sq >> 64);
+            rows = 1ull;
+        }
+        if (pred) pred[row] = p;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long olo = __shfl_xor_sync(kFull, lo, o), ohi = __shfl_xor_sync(kFull, hi, o);
+        const unsigned long long nlo = lo + olo;
+        hi += ohi + (nlo < lo ? 1ull : 0ull);
+        lo = nlo;
+        rows += __shfl_xor_sync(kFull, rows, o);
+    }
+    if (lane == 0) { red[warp].lo = lo; red[warp].hi = hi; red[warp].rows = rows; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        OobPart t = red[0];
+        for (int w = 1; w < kOobErrThreads / 32; ++w) {
+            const unsigned long long nlo = t.lo + red[w].lo;
+            t.hi += red[w].hi + (nlo < t.lo ? 1ull : 0ull);
+            t.lo = nlo;
+            t.rows += red[w].rows;
+        }
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void oob_error_finish_kernel(const OobPart *part, int nparts, OobResult *res)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long lo = 0ull, hi = 0ull, rows = 0ull;
+    for (int i = 0; i < nparts; ++i) {
+        const unsigned long long nlo = lo + part[i].lo;
+        hi += part[i].hi + (nlo < lo ? 1ull : 0ull);
+        lo = nlo;
+        rows += part[i].rows;
+    }
+    res->sq_lo = lo;
+    res->sq_hi = hi;
+    res->rows = (long long)rows;
+    // sum < 2^106: hi converts exactly, lo once rounded; mean in units of the target squared
+    const double sq = __dadd_rn(__dmul_rn((double)hi, 18446744073709551616.0), (double)lo);
+    res->mse = rows ? __dmul_rn(__ddiv_rn(sq, (double)rows), 5.42101086242752217e-20) : 0.0;   // 2^-64
+}
+
+int oob_error_launch(const int64_t *d_sum, const int32_t *d_count, const int64_t *d_y, int64_t N, int64_t *d_pred,
+                     OobPart *d_parts, OobResult *d_res, uint32_t *d_err, cudaStream_t s)
+{
+    const int nparts = (int)std::max<int64_t>(1, (N + kOobErrThreads - 1) / kOobErrThreads);
+    oob_error_kernel<<<(unsigned)nparts, kOobErrThreads, 0, s>>>(d_sum, d_count, d_y, N, d_pred, d_parts, d_err);
+    oob_error_finish_kernel<<<1, 32, 0, s>>>(d_parts, nparts, d_res);
+    count_launches(2);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "oob_error launch");
+    return AIWCRF_OK;
+}
+
+size_t oob_error_parts(int64_t N)
+{
+    return (size_t)std::max<int64_t>(1, (N + kOobErrThreads - 1) / kOobErrThreads);
 }
 
 __global__ void round_mean_kernel(const int64_t *sums, int64_t n, int64_t T, int64_t *out)
@@ -531,39 +679,49 @@ constexpr int kQPT = 2;
 // compact-forest batches of at least this many queries are walked in sorted order
 constexpr int64_t kSortMinQueries = 1 << 16;
 
+// Shared memory of the 8-byte node walk (predict_kernel): kQPT code rows per thread, 256 bytes
+// after them, and two tree slots sized to the forest's largest tree up to 48 KB each.
+struct WalkSmem {
+    int tree_cap;
+    int bytes;
+};
+
+WalkSmem walk8_smem(const aiwcrf_forest *f, int row_words)
+{
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int xs_bytes = kPredThreads * kQPT * row_words * 4 + 256;
+    int tree_cap = std::min<int>((optin - xs_bytes - 1024) / 16, 6144);
+    if ((int64_t)tree_cap > f->max_tree_nodes) tree_cap = (int)f->max_tree_nodes;
+    tree_cap &= ~1;
+    if (tree_cap < 2) tree_cap = 2;
+    return WalkSmem{tree_cap, 2 * tree_cap * 8 + xs_bytes};
+}
+
 template <typename CT, bool VAR>
 int launch_predict(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum, int64_t *d_pred,
                    uint64_t *d_var, int64_t total_trees, cudaStream_t s, uint32_t *d_err, void *codes_scratch,
                    int64_t walk_T)
 {
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    int ld_words = (int)((f->F * (int)sizeof(CT) + 3) / 4);
-    if ((ld_words & 1) == 0) ++ld_words;                       // odd: conflict-free rows
-    const int ld = ld_words * 4 / (int)sizeof(CT);
+    const int ld_words = code_row_words(f->F, (int)sizeof(CT));
     CT *d_codes = static_cast<CT *>(codes_scratch);
     cudaError_t e = cudaSuccess;
     if (!d_codes && cudaMallocAsync(&d_codes, (size_t)Q * (size_t)ld_words * 4, s) != cudaSuccess)
         return fail(AIWCRF_E_OOM, "device allocation of the query codes failed");
     struct Free { CT *p; cudaStream_t s; ~Free() { if (p) cudaFreeAsync(p, s); } } fr{codes_scratch ? nullptr : d_codes, s};
-    code_queries_kernel<CT><<<dim3((unsigned)((Q + 255) / 256), (unsigned)f->F), 256, 0, s>>>(
-        dXq, Q, f->F, f->d_fvals, f->fstride, f->d_fcard, d_codes, ld);
-    count_launches(1);
-    // query code rows, then 256 bytes that a leaf's code read (feature field 255) may touch
-    const int xs_bytes = kPredThreads * kQPT * ld_words * 4 + 256;
-    // two tree slots, sized to the largest tree up to 48 KB each
-    int tree_cap = std::min<int>((optin - xs_bytes - 1024) / 16, 6144);
-    if ((int64_t)tree_cap > f->max_tree_nodes) tree_cap = (int)f->max_tree_nodes;
-    tree_cap &= ~1;
-    if (tree_cap < 2) tree_cap = 2;
-    const int smem = 2 * tree_cap * 8 + xs_bytes;
+    if ((e = launch_code_queries<CT>(f, dXq, Q, d_codes, ld_words, s)) != cudaSuccess)
+        return cuda_fail(e, "code_queries_kernel launch");
+    const WalkSmem ws = walk8_smem(f, ld_words);
+    const int tree_cap = ws.tree_cap, smem = ws.bytes;
     auto kern = predict_kernel<CT, kQPT, VAR>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(predict_kernel)");
     const int64_t grid = (Q + (int64_t)kPredThreads * kQPT - 1) / ((int64_t)kPredThreads * kQPT);
+    prof_begin(s, kProfWalk);
     kern<<<(unsigned)grid, kPredThreads, smem, s>>>(f->d_cnodes, f->d_tree_off, (int)walk_T, d_codes, Q, ld_words,
                                                     total_trees, tree_cap, d_sum, d_pred, d_var, d_err);
+    prof_end(s, kProfWalk);
     count_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "predict_kernel launch");
@@ -578,16 +736,14 @@ int launch_predict4(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    int ld_words = (f->F + 3) / 4;
-    if ((ld_words & 1) == 0) ++ld_words;                       // odd: conflict-free rows
+    const int ld_words = code_row_words(f->F, 1);
     uint8_t *d_codes = static_cast<uint8_t *>(codes_scratch);
     cudaError_t e = cudaSuccess;
     if (!d_codes && cudaMallocAsync(&d_codes, (size_t)Q * (size_t)ld_words * 4, s) != cudaSuccess)
         return fail(AIWCRF_E_OOM, "device allocation of the query codes failed");
     struct Free { uint8_t *p; cudaStream_t s; ~Free() { if (p) cudaFreeAsync(p, s); } } fr{codes_scratch ? nullptr : d_codes, s};
-    code_queries_kernel<uint8_t><<<dim3((unsigned)((Q + 255) / 256), (unsigned)f->F), 256, 0, s>>>(
-        dXq, Q, f->F, f->d_fvals, f->fstride, f->d_fcard, d_codes, ld_words * 4);
-    count_launches(1);
+    if ((e = launch_code_queries<uint8_t>(f, dXq, Q, d_codes, ld_words, s)) != cudaSuccess)
+        return cuda_fail(e, "code_queries_kernel launch");
     // query code rows, then 256 bytes that a leaf's code read (feature field 255) may touch
     const int xs_bytes = kPredThreads * kQPT * ld_words * 4 + 256;
     // two tree slots of 4-byte nodes, sized to the largest tree up to 48 KB each
@@ -618,9 +774,11 @@ int launch_predict4(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(predict4_kernel)");
     const int64_t grid = (Q + (int64_t)kPredThreads * kQPT - 1) / ((int64_t)kPredThreads * kQPT);
+    prof_begin(s, kProfWalk);
     kern<<<(unsigned)grid, kPredThreads, smem, s>>>(f->d_c32, f->d_tree_off4, f->d_nodes, f->d_tree_off, (int)walk_T,
                                                     d_codes, Q, ld_words, total_trees, tree_cap, d_sum, d_pred, d_var,
                                                     d_err, perm);
+    prof_end(s, kProfWalk);
     count_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "predict4_kernel launch");
@@ -644,10 +802,7 @@ int launch_predict_ct(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64
 
 size_t predict_codes_bytes(const aiwcrf_forest *f, int64_t Q)
 {
-    const int cb = f->max_card <= 255u ? 1 : (f->max_card <= 65535u ? 2 : 4);
-    int ld_words = (f->F * cb + 3) / 4;
-    if ((ld_words & 1) == 0) ++ld_words;
-    return (size_t)Q * (size_t)ld_words * 4;
+    return (size_t)Q * (size_t)code_row_words(f->F, code_bytes_of(f)) * 4;
 }
 
 int predict_enqueue(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum, int64_t *d_pred,
@@ -712,16 +867,17 @@ namespace {
 template <typename CT>
 int oob_ct(const aiwcrf_forest *f, const float *dX, int64_t N, int64_t *d_sum, int32_t *d_count, cudaStream_t s)
 {
-    const int ld = f->F;
+    const int ld_words = code_row_words(f->F, (int)sizeof(CT));
+    const int ld = ld_words * 4 / (int)sizeof(CT);
     CT *d_codes = nullptr;
-    cudaError_t e = cudaMallocAsync(&d_codes, sizeof(CT) * (size_t)N * (size_t)ld, s);
+    cudaError_t e = cudaMallocAsync(&d_codes, (size_t)N * (size_t)ld_words * 4, s);
     if (e != cudaSuccess) return fail(AIWCRF_E_OOM, "device allocation of the row codes failed");
     struct Free { CT *p; cudaStream_t s; ~Free() { cudaFreeAsync(p, s); } } fr{d_codes, s};
-    code_queries_kernel<CT><<<dim3((unsigned)((N + 255) / 256), (unsigned)f->F), 256, 0, s>>>(
-        dX, N, f->F, f->d_fvals, f->fstride, f->d_fcard, d_codes, ld);
+    if ((e = launch_code_queries<CT>(f, dX, N, d_codes, ld_words, s)) != cudaSuccess)
+        return cuda_fail(e, "code_queries_kernel launch");
     oob_kernel<CT><<<(unsigned)((N + 127) / 128), 128, 0, s>>>(f->d_cnodes, f->d_tree_off, (int)f->T, d_codes, ld, N,
                                                               f->d_inbag, f->inbag_words, d_sum, d_count);
-    count_launches(2);
+    count_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "oob launch");
     return AIWCRF_OK;
@@ -822,10 +978,7 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 int code_ld_words(const aiwcrf_forest *f)
 {
-    const int cb = f->max_card <= 255u ? 1 : (f->max_card <= 65535u ? 2 : 4);
-    int ld_words = (f->F * cb + 3) / 4;
-    if ((ld_words & 1) == 0) ++ld_words;
-    return ld_words;
+    return code_row_words(f->F, code_bytes_of(f));
 }
 
 template <typename CT>
@@ -835,22 +988,14 @@ int select_noalloc_ct(const aiwcrf_forest *f, const float *d_kfeat, int32_t K, i
 {
     const int64_t Qn = (int64_t)K * D;
     const int ld_words = code_ld_words(f);
-    const int ld = ld_words * 4 / (int)sizeof(CT);
     expand_queries_kernel<<<(unsigned)((Qn + 255) / 256), 256, 0, s>>>(d_kfeat, K, size_class, d_dev, D, f->F, d_q);
-    code_queries_kernel<CT><<<dim3((unsigned)((Qn + 255) / 256), (unsigned)f->F), 256, 0, s>>>(
-        d_q, Qn, f->F, f->d_fvals, f->fstride, f->d_fcard, reinterpret_cast<CT *>(d_codes), ld);
-    count_launches(2);
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const int xs_bytes = kPredThreads * kQPT * ld_words * 4;
-    int tree_cap = std::min<int>((optin - xs_bytes - 1024) / 16, 6144);
-    if ((int64_t)tree_cap > f->max_tree_nodes) tree_cap = (int)f->max_tree_nodes;
-    tree_cap &= ~1;
-    if (tree_cap < 2) tree_cap = 2;
-    const int smem = 2 * tree_cap * 8 + xs_bytes;
+    count_launches(1);
+    cudaError_t e = launch_code_queries<CT>(f, d_q, Qn, reinterpret_cast<CT *>(d_codes), ld_words, s);
+    if (e != cudaSuccess) return cuda_fail(e, "code_queries_kernel launch");
+    const WalkSmem ws = walk8_smem(f, ld_words);
+    const int tree_cap = ws.tree_cap, smem = ws.bytes;
     auto kern = predict_kernel<CT, kQPT, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(predict_kernel)");
     const int64_t grid = (Qn + (int64_t)kPredThreads * kQPT - 1) / ((int64_t)kPredThreads * kQPT);
     kern<<<(unsigned)grid, kPredThreads, smem, s>>>(f->d_cnodes, f->d_tree_off, (int)f->T,
@@ -887,9 +1032,13 @@ int select_launch_noalloc(const aiwcrf_forest *f, const float *d_kfeat, int32_t 
     int64_t *d_p = reinterpret_cast<int64_t *>(p);
     p += align256(sizeof(int64_t) * Qn);
     uint32_t *d_err = reinterpret_cast<uint32_t *>(p);
-    cudaError_t e = cudaMemcpyAsync(d_dev, h_dev, sizeof(int32_t) * (size_t)D, cudaMemcpyHostToDevice, s);
+    // device_ids may be host or device memory (unified addressing: no staging buffer needed)
+    cudaError_t e = cudaMemcpyAsync(d_dev, h_dev, sizeof(int32_t) * (size_t)D, cudaMemcpyDefault, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s);    // the flag must start at 0
-    if (e != cudaSuccess) return cuda_fail(e, "select_device scratch set-up");
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(s);     // nothing this call enqueued may still use the shared array
+        return cuda_fail(e, "select_device scratch set-up");
+    }
     prof_begin(s, kProfSelect);
     int rc;
     if (f->max_card <= 255u)
@@ -899,7 +1048,10 @@ int select_launch_noalloc(const aiwcrf_forest *f, const float *d_kfeat, int32_t 
     else
         rc = select_noalloc_ct<uint32_t>(f, d_kfeat, K, size_class, D, d_best, d_pred, d_dev, d_q, d_codes, d_p, d_err, s);
     prof_end(s, kProfSelect);
-    if (rc != AIWCRF_OK) return rc;
+    if (rc != AIWCRF_OK) {
+        cudaStreamSynchronize(s);     // kernels enqueued before the failure finish with the array
+        return rc;
+    }
     uint32_t h_err = 0;
     e = cudaMemcpyAsync(&h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -908,4 +1060,8 @@ int select_launch_noalloc(const aiwcrf_forest *f, const float *d_kfeat, int32_t 
     return AIWCRF_OK;
 }
 
+}  // namespace aiwcrf
+
+namespace aiwcrf {
+AIWCRF_BOUNDS_READER(bounds_flags_predict)
 }  // namespace aiwcrf

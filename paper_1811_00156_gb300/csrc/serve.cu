@@ -27,6 +27,8 @@
 // of the order in which CTAs finish: a request gets the same answer alone or batched with any
 // others.
 #include <cuda_runtime.h>
+#include <sys/resource.h>
+#include <time.h>
 
 #include <algorithm>
 #include <atomic>
@@ -219,6 +221,25 @@ int64_t now_ns()
     return std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now().time_since_epoch()).count();
 }
 
+// CPU time and context switches of the calling thread (where a stalled dispatcher's time went)
+struct ThreadUsage {
+    int64_t cpu_ns = 0;
+    long vol = 0, invol = 0;
+};
+
+ThreadUsage thread_usage()
+{
+    ThreadUsage u;
+    timespec ts;
+    if (clock_gettime(CLOCK_THREAD_CPUTIME_ID, &ts) == 0) u.cpu_ns = (int64_t)ts.tv_sec * 1000000000ll + ts.tv_nsec;
+    rusage ru;
+    if (getrusage(RUSAGE_THREAD, &ru) == 0) {
+        u.vol = ru.ru_nvcsw;
+        u.invol = ru.ru_nivcsw;
+    }
+    return u;
+}
+
 size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 constexpr int64_t kIdlePollNs = 200000;   // the dispatcher polls this long before sleeping
@@ -365,6 +386,8 @@ struct Slot {
     int64_t off = -1, bytes = 0;
     int32_t Kb = 0;
     int64_t t_formed = 0, t_enqueued = 0;
+    int64_t enq_cpu = 0, last_poll = 0, poll_gap_max = 0;
+    int32_t enq_vol = 0, enq_invol = 0;
     std::shared_ptr<Model> model;
     std::vector<std::shared_ptr<Request>> reqs;
 };
@@ -541,6 +564,10 @@ struct aiwcrf_server {
             tr.t_done_ns = t;
             tr.kernels = sl.Kb;
             tr.generation = (int32_t)gen;
+            tr.enqueue_cpu_ns = sl.enq_cpu;
+            tr.enqueue_voluntary_switches = sl.enq_vol;
+            tr.enqueue_involuntary_switches = sl.enq_invol;
+            tr.poll_gap_max_ns = std::max(sl.poll_gap_max, t - sl.last_poll);
             arena.release(sl.off, sl.bytes);
             st.completed += (int64_t)sl.reqs.size();
             if (status != AIWCRF_OK) st.failed += (int64_t)sl.reqs.size();
@@ -569,6 +596,7 @@ struct aiwcrf_server {
         int64_t *d_pred = reinterpret_cast<int64_t *>(base + up256(in_bytes));
         int32_t *d_best = reinterpret_cast<int32_t *>(d_pred + (size_t)sl.Kb * (size_t)D);
         const size_t out_bytes = (size_t)sl.Kb * ((size_t)D * 8 + 4);
+        const ThreadUsage u0 = thread_usage();
         cudaError_t e = cudaMemcpyAsync(d_in, sl.h_in, in_bytes, cudaMemcpyHostToDevice, sl.s);
         if (e == cudaSuccess &&
             serve_launch(sl.model->f, d_in, sl.Kb, d_dev, D, -1, sl.d_sum, sl.d_cnt, d_pred, d_best, sl.s) != AIWCRF_OK)
@@ -576,6 +604,12 @@ struct aiwcrf_server {
         if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_out, d_pred, out_bytes, cudaMemcpyDeviceToHost, sl.s);
         if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.s);
         sl.t_enqueued = now_ns();
+        const ThreadUsage u1 = thread_usage();
+        sl.enq_cpu = u1.cpu_ns - u0.cpu_ns;
+        sl.enq_vol = (int32_t)(u1.vol - u0.vol);
+        sl.enq_invol = (int32_t)(u1.invol - u0.invol);
+        sl.last_poll = sl.t_enqueued;
+        sl.poll_gap_max = 0;
         sl.busy = true;
         if (e != cudaSuccess) {
             cudaStreamSynchronize(sl.s);
@@ -592,7 +626,13 @@ struct aiwcrf_server {
             for (auto &sl : slots) {
                 if (!sl.busy) continue;
                 const cudaError_t e = cudaEventQuery(sl.ev);
-                if (e == cudaErrorNotReady) { any_busy = true; continue; }
+                if (e == cudaErrorNotReady) {
+                    const int64_t t = now_ns();
+                    sl.poll_gap_max = std::max(sl.poll_gap_max, t - sl.last_poll);
+                    sl.last_poll = t;
+                    any_busy = true;
+                    continue;
+                }
                 complete(sl, e);
                 progressed = true;
             }
@@ -818,6 +858,7 @@ int aiwcrf_server_create(const aiwcrf_server_params *params, const aiwcrf_fit_pa
                          const int64_t *y, int64_t n_rows, int32_t n_features, const int32_t *device_ids,
                          int32_t n_devices, aiwcrf_server **out)
 {
+    aiwcrf::clear_last_error();
     if (!params || !fit || !X || !y || !device_ids || !out) return fail(AIWCRF_E_INVALID_ARG, "null argument");
     *out = nullptr;
     const aiwcrf_server_params &p = *params;
@@ -909,6 +950,7 @@ int aiwcrf_server_create(const aiwcrf_server_params *params, const aiwcrf_fit_pa
 int aiwcrf_server_submit(aiwcrf_server *server, const float *kfeat, int32_t n_kernels, int32_t size_class,
                          int64_t *ticket)
 {
+    aiwcrf::clear_last_error();
     if (!server || !kfeat || !ticket) return fail(AIWCRF_E_INVALID_ARG, "null argument");
     if (n_kernels < 1) return fail(AIWCRF_E_INVALID_ARG, "n_kernels must be >= 1");
     if (n_kernels > server->sp.max_request_kernels) {
@@ -931,6 +973,7 @@ int aiwcrf_server_submit(aiwcrf_server *server, const float *kfeat, int32_t n_ke
 int aiwcrf_server_wait(aiwcrf_server *server, int64_t ticket, int32_t timeout_ms, int32_t *best, int64_t *pred,
                        int64_t *generation)
 {
+    aiwcrf::clear_last_error();
     if (!server) return fail(AIWCRF_E_INVALID_ARG, "null server");
     std::unique_lock<std::mutex> lk(server->mu);
     auto it = server->tickets.find(ticket);
@@ -950,6 +993,7 @@ int aiwcrf_server_wait(aiwcrf_server *server, int64_t ticket, int32_t timeout_ms
 
 int aiwcrf_server_append(aiwcrf_server *server, const float *X, const int64_t *y, int64_t n_rows)
 {
+    aiwcrf::clear_last_error();
     if (!server || !X || !y) return fail(AIWCRF_E_INVALID_ARG, "null argument");
     if (n_rows < 0) return fail(AIWCRF_E_INVALID_ARG, "n_rows < 0");
     int rc = check_rows(X, y, n_rows, server->F);
@@ -966,6 +1010,7 @@ int aiwcrf_server_append(aiwcrf_server *server, const float *X, const int64_t *y
 
 int aiwcrf_server_refit(aiwcrf_server *server, int32_t wait)
 {
+    aiwcrf::clear_last_error();
     if (!server) return fail(AIWCRF_E_INVALID_ARG, "null server");
     std::unique_lock<std::mutex> lk(server->rmu);
     // a refit already running read its rows before this call: wait for the one after it
@@ -980,6 +1025,7 @@ int aiwcrf_server_refit(aiwcrf_server *server, int32_t wait)
 
 int aiwcrf_server_pause(aiwcrf_server *server, int32_t paused)
 {
+    aiwcrf::clear_last_error();
     if (!server) return fail(AIWCRF_E_INVALID_ARG, "null server");
     std::lock_guard<std::mutex> lk(server->mu);
     server->paused = paused != 0;
@@ -989,6 +1035,7 @@ int aiwcrf_server_pause(aiwcrf_server *server, int32_t paused)
 
 int aiwcrf_server_stats(aiwcrf_server *server, aiwcrf_server_counters *out)
 {
+    aiwcrf::clear_last_error();
     if (!server || !out) return fail(AIWCRF_E_INVALID_ARG, "null argument");
     {
         std::lock_guard<std::mutex> lk(server->mu);
@@ -1005,6 +1052,7 @@ int aiwcrf_server_run_load(aiwcrf_server *server, const float *pool, int64_t poo
                            uint64_t seed, int32_t timeout_ms, int32_t *best, int64_t *generation, int64_t *latency_ns,
                            aiwcrf_load_report *report)
 {
+    aiwcrf::clear_last_error();
     if (!server || !pool || !first || !n_kernels || !size_class || !report)
         return fail(AIWCRF_E_INVALID_ARG, "null argument");
     if (n_requests < 1 || !(rate_per_s > 0.0) || pool_kernels < 1)
@@ -1126,6 +1174,7 @@ int aiwcrf_server_run_load(aiwcrf_server *server, const float *pool, int64_t poo
 int aiwcrf_server_trace(aiwcrf_server *server, aiwcrf_batch_trace *batches, int64_t cap, int64_t *n,
                         aiwcrf_refit_trace *refits, int64_t rcap, int64_t *rn)
 {
+    aiwcrf::clear_last_error();
     if (!server || !n || !rn || cap < 0 || rcap < 0 || (cap && !batches) || (rcap && !refits))
         return fail(AIWCRF_E_INVALID_ARG, "bad trace arguments");
     std::lock_guard<std::mutex> lk(server->mu);
@@ -1142,6 +1191,7 @@ int aiwcrf_server_trace(aiwcrf_server *server, aiwcrf_batch_trace *batches, int6
 
 int aiwcrf_server_destroy(aiwcrf_server *server)
 {
+    aiwcrf::clear_last_error();
     if (!server) return AIWCRF_OK;
     server->shutdown();
     delete server;

@@ -621,6 +621,7 @@ extern "C" {
 int aiwcrf_surrogate_fit(const aiwcrf_surrogate_params *p, const aiwcrf_forest *teacher, const float *X, int64_t n,
                          int32_t n_features, void *cuda_stream, aiwcrf_surrogate **out)
 {
+    aiwcrf::clear_last_error();
     if (!p || !teacher || !X || !out) return fail(AIWCRF_E_INVALID_ARG, "params, teacher, X and out must not be NULL");
     if (n_features != teacher->F) return fail(AIWCRF_E_INVALID_ARG, "X must have the teacher's features");
     if (p->batch < 128 || p->batch % 128 || p->batch > 65536 || p->epochs < 1 || !(p->lr > 0.0f) || n < p->batch)
@@ -723,6 +724,7 @@ int aiwcrf_surrogate_fit(const aiwcrf_surrogate_params *p, const aiwcrf_forest *
 
 int aiwcrf_surrogate_predict(const aiwcrf_surrogate *sg, const float *Xq, int64_t n, float *out, void *cuda_stream)
 {
+    aiwcrf::clear_last_error();
     if (!sg || !Xq || !out) return fail(AIWCRF_E_INVALID_ARG, "surrogate, Xq and out must not be NULL");
     if (n < 0) return fail(AIWCRF_E_INVALID_ARG, "n must be >= 0");
     cudaPointerAttributes a1, a2;
@@ -737,6 +739,7 @@ int aiwcrf_surrogate_predict(const aiwcrf_surrogate *sg, const float *Xq, int64_
 int aiwcrf_surrogate_grad(const aiwcrf_surrogate *sg, const float *X, const float *y, int32_t n, float *grad,
                           float *loss, void *cuda_stream)
 {
+    aiwcrf::clear_last_error();
     if (!sg || !X || !y || !grad || !loss || n < 128 || n % 128)
         return fail(AIWCRF_E_INVALID_ARG, "arguments must not be NULL; n a positive multiple of 128");
     cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -753,6 +756,7 @@ int aiwcrf_surrogate_grad(const aiwcrf_surrogate *sg, const float *X, const floa
 int aiwcrf_surrogate_create(int32_t n_features, int32_t n_devices, int32_t n_sizes, const float *params,
                             const float *mu, const float *sd, const uint8_t *log2_cols, aiwcrf_surrogate **out)
 {
+    aiwcrf::clear_last_error();
     if (!params || !mu || !sd || !log2_cols || !out) return fail(AIWCRF_E_INVALID_ARG, "arguments must not be NULL");
     aiwcrf_surrogate *sg = nullptr;
     int rc = new_surrogate(n_features, n_devices, n_sizes, &sg);
@@ -773,6 +777,7 @@ int aiwcrf_surrogate_create(int32_t n_features, int32_t n_devices, int32_t n_siz
 
 int aiwcrf_surrogate_export(const aiwcrf_surrogate *sg, float *params, float *mu, float *sd, uint8_t *log2_cols)
 {
+    aiwcrf::clear_last_error();
     if (!sg) return fail(AIWCRF_E_INVALID_ARG, "surrogate is NULL");
     if (params && cudaMemcpy(params, sg->d_param, 4 * (size_t)kParams, cudaMemcpyDeviceToHost) != cudaSuccess)
         return cuda_fail(cudaGetLastError(), "surrogate export");
@@ -784,6 +789,7 @@ int aiwcrf_surrogate_export(const aiwcrf_surrogate *sg, float *params, float *mu
 
 int aiwcrf_surrogate_stats(const aiwcrf_surrogate *sg, aiwcrf_surrogate_fit_stats *out)
 {
+    aiwcrf::clear_last_error();
     if (!sg || !out) return fail(AIWCRF_E_INVALID_ARG, "arguments must not be NULL");
     *out = sg->stats;
     return AIWCRF_OK;
@@ -793,6 +799,7 @@ int32_t aiwcrf_surrogate_num_params(void) { return kParams; }
 
 int aiwcrf_surrogate_free(aiwcrf_surrogate *sg)
 {
+    aiwcrf::clear_last_error();
     if (!sg) return AIWCRF_OK;
     surrogate_release(sg);
     return AIWCRF_OK;

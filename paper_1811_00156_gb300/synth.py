@@ -150,6 +150,28 @@ def scaled_forest_workload(seed: int = DATA_SEED, replicates: int = 50) -> Workl
                     meta=meta)
 
 
+def per_row_forest_workload(seed: int = DATA_SEED, replicates: int = 50) -> Workload:
+    """The 111,000-row workload read with features per row: the same (kernel, device, size)
+    grid and replicate count as scaled_forest_workload, but every row draws its own AIWC vector
+    from the feature distributions (no two rows share one), with the target from the same hidden
+    model on the row's own features plus N(0, 0.02) and the 3 % run noise. The continuous
+    columns then hold about one distinct value per row."""
+    rng, pop, model = _population(seed)
+    X0, k, d, s = _grid_rows(pop)
+    n = k.size * replicates
+    rng2 = np.random.default_rng(seed + 3)
+    X = np.empty((N_FEATURES, n), dtype=np.float32)
+    X[:N_AIWC] = aiwc_features(rng2, n)
+    dev = np.repeat(d, replicates)
+    size = np.repeat(s, replicates)
+    X[COL_DEVICE] = dev.astype(np.float32)
+    X[COL_SIZE] = size.astype(np.float32)
+    ylog = model(X[:N_AIWC], dev, size) + rng2.normal(0.0, 0.02, size=n)
+    ylog = ylog + rng2.normal(0.0, 0.03 / math.log(10.0), size=n)
+    return Workload(X=np.ascontiguousarray(X), y=quantise(ylog), name=f"aiwc-{n}-per-row",
+                    meta=dict(seed=seed, kernel=np.repeat(k, replicates), device=dev, size=size))
+
+
 def queries(q: int, seed: int = QUERY_SEED) -> np.ndarray:
     """q fresh query rows from the same feature distributions (continuous, off the training
     grid); device and size class uniform. float32 [32][q]."""

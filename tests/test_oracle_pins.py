@@ -336,3 +336,21 @@ def test_oob_sums_are_the_out_of_bag_trees():
     assert 0.2 < (c > 0).mean() <= 1.0                       # about 1 - 0.632^9 of the rows
     nb = O.fit(wl.X, wl.y, 3, 3, 2, seed=12, bootstrap=False)
     assert not nb.oob(wl.X)[1].any()
+
+
+def test_oob_error_is_the_mean_squared_out_of_bag_residual():
+    """The oracle's out-of-bag error: each out-of-bag prediction is the round-half-up mean of
+    the out-of-bag leaf sums, and the error their mean squared residual in the target's units
+    (against a float64 evaluation of the same definition)."""
+    wl = synth.small_case(76, 300, 6, card=11)
+    fr = O.fit(wl.X, wl.y, 12, 3, 2, seed=5)
+    s, c = fr.oob(wl.X)
+    pred, mse, rows = fr.oob_error(wl.X, wl.y)
+    m = c > 0
+    assert rows == int(m.sum()) and 0 < rows < wl.n_rows and not pred[~m].any()
+    exact = np.array([Fraction(int(a), int(b)) for a, b in zip(s[m], c[m])], object)
+    # round half up: the prediction is within 1/2 of the exact mean, and ties go up
+    assert all(abs(Fraction(int(p)) - e) <= Fraction(1, 2) and Fraction(int(p)) - e != Fraction(-1, 2)
+               for p, e in zip(pred[m], exact))
+    ref = np.mean(((pred[m].astype(np.float64) - wl.y[m].astype(np.float64)) / 2.0 ** 32) ** 2)
+    assert abs(mse - ref) <= 1e-12 * ref

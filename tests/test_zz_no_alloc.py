@@ -43,6 +43,57 @@ def test_noalloc_matches_allocating_select_twice(A):
         assert set(best_b.cpu().tolist()) <= set(devices)
 
 
+class _DefaultPool:
+    """The current device's default stream-ordered memory pool, read through the driver API:
+    the library's stream-ordered allocations (cudaMallocAsync) come from it."""
+    USED_MEM_CURRENT, USED_MEM_HIGH = 7, 8          # CUmemPool_attribute values
+
+    def __init__(self):
+        import ctypes as C
+        self.C = C
+        self.cu = C.CDLL("libcuda.so.1")
+        dev = C.c_int(0)
+        assert self.cu.cuDeviceGet(C.byref(dev), torch.cuda.current_device()) == 0
+        self.pool = C.c_void_p()
+        assert self.cu.cuDeviceGetDefaultMemPool(C.byref(self.pool), dev) == 0
+
+    def get(self, attr):
+        v = self.C.c_uint64(0)
+        assert self.cu.cuMemPoolGetAttribute(self.pool, attr, self.C.byref(v)) == 0
+        return v.value
+
+    def reset_high(self):
+        """Reset the high-water mark of used pool memory to the current use."""
+        zero = self.C.c_uint64(0)
+        assert self.cu.cuMemPoolSetAttribute(self.pool, self.USED_MEM_HIGH, self.C.byref(zero)) == 0
+
+
+def test_noalloc_allocates_no_device_memory(A):
+    """Across a warm call, neither the default pool's high-water mark of used memory nor the
+    device's free memory moves; the same probe sees the allocating entry point allocate."""
+    from paper_1811_00156_gb300 import synth
+    wl = synth.plain_forest_workload()
+    forest = A.aiwcrf_fit(A.params(16, 10, 5), torch.from_numpy(wl.X).cuda(), torch.from_numpy(wl.y).cuda())
+    K, devices = 48, list(range(15))
+    kfeat = torch.from_numpy(np.ascontiguousarray(synth.queries(K, seed=21)[:30])).cuda()
+    best = torch.empty(K, dtype=torch.int32, device="cuda")
+    pred = torch.empty(K * len(devices), dtype=torch.int64, device="cuda")
+    A.aiwcrf_select_device_noalloc(forest, kfeat, 1, devices, best, pred)       # warm: modules loaded
+    A.aiwcrf_select_device(forest, kfeat, 1, devices, best, pred)
+    torch.cuda.synchronize()
+    pool = _DefaultPool()
+    used0 = pool.get(pool.USED_MEM_CURRENT)
+    pool.reset_high()
+    free0 = torch.cuda.mem_get_info()[0]
+    A.aiwcrf_select_device_noalloc(forest, kfeat, 1, devices, best, pred)
+    torch.cuda.synchronize()
+    assert pool.get(pool.USED_MEM_HIGH) == used0
+    assert torch.cuda.mem_get_info()[0] == free0
+    A.aiwcrf_select_device(forest, kfeat, 1, devices, best, pred)              # the probe's control
+    torch.cuda.synchronize()
+    assert pool.get(pool.USED_MEM_HIGH) > used0
+
+
 def test_noalloc_rejects_requests_beyond_the_static_scratch(A):
     from paper_1811_00156_gb300 import synth
     wl = synth.small_case(3, 300, 32, card=20)
