@@ -495,6 +495,16 @@ int aiwcrf_fit_plan_set_schedule(aiwcrf_fit_plan *plan, const aiwcrf_fit_schedul
  * stream-ordered pool (no cudaFree, so no device-wide wait inside the free). NULL is accepted. */
 int aiwcrf_fit_plan_free(aiwcrf_fit_plan *plan);
 
+/* Bounds checks of a debug build (no counterpart in the paper; the stand-in for an external
+ * memory checker). A library built with -DAIWCRF_DEBUG_BOUNDS (libaiwcrf_debug.so) checks every
+ * gathered entry row or group id, node id of a level's tables and of a tree walk, split
+ * feature, histogram bin and output position of the fit, predict and selection kernels
+ * against its array's extent; a violation is recorded and the access redirected to index 0.
+ * Returns the OR of the violated sites since the last call (1 row/group, 2 node, 4 walk node,
+ * 8 feature, 16 bin, 32 output position; 0 = none) and clears it; -1 in a release build, which
+ * compiles the checks away. Reading the flags synchronises the device. */
+int64_t aiwcrf_debug_bounds(void);
+
 /* Which kernels grow the trees of the following fits in this process (the paper has no
  * counterpart: both give the same forest, node for node, for the model of Sec. III-B).
  *  AIWCRF_GROWER_AUTO (default): tree-resident when it fits, else level-synchronous.

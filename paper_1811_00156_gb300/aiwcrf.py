@@ -13,7 +13,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libaiwcrf.so")
+# AIWCRF_LIB=debug selects the bounds-checking build (libaiwcrf_debug.so), for tests
+LIB_PATH = os.path.join(_HERE, "libaiwcrf_debug.so" if os.environ.get("AIWCRF_LIB") == "debug" else "libaiwcrf.so")
 
 AIWCRF_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "NAN_INPUT", -3: "BAD_POINTER", -4: "OOM", -5: "CUDA",
@@ -126,7 +127,7 @@ EXPORTS = ["aiwcrf_fit", "aiwcrf_fit_subsets", "aiwcrf_predict", "aiwcrf_predict
            "aiwcrf_server_refit", "aiwcrf_server_pause", "aiwcrf_server_stats", "aiwcrf_server_run_load",
            "aiwcrf_server_trace", "aiwcrf_server_destroy", "aiwcrf_select_device_gated",
            "aiwcrf_fit_plan_create", "aiwcrf_fit_plan_run", "aiwcrf_fit_plan_tune", "aiwcrf_fit_plan_set_schedule",
-           "aiwcrf_fit_plan_free", "aiwcrf_profile_classes", "aiwcrf_set_grower"]
+           "aiwcrf_fit_plan_free", "aiwcrf_profile_classes", "aiwcrf_set_grower", "aiwcrf_debug_bounds"]
 
 _lib = None
 _lock = threading.Lock()
@@ -178,6 +179,7 @@ def load():
         L.aiwcrf_profile_name.restype = C.c_char_p
         L.aiwcrf_profile_num_classes.restype = C.c_int32
         L.aiwcrf_set_grower.argtypes = [C.c_int32]
+        L.aiwcrf_debug_bounds.restype = C.c_int64
         L.aiwcrf_launch_count.restype = C.c_int64
         L.aiwcrf_server_create.argtypes = [C.POINTER(ServerParams), C.POINTER(FitParams), _vp, _vp, C.c_int64,
                                            C.c_int32, _vp, C.c_int32, C.POINTER(_vp)]
@@ -612,6 +614,11 @@ def aiwcrf_launch_count() -> int:
 
 
 GROWER_AUTO, GROWER_LEVEL, GROWER_TREE = 0, 1, 2
+
+
+def aiwcrf_debug_bounds() -> int:
+    """Bounds-check violations since the last call in a debug build (0 none), -1 in a release build."""
+    return int(load().aiwcrf_debug_bounds())
 
 
 def aiwcrf_set_grower(grower: int):

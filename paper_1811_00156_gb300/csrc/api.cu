@@ -865,6 +865,16 @@ const char *aiwcrf_profile_name(int32_t k)
 
 int32_t aiwcrf_profile_num_classes(void) { return kProfNum; }
 
+int64_t aiwcrf_debug_bounds(void)
+{
+    aiwcrf::clear_last_error();
+#ifdef AIWCRF_DEBUG_BOUNDS
+    return (int64_t)(aiwcrf::bounds_flags_fit() | aiwcrf::bounds_flags_predict() | aiwcrf::bounds_flags_serve());
+#else
+    return -1;
+#endif
+}
+
 int aiwcrf_set_grower(int32_t grower)
 {
     aiwcrf::clear_last_error();

@@ -348,6 +348,7 @@ struct LevelArgs {
     SplitRes *res;
     uint32_t *tile_splits;      // per tile of kScanTile nodes: nodes that split (zero on entry)
     const uint32_t *depth_ptr;  // when set, the depth is read here (a graph replays one level body)
+    uint32_t node_cap;          // entries of the node table (bounds checks of debug builds)
 };
 
 __device__ __forceinline__ int level_depth(const LevelArgs &a)
@@ -468,6 +469,7 @@ __device__ __forceinline__ int nth_feature(const uint32_t (&mask)[4], int n)
 template <typename RT>
 __device__ __forceinline__ void small_node(const LevelArgs &a, const RT *__restrict__ Rr, int j, int lane)
 {
+    j = AIWCRF_IDX(j, a.node_cap, kBoundNode);
     const NodeRec nd = a.nodes[j];
     if (node_stops(a, nd)) {
         if (lane == 0) write_leaf(a.res, j, -2, round_mean(nd.S, nd.n));
@@ -481,7 +483,7 @@ __device__ __forceinline__ void small_node(const LevelArgs &a, const RT *__restr
     Entry e;
     e.row = 0u; e.w = 0u; e.wy = 0;
     if (valid) e = load_entry(a.rows_in + tb + pos);
-    const size_t rec = (size_t)e.row * (size_t)a.F;
+    const size_t rec = (size_t)AIWCRF_IDX(e.row, (uint32_t)a.N, kBoundRow) * (size_t)a.F;
 
     uint32_t mask[4];
     warp_mtry(a, a.tree_rng[nd.tree], nd.idx, mask);
@@ -543,12 +545,13 @@ __device__ __forceinline__ void small_node(const LevelArgs &a, const RT *__restr
         el.row = 0u; el.w = 0u; el.wy = 0;
         if (lv) el = load_entry(a.rows_in + tb + lane);
     }
-    const uint32_t rk = lv ? (uint32_t)__ldg(&Rr[(size_t)el.row * (size_t)a.F + best.f]) : kRankSentinel;
+    const uint32_t rk =
+        lv ? (uint32_t)__ldg(&Rr[(size_t)AIWCRF_IDX(el.row, (uint32_t)a.N, kBoundRow) * (size_t)a.F + best.f]) : kRankSentinel;
     const bool left = lv && rk <= best.r;
     const uint32_t bl = __ballot_sync(kFull, left), bv = __ballot_sync(kFull, lv);
     const uint32_t lenL = __popc(bl), lt = lanemask_lt();
     const uint32_t pos_out = left ? __popc(bl & lt) : lenL + __popc(bv & ~bl & lt);
-    if (lv) store_entry(a.rows_out + tb + pos_out, el);
+    if (lv) store_entry(a.rows_out + tb + AIWCRF_IDX(pos_out, nd.len, kBoundOut), el);
     if (lane == 0) {
         SplitRes sr;
         sr.feature = best.f; sr.rank = best.r;
@@ -611,6 +614,7 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
     __shared__ uint32_t warp_tmp[32];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    j = AIWCRF_IDX(j, a.node_cap, kBoundNode);
     const NodeRec nd = a.nodes[j];
     if (node_stops(a, nd)) {
         if (tid == 0) write_leaf(a.res, j, -2, round_mean(nd.S, nd.n));
@@ -688,7 +692,9 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
                     const int fk = kv ? feats[k0 + c] : 0;
 #pragma unroll
                     for (int u = 0; u < kRowsPerIter; ++u)
-                        rk[u][c] = (kv && wv[u]) ? (uint32_t)__ldg(&Rr[(size_t)rowv[u] * (size_t)a.F + fk]) : 0u;
+                        rk[u][c] = (kv && wv[u])
+                                       ? (uint32_t)__ldg(&Rr[(size_t)AIWCRF_IDX(rowv[u], (uint32_t)a.N, kBoundRow) * (size_t)a.F + fk])
+                                       : 0u;
                 }
 #pragma unroll
                 for (int c = 0; c < kFeatChunk; ++c) {
@@ -822,7 +828,7 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
     // first pass counts the entries that go left
     uint32_t cnt = 0;
     for (uint32_t i = tid; i < nd.len; i += kBigThreads) {
-        const uint32_t row = __ldg(&rin[i].row);
+        const uint32_t row = AIWCRF_IDX(__ldg(&rin[i].row), (uint32_t)a.N, kBoundRow);
         cnt += (uint32_t)__ldg(&Rr[(size_t)row * (size_t)a.F + win.f]) <= win.r ? 1u : 0u;
     }
     uint32_t lenL;
@@ -835,12 +841,13 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
         Entry e;
         e.row = 0u; e.w = 0u; e.wy = 0;
         if (valid) e = load_entry(rin + i);
-        const bool left = valid && (uint32_t)__ldg(&Rr[(size_t)e.row * (size_t)a.F + win.f]) <= win.r;
+        const bool left =
+            valid && (uint32_t)__ldg(&Rr[(size_t)AIWCRF_IDX(e.row, (uint32_t)a.N, kBoundRow) * (size_t)a.F + win.f]) <= win.r;
         uint32_t tot;
         const uint32_t incl = block_incl_scan(left ? 1u : 0u, warp_tmp, tot);
         if (valid) {
             const uint32_t before_l = incl - (left ? 1u : 0u);
-            store_entry(left ? &rout[run_l + before_l] : &rout[lenL + run_r + ((uint32_t)tid - before_l)], e);
+            store_entry(&rout[AIWCRF_IDX(left ? run_l + before_l : lenL + run_r + ((uint32_t)tid - before_l), nd.len, kBoundOut)], e);
         }
         run_l += tot;
         run_r += min((uint32_t)kBigThreads, nd.len - b0) - tot;
@@ -909,6 +916,7 @@ struct TreeArgs {
     int64_t N;
     const uint32_t *card;         // values per feature (<= bins)
     const uint32_t *tree_rng;     // global tree index per tree (Philox counter word 0)
+    uint32_t n_groups;            // rows of Rg (debug bounds checks)
     int T, F, mtry, min_node, max_depth;
     uint32_t seed_lo, seed_hi;
     int ecap;                     // entry capacity of the shared-memory arrays (>= row_cap)
@@ -985,10 +993,10 @@ __device__ __forceinline__ void tree_small_node(const TreeArgs &a, const TreeSme
     uint32_t ew = 0u, eg = 0u;
     long long ewy = 0ll;
     if (valid) {
-        const int ei = ix[nd.start + pos];
+        const int ei = AIWCRF_IDX(ix[nd.start + pos], a.ecap, kBoundRow);
         ew = sm.w[ei]; ewy = sm.wy[ei]; eg = sm.g[ei];
     }
-    const uint8_t *rec = a.Rg + (size_t)eg * (size_t)a.F;
+    const uint8_t *rec = a.Rg + (size_t)AIWCRF_IDX(eg, a.n_groups, kBoundRow) * (size_t)a.F;
 
     uint32_t mask[4];
     warp_mtry_s(a.F, a.mtry, depth, a.seed_lo, a.seed_hi, tg, nd.idx, mask);
@@ -1041,13 +1049,14 @@ __device__ __forceinline__ void tree_small_node(const TreeArgs &a, const TreeSme
     }
     // partition: entry i on lane i
     const bool lv = lane < len;
-    const int el = lv ? ix[nd.start + lane] : 0;
-    const uint32_t rk = lv ? (uint32_t)__ldg(&a.Rg[(size_t)sm.g[el] * (size_t)a.F + best.f]) : kRankSentinel;
+    const int el = lv ? AIWCRF_IDX(ix[nd.start + lane], a.ecap, kBoundRow) : 0;
+    const uint32_t rk =
+        lv ? (uint32_t)__ldg(&a.Rg[(size_t)AIWCRF_IDX(sm.g[el], a.n_groups, kBoundRow) * (size_t)a.F + best.f]) : kRankSentinel;
     const bool left = lv && rk <= best.r;
     const uint32_t bl = __ballot_sync(kFull, left), bv = __ballot_sync(kFull, lv);
     const uint32_t lenL = __popc(bl), lt = lanemask_lt();
     const uint32_t pos_out = left ? __popc(bl & lt) : lenL + __popc(bv & ~bl & lt);
-    if (lv) ox[nd.start + pos_out] = (uint16_t)el;
+    if (lv) ox[nd.start + AIWCRF_IDX(pos_out, (uint32_t)len, kBoundOut)] = (uint16_t)el;
     if (lane == 0) {
         SplitRes sr;
         sr.feature = best.f; sr.rank = best.r;
@@ -1080,12 +1089,13 @@ __device__ __forceinline__ void tree_big_item(const TreeArgs &a, const TreeSmem 
             const int i = base + u * 32 + lane;
             wv[u] = 0u; rk[u] = 0u; lov[u] = 0u; hiv[u] = 0;
             if (i < len) {
-                const int e = ix[nd.start + i];
+                const int e = AIWCRF_IDX(ix[nd.start + i], a.ecap, kBoundRow);
                 const int64_t y = sm.wy[e];
                 wv[u] = sm.w[e];
                 lov[u] = (uint32_t)(uint64_t)y;
                 hiv[u] = (int32_t)(y >> 32);
-                rk[u] = (uint32_t)__ldg(&Rf[(size_t)sm.g[e] * (size_t)a.F]);
+                rk[u] = AIWCRF_IDX((uint32_t)__ldg(&Rf[(size_t)AIWCRF_IDX(sm.g[e], a.n_groups, kBoundRow) * (size_t)a.F]),
+                                   (uint32_t)card, kBoundBin);
             }
         }
 #pragma unroll
@@ -1156,7 +1166,9 @@ __device__ __forceinline__ void tree_big_split(const TreeArgs &a, const TreeSmem
 #pragma unroll
         for (int u = 0; u < kTreeIlp; ++u) {
             const int i = base + u * 32 + lane;
-            rk[u] = i < len ? (uint32_t)__ldg(&Rf[(size_t)sm.g[ix[nd.start + i]] * (size_t)a.F]) : kRankSentinel;
+            rk[u] = i < len ? (uint32_t)__ldg(&Rf[(size_t)AIWCRF_IDX(sm.g[AIWCRF_IDX(ix[nd.start + i], a.ecap, kBoundRow)],
+                                                                     a.n_groups, kBoundRow) * (size_t)a.F])
+                            : kRankSentinel;
         }
 #pragma unroll
         for (int u = 0; u < kTreeIlp; ++u) {
@@ -1246,7 +1258,7 @@ __global__ void __launch_bounds__(kTreeThreads, kTreeCtasPerSm) tree_grow_kernel
             for (uint32_t j = (uint32_t)warp; j < items; j += kTreeWarps) {
                 if (j < nb * (uint32_t)m) {
                     const uint32_t bi = j / (uint32_t)m, k = j - bi * (uint32_t)m;
-                    const TNode nd = cn[big[bi]];
+                    const TNode nd = cn[AIWCRF_IDX(big[bi], a.ecap, kBoundNode)];
                     tree_big_item(a, sm, ix, nd, tg, depth, (int)k, wbins, &cands[(size_t)bi * 32 + k], lane);
                 } else {
                     const uint32_t i = j - nb * (uint32_t)m;
@@ -1258,7 +1270,7 @@ __global__ void __launch_bounds__(kTreeThreads, kTreeCtasPerSm) tree_grow_kernel
             __syncthreads();
             // B: big nodes' decisions and partitions
             for (uint32_t bi = (uint32_t)warp; bi < nb; bi += kTreeWarps) {
-                const uint32_t i = big[bi];
+                const uint32_t i = AIWCRF_IDX(big[bi], a.ecap, kBoundNode);
                 tree_big_split(a, sm, ix, ox, cn[i], m, &cands[(size_t)bi * 32], &res[i], lane);
             }
             __syncthreads();
@@ -1281,14 +1293,14 @@ __global__ void __launch_bounds__(kTreeThreads, kTreeCtasPerSm) tree_grow_kernel
                     const uint32_t pos = base + i;
                     const uint32_t left = base + C + 2u * loc;
                     const uint64_t node = split ? encode_split(r.feature, left, r.thr_bits) : encode_leaf(r.v);
-                    onodes[pos] = node;
-                    ocnodes[pos] = split ? encode_split_coded(r.feature, left, r.rank) : node;
+                    onodes[AIWCRF_IDX(pos, a.node_cap, kBoundOut)] = node;
+                    ocnodes[AIWCRF_IDX(pos, a.node_cap, kBoundOut)] = split ? encode_split_coded(r.feature, left, r.rank) : node;
                     if (split) {
                         L.start = nd.start; L.len = (uint16_t)r.lenL; L.n = r.nL; L.S = r.v; L.idx = 2u * loc; L.pad = 0u;
                         R.start = (uint16_t)(nd.start + r.lenL); R.len = (uint16_t)(nd.len - r.lenL); R.n = nd.n - r.nL;
                         R.S = nd.S - r.v; R.idx = 2u * loc + 1u; R.pad = 0u;
-                        nx[2u * loc] = L;
-                        nx[2u * loc + 1u] = R;
+                        nx[AIWCRF_IDX(2u * loc, a.ecap, kBoundOut)] = L;
+                        nx[AIWCRF_IDX(2u * loc + 1u, a.ecap, kBoundOut)] = R;
                         bigL = tnode_big(a, L, depth + 1u);
                         bigR = tnode_big(a, R, depth + 1u);
                     }
@@ -1304,8 +1316,8 @@ __global__ void __launch_bounds__(kTreeThreads, kTreeCtasPerSm) tree_grow_kernel
                 const uint32_t nbi = (bigL ? 1u : 0u) + (bigR ? 1u : 0u);
                 uint32_t totb;
                 uint32_t bpos = run_big + block_incl_scan(nbi, warp_tmp, totb) - nbi;
-                if (bigL) nbig[bpos++] = (uint16_t)(2u * loc);
-                if (bigR) nbig[bpos] = (uint16_t)(2u * loc + 1u);
+                if (bigL) nbig[AIWCRF_IDX(bpos++, a.big_cap, kBoundOut)] = (uint16_t)(2u * loc);
+                if (bigR) nbig[AIWCRF_IDX(bpos, a.big_cap, kBoundOut)] = (uint16_t)(2u * loc + 1u);
                 run_split += tot;
                 run_big += totb;
             }
@@ -1353,7 +1365,7 @@ __global__ void tree_place_kernel(const uint64_t *slot_nodes, const uint64_t *sl
                                   const uint32_t *counts, uint64_t *const *tree_dst, uint64_t *const *tree_cdst)
 {
     const int t = blockIdx.x;
-    const uint32_t c = counts[t];
+    const uint32_t c = (uint32_t)AIWCRF_IDX(counts[t], (uint64_t)node_cap, kBoundOut);
     const uint64_t *sn = slot_nodes + (size_t)t * (size_t)node_cap, *sc = slot_cnodes + (size_t)t * (size_t)node_cap;
     uint64_t *dn = tree_dst[t], *dc = tree_cdst[t];
     for (uint32_t i = threadIdx.x; i < c; i += blockDim.x) { dn[i] = sn[i]; dc[i] = sc[i]; }
@@ -1438,6 +1450,7 @@ struct FinalArgs {
     uint32_t *tile_splits;         // the level kernels' split counts per tile, cleared for the next depth
     uint32_t *excl_out;            // n + 1: exclusive split count of every node (written here)
     int parity;                    // this depth's parity: its list counts, cleared at the end
+    uint32_t next_cap;             // entries of the next depth's node table (debug bounds checks)
 };
 
 __device__ __forceinline__ void push_list(int32_t *list, uint32_t *counter, bool want, int32_t value)
@@ -1521,8 +1534,8 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(FinalArgs a)
             L.tree = t; L.idx = 2u * local; L.start = nd.start; L.len = r.lenL; L.n = r.nL; L.pad = 0u; L.S = r.v;
             Rn.tree = t; Rn.idx = 2u * local + 1u; Rn.start = nd.start + r.lenL; Rn.len = nd.len - r.lenL;
             Rn.n = nd.n - r.nL; Rn.pad = 0u; Rn.S = nd.S - r.v;
-            a.next[2u * g] = L;
-            a.next[2u * g + 1u] = Rn;
+            a.next[AIWCRF_IDX(2u * g, a.next_cap, kBoundOut)] = L;
+            a.next[AIWCRF_IDX(2u * g + 1u, a.next_cap, kBoundOut)] = Rn;
         }
         push_list(a.small_list, &n_next[0], split && L.len <= (uint32_t)kSmallNodeRows, (int32_t)(2u * g));
         push_list(a.big_list, &n_next[1], split && L.len > (uint32_t)kSmallNodeRows, (int32_t)(2u * g));
@@ -2082,7 +2095,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         AIWCRF_CUDA(cudaMemsetAsync(levels, 0, sizeof(uint32_t), s));
         TreeArgs ta;
         ta.rows = rows_a; ta.root = nodes_cur; ta.row_cap = row_cap; ta.Rg = d_Rg; ta.vals = d_vals; ta.N = N;
-        ta.card = d_card; ta.tree_rng = d_rng; ta.T = (int)T; ta.F = F; ta.mtry = p.mtry;
+        ta.card = d_card; ta.tree_rng = d_rng; ta.n_groups = n_groups; ta.T = (int)T; ta.F = F; ta.mtry = p.mtry;
         ta.min_node = p.min_node_size; ta.max_depth = p.max_depth;
         ta.seed_lo = (uint32_t)p.seed; ta.seed_hi = (uint32_t)(p.seed >> 32);
         ta.ecap = tree_ecap; ta.bins = tree_bins; ta.big_cap = tree_big_cap;
@@ -2139,6 +2152,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     la.tree_rng = d_rng; la.F = F; la.mtry = p.mtry; la.min_node = p.min_node_size;
     la.max_depth = p.max_depth; la.seed_lo = (uint32_t)p.seed; la.seed_hi = (uint32_t)(p.seed >> 32);
     la.depth_ptr = nullptr;
+    la.node_cap = 0;
 
     // The two level kernels of a depth are independent (disjoint nodes, disjoint entry
     // segments): a foreground fit runs the small-node kernel on a second stream of the same
@@ -2184,7 +2198,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         for (int k = 0; k < chunk; ++k, ++depth) {
             const int64_t Cb = bound(k);                        // bound on this depth's nodes
             la.nodes = nodes_cur; la.rows_in = rin; la.rows_out = rout; la.depth = depth; la.res = res;
-            la.tile_splits = block_sums;
+            la.tile_splits = block_sums; la.node_cap = (uint32_t)node_cap;
             if (fork) {
                 AIWCRF_CUDA(cudaEventRecord(fk.ev_fork, s));
                 AIWCRF_CUDA(cudaStreamWaitEvent(fk.side, fk.ev_fork, 0));
@@ -2217,7 +2231,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
             fa.cnt = d_cnt; fa.next = nodes_nxt; fa.small_list = small_a; fa.big_list = big_a;
             fa.packed = packed; fa.stats = d_stats;
             fa.next_tree_off = tree_off_nxt; fa.T = (int)T; fa.done = d_done; fa.tile_splits = block_sums;
-            fa.parity = depth & 1;
+            fa.parity = depth & 1; fa.next_cap = (uint32_t)(2 * node_cap);
             // tiles of the depth's (bounded) node count, at most four (256-thread) CTAs per SM
             const unsigned fgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + kScanTile - 1) / kScanTile, 4 * (int64_t)dev_sms));
             prof_begin(s, kProfFinalize);
@@ -2439,6 +2453,7 @@ int plan_level(FitPlan &P, cudaStream_t s, cudaStream_t side, cudaEvent_t ev_for
     la.max_depth = P.p.max_depth; la.seed_lo = (uint32_t)P.p.seed; la.seed_hi = (uint32_t)(P.p.seed >> 32);
     la.depth = 0; la.depth_ptr = &P.d_cnt->levels;
     la.nodes = nodes_in; la.rows_in = rin; la.rows_out = rout; la.res = P.res; la.tile_splits = P.block_sums;
+    la.node_cap = (uint32_t)P.C_max;
     const int bin_cap = big_bin_cap(P.p.mtry, P.F, P.max_card), big_smem = bin_cap * 14;
     la.list = P.big_l; la.list_n = &P.d_cnt->n_list[parity][1];
     const unsigned gbig = (unsigned)(P.cps_big * P.sms), gsmall = (unsigned)(P.cps_small * P.sms);
@@ -2456,7 +2471,7 @@ int plan_level(FitPlan &P, cudaStream_t s, cudaStream_t side, cudaEvent_t ev_for
     fa.cnt = P.d_cnt; fa.next = nodes_out; fa.small_list = P.small_l; fa.big_list = P.big_l;
     fa.packed = P.packed; fa.stats = P.d_stats;
     fa.next_tree_off = toff_out; fa.T = (int)P.T; fa.done = P.d_done; fa.tile_splits = P.block_sums;
-    fa.parity = parity;
+    fa.parity = parity; fa.next_cap = (uint32_t)P.C_max;
     finalize_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((P.C_max + kScanTile - 1) / kScanTile, 4 * (int64_t)P.sms)), kFinThreads, 0, s>>>(fa);
     AIWCRF_LAUNCH_CHECK("finalize_kernel");
     return AIWCRF_OK;
@@ -2677,4 +2692,8 @@ void fit_plan_free(FitPlan *P)
     delete P;
 }
 
+}  // namespace aiwcrf
+
+namespace aiwcrf {
+AIWCRF_BOUNDS_READER(bounds_flags_fit)
 }  // namespace aiwcrf

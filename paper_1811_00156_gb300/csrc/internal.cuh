@@ -46,13 +46,14 @@ constexpr uint32_t kBoundOut = 32u;      // output position (entries, children, 
 #ifdef AIWCRF_DEBUG_BOUNDS
 static __device__ unsigned int g_bounds_flag;
 
-__device__ __forceinline__ uint64_t checked_index(uint64_t i, uint64_t n, uint32_t site)
+template <typename T>
+__device__ __forceinline__ T checked_index(T i, uint64_t n, uint32_t site)
 {
-    if (i < n) return i;
+    if ((uint64_t)i < n) return i;
     atomicOr(&g_bounds_flag, site);
-    return 0;
+    return T(0);
 }
-#define AIWCRF_IDX(i, n, site) ((decltype(i))::aiwcrf::checked_index((uint64_t)(i), (uint64_t)(n), (site)))
+#define AIWCRF_IDX(i, n, site) ::aiwcrf::checked_index((i), (uint64_t)(n), (site))
 // host: this translation unit's flag, cleared by the read
 #define AIWCRF_BOUNDS_READER(fn)                                                                   \
     uint32_t fn()                                                                                   \

@@ -90,6 +90,10 @@ __device__ __forceinline__ int64_t serve_walk2(const ServeForest &sf, int t0, in
     if (COMPACT) {
         const uint32_t *n0 = sf.c32 + (t0 >= 0 ? sf.tree_off4[t0] : 0);
         const uint32_t *n1 = sf.c32 + (t1 >= 0 ? sf.tree_off4[t1] : 0);
+#ifdef AIWCRF_DEBUG_BOUNDS
+        const uint32_t m0 = t0 >= 0 ? (uint32_t)(sf.tree_off4[t0 + 1] - sf.tree_off4[t0]) : 1u;
+        const uint32_t m1 = t1 >= 0 ? (uint32_t)(sf.tree_off4[t1 + 1] - sf.tree_off4[t1]) : 1u;
+#endif
         uint32_t j0 = 0, j1 = 0;
         bool l0 = t0 < 0, l1 = t1 < 0;
         while (!(l0 && l1)) {
@@ -97,8 +101,8 @@ __device__ __forceinline__ int64_t serve_walk2(const ServeForest &sf, int t0, in
             const bool la = l0 || (int32_t)a < 0, lb = l1 || (int32_t)b < 0;
             const uint32_t ca = serve_code(kcode, la ? 0u : (a >> 24), fd, dc);
             const uint32_t cb = serve_code(kcode, lb ? 0u : (b >> 24), fd, dc);
-            j0 = la ? j0 : (a & 0xFFFFu) + (ca > ((a >> 16) & 0xFFu) ? 1u : 0u);
-            j1 = lb ? j1 : (b & 0xFFFFu) + (cb > ((b >> 16) & 0xFFu) ? 1u : 0u);
+            j0 = la ? j0 : AIWCRF_IDX((a & 0xFFFFu) + (ca > ((a >> 16) & 0xFFu) ? 1u : 0u), m0, kBoundWalk);
+            j1 = lb ? j1 : AIWCRF_IDX((b & 0xFFFFu) + (cb > ((b >> 16) & 0xFFu) ? 1u : 0u), m1, kBoundWalk);
             l0 = la;
             l1 = lb;
         }
@@ -107,6 +111,10 @@ __device__ __forceinline__ int64_t serve_walk2(const ServeForest &sf, int t0, in
     } else {
         const uint64_t *n0 = sf.cnodes + (t0 >= 0 ? sf.tree_off[t0] : 0);
         const uint64_t *n1 = sf.cnodes + (t1 >= 0 ? sf.tree_off[t1] : 0);
+#ifdef AIWCRF_DEBUG_BOUNDS
+        const uint32_t m0 = t0 >= 0 ? (uint32_t)(sf.tree_off[t0 + 1] - sf.tree_off[t0]) : 1u;
+        const uint32_t m1 = t1 >= 0 ? (uint32_t)(sf.tree_off[t1 + 1] - sf.tree_off[t1]) : 1u;
+#endif
         uint32_t j0 = 0, j1 = 0;
         bool l0 = t0 < 0, l1 = t1 < 0;
         while (!(l0 && l1)) {
@@ -114,8 +122,8 @@ __device__ __forceinline__ int64_t serve_walk2(const ServeForest &sf, int t0, in
             const bool la = l0 || (a >> 63), lb = l1 || (b >> 63);
             const uint32_t ca = serve_code(kcode, la ? 0u : (uint32_t)(a >> 56) & 0x7Fu, fd, dc);
             const uint32_t cb = serve_code(kcode, lb ? 0u : (uint32_t)(b >> 56) & 0x7Fu, fd, dc);
-            j0 = la ? j0 : ((uint32_t)(a >> 32) & 0xFFFFFFu) + (ca > ((uint32_t)a & 0xFFFFFFu) ? 1u : 0u);
-            j1 = lb ? j1 : ((uint32_t)(b >> 32) & 0xFFFFFFu) + (cb > ((uint32_t)b & 0xFFFFFFu) ? 1u : 0u);
+            j0 = la ? j0 : AIWCRF_IDX(((uint32_t)(a >> 32) & 0xFFFFFFu) + (ca > ((uint32_t)a & 0xFFFFFFu) ? 1u : 0u), m0, kBoundWalk);
+            j1 = lb ? j1 : AIWCRF_IDX(((uint32_t)(b >> 32) & 0xFFFFFFu) + (cb > ((uint32_t)b & 0xFFFFFFu) ? 1u : 0u), m1, kBoundWalk);
             l0 = la;
             l1 = lb;
         }
@@ -1199,3 +1207,7 @@ int aiwcrf_server_destroy(aiwcrf_server *server)
 }
 
 }  // extern "C"
+
+namespace aiwcrf {
+AIWCRF_BOUNDS_READER(bounds_flags_serve)
+}  // namespace aiwcrf
