@@ -57,6 +57,9 @@ def parse():
                          "(dram__bytes_read.sum, dram__bytes_write.sum, smsp__inst_executed.sum, "
                          "l1tex__data_pipe_lsu_wavefronts_mem_shared.sum) and exit")
     ap.add_argument("--counters-command", default="", help="the ncu command that made the CSV (recorded)")
+    ap.add_argument("--counters-scale", nargs="*", default=None, metavar="CLASS=FACTOR",
+                    help="keep only these classes, their instruction and wavefront counts multiplied by FACTOR "
+                         "(a smaller case scaled to the full launch)")
     ap.add_argument("--trees", type=int, default=T_TREES,
                     help="forest size per GPU; smaller values are for profiler captures only")
     ap.add_argument("--queries", type=int, default=N_QUERIES,
@@ -409,7 +412,9 @@ def run_ours(args):
         out["oob"] = oob_report(A, wl, X, f)
         del f
         out["loko"] = loko_report(A, dev)
-        out["per_row"] = per_row_report(A, dev)
+        # 20 of the 500 trees: on this reading the level kernels' bin-group histograms take
+        # about 160 ms per tree (rows.trees/s is per tree)
+        out["per_row"] = per_row_report(A, dev, n_trees=20)
         f = A.aiwcrf_fit(params, X, y)
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
@@ -519,6 +524,7 @@ def per_row_report(A, dev, n_trees: int = T_TREES, steps: int = 1):
     achieved = alg / (scan_ms / 1e3) / 1e9 if scan_ms else None
     return {"workload": f"aiwc-111000 per-row features: fit {n_trees} trees (mtry 10, min_node 5) on 111,000 "
                         "rows x 32 features, every row its own feature vector",
+            "trees": n_trees,
             "fit_ms": ms / steps, "rows_trees_per_s": wl.n_rows * n_trees * steps / (ms / 1e3),
             "stats": st,
             "roofline_fit": {"kernels": "level_big + level_small (histogram, scan, argmax, partition)",
@@ -842,7 +848,7 @@ COUNTER_METRICS = {"dram__bytes_read.sum": "dram_bytes", "dram__bytes_write.sum"
                    "smsp__inst_executed.sum": "inst", "l1tex__data_pipe_lsu_wavefronts_mem_shared.sum": "smem_wavefronts"}
 
 
-def write_counters(csv_path: str, command: str, out_path: str | None = None) -> dict:
+def write_counters(csv_path: str, command: str, out_path: str | None = None, scale: dict | None = None) -> dict:
     """Per-launch ncu counters of each kernel class from an ncu --csv capture (metrics of
     COUNTER_METRICS), keyed by the kernel source hash so that the bench reports them only while
     the kernels are unchanged. Classes: tree, level_big, level_small (one kernel each); walk
@@ -853,8 +859,8 @@ def write_counters(csv_path: str, command: str, out_path: str | None = None) -> 
     hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
     hdr = rows[hi]
     ki, ii, mi, ui, vi = (hdr.index(c) for c in ("Kernel Name", "ID", "Metric Name", "Metric Unit", "Metric Value"))
-    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9, "": 1,
-             "inst": 1, "warp": 1}
+    unit = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9, "": 1,
+            "inst": 1, "warp": 1}
     launches = {}                                   # launch ID -> [kernel name, {counter: value}]
     for r in rows[hi + 1:]:
         if len(r) != len(hdr) or r[mi] not in COUNTER_METRICS:
@@ -862,7 +868,7 @@ def write_counters(csv_path: str, command: str, out_path: str | None = None) -> 
         name = r[ki].split("(")[0].split("<")[0].split("::")[-1].replace("void ", "").strip()
         e = launches.setdefault(int(r[ii]), [name, {}])
         c = COUNTER_METRICS[r[mi]]
-        e[1][c] = e[1].get(c, 0.0) + float(r[vi].replace(",", "")) * scale.get(r[ui], 1)
+        e[1][c] = e[1].get(c, 0.0) + float(r[vi].replace(",", "")) * unit.get(r[ui], 1)
     per = {}                                        # class -> list of per-launch (or per-call) counters
     in_predict, acc = False, {}
     for lid in sorted(launches):
@@ -883,9 +889,17 @@ def write_counters(csv_path: str, command: str, out_path: str | None = None) -> 
     sha = source_sha()
     out = {}
     for cls, v in per.items():
+        if scale is not None and cls not in scale:
+            continue
         keys = sorted({k for c in v for k in c})
         out[cls] = {k: sum(c.get(k, 0.0) for c in v) / len(v) for k in keys}
         out[cls].update({"launches": len(v), "source_sha": sha, "command": command})
+        if scale is not None:
+            # a smaller case scaled to a full launch by the units it processes: instructions and
+            # shared wavefronts grow in proportion; DRAM bytes (cache reuse) do not and are dropped
+            out[cls] = {k: (x * scale[cls] if k in ("inst", "smem_wavefronts") else x)
+                        for k, x in out[cls].items() if k != "dram_bytes"}
+            out[cls]["scaled_by"] = scale[cls]
     path = out_path or os.path.join(ROOT, "profiles", "counters.json")
     old = json.load(open(path)) if os.path.exists(path) else {}
     old.update(out)
@@ -897,7 +911,10 @@ def write_counters(csv_path: str, command: str, out_path: str | None = None) -> 
 def main():
     args = parse()
     if args.write_counters:
-        print(json.dumps(write_counters(args.write_counters, args.counters_command)))
+        scale = None
+        if args.counters_scale is not None:
+            scale = {kv.split("=")[0]: float(kv.split("=")[1]) for kv in args.counters_scale}
+        print(json.dumps(write_counters(args.write_counters, args.counters_command, scale=scale)))
         return
     if args.impl == "reference":
         run_reference(args)

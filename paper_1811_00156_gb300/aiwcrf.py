@@ -13,8 +13,11 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-# AIWCRF_LIB=debug selects the bounds-checking build (libaiwcrf_debug.so), for tests
-LIB_PATH = os.path.join(_HERE, "libaiwcrf_debug.so" if os.environ.get("AIWCRF_LIB") == "debug" else "libaiwcrf.so")
+# AIWCRF_LIB=debug selects the bounds-checking build (libaiwcrf_debug.so), for tests;
+# AIWCRF_LIB_PATH names another build of the same library (for example one compiled with other
+# tuning macros)
+LIB_PATH = os.environ.get("AIWCRF_LIB_PATH") or os.path.join(
+    _HERE, "libaiwcrf_debug.so" if os.environ.get("AIWCRF_LIB") == "debug" else "libaiwcrf.so")
 
 AIWCRF_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "NAN_INPUT", -3: "BAD_POINTER", -4: "OOM", -5: "CUDA",

@@ -82,31 +82,83 @@ __global__ void key_init_kernel(const float *__restrict__ X, int64_t N, uint32_t
     vals[(size_t)f * (size_t)N + i] = (uint32_t)i;
 }
 
-// dense ranks of one sorted column per CTA: equal keys share a rank
-__global__ void __launch_bounds__(1024) dense_rank_kernel(const uint32_t *__restrict__ keys,
-                                                          const uint32_t *__restrict__ idx, int64_t N,
-                                                          uint32_t *__restrict__ Rcol, float *__restrict__ vals,
-                                                          uint32_t *__restrict__ card, uint32_t *err)
+// Dense ranks of the sorted columns (equal keys share a rank; the rank -> value table and every
+// column's value count), with the columns cut into chunks of kRankChunk sorted keys (many CTAs
+// per column): rank_count_kernel counts each chunk's distinct-value starts, rank_write_kernel
+// adds the counts of the column's earlier chunks to its own block scan.
+constexpr int kRankThreads = 1024;
+constexpr int kRankChunk = 4 * kRankThreads;
+
+__global__ void __launch_bounds__(kRankThreads) rank_count_kernel(const uint32_t *__restrict__ keys, int64_t N,
+                                                                  uint32_t *__restrict__ chunk_count)
 {
     __shared__ uint32_t warp_tmp[32];
-    const int f = blockIdx.x, tid = threadIdx.x;
+    const int f = blockIdx.y;
     const size_t off = (size_t)f * (size_t)N;
-    uint32_t running = 0;
-    for (int64_t t0 = 0; t0 < N; t0 += 1024) {
-        const int64_t i = t0 + tid;
+    const int64_t i0 = (int64_t)blockIdx.x * kRankChunk;
+    uint32_t c = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int64_t i = i0 + u * kRankThreads + threadIdx.x;
+        if (i < N && (i == 0 || keys[off + i - 1] != keys[off + i])) ++c;
+    }
+    uint32_t tot;
+    block_incl_scan(c, warp_tmp, tot);
+    if (threadIdx.x == 0) chunk_count[(size_t)f * gridDim.x + blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kRankThreads) rank_write_kernel(const uint32_t *__restrict__ keys,
+                                                                  const uint32_t *__restrict__ idx, int64_t N,
+                                                                  const uint32_t *__restrict__ chunk_count,
+                                                                  uint32_t *__restrict__ Rcol, float *__restrict__ vals,
+                                                                  uint32_t *__restrict__ card)
+{
+    __shared__ uint32_t warp_tmp[32];
+    __shared__ uint32_t s_base;
+    const int f = blockIdx.y, tid = threadIdx.x;
+    const size_t off = (size_t)f * (size_t)N;
+    if (tid < 32) {                        // distinct values before this chunk
+        uint32_t b = 0;
+        for (uint32_t c = tid; c < blockIdx.x; c += 32) b += chunk_count[(size_t)f * gridDim.x + c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(kFull, b, o);
+        if (tid == 0) s_base = b;
+    }
+    __syncthreads();
+    uint32_t running = s_base;
+    const int64_t i0 = (int64_t)blockIdx.x * kRankChunk;
+    for (int u = 0; u < 4; ++u) {                                  // block-uniform
+        const int64_t i = i0 + u * kRankThreads + tid;
         const bool valid = i < N;
         const uint32_t k = valid ? keys[off + i] : 0u;
         const uint32_t flag = (valid && (i == 0 || keys[off + i - 1] != k)) ? 1u : 0u;
         uint32_t tot;
         const uint32_t incl = block_incl_scan(flag, warp_tmp, tot);
         if (valid) {
-            const uint32_t r = running + incl - 1u;             // < N < 2^22
+            const uint32_t r = running + incl - 1u;                 // < N < 2^22
             Rcol[off + idx[off + i]] = r;
             if (flag) vals[off + r] = key_float(k);
         }
         running += tot;
     }
-    if (tid == 0) card[f] = running;
+    if (tid == 0 && blockIdx.x == gridDim.x - 1) card[f] = running;
+}
+
+int dense_ranks(const uint32_t *keys, const uint32_t *idx, int64_t N, int F, uint32_t *chunk_count, uint32_t *Rcol,
+                float *vals, uint32_t *card, cudaStream_t s)
+{
+    const dim3 grid((unsigned)((N + kRankChunk - 1) / kRankChunk), (unsigned)F);
+    rank_count_kernel<<<grid, kRankThreads, 0, s>>>(keys, N, chunk_count);
+    rank_write_kernel<<<grid, kRankThreads, 0, s>>>(keys, idx, N, chunk_count, Rcol, vals, card);
+    count_launches(2);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "dense rank launch");
+    return AIWCRF_OK;
+}
+
+size_t dense_rank_chunk_words(int64_t N, int F)
+{
+    return (size_t)((N + kRankChunk - 1) / kRankChunk) * (size_t)F;
 }
 
 // Row-major copy of the ranks: the tried features of one row share one record.
@@ -172,6 +224,18 @@ __global__ void group_offsets_kernel(const uint32_t *__restrict__ flags, const u
     }
 }
 
+// group order: y of every position (rows in group order) and the group it belongs to (flags
+// mark group starts, excl is their exclusive scan)
+__global__ void group_order_kernel(const uint32_t *__restrict__ rows, const uint32_t *__restrict__ flags,
+                                   const uint32_t *__restrict__ excl, const int64_t *__restrict__ y, int64_t N,
+                                   int64_t *__restrict__ y_g, uint32_t *__restrict__ grp_of)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    y_g[k] = y[rows[k]];
+    grp_of[k] = excl[k] + flags[k] - 1u;
+}
+
 // ------------------------------------------------------------------------------------------
 // a2: bootstrap, one CTA per tree. Multiplicities are byte counters per row, packed four to a
 // word, in shared memory when they fit, else in a per-tree global scratch. Entries are then
@@ -204,6 +268,11 @@ struct BootArgs {
     uint32_t *inbag;                // per tree ceil(N / 32) words: bit r set = row r drawn (or null)
     int64_t inbag_words;
     int store_group;                // entries name their group (tree-resident growth) instead of a row
+    // group-ordered pass (when set): y in group order and the group of every group-ordered
+    // position; the per-group sums (sum w, sum w*y) go to gsum, 2 * G words per tree
+    const int64_t *y_g;
+    const uint32_t *grp_of;
+    unsigned long long *gsum;
 };
 
 __global__ void __launch_bounds__(kBootThreads) bootstrap_kernel(BootArgs a)
@@ -264,19 +333,58 @@ __global__ void __launch_bounds__(kBootThreads) bootstrap_kernel(BootArgs a)
     long long acc_s = 0;
     Entry *out = a.rows_out + (size_t)t * (size_t)a.row_cap;
     const uint32_t G = a.G_ptr ? *a.G_ptr : a.G;
+    // group-ordered pass: every position k of the group order (coalesced row and y reads) adds
+    // its row's w and w*y to its group's shared-memory sums, one atomic per run of a group
+    // within a warp (groups are contiguous in that order)
+    unsigned long long *gsum = nullptr;
+    if (a.y_g) {
+        gsum = a.gsum + (size_t)t * 2 * (size_t)G;
+        for (uint32_t g = tid; g < 2 * G; g += kBootThreads) gsum[g] = 0ull;
+        __syncthreads();
+        for (int64_t k0 = 0; k0 < a.N; k0 += kBootThreads) {
+            const int64_t k = k0 + tid;
+            const bool valid = k < a.N;
+            uint32_t w = 0u, g = 0xFFFFFFFFu;
+            long long wy = 0ll;
+            if (valid) {
+                const uint32_t row = a.grp_rows[k];
+                g = a.grp_of[k];
+                w = (cnt[row >> 2] >> (8u * (row & 3u))) & 255u;
+                if (w) wy = (long long)w * a.y_g[k];
+            }
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t tw = __shfl_up_sync(kFull, w, o);
+                const long long ty = __shfl_up_sync(kFull, wy, o);
+                const uint32_t tg = __shfl_up_sync(kFull, g, o);
+                if (lane >= o && tg == g) { w += tw; wy += ty; }
+            }
+            const uint32_t ng = __shfl_down_sync(kFull, g, 1);
+            if (valid && w && (lane == 31 || ng != g)) {
+                atomicAdd(&gsum[2 * (size_t)g], (unsigned long long)w);
+                atomicAdd(&gsum[2 * (size_t)g + 1], (unsigned long long)wy);
+            }
+        }
+        __syncthreads();
+    }
     for (uint32_t g0 = 0; g0 < G; g0 += kBootThreads) {
         const uint32_t g = g0 + tid;
         uint32_t sw = 0, rep = 0;
         long long swy = 0;
         if (g < G) {
-            const uint32_t e = a.grp_off[g + 1];
             rep = a.grp_rows[a.grp_off[g]];
-            for (uint32_t k = a.grp_off[g]; k < e; ++k) {
-                const uint32_t row = a.grp_rows[k];
-                const uint32_t w = (cnt[row >> 2] >> (8u * (row & 3u))) & 255u;
-                if (w) {
-                    sw += w;
-                    swy += (long long)w * a.y[row];
+            if (gsum) {                 // the sums were made by L2 atomics: read them from L2
+                sw = (uint32_t)__ldcg(&gsum[2 * (size_t)g]);
+                swy = (long long)__ldcg(&gsum[2 * (size_t)g + 1]);
+            } else {
+                const uint32_t e = a.grp_off[g + 1];
+                for (uint32_t k = a.grp_off[g]; k < e; ++k) {
+                    const uint32_t row = a.grp_rows[k];
+                    const uint32_t w = (cnt[row >> 2] >> (8u * (row & 3u))) & 255u;
+                    if (w) {
+                        sw += w;
+                        swy += (long long)w * a.y[row];
+                    }
                 }
             }
         }
@@ -472,7 +580,7 @@ __device__ __forceinline__ void small_node(const LevelArgs &a, const RT *__restr
     j = AIWCRF_IDX(j, a.node_cap, kBoundNode);
     const NodeRec nd = a.nodes[j];
     if (node_stops(a, nd)) {
-        if (lane == 0) write_leaf(a.res, j, -2, round_mean(nd.S, nd.n));
+        if (lane == 0) write_leaf(a.res, j, -2, 0);
         return;
     }
     const size_t tb = (size_t)nd.tree * (size_t)a.row_cap + nd.start;
@@ -535,7 +643,7 @@ __device__ __forceinline__ void small_node(const LevelArgs &a, const RT *__restr
     }
     best = warp_best(best, nd.n, nd.S);
     if (best.h < 0.0f) {
-        if (lane == 0) write_leaf(a.res, j, -1, round_mean(nd.S, nd.n));
+        if (lane == 0) write_leaf(a.res, j, -1, 0);
         return;
     }
     // partition: entry i on lane i
@@ -555,7 +663,7 @@ __device__ __forceinline__ void small_node(const LevelArgs &a, const RT *__restr
     if (lane == 0) {
         SplitRes sr;
         sr.feature = best.f; sr.rank = best.r;
-        sr.thr_bits = __float_as_uint(a.vals[(size_t)best.f * (size_t)a.N + best.r]);
+        sr.thr_bits = 0u;                                   // looked up where the node is encoded
         sr.nL = best.nL; sr.lenL = lenL; sr.pad = 0u; sr.v = best.SL;
         a.res[j] = sr;
         atomicAdd(&a.tile_splits[(uint32_t)j / (uint32_t)kScanTile], 1u);
@@ -617,7 +725,7 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
     j = AIWCRF_IDX(j, a.node_cap, kBoundNode);
     const NodeRec nd = a.nodes[j];
     if (node_stops(a, nd)) {
-        if (tid == 0) write_leaf(a.res, j, -2, round_mean(nd.S, nd.n));
+        if (tid == 0) write_leaf(a.res, j, -2, 0);
         return;
     }
     const size_t tb = (size_t)nd.tree * (size_t)a.row_cap + nd.start;
@@ -820,7 +928,7 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
     __syncthreads();
     const Cand win = winner;
     if (win.h < 0.0f) {
-        if (tid == 0) write_leaf(a.res, j, -1, round_mean(nd.S, nd.n));
+        if (tid == 0) write_leaf(a.res, j, -1, 0);
         return;
     }
 
@@ -855,7 +963,7 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
     if (tid == 0) {
         SplitRes sr;
         sr.feature = win.f; sr.rank = win.r;
-        sr.thr_bits = __float_as_uint(a.vals[(size_t)win.f * (size_t)a.N + win.r]);
+        sr.thr_bits = 0u;                                   // looked up where the node is encoded
         sr.nL = win.nL; sr.lenL = lenL; sr.pad = 0u; sr.v = win.SL;
         a.res[j] = sr;
         atomicAdd(&a.tile_splits[(uint32_t)j / (uint32_t)kScanTile], 1u);
@@ -893,7 +1001,17 @@ __global__ void __launch_bounds__(kBigThreads, kBigCtasPerSm) level_big_kernel(L
 // same node for node: the same BFS numbering, mtry draws, exact candidate comparison,
 // tie-breaks and leaf values.
 // ------------------------------------------------------------------------------------------
-constexpr int kTreeThreads = 256;
+// build-time tuning of the tree kernel (the forest does not depend on them)
+#ifndef AIWCRF_TREE_THREADS
+#define AIWCRF_TREE_THREADS 256        // threads per CTA
+#endif
+#ifndef AIWCRF_TREE_UNROLL
+#define AIWCRF_TREE_UNROLL 0           // 1: small-node sort and scan unrolled per segment width
+#endif
+#ifndef AIWCRF_TREE_PREFETCH
+#define AIWCRF_TREE_PREFETCH 1         // small-node passes whose ranks are loaded together
+#endif
+constexpr int kTreeThreads = AIWCRF_TREE_THREADS;
 constexpr int kTreeWarps = kTreeThreads / 32;
 constexpr int kTreeCtasPerSm = 4;      // resident CTAs per SM the tree kernel is compiled for
 constexpr int kTreeIlp = 8;            // rank loads in flight per lane in a histogram pass
@@ -947,6 +1065,7 @@ struct TreeSmem {
     uint8_t *flag;
     uint32_t *bins;
     uint16_t *big[2];
+    uint32_t *big_mask;      // tried features of the depth's big nodes (aliases flag)
 };
 
 __device__ __forceinline__ TreeSmem tree_smem(unsigned char *base, const TreeArgs &a)
@@ -963,6 +1082,9 @@ __device__ __forceinline__ TreeSmem tree_smem(unsigned char *base, const TreeArg
     m.bins = reinterpret_cast<uint32_t *>(p); p += (size_t)kTreeWarps * (size_t)a.bins * 12;
     m.big[0] = reinterpret_cast<uint16_t *>(p); p += ((size_t)a.big_cap * 2 + 15) & ~(size_t)15;
     m.big[1] = reinterpret_cast<uint16_t *>(p);
+    // the big nodes' masks are read in phase A only, the partition flags written in phase B only:
+    // they share the flag array (4 * big_cap <= its 16-byte-rounded ecap bytes)
+    m.big_mask = reinterpret_cast<uint32_t *>(m.flag);
     return m;
 }
 
@@ -976,13 +1098,75 @@ __device__ __forceinline__ bool tnode_big(const TreeArgs &a, const TNode &nd, ui
     return nd.len > (uint32_t)kSmallNodeRows && !tnode_stops(a, nd.n, depth);
 }
 
+// One pass of a small node's search with K-entry segments (K a power of two): the keys
+// (rank, entry lane) of every segment sorted by a bitonic network, then the prefix of (w, w*y)
+// in that order. r: this lane's rank in sorted order; nr: the next lane's (sentinel at the end).
+template <int K>
+__device__ __forceinline__ void small_sort_scan(uint32_t rank, int pos, int lane, uint32_t w_live, long long wy_live,
+                                                uint32_t &r, uint32_t &cw, long long &cs, uint32_t &nr)
+{
+    uint32_t key = (rank << 5) | (uint32_t)pos;
+#pragma unroll
+    for (int k = 2; k <= K; k <<= 1) {
+#pragma unroll
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            const uint32_t ok = __shfl_xor_sync(kFull, key, jj);
+            const bool asc = (pos & k) == 0;
+            const bool lower = (pos & jj) == 0;
+            key = ((lower == asc) ? (ok < key) : (ok > key)) ? ok : key;
+        }
+    }
+    const int src = (lane & ~(K - 1)) | (int)(key & 31u);
+    r = key >> 5;
+    cw = __shfl_sync(kFull, w_live, src);
+    cs = __shfl_sync(kFull, wy_live, src);
+#pragma unroll
+    for (int o = 1; o < K; o <<= 1) {
+        const uint32_t tw = __shfl_up_sync(kFull, cw, o);
+        const long long ts = __shfl_up_sync(kFull, cs, o);
+        if (pos >= o) { cw += tw; cs += ts; }
+    }
+    nr = __shfl_down_sync(kFull, r, 1);
+    if (pos == K - 1) nr = kRankSentinel;
+}
+
+constexpr int kSmallPrefetch = AIWCRF_TREE_PREFETCH;   // passes whose ranks a small node loads at once
+
+// the same pass with the segment width a runtime value (one loop for every width)
+__device__ __forceinline__ void small_sort_scan_rt(int K, uint32_t rank, int pos, int lane, uint32_t w_live,
+                                                   long long wy_live, uint32_t &r, uint32_t &cw, long long &cs,
+                                                   uint32_t &nr)
+{
+    uint32_t key = (rank << 5) | (uint32_t)pos;
+    for (int k = 2; k <= K; k <<= 1) {
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            const uint32_t ok = __shfl_xor_sync(kFull, key, jj);
+            const bool asc = (pos & k) == 0;
+            const bool lower = (pos & jj) == 0;
+            key = ((lower == asc) ? (ok < key) : (ok > key)) ? ok : key;
+        }
+    }
+    const int src = (lane & ~(K - 1)) | (int)(key & 31u);
+    r = key >> 5;
+    cw = __shfl_sync(kFull, w_live, src);
+    cs = __shfl_sync(kFull, wy_live, src);
+    for (int o = 1; o < K; o <<= 1) {
+        const uint32_t tw = __shfl_up_sync(kFull, cw, o);
+        const long long ts = __shfl_up_sync(kFull, cs, o);
+        if (pos >= o) { cw += tw; cs += ts; }
+    }
+    nr = __shfl_down_sync(kFull, r, 1);
+    if (pos == K - 1) nr = kRankSentinel;
+}
+
 // A small node (or a node that stops) searched whole by one warp: as small_node, on the tree's
-// shared-memory entries and the group records.
+// shared-memory entries and the group records, with the passes' rank loads issued together and
+// the sort and scan unrolled for the node's segment width.
 __device__ __forceinline__ void tree_small_node(const TreeArgs &a, const TreeSmem &sm, const uint16_t *ix, uint16_t *ox,
                                                 const TNode &nd, uint32_t tg, uint32_t depth, SplitRes *res_j, int lane)
 {
     if (tnode_stops(a, nd.n, depth)) {
-        if (lane == 0) write_leaf(res_j, 0, -2, round_mean(nd.S, nd.n));
+        if (lane == 0) write_leaf(res_j, 0, -2, 0);
         return;
     }
     const int len = nd.len;
@@ -1004,47 +1188,55 @@ __device__ __forceinline__ void tree_small_node(const TreeArgs &a, const TreeSme
     const int f_lane = lane < n_tried ? nth_feature(mask, lane) : -1;
 
     Cand best = cand_none();
-    for (int q0 = 0; q0 < n_tried; q0 += P) {
-        const int qf = q0 + seg;
-        const int fs = __shfl_sync(kFull, f_lane, qf & 31);
-        const int f = qf < n_tried ? fs : -1;
-        const bool live = valid && f >= 0;
-        const uint32_t rank = live ? (uint32_t)__ldg(&rec[f]) : kRankSentinel;
-        const uint32_t rank0 = __shfl_sync(kFull, rank, lane & ~(K - 1));
-        if (__all_sync(kFull, !live || rank == rank0)) continue;
-        uint32_t key = (rank << 5) | (uint32_t)pos;
-        for (int k = 2; k <= K; k <<= 1) {
-            for (int jj = k >> 1; jj > 0; jj >>= 1) {
-                const uint32_t ok = __shfl_xor_sync(kFull, key, jj);
-                const bool asc = (pos & k) == 0;
-                const bool lower = (pos & jj) == 0;
-                key = ((lower == asc) ? (ok < key) : (ok > key)) ? ok : key;
+    for (int q0 = 0; q0 < n_tried; q0 += kSmallPrefetch * P) {
+        uint32_t rk[kSmallPrefetch];
+#pragma unroll
+        for (int u = 0; u < kSmallPrefetch; ++u) {
+            const int qf = q0 + u * P + seg;
+            const int fs = __shfl_sync(kFull, f_lane, qf & 31);
+            rk[u] = (valid && qf < n_tried) ? (uint32_t)__ldg(&rec[fs]) : kRankSentinel;
+        }
+#pragma unroll
+        for (int u = 0; u < kSmallPrefetch; ++u) {
+            if (q0 + u * P >= n_tried) break;                       // warp-uniform
+            const int qf = q0 + u * P + seg;
+            const int fs = __shfl_sync(kFull, f_lane, qf & 31);
+            const int f = qf < n_tried ? fs : -1;
+            const bool live = valid && f >= 0;
+            const uint32_t rank = rk[u];
+            // a pass whose features are all constant over the node has no boundary (lane seg*K
+            // always holds an entry; the shuffle runs in every lane before the vote)
+            const uint32_t rank0 = __shfl_sync(kFull, rank, lane & ~(K - 1));
+            if (__all_sync(kFull, !live || rank == rank0)) continue;
+            uint32_t r, cw, nr;
+            long long cs;
+            const uint32_t wl = live ? ew : 0u;
+            const long long yl = live ? ewy : 0ll;
+#if AIWCRF_TREE_UNROLL
+            switch (K) {                                            // warp-uniform
+            case 2: small_sort_scan<2>(rank, pos, lane, wl, yl, r, cw, cs, nr); break;
+            case 4: small_sort_scan<4>(rank, pos, lane, wl, yl, r, cw, cs, nr); break;
+            case 8: small_sort_scan<8>(rank, pos, lane, wl, yl, r, cw, cs, nr); break;
+            case 16: small_sort_scan<16>(rank, pos, lane, wl, yl, r, cw, cs, nr); break;
+            default: small_sort_scan<32>(rank, pos, lane, wl, yl, r, cw, cs, nr); break;
             }
-        }
-        const int src = (lane & ~(K - 1)) | (int)(key & 31u);
-        const uint32_t r = key >> 5;
-        uint32_t cw = __shfl_sync(kFull, live ? ew : 0u, src);
-        long long cs = __shfl_sync(kFull, live ? ewy : 0ll, src);
-        for (int o = 1; o < K; o <<= 1) {
-            const uint32_t tw = __shfl_up_sync(kFull, cw, o);
-            const long long ts = __shfl_up_sync(kFull, cs, o);
-            if (pos >= o) { cw += tw; cs += ts; }
-        }
-        uint32_t nr = __shfl_down_sync(kFull, r, 1);
-        if (pos == K - 1) nr = kRankSentinel;
-        if (f >= 0 && r != kRankSentinel && nr != kRankSentinel && r != nr) {
-            const i128_t delta = cand_delta(nd.n, nd.S, cw, cs);
-            if (delta != 0) {
-                Cand cd;
-                cd.h = cand_h(delta, nd.n, cw);
-                cd.f = f; cd.r = r; cd.nL = cw; cd.SL = cs;
-                if (cand_better(cd, best, nd.n, nd.S)) best = cd;
+#else
+            small_sort_scan_rt(K, rank, pos, lane, wl, yl, r, cw, cs, nr);
+#endif
+            if (f >= 0 && r != kRankSentinel && nr != kRankSentinel && r != nr) {
+                const i128_t delta = cand_delta(nd.n, nd.S, cw, cs);
+                if (delta != 0) {
+                    Cand cd;
+                    cd.h = cand_h(delta, nd.n, cw);
+                    cd.f = f; cd.r = r; cd.nL = cw; cd.SL = cs;
+                    if (cand_better(cd, best, nd.n, nd.S)) best = cd;
+                }
             }
         }
     }
     best = warp_best(best, nd.n, nd.S);
     if (best.h < 0.0f) {
-        if (lane == 0) write_leaf(res_j, 0, -1, round_mean(nd.S, nd.n));
+        if (lane == 0) write_leaf(res_j, 0, -1, 0);
         return;
     }
     // partition: entry i on lane i
@@ -1060,7 +1252,7 @@ __device__ __forceinline__ void tree_small_node(const TreeArgs &a, const TreeSme
     if (lane == 0) {
         SplitRes sr;
         sr.feature = best.f; sr.rank = best.r;
-        sr.thr_bits = __float_as_uint(a.vals[(size_t)best.f * (size_t)a.N + best.r]);
+        sr.thr_bits = 0u;                                   // looked up where the node is encoded
         sr.nL = best.nL; sr.lenL = lenL; sr.pad = 0u; sr.v = best.SL;
         *res_j = sr;
     }
@@ -1069,10 +1261,9 @@ __device__ __forceinline__ void tree_small_node(const TreeArgs &a, const TreeSme
 // Work item (big node, k-th tried feature): a warp-private histogram over the feature's ranks,
 // its scan, and the best candidate of the feature.
 __device__ __forceinline__ void tree_big_item(const TreeArgs &a, const TreeSmem &sm, const uint16_t *ix, const TNode &nd,
-                                              uint32_t tg, uint32_t depth, int k, uint32_t *bins, Cand *out, int lane)
+                                              uint32_t tried, int k, uint32_t *bins, Cand *out, int lane)
 {
-    uint32_t mask[4];
-    warp_mtry_s(a.F, a.mtry, depth, a.seed_lo, a.seed_hi, tg, nd.idx, mask);
+    uint32_t mask[4] = {tried, 0u, 0u, 0u};
     const int f = nth_feature(mask, k);
     const int card = (int)__ldg(&a.card[f]);
     uint32_t *bw = bins, *blo = bins + a.bins;
@@ -1155,7 +1346,7 @@ __device__ __forceinline__ void tree_big_split(const TreeArgs &a, const TreeSmem
     Cand c = lane < m ? cands[lane] : cand_none();
     c = warp_best(c, nd.n, nd.S);
     if (c.h < 0.0f) {
-        if (lane == 0) write_leaf(res_j, 0, -1, round_mean(nd.S, nd.n));
+        if (lane == 0) write_leaf(res_j, 0, -1, 0);
         return;
     }
     const int len = nd.len;
@@ -1200,7 +1391,7 @@ __device__ __forceinline__ void tree_big_split(const TreeArgs &a, const TreeSmem
     if (lane == 0) {
         SplitRes sr;
         sr.feature = c.f; sr.rank = c.r;
-        sr.thr_bits = __float_as_uint(a.vals[(size_t)c.f * (size_t)a.N + c.r]);
+        sr.thr_bits = 0u;                                   // looked up where the node is encoded
         sr.nL = c.nL; sr.lenL = lenL; sr.pad = 0u; sr.v = c.SL;
         *res_j = sr;
     }
@@ -1253,13 +1444,23 @@ __global__ void __launch_bounds__(kTreeThreads, kTreeCtasPerSm) tree_grow_kernel
             uint16_t *ox = sm.ix[p ^ 1];
             const uint16_t *big = sm.big[p];
             const uint32_t nb = s_nb[p];
+            // the big nodes' tried features, once per node (their items share them)
+            if (nb) {
+                for (uint32_t bi = (uint32_t)warp; bi < nb; bi += kTreeWarps) {
+                    const TNode nd = cn[AIWCRF_IDX(big[bi], a.ecap, kBoundNode)];
+                    uint32_t mask[4];
+                    warp_mtry_s(a.F, a.mtry, depth, a.seed_lo, a.seed_hi, tg, nd.idx, mask);
+                    if (lane == 0) sm.big_mask[bi] = mask[0];
+                }
+                __syncthreads();
+            }
             // A: big-node feature items first (they are the long ones), then the small nodes
             const uint32_t items = nb * (uint32_t)m + C;
             for (uint32_t j = (uint32_t)warp; j < items; j += kTreeWarps) {
                 if (j < nb * (uint32_t)m) {
                     const uint32_t bi = j / (uint32_t)m, k = j - bi * (uint32_t)m;
                     const TNode nd = cn[AIWCRF_IDX(big[bi], a.ecap, kBoundNode)];
-                    tree_big_item(a, sm, ix, nd, tg, depth, (int)k, wbins, &cands[(size_t)bi * 32 + k], lane);
+                    tree_big_item(a, sm, ix, nd, sm.big_mask[bi], (int)k, wbins, &cands[(size_t)bi * 32 + k], lane);
                 } else {
                     const uint32_t i = j - nb * (uint32_t)m;
                     const TNode nd = cn[i];
@@ -1292,7 +1493,9 @@ __global__ void __launch_bounds__(kTreeThreads, kTreeCtasPerSm) tree_grow_kernel
                 if (valid) {
                     const uint32_t pos = base + i;
                     const uint32_t left = base + C + 2u * loc;
-                    const uint64_t node = split ? encode_split(r.feature, left, r.thr_bits) : encode_leaf(r.v);
+                    const uint64_t node =
+                        split ? encode_split(r.feature, left, __float_as_uint(a.vals[(size_t)r.feature * (size_t)a.N + r.rank]))
+                              : encode_leaf(round_mean(nd.S, nd.n));
                     onodes[AIWCRF_IDX(pos, a.node_cap, kBoundOut)] = node;
                     ocnodes[AIWCRF_IDX(pos, a.node_cap, kBoundOut)] = split ? encode_split_coded(r.feature, left, r.rank) : node;
                     if (split) {
@@ -1451,6 +1654,8 @@ struct FinalArgs {
     uint32_t *excl_out;            // n + 1: exclusive split count of every node (written here)
     int parity;                    // this depth's parity: its list counts, cleared at the end
     uint32_t next_cap;             // entries of the next depth's node table (debug bounds checks)
+    const float *vals;             // rank -> value tables [F][N]: thresholds of the splits
+    int64_t N;
 };
 
 __device__ __forceinline__ void push_list(int32_t *list, uint32_t *counter, bool want, int32_t value)
@@ -1526,7 +1731,10 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(FinalArgs a)
             PackedRec pr;
             pr.tree = t;
             pr.pos = base_t + nd.idx;
-            pr.node = split ? encode_split(r.feature, base_t + cnt_t + 2u * local, r.thr_bits) : encode_leaf(r.v);
+            // a leaf's value: one thread per node, here (the searches leave it to this pass)
+            pr.node = split ? encode_split(r.feature, base_t + cnt_t + 2u * local,
+                                           __float_as_uint(a.vals[(size_t)r.feature * (size_t)a.N + r.rank]))
+                            : encode_leaf(round_mean(nd.S, nd.n));
             pr.cnode = split ? encode_split_coded(r.feature, base_t + cnt_t + 2u * local, r.rank) : pr.node;
             packed[j] = pr;
         }
@@ -1895,8 +2103,8 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         key_init_kernel<<<dim3(yblocks, (unsigned)F), 256, 0, s>>>(dX, N, kA, vA, d_err);
         AIWCRF_LAUNCH_CHECK("key_init_kernel");
         if ((rc = radix_sort_segments(kA, vA, kB, vB, N, F, N, hist, s)) != AIWCRF_OK) return rc;
-        dense_rank_kernel<<<F, 1024, 0, s>>>(kA, vA, N, d_R, d_vals, d_card, d_err);
-        AIWCRF_LAUNCH_CHECK("dense_rank_kernel");
+        // the sort's histogram scratch is free again: it holds the chunk counts
+        if ((rc = dense_ranks(kA, vA, N, F, hist, d_R, d_vals, d_card, s)) != AIWCRF_OK) return rc;
         prof_end(s, kProfRank);
         std::vector<uint32_t> h_card((size_t)F);
         uint32_t h_err = 0;
@@ -1936,6 +2144,11 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         AIWCRF_CUDA(cudaStreamSynchronize(s));
     }
     const uint32_t *grp_rows = vA;            // rows in group order
+    // the bootstrap's group-ordered pass: y in group order and every position's group
+    int64_t *d_y_g = sc.get<int64_t>((size_t)N, &rc); if (rc) return rc;
+    uint32_t *d_grp_of = sc.get<uint32_t>((size_t)N, &rc); if (rc) return rc;
+    group_order_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(vA, kB, vB, dy, N, d_y_g, d_grp_of);
+    AIWCRF_LAUNCH_CHECK("group_order_kernel");
     sc.drop(d_R); sc.drop(kA); sc.drop(kB); sc.drop(vB); sc.drop(hist);
     row_cap = std::min<int64_t>(row_cap, (int64_t)n_groups);
 
@@ -2056,6 +2269,10 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
             gstride = words;
             gcnt = sc.get<uint32_t>((size_t)T * (size_t)words, &rc); if (rc) return rc;
         }
+        // the group-ordered pass (counters in shared memory, per-group sums in a global scratch)
+        const bool grouped = !gcnt;
+        unsigned long long *d_gsum = nullptr;
+        if (grouped) { d_gsum = sc.get<unsigned long long>((size_t)T * 2 * (size_t)n_groups, &rc); if (rc) return rc; }
         const int smem_bytes = gcnt ? 0 : (int)words * 4;
         AIWCRF_CUDA(cudaFuncSetAttribute(bootstrap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          std::max(smem_bytes, 1)));
@@ -2070,6 +2287,9 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         ba.inbag = d_inbag; ba.inbag_words = inbag_words;
         ba.G_ptr = nullptr;
         ba.store_group = use_tree ? 1 : 0;
+        ba.y_g = grouped ? d_y_g : nullptr;
+        ba.grp_of = grouped ? d_grp_of : nullptr;
+        ba.gsum = d_gsum;
         prof_begin(s, kProfBoot);
         bootstrap_kernel<<<(unsigned)T, kBootThreads, smem_bytes, s>>>(ba);
         AIWCRF_LAUNCH_CHECK("bootstrap_kernel");
@@ -2079,6 +2299,9 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     if (use_tree) {
         // one CTA per tree at a time, as many as fit (a background fit: at most ctas_per_sm per SM)
         AIWCRF_CUDA(cudaFuncSetAttribute(tree_grow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tree_smem));
+        // shared memory over L1: the occupancy (and one wave of trees) depends on it
+        AIWCRF_CUDA(cudaFuncSetAttribute(tree_grow_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared));
         int occ = 0;
         AIWCRF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tree_grow_kernel, kTreeThreads, tree_smem));
         if (occ < 1) return fail(AIWCRF_E_LIMIT, "tree-resident growth: no CTA fits on an SM");
@@ -2231,7 +2454,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
             fa.cnt = d_cnt; fa.next = nodes_nxt; fa.small_list = small_a; fa.big_list = big_a;
             fa.packed = packed; fa.stats = d_stats;
             fa.next_tree_off = tree_off_nxt; fa.T = (int)T; fa.done = d_done; fa.tile_splits = block_sums;
-            fa.parity = depth & 1; fa.next_cap = (uint32_t)(2 * node_cap);
+            fa.parity = depth & 1; fa.next_cap = (uint32_t)(2 * node_cap); fa.vals = d_vals; fa.N = N;
             // tiles of the depth's (bounded) node count, at most four (256-thread) CTAs per SM
             const unsigned fgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((Cb + kScanTile - 1) / kScanTile, 4 * (int64_t)dev_sms));
             prof_begin(s, kProfFinalize);
@@ -2377,8 +2600,7 @@ int plan_phase_a(FitPlan &P, cudaStream_t s, bool probe)
     AIWCRF_LAUNCH_CHECK("key_init_kernel");
     int rc;
     if ((rc = radix_sort_segments(P.kA, P.vA, P.kB, P.vB, N, F, N, P.hist, s)) != AIWCRF_OK) return rc;
-    dense_rank_kernel<<<F, 1024, 0, s>>>(P.kA, P.vA, N, P.d_R, P.d_vals, P.d_card, P.d_err);
-    AIWCRF_LAUNCH_CHECK("dense_rank_kernel");
+    if ((rc = dense_ranks(P.kA, P.vA, N, F, P.hist, P.d_R, P.d_vals, P.d_card, s)) != AIWCRF_OK) return rc;
     if (probe) {
         std::vector<uint32_t> h_card((size_t)F);
         uint32_t h_err = 0;
@@ -2431,6 +2653,9 @@ int plan_bootstrap(FitPlan &P, cudaStream_t s)
     ba.small_list = P.small_l; ba.big_list = P.big_l; ba.counters = P.d_cnt->n_list[0]; ba.err = P.d_err;
     ba.inbag = P.d_inbag; ba.inbag_words = P.inbag_words;
     ba.store_group = 0;
+    ba.y_g = nullptr;
+    ba.grp_of = nullptr;
+    ba.gsum = nullptr;
     bootstrap_kernel<<<(unsigned)P.T, kBootThreads, P.boot_smem, s>>>(ba);
     AIWCRF_LAUNCH_CHECK("bootstrap_kernel");
     iota_kernel<<<(unsigned)((P.T + 256) / 256), 256, 0, s>>>(P.toff_a, (int)P.T);
@@ -2471,7 +2696,7 @@ int plan_level(FitPlan &P, cudaStream_t s, cudaStream_t side, cudaEvent_t ev_for
     fa.cnt = P.d_cnt; fa.next = nodes_out; fa.small_list = P.small_l; fa.big_list = P.big_l;
     fa.packed = P.packed; fa.stats = P.d_stats;
     fa.next_tree_off = toff_out; fa.T = (int)P.T; fa.done = P.d_done; fa.tile_splits = P.block_sums;
-    fa.parity = parity; fa.next_cap = (uint32_t)P.C_max;
+    fa.parity = parity; fa.next_cap = (uint32_t)P.C_max; fa.vals = P.d_vals; fa.N = P.N;
     finalize_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((P.C_max + kScanTile - 1) / kScanTile, 4 * (int64_t)P.sms)), kFinThreads, 0, s>>>(fa);
     AIWCRF_LAUNCH_CHECK("finalize_kernel");
     return AIWCRF_OK;

@@ -248,8 +248,14 @@ static __device__ __noinline__ bool cand_better_exact_s(uint32_t a_nL, int64_t a
     return a_r < b_r;
 }
 
+// Two candidates with the same left sums, or with mirrored ones (nL' = n - nL, SL' = S - SL:
+// delta' = -delta, the same n_L n_R), have equal gains: their order is the tie-break alone.
+// Many tried features induce the same partition of a node's entries, so this case is settled
+// inline and the exact 256-bit comparison (an out-of-line call) runs only for distinct gains.
 __device__ __forceinline__ bool cand_better_exact(const Cand &a, const Cand &b, uint32_t n, int64_t S)
 {
+    if ((a.nL == b.nL && a.SL == b.SL) || (a.nL == n - b.nL && a.SL == S - b.SL))
+        return a.f != b.f ? a.f < b.f : a.r < b.r;
     return cand_better_exact_s(a.nL, a.SL, a.f, a.r, b.nL, b.SL, b.f, b.r, n, S);
 }
 
@@ -298,9 +304,16 @@ __device__ __forceinline__ Cand warp_best(const Cand &mine, uint32_t n, int64_t 
     return best;
 }
 
-// Leaf value round(S/n), half up: floor((2S + n) / (2n)).
+// Leaf value round(S/n), half up: floor((2S + n) / (2n)). 64-bit when 2S + n cannot overflow
+// (|S| <= 2^61, always so for the targets' 2^40 bound and up to 2^21 rows of weight), else 128-bit.
 __device__ __forceinline__ int64_t round_mean(int64_t S, uint32_t n)
 {
+    if (S <= ((int64_t)1 << 61) && S >= -((int64_t)1 << 61)) {
+        const int64_t a = 2 * S + (int64_t)n, b = 2 * (int64_t)n;
+        int64_t q = a / b;
+        if (q * b != a && a < 0) q -= 1;
+        return q;
+    }
     const i128_t a = (i128_t)2 * S + n, b = (i128_t)2 * n;
     i128_t q = a / b;
     if (a % b != 0 && a < 0) q -= 1;
@@ -327,7 +340,7 @@ struct SplitRes {         // outcome of one active node
     uint32_t nL;
     uint32_t lenL;
     uint32_t pad;
-    int64_t v;            // S_L for a split, the leaf value for a leaf
+    int64_t v;            // S_L for a split (a leaf's value is computed where the node is encoded)
 };
 
 struct PackedRec {        // a finished node waiting for the final packing
