@@ -163,9 +163,15 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------ ours
-def source_sha():
+# the sources of each kernel class: its ncu counters are reported only while these are unchanged
+CLASS_SOURCES = {"tree": ("fit.cu", "internal.cuh"), "level_big": ("fit.cu", "internal.cuh"),
+                 "level_small": ("fit.cu", "internal.cuh"), "walk": ("predict.cu", "internal.cuh"),
+                 "predict": ("predict.cu", "sort.cu", "internal.cuh")}
+
+
+def source_sha(cls: str | None = None):
     h = hashlib.sha256()
-    for f in ("fit.cu", "predict.cu", "sort.cu", "internal.cuh"):
+    for f in CLASS_SOURCES.get(cls, ("fit.cu", "predict.cu", "sort.cu", "internal.cuh")):
         h.update(open(os.path.join(ROOT, "paper_1811_00156_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -327,7 +333,6 @@ def run_ours(args):
         "tree": K * (stats["entries_evaluated"] * per_eval + stats["entries_partitioned"] * per_part),
         "predict": K * n_queries * (F * 4 + 8),
     }
-    sha = source_sha()
     kernels = {}
     for name, (n_launch, ms) in prof.items():
         if n_launch == 0:
@@ -347,7 +352,7 @@ def run_ours(args):
         achieved = alg[name] / (ms / 1e3) / 1e9
         return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind} peaks",
-                "traffic": ncu_traffic(name, sha), "alg_bytes_per_launch": alg[name] / n_l,
+                "traffic": ncu_traffic(name, source_sha(name)), "alg_bytes_per_launch": alg[name] / n_l,
                 "ms_per_launch": ms / n_l, "timing": timing}
 
     def issue_roofline(name):
@@ -356,11 +361,11 @@ def run_ours(args):
         source) / event-timed duration; peak = 152 SMs x 4 schedulers x 1 warp instruction per
         cycle at the median SM clock sampled in the timed region."""
         n_l, ms = prof_dom[name]
-        inst = ncu_counter(name, "inst", sha)
+        inst = ncu_counter(name, "inst", source_sha(name))
         pk = 152 * 4 * sm_mhz * 1e6 / 1e12                  # T warp-instructions/s
         r = {"kernel": name, "bound": "alu", "unit": "T warp-inst/s", "peak": pk,
              "peak_source": f"152 SMs x 4 issue slots x {sm_mhz:.0f} MHz (median sampled SM clock)",
-             "ms_per_launch": ms / n_l, "timing": timing, "traffic": ncu_traffic(name, sha),
+             "ms_per_launch": ms / n_l, "timing": timing, "traffic": ncu_traffic(name, source_sha(name)),
              "alg_bytes_per_launch": alg[name] / n_l, "inst_per_launch": inst,
              "achieved": None, "frac": None}
         if inst:
@@ -374,8 +379,8 @@ def run_ours(args):
     if dom == "predict" and prof_dom.get("walk", (0, 0.0))[0]:
         # the walk's real bound: shared-memory wavefronts (one per SM per cycle) and issue
         n_w, ms_w = prof_dom["walk"]
-        wf = ncu_counter("walk", "smem_wavefronts", sha)
-        wi = ncu_counter("walk", "inst", sha)
+        wf = ncu_counter("walk", "smem_wavefronts", source_sha("walk"))
+        wi = ncu_counter("walk", "inst", source_sha("walk"))
         smem_peak = 152 * sm_mhz * 1e6 / 1e9                  # G wavefronts/s
         roofline["walk"] = {"ms_per_launch": ms_w / n_w, "smem_wavefronts_per_launch": wf,
                             "smem_peak_gwf_s": smem_peak, "inst_per_launch": wi,
@@ -886,14 +891,13 @@ def write_counters(csv_path: str, command: str, out_path: str | None = None, sca
         elif name in ("level_small_kernel", "level_big_kernel", "tree_grow_kernel"):
             cls = {"tree_grow_kernel": "tree"}.get(name, name.replace("_kernel", ""))
             per.setdefault(cls, []).append(cnt)
-    sha = source_sha()
     out = {}
     for cls, v in per.items():
         if scale is not None and cls not in scale:
             continue
         keys = sorted({k for c in v for k in c})
         out[cls] = {k: sum(c.get(k, 0.0) for c in v) / len(v) for k in keys}
-        out[cls].update({"launches": len(v), "source_sha": sha, "command": command})
+        out[cls].update({"launches": len(v), "source_sha": source_sha(cls), "command": command})
         if scale is not None:
             # a smaller case scaled to a full launch by the units it processes: instructions and
             # shared wavefronts grow in proportion; DRAM bytes (cache reuse) do not and are dropped
@@ -902,7 +906,15 @@ def write_counters(csv_path: str, command: str, out_path: str | None = None, sca
             out[cls]["scaled_by"] = scale[cls]
     path = out_path or os.path.join(ROOT, "profiles", "counters.json")
     old = json.load(open(path)) if os.path.exists(path) else {}
-    old.update(out)
+    for cls, e in out.items():
+        prev = old.get(cls, {})
+        if prev.get("source_sha") != e["source_sha"]:
+            prev = {}                                   # counters of changed kernels are dropped
+        cmds = prev.get("commands", [prev["command"]] if "command" in prev else [])
+        merged = {**prev, **e}
+        merged.pop("command", None)
+        merged["commands"] = cmds + [command] if command not in cmds else cmds
+        old[cls] = merged
     with open(path, "w") as fh:
         json.dump(old, fh, indent=1, sort_keys=True)
     return out

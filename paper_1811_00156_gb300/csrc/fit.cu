@@ -341,28 +341,39 @@ __global__ void __launch_bounds__(kBootThreads) bootstrap_kernel(BootArgs a)
         gsum = a.gsum + (size_t)t * 2 * (size_t)G;
         for (uint32_t g = tid; g < 2 * G; g += kBootThreads) gsum[g] = 0ull;
         __syncthreads();
-        for (int64_t k0 = 0; k0 < a.N; k0 += kBootThreads) {
-            const int64_t k = k0 + tid;
-            const bool valid = k < a.N;
-            uint32_t w = 0u, g = 0xFFFFFFFFu;
-            long long wy = 0ll;
-            if (valid) {
-                const uint32_t row = a.grp_rows[k];
-                g = a.grp_of[k];
-                w = (cnt[row >> 2] >> (8u * (row & 3u))) & 255u;
-                if (w) wy = (long long)w * a.y_g[k];
+        // kBootIlp positions per thread per round: their loads are issued before any is reduced
+        constexpr int kBootIlp = 4;
+        for (int64_t k0 = 0; k0 < a.N; k0 += (int64_t)kBootThreads * kBootIlp) {
+            uint32_t rw[kBootIlp], rg[kBootIlp];
+            long long ry[kBootIlp];
+#pragma unroll
+            for (int u = 0; u < kBootIlp; ++u) {
+                const int64_t k = k0 + (int64_t)u * kBootThreads + tid;
+                rg[u] = 0xFFFFFFFFu; rw[u] = 0u; ry[u] = 0ll;
+                if (k < a.N) {
+                    const uint32_t row = a.grp_rows[k];
+                    rg[u] = a.grp_of[k];
+                    ry[u] = a.y_g[k];
+                    rw[u] = (cnt[row >> 2] >> (8u * (row & 3u))) & 255u;
+                }
             }
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t tw = __shfl_up_sync(kFull, w, o);
-                const long long ty = __shfl_up_sync(kFull, wy, o);
-                const uint32_t tg = __shfl_up_sync(kFull, g, o);
-                if (lane >= o && tg == g) { w += tw; wy += ty; }
-            }
-            const uint32_t ng = __shfl_down_sync(kFull, g, 1);
-            if (valid && w && (lane == 31 || ng != g)) {
-                atomicAdd(&gsum[2 * (size_t)g], (unsigned long long)w);
-                atomicAdd(&gsum[2 * (size_t)g + 1], (unsigned long long)wy);
+            for (int u = 0; u < kBootIlp; ++u) {
+                uint32_t w = rw[u];
+                const uint32_t g = rg[u];
+                long long wy = w ? (long long)w * ry[u] : 0ll;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t tw = __shfl_up_sync(kFull, w, o);
+                    const long long ty = __shfl_up_sync(kFull, wy, o);
+                    const uint32_t tg = __shfl_up_sync(kFull, g, o);
+                    if (lane >= o && tg == g) { w += tw; wy += ty; }
+                }
+                const uint32_t ng = __shfl_down_sync(kFull, g, 1);
+                if (g != 0xFFFFFFFFu && w && (lane == 31 || ng != g)) {
+                    atomicAdd(&gsum[2 * (size_t)g], (unsigned long long)w);
+                    atomicAdd(&gsum[2 * (size_t)g + 1], (unsigned long long)wy);
+                }
             }
         }
         __syncthreads();

@@ -54,7 +54,8 @@ def test_classes_and_sums(tmp_path):
     write_csv(path, launches)
     out = tmp_path / "counters.json"
     d = bench.write_counters(str(path), "ncu ...", str(out))
-    assert json.load(open(out)) == d
+    saved = json.load(open(out))
+    assert set(saved) == set(d) and all(saved[c]["commands"] == ["ncu ..."] for c in d)
     assert d["level_big"]["launches"] == 2 and d["level_big"]["dram_bytes"] == (120 + 360) / 2
     assert d["level_small"]["launches"] == 2 and d["level_small"]["dram_bytes"] == (60 + 180) / 2
     assert d["tree"]["dram_bytes"] == 100 and d["tree"]["inst"] == 9_000_000
@@ -63,17 +64,27 @@ def test_classes_and_sums(tmp_path):
     assert d["predict"]["launches"] == 1
     assert d["predict"]["dram_bytes"] == 164_000 + 44 + 9 + 48
     assert set(d) == {"level_big", "level_small", "tree", "walk", "predict"}
-    assert all(v["source_sha"] == bench.source_sha() for v in d.values())
+    assert all(v["source_sha"] == bench.source_sha(c) for c, v in d.items())
 
 
 def test_units_scale_and_merge(tmp_path):
     path = tmp_path / "t.csv"
     write_csv(path, [("void aiwcrf::level_small_kernel<unsigned short>(aiwcrf::LevelArgs)", 1.5, 0.5, "Mbyte")])
     o = tmp_path / "o.json"
-    o.write_text(json.dumps({"walk": {"inst": 3, "source_sha": "x"}}))
-    d = bench.write_counters(str(path), "", str(o))
+    o.write_text(json.dumps({"walk": {"inst": 3, "source_sha": "x"},
+                             "level_small": {"inst": 7, "source_sha": bench.source_sha("level_small"), "command": "a"}}))
+    d = bench.write_counters(str(path), "b", str(o))
     assert d["level_small"]["dram_bytes"] == 2_000_000
-    assert set(json.load(open(o))) == {"walk", "level_small"}          # earlier captures are kept
+    saved = json.load(open(o))
+    assert set(saved) == {"walk", "level_small"}                        # earlier captures are kept
+    assert saved["level_small"]["inst"] == 7 and saved["level_small"]["commands"] == ["a", "b"]   # merged
+
+
+def test_scaled_capture_keeps_instruction_counts_only(tmp_path):
+    path = tmp_path / "t.csv"
+    write_csv(path, [("aiwcrf::tree_grow_kernel(aiwcrf::TreeArgs)", 70, 30, "byte", 1000, 40)])
+    d = bench.write_counters(str(path), "c", str(tmp_path / "o.json"), scale={"tree": 8.0})
+    assert d["tree"]["inst"] == 8000 and d["tree"]["smem_wavefronts"] == 320 and "dram_bytes" not in d["tree"]
 
 
 def test_counters_reported_only_for_the_captured_sources(tmp_path):
