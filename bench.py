@@ -423,13 +423,14 @@ def run_ours(args):
         f = A.aiwcrf_fit(params, X, y)
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-        out["surrogate"] = surrogate_report(A, f, Xq, bf16_peak_tflops=peaks.get("bf16_tflops"))
+        out["surrogate"], sg = surrogate_report(A, f, Xq, bf16_peak_tflops=peaks.get("bf16_tflops"))
         del f
         # the earlier reports' forests, plans and networks are freed now, not by the garbage
         # collector in the middle of the load test
         gc.collect()
         torch.cuda.synchronize()
-        out["serving"] = serving_report(A, wl)
+        out["serving"] = serving_report(A, wl, surrogate=sg)
+        del sg
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
@@ -631,15 +632,19 @@ def loko_report(A, dev, steps: int = 2):
                        "mape_max": float(np.max(smape))}}
 
 
-def surrogate_report(A, forest, Xq, n_train=4_000_000, epochs=20, bf16_peak_tflops=None):
-    """The learned surrogate distilled from the benchmark forest: 4,000,000 samples of the query
-    distribution labelled by the forest, Adam (lr 1e-3, batch 4096, 20 epochs); then both models
-    predict the benchmark's 1,000,000 queries. Error against the forest for the BF16 tensor-core
-    network and, on a 20,000-query sample, for the same weights evaluated in FP64 by the oracle."""
+def surrogate_report(A, forest, Xq, n_train=4_000_000, n_near=1_000_000, epochs=20, bf16_peak_tflops=None):
+    """The learned surrogate distilled from the benchmark forest: 4,000,000 samples labelled by
+    the forest -- 3,000,000 of the query distribution and 1,000,000 neighbours of the training
+    kernels (synth.neighbour_queries, the scheduler's own use: kernels like those it was trained
+    on) -- Adam (lr 1e-3, batch 4096, 20 epochs); then both models predict the benchmark's
+    1,000,000 queries and 200,000 fresh neighbour queries. Error against the forest on both
+    populations for the BF16 tensor-core network and, on a 20,000-query sample, for the same
+    weights evaluated in FP64 by the oracle. Returns (report, surrogate)."""
     import torch
     from oracle import mlp as M
     dev = Xq.device
-    Xs = torch.from_numpy(synth.queries(n_train, seed=4242)).to(dev)
+    Xs = torch.from_numpy(np.concatenate([synth.queries(n_train - n_near, seed=4242),
+                                          synth.neighbour_queries(n_near, seed=4343)], axis=1)).to(dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     sg = A.aiwcrf_surrogate_fit(A.surrogate_params(epochs=epochs, batch=4096), forest, Xs)
@@ -665,34 +670,49 @@ def surrogate_report(A, forest, Xq, n_train=4_000_000, epochs=20, bf16_peak_tflo
     Xh = Xq[:, idx].cpu().numpy()
     r64, _ = M.forward(P.astype(np.float64), M.encode(Xh, mu, sd, lg, 15, 4), rounding=False)
     flops = 2.0 * Q * (64 * 256 + 256 * 256 + 256)
-    rep = {"train_samples": n_train, "epochs": epochs, "train_s": train_s, "stats": sg.stats(),
+    Xn = torch.from_numpy(synth.neighbour_queries(200_000, seed=4444)).to(dev)
+    refn = torch.empty(Xn.shape[1], dtype=torch.int64, device=dev)
+    outn = torch.empty(Xn.shape[1], dtype=torch.float32, device=dev)
+    A.aiwcrf_predict(forest, Xn, refn)
+    sg.predict(Xn, outn)
+    errn = np.abs(outn.cpu().numpy().astype(np.float64) - refn.cpu().numpy() / 2.0 ** 32)
+    del Xn, refn, outn
+    rep = {"train_samples": n_train, "train_samples_neighbours": n_near, "epochs": epochs, "train_s": train_s,
+           "stats": sg.stats(),
            "queries_per_s": Q / (s_ms / 1e3), "forest_queries_per_s": Q / (f_ms / 1e3),
            "speedup_vs_forest": f_ms / s_ms, "mae_vs_forest_log10": float(err.mean()),
            "p99_abs_err_log10": float(np.percentile(err, 99)),
            "mae_vs_forest_fp64_oracle_log10": float(np.abs(r64 - f[idx]).mean()),
            "mae_of_mean_predictor_log10": float(np.abs(f - f.mean()).mean()),
+           "neighbours": {"queries": int(errn.size), "mae_vs_forest_log10": float(errn.mean()),
+                          "p99_abs_err_log10": float(np.percentile(errn, 99))},
            "tensor_tflops": flops / (s_ms / 1e3) / 1e12}
     if bf16_peak_tflops:
         rep["tensor_frac_of_measured_bf16"] = rep["tensor_tflops"] / bf16_peak_tflops
     rep["gated_selection"] = gated_selection_report(A, forest, sg)
-    return rep
+    return rep, sg
 
 
-def gated_selection_report(A, forest, sg, K=65536, var_trees=32, zs=(0.1, 0.25, 0.5, 1.0, 2.0, None)):
+GATE_SETTINGS = ([("var", z, True) for z in (0.1, 0.25, 0.5, 1.0, 2.0)] +
+                 [("tau", t, ood) for ood in (True, False) for t in (0.01, 0.02, 0.05, 0.1, 0.2)] +
+                 [("alone", None, False)])
+
+
+def gated_selection_report(A, forest, sg, K=65536, var_trees=32, settings=GATE_SETTINGS):
     """The gated selection on two kernel populations: fresh draws of the feature distributions
     (far from the 37 training kernels) and neighbours of the training kernels."""
     far = np.ascontiguousarray(synth.queries(K, seed=555)[:synth.N_AIWC])
     near = synth.kernel_neighbours(K, 2, jitter=0.05, seed=556)
-    return {"random_kernels": gated_selection_case(A, forest, sg, far, var_trees, zs),
-            "training_neighbours": gated_selection_case(A, forest, sg, near, var_trees, zs)}
+    return {"random_kernels": gated_selection_case(A, forest, sg, far, var_trees, settings),
+            "training_neighbours": gated_selection_case(A, forest, sg, near, var_trees, settings)}
 
 
-def gated_selection_case(A, forest, sg, kf_h, var_trees, zs):
+def gated_selection_case(A, forest, sg, kf_h, var_trees, settings):
     """Device selection for K kernels x 15 devices: the forest alone, and the surrogate whose
-    choice falls back to the forest on out-of-range features or when its margin between the two
-    best devices is within z standard deviations of their ensemble spread over the forest's first
-    32 trees (None: the surrogate alone). Agreement and regret are judged by the forest's own
-    predictions."""
+    choice falls back to the forest (ood: on out-of-range features) when its margin between the
+    two best devices is within z standard deviations of their ensemble spread over the forest's
+    first 32 trees ("var"), or below tau log10 seconds ("tau"), or never ("alone"). Agreement
+    and regret are judged by the forest's own predictions."""
     import torch
     dev = torch.device("cuda")
     K = kf_h.shape[1]
@@ -719,12 +739,14 @@ def gated_selection_case(A, forest, sg, kf_h, var_trees, zs):
     fbest = fb_best.cpu().numpy()
     rep = {"kernels": K, "devices": SEL_DEVICES, "var_trees": var_trees,
            "forest": {"ms": 1e3 * t_forest, "queries_per_s": K * SEL_DEVICES / t_forest}, "gated": []}
-    for z in zs:
-        g = A.gate_params(var_trees, z, ood=True) if z is not None else A.gate_params(1, 0.0, ood=False)
+    for kind, x, ood in settings:
+        g = {"var": lambda: A.gate_params(var_trees, x, ood=ood), "tau": lambda: A.gate_params(1, 0.0, ood=ood, tau=x),
+             "alone": lambda: A.gate_params(1, 0.0, ood=False)}[kind]()
         t, st = timed(lambda: A.aiwcrf_select_device_gated(forest, sg, g, kf, 2, devices, best, None, flags))
         b = best.cpu().numpy()
         regret = fp[np.arange(K), b] - fp[np.arange(K), fbest]
-        rep["gated"].append({"z": z, "ms": 1e3 * t, "queries_per_s": K * SEL_DEVICES / t,
+        rep["gated"].append({"gate": kind, "z" if kind == "var" else "tau": x, "ood": ood, "ms": 1e3 * t,
+                             "queries_per_s": K * SEL_DEVICES / t,
                              "speedup_vs_forest": t_forest / t, "fallback_frac": st["fallback"] / K,
                              "fallback_ood": st["fallback_ood"], "fallback_var": st["fallback_var"],
                              "agreement_with_forest": float((b == fbest).mean()),
@@ -732,12 +754,16 @@ def gated_selection_case(A, forest, sg, kf_h, var_trees, zs):
     return rep
 
 
-def serving_report(A, wl, rates=(5000.0, 20000.0, 50000.0), n_requests=20000, refit_every=10000):
+def serving_report(A, wl, rates=(5000.0, 20000.0, 50000.0), n_requests=20000, refit_every=10000, surrogate=None,
+                   gated_rates=(20000.0, 50000.0), gate_z=0.5, gate_var_trees=32):
     """The device-selection server under open-loop Poisson load: a 500-tree forest of the
     111,000-row workload resident, requests of 1-64 kernels (uniform) x 15 devices x one size
     class (uniform), a refit every 10,000 requests on 2,220 appended rows. Latency runs from the
     scheduled arrival to the completed batch being seen on the host. A sample of the answers is
-    checked against aiwcrf_select_device on the creation forest."""
+    checked against aiwcrf_select_device on the creation forest. With a surrogate, the same load
+    again with every request gated (the surrogate resident in the server, the forest answering
+    where the gate falls back; no refits): throughput, latency, fallback share and agreement of
+    the gated devices with the forest's own choice."""
     rng = np.random.default_rng(2024)
     pool = np.ascontiguousarray(synth.queries(4096, seed=77)[:synth.N_AIWC])
     devices = np.arange(SEL_DEVICES, dtype=np.int32)
@@ -835,6 +861,32 @@ def serving_report(A, wl, rates=(5000.0, 20000.0, 50000.0), n_requests=20000, re
             rep["generation_0_mismatches"] = mism
             out["runs"].append(rep)
         out["counters"] = srv.stats()
+    if surrogate is not None:
+        out["gated"] = {"z": gate_z, "var_trees": gate_var_trees, "runs": []}
+        sp0 = A.server_params(n_streams=4, max_request_kernels=64, batch_kernels=1024, arena_bytes=64 << 20)
+        with A.Server(sp0, fp, wl.X, wl.y, devices) as srv:
+            srv.set_surrogate(surrogate, A.gate_params(gate_var_trees, gate_z, ood=True))
+            for rate in gated_rates:
+                k = rng.integers(1, 65, n_requests).astype(np.int32)
+                first = (rng.integers(0, pool.shape[1] - 64, n_requests)).astype(np.int64)
+                size = rng.integers(0, synth.N_SIZES, n_requests).astype(np.int32)
+                c0 = srv.stats()
+                rep, best, gen, lat = srv.run_load(pool, first, k, size, rate_per_s=rate, seed=int(rate) + 1,
+                                                   timeout_ms=600000, gated=np.ones(n_requests, np.uint8))
+                c1 = srv.stats()
+                gk = c1["gated_kernels"] - c0["gated_kernels"]
+                rep["fallback_frac"] = (c1["gated_fallback"] - c0["gated_fallback"]) / max(gk, 1)
+                agree = tot = 0
+                off = 0
+                for i in range(n_requests):
+                    want = ref[int(size[i])][first[i]:first[i] + k[i]]
+                    agree += int((best[off:off + k[i]] == want).sum())
+                    tot += int(k[i])
+                    off += k[i]
+                rep["agreement_with_forest"] = agree / tot
+                rep["requests_over_1ms"] = int((lat > 1_000_000).sum())
+                out["gated"]["runs"].append(rep)
+            out["gated"]["counters"] = srv.stats()
     return out
 
 

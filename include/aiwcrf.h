@@ -91,7 +91,8 @@ typedef struct {
     int32_t n_features;
     int32_t mtry;
     int32_t rank_bytes;          /* bytes per stored rank: 1 if every column has <= 256 values */
-    int32_t grower;              /* 1: level-synchronous kernels, 2: tree-resident kernel */
+    int32_t grower;              /* 1: level-synchronous kernels, 2: tree-resident kernel,
+                                    3: level-synchronous with presorted lists */
 } aiwcrf_fit_stats;
 
 /* Fit a forest (Sec. III-B). X: F x N column-major float32 (no NaN); y: N int64 Q32.32.
@@ -316,6 +317,11 @@ typedef struct {
     int64_t forest_bytes;         /* device bytes of the current forest */
     int64_t refit_us_total;       /* wall time of all refits (rows staged, fit, swap) */
     int64_t refit_us_max;
+    int64_t gated_kernels;        /* kernels of completed gated requests */
+    int64_t gated_fallback;       /* ... answered by the forest */
+    int64_t gated_fallback_ood;   /* ... with an out-of-range feature */
+    int64_t gated_fallback_var;   /* ... whose surrogate margin was within z deviations */
+    int64_t surrogate_bytes;      /* device bytes of the resident surrogate (0: none) */
 } aiwcrf_server_counters;
 
 typedef struct {
@@ -399,6 +405,8 @@ typedef struct {
     int64_t enqueue_cpu_ns;
     int32_t enqueue_voluntary_switches, enqueue_involuntary_switches;
     int64_t poll_gap_max_ns;
+    int32_t gated_kernels;        /* kernels of gated requests in the batch */
+    int32_t fallback_kernels;     /* ... of which the forest answered */
 } aiwcrf_batch_trace;
 
 typedef struct {
@@ -426,8 +434,10 @@ int aiwcrf_server_destroy(aiwcrf_server *server);
  *    var_trees trees' leaf values v_t (Q32.32, exact), the test is
  *        ((s_r - s_b)^2 * var_trees^2) * 2^64  <=  (z * z) * (V_b + V_r)
  *    evaluated in IEEE double with round-to-nearest in exactly this order, V_b + V_r converted
- *    as double(high 64 bits) * 2^64 + double(low 64 bits). With one device there is no
- *    runner-up and only the range test applies.
+ *    as double(high 64 bits) * 2^64 + double(low 64 bits); or
+ *  - the surrogate's margin is below a fixed threshold: double(s_r) - double(s_b) < tau (log10
+ *    seconds; tau = 0 never holds).
+ * With one device there is no runner-up and only the range test applies.
  * A kernel that falls back gets exactly aiwcrf_select_device's device and the forest's
  * predictions (converted to float log10 s); the others get b and the surrogate's predictions.
  * kfeat ((F-2) x K), out_best (K), out_pred (K x D float, or NULL) and out_fallback (K bytes,
@@ -437,14 +447,14 @@ typedef struct {
     int32_t var_trees;      /* 1..num_trees (32) */
     float z;                /* margin in ensemble standard deviations, 0 <= z < 2^20 (1) */
     int32_t ood;            /* 1: out-of-range features fall back (1) */
-    int32_t reserved;       /* must be 0 */
+    float tau;              /* margin threshold in log10 seconds, 0 <= tau < 2^20 (0: none) */
 } aiwcrf_gate_params;
 
 typedef struct {
     int64_t kernels;
     int64_t fallback;       /* kernels answered by the forest */
     int64_t fallback_ood;   /* ... with an out-of-range feature */
-    int64_t fallback_var;   /* ... whose surrogate margin was within z deviations */
+    int64_t fallback_var;   /* ... whose surrogate margin was within z deviations or below tau */
 } aiwcrf_gate_stats;
 
 int aiwcrf_select_device_gated(const aiwcrf_forest *forest, const aiwcrf_surrogate *surrogate,
@@ -452,6 +462,38 @@ int aiwcrf_select_device_gated(const aiwcrf_forest *forest, const aiwcrf_surroga
                                int32_t size_class, const int32_t *device_ids, int32_t n_devices,
                                int32_t *out_best, float *out_pred, uint8_t *out_fallback,
                                aiwcrf_gate_stats *stats, void *cuda_stream);
+
+/* Gated requests in the device-selection server: the surrogate resident beside the forest.
+ * aiwcrf_server_set_surrogate copies the surrogate (the caller may free its own afterwards) and
+ * keeps gate (checked as for aiwcrf_select_device_gated against the server's forest); NULL
+ * removes it, and gated requests still queued then fail with AIWCRF_E_INVALID_ARG. The surrogate
+ * must have the server's n_features and live on the server's device. Batches already formed keep
+ * the surrogate they were formed with; a refit replaces the forest but not the surrogate (the gate
+ * and the fallback use the new forest).
+ * A gated request (aiwcrf_server_submit_gated: as aiwcrf_server_submit; refused with
+ * AIWCRF_E_INVALID_ARG while no surrogate is held, and with AIWCRF_E_LIMIT if its batch bytes can
+ * never fit the arena) is answered as aiwcrf_select_device_gated answers the same kernels on the
+ * forest of its batch's generation: the surrogate's device, or the forest's where the gate
+ * falls back. It shares batches with exact requests: a batch puts its gated requests' kernels
+ * first, runs the surrogate, the prefix variances and the gate on those, then one selection kernel
+ * for the exact kernels and the gated kernels that fell back, with no host synchronisation in
+ * between. aiwcrf_server_wait_gated writes best (host, n_kernels device ids), pred (host
+ * n_kernels x n_devices row-major float log10 seconds, or NULL) and fallback (host n_kernels bytes,
+ * 1 = the forest answered, or NULL); aiwcrf_server_wait refuses a gated ticket and
+ * aiwcrf_server_wait_gated an exact one, without retiring it.
+ * aiwcrf_server_run_load_gated is aiwcrf_server_run_load with request i gated where gated[i] != 0
+ * (gated may be NULL: none). */
+int aiwcrf_server_set_surrogate(aiwcrf_server *server, const aiwcrf_surrogate *surrogate,
+                                const aiwcrf_gate_params *gate);
+int aiwcrf_server_submit_gated(aiwcrf_server *server, const float *kfeat, int32_t n_kernels,
+                               int32_t size_class, int64_t *ticket);
+int aiwcrf_server_wait_gated(aiwcrf_server *server, int64_t ticket, int32_t timeout_ms, int32_t *best,
+                             float *pred, uint8_t *fallback, int64_t *generation);
+int aiwcrf_server_run_load_gated(aiwcrf_server *server, const float *pool, int64_t pool_kernels,
+                                 const int64_t *first, const int32_t *n_kernels,
+                                 const int32_t *size_class, const uint8_t *gated, int64_t n_requests,
+                                 double rate_per_s, uint64_t seed, int32_t timeout_ms, int32_t *best,
+                                 int64_t *generation, int64_t *latency_ns, aiwcrf_load_report *report);
 
 /* Fit plan: the whole fit of aiwcrf_fit / aiwcrf_fit_subsets captured once as a CUDA graph and
  * replayed (the batched leave-one-kernel-out fits of Alg. 1 run as one graph launch). The graph
@@ -507,9 +549,15 @@ int64_t aiwcrf_debug_bounds(void);
 
 /* Which kernels grow the trees of the following fits in this process (the paper has no
  * counterpart: both give the same forest, node for node, for the model of Sec. III-B).
- *  AIWCRF_GROWER_AUTO (default): tree-resident when it fits, else level-synchronous.
+ *  AIWCRF_GROWER_AUTO (default): tree-resident when it fits, else level-synchronous with
+ *    presorted lists when a column has more than 4,096 distinct values, else level-synchronous.
  *  AIWCRF_GROWER_LEVEL: level-synchronous, every depth of every tree as three launches
- *    (big-node CTAs, small-node warps, a finalize pass).
+ *    (big-node CTAs, small-node warps, a finalize pass); a big node's search builds shared-memory
+ *    histograms over every rank of its tried features.
+ *  AIWCRF_GROWER_LISTS: level-synchronous, a big node's search scans presorted lists instead:
+ *    every tree keeps its entries in rank order per feature (4 bytes per entry and feature, twice,
+ *    and 12 bytes per tree and row) and each depth partitions them with the entries. Its cost per
+ *    node follows the node's entries, not the columns' value counts.
  *  AIWCRF_GROWER_TREE: tree-resident, one CTA grows a whole tree with its entries in shared
  *    memory; a fit whose trees do not fit (ranks wider than one byte, more than 32 features,
  *    more than 65,535 groups, or too many entries per tree for shared memory) fails with
@@ -519,6 +567,7 @@ int64_t aiwcrf_debug_bounds(void);
 #define AIWCRF_GROWER_AUTO 0
 #define AIWCRF_GROWER_LEVEL 1
 #define AIWCRF_GROWER_TREE 2
+#define AIWCRF_GROWER_LISTS 3
 int aiwcrf_set_grower(int32_t grower);
 
 /* Counters of the fit that produced the forest (zeros for a deserialized forest). The paper has

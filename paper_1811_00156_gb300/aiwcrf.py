@@ -68,7 +68,8 @@ class ServerCounters(C.Structure):
     _fields_ = [(k, C.c_int64) for k in (
         "submitted", "rejected", "completed", "failed", "batches", "batch_kernels_total", "batch_kernels_max",
         "arena_waits", "arena_bytes", "arena_peak_bytes", "refits", "refit_failures", "generation",
-        "training_rows", "appended_rows", "forest_bytes", "refit_us_total", "refit_us_max")]
+        "training_rows", "appended_rows", "forest_bytes", "refit_us_total", "refit_us_max", "gated_kernels",
+        "gated_fallback", "gated_fallback_ood", "gated_fallback_var", "surrogate_bytes")]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -86,7 +87,7 @@ class LoadReport(C.Structure):
 
 
 class GateParams(C.Structure):
-    _fields_ = [("var_trees", C.c_int32), ("z", C.c_float), ("ood", C.c_int32), ("reserved", C.c_int32)]
+    _fields_ = [("var_trees", C.c_int32), ("z", C.c_float), ("ood", C.c_int32), ("tau", C.c_float)]
 
 
 class GateStats(C.Structure):
@@ -109,7 +110,7 @@ class BatchTrace(C.Structure):
     _fields_ = [("t_formed_ns", C.c_int64), ("t_enqueued_ns", C.c_int64), ("t_done_ns", C.c_int64),
                 ("kernels", C.c_int32), ("generation", C.c_int32), ("enqueue_cpu_ns", C.c_int64),
                 ("enqueue_voluntary_switches", C.c_int32), ("enqueue_involuntary_switches", C.c_int32),
-                ("poll_gap_max_ns", C.c_int64)]
+                ("poll_gap_max_ns", C.c_int64), ("gated_kernels", C.c_int32), ("fallback_kernels", C.c_int32)]
 
 
 class RefitTrace(C.Structure):
@@ -129,6 +130,8 @@ EXPORTS = ["aiwcrf_fit", "aiwcrf_fit_subsets", "aiwcrf_predict", "aiwcrf_predict
            "aiwcrf_server_create", "aiwcrf_server_submit", "aiwcrf_server_wait", "aiwcrf_server_append",
            "aiwcrf_server_refit", "aiwcrf_server_pause", "aiwcrf_server_stats", "aiwcrf_server_run_load",
            "aiwcrf_server_trace", "aiwcrf_server_destroy", "aiwcrf_select_device_gated",
+           "aiwcrf_server_set_surrogate", "aiwcrf_server_submit_gated", "aiwcrf_server_wait_gated",
+           "aiwcrf_server_run_load_gated",
            "aiwcrf_fit_plan_create", "aiwcrf_fit_plan_run", "aiwcrf_fit_plan_tune", "aiwcrf_fit_plan_set_schedule",
            "aiwcrf_fit_plan_free", "aiwcrf_profile_classes", "aiwcrf_set_grower", "aiwcrf_debug_bounds"]
 
@@ -206,6 +209,11 @@ def load():
                                                  C.c_int32, _vp, _vp, _vp, C.POINTER(GateStats), _vp]
         L.aiwcrf_server_trace.argtypes = [_vp, _vp, C.c_int64, C.POINTER(C.c_int64), _vp, C.c_int64,
                                           C.POINTER(C.c_int64)]
+        L.aiwcrf_server_set_surrogate.argtypes = [_vp, _vp, C.POINTER(GateParams)]
+        L.aiwcrf_server_submit_gated.argtypes = [_vp, _vp, C.c_int32, C.c_int32, C.POINTER(C.c_int64)]
+        L.aiwcrf_server_wait_gated.argtypes = [_vp, C.c_int64, C.c_int32, _vp, _vp, _vp, C.POINTER(C.c_int64)]
+        L.aiwcrf_server_run_load_gated.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp, _vp, C.c_int64, C.c_double,
+                                                   C.c_uint64, C.c_int32, _vp, _vp, _vp, C.POINTER(LoadReport)]
         for name in EXPORTS:
             if name not in ("aiwcrf_last_error", "aiwcrf_profile_name", "aiwcrf_profile_num_classes",
                             "aiwcrf_launch_count", "aiwcrf_surrogate_num_params"):
@@ -458,14 +466,32 @@ class Server:
     def __exit__(self, *exc):
         self.close()
 
-    def submit(self, kfeat: np.ndarray, size_class: int) -> int:
+    def submit(self, kfeat: np.ndarray, size_class: int, gated: bool = False) -> int:
+        """Queue a request (gated: answered through the resident surrogate, see set_surrogate)."""
         kfeat = np.ascontiguousarray(kfeat, dtype=np.float32)
         t = C.c_int64()
-        _check(load().aiwcrf_server_submit(self.handle, kfeat.ctypes.data, int(kfeat.shape[1]), int(size_class),
-                                           C.byref(t)))
+        fn = load().aiwcrf_server_submit_gated if gated else load().aiwcrf_server_submit
+        _check(fn(self.handle, kfeat.ctypes.data, int(kfeat.shape[1]), int(size_class), C.byref(t)))
         self._k = getattr(self, "_k", {})
         self._k[t.value] = int(kfeat.shape[1])
         return t.value
+
+    def set_surrogate(self, surrogate, gate: "GateParams | None" = None):
+        """Keep a copy of surrogate resident for gated requests (None removes it)."""
+        _check(load().aiwcrf_server_set_surrogate(self.handle, None if surrogate is None else surrogate.handle,
+                                                  None if gate is None else C.byref(gate)))
+
+    def wait_gated(self, ticket: int, timeout_ms: int = -1):
+        """(best[K], pred[K, D] float log10 s, fallback[K] uint8, generation) of a gated request."""
+        K = self._k[ticket]
+        best = np.zeros(K, np.int32)
+        pred = np.zeros((K, self.D), np.float32)
+        fb = np.zeros(K, np.uint8)
+        g = C.c_int64()
+        _check(load().aiwcrf_server_wait_gated(self.handle, ticket, timeout_ms, best.ctypes.data, pred.ctypes.data,
+                                               fb.ctypes.data, C.byref(g)))
+        del self._k[ticket]
+        return best, pred, fb, g.value
 
     def wait(self, ticket: int, timeout_ms: int = -1):
         """(best[K], pred[K, D], generation)."""
@@ -505,8 +531,9 @@ class Server:
         return b, r
 
     def run_load(self, pool: np.ndarray, first, n_kernels, size_class, rate_per_s: float, seed: int = 1,
-                 timeout_ms: int = 120000):
-        """Open-loop Poisson load. Returns (report dict, best[sum K], generation[n], latency_ns[n])."""
+                 timeout_ms: int = 120000, gated=None):
+        """Open-loop Poisson load (gated: per-request flags, or None for none). Returns (report dict,
+        best[sum K], generation[n], latency_ns[n])."""
         pool = np.ascontiguousarray(pool, dtype=np.float32)
         first = np.ascontiguousarray(first, dtype=np.int64)
         nk = np.ascontiguousarray(n_kernels, dtype=np.int32)
@@ -516,9 +543,18 @@ class Server:
         gen = np.full(n, -1, np.int64)
         lat = np.full(n, -1, np.int64)
         rep = LoadReport()
-        _check(load().aiwcrf_server_run_load(self.handle, pool.ctypes.data, int(pool.shape[1]), first.ctypes.data,
-                                             nk.ctypes.data, sc.ctypes.data, n, float(rate_per_s), seed, timeout_ms,
-                                             best.ctypes.data, gen.ctypes.data, lat.ctypes.data, C.byref(rep)))
+        if gated is None:
+            _check(load().aiwcrf_server_run_load(self.handle, pool.ctypes.data, int(pool.shape[1]), first.ctypes.data,
+                                                 nk.ctypes.data, sc.ctypes.data, n, float(rate_per_s), seed,
+                                                 timeout_ms, best.ctypes.data, gen.ctypes.data, lat.ctypes.data,
+                                                 C.byref(rep)))
+        else:
+            g = np.ascontiguousarray(gated, dtype=np.uint8)
+            _check(load().aiwcrf_server_run_load_gated(self.handle, pool.ctypes.data, int(pool.shape[1]),
+                                                       first.ctypes.data, nk.ctypes.data, sc.ctypes.data,
+                                                       g.ctypes.data, n, float(rate_per_s), seed, timeout_ms,
+                                                       best.ctypes.data, gen.ctypes.data, lat.ctypes.data,
+                                                       C.byref(rep)))
         return rep.as_dict(), best, gen, lat
 
 
@@ -563,8 +599,8 @@ class FitPlan:
         self.close()
 
 
-def gate_params(var_trees: int = 32, z: float = 1.0, ood: bool = True) -> GateParams:
-    return GateParams(var_trees, z, 1 if ood else 0, 0)
+def gate_params(var_trees: int = 32, z: float = 1.0, ood: bool = True, tau: float = 0.0) -> GateParams:
+    return GateParams(var_trees, z, 1 if ood else 0, tau)
 
 
 def aiwcrf_select_device_gated(forest: Forest, surrogate, gate: GateParams, kfeat, size_class: int, device_ids,
@@ -616,7 +652,7 @@ def aiwcrf_launch_count() -> int:
     return int(load().aiwcrf_launch_count())
 
 
-GROWER_AUTO, GROWER_LEVEL, GROWER_TREE = 0, 1, 2
+GROWER_AUTO, GROWER_LEVEL, GROWER_TREE, GROWER_LISTS = 0, 1, 2, 3
 
 
 def aiwcrf_debug_bounds() -> int:
@@ -625,7 +661,8 @@ def aiwcrf_debug_bounds() -> int:
 
 
 def aiwcrf_set_grower(grower: int):
-    """Kernels that grow the trees of the following fits (GROWER_AUTO, GROWER_LEVEL, GROWER_TREE)."""
+    """Kernels that grow the trees of the following fits (GROWER_AUTO, GROWER_LEVEL, GROWER_TREE,
+    GROWER_LISTS)."""
     _check(load().aiwcrf_set_grower(grower))
 
 

@@ -468,6 +468,15 @@ struct LevelArgs {
     uint32_t *tile_splits;      // per tile of kScanTile nodes: nodes that split (zero on entry)
     const uint32_t *depth_ptr;  // when set, the depth is read here (a graph replays one level body)
     uint32_t node_cap;          // entries of the node table (bounds checks of debug builds)
+    // presorted lists (null: the big-node search builds histograms): per feature f, per tree t,
+    // lists_in[f * list_stride + t * row_cap + i] is the representative row of an entry, each
+    // node's segment in increasing rank of f; list_w / list_wy give the tree's entry of a
+    // representative row ([T][N])
+    const uint32_t *lists_in = nullptr;
+    uint32_t *lists_out = nullptr;
+    int64_t list_stride = 0;
+    const uint32_t *list_w = nullptr;
+    const int64_t *list_wy = nullptr;
 };
 
 __device__ __forceinline__ int level_depth(const LevelArgs &a)
@@ -695,6 +704,105 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallCtasPerSm) level_small_ke
 }
 
 
+// ------------------------------------------------------------------------------------------
+// Presorted lists: the level-synchronous search for columns with many distinct values. A
+// histogram over every rank of the tried features costs a node O(sum of their cardinalities)
+// whatever its size; instead every tree keeps, per feature, its entries in increasing rank of
+// that feature, and each depth partitions these lists stably together with the entries. A node's
+// segment of a list is then its entries sorted by that feature, and its split search is one
+// ordered scan per tried feature. The candidates (every present rank but the largest) and their
+// exact comparison are those of the histogram search, so the trees are the same node for node.
+// ------------------------------------------------------------------------------------------
+constexpr uint32_t kListMinCard = 4096;   // automatic choice: lists above this many values in a column
+
+__global__ void rep_mark_kernel(const uint32_t *__restrict__ grp_rows, const uint32_t *__restrict__ grp_off,
+                                uint32_t G, uint8_t *__restrict__ is_rep)
+{
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < G) is_rep[grp_rows[grp_off[g]]] = 1u;
+}
+
+// one CTA per feature: the groups' representative rows in the column's sorted row order
+__global__ void __launch_bounds__(1024) rep_order_kernel(const uint32_t *__restrict__ ordF, int64_t N,
+                                                         const uint8_t *__restrict__ is_rep, uint32_t G,
+                                                         uint32_t *__restrict__ ordG)
+{
+    __shared__ uint32_t warp_tmp[32];
+    const uint32_t *src = ordF + (size_t)blockIdx.x * (size_t)N;
+    uint32_t *dst = ordG + (size_t)blockIdx.x * (size_t)G;
+    uint32_t running = 0;
+    for (int64_t b0 = 0; b0 < N; b0 += 1024) {
+        const int64_t i = b0 + threadIdx.x;
+        const uint32_t row = i < N ? src[i] : 0u;
+        const bool keep = i < N && is_rep[row];
+        uint32_t tot;
+        const uint32_t incl = block_incl_scan(keep ? 1u : 0u, warp_tmp, tot);
+        if (keep && running + incl - 1u < G) dst[running + incl - 1u] = row;
+        running += tot;
+    }
+}
+
+// the w and w*y of every tree's entries, by representative row
+__global__ void list_tables_kernel(const Entry *__restrict__ rows, int64_t row_cap, const NodeRec *__restrict__ root,
+                                   int64_t N, uint32_t *__restrict__ Wt, int64_t *__restrict__ WYt)
+{
+    const int64_t t = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)root[t].len) return;
+    const Entry e = load_entry(rows + (size_t)t * (size_t)row_cap + (size_t)i);
+    const uint32_t row = AIWCRF_IDX(e.row, (uint32_t)N, kBoundRow);
+    Wt[(size_t)t * (size_t)N + row] = e.w;
+    WYt[(size_t)t * (size_t)N + row] = e.wy;
+}
+
+// CTA (tree, feature): the tree's entries in increasing rank of the feature
+__global__ void __launch_bounds__(1024) list_build_kernel(const uint32_t *__restrict__ ordG, uint32_t G,
+                                                          const uint32_t *__restrict__ Wt, int64_t N, int64_t row_cap,
+                                                          int64_t stride, uint32_t *__restrict__ lists)
+{
+    __shared__ uint32_t warp_tmp[32];
+    const int64_t t = blockIdx.x;
+    const uint32_t *src = ordG + (size_t)blockIdx.y * (size_t)G;
+    const uint32_t *W = Wt + (size_t)t * (size_t)N;
+    uint32_t *dst = lists + (size_t)blockIdx.y * (size_t)stride + (size_t)t * (size_t)row_cap;
+    uint32_t running = 0;
+    for (uint32_t b0 = 0; b0 < G; b0 += 1024) {
+        const uint32_t i = b0 + threadIdx.x;
+        const uint32_t row = i < G ? src[i] : 0u;
+        const bool keep = i < G && W[row] > 0u;
+        uint32_t tot;
+        const uint32_t incl = block_incl_scan(keep ? 1u : 0u, warp_tmp, tot);
+        if (keep && (int64_t)(running + incl - 1u) < row_cap) dst[running + incl - 1u] = row;
+        running += tot;
+    }
+}
+
+// Block inclusive scan of (w, w*y) pairs; totals in tot_w / tot_s (every thread)
+__device__ __forceinline__ void block_scan_ws(uint32_t w, long long s, uint32_t *tw, long long *ts, uint32_t &pw,
+                                              long long &ps, uint32_t &tot_w, long long &tot_s)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t xw = w;
+    long long xs = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t a = __shfl_up_sync(kFull, xw, o);
+        const long long b = __shfl_up_sync(kFull, xs, o);
+        if (lane >= o) { xw += a; xs += b; }
+    }
+    if (lane == 31) { tw[warp] = xw; ts[warp] = xs; }
+    __syncthreads();
+    uint32_t ow = 0;
+    long long os = 0;
+    for (int k = 0; k < warp; ++k) { ow += tw[k]; os += ts[k]; }
+    tot_w = 0;
+    tot_s = 0;
+    for (int k = 0; k < nw; ++k) { tot_w += tw[k]; tot_s += ts[k]; }
+    __syncthreads();
+    pw = xw + ow;
+    ps = xs + os;
+}
+
 constexpr int kBigThreads = 128;
 constexpr int kBigWarps = kBigThreads / 32;
 constexpr int kBigCtasPerSm = 6;       // resident CTAs per SM the big-node kernel is compiled for
@@ -707,6 +815,62 @@ inline int big_bin_cap(int mtry, int F, uint32_t max_card)
 {
     const int64_t need = (int64_t)std::min(mtry, F) * (int64_t)std::max<uint32_t>(max_card, 1u);
     return (int)std::min<int64_t>(4096, (need + 31) & ~(int64_t)31);
+}
+
+// A big node's split search from the presorted lists: per tried feature, a block scan of
+// (w, w*y) along the node's segment of the feature's list gives the left sums of every
+// threshold; a candidate sits at the last entry of each run of equal ranks but the last run.
+template <typename RT>
+__device__ __forceinline__ Cand list_search(const LevelArgs &a, const NodeRec &nd, const int *feats, int m)
+{
+    __shared__ uint32_t tw[kBigWarps];
+    __shared__ long long ts[kBigWarps];
+    const RT *__restrict__ Rr = static_cast<const RT *>(a.Rr);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const size_t tb = (size_t)nd.tree * (size_t)a.row_cap + nd.start;
+    const uint32_t *__restrict__ Wt = a.list_w + (size_t)nd.tree * (size_t)a.N;
+    const int64_t *__restrict__ WYt = a.list_wy + (size_t)nd.tree * (size_t)a.N;
+    Cand best = cand_none();
+    for (int k = 0; k < m; ++k) {
+        const int f = feats[k];
+        const uint32_t *__restrict__ L = a.lists_in + (size_t)f * (size_t)a.list_stride + tb;
+        uint32_t cw = 0u;                       // sums of the earlier chunks (block-uniform)
+        long long cs = 0ll;
+        for (uint32_t b0 = 0; b0 < nd.len; b0 += kBigThreads) {
+            const uint32_t i = b0 + (uint32_t)tid;
+            const bool valid = i < nd.len;
+            uint32_t w = 0u, rank = 0u;
+            long long wy = 0ll;
+            if (valid) {
+                const uint32_t row = AIWCRF_IDX(__ldg(&L[i]), (uint32_t)a.N, kBoundRow);
+                w = __ldg(&Wt[row]);
+                wy = (long long)__ldg(&WYt[row]);
+                rank = (uint32_t)__ldg(&Rr[(size_t)row * (size_t)a.F + f]);
+            }
+            uint32_t nrank = __shfl_down_sync(kFull, rank, 1);
+            if (lane == 31 && i + 1u < nd.len) {
+                const uint32_t row2 = AIWCRF_IDX(__ldg(&L[i + 1u]), (uint32_t)a.N, kBoundRow);
+                nrank = (uint32_t)__ldg(&Rr[(size_t)row2 * (size_t)a.F + f]);
+            }
+            uint32_t pw, tot_w;
+            long long ps, tot_s;
+            block_scan_ws(w, wy, tw, ts, pw, ps, tot_w, tot_s);
+            if (valid && i + 1u < nd.len && nrank != rank) {     // the last entry of a rank's run
+                const uint32_t nL = cw + pw;
+                const long long SL = cs + ps;
+                const i128_t delta = cand_delta(nd.n, nd.S, nL, SL);
+                if (delta != 0) {
+                    Cand cd;
+                    cd.h = cand_h(delta, nd.n, nL);
+                    cd.f = f; cd.r = rank; cd.nL = nL; cd.SL = SL;
+                    if (cand_better(cd, best, nd.n, nd.S)) best = cd;
+                }
+            }
+            cw += tot_w;
+            cs += tot_s;
+        }
+    }
+    return best;
 }
 
 // One CTA per node with more than 32 entries. Shared bins, bin_cap of them, hold per rank
@@ -777,7 +941,8 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
     const uint32_t total_bins = fbase[m];
     Cand best = cand_none();
 
-    for (uint32_t g0 = 0; g0 < total_bins; g0 += (uint32_t)bin_cap) {
+    if (a.lists_in) best = list_search<RT>(a, nd, feats, m);
+    else for (uint32_t g0 = 0; g0 < total_bins; g0 += (uint32_t)bin_cap) {
         const uint32_t g1 = min(total_bins, g0 + (uint32_t)bin_cap);
         const int nb = (int)(g1 - g0);
         for (int b = tid; b < nb; b += kBigThreads) { bw[b] = 0u; blo[b] = 0u; bhi[b] = 0; }
@@ -970,6 +1135,29 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
         }
         run_l += tot;
         run_r += min((uint32_t)kBigThreads, nd.len - b0) - tot;
+    }
+    if (a.lists_in) {
+        // every feature's list, partitioned stably the same way: the children's segments stay
+        // in rank order
+        for (int f = 0; f < a.F; ++f) {
+            const uint32_t *Li = a.lists_in + (size_t)f * (size_t)a.list_stride + tb;
+            uint32_t *Lo = a.lists_out + (size_t)f * (size_t)a.list_stride + tb;
+            uint32_t rl = 0u, rr = 0u;
+            for (uint32_t b0 = 0; b0 < nd.len; b0 += kBigThreads) {
+                const uint32_t i = b0 + tid;
+                const bool valid = i < nd.len;
+                const uint32_t row = valid ? AIWCRF_IDX(__ldg(&Li[i]), (uint32_t)a.N, kBoundRow) : 0u;
+                const bool left = valid && (uint32_t)__ldg(&Rr[(size_t)row * (size_t)a.F + win.f]) <= win.r;
+                uint32_t tot;
+                const uint32_t incl = block_incl_scan(left ? 1u : 0u, warp_tmp, tot);
+                if (valid) {
+                    const uint32_t before_l = incl - (left ? 1u : 0u);
+                    Lo[AIWCRF_IDX(left ? rl + before_l : lenL + rr + ((uint32_t)tid - before_l), nd.len, kBoundOut)] = row;
+                }
+                rl += tot;
+                rr += min((uint32_t)kBigThreads, nd.len - b0) - tot;
+            }
+        }
     }
     if (tid == 0) {
         SplitRes sr;
@@ -1856,8 +2044,10 @@ static std::atomic<int> g_grower{AIWCRF_GROWER_AUTO};
 
 int set_grower_mode(int mode)
 {
-    if (mode != AIWCRF_GROWER_AUTO && mode != AIWCRF_GROWER_LEVEL && mode != AIWCRF_GROWER_TREE)
-        return fail(AIWCRF_E_INVALID_ARG, "grower: 0 (automatic), 1 (level-synchronous) or 2 (tree-resident)");
+    if (mode != AIWCRF_GROWER_AUTO && mode != AIWCRF_GROWER_LEVEL && mode != AIWCRF_GROWER_TREE &&
+        mode != AIWCRF_GROWER_LISTS)
+        return fail(AIWCRF_E_INVALID_ARG,
+                    "grower: 0 (automatic), 1 (level-synchronous), 2 (tree-resident) or 3 (presorted lists)");
     g_grower.store(mode);
     return AIWCRF_OK;
 }
@@ -2129,6 +2319,15 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     const bool rank8 = rank_bytes == 1;
     void *d_Rr = sc.get<uint8_t>((size_t)F * (size_t)N * (size_t)rank_bytes, &rc);
     if (rc) return rc;
+    // presorted lists for columns with many values (or when asked for): keep every column's
+    // sorted row order before the grouping reuses the sort buffers
+    const int gmode = grower_mode();
+    const bool use_lists = gmode == AIWCRF_GROWER_LISTS || (gmode == AIWCRF_GROWER_AUTO && max_card > kListMinCard);
+    uint32_t *d_ordF = nullptr;
+    if (use_lists) {
+        d_ordF = sc.get<uint32_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
+        AIWCRF_CUDA(cudaMemcpyAsync(d_ordF, vA, sizeof(uint32_t) * (size_t)F * (size_t)N, cudaMemcpyDeviceToDevice, s));
+    }
 
     // grouping of identical feature vectors
     uint32_t *grp_off = sc.get<uint32_t>((size_t)N + 1, &rc); if (rc) return rc;
@@ -2155,6 +2354,19 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         AIWCRF_CUDA(cudaStreamSynchronize(s));
     }
     const uint32_t *grp_rows = vA;            // rows in group order
+    // the groups' representative rows in every column's order
+    uint32_t *d_ordG = nullptr;
+    if (use_lists) {
+        uint8_t *is_rep = sc.get<uint8_t>((size_t)N, &rc); if (rc) return rc;
+        d_ordG = sc.get<uint32_t>((size_t)F * (size_t)n_groups, &rc); if (rc) return rc;
+        AIWCRF_CUDA(cudaMemsetAsync(is_rep, 0, (size_t)N, s));
+        rep_mark_kernel<<<(unsigned)((n_groups + 255) / 256), 256, 0, s>>>(grp_rows, grp_off, n_groups, is_rep);
+        rep_order_kernel<<<(unsigned)F, 1024, 0, s>>>(d_ordF, N, is_rep, n_groups, d_ordG);
+        count_launches(1);
+        AIWCRF_LAUNCH_CHECK("rep_mark / rep_order");
+        sc.drop(is_rep);
+        sc.drop(d_ordF);
+    }
     // the bootstrap's group-ordered pass: y in group order and every position's group
     int64_t *d_y_g = sc.get<int64_t>((size_t)N, &rc); if (rc) return rc;
     uint32_t *d_grp_of = sc.get<uint32_t>((size_t)N, &rc); if (rc) return rc;
@@ -2256,12 +2468,11 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     const int tree_ecap = (int)std::max<int64_t>(row_cap, 1);
     const int tree_big_cap = tree_ecap / (kSmallNodeRows + 1) + 1;
     const size_t tree_smem = tree_smem_bytes(tree_ecap, tree_bins, tree_big_cap);
-    const int gmode = grower_mode();
     const bool tree_fits = rank8 && F <= 32 && n_groups <= 65535u && row_cap <= 65535 &&
                            tree_smem + 1024 <= (size_t)max_smem_optin;
     if (gmode == AIWCRF_GROWER_TREE && !tree_fits)
         return fail(AIWCRF_E_LIMIT, "tree-resident growth needs one-byte ranks, F <= 32 and a tree's entries in shared memory");
-    const bool use_tree = tree_fits && gmode != AIWCRF_GROWER_LEVEL;
+    const bool use_tree = tree_fits && !use_lists && gmode != AIWCRF_GROWER_LEVEL;
     uint8_t *d_Rg = nullptr;
     if (use_tree) {
         d_Rg = sc.get<uint8_t>((size_t)n_groups * (size_t)F, &rc); if (rc) return rc;
@@ -2305,6 +2516,27 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         bootstrap_kernel<<<(unsigned)T, kBootThreads, smem_bytes, s>>>(ba);
         AIWCRF_LAUNCH_CHECK("bootstrap_kernel");
         prof_end(s, kProfBoot);
+    }
+
+    // presorted lists of every tree: its entries by representative row, then per feature in rank order
+    const int64_t list_stride = T * row_cap;
+    uint32_t *lists_a = nullptr, *lists_b = nullptr, *list_w = nullptr;
+    int64_t *list_wy = nullptr;
+    if (use_lists) {
+        list_w = sc.get<uint32_t>((size_t)T * (size_t)N, &rc); if (rc) return rc;
+        list_wy = sc.get<int64_t>((size_t)T * (size_t)N, &rc); if (rc) return rc;
+        lists_a = sc.get<uint32_t>((size_t)F * (size_t)list_stride, &rc); if (rc) return rc;
+        lists_b = sc.get<uint32_t>((size_t)F * (size_t)list_stride, &rc); if (rc) return rc;
+        prof_begin(s, kProfBoot);
+        AIWCRF_CUDA(cudaMemsetAsync(list_w, 0, sizeof(uint32_t) * (size_t)T * (size_t)N, s));
+        list_tables_kernel<<<dim3((unsigned)((row_cap + 255) / 256), (unsigned)T), 256, 0, s>>>(rows_a, row_cap, nodes_cur,
+                                                                                              N, list_w, list_wy);
+        AIWCRF_LAUNCH_CHECK("list_tables_kernel");
+        list_build_kernel<<<dim3((unsigned)T, (unsigned)F), 1024, 0, s>>>(d_ordG, n_groups, list_w, N, row_cap,
+                                                                         list_stride, lists_a);
+        AIWCRF_LAUNCH_CHECK("list_build_kernel");
+        prof_end(s, kProfBoot);
+        sc.drop(d_ordG);
     }
 
     if (use_tree) {
@@ -2373,7 +2605,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
 
     // bins: the tried features' value counts side by side (one pass over the entries)
     const int bin_cap = big_bin_cap(p.mtry, F, max_card);
-    const int big_smem = bin_cap * 14;
+    const int big_smem = use_lists ? 0 : bin_cap * 14;       // the list search needs no bins
     {
         cudaError_t e_ = cudaSuccess;
         AIWCRF_BY_RANK(rank_bytes, e_ = cudaFuncSetAttribute(level_big_kernel<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2387,6 +2619,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     la.max_depth = p.max_depth; la.seed_lo = (uint32_t)p.seed; la.seed_hi = (uint32_t)(p.seed >> 32);
     la.depth_ptr = nullptr;
     la.node_cap = 0;
+    la.list_stride = list_stride; la.list_w = list_w; la.list_wy = list_wy;
 
     // The two level kernels of a depth are independent (disjoint nodes, disjoint entry
     // segments): a foreground fit runs the small-node kernel on a second stream of the same
@@ -2413,6 +2646,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     cudaStream_t s_small = fork ? fk.side : s;
 
     Entry *rin = rows_a, *rout = rows_b;
+    uint32_t *lin = lists_a, *lout = lists_b;
     int depth = 0;
     int64_t C_known = T;                 // node count at the start of the next chunk (exact)
     uint64_t packed_known = 0;           // finished nodes before it (exact)
@@ -2433,6 +2667,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
             const int64_t Cb = bound(k);                        // bound on this depth's nodes
             la.nodes = nodes_cur; la.rows_in = rin; la.rows_out = rout; la.depth = depth; la.res = res;
             la.tile_splits = block_sums; la.node_cap = (uint32_t)node_cap;
+            la.lists_in = lin; la.lists_out = lout;
             if (fork) {
                 AIWCRF_CUDA(cudaEventRecord(fk.ev_fork, s));
                 AIWCRF_CUDA(cudaStreamWaitEvent(fk.side, fk.ev_fork, 0));
@@ -2475,6 +2710,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
 
             std::swap(nodes_cur, nodes_nxt);
             std::swap(rin, rout);
+            std::swap(lin, lout);
             std::swap(tree_off, tree_off_nxt);
         }
         AIWCRF_CUDA(cudaMemcpyAsync(h_cnt, d_cnt, sizeof(LevelCounts), cudaMemcpyDeviceToHost, s));
@@ -2489,7 +2725,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     pin.tree_base = tree_base; pin.d_stats = d_stats; pin.packed = packed; pin.packed_n = (size_t)packed_known;
     pin.levels = (int)h_cnt->levels; pin.d_inbag = d_inbag; pin.inbag_words = inbag_words;
     pin.d_vals = d_vals; pin.d_card = d_card; pin.max_card = max_card; pin.rank_bytes = rank_bytes; pin.n_groups = n_groups;
-    pin.grower = AIWCRF_GROWER_LEVEL;
+    pin.grower = use_lists ? AIWCRF_GROWER_LISTS : AIWCRF_GROWER_LEVEL;
     rc = package_forests(pin, s, out);
     sc.release();
     if (rc == AIWCRF_OK) AIWCRF_CUDA(cudaStreamSynchronize(s));

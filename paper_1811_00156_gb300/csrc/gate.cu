@@ -8,8 +8,8 @@
 //  3. exact ensemble-variance numerators over the forest's first var_trees trees;
 //  4. gate_kernel, one warp per kernel: out-of-range test of every feature of its D queries
 //     against the forest's value tables, the surrogate's best and runner-up devices, the test of
-//     their margin against the two contenders' ensemble spread, and the kernels that fall back
-//     appended to a list;
+//     their margin against the two contenders' ensemble spread and against a fixed threshold,
+//     and the kernels that fall back appended to a list;
 //  5. the fallback kernels' queries gathered, predicted by the whole forest, and their device
 //     chosen from the exact int64 predictions (fix_kernel).
 // Which kernel lands where in the fallback list depends on the order of the atomics, but every
@@ -41,10 +41,14 @@ __device__ __forceinline__ void warp_min(float &bs, int32_t &bd)
 }
 
 // One warp per kernel: range test of every feature of its D queries, the surrogate's best and
-// runner-up devices, and the margin test against the two contenders' prefix variances.
+// runner-up devices, and the margin tests: against the two contenders' prefix variances, and
+// against the fixed threshold tau. With list
+// set, flag[k] is 1 for a kernel that falls back and the kernel is appended to list (counts:
+// fallbacks, out-of-range, margin); without, flag[k] holds the reasons as bits (kGateForest,
+// kGateOod, kGateVar) and nothing is counted.
 __global__ void gate_kernel(const float *__restrict__ q, int64_t Qn, int F, int D, const float *__restrict__ fvals,
                             int64_t fstride, const uint32_t *__restrict__ fcard, const uint64_t *__restrict__ var,
-                            double z2, double scale, int ood, const float *__restrict__ sur,
+                            double z2, double scale, double tau, int ood, const float *__restrict__ sur,
                             const int32_t *__restrict__ dev, int K, uint8_t *flag, int32_t *best, float *pred,
                             int32_t *list, unsigned long long *counts)
 {
@@ -100,12 +104,13 @@ __global__ void gate_kernel(const float *__restrict__ q, int64_t Qn, int F, int 
             const double m = __dsub_rn((double)rs, (double)bs);
             const double lhs = __dmul_rn(__dmul_rn(m, m), scale);
             const double rhs = __dmul_rn(z2, vs);
-            v = lhs <= rhs;
+            v = lhs <= rhs || m < tau;
         }
         const bool fb = any_o || v;
-        flag[k] = fb ? 1 : 0;
+        flag[k] = !list ? (uint8_t)((fb ? kGateForest : 0u) | (any_o ? kGateOod : 0u) | (v ? kGateVar : 0u))
+                        : (uint8_t)(fb ? 1 : 0);
         best[k] = bd;
-        if (fb) {
+        if (fb && list) {
             const unsigned long long slot = atomicAdd(&counts[0], 1ull);
             list[slot] = (int32_t)k;
             if (any_o) atomicAdd(&counts[1], 1ull);
@@ -167,6 +172,59 @@ bool on_device(const void *p)
 }
 
 }  // namespace
+
+int gate_check(const aiwcrf_forest *forest, const aiwcrf_gate_params *gate)
+{
+    if (gate->var_trees < 1 || gate->var_trees > forest->T || !(gate->z >= 0.0f) || !(gate->z < 1048576.0f) ||
+        (gate->ood != 0 && gate->ood != 1) || !(gate->tau >= 0.0f) || !(gate->tau < 1048576.0f))
+        return fail(AIWCRF_E_INVALID_ARG, "gate parameters out of range");
+    return AIWCRF_OK;
+}
+
+size_t gate_scratch_bytes(int32_t F, int64_t Qn)
+{
+    return a256(4 * (size_t)F * (size_t)Qn) + a256(4 * (size_t)Qn) + a256(16 * (size_t)Qn) +
+           a256(predict_codes_bytes_max(F, Qn));
+}
+
+GateBuffers gate_scratch_split(void *scratch, int32_t F, int64_t Qn)
+{
+    GateBuffers b{};
+    unsigned char *c = static_cast<unsigned char *>(scratch);
+    b.q = reinterpret_cast<float *>(c);
+    c += a256(4 * (size_t)F * (size_t)Qn);
+    b.sur = reinterpret_cast<float *>(c);
+    c += a256(4 * (size_t)Qn);
+    b.var = reinterpret_cast<uint64_t *>(c);
+    c += a256(16 * (size_t)Qn);
+    b.codes = c;
+    return b;
+}
+
+int gate_enqueue(const aiwcrf_forest *forest, const aiwcrf_surrogate *sg, const aiwcrf_gate_params &gate,
+                 const float *d_kfeat, int32_t K, int64_t ld, int32_t size_class, const float *d_size_row,
+                 const int32_t *d_dev, int32_t D, const GateBuffers &b, cudaStream_t s)
+{
+    if (K == 0) return AIWCRF_OK;
+    const int F = forest->F;
+    const int64_t Qn = (int64_t)K * D;
+    // the margin test's constants: (z * z) and var_trees^2 * 2^64 (exact in double)
+    const double z2 = (double)gate.z * (double)gate.z;
+    const double scale = (double)gate.var_trees * (double)gate.var_trees * 0x1p64;
+    int rc;
+    if ((rc = expand_launch(d_kfeat, K, ld, size_class, d_size_row, d_dev, D, F, b.q, s))) return rc;
+    if ((rc = surrogate_predict_enqueue(sg, b.q, Qn, b.sur, b.err, s))) return rc;
+    if ((rc = predict_prefix_var_enqueue(forest, b.q, Qn, gate.var_trees, b.var, s, b.err, b.codes))) return rc;
+    const unsigned gblocks = (unsigned)(((int64_t)K * 32 + 255) / 256);
+    gate_kernel<<<gblocks, 256, 0, s>>>(b.q, Qn, F, D, forest->d_fvals, forest->fstride, forest->d_fcard, b.var, z2,
+                                        scale, (double)gate.tau, gate.ood, b.sur, d_dev, K, b.flag, b.best, b.pred,
+                                        b.list, b.counts);
+    count_launches(1);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "gate_kernel launch");
+    return AIWCRF_OK;
+}
+
 }  // namespace aiwcrf
 
 using namespace aiwcrf;
@@ -181,9 +239,8 @@ extern "C" int aiwcrf_select_device_gated(const aiwcrf_forest *forest, const aiw
     if (!forest || !surrogate || !gate || !device_ids)
         return fail(AIWCRF_E_INVALID_ARG, "forest, surrogate, gate and device_ids must not be NULL");
     if (n_kernels < 0 || n_devices < 1) return fail(AIWCRF_E_INVALID_ARG, "n_kernels >= 0 and n_devices >= 1");
-    if (gate->var_trees < 1 || gate->var_trees > forest->T || !(gate->z >= 0.0f) || !(gate->z < 1048576.0f) ||
-        (gate->ood != 0 && gate->ood != 1) || gate->reserved != 0)
-        return fail(AIWCRF_E_INVALID_ARG, "gate parameters out of range");
+    int rc = gate_check(forest, gate);
+    if (rc) return rc;
     if (stats) *stats = aiwcrf_gate_stats{n_kernels, 0, 0, 0};
     if (n_kernels == 0) return AIWCRF_OK;
     if (!kfeat || !out_best) return fail(AIWCRF_E_INVALID_ARG, "kfeat and out_best must not be NULL");
@@ -194,10 +251,6 @@ extern "C" int aiwcrf_select_device_gated(const aiwcrf_forest *forest, const aiw
     const int F = forest->F, D = n_devices, K = n_kernels;
     const int64_t Qn = (int64_t)K * D;
     keep_pool_memory(forest->device);
-
-    // the margin test's constants: (z * z) and var_trees^2 * 2^64 (exact in double)
-    const double z2 = (double)gate->z * (double)gate->z;
-    const double scale = (double)gate->var_trees * (double)gate->var_trees * 0x1p64;
 
     // scratch: device ids, queries, surrogate outputs, variance numerators, query codes, flags,
     // list, counters, error flag; then the fallback's gathered queries and predictions
@@ -225,17 +278,9 @@ extern "C" int aiwcrf_select_device_gated(const aiwcrf_forest *forest, const aiw
     cudaError_t e = cudaMemcpyAsync(d_dev, device_ids, 4 * (size_t)D, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, 32, s);
     if (e != cudaSuccess) return cuda_fail(e, "gated selection set-up");
-    int rc;
     prof_begin(s, kProfSelect);
-    if ((rc = expand_launch(kfeat, K, size_class, d_dev, D, F, d_q, s))) return rc;
-    if ((rc = surrogate_predict_enqueue(surrogate, d_q, Qn, d_sur, d_err, s))) return rc;
-    if ((rc = predict_prefix_var_enqueue(forest, d_q, Qn, gate->var_trees, d_var, s, d_err, d_codes))) return rc;
-    const unsigned gblocks = (unsigned)(((int64_t)K * 32 + 255) / 256);
-    gate_kernel<<<gblocks, 256, 0, s>>>(d_q, Qn, F, D, forest->d_fvals, forest->fstride, forest->d_fcard, d_var,
-                                        z2, scale, gate->ood, d_sur, d_dev, K, d_flag,
-                                        out_best, out_pred, d_list, d_cnt);
-    count_launches(1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gate_kernel launch");
+    const GateBuffers gb{d_q, d_sur, d_var, d_codes, d_flag, out_best, out_pred, d_list, d_cnt, d_err};
+    if ((rc = gate_enqueue(forest, surrogate, *gate, kfeat, K, K, size_class, nullptr, d_dev, D, gb, s))) return rc;
     unsigned long long h_cnt[4] = {0, 0, 0, 0};
     e = cudaMemcpyAsync(h_cnt, d_cnt, 32, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

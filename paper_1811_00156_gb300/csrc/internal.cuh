@@ -488,6 +488,8 @@ int tc_gemm(const __nv_bfloat16 *A, int lda, bool a_trans, const __nv_bfloat16 *
             int M, int N, int K, int ksplit, float *part, uint32_t *d_err, cudaStream_t s);
 // predict without allocating or synchronising: codes_scratch holds predict_codes_bytes(f, Q)
 size_t predict_codes_bytes(const aiwcrf_forest *f, int64_t Q);
+// the most predict_codes_bytes can be for any forest of F features
+size_t predict_codes_bytes_max(int32_t F, int64_t Q);
 int predict_enqueue(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum, int64_t *d_pred,
                     cudaStream_t s, uint32_t *d_err, void *codes_scratch);
 // fused surrogate inference on the stream, timeouts flagged in d_err (no allocation, no sync)
@@ -502,10 +504,48 @@ int select_small_launch(const aiwcrf_forest *f, const float *d_kfeat, int32_t K,
 // exact ensemble variance numerators of the first n_trees trees (2 u64 words per query)
 int predict_prefix_var_enqueue(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t n_trees,
                                uint64_t *d_var, cudaStream_t s, uint32_t *d_err, void *codes_scratch);
-// F x (K * D) queries: kernel k's F-2 features, device d_dev[j], size class (query k * D + j)
-int expand_launch(const float *d_kfeat, int32_t K, int32_t size_class, const int32_t *d_dev, int32_t D, int32_t F,
-                  float *d_q, cudaStream_t s);
+// F x (K * D) queries: kernel k's F-2 features, device d_dev[j], size class (query k * D + j);
+// d_kfeat has leading dimension ld; the size class is size_class, or d_size_row[k] if given
+int expand_launch(const float *d_kfeat, int32_t K, int64_t ld, int32_t size_class, const float *d_size_row,
+                  const int32_t *d_dev, int32_t D, int32_t F, float *d_q, cudaStream_t s);
 int oob_launch(const aiwcrf_forest *f, const float *dX, int64_t N, int64_t *d_sum, int32_t *d_count, cudaStream_t s);
+
+// Gated selection (gate.cu). A kernel's gate flag, when the reasons are kept: the forest answers
+// it (kGateForest), a feature lay outside the training range (kGateOod), the surrogate's margin
+// was within z deviations (kGateVar).
+constexpr uint8_t kGateForest = 1u, kGateOod = 2u, kGateVar = 4u;
+struct GateBuffers {
+    float *q;                      // F x (K * D) queries
+    float *sur;                    // K * D surrogate outputs
+    uint64_t *var;                 // 2 words per query: prefix variance numerators
+    void *codes;                   // predict_codes_bytes(forest, K * D)
+    uint8_t *flag;                 // K
+    int32_t *best;                 // K: the surrogate's device (the forest's is the caller's to write)
+    float *pred;                   // K x D surrogate predictions, or null
+    int32_t *list;                 // K fallback list with flag 0/1, or null for reason bits
+    unsigned long long *counts;    // 3 counters with list, else unused
+    uint32_t *err;                 // bounded-wait error flags
+};
+int gate_check(const aiwcrf_forest *forest, const aiwcrf_gate_params *gate);
+// bytes of q, sur, var and codes for Qn queries of any forest of F features (256-byte aligned parts)
+size_t gate_scratch_bytes(int32_t F, int64_t Qn);
+// steps 1-4 of the gated selection for K kernels (d_kfeat leading dimension ld; size class
+// size_class, or d_size_row[k] if given) on s, without allocating or synchronising
+int gate_enqueue(const aiwcrf_forest *forest, const aiwcrf_surrogate *sg, const aiwcrf_gate_params &gate,
+                 const float *d_kfeat, int32_t K, int64_t ld, int32_t size_class, const float *d_size_row,
+                 const int32_t *d_dev, int32_t D, const GateBuffers &b, cudaStream_t s);
+// a device copy of a surrogate on its device (parameters, transform, BF16 weights, statistics)
+int surrogate_clone(const aiwcrf_surrogate *src, aiwcrf_surrogate **out);
+// frees a surrogate in stream order on s; the caller has seen all work reading it complete
+void surrogate_release_async(aiwcrf_surrogate *sg, cudaStream_t s);
+struct SurrogateInfo {
+    int device;
+    int32_t F;
+    int64_t bytes;     // device bytes it holds
+};
+SurrogateInfo surrogate_info(const aiwcrf_surrogate *sg);
+// q, sur, var and codes of GateBuffers carved from gate_scratch_bytes(F, Qn) bytes at scratch
+GateBuffers gate_scratch_split(void *scratch, int32_t F, int64_t Qn);
 // out-of-bag error from aiwcrf_oob's sums and counts (d_y: the training targets): d_pred (or
 // null) gets the out-of-bag predictions, d_res the exact sum of squared errors and the mean
 struct OobPart { unsigned long long lo, hi, rows; };

@@ -644,17 +644,19 @@ __global__ void round_mean_kernel(const int64_t *sums, int64_t n, int64_t T, int
     out[i] = (int64_t)d;
 }
 
-// query (k, j) of device selection: kernel k's features, device_ids[j], size_class
-__global__ void expand_queries_kernel(const float *kfeat, int32_t K, int32_t size_class, const int32_t *dev,
-                                      int32_t D, int32_t F, float *q)
+// query (k, j) of device selection: kernel k's features (kfeat, leading dimension ld),
+// device_ids[j], and size_class, or size_row[k] where size_row is given
+__global__ void expand_queries_kernel(const float *kfeat, int32_t K, int64_t ld, int32_t size_class,
+                                      const float *size_row, const int32_t *dev, int32_t D, int32_t F, float *q)
 {
     const int64_t Qn = (int64_t)K * D;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= Qn) return;
     const int32_t k = (int32_t)(i / D), jd = (int32_t)(i % D);
-    for (int f = 0; f < F - 2; ++f) q[(size_t)f * (size_t)Qn + i] = kfeat[(size_t)f * (size_t)K + k];
+    for (int f = 0; f < F - 2; ++f) q[(size_t)f * (size_t)Qn + i] = kfeat[(size_t)f * (size_t)ld + k];
     q[(size_t)(F - 2) * (size_t)Qn + i] = (float)dev[jd];
-    q[(size_t)(F - 1) * (size_t)Qn + i] = (float)size_class;
+    q[(size_t)(F - 1) * (size_t)Qn + i] =
+        size_row ? size_row[k] : (float)size_class;
 }
 
 // argmin over devices per kernel; ties to the lower device id
@@ -805,6 +807,11 @@ size_t predict_codes_bytes(const aiwcrf_forest *f, int64_t Q)
     return (size_t)Q * (size_t)code_row_words(f->F, code_bytes_of(f)) * 4;
 }
 
+size_t predict_codes_bytes_max(int32_t F, int64_t Q)
+{
+    return (size_t)Q * (size_t)code_row_words(F, 4) * 4;
+}
+
 int predict_enqueue(const aiwcrf_forest *f, const float *dXq, int64_t Q, int64_t *d_sum, int64_t *d_pred,
                     cudaStream_t s, uint32_t *d_err, void *codes_scratch)
 {
@@ -825,12 +832,13 @@ int predict_prefix_var_enqueue(const aiwcrf_forest *f, const float *dXq, int64_t
     return launch_predict_ct<uint32_t>(f, dXq, Q, nullptr, nullptr, d_var, n_trees, s, d_err, codes_scratch, n_trees);
 }
 
-int expand_launch(const float *d_kfeat, int32_t K, int32_t size_class, const int32_t *d_dev, int32_t D, int32_t F,
-                  float *d_q, cudaStream_t s)
+int expand_launch(const float *d_kfeat, int32_t K, int64_t ld, int32_t size_class, const float *d_size_row,
+                  const int32_t *d_dev, int32_t D, int32_t F, float *d_q, cudaStream_t s)
 {
     const int64_t Qn = (int64_t)K * D;
     if (Qn == 0) return AIWCRF_OK;
-    expand_queries_kernel<<<(unsigned)((Qn + 255) / 256), 256, 0, s>>>(d_kfeat, K, size_class, d_dev, D, F, d_q);
+    expand_queries_kernel<<<(unsigned)((Qn + 255) / 256), 256, 0, s>>>(d_kfeat, K, ld, size_class, d_size_row, d_dev,
+                                                                        D, F, d_q);
     count_launches(1);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "expand_queries_kernel launch");
@@ -951,7 +959,9 @@ int select_launch(const aiwcrf_forest *f, const float *d_kfeat, int32_t K, int32
         return rc;
     }
     prof_begin(s, kProfSelect);
-    expand_queries_kernel<<<(unsigned)((Qn + 255) / 256), 256, 0, s>>>(d_kfeat, K, size_class, d_dev, D, f->F, d_q);
+    expand_queries_kernel<<<(unsigned)((Qn + 255) / 256), 256, 0, s>>>(d_kfeat, K, (int64_t)K, size_class, nullptr, d_dev, D,
+                                                                        f->F,
+                                                                        d_q);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "expand_queries_kernel launch");
@@ -988,7 +998,9 @@ int select_noalloc_ct(const aiwcrf_forest *f, const float *d_kfeat, int32_t K, i
 {
     const int64_t Qn = (int64_t)K * D;
     const int ld_words = code_ld_words(f);
-    expand_queries_kernel<<<(unsigned)((Qn + 255) / 256), 256, 0, s>>>(d_kfeat, K, size_class, d_dev, D, f->F, d_q);
+    expand_queries_kernel<<<(unsigned)((Qn + 255) / 256), 256, 0, s>>>(d_kfeat, K, (int64_t)K, size_class, nullptr, d_dev, D,
+                                                                        f->F,
+                                                                        d_q);
     count_launches(1);
     cudaError_t e = launch_code_queries<CT>(f, d_q, Qn, reinterpret_cast<CT *>(d_codes), ld_words, s);
     if (e != cudaSuccess) return cuda_fail(e, "code_queries_kernel launch");

@@ -151,18 +151,23 @@ __device__ __forceinline__ uint32_t rank_code(const float *V, uint32_t card, flo
 // coincide. kq: F x Kb column-major batch features (row F-2 unused: the device id comes from
 // dev[]; row F-1 the size class, unless size_override >= 0 gives it for every kernel, and then kq
 // may have only F-2 rows). sums (Kb * D) and cnt (Kb) are zero on entry and left zero.
-// pred: Kb x D row-major predictions; best: Kb device ids.
+// pred: Kb x D row-major predictions; best: Kb device ids. Kernels k < n_gated went through the
+// gate first: only those whose gate flag has kGateForest are answered here, and their
+// predictions are also written to fpred as float log10 seconds.
 template <bool COMPACT>
 __global__ void __launch_bounds__(kServeThreads) serve_select_kernel(ServeForest sf, const float *__restrict__ kq,
                                                                      int Kb, const int32_t *__restrict__ dev, int D,
                                                                      int size_override, unsigned long long *sums,
-                                                                     uint32_t *cnt, int64_t *pred, int32_t *best)
+                                                                     uint32_t *cnt, int64_t *pred, int32_t *best,
+                                                                     const uint8_t *__restrict__ only, int n_gated,
+                                                                     float *fpred)
 {
     __shared__ uint32_t kcode[AIWCRF_MAX_FEATURES];
     __shared__ uint32_t dcode[kServeMaxDevices];
     __shared__ int64_t red[kServeThreads / 32][kDevSlots];
     __shared__ int last;
     const int k = blockIdx.x, g = blockIdx.y;
+    if (k < n_gated && !(only[k] & kGateForest)) return;      // the surrogate's answer stands
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ts = tid / kDevSlots, jl = tid % kDevSlots;
     const uint32_t fd = (uint32_t)sf.F - 2u;
@@ -205,6 +210,7 @@ __global__ void __launch_bounds__(kServeThreads) serve_select_kernel(ServeForest
         if (num % den != 0 && num < 0) d -= 1;
         const int64_t p = (int64_t)d;
         pred[(size_t)k * (size_t)D + (size_t)j] = p;
+        if (k < n_gated) fpred[(size_t)k * (size_t)D + (size_t)j] = (float)((double)p * 0x1p-32);
         const int32_t id = dev[j];
         if (p < bp || (p == bp && id < bd)) { bp = p; bd = id; }
     }
@@ -253,7 +259,8 @@ size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr int64_t kIdlePollNs = 200000;   // the dispatcher polls this long before sleeping
 
 int serve_launch(const aiwcrf_forest *f, const float *d_kq, int Kb, const int32_t *d_dev, int D, int size_override,
-                 unsigned long long *d_sum, uint32_t *d_cnt, int64_t *d_pred, int32_t *d_best, cudaStream_t s)
+                 unsigned long long *d_sum, uint32_t *d_cnt, int64_t *d_pred, int32_t *d_best, cudaStream_t s,
+                 const uint8_t *d_only = nullptr, int n_gated = 0, float *d_fpred = nullptr)
 {
     ServeForest sf;
     sf.c32 = f->d_c32;
@@ -270,10 +277,10 @@ int serve_launch(const aiwcrf_forest *f, const float *d_kq, int Kb, const int32_
     prof_begin(s, kProfServe);
     if (f->compact)
         serve_select_kernel<true><<<grid, kServeThreads, 0, s>>>(sf, d_kq, Kb, d_dev, D, size_override, d_sum, d_cnt,
-                                                                 d_pred, d_best);
+                                                                 d_pred, d_best, d_only, n_gated, d_fpred);
     else
         serve_select_kernel<false><<<grid, kServeThreads, 0, s>>>(sf, d_kq, Kb, d_dev, D, size_override, d_sum, d_cnt,
-                                                                  d_pred, d_best);
+                                                                  d_pred, d_best, d_only, n_gated, d_fpred);
     prof_end(s, kProfServe);
     count_launches(1);
     const cudaError_t e = cudaGetLastError();
@@ -371,6 +378,10 @@ struct Request {
     int64_t generation = -1;
     std::vector<int32_t> best;
     std::vector<int64_t> pred;
+    // gated request: the surrogate answers unless the gate sends the kernel to the forest
+    bool gated = false;
+    std::vector<float> fpred;
+    std::vector<uint8_t> fallback;
     // load-generator request
     std::shared_ptr<LoadRun> run;
     int64_t run_index = 0, run_best_off = 0;
@@ -383,6 +394,22 @@ struct Model {
     int64_t bytes = 0;
 };
 
+// the server's own copy of a surrogate and the gate that decides when the forest answers instead
+struct SurModel {
+    aiwcrf_surrogate *sg = nullptr;
+    aiwcrf_gate_params gate{};
+    int64_t bytes = 0;
+};
+
+// Device bytes of one batch of Kb kernels, Kg of them gated (placed first): features, then the
+// results copied back in one piece (exact predictions, devices, and for the gated kernels their
+// float predictions, gate flags and the error word), then the gate's scratch.
+struct BatchLayout {
+    size_t out = 0;                                   // results, from the batch's start
+    size_t pred = 0, best = 0, fpred = 0, flag = 0, err = 0, out_bytes = 0;   // within the results
+    size_t scratch = 0, total = 0;
+};
+
 struct Slot {
     cudaStream_t s = nullptr;
     cudaEvent_t ev = nullptr;
@@ -392,7 +419,9 @@ struct Slot {
     uint32_t *d_cnt = nullptr;            // batch_kernels, kept zero between batches
     bool busy = false;
     int64_t off = -1, bytes = 0;
-    int32_t Kb = 0;
+    int32_t Kb = 0, Kg = 0;               // kernels, of which the first Kg gated
+    std::shared_ptr<SurModel> sur;        // the surrogate of the gated kernels
+    std::vector<int64_t> offs;            // each request's first kernel in the batch
     int64_t t_formed = 0, t_enqueued = 0;
     int64_t enq_cpu = 0, last_poll = 0, poll_gap_max = 0;
     int32_t enq_vol = 0, enq_invol = 0;
@@ -435,6 +464,7 @@ struct aiwcrf_server {
     int64_t next_ticket = 1;
     bool stop = false, paused = false;
     std::shared_ptr<Model> current;
+    std::shared_ptr<SurModel> cur_sur;    // null: gated requests are refused
     aiwcrf_server_counters st{};
     int64_t refit_mark = 0;
 
@@ -448,8 +478,9 @@ struct aiwcrf_server {
     std::vector<int64_t> ytrain, yapp;
     cudaStream_t refit_stream = nullptr;
 
-    std::mutex gmu;                       // forests waiting to be freed (on the refit stream)
+    std::mutex gmu;                       // forests and surrogates waiting to be freed (on the refit stream)
     std::vector<aiwcrf_forest *> graveyard;
+    std::vector<aiwcrf_surrogate *> sgraveyard;
 
     std::thread disp, refitter;
 
@@ -459,11 +490,27 @@ struct aiwcrf_server {
     std::vector<aiwcrf_refit_trace> rtrace = std::vector<aiwcrf_refit_trace>((size_t)kRefitRing);
     int64_t n_btrace = 0, n_rtrace = 0;
 
-    int64_t req_bytes(int64_t K) const
+    BatchLayout layout(int64_t Kb, int64_t Kg) const
     {
-        return (int64_t)(up256(sizeof(float) * (size_t)F * (size_t)K) +
-                         up256((size_t)K * ((size_t)D * 8 + 4)));
+        auto up16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+        BatchLayout L;
+        L.out = up256(sizeof(float) * (size_t)F * (size_t)Kb);
+        L.pred = 0;
+        L.best = 8 * (size_t)Kb * (size_t)D;
+        size_t o = L.best + 4 * (size_t)Kb;
+        if (Kg > 0) {
+            L.fpred = up16(o);
+            L.flag = L.fpred + 4 * (size_t)Kg * (size_t)D;
+            L.err = up16(L.flag + (size_t)Kg);
+            o = L.err + 4;
+        }
+        L.out_bytes = o;
+        L.scratch = L.out + up256(o);
+        L.total = L.scratch + (Kg > 0 ? gate_scratch_bytes(F, Kg * (int64_t)D) : 0);
+        return L;
     }
+
+    int64_t req_bytes(int64_t K) const { return (int64_t)layout(K, 0).total; }
 
     std::shared_ptr<Model> wrap(aiwcrf_forest *f, int64_t gen, int64_t rows)
     {
@@ -482,14 +529,32 @@ struct aiwcrf_server {
         });
     }
 
+    std::shared_ptr<SurModel> wrap_surrogate(aiwcrf_surrogate *sg, const aiwcrf_gate_params &gate)
+    {
+        SurModel *m = new SurModel();
+        m->sg = sg;
+        m->gate = gate;
+        m->bytes = surrogate_info(sg).bytes;
+        return std::shared_ptr<SurModel>(m, [this](SurModel *p) {
+            {
+                std::lock_guard<std::mutex> lk(gmu);
+                sgraveyard.push_back(p->sg);
+            }
+            delete p;
+        });
+    }
+
     void drain_graveyard()
     {
         std::vector<aiwcrf_forest *> g;
+        std::vector<aiwcrf_surrogate *> sgs;
         {
             std::lock_guard<std::mutex> lk(gmu);
             g.swap(graveyard);
+            sgs.swap(sgraveyard);
         }
         for (auto f : g) forest_release_async(f, refit_stream);
+        for (auto sg : sgs) surrogate_release_async(sg, refit_stream);
     }
 
     // fit a forest on the current training rows (refit thread or creation)
@@ -520,7 +585,8 @@ struct aiwcrf_server {
     }
 
     void finish(const std::shared_ptr<Request> &r, int status, const std::string &msg, int64_t gen,
-                const int32_t *best, const int64_t *pred, int64_t t_done)
+                const int32_t *best, const int64_t *pred, int64_t t_done, const float *fpred = nullptr,
+                const uint8_t *flags = nullptr)
     {
         if (r->run) {
             LoadRun &run = *r->run;
@@ -544,7 +610,13 @@ struct aiwcrf_server {
         r->generation = gen;
         if (status == AIWCRF_OK) {
             r->best.assign(best, best + r->K);
-            r->pred.assign(pred, pred + (size_t)r->K * (size_t)D);
+            if (r->gated) {
+                r->fpred.assign(fpred, fpred + (size_t)r->K * (size_t)D);
+                r->fallback.resize((size_t)r->K);
+                for (int32_t k = 0; k < r->K; ++k) r->fallback[(size_t)k] = (flags[k] & kGateForest) ? 1 : 0;
+            } else {
+                r->pred.assign(pred, pred + (size_t)r->K * (size_t)D);
+            }
         }
         r->done = true;
         cv_done.notify_all();
@@ -553,16 +625,30 @@ struct aiwcrf_server {
     void complete(Slot &sl, cudaError_t e)
     {
         const int64_t t = now_ns();
-        const int status = e == cudaSuccess ? AIWCRF_OK : AIWCRF_E_CUDA;
-        const std::string msg = e == cudaSuccess ? std::string() : std::string("selection batch: ") + cudaGetErrorString(e);
-        const int64_t *hp = reinterpret_cast<const int64_t *>(sl.h_out);
-        const int32_t *hb = reinterpret_cast<const int32_t *>(sl.h_out + (size_t)sl.Kb * (size_t)D * 8);
-        int64_t off = 0;
-        const int64_t gen = sl.model ? sl.model->gen : -1;
-        for (auto &r : sl.reqs) {
-            finish(r, status, msg, gen, hb + off, hp + off * D, t);
-            off += r->K;
+        const BatchLayout L = layout(sl.Kb, sl.Kg);
+        int status = e == cudaSuccess ? AIWCRF_OK : AIWCRF_E_CUDA;
+        std::string msg = e == cudaSuccess ? std::string() : std::string("selection batch: ") + cudaGetErrorString(e);
+        const int64_t *hp = reinterpret_cast<const int64_t *>(sl.h_out + L.pred);
+        const int32_t *hb = reinterpret_cast<const int32_t *>(sl.h_out + L.best);
+        const float *hf = sl.Kg ? reinterpret_cast<const float *>(sl.h_out + L.fpred) : nullptr;
+        const uint8_t *hfl = sl.Kg ? sl.h_out + L.flag : nullptr;
+        if (status == AIWCRF_OK && sl.Kg && (*reinterpret_cast<const uint32_t *>(sl.h_out + L.err) & kErrTimeout)) {
+            status = AIWCRF_E_TIMEOUT;
+            msg = "selection batch: a bounded device wait gave up";
         }
+        const int64_t gen = sl.model ? sl.model->gen : -1;
+        for (size_t i = 0; i < sl.reqs.size(); ++i) {
+            const int64_t off = sl.offs[i];
+            finish(sl.reqs[i], status, msg, gen, hb + off, hp + off * D, t, hf ? hf + off * D : nullptr,
+                   hfl ? hfl + off : nullptr);
+        }
+        int64_t n_fb = 0, n_ood = 0, n_var = 0;
+        if (status == AIWCRF_OK)
+            for (int32_t k = 0; k < sl.Kg; ++k) {
+                n_fb += (hfl[k] & kGateForest) ? 1 : 0;
+                n_ood += (hfl[k] & kGateOod) ? 1 : 0;
+                n_var += (hfl[k] & kGateVar) ? 1 : 0;
+            }
         bool want_refit = false;
         {
             std::lock_guard<std::mutex> lk(mu);
@@ -576,6 +662,12 @@ struct aiwcrf_server {
             tr.enqueue_voluntary_switches = sl.enq_vol;
             tr.enqueue_involuntary_switches = sl.enq_invol;
             tr.poll_gap_max_ns = std::max(sl.poll_gap_max, t - sl.last_poll);
+            tr.gated_kernels = sl.Kg;
+            tr.fallback_kernels = (int32_t)n_fb;
+            st.gated_kernels += sl.Kg;
+            st.gated_fallback += n_fb;
+            st.gated_fallback_ood += n_ood;
+            st.gated_fallback_var += n_var;
             arena.release(sl.off, sl.bytes);
             st.completed += (int64_t)sl.reqs.size();
             if (status != AIWCRF_OK) st.failed += (int64_t)sl.reqs.size();
@@ -587,7 +679,9 @@ struct aiwcrf_server {
         sl.busy = false;
         sl.off = -1;
         sl.reqs.clear();
+        sl.offs.clear();
         sl.model.reset();
+        sl.sur.reset();
         if (want_refit) {
             std::lock_guard<std::mutex> lk(rmu);
             refit_req = true;
@@ -596,20 +690,39 @@ struct aiwcrf_server {
     }
 
     // Takes the batch (popped under mu, features staged in sl.h_in) to the GPU.
+    // Gated kernels (the first Kg): expand, surrogate, prefix variances and gate (gate.cu); then
+    // the selection kernel answers the exact kernels and the gated kernels the gate sent to the
+    // forest. No host synchronisation inside a batch.
     void launch(Slot &sl)
     {
+        const BatchLayout L = layout(sl.Kb, sl.Kg);
         const size_t in_bytes = sizeof(float) * (size_t)F * (size_t)sl.Kb;
         unsigned char *base = d_arena + sl.off;
         float *d_in = reinterpret_cast<float *>(base);
-        int64_t *d_pred = reinterpret_cast<int64_t *>(base + up256(in_bytes));
-        int32_t *d_best = reinterpret_cast<int32_t *>(d_pred + (size_t)sl.Kb * (size_t)D);
-        const size_t out_bytes = (size_t)sl.Kb * ((size_t)D * 8 + 4);
+        unsigned char *d_out = base + L.out;
+        int64_t *d_pred = reinterpret_cast<int64_t *>(d_out + L.pred);
+        int32_t *d_best = reinterpret_cast<int32_t *>(d_out + L.best);
+        float *d_fpred = sl.Kg ? reinterpret_cast<float *>(d_out + L.fpred) : nullptr;
+        uint8_t *d_flag = sl.Kg ? d_out + L.flag : nullptr;
+        uint32_t *d_err = sl.Kg ? reinterpret_cast<uint32_t *>(d_out + L.err) : nullptr;
         const ThreadUsage u0 = thread_usage();
         cudaError_t e = cudaMemcpyAsync(d_in, sl.h_in, in_bytes, cudaMemcpyHostToDevice, sl.s);
-        if (e == cudaSuccess &&
-            serve_launch(sl.model->f, d_in, sl.Kb, d_dev, D, -1, sl.d_sum, sl.d_cnt, d_pred, d_best, sl.s) != AIWCRF_OK)
+        if (e == cudaSuccess && sl.Kg) {
+            e = cudaMemsetAsync(d_err, 0, sizeof(uint32_t), sl.s);
+            GateBuffers gb = gate_scratch_split(base + L.scratch, F, (int64_t)sl.Kg * D);
+            gb.flag = d_flag;
+            gb.best = d_best;
+            gb.pred = d_fpred;
+            gb.err = d_err;
+            if (e == cudaSuccess && gate_enqueue(sl.model->f, sl.sur->sg, sl.sur->gate, d_in, sl.Kg, sl.Kb, 0,
+                                                 d_in + (size_t)(F - 1) * (size_t)sl.Kb, d_dev, D, gb,
+                                                 sl.s) != AIWCRF_OK)
+                e = cudaErrorLaunchFailure;
+        }
+        if (e == cudaSuccess && serve_launch(sl.model->f, d_in, sl.Kb, d_dev, D, -1, sl.d_sum, sl.d_cnt, d_pred, d_best,
+                                             sl.s, d_flag, sl.Kg, d_fpred) != AIWCRF_OK)
             e = cudaErrorLaunchFailure;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_out, d_pred, out_bytes, cudaMemcpyDeviceToHost, sl.s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_out, d_out, L.out_bytes, cudaMemcpyDeviceToHost, sl.s);
         if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.s);
         sl.t_enqueued = now_ns();
         const ThreadUsage u1 = thread_usage();
@@ -667,14 +780,15 @@ struct aiwcrf_server {
             if (free_slot && !paused && !pending.empty()) {
                 // form a batch: arrival order, within the batch size and the arena's free space
                 const int64_t room = arena.largest();
-                int64_t Kb = 0;
+                int64_t Kb = 0, Kg = 0;
                 size_t n = 0;
                 bool cut = false;
                 while (n < pending.size()) {
-                    const int64_t K2 = Kb + pending[n]->K;
+                    const int64_t K2 = Kb + pending[n]->K, G2 = Kg + (pending[n]->gated ? pending[n]->K : 0);
                     if (K2 > sp.batch_kernels) break;
-                    if (req_bytes(K2) > room) { cut = true; break; }
+                    if ((int64_t)layout(K2, G2).total > room) { cut = true; break; }
                     Kb = K2;
+                    Kg = G2;
                     ++n;
                 }
                 if (n > 0) {
@@ -682,30 +796,37 @@ struct aiwcrf_server {
                     Slot &sl = *free_slot;
                     sl.t_formed = now_ns();
                     sl.Kb = (int32_t)Kb;
-                    sl.bytes = req_bytes(Kb);
+                    sl.Kg = (int32_t)Kg;
+                    sl.bytes = (int64_t)layout(Kb, Kg).total;
                     sl.off = arena.alloc(sl.bytes);
                     sl.reqs.assign(pending.begin(), pending.begin() + (std::ptrdiff_t)n);
                     pending.erase(pending.begin(), pending.begin() + (std::ptrdiff_t)n);
                     n_pending.store((int64_t)pending.size());
                     sl.model = current;
+                    sl.sur = Kg ? cur_sur : nullptr;
                     ++st.batches;
                     st.batch_kernels_total += Kb;
                     st.batch_kernels_max = std::max(st.batch_kernels_max, Kb);
                     st.arena_peak_bytes = std::max(st.arena_peak_bytes, arena.peak);
-                    // stage features while the requests' sources are guaranteed alive
-                    int64_t k0 = 0;
-                    for (auto &r : sl.reqs) {
+                    // stage features while the requests' sources are guaranteed alive: the gated
+                    // requests' kernels first, then the others, each request's kernels together
+                    sl.offs.assign(sl.reqs.size(), 0);
+                    int64_t kg = 0, kx = Kg;
+                    for (size_t i = 0; i < sl.reqs.size(); ++i) {
+                        const Request &r = *sl.reqs[i];
+                        int64_t &k0 = r.gated ? kg : kx;
+                        sl.offs[i] = k0;
                         for (int32_t f = 0; f < F; ++f) {
                             float *dst = sl.h_in + (size_t)f * (size_t)Kb + (size_t)k0;
                             if (f < F - 2) {
-                                const float *src = r->src + (size_t)f * (size_t)r->ld;
-                                std::memcpy(dst, src, sizeof(float) * (size_t)r->K);
+                                const float *src = r.src + (size_t)f * (size_t)r.ld;
+                                std::memcpy(dst, src, sizeof(float) * (size_t)r.K);
                             } else {
-                                const float val = f == F - 2 ? 0.0f : (float)r->size;
-                                std::fill(dst, dst + r->K, val);
+                                const float val = f == F - 2 ? 0.0f : (float)r.size;
+                                std::fill(dst, dst + r.K, val);
                             }
                         }
-                        k0 += r->K;
+                        k0 += r.K;
                     }
                     lk.unlock();
                     launch(sl);
@@ -801,6 +922,7 @@ struct aiwcrf_server {
     {
         std::lock_guard<std::mutex> lk(mu);
         if (stop) return fail(AIWCRF_E_INVALID_ARG, "server is shutting down");
+        if (r->gated && !cur_sur) return fail(AIWCRF_E_INVALID_ARG, "gated request: the server holds no surrogate");
         if ((int64_t)pending.size() >= sp.max_pending) {
             ++st.rejected;
             return fail(AIWCRF_E_LIMIT, "request refused: max_pending requests are waiting");
@@ -831,6 +953,7 @@ struct aiwcrf_server {
         }
         if (refitter.joinable()) refitter.join();
         current.reset();
+        cur_sur.reset();
         drain_graveyard();
         if (refit_stream) cudaStreamSynchronize(refit_stream);
         for (auto &sl : slots) {
@@ -918,7 +1041,7 @@ int aiwcrf_server_create(const aiwcrf_server_params *params, const aiwcrf_fit_pa
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&sl.s, cudaStreamNonBlocking, prio_high);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_in, sizeof(float) * (size_t)n_features * KB);
-        if (e == cudaSuccess) e = cudaMallocHost(&sl.h_out, KB * (D * 8 + 4));
+        if (e == cudaSuccess) e = cudaMallocHost(&sl.h_out, s->layout((int64_t)KB, (int64_t)KB).out_bytes);
         if (e == cudaSuccess) e = cudaMalloc(&sl.d_sum, sizeof(unsigned long long) * KB * D);
         if (e == cudaSuccess) e = cudaMalloc(&sl.d_cnt, sizeof(uint32_t) * KB);
         if (e == cudaSuccess) e = cudaMemset(sl.d_sum, 0, sizeof(unsigned long long) * KB * D);
@@ -955,20 +1078,27 @@ int aiwcrf_server_create(const aiwcrf_server_params *params, const aiwcrf_fit_pa
     return AIWCRF_OK;
 }
 
-int aiwcrf_server_submit(aiwcrf_server *server, const float *kfeat, int32_t n_kernels, int32_t size_class,
-                         int64_t *ticket)
+}  // extern "C"
+
+namespace {
+
+int submit_request(aiwcrf_server *server, const float *kfeat, int32_t n_kernels, int32_t size_class, bool gated,
+                   int64_t *ticket)
 {
-    aiwcrf::clear_last_error();
     if (!server || !kfeat || !ticket) return fail(AIWCRF_E_INVALID_ARG, "null argument");
     if (n_kernels < 1) return fail(AIWCRF_E_INVALID_ARG, "n_kernels must be >= 1");
-    if (n_kernels > server->sp.max_request_kernels) {
+    if (n_kernels > server->sp.max_request_kernels ||
+        (gated && (int64_t)server->layout(n_kernels, n_kernels).total > server->sp.arena_bytes)) {
         std::lock_guard<std::mutex> lk(server->mu);
         ++server->st.rejected;
-        return fail(AIWCRF_E_LIMIT, "request has more than max_request_kernels kernels");
+        return fail(AIWCRF_E_LIMIT, n_kernels > server->sp.max_request_kernels
+                                        ? "request has more than max_request_kernels kernels"
+                                        : "a gated request of this size cannot fit the arena");
     }
     auto r = std::make_shared<Request>();
     r->K = n_kernels;
     r->size = size_class;
+    r->gated = gated;
     r->own.assign(kfeat, kfeat + (size_t)(server->F - 2) * (size_t)n_kernels);
     r->src = r->own.data();
     r->ld = n_kernels;
@@ -978,24 +1108,118 @@ int aiwcrf_server_submit(aiwcrf_server *server, const float *kfeat, int32_t n_ke
     return rc;
 }
 
-int aiwcrf_server_wait(aiwcrf_server *server, int64_t ticket, int32_t timeout_ms, int32_t *best, int64_t *pred,
-                       int64_t *generation)
+// waits for a ticket of the given kind; on completion retires it and returns the request
+int wait_request(aiwcrf_server *server, int64_t ticket, int32_t timeout_ms, bool gated, std::shared_ptr<Request> *out)
 {
-    aiwcrf::clear_last_error();
     if (!server) return fail(AIWCRF_E_INVALID_ARG, "null server");
     std::unique_lock<std::mutex> lk(server->mu);
     auto it = server->tickets.find(ticket);
     if (it == server->tickets.end()) return fail(AIWCRF_E_INVALID_ARG, "unknown ticket");
     std::shared_ptr<Request> r = it->second;
+    if (r->gated != gated)
+        return fail(AIWCRF_E_INVALID_ARG, gated ? "not a gated request: use aiwcrf_server_wait"
+                                                : "a gated request: use aiwcrf_server_wait_gated");
     auto ready = [&] { return r->done; };
     if (timeout_ms < 0) server->cv_done.wait(lk, ready);
     else if (!server->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
         return fail(AIWCRF_E_TIMEOUT, "request still running");
     server->tickets.erase(ticket);
     if (r->status != AIWCRF_OK) return fail(r->status, r->msg);
+    *out = r;
+    return AIWCRF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int aiwcrf_server_submit(aiwcrf_server *server, const float *kfeat, int32_t n_kernels, int32_t size_class,
+                         int64_t *ticket)
+{
+    aiwcrf::clear_last_error();
+    return submit_request(server, kfeat, n_kernels, size_class, false, ticket);
+}
+
+int aiwcrf_server_submit_gated(aiwcrf_server *server, const float *kfeat, int32_t n_kernels, int32_t size_class,
+                               int64_t *ticket)
+{
+    aiwcrf::clear_last_error();
+    return submit_request(server, kfeat, n_kernels, size_class, true, ticket);
+}
+
+int aiwcrf_server_wait(aiwcrf_server *server, int64_t ticket, int32_t timeout_ms, int32_t *best, int64_t *pred,
+                       int64_t *generation)
+{
+    aiwcrf::clear_last_error();
+    std::shared_ptr<Request> r;
+    const int rc = wait_request(server, ticket, timeout_ms, false, &r);
+    if (rc) return rc;
     if (best) std::copy(r->best.begin(), r->best.end(), best);
     if (pred) std::copy(r->pred.begin(), r->pred.end(), pred);
     if (generation) *generation = r->generation;
+    return AIWCRF_OK;
+}
+
+int aiwcrf_server_wait_gated(aiwcrf_server *server, int64_t ticket, int32_t timeout_ms, int32_t *best, float *pred,
+                             uint8_t *fallback, int64_t *generation)
+{
+    aiwcrf::clear_last_error();
+    std::shared_ptr<Request> r;
+    const int rc = wait_request(server, ticket, timeout_ms, true, &r);
+    if (rc) return rc;
+    if (best) std::copy(r->best.begin(), r->best.end(), best);
+    if (pred) std::copy(r->fpred.begin(), r->fpred.end(), pred);
+    if (fallback) std::copy(r->fallback.begin(), r->fallback.end(), fallback);
+    if (generation) *generation = r->generation;
+    return AIWCRF_OK;
+}
+
+int aiwcrf_server_set_surrogate(aiwcrf_server *server, const aiwcrf_surrogate *surrogate,
+                                const aiwcrf_gate_params *gate)
+{
+    aiwcrf::clear_last_error();
+    if (!server) return fail(AIWCRF_E_INVALID_ARG, "null server");
+    std::shared_ptr<SurModel> sm;
+    if (surrogate) {
+        if (!gate) return fail(AIWCRF_E_INVALID_ARG, "gate must not be NULL with a surrogate");
+        std::shared_ptr<Model> cur;
+        {
+            std::lock_guard<std::mutex> lk(server->mu);
+            cur = server->current;
+        }
+        int rc = gate_check(cur->f, gate);
+        if (rc) return rc;
+        const SurrogateInfo si = surrogate_info(surrogate);
+        if (si.F != server->F) return fail(AIWCRF_E_INVALID_ARG, "the surrogate's n_features differs from the server's");
+        if (si.device != server->device) return fail(AIWCRF_E_INVALID_ARG, "the surrogate is on another device");
+        aiwcrf_surrogate *copy = nullptr;
+        if ((rc = surrogate_clone(surrogate, &copy))) return rc;
+        sm = server->wrap_surrogate(copy, *gate);
+    }
+    std::shared_ptr<SurModel> old;
+    std::vector<std::shared_ptr<Request>> drop;
+    {
+        std::lock_guard<std::mutex> lk(server->mu);
+        old = server->cur_sur;
+        server->cur_sur = sm;
+        server->st.surrogate_bytes = sm ? sm->bytes : 0;
+        if (!sm) {
+            // queued gated requests can no longer be answered
+            std::deque<std::shared_ptr<Request>> keep;
+            for (auto &r : server->pending) {
+                if (r->gated) drop.push_back(r);
+                else keep.push_back(r);
+            }
+            if (!drop.empty()) {
+                server->pending.swap(keep);
+                server->n_pending.store((int64_t)server->pending.size());
+            }
+        }
+    }
+    old.reset();
+    for (auto &r : drop)
+        server->finish(r, AIWCRF_E_INVALID_ARG, "gated request: the server's surrogate was removed", -1, nullptr,
+                       nullptr, now_ns());
     return AIWCRF_OK;
 }
 
@@ -1055,12 +1279,15 @@ int aiwcrf_server_stats(aiwcrf_server *server, aiwcrf_server_counters *out)
     return AIWCRF_OK;
 }
 
-int aiwcrf_server_run_load(aiwcrf_server *server, const float *pool, int64_t pool_kernels, const int64_t *first,
-                           const int32_t *n_kernels, const int32_t *size_class, int64_t n_requests, double rate_per_s,
-                           uint64_t seed, int32_t timeout_ms, int32_t *best, int64_t *generation, int64_t *latency_ns,
-                           aiwcrf_load_report *report)
+}  // extern "C"
+
+namespace {
+
+int run_load(aiwcrf_server *server, const float *pool, int64_t pool_kernels, const int64_t *first,
+             const int32_t *n_kernels, const int32_t *size_class, const uint8_t *gated, int64_t n_requests,
+             double rate_per_s, uint64_t seed, int32_t timeout_ms, int32_t *best, int64_t *generation,
+             int64_t *latency_ns, aiwcrf_load_report *report)
 {
-    aiwcrf::clear_last_error();
     if (!server || !pool || !first || !n_kernels || !size_class || !report)
         return fail(AIWCRF_E_INVALID_ARG, "null argument");
     if (n_requests < 1 || !(rate_per_s > 0.0) || pool_kernels < 1)
@@ -1108,7 +1335,10 @@ int aiwcrf_server_run_load(aiwcrf_server *server, const float *pool, int64_t poo
         r->run = run;
         r->run_index = i;
         r->run_best_off = best_off[(size_t)i];
-        int rc = r->K > server->sp.max_request_kernels ? AIWCRF_E_LIMIT : server->enqueue(r);
+        r->gated = gated && gated[i];
+        const bool too_big = r->K > server->sp.max_request_kernels ||
+                             (r->gated && (int64_t)server->layout(r->K, r->K).total > server->sp.arena_bytes);
+        int rc = too_big ? AIWCRF_E_LIMIT : server->enqueue(r);
         if (rc != AIWCRF_OK) {
             std::lock_guard<std::mutex> lk(run->mu);
             --run->remaining;
@@ -1177,6 +1407,30 @@ int aiwcrf_server_run_load(aiwcrf_server *server, const float *pool, int64_t poo
     if (timed_out) return fail(AIWCRF_E_TIMEOUT, "requests still running at the time limit");
     if (run->first_error != AIWCRF_OK) return fail(run->first_error, "a request failed");
     return AIWCRF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int aiwcrf_server_run_load(aiwcrf_server *server, const float *pool, int64_t pool_kernels, const int64_t *first,
+                           const int32_t *n_kernels, const int32_t *size_class, int64_t n_requests, double rate_per_s,
+                           uint64_t seed, int32_t timeout_ms, int32_t *best, int64_t *generation, int64_t *latency_ns,
+                           aiwcrf_load_report *report)
+{
+    aiwcrf::clear_last_error();
+    return run_load(server, pool, pool_kernels, first, n_kernels, size_class, nullptr, n_requests, rate_per_s, seed,
+                    timeout_ms, best, generation, latency_ns, report);
+}
+
+int aiwcrf_server_run_load_gated(aiwcrf_server *server, const float *pool, int64_t pool_kernels, const int64_t *first,
+                                 const int32_t *n_kernels, const int32_t *size_class, const uint8_t *gated,
+                                 int64_t n_requests, double rate_per_s, uint64_t seed, int32_t timeout_ms,
+                                 int32_t *best, int64_t *generation, int64_t *latency_ns, aiwcrf_load_report *report)
+{
+    aiwcrf::clear_last_error();
+    return run_load(server, pool, pool_kernels, first, n_kernels, size_class, gated, n_requests, rate_per_s, seed,
+                    timeout_ms, best, generation, latency_ns, report);
 }
 
 int aiwcrf_server_trace(aiwcrf_server *server, aiwcrf_batch_trace *batches, int64_t cap, int64_t *n,

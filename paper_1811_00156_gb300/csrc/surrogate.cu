@@ -383,18 +383,25 @@ void surrogate_release(aiwcrf_surrogate *s)
     delete s;
 }
 
+size_t surrogate_block_bytes(int32_t n_aiwc)
+{
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    return up(4 * (size_t)kParams) + 2 * up(4 * (size_t)n_aiwc) + up((size_t)n_aiwc) + up(2 * (size_t)kHid * kIn) +
+           up(2 * (size_t)kHid * kHid);
+}
+
 int surrogate_alloc(aiwcrf_surrogate *s)
 {
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t bp = up(4 * (size_t)kParams), bf = up(4 * (size_t)s->n_aiwc), bl = up((size_t)s->n_aiwc);
-    const size_t bw1 = up(2 * (size_t)kHid * kIn), bw2 = up(2 * (size_t)kHid * kHid);
+    const size_t bw1 = up(2 * (size_t)kHid * kIn);
     // from the stream-ordered pool, whose frees never wait for the whole device (a
     // selection server may be busy on other streams)
     int dev = 0;
     cudaGetDevice(&dev);
     keep_pool_memory(dev);
     void *p = nullptr;
-    cudaError_t e = cudaMallocAsync(&p, bp + 2 * bf + bl + bw1 + bw2, cudaStreamPerThread);
+    cudaError_t e = cudaMallocAsync(&p, surrogate_block_bytes(s->n_aiwc), cudaStreamPerThread);
     if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamPerThread);
     if (e != cudaSuccess) return fail(AIWCRF_E_OOM, "surrogate allocation");
     unsigned char *c = static_cast<unsigned char *>(p);
@@ -573,6 +580,46 @@ int new_surrogate(int32_t F, int32_t n_dev, int32_t n_size, aiwcrf_surrogate **o
 }
 
 }  // namespace
+
+int surrogate_clone(const aiwcrf_surrogate *src, aiwcrf_surrogate **out)
+{
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != src->device) cudaSetDevice(src->device);
+    aiwcrf_surrogate *sg = nullptr;
+    int rc = new_surrogate(src->F, src->n_dev, src->n_size, &sg);
+    if (!rc) {
+        sg->mu = src->mu;
+        sg->sd = src->sd;
+        sg->logf = src->logf;
+        sg->stats = src->stats;
+        // the same sizes give the same block layout: one device-to-device copy
+        cudaError_t e = cudaMemcpyAsync(sg->d_block, src->d_block, surrogate_block_bytes(src->n_aiwc),
+                                        cudaMemcpyDeviceToDevice, cudaStreamPerThread);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamPerThread);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "surrogate copy");
+            surrogate_release(sg);
+            sg = nullptr;
+        }
+    }
+    if (cur != src->device) cudaSetDevice(cur);
+    if (rc) return rc;
+    *out = sg;
+    return AIWCRF_OK;
+}
+
+SurrogateInfo surrogate_info(const aiwcrf_surrogate *sg)
+{
+    return SurrogateInfo{sg->device, sg->F, (int64_t)surrogate_block_bytes(sg->n_aiwc)};
+}
+
+void surrogate_release_async(aiwcrf_surrogate *sg, cudaStream_t s)
+{
+    if (!sg) return;
+    if (sg->d_block) cudaFreeAsync(sg->d_block, s);
+    delete sg;
+}
 
 int surrogate_predict_enqueue(const aiwcrf_surrogate *sg, const float *dXq, int64_t Q, float *d_out, uint32_t *d_err,
                               cudaStream_t s)

@@ -200,6 +200,21 @@ def kernel_neighbours(K: int, size: int, jitter: float = 0.05, seed: int = QUERY
     return np.ascontiguousarray(out.astype(np.float32))
 
 
+def neighbour_queries(q: int, jitter: float = 0.05, seed: int = QUERY_SEED) -> np.ndarray:
+    """q query rows near the training kernels: kernel_neighbours' AIWC vectors, the size class
+    uniform (each size's vectors drawn at that size), the device uniform. float32 [32][q]."""
+    rng = np.random.default_rng(seed)
+    size = rng.integers(0, N_SIZES, size=q)
+    Xq = np.empty((N_FEATURES, q), dtype=np.float32)
+    for s in range(N_SIZES):
+        idx = np.nonzero(size == s)[0]
+        if idx.size:
+            Xq[:N_AIWC, idx] = kernel_neighbours(int(idx.size), s, jitter=jitter, seed=seed * N_SIZES + s + 1)
+    Xq[COL_DEVICE] = rng.integers(0, N_DEVICES, size=q).astype(np.float32)
+    Xq[COL_SIZE] = size.astype(np.float32)
+    return Xq
+
+
 def loko_folds(seed: int = DATA_SEED):
     """Leave-one-kernel-out folds over the 2,220-row workload.
 

@@ -85,7 +85,7 @@ def margin_terms(models, kf, size):
     return s, b, m, Vs
 
 
-def expected(A, models, kf, size, z, ood):
+def expected(A, models, kf, size, z, ood, tau=0.0):
     """The gate written out from its definition in the header, in Python doubles."""
     wl, f, sg, of, op = models
     K = kf.shape[1]
@@ -96,7 +96,7 @@ def expected(A, models, kf, size, z, ood):
     var_fb = np.zeros(K, bool)
     for k in range(K):
         vs = float(Vs[k] >> 64) * 2.0 ** 64 + float(Vs[k] & (2 ** 64 - 1))
-        var_fb[k] = (m[k] * m[k]) * scale <= z2 * vs
+        var_fb[k] = (m[k] * m[k]) * scale <= z2 * vs or m[k] < float(np.float32(tau))
     Xq = expand(kf, size)
     lo = wl.X.min(axis=1)[:, None]
     hi = wl.X.max(axis=1)[:, None]
@@ -119,33 +119,40 @@ def median_critical_z(models, kf, size):
     return float(np.float32(np.median(zc)))
 
 
-@pytest.mark.parametrize("z,ood", [("median", True), (0.0, False), (1e5, False), ("median", False)])
-def test_gate_matches_oracle(A, models, z, ood):
+def median_margin(models, kf, size):
+    return float(np.float32(np.median(margin_terms(models, kf, size)[2])))
+
+
+@pytest.mark.parametrize("z,ood,tau", [("median", True, 0.0), (0.0, False, 0.0), (1e5, False, 0.0),
+                                       ("median", False, 0.0), (0.0, True, "median"), (0.0, False, "median")])
+def test_gate_matches_oracle(A, models, z, ood, tau):
     wl, f, sg, of, op = models
     K, size = 300, 2
     kf = kernels(K, seed=41)
     if z == "median":
         z = median_critical_z(models, kf, size)
-    fb, ood_fb, var_fb, best, pred = expected(A, models, kf, size, z, ood)
+    if tau == "median":
+        tau = median_margin(models, kf, size)
+    fb, ood_fb, var_fb, best, pred = expected(A, models, kf, size, z, ood, tau)
     ob = torch.empty(K, dtype=torch.int32, device="cuda")
     opr = torch.empty(K * DEV.size, dtype=torch.float32, device="cuda")
     ofb = torch.empty(K, dtype=torch.uint8, device="cuda")
-    st = A.aiwcrf_select_device_gated(f, sg, A.gate_params(VAR_TREES, z, ood), torch.from_numpy(kf).cuda(), size,
-                                      DEV, ob, opr, ofb)
+    st = A.aiwcrf_select_device_gated(f, sg, A.gate_params(VAR_TREES, z, ood, tau), torch.from_numpy(kf).cuda(),
+                                      size, DEV, ob, opr, ofb)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(ofb.cpu().numpy().astype(bool), fb)
     np.testing.assert_array_equal(ob.cpu().numpy(), best)
     np.testing.assert_array_equal(opr.cpu().numpy().reshape(K, -1), pred)
     assert st == {"kernels": K, "fallback": int(fb.sum()), "fallback_ood": int(ood_fb.sum()),
                   "fallback_var": int(var_fb.sum())}
-    if z == 0.0:        # only exact ties between the two best devices are uncertain at z = 0
+    if z == 0.0 and tau == 0.0:     # only exact ties between the two best devices are uncertain at z = 0
         m = margin_terms(models, kf, size)[2]
         np.testing.assert_array_equal(var_fb, np.array(m) == 0.0)
     if z == 1e5:
         assert st["fallback_var"] > K * 9 // 10
     if ood:
         assert ood_fb[[3, 5, 7]].all()
-    if not isinstance(z, float) or z not in (0.0, 1e5):
+    if not isinstance(z, float) or z not in (0.0, 1e5) or tau != 0.0:
         assert K // 4 < st["fallback_var"] < 3 * K // 4         # both paths taken
 
 
@@ -171,7 +178,8 @@ def test_gate_argument_checks(A, models):
     kf = torch.from_numpy(kernels(8, seed=44)).cuda()
     ob = torch.empty(8, dtype=torch.int32, device="cuda")
     for g in (A.gate_params(0, 1.0), A.gate_params(T + 1, 1.0), A.gate_params(8, -1.0),
-              A.gate_params(8, 2.0 ** 21), A.GateParams(8, 1.0, 2, 0), A.GateParams(8, 1.0, 1, 1)):
+              A.gate_params(8, 2.0 ** 21), A.GateParams(8, 1.0, 2, 0), A.GateParams(8, 1.0, 1, -1.0),
+              A.GateParams(8, 1.0, 1, 2.0 ** 21), A.GateParams(8, 1.0, 1, float("nan"))):
         with pytest.raises(A.AiwcrfError) as e:
             A.aiwcrf_select_device_gated(f, sg, g, kf, 0, DEV, ob)
         assert e.value.code == -1

@@ -1,8 +1,9 @@
-"""The two growers give the same forest: the tree-resident kernel (one CTA per tree, every
-depth in shared memory) and the level-synchronous kernels (three launches per depth), byte for
-byte in the serialized forest and in every fit counter. The oracle comparisons of
-test_gpu_parity.py run with the automatic choice, which takes the tree-resident kernel for
-every case whose trees fit."""
+"""The growers give the same forest: the tree-resident kernel (one CTA per tree, every depth in
+shared memory), the level-synchronous kernels (three launches per depth) with histogram search,
+and the level-synchronous kernels with presorted lists, byte for byte in the serialized forest
+and in every fit counter. The oracle comparisons of test_gpu_parity.py run with the automatic
+choice, which takes the tree-resident kernel for every case whose trees fit and the lists for
+columns of more than 4,096 values."""
 import numpy as np
 import pytest
 
@@ -39,10 +40,12 @@ def fit_with(grower, wl, prm):
         A.aiwcrf_set_grower(A.GROWER_AUTO)
 
 
-def same_forest(a, b):
+def same_forest(a, b, ga=None, gb=None):
+    ga = A.GROWER_TREE if ga is None else ga
+    gb = A.GROWER_LEVEL if gb is None else gb
     assert a.serialize() == b.serialize()
     sa, sb = a.stats(), b.stats()
-    assert sa.pop("grower") == A.GROWER_TREE and sb.pop("grower") == A.GROWER_LEVEL
+    assert sa.pop("grower") == ga and sb.pop("grower") == gb
     assert sa == sb
 
 
@@ -109,3 +112,64 @@ def test_tree_grower_refuses_trees_that_do_not_fit_and_auto_falls_back():
     assert f.stats()["grower"] == A.GROWER_LEVEL
     with pytest.raises(A.AiwcrfError):
         A.aiwcrf_set_grower(7)
+
+
+LIST_CASES = CASES + [
+    ("card-5000", lambda: synth.small_case(11, 5000, 6), dict(T=6, mtry=3, min_node=2)),
+    ("card-70000", lambda: synth.small_case(12, 70000, 3), dict(T=2, mtry=2, min_node=40)),
+    ("card-3000-depth4", lambda: synth.small_case(13, 3000, 5, card=3000), dict(T=5, mtry=5, min_node=1, max_depth=4)),
+    ("card-9000-no-bootstrap", lambda: synth.small_case(14, 9000, 4), dict(T=3, mtry=4, min_node=3, bootstrap=False)),
+]
+
+
+@pytest.mark.parametrize("case", LIST_CASES, ids=[c[0] for c in LIST_CASES])
+def test_list_search_gives_identical_forests(case):
+    """Presorted lists against the histogram search, on the growers' cases and on columns with
+    thousands to tens of thousands of values (several histogram passes per node)."""
+    _, make, kw = case
+    wl = make()
+    prm = A.params(kw["T"], kw["mtry"], kw["min_node"], kw.get("max_depth", 0), 156, kw.get("bootstrap", True))
+    same_forest(fit_with(A.GROWER_LISTS, wl, prm), fit_with(A.GROWER_LEVEL, wl, prm), A.GROWER_LISTS, A.GROWER_LEVEL)
+
+
+def test_subset_fits_agree_with_lists():
+    wl, folds = synth.loko_folds()
+    folds = folds[:4]
+    off = np.zeros(len(folds) + 1, np.int64)
+    rows = []
+    for i, (train, _) in enumerate(folds):
+        rows.append(train.astype(np.int32))
+        off[i + 1] = off[i] + len(train)
+    rows = np.concatenate(rows)
+    prm = A.params(16, 10, 5)
+    out = {}
+    for g in (A.GROWER_LISTS, A.GROWER_LEVEL):
+        A.aiwcrf_set_grower(g)
+        try:
+            out[g] = A.aiwcrf_fit_subsets(prm, dev(wl.X), dev(wl.y), off, dev(rows))
+        finally:
+            A.aiwcrf_set_grower(A.GROWER_AUTO)
+    for a, b in zip(out[A.GROWER_LISTS], out[A.GROWER_LEVEL]):
+        same_forest(a, b, A.GROWER_LISTS, A.GROWER_LEVEL)
+
+
+def test_auto_takes_lists_for_many_values_and_matches_the_oracle():
+    wl = synth.small_case(15, 6000, 5)                # about 6,000 values per column
+    prm = A.params(4, 3, 3)
+    f = A.aiwcrf_fit(prm, dev(wl.X), dev(wl.y))
+    assert f.stats()["grower"] == A.GROWER_LISTS
+    ref = O.fit(wl.X, wl.y, 4, 3, 3, seed=156)
+    dec = A.decode_forest(f.serialize())
+    for k in range(4):
+        assert_tree_equal(gpu_tree(dec, k), ref.tree(k), where=f"tree {k}")
+
+
+def test_per_row_benchmark_trees_with_lists_match_the_oracle():
+    """A tree of the 111,000-row per-row workload (every row its own feature vector)."""
+    wl = synth.per_row_forest_workload()
+    f = A.aiwcrf_fit(A.params(1, 10, 5, first_tree=17), dev(wl.X), dev(wl.y))
+    assert f.stats()["grower"] == A.GROWER_LISTS
+    ref = O.fit(wl.X, wl.y, 1, 10, 5, seed=156, t0=17)
+    dec = A.decode_forest(f.serialize())
+    for k in range(1):
+        assert_tree_equal(gpu_tree(dec, k), ref.tree(k), where=f"tree {k}")

@@ -94,7 +94,8 @@ def test_plan_and_gate_layouts():
 
 def test_server_layouts_and_validation_without_gpu():
     assert C.sizeof(A.ServerParams) == 40
-    assert C.sizeof(A.ServerCounters) == 18 * 8
+    assert C.sizeof(A.ServerCounters) == 23 * 8
+    assert C.sizeof(A.BatchTrace) == 64
     assert C.sizeof(A.LoadReport) == 15 * 8
     L = _lib()
     F, N, D = 4, 10, 3
@@ -121,3 +122,12 @@ def test_server_layouts_and_validation_without_gpu():
     yb[0] = (1 << 40) + 1
     assert create(A.server_params(), y=yb) == -8
     assert L.aiwcrf_server_destroy(None) == 0
+    # the gated entry points check their arguments before touching a device
+    t = C.c_int64()
+    kf = np.zeros((F - 2, 1), np.float32)
+    assert L.aiwcrf_server_set_surrogate(None, None, None) == -1
+    assert L.aiwcrf_server_submit_gated(None, kf.ctypes.data, 1, 0, C.byref(t)) == -1
+    assert L.aiwcrf_server_wait_gated(None, 1, 0, None, None, None, None) == -1
+    rep = A.LoadReport()
+    assert L.aiwcrf_server_run_load_gated(None, kf.ctypes.data, 1, None, None, None, None, 1, 1.0, 1, 0, None, None,
+                                          None, C.byref(rep)) == -1
