@@ -468,15 +468,14 @@ struct LevelArgs {
     uint32_t *tile_splits;      // per tile of kScanTile nodes: nodes that split (zero on entry)
     const uint32_t *depth_ptr;  // when set, the depth is read here (a graph replays one level body)
     uint32_t node_cap;          // entries of the node table (bounds checks of debug builds)
-    // presorted lists (null: the big-node search builds histograms): per feature f, per tree t,
-    // lists_in[f * list_stride + t * row_cap + i] is the representative row of an entry, each
-    // node's segment in increasing rank of f; list_w / list_wy give the tree's entry of a
-    // representative row ([T][N])
+    // presorted lists (the list kernel): per feature f, per tree t, a node's segment of
+    // lists_in[f * list_stride + t * row_cap + ...] holds the positions of its entries within its
+    // segment of rows_in, in increasing rank of f; newpos[t * row_cap + start + p] receives the
+    // position in rows_out of the entry at position p when the node splits
     const uint32_t *lists_in = nullptr;
     uint32_t *lists_out = nullptr;
     int64_t list_stride = 0;
-    const uint32_t *list_w = nullptr;
-    const int64_t *list_wy = nullptr;
+    uint32_t *newpos = nullptr;
 };
 
 __device__ __forceinline__ int level_depth(const LevelArgs &a)
@@ -742,65 +741,36 @@ __global__ void __launch_bounds__(1024) rep_order_kernel(const uint32_t *__restr
     }
 }
 
-// the w and w*y of every tree's entries, by representative row
-__global__ void list_tables_kernel(const Entry *__restrict__ rows, int64_t row_cap, const NodeRec *__restrict__ root,
-                                   int64_t N, uint32_t *__restrict__ Wt, int64_t *__restrict__ WYt)
+// every tree's entry position (plus one) by representative row ([T][N], zero elsewhere)
+__global__ void list_pos_kernel(const Entry *__restrict__ rows, int64_t row_cap, const NodeRec *__restrict__ root,
+                                int64_t N, uint32_t *__restrict__ P)
 {
     const int64_t t = blockIdx.y;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)root[t].len) return;
     const Entry e = load_entry(rows + (size_t)t * (size_t)row_cap + (size_t)i);
-    const uint32_t row = AIWCRF_IDX(e.row, (uint32_t)N, kBoundRow);
-    Wt[(size_t)t * (size_t)N + row] = e.w;
-    WYt[(size_t)t * (size_t)N + row] = e.wy;
+    P[(size_t)t * (size_t)N + AIWCRF_IDX(e.row, (uint32_t)N, kBoundRow)] = (uint32_t)i + 1u;
 }
 
-// CTA (tree, feature): the tree's entries in increasing rank of the feature
+// CTA (tree, feature): the positions of the tree's entries in increasing rank of the feature
 __global__ void __launch_bounds__(1024) list_build_kernel(const uint32_t *__restrict__ ordG, uint32_t G,
-                                                          const uint32_t *__restrict__ Wt, int64_t N, int64_t row_cap,
+                                                          const uint32_t *__restrict__ P, int64_t N, int64_t row_cap,
                                                           int64_t stride, uint32_t *__restrict__ lists)
 {
     __shared__ uint32_t warp_tmp[32];
     const int64_t t = blockIdx.x;
     const uint32_t *src = ordG + (size_t)blockIdx.y * (size_t)G;
-    const uint32_t *W = Wt + (size_t)t * (size_t)N;
+    const uint32_t *Pt = P + (size_t)t * (size_t)N;
     uint32_t *dst = lists + (size_t)blockIdx.y * (size_t)stride + (size_t)t * (size_t)row_cap;
     uint32_t running = 0;
     for (uint32_t b0 = 0; b0 < G; b0 += 1024) {
         const uint32_t i = b0 + threadIdx.x;
-        const uint32_t row = i < G ? src[i] : 0u;
-        const bool keep = i < G && W[row] > 0u;
+        const uint32_t pos = i < G ? Pt[src[i]] : 0u;
         uint32_t tot;
-        const uint32_t incl = block_incl_scan(keep ? 1u : 0u, warp_tmp, tot);
-        if (keep && (int64_t)(running + incl - 1u) < row_cap) dst[running + incl - 1u] = row;
+        const uint32_t incl = block_incl_scan(pos > 0u ? 1u : 0u, warp_tmp, tot);
+        if (pos > 0u && (int64_t)(running + incl - 1u) < row_cap) dst[running + incl - 1u] = pos - 1u;
         running += tot;
     }
-}
-
-// Block inclusive scan of (w, w*y) pairs; totals in tot_w / tot_s (every thread)
-__device__ __forceinline__ void block_scan_ws(uint32_t w, long long s, uint32_t *tw, long long *ts, uint32_t &pw,
-                                              long long &ps, uint32_t &tot_w, long long &tot_s)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    uint32_t xw = w;
-    long long xs = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t a = __shfl_up_sync(kFull, xw, o);
-        const long long b = __shfl_up_sync(kFull, xs, o);
-        if (lane >= o) { xw += a; xs += b; }
-    }
-    if (lane == 31) { tw[warp] = xw; ts[warp] = xs; }
-    __syncthreads();
-    uint32_t ow = 0;
-    long long os = 0;
-    for (int k = 0; k < warp; ++k) { ow += tw[k]; os += ts[k]; }
-    tot_w = 0;
-    tot_s = 0;
-    for (int k = 0; k < nw; ++k) { tot_w += tw[k]; tot_s += ts[k]; }
-    __syncthreads();
-    pw = xw + ow;
-    ps = xs + os;
 }
 
 constexpr int kBigThreads = 128;
@@ -817,66 +787,122 @@ inline int big_bin_cap(int mtry, int F, uint32_t max_card)
     return (int)std::min<int64_t>(4096, (need + 31) & ~(int64_t)31);
 }
 
-// A big node's split search from the presorted lists: per tried feature, a block scan of
-// (w, w*y) along the node's segment of the feature's list gives the left sums of every
-// threshold; a candidate sits at the last entry of each run of equal ranks but the last run.
+// A big node's split search from the presorted lists. The warps take the tried features in
+// turn; a warp scans (w, w*y) along the node's segment of its feature's list (entry positions,
+// read from the node's own entry segment), 32 entries a step and kListIlp steps' loads in
+// flight, so the left sums of every threshold come without block barriers. A candidate sits at
+// the last entry of each run of equal ranks but the last run.
+constexpr int kListIlp = 4;
+
 template <typename RT>
 __device__ __forceinline__ Cand list_search(const LevelArgs &a, const NodeRec &nd, const int *feats, int m)
 {
-    __shared__ uint32_t tw[kBigWarps];
-    __shared__ long long ts[kBigWarps];
     const RT *__restrict__ Rr = static_cast<const RT *>(a.Rr);
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const size_t tb = (size_t)nd.tree * (size_t)a.row_cap + nd.start;
-    const uint32_t *__restrict__ Wt = a.list_w + (size_t)nd.tree * (size_t)a.N;
-    const int64_t *__restrict__ WYt = a.list_wy + (size_t)nd.tree * (size_t)a.N;
+    const Entry *__restrict__ rin = a.rows_in + tb;
     Cand best = cand_none();
-    for (int k = 0; k < m; ++k) {
+    for (int k = warp; k < m; k += kBigWarps) {
         const int f = feats[k];
         const uint32_t *__restrict__ L = a.lists_in + (size_t)f * (size_t)a.list_stride + tb;
-        uint32_t cw = 0u;                       // sums of the earlier chunks (block-uniform)
+        uint32_t cw = 0u;                       // sums of the earlier steps (warp-uniform)
         long long cs = 0ll;
-        for (uint32_t b0 = 0; b0 < nd.len; b0 += kBigThreads) {
-            const uint32_t i = b0 + (uint32_t)tid;
-            const bool valid = i < nd.len;
-            uint32_t w = 0u, rank = 0u;
-            long long wy = 0ll;
-            if (valid) {
-                const uint32_t row = AIWCRF_IDX(__ldg(&L[i]), (uint32_t)a.N, kBoundRow);
-                w = __ldg(&Wt[row]);
-                wy = (long long)__ldg(&WYt[row]);
-                rank = (uint32_t)__ldg(&Rr[(size_t)row * (size_t)a.F + f]);
-            }
-            uint32_t nrank = __shfl_down_sync(kFull, rank, 1);
-            if (lane == 31 && i + 1u < nd.len) {
-                const uint32_t row2 = AIWCRF_IDX(__ldg(&L[i + 1u]), (uint32_t)a.N, kBoundRow);
-                nrank = (uint32_t)__ldg(&Rr[(size_t)row2 * (size_t)a.F + f]);
-            }
-            uint32_t pw, tot_w;
-            long long ps, tot_s;
-            block_scan_ws(w, wy, tw, ts, pw, ps, tot_w, tot_s);
-            if (valid && i + 1u < nd.len && nrank != rank) {     // the last entry of a rank's run
-                const uint32_t nL = cw + pw;
-                const long long SL = cs + ps;
-                const i128_t delta = cand_delta(nd.n, nd.S, nL, SL);
-                if (delta != 0) {
-                    Cand cd;
-                    cd.h = cand_h(delta, nd.n, nL);
-                    cd.f = f; cd.r = rank; cd.nL = nL; cd.SL = SL;
-                    if (cand_better(cd, best, nd.n, nd.S)) best = cd;
+        for (uint32_t b0 = 0; b0 < nd.len; b0 += 32u * kListIlp) {
+            uint32_t w[kListIlp], rank[kListIlp], nrank[kListIlp];
+            long long wy[kListIlp];
+#pragma unroll
+            for (int u = 0; u < kListIlp; ++u) {
+                const uint32_t i = b0 + 32u * u + (uint32_t)lane;
+                w[u] = 0u; wy[u] = 0ll; rank[u] = 0u; nrank[u] = 0u;
+                if (i < nd.len) {
+                    const Entry e = load_entry(rin + AIWCRF_IDX(__ldg(&L[i]), nd.len, kBoundOut));
+                    w[u] = e.w;
+                    wy[u] = (long long)e.wy;
+                    rank[u] = (uint32_t)__ldg(&Rr[(size_t)AIWCRF_IDX(e.row, (uint32_t)a.N, kBoundRow) * (size_t)a.F + f]);
+                }
+                // the rank after the warp's last entry of this step
+                if (lane == 31 && i + 1u < nd.len) {
+                    const uint32_t row2 = __ldg(&rin[AIWCRF_IDX(__ldg(&L[i + 1u]), nd.len, kBoundOut)].row);
+                    nrank[u] = (uint32_t)__ldg(&Rr[(size_t)AIWCRF_IDX(row2, (uint32_t)a.N, kBoundRow) * (size_t)a.F + f]);
                 }
             }
-            cw += tot_w;
-            cs += tot_s;
+#pragma unroll
+            for (int u = 0; u < kListIlp; ++u) {
+                const uint32_t i = b0 + 32u * u + (uint32_t)lane;
+                const uint32_t nr_lane = __shfl_down_sync(kFull, rank[u], 1);
+                const uint32_t nr = lane == 31 ? nrank[u] : nr_lane;
+                uint32_t pw = w[u];
+                long long ps = wy[u];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t tw = __shfl_up_sync(kFull, pw, o);
+                    const long long tsum = __shfl_up_sync(kFull, ps, o);
+                    if (lane >= o) { pw += tw; ps += tsum; }
+                }
+                if (i + 1u < nd.len && nr != rank[u]) {        // the last entry of a rank's run
+                    const uint32_t nL = cw + pw;
+                    const long long SL = cs + ps;
+                    const i128_t delta = cand_delta(nd.n, nd.S, nL, SL);
+                    if (delta != 0) {
+                        Cand cd;
+                        cd.h = cand_h(delta, nd.n, nL);
+                        cd.f = f; cd.r = rank[u]; cd.nL = nL; cd.SL = SL;
+                        if (cand_better(cd, best, nd.n, nd.S)) best = cd;
+                    }
+                }
+                cw += __shfl_sync(kFull, pw, 31);
+                cs += __shfl_sync(kFull, ps, 31);
+            }
         }
     }
     return best;
 }
 
+// Stable partition of a big node's segment of every feature's list by the split (the warps take
+// the features in turn; ballots give each entry its place, so the children's segments stay in
+// rank order). An entry's new position, written by the entry partition, also says its side.
+__device__ __forceinline__ void list_partition(const LevelArgs &a, const NodeRec &nd, uint32_t lenL)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
+    const size_t tb = (size_t)nd.tree * (size_t)a.row_cap + nd.start;
+    const uint32_t *__restrict__ np = a.newpos + tb;
+    for (int f = warp; f < a.F; f += kBigWarps) {
+        const uint32_t *__restrict__ Li = a.lists_in + (size_t)f * (size_t)a.list_stride + tb;
+        uint32_t *__restrict__ Lo = a.lists_out + (size_t)f * (size_t)a.list_stride + tb;
+        uint32_t rl = 0u, rr = 0u;
+        for (uint32_t b0 = 0; b0 < nd.len; b0 += 32u * kListIlp) {
+            uint32_t d[kListIlp];
+            bool left[kListIlp];
+#pragma unroll
+            for (int u = 0; u < kListIlp; ++u) {
+                const uint32_t i = b0 + 32u * u + (uint32_t)lane;
+                // the entry's position in the children's segments (written by this CTA: plain loads)
+                d[u] = i < nd.len ? AIWCRF_IDX(np[AIWCRF_IDX(__ldg(&Li[i]), nd.len, kBoundOut)], nd.len, kBoundOut) : 0u;
+                left[u] = i < nd.len && d[u] < lenL;
+            }
+#pragma unroll
+            for (int u = 0; u < kListIlp; ++u) {
+                const uint32_t s0 = b0 + 32u * u;
+                if (s0 >= nd.len) break;                            // warp-uniform
+                const uint32_t i = s0 + (uint32_t)lane;
+                const uint32_t bal = __ballot_sync(kFull, left[u]);
+                const uint32_t before = (uint32_t)__popc(bal & lt);
+                if (i < nd.len)          // positions within the child's own segment
+                    Lo[AIWCRF_IDX(left[u] ? rl + before : lenL + rr + ((uint32_t)lane - before), nd.len, kBoundOut)] =
+                        left[u] ? d[u] : d[u] - lenL;
+                const uint32_t nl = (uint32_t)__popc(bal);
+                rl += nl;
+                rr += min(32u, nd.len - s0) - nl;
+            }
+        }
+    }
+}
+
 // One CTA per node with more than 32 entries. Shared bins, bin_cap of them, hold per rank
 // of every tried feature: sum w (u32) and sum w*y as an exact (low u32, high i32) pair. All
 // updates are native 32-bit shared atomics; a wrap of the low word carries into the high word.
-template <typename RT>
+template <typename RT, bool LISTS>
 __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
 {
     const RT *__restrict__ Rr = static_cast<const RT *>(a.Rr);
@@ -941,7 +967,7 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
     const uint32_t total_bins = fbase[m];
     Cand best = cand_none();
 
-    if (a.lists_in) best = list_search<RT>(a, nd, feats, m);
+    if constexpr (LISTS) best = list_search<RT>(a, nd, feats, m);
     else for (uint32_t g0 = 0; g0 < total_bins; g0 += (uint32_t)bin_cap) {
         const uint32_t g1 = min(total_bins, g0 + (uint32_t)bin_cap);
         const int nb = (int)(g1 - g0);
@@ -1131,33 +1157,16 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
         const uint32_t incl = block_incl_scan(left ? 1u : 0u, warp_tmp, tot);
         if (valid) {
             const uint32_t before_l = incl - (left ? 1u : 0u);
-            store_entry(&rout[AIWCRF_IDX(left ? run_l + before_l : lenL + run_r + ((uint32_t)tid - before_l), nd.len, kBoundOut)], e);
+            const uint32_t dst = AIWCRF_IDX(left ? run_l + before_l : lenL + run_r + ((uint32_t)tid - before_l), nd.len, kBoundOut);
+            store_entry(&rout[dst], e);
+            if constexpr (LISTS) a.newpos[tb + i] = dst;
         }
         run_l += tot;
         run_r += min((uint32_t)kBigThreads, nd.len - b0) - tot;
     }
-    if (a.lists_in) {
-        // every feature's list, partitioned stably the same way: the children's segments stay
-        // in rank order
-        for (int f = 0; f < a.F; ++f) {
-            const uint32_t *Li = a.lists_in + (size_t)f * (size_t)a.list_stride + tb;
-            uint32_t *Lo = a.lists_out + (size_t)f * (size_t)a.list_stride + tb;
-            uint32_t rl = 0u, rr = 0u;
-            for (uint32_t b0 = 0; b0 < nd.len; b0 += kBigThreads) {
-                const uint32_t i = b0 + tid;
-                const bool valid = i < nd.len;
-                const uint32_t row = valid ? AIWCRF_IDX(__ldg(&Li[i]), (uint32_t)a.N, kBoundRow) : 0u;
-                const bool left = valid && (uint32_t)__ldg(&Rr[(size_t)row * (size_t)a.F + win.f]) <= win.r;
-                uint32_t tot;
-                const uint32_t incl = block_incl_scan(left ? 1u : 0u, warp_tmp, tot);
-                if (valid) {
-                    const uint32_t before_l = incl - (left ? 1u : 0u);
-                    Lo[AIWCRF_IDX(left ? rl + before_l : lenL + rr + ((uint32_t)tid - before_l), nd.len, kBoundOut)] = row;
-                }
-                rl += tot;
-                rr += min((uint32_t)kBigThreads, nd.len - b0) - tot;
-            }
-        }
+    if constexpr (LISTS) {
+        __syncthreads();                        // every entry's new position is written
+        list_partition(a, nd, lenL);
     }
     if (tid == 0) {
         SplitRes sr;
@@ -1176,7 +1185,20 @@ __global__ void __launch_bounds__(kBigThreads, kBigCtasPerSm) level_big_kernel(L
     const uint32_t list_n = *a.list_n;
     for (uint32_t k = blockIdx.x; k < list_n; k += gridDim.x) {
         __syncthreads();                 // the previous node's shared state is no longer read
-        big_node<RT>(a, bin_cap, a.list[k]);
+        big_node<RT, false>(a, bin_cap, a.list[k]);
+    }
+}
+
+// the same with the presorted-list search (a.lists_in set): more registers per thread for the
+// loads the warps keep in flight
+constexpr int kListCtasPerSm = 4;
+template <typename RT>
+__global__ void __launch_bounds__(kBigThreads, kListCtasPerSm) level_list_kernel(LevelArgs a)
+{
+    const uint32_t list_n = *a.list_n;
+    for (uint32_t k = blockIdx.x; k < list_n; k += gridDim.x) {
+        __syncthreads();
+        big_node<RT, true>(a, 0, a.list[k]);
     }
 }
 
@@ -2396,8 +2418,6 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     const size_t budget = (size_t)4 << 30;                      // level-table budget per fit
     int dev_sms = 0;
     AIWCRF_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, device));
-    // CTAs per SM of the grid-stride level, scan and finalize kernels (a background fit takes fewer)
-    const int64_t cps = p.ctas_per_sm > 0 ? p.ctas_per_sm : 3;
 
     size_t node_cap = 0, packed_cap = 0;
     NodeRec *nodes_cur = nullptr, *nodes_nxt = nullptr;
@@ -2520,23 +2540,22 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
 
     // presorted lists of every tree: its entries by representative row, then per feature in rank order
     const int64_t list_stride = T * row_cap;
-    uint32_t *lists_a = nullptr, *lists_b = nullptr, *list_w = nullptr;
-    int64_t *list_wy = nullptr;
+    uint32_t *lists_a = nullptr, *lists_b = nullptr, *newpos = nullptr;
     if (use_lists) {
-        list_w = sc.get<uint32_t>((size_t)T * (size_t)N, &rc); if (rc) return rc;
-        list_wy = sc.get<int64_t>((size_t)T * (size_t)N, &rc); if (rc) return rc;
+        uint32_t *P = sc.get<uint32_t>((size_t)T * (size_t)N, &rc); if (rc) return rc;
         lists_a = sc.get<uint32_t>((size_t)F * (size_t)list_stride, &rc); if (rc) return rc;
         lists_b = sc.get<uint32_t>((size_t)F * (size_t)list_stride, &rc); if (rc) return rc;
+        newpos = sc.get<uint32_t>((size_t)list_stride, &rc); if (rc) return rc;
         prof_begin(s, kProfBoot);
-        AIWCRF_CUDA(cudaMemsetAsync(list_w, 0, sizeof(uint32_t) * (size_t)T * (size_t)N, s));
-        list_tables_kernel<<<dim3((unsigned)((row_cap + 255) / 256), (unsigned)T), 256, 0, s>>>(rows_a, row_cap, nodes_cur,
-                                                                                              N, list_w, list_wy);
-        AIWCRF_LAUNCH_CHECK("list_tables_kernel");
-        list_build_kernel<<<dim3((unsigned)T, (unsigned)F), 1024, 0, s>>>(d_ordG, n_groups, list_w, N, row_cap,
-                                                                         list_stride, lists_a);
+        AIWCRF_CUDA(cudaMemsetAsync(P, 0, sizeof(uint32_t) * (size_t)T * (size_t)N, s));
+        list_pos_kernel<<<dim3((unsigned)((row_cap + 255) / 256), (unsigned)T), 256, 0, s>>>(rows_a, row_cap, nodes_cur, N, P);
+        AIWCRF_LAUNCH_CHECK("list_pos_kernel");
+        list_build_kernel<<<dim3((unsigned)T, (unsigned)F), 1024, 0, s>>>(d_ordG, n_groups, P, N, row_cap, list_stride,
+                                                                         lists_a);
         AIWCRF_LAUNCH_CHECK("list_build_kernel");
         prof_end(s, kProfBoot);
         sc.drop(d_ordG);
+        sc.drop(P);
     }
 
     if (use_tree) {
@@ -2605,7 +2624,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
 
     // bins: the tried features' value counts side by side (one pass over the entries)
     const int bin_cap = big_bin_cap(p.mtry, F, max_card);
-    const int big_smem = use_lists ? 0 : bin_cap * 14;       // the list search needs no bins
+    const int big_smem = bin_cap * 14;
     {
         cudaError_t e_ = cudaSuccess;
         AIWCRF_BY_RANK(rank_bytes, e_ = cudaFuncSetAttribute(level_big_kernel<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2619,7 +2638,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     la.max_depth = p.max_depth; la.seed_lo = (uint32_t)p.seed; la.seed_hi = (uint32_t)(p.seed >> 32);
     la.depth_ptr = nullptr;
     la.node_cap = 0;
-    la.list_stride = list_stride; la.list_w = list_w; la.list_wy = list_wy;
+    la.list_stride = list_stride; la.newpos = newpos;
 
     // The two level kernels of a depth are independent (disjoint nodes, disjoint entry
     // segments): a foreground fit runs the small-node kernel on a second stream of the same
@@ -2677,8 +2696,15 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
                 const int64_t cps_big = p.ctas_per_sm > 0 ? p.ctas_per_sm : kBigCtasPerSm;
                 const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(Cb, cps_big * dev_sms));
                 prof_begin(s, kProfLevelBig);
-                AIWCRF_BY_RANK(rank_bytes, level_big_kernel<RT><<<grid, kBigThreads, big_smem, s>>>(la, bin_cap))
-                AIWCRF_LAUNCH_CHECK("level_big_kernel");
+                if (use_lists) {
+                    const int64_t cps_list = p.ctas_per_sm > 0 ? p.ctas_per_sm : kListCtasPerSm;
+                    const unsigned lgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(Cb, cps_list * dev_sms));
+                    AIWCRF_BY_RANK(rank_bytes, level_list_kernel<RT><<<lgrid, kBigThreads, 0, s>>>(la))
+                    AIWCRF_LAUNCH_CHECK("level_list_kernel");
+                } else {
+                    AIWCRF_BY_RANK(rank_bytes, level_big_kernel<RT><<<grid, kBigThreads, big_smem, s>>>(la, bin_cap))
+                    AIWCRF_LAUNCH_CHECK("level_big_kernel");
+                }
                 prof_end(s, kProfLevelBig);
             }
             {
