@@ -794,7 +794,7 @@ inline int big_bin_cap(int mtry, int F, uint32_t max_card)
 // the last entry of each run of equal ranks but the last run.
 constexpr int kListIlp = 4;
 
-template <typename RT>
+template <typename RT, int NW>
 __device__ __forceinline__ Cand list_search(const LevelArgs &a, const NodeRec &nd, const int *feats, int m)
 {
     const RT *__restrict__ Rr = static_cast<const RT *>(a.Rr);
@@ -802,7 +802,7 @@ __device__ __forceinline__ Cand list_search(const LevelArgs &a, const NodeRec &n
     const size_t tb = (size_t)nd.tree * (size_t)a.row_cap + nd.start;
     const Entry *__restrict__ rin = a.rows_in + tb;
     Cand best = cand_none();
-    for (int k = warp; k < m; k += kBigWarps) {
+    for (int k = warp; k < m; k += NW) {
         const int f = feats[k];
         const uint32_t *__restrict__ L = a.lists_in + (size_t)f * (size_t)a.list_stride + tb;
         uint32_t cw = 0u;                       // sums of the earlier steps (warp-uniform)
@@ -858,51 +858,71 @@ __device__ __forceinline__ Cand list_search(const LevelArgs &a, const NodeRec &n
     return best;
 }
 
-// Stable partition of a big node's segment of every feature's list by the split (the warps take
-// the features in turn; ballots give each entry its place, so the children's segments stay in
-// rank order). An entry's new position, written by the entry partition, also says its side.
-__device__ __forceinline__ void list_partition(const LevelArgs &a, const NodeRec &nd, uint32_t lenL)
+// Stable partition of a split big node's segment of one feature's list, by one warp: ballots
+// give each entry its place, so the children's segments stay in rank order. An entry's new
+// position, written by the entry partition, also says its side; the list receives the positions
+// within the child's own segment.
+constexpr int kPartIlp = 8;
+
+__device__ __forceinline__ void list_partition_feature(const LevelArgs &a, const NodeRec &nd, int f, uint32_t lenL)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
     const size_t tb = (size_t)nd.tree * (size_t)a.row_cap + nd.start;
     const uint32_t *__restrict__ np = a.newpos + tb;
-    for (int f = warp; f < a.F; f += kBigWarps) {
-        const uint32_t *__restrict__ Li = a.lists_in + (size_t)f * (size_t)a.list_stride + tb;
-        uint32_t *__restrict__ Lo = a.lists_out + (size_t)f * (size_t)a.list_stride + tb;
-        uint32_t rl = 0u, rr = 0u;
-        for (uint32_t b0 = 0; b0 < nd.len; b0 += 32u * kListIlp) {
-            uint32_t d[kListIlp];
-            bool left[kListIlp];
+    const uint32_t *__restrict__ Li = a.lists_in + (size_t)f * (size_t)a.list_stride + tb;
+    uint32_t *__restrict__ Lo = a.lists_out + (size_t)f * (size_t)a.list_stride + tb;
+    uint32_t rl = 0u, rr = 0u;
+    for (uint32_t b0 = 0; b0 < nd.len; b0 += 32u * kPartIlp) {
+        uint32_t p[kPartIlp], d[kPartIlp];
 #pragma unroll
-            for (int u = 0; u < kListIlp; ++u) {
-                const uint32_t i = b0 + 32u * u + (uint32_t)lane;
-                // the entry's position in the children's segments (written by this CTA: plain loads)
-                d[u] = i < nd.len ? AIWCRF_IDX(np[AIWCRF_IDX(__ldg(&Li[i]), nd.len, kBoundOut)], nd.len, kBoundOut) : 0u;
-                left[u] = i < nd.len && d[u] < lenL;
-            }
-#pragma unroll
-            for (int u = 0; u < kListIlp; ++u) {
-                const uint32_t s0 = b0 + 32u * u;
-                if (s0 >= nd.len) break;                            // warp-uniform
-                const uint32_t i = s0 + (uint32_t)lane;
-                const uint32_t bal = __ballot_sync(kFull, left[u]);
-                const uint32_t before = (uint32_t)__popc(bal & lt);
-                if (i < nd.len)          // positions within the child's own segment
-                    Lo[AIWCRF_IDX(left[u] ? rl + before : lenL + rr + ((uint32_t)lane - before), nd.len, kBoundOut)] =
-                        left[u] ? d[u] : d[u] - lenL;
-                const uint32_t nl = (uint32_t)__popc(bal);
-                rl += nl;
-                rr += min(32u, nd.len - s0) - nl;
-            }
+        for (int u = 0; u < kPartIlp; ++u) {
+            const uint32_t i = b0 + 32u * u + (uint32_t)lane;
+            p[u] = i < nd.len ? AIWCRF_IDX(__ldg(&Li[i]), nd.len, kBoundOut) : 0u;
         }
+#pragma unroll
+        for (int u = 0; u < kPartIlp; ++u) {
+            const uint32_t i = b0 + 32u * u + (uint32_t)lane;
+            d[u] = i < nd.len ? AIWCRF_IDX(__ldg(&np[p[u]]), nd.len, kBoundOut) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kPartIlp; ++u) {
+            const uint32_t s0 = b0 + 32u * u;
+            if (s0 >= nd.len) break;                                // warp-uniform
+            const uint32_t i = s0 + (uint32_t)lane;
+            const bool left = i < nd.len && d[u] < lenL;
+            const uint32_t bal = __ballot_sync(kFull, left);
+            const uint32_t before = (uint32_t)__popc(bal & lt);
+            if (i < nd.len)
+                Lo[AIWCRF_IDX(left ? rl + before : lenL + rr + ((uint32_t)lane - before), nd.len, kBoundOut)] =
+                    left ? d[u] : d[u] - lenL;
+            const uint32_t nl = (uint32_t)__popc(bal);
+            rl += nl;
+            rr += min(32u, nd.len - s0) - nl;
+        }
+    }
+}
+
+// After the list kernel of a depth: one warp per (split big node, feature), node-major, so the
+// warps of a node share its new-position lines.
+constexpr int kPartThreads = 256;
+constexpr int kPartCtasPerSm = 4;
+__global__ void __launch_bounds__(kPartThreads, kPartCtasPerSm) list_partition_kernel(LevelArgs a)
+{
+    const uint64_t items = (uint64_t)*a.list_n * (uint64_t)a.F;
+    const uint64_t nw = ((uint64_t)gridDim.x * kPartThreads) >> 5;
+    for (uint64_t it = ((uint64_t)blockIdx.x * kPartThreads + threadIdx.x) >> 5; it < items; it += nw) {
+        const int j = AIWCRF_IDX(a.list[it / (uint64_t)a.F], a.node_cap, kBoundNode);
+        const SplitRes sr = a.res[j];
+        if (sr.feature < 0) continue;                                // warp-uniform: a leaf
+        list_partition_feature(a, a.nodes[j], (int)(it % (uint64_t)a.F), sr.lenL);
     }
 }
 
 // One CTA per node with more than 32 entries. Shared bins, bin_cap of them, hold per rank
 // of every tried feature: sum w (u32) and sum w*y as an exact (low u32, high i32) pair. All
 // updates are native 32-bit shared atomics; a wrap of the low word carries into the high word.
-template <typename RT, bool LISTS>
+template <typename RT, bool LISTS, int NT = kBigThreads>
 __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
 {
     const RT *__restrict__ Rr = static_cast<const RT *>(a.Rr);
@@ -915,10 +935,10 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
     __shared__ uint32_t fbase[AIWCRF_MAX_FEATURES + 1];
     __shared__ uint32_t carry_w[AIWCRF_MAX_FEATURES];
     __shared__ long long carry_s[AIWCRF_MAX_FEATURES];
-    __shared__ uint32_t tot_w[kBigThreads];
-    __shared__ long long tot_s[kBigThreads];
+    __shared__ uint32_t tot_w[NT];
+    __shared__ long long tot_s[NT];
     __shared__ int m_sh;
-    __shared__ Cand wbest[kBigWarps];
+    __shared__ Cand wbest[(NT / 32)];
     __shared__ Cand winner;
     __shared__ uint32_t warp_tmp[32];
 
@@ -967,11 +987,11 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
     const uint32_t total_bins = fbase[m];
     Cand best = cand_none();
 
-    if constexpr (LISTS) best = list_search<RT>(a, nd, feats, m);
+    if constexpr (LISTS) best = list_search<RT, NT / 32>(a, nd, feats, m);
     else for (uint32_t g0 = 0; g0 < total_bins; g0 += (uint32_t)bin_cap) {
         const uint32_t g1 = min(total_bins, g0 + (uint32_t)bin_cap);
         const int nb = (int)(g1 - g0);
-        for (int b = tid; b < nb; b += kBigThreads) { bw[b] = 0u; blo[b] = 0u; bhi[b] = 0; }
+        for (int b = tid; b < nb; b += NT) { bw[b] = 0u; blo[b] = 0u; bhi[b] = 0; }
         int k_lo = 0;
         while (fbase[k_lo + 1] <= g0) ++k_lo;
         int k_hi = k_lo;
@@ -980,12 +1000,12 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
 
         // histogram: per pass a thread loads kRowsPerIter entries and gathers the tried
         // features' ranks of their rows, then adds them to the shared bins
-        for (uint32_t base = 0; base < nd.len; base += kBigThreads * kRowsPerIter) {
+        for (uint32_t base = 0; base < nd.len; base += NT * kRowsPerIter) {
             uint32_t rowv[kRowsPerIter], wv[kRowsPerIter], lov[kRowsPerIter];
             int32_t hiv[kRowsPerIter];
 #pragma unroll
             for (int u = 0; u < kRowsPerIter; ++u) {
-                const uint32_t i = base + (uint32_t)(u * kBigThreads + tid);
+                const uint32_t i = base + (uint32_t)(u * NT + tid);
                 Entry e;
                 e.row = 0u; e.w = 0u; e.wy = 0;                           // w = 0: no entry
                 if (i < nd.len) e = load_entry(rin + i);
@@ -1027,7 +1047,7 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
         __syncthreads();
 
         // block inclusive prefix over the group's bins (unsegmented), in place
-        const int per = (nb + kBigThreads - 1) / kBigThreads;
+        const int per = (nb + NT - 1) / NT;
         const int lo = min(nb, tid * per), hi = min(nb, lo + per);
         uint32_t lw = 0;
         long long ls = 0;
@@ -1039,7 +1059,7 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
         tot_s[tid] = ls;
         __syncthreads();
         if (warp == 0) {            // exclusive scan of the thread totals by one warp
-            constexpr int kPer = kBigThreads / 32;
+            constexpr int kPer = NT / 32;
             uint32_t w8[kPer];
             long long s8[kPer];
             uint32_t ws = 0;
@@ -1123,7 +1143,7 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
     if (lane == 0) wbest[warp] = best;
     __syncthreads();
     if (warp == 0) {
-        Cand c = lane < kBigWarps ? wbest[lane] : cand_none();
+        Cand c = lane < (NT / 32) ? wbest[lane] : cand_none();
         c = warp_best(c, nd.n, nd.S);
         if (lane == 0) winner = c;
     }
@@ -1137,7 +1157,7 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
     // a5: stable partition of the node's entries into [left | right] at the same offsets; a
     // first pass counts the entries that go left
     uint32_t cnt = 0;
-    for (uint32_t i = tid; i < nd.len; i += kBigThreads) {
+    for (uint32_t i = tid; i < nd.len; i += NT) {
         const uint32_t row = AIWCRF_IDX(__ldg(&rin[i].row), (uint32_t)a.N, kBoundRow);
         cnt += (uint32_t)__ldg(&Rr[(size_t)row * (size_t)a.F + win.f]) <= win.r ? 1u : 0u;
     }
@@ -1145,7 +1165,7 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
     block_incl_scan(cnt, warp_tmp, lenL);
     uint32_t run_l = 0u, run_r = 0u;           // block-uniform running counts
     Entry *rout = a.rows_out + tb;
-    for (uint32_t b0 = 0; b0 < nd.len; b0 += kBigThreads) {
+    for (uint32_t b0 = 0; b0 < nd.len; b0 += NT) {
         const uint32_t i = b0 + tid;
         const bool valid = i < nd.len;
         Entry e;
@@ -1162,12 +1182,9 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
             if constexpr (LISTS) a.newpos[tb + i] = dst;
         }
         run_l += tot;
-        run_r += min((uint32_t)kBigThreads, nd.len - b0) - tot;
+        run_r += min((uint32_t)NT, nd.len - b0) - tot;
     }
-    if constexpr (LISTS) {
-        __syncthreads();                        // every entry's new position is written
-        list_partition(a, nd, lenL);
-    }
+
     if (tid == 0) {
         SplitRes sr;
         sr.feature = win.f; sr.rank = win.r;
@@ -1189,16 +1206,21 @@ __global__ void __launch_bounds__(kBigThreads, kBigCtasPerSm) level_big_kernel(L
     }
 }
 
-// the same with the presorted-list search (a.lists_in set): more registers per thread for the
-// loads the warps keep in flight
-constexpr int kListCtasPerSm = 4;
+// the same with the presorted-list search (a.lists_in set): wider CTAs (a node's lists are
+// shared among more warps: the top depths hold few, long nodes) with 128 registers per thread
+// for the loads the warps keep in flight
+#ifndef AIWCRF_LIST_THREADS
+#define AIWCRF_LIST_THREADS 128
+#endif
+constexpr int kListThreads = AIWCRF_LIST_THREADS;
+constexpr int kListCtasPerSm = 65536 / (kListThreads * 128);
 template <typename RT>
-__global__ void __launch_bounds__(kBigThreads, kListCtasPerSm) level_list_kernel(LevelArgs a)
+__global__ void __launch_bounds__(kListThreads, kListCtasPerSm) level_list_kernel(LevelArgs a)
 {
     const uint32_t list_n = *a.list_n;
     for (uint32_t k = blockIdx.x; k < list_n; k += gridDim.x) {
         __syncthreads();
-        big_node<RT, true>(a, 0, a.list[k]);
+        big_node<RT, true, kListThreads>(a, 0, a.list[k]);
     }
 }
 
@@ -2699,8 +2721,13 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
                 if (use_lists) {
                     const int64_t cps_list = p.ctas_per_sm > 0 ? p.ctas_per_sm : kListCtasPerSm;
                     const unsigned lgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(Cb, cps_list * dev_sms));
-                    AIWCRF_BY_RANK(rank_bytes, level_list_kernel<RT><<<lgrid, kBigThreads, 0, s>>>(la))
+                    AIWCRF_BY_RANK(rank_bytes, level_list_kernel<RT><<<lgrid, kListThreads, 0, s>>>(la))
                     AIWCRF_LAUNCH_CHECK("level_list_kernel");
+                    const int64_t cps_part = p.ctas_per_sm > 0 ? p.ctas_per_sm : kPartCtasPerSm;
+                    const unsigned pgrid = (unsigned)std::max<int64_t>(
+                        1, std::min<int64_t>((Cb * F + kPartThreads / 32 - 1) / (kPartThreads / 32), cps_part * dev_sms));
+                    list_partition_kernel<<<pgrid, kPartThreads, 0, s>>>(la);
+                    AIWCRF_LAUNCH_CHECK("list_partition_kernel");
                 } else {
                     AIWCRF_BY_RANK(rank_bytes, level_big_kernel<RT><<<grid, kBigThreads, big_smem, s>>>(la, bin_cap))
                     AIWCRF_LAUNCH_CHECK("level_big_kernel");
