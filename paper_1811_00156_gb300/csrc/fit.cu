@@ -1254,6 +1254,9 @@ __global__ void __launch_bounds__(kListThreads, kListCtasPerSm) level_list_kerne
 #ifndef AIWCRF_TREE_PREFETCH
 #define AIWCRF_TREE_PREFETCH 1         // small-node passes whose ranks are loaded together
 #endif
+#ifndef AIWCRF_TREE_DYN
+#define AIWCRF_TREE_DYN 1              // 1: phase-A items handed out by a shared counter
+#endif
 constexpr int kTreeThreads = AIWCRF_TREE_THREADS;
 constexpr int kTreeWarps = kTreeThreads / 32;
 constexpr int kTreeCtasPerSm = 4;      // resident CTAs per SM the tree kernel is compiled for
@@ -1646,6 +1649,7 @@ __global__ void __launch_bounds__(kTreeThreads, kTreeCtasPerSm) tree_grow_kernel
     __shared__ uint32_t warp_tmp[32];
     __shared__ unsigned long long red[6][kTreeWarps];
     __shared__ uint32_t s_nb[2];
+    __shared__ uint32_t s_next;                                 // the next phase-A item to hand out
     const TreeSmem sm = tree_smem(tree_sm, a);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     TNode *const nodes0 = a.nodes + (size_t)blockIdx.x * 2 * (size_t)a.ecap;
@@ -1673,6 +1677,7 @@ __global__ void __launch_bounds__(kTreeThreads, kTreeCtasPerSm) tree_grow_kernel
             const bool big = tnode_big(a, r, 0u);
             s_nb[0] = big ? 1u : 0u;
             sm.big[0][0] = 0;
+            s_next = kTreeWarps;
         }
         const uint32_t tg = a.tree_rng[t];
         uint64_t *onodes = a.out_nodes + (size_t)t * (size_t)a.node_cap;
@@ -1697,9 +1702,10 @@ __global__ void __launch_bounds__(kTreeThreads, kTreeCtasPerSm) tree_grow_kernel
                 }
                 __syncthreads();
             }
-            // A: big-node feature items first (they are the long ones), then the small nodes
+            // A: big-node feature items first (they are the long ones), then the small nodes; a
+            // warp that finishes an item takes the next one not yet handed out
             const uint32_t items = nb * (uint32_t)m + C;
-            for (uint32_t j = (uint32_t)warp; j < items; j += kTreeWarps) {
+            for (uint32_t j = (uint32_t)warp; j < items;) {
                 if (j < nb * (uint32_t)m) {
                     const uint32_t bi = j / (uint32_t)m, k = j - bi * (uint32_t)m;
                     const TNode nd = cn[AIWCRF_IDX(big[bi], a.ecap, kBoundNode)];
@@ -1707,9 +1713,15 @@ __global__ void __launch_bounds__(kTreeThreads, kTreeCtasPerSm) tree_grow_kernel
                 } else {
                     const uint32_t i = j - nb * (uint32_t)m;
                     const TNode nd = cn[i];
-                    if (tnode_big(a, nd, depth)) continue;
-                    tree_small_node(a, sm, ix, ox, nd, tg, depth, &res[i], lane);
+                    if (!tnode_big(a, nd, depth)) tree_small_node(a, sm, ix, ox, nd, tg, depth, &res[i], lane);
                 }
+#if AIWCRF_TREE_DYN
+                uint32_t jn = 0u;
+                if (lane == 0) jn = atomicAdd(&s_next, 1u);
+                j = __shfl_sync(kFull, jn, 0);
+#else
+                j += kTreeWarps;
+#endif
             }
             __syncthreads();
             // B: big nodes' decisions and partitions
@@ -1767,7 +1779,7 @@ __global__ void __launch_bounds__(kTreeThreads, kTreeCtasPerSm) tree_grow_kernel
                 run_split += tot;
                 run_big += totb;
             }
-            if (tid == 0) s_nb[p ^ 1] = run_big;
+            if (tid == 0) { s_nb[p ^ 1] = run_big; s_next = kTreeWarps; }
             base += C;
             C = 2u * run_split;
             ++depth;
