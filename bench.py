@@ -508,7 +508,7 @@ def per_row_report(A, dev, n_trees: int = T_TREES, steps: int = 1):
     f = A.aiwcrf_fit(params, X, y)                                     # warm-up
     st = f.stats()
     del f
-    A.aiwcrf_profile_classes(["level_small", "level_big", "finalize", "tree"])
+    A.aiwcrf_profile_classes(["level_small", "level_big", "list_partition", "finalize", "tree"])
     A.aiwcrf_profile_enable(True)
     A.aiwcrf_profile_read()
     ms = 0.0
@@ -525,7 +525,7 @@ def per_row_report(A, dev, n_trees: int = T_TREES, steps: int = 1):
     A.aiwcrf_profile_enable(False)
     A.aiwcrf_profile_classes(None)
     peak, peak_kind = measured_peaks()
-    scan_ms = sum(prof.get(c, (0, 0.0))[1] for c in ("level_small", "level_big", "tree")) / steps
+    scan_ms = sum(prof.get(c, (0, 0.0))[1] for c in ("level_small", "level_big", "list_partition", "tree")) / steps
     alg = 33 * st["entries_evaluated"] + 10 * st["entries_partitioned"]
     achieved = alg / (scan_ms / 1e3) / 1e9 if scan_ms else None
     achieved_fit = alg / (ms / steps / 1e3) / 1e9
@@ -544,7 +544,7 @@ def per_row_report(A, dev, n_trees: int = T_TREES, steps: int = 1):
                              "achieved_over_whole_fit": achieved_fit, "frac_over_whole_fit": achieved_fit / peak,
                              "peak_source": f"hbm_gbs of {peak_kind} peaks",
                              "timing": "CUDA events around every level kernel launch of the fit"},
-            "kernels_ms": {c: prof[c][1] / steps for c in ("level_small", "level_big", "finalize", "tree")
+            "kernels_ms": {c: prof[c][1] / steps for c in ("level_small", "level_big", "list_partition", "finalize", "tree")
                            if c in prof and prof[c][0]}}
 
 

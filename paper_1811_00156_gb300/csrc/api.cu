@@ -154,7 +154,7 @@ cudaEvent_t take_event()
 
 const char *kProfNames[kProfNum] = {"rank",    "bootstrap", "level_big", "level_small", "finalize",
                                     "pack",    "predict",   "select",    "serve",       "tree",
-                                    "walk"};
+                                    "walk",    "list_partition"};
 }  // namespace
 
 // Every kernel class bracket is also an NVTX range on the launching host thread (a profiler's

@@ -792,21 +792,54 @@ inline int big_bin_cap(int mtry, int F, uint32_t max_card)
 // read from the node's own entry segment), 32 entries a step and kListIlp steps' loads in
 // flight, so the left sums of every threshold come without block barriers. A candidate sits at
 // the last entry of each run of equal ranks but the last run.
+// With AIWCRF_LIST_STAGE > 0, a node of at most that many entries is staged in shared memory
+// first (its entries, then per warp the ranks of the feature it scans, gathered in entry order
+// with no dependence on the list), so that each scan step reads one list position from HBM and
+// the rest from shared memory. Off by default: on the per-row fit the staging passes and the
+// smaller L1 cost more than the dependent loads they remove.
 constexpr int kListIlp = 4;
+#ifndef AIWCRF_LIST_STAGE
+#define AIWCRF_LIST_STAGE 0            // entries staged per node (0: none; 768 and 1536 were slower)
+#endif
+constexpr int kListStage = AIWCRF_LIST_STAGE;
+
+template <int NW>
+constexpr int list_stage_bytes() { return kListStage > 0 ? kListStage * 16 + NW * kListStage * 4 : 0; }
 
 template <typename RT, int NW>
-__device__ __forceinline__ Cand list_search(const LevelArgs &a, const NodeRec &nd, const int *feats, int m)
+__device__ __forceinline__ Cand list_search(const LevelArgs &a, const NodeRec &nd, const int *feats, int m,
+                                            unsigned char *stage)
 {
     const RT *__restrict__ Rr = static_cast<const RT *>(a.Rr);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const size_t tb = (size_t)nd.tree * (size_t)a.row_cap + nd.start;
     const Entry *__restrict__ rin = a.rows_in + tb;
+    const bool staged = kListStage > 0 && nd.len <= (uint32_t)kListStage;   // block-uniform
+    long long *s_wy = reinterpret_cast<long long *>(stage);
+    uint32_t *s_w = reinterpret_cast<uint32_t *>(stage + 8 * kListStage);
+    uint32_t *s_row = s_w + kListStage;
+    uint32_t *s_rk = s_row + kListStage + warp * kListStage;     // this warp's ranks
+    if (staged) {
+        for (uint32_t q = threadIdx.x; q < nd.len; q += 32u * NW) {
+            const Entry e = load_entry(rin + q);
+            s_wy[q] = (long long)e.wy;
+            s_w[q] = e.w;
+            s_row[q] = AIWCRF_IDX(e.row, (uint32_t)a.N, kBoundRow);
+        }
+        __syncthreads();
+    }
     Cand best = cand_none();
     for (int k = warp; k < m; k += NW) {
         const int f = feats[k];
         const uint32_t *__restrict__ L = a.lists_in + (size_t)f * (size_t)a.list_stride + tb;
         uint32_t cw = 0u;                       // sums of the earlier steps (warp-uniform)
         long long cs = 0ll;
+        if (staged) {
+            __syncwarp();                       // the previous feature's ranks are no longer read
+#pragma unroll 8
+            for (uint32_t q = (uint32_t)lane; q < nd.len; q += 32u) s_rk[q] = (uint32_t)__ldg(&Rr[(size_t)s_row[q] * (size_t)a.F + f]);
+            __syncwarp();
+        }
         for (uint32_t b0 = 0; b0 < nd.len; b0 += 32u * kListIlp) {
             uint32_t w[kListIlp], rank[kListIlp], nrank[kListIlp];
             long long wy[kListIlp];
@@ -814,14 +847,22 @@ __device__ __forceinline__ Cand list_search(const LevelArgs &a, const NodeRec &n
             for (int u = 0; u < kListIlp; ++u) {
                 const uint32_t i = b0 + 32u * u + (uint32_t)lane;
                 w[u] = 0u; wy[u] = 0ll; rank[u] = 0u; nrank[u] = 0u;
-                if (i < nd.len) {
+                if (staged) {
+                    if (i < nd.len) {
+                        const uint32_t q = AIWCRF_IDX(__ldg(&L[i]), nd.len, kBoundOut);
+                        w[u] = s_w[q];
+                        wy[u] = s_wy[q];
+                        rank[u] = s_rk[q];
+                    }
+                    if (lane == 31 && i + 1u < nd.len) nrank[u] = s_rk[AIWCRF_IDX(__ldg(&L[i + 1u]), nd.len, kBoundOut)];
+                } else if (i < nd.len) {
                     const Entry e = load_entry(rin + AIWCRF_IDX(__ldg(&L[i]), nd.len, kBoundOut));
                     w[u] = e.w;
                     wy[u] = (long long)e.wy;
                     rank[u] = (uint32_t)__ldg(&Rr[(size_t)AIWCRF_IDX(e.row, (uint32_t)a.N, kBoundRow) * (size_t)a.F + f]);
                 }
                 // the rank after the warp's last entry of this step
-                if (lane == 31 && i + 1u < nd.len) {
+                if (!staged && lane == 31 && i + 1u < nd.len) {
                     const uint32_t row2 = __ldg(&rin[AIWCRF_IDX(__ldg(&L[i + 1u]), nd.len, kBoundOut)].row);
                     nrank[u] = (uint32_t)__ldg(&Rr[(size_t)AIWCRF_IDX(row2, (uint32_t)a.N, kBoundRow) * (size_t)a.F + f]);
                 }
@@ -864,12 +905,12 @@ __device__ __forceinline__ Cand list_search(const LevelArgs &a, const NodeRec &n
 // within the child's own segment.
 constexpr int kPartIlp = 8;
 
-__device__ __forceinline__ void list_partition_feature(const LevelArgs &a, const NodeRec &nd, int f, uint32_t lenL)
+__device__ __forceinline__ void list_partition_feature(const LevelArgs &a, const NodeRec &nd, int f, uint32_t lenL,
+                                                       const uint32_t *np)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
     const size_t tb = (size_t)nd.tree * (size_t)a.row_cap + nd.start;
-    const uint32_t *__restrict__ np = a.newpos + tb;
     const uint32_t *__restrict__ Li = a.lists_in + (size_t)f * (size_t)a.list_stride + tb;
     uint32_t *__restrict__ Lo = a.lists_out + (size_t)f * (size_t)a.list_stride + tb;
     uint32_t rl = 0u, rr = 0u;
@@ -883,7 +924,7 @@ __device__ __forceinline__ void list_partition_feature(const LevelArgs &a, const
 #pragma unroll
         for (int u = 0; u < kPartIlp; ++u) {
             const uint32_t i = b0 + 32u * u + (uint32_t)lane;
-            d[u] = i < nd.len ? AIWCRF_IDX(__ldg(&np[p[u]]), nd.len, kBoundOut) : 0u;
+            d[u] = i < nd.len ? AIWCRF_IDX(np[p[u]], nd.len, kBoundOut) : 0u;
         }
 #pragma unroll
         for (int u = 0; u < kPartIlp; ++u) {
@@ -903,19 +944,31 @@ __device__ __forceinline__ void list_partition_feature(const LevelArgs &a, const
     }
 }
 
-// After the list kernel of a depth: one warp per (split big node, feature), node-major, so the
-// warps of a node share its new-position lines.
+// After the list kernel of a depth: one CTA per split big node, its warps taking the features
+// in turn. A node of at most kPartStage entries first copies its new positions into shared
+// memory, so each step's second load is a shared-memory read.
 constexpr int kPartThreads = 256;
 constexpr int kPartCtasPerSm = 4;
+constexpr int kPartStage = 8192;
 __global__ void __launch_bounds__(kPartThreads, kPartCtasPerSm) list_partition_kernel(LevelArgs a)
 {
-    const uint64_t items = (uint64_t)*a.list_n * (uint64_t)a.F;
-    const uint64_t nw = ((uint64_t)gridDim.x * kPartThreads) >> 5;
-    for (uint64_t it = ((uint64_t)blockIdx.x * kPartThreads + threadIdx.x) >> 5; it < items; it += nw) {
-        const int j = AIWCRF_IDX(a.list[it / (uint64_t)a.F], a.node_cap, kBoundNode);
+    __shared__ uint32_t s_np[kPartStage];
+    const uint32_t list_n = *a.list_n;
+    const int warp = threadIdx.x >> 5;
+    for (uint32_t k = blockIdx.x; k < list_n; k += gridDim.x) {
+        const int j = AIWCRF_IDX(a.list[k], a.node_cap, kBoundNode);
         const SplitRes sr = a.res[j];
-        if (sr.feature < 0) continue;                                // warp-uniform: a leaf
-        list_partition_feature(a, a.nodes[j], (int)(it % (uint64_t)a.F), sr.lenL);
+        if (sr.feature < 0) continue;                                // block-uniform: a leaf
+        const NodeRec nd = a.nodes[j];
+        const uint32_t *np = a.newpos + (size_t)nd.tree * (size_t)a.row_cap + nd.start;
+        const bool staged = nd.len <= (uint32_t)kPartStage;
+        __syncthreads();                                             // the previous node's copy is read
+        if (staged) {
+            for (uint32_t q = threadIdx.x; q < nd.len; q += kPartThreads) s_np[q] = __ldg(&np[q]);
+            __syncthreads();
+        }
+        for (int f = warp; f < a.F; f += kPartThreads / 32)
+            list_partition_feature(a, nd, f, sr.lenL, staged ? s_np : np);
     }
 }
 
@@ -987,7 +1040,7 @@ __device__ __forceinline__ void big_node(const LevelArgs &a, int bin_cap, int j)
     const uint32_t total_bins = fbase[m];
     Cand best = cand_none();
 
-    if constexpr (LISTS) best = list_search<RT, NT / 32>(a, nd, feats, m);
+    if constexpr (LISTS) best = list_search<RT, NT / 32>(a, nd, feats, m, reinterpret_cast<unsigned char *>(sm_bins));
     else for (uint32_t g0 = 0; g0 < total_bins; g0 += (uint32_t)bin_cap) {
         const uint32_t g1 = min(total_bins, g0 + (uint32_t)bin_cap);
         const int nb = (int)(g1 - g0);
@@ -2664,6 +2717,11 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         AIWCRF_BY_RANK(rank_bytes, e_ = cudaFuncSetAttribute(level_big_kernel<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                              big_smem))
         if (e_ != cudaSuccess) return cuda_fail(e_, "level_big_kernel attribute");
+        if (use_lists) {
+            AIWCRF_BY_RANK(rank_bytes, e_ = cudaFuncSetAttribute(level_list_kernel<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                                 list_stage_bytes<kListThreads / 32>()))
+            if (e_ != cudaSuccess) return cuda_fail(e_, "level_list_kernel attribute");
+        }
     }
 
     LevelArgs la;
@@ -2733,18 +2791,20 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
                 if (use_lists) {
                     const int64_t cps_list = p.ctas_per_sm > 0 ? p.ctas_per_sm : kListCtasPerSm;
                     const unsigned lgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(Cb, cps_list * dev_sms));
-                    AIWCRF_BY_RANK(rank_bytes, level_list_kernel<RT><<<lgrid, kListThreads, 0, s>>>(la))
+                    AIWCRF_BY_RANK(rank_bytes, level_list_kernel<RT><<<lgrid, kListThreads, list_stage_bytes<kListThreads / 32>(), s>>>(la))
                     AIWCRF_LAUNCH_CHECK("level_list_kernel");
+                    prof_end(s, kProfLevelBig);
+                    prof_begin(s, kProfListPart);
                     const int64_t cps_part = p.ctas_per_sm > 0 ? p.ctas_per_sm : kPartCtasPerSm;
-                    const unsigned pgrid = (unsigned)std::max<int64_t>(
-                        1, std::min<int64_t>((Cb * F + kPartThreads / 32 - 1) / (kPartThreads / 32), cps_part * dev_sms));
+                    const unsigned pgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(Cb, cps_part * dev_sms));
                     list_partition_kernel<<<pgrid, kPartThreads, 0, s>>>(la);
                     AIWCRF_LAUNCH_CHECK("list_partition_kernel");
+                    prof_end(s, kProfListPart);
                 } else {
                     AIWCRF_BY_RANK(rank_bytes, level_big_kernel<RT><<<grid, kBigThreads, big_smem, s>>>(la, bin_cap))
                     AIWCRF_LAUNCH_CHECK("level_big_kernel");
+                    prof_end(s, kProfLevelBig);
                 }
-                prof_end(s, kProfLevelBig);
             }
             {
                 la.list = small_a; la.list_n = &d_cnt->n_list[depth & 1][0];

@@ -390,7 +390,7 @@ size_t radix_sort_hist_words(int64_t n, int S);
 
 enum ProfClass {
     kProfRank = 0, kProfBoot, kProfLevelBig, kProfLevelSmall, kProfFinalize,
-    kProfPack, kProfPredict, kProfSelect, kProfServe, kProfTree, kProfWalk, kProfNum
+    kProfPack, kProfPredict, kProfSelect, kProfServe, kProfTree, kProfWalk, kProfListPart, kProfNum
 };
 
 void prof_begin(cudaStream_t s, int cls);
