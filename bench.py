@@ -410,7 +410,7 @@ def run_ours(args):
            "gpu_launches": launches, "clocks": clk, "parity": "bit-exact vs oracle (tests/test_gpu_parity.py)"}
 
     if not args.no_e2e:
-        out["e2e"] = e2e(A, wl, Xq_h, kfeat_h, params, devices, world, dev, max(1, min(K, 3)))
+        out["e2e"] = e2e(A, wl, Xq_h, kfeat_h, params, devices, world, dev, max(1, min(K, 5)))
     if rank == 0 and not args.no_extras:
         out["fit_graph"] = fit_graph_report(A, params, X, y, stats)
         f = A.aiwcrf_fit(params, X, y)
@@ -446,6 +446,10 @@ def e2e(A, wl, Xq_h, kfeat_h, params, devices, world, dev, steps):
     pred = torch.empty(Xq.shape[1], dtype=torch.int64).pin_memory().numpy()
     best = torch.empty(kf.shape[1], dtype=torch.int32).pin_memory().numpy()
     selp = torch.empty(kf.shape[1] * len(devices), dtype=torch.int64).pin_memory().numpy()
+    f = A.aiwcrf_fit(params, X, y)                    # one untimed step: the staging pool is warm
+    A.aiwcrf_predict(f, Xq, pred)
+    A.aiwcrf_select_device(f, kf, 2, devices, best, selp)
+    del f
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
