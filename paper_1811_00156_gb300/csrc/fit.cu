@@ -602,6 +602,10 @@ __device__ __forceinline__ void small_node(const LevelArgs &a, const RT *__restr
         if (lane == 0) write_leaf(a.res, j, -2, 0);
         return;
     }
+    if (nd.len == 1) {                  // one entry: every candidate is its last rank, a leaf
+        if (lane == 0) write_leaf(a.res, j, -1, 0);
+        return;
+    }
     const size_t tb = (size_t)nd.tree * (size_t)a.row_cap + nd.start;
     const int K = nd.len <= 2 ? 2 : (int)(1u << (32 - __clz((int)nd.len - 1)));
     const int P = 32 / K;                                        // features per pass
@@ -1466,6 +1470,10 @@ __device__ __forceinline__ void tree_small_node(const TreeArgs &a, const TreeSme
 {
     if (tnode_stops(a, nd.n, depth)) {
         if (lane == 0) write_leaf(res_j, 0, -2, 0);
+        return;
+    }
+    if (nd.len == 1) {                  // one entry: every candidate is its last rank, a leaf
+        if (lane == 0) write_leaf(res_j, 0, -1, 0);
         return;
     }
     const int len = nd.len;
