@@ -106,12 +106,15 @@ __device__ __forceinline__ float encode_value(const Encoder &e, const float *X, 
 // ------------------------------------------------------------------------------------------
 // training kernels
 // ------------------------------------------------------------------------------------------
+// step: when set, the batch starts at row (*step mod spe) * B of the permutation instead of r0
+// (a replayed training step reads its place in the epoch from the device step counter)
 __global__ void encode_batch_kernel(Encoder e, const float *__restrict__ X, int64_t ld, const uint32_t *__restrict__ perm,
                                     int64_t r0, int B, const float *__restrict__ yall, bf16 *__restrict__ xin,
-                                    float *__restrict__ yb)
+                                    float *__restrict__ yb, const int64_t *step, int64_t spe)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B * kIn) return;
+    if (step) r0 = (*step % spe) * (int64_t)B;
     const int b = i / kIn, k = i % kIn;
     const int64_t row = perm ? (int64_t)perm[r0 + b] : r0 + b;
     xin[i] = __float2bfloat16_rn(encode_value(e, X, ld, row, k));
@@ -196,11 +199,15 @@ __global__ void __launch_bounds__(256) colsum_kernel(const float *__restrict__ v
     if (threadIdx.x == 0) dst[j] = red[0];
 }
 
+// c12: when set, the bias corrections of step *step are c12[2 * step] and c12[2 * step + 1]
+// (computed on the host for every step, as c1 and c2 are otherwise)
 __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
-                            float *__restrict__ v, int n, float lr, float beta1, float beta2, float eps, float c1, float c2)
+                            float *__restrict__ v, int n, float lr, float beta1, float beta2, float eps, float c1, float c2,
+                            const float *__restrict__ c12, const int64_t *step)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (c12) { c1 = c12[2 * *step]; c2 = c12[2 * *step + 1]; }
     const float gi = g[i];
     const float mi = beta1 * m[i] + (1.0f - beta1) * gi;
     const float vi = beta2 * v[i] + (1.0f - beta2) * gi * gi;
@@ -208,6 +215,8 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, 
     v[i] = vi;
     p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
+
+__global__ void step_advance_kernel(int64_t *step) { *step += 1; }
 
 __global__ void to_bf16_kernel(const float *__restrict__ src, bf16 *__restrict__ dst, int n)
 {
@@ -523,13 +532,13 @@ struct Batch {
 
 // forward + backward of one batch; gradients land in bt.grad (parameter layout)
 int forward_backward(const aiwcrf_surrogate *sg, Batch &bt, const float *X, int64_t ld, const uint32_t *perm,
-                     int64_t r0, const float *y, cudaStream_t s)
+                     int64_t r0, const float *y, cudaStream_t s, const int64_t *step = nullptr, int64_t spe = 1)
 {
     const int B = bt.B, BH = B * kHid, ks = 16;
     const Encoder e = encoder_of(sg);
     const float *P = sg->d_param;
     int rc;
-    encode_batch_kernel<<<(B * kIn + 255) / 256, 256, 0, s>>>(e, X, ld, perm, r0, B, y, bt.xin, bt.yb);
+    encode_batch_kernel<<<(B * kIn + 255) / 256, 256, 0, s>>>(e, X, ld, perm, r0, B, y, bt.xin, bt.yb, step, spe);
     if ((rc = tc_gemm(bt.xin, kIn, false, sg->d_W1b, kIn, false, bt.z1, B, kHid, kIn, 1, bt.part, bt.err, s))) return rc;
     act1_kernel<<<(BH + 255) / 256, 256, 0, s>>>(bt.z1, P + ob1, bt.h1, BH);
     if ((rc = tc_gemm(bt.h1, kHid, false, sg->d_W2b, kHid, false, bt.z2, B, kHid, kHid, 1, bt.part, bt.err, s))) return rc;
@@ -552,6 +561,42 @@ int forward_backward(const aiwcrf_surrogate *sg, Batch &bt, const float *X, int6
     SG_LAUNCH_CHECK("surrogate backward");
     return AIWCRF_OK;
 }
+
+// A training step captured as a CUDA graph on its own stream (so that a caller's legacy default
+// stream is never captured), instantiated once and replayed.
+struct TrainGraph {
+    cudaStream_t ts = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    size_t nodes = 0;
+    ~TrainGraph()
+    {
+        if (x) cudaGraphExecDestroy(x);
+        if (g) cudaGraphDestroy(g);
+        if (ts) cudaStreamDestroy(ts);
+    }
+    template <class F>
+    int capture(F &&body)
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "surrogate step capture");
+        const int rc = body(ts);
+        e = cudaStreamEndCapture(ts, &g);
+        if (rc) return rc;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+        if (e == cudaSuccess) e = cudaGraphGetNodes(g, nullptr, &nodes);
+        if (e != cudaSuccess) return cuda_fail(e, "surrogate step graph");
+        return AIWCRF_OK;
+    }
+    int replay()
+    {
+        const cudaError_t e = cudaGraphLaunch(x, ts);
+        if (e != cudaSuccess) return cuda_fail(e, "surrogate step replay");
+        count_launches((int64_t)nodes);
+        return AIWCRF_OK;
+    }
+};
 
 int check_err(const Batch &bt, cudaStream_t s)
 {
@@ -778,33 +823,59 @@ int aiwcrf_surrogate_fit(const aiwcrf_surrogate_params *p, const aiwcrf_forest *
     for (int64_t i = 0; i < n; ++i) perm[(size_t)i] = (uint32_t)i;
     std::mt19937_64 rng(p->seed ^ 0x5DEECE66Dull);
     float first_loss = -1.0f, last_loss = -1.0f;
+    const int64_t total_steps = (int64_t)p->epochs * steps_per_epoch;
+    // Adam's bias corrections of every step, as the step-by-step loop computes them
+    std::vector<float> c12((size_t)(2 * total_steps));
+    for (int64_t t1 = 1; t1 <= total_steps; ++t1) {
+        c12[(size_t)(2 * (t1 - 1))] = 1.0f - std::pow(p->beta1, (float)t1);
+        c12[(size_t)(2 * (t1 - 1) + 1)] = 1.0f - std::pow(p->beta2, (float)t1);
+    }
+    // One training step (forward, backward, Adam, BF16 weight copies, step counter) is captured
+    // once as a CUDA graph on a private stream and replayed: it reads its batch offset and bias
+    // corrections through the device step counter, so the replays are the step-by-step loop's
+    // launches without their host cost.
+    TrainGraph tg;
+    float *d_c12 = nullptr;
+    int64_t *d_step = nullptr;
+    if (cudaMallocAsync(&d_c12, 4 * c12.size(), s) != cudaSuccess || cudaMallocAsync(&d_step, 8, s) != cudaSuccess)
+        return fail(AIWCRF_E_OOM, "surrogate step tables");
+    struct FreeC { float *a; int64_t *b; cudaStream_t s; ~FreeC() { cudaFreeAsync(a, s); cudaFreeAsync(b, s); } } fc{d_c12, d_step, s};
+    e = cudaMemcpyAsync(d_c12, c12.data(), 4 * c12.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_step, 0, 8, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "surrogate step tables");
+    if ((rc = tg.capture([&](cudaStream_t ts) {
+             int r = forward_backward(sg, bt, X, n, d_perm, 0, d_y, ts, d_step, steps_per_epoch);
+             if (r) return r;
+             adam_kernel<<<(kParams + 255) / 256, 256, 0, ts>>>(sg->d_param, bt.grad, bt.m, bt.v, kParams, p->lr,
+                                                                p->beta1, p->beta2, p->eps, 1.0f, 1.0f, d_c12, d_step);
+             if ((r = refresh_bf16(sg, ts))) return r;
+             step_advance_kernel<<<1, 1, 0, ts>>>(d_step);
+             const cudaError_t e2 = cudaGetLastError();
+             return e2 == cudaSuccess ? AIWCRF_OK : cuda_fail(e2, "surrogate step launches");
+         })))
+        return rc;
     int64_t t = 0;
     for (int ep = 0; ep < p->epochs; ++ep) {
         std::shuffle(perm.begin(), perm.end(), rng);
-        e = cudaMemcpyAsync(d_perm, perm.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);        // the host array is reshuffled next epoch
+        e = cudaMemcpyAsync(d_perm, perm.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, tg.ts);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(tg.ts);      // the host array is reshuffled next epoch
         if (e != cudaSuccess) return cuda_fail(e, "surrogate permutation");
-        double ep_loss = 0.0;
-        std::vector<float> losses;
         for (int64_t k = 0; k < steps_per_epoch; ++k) {
-            if ((rc = forward_backward(sg, bt, X, n, d_perm, k * p->batch, d_y, s))) return rc;
+            if ((rc = tg.replay())) return rc;
             ++t;
-            const float c1 = 1.0f - std::pow(p->beta1, (float)t), c2 = 1.0f - std::pow(p->beta2, (float)t);
-            adam_kernel<<<(kParams + 255) / 256, 256, 0, s>>>(sg->d_param, bt.grad, bt.m, bt.v, kParams, p->lr, p->beta1,
-                                                              p->beta2, p->eps, c1, c2);
-            count_launches(1);
-            if ((rc = refresh_bf16(sg, s))) return rc;
             if (k == 0 || k == steps_per_epoch - 1) {
                 float hl = 0.0f;
-                e = cudaMemcpyAsync(&hl, bt.loss, 4, cudaMemcpyDeviceToHost, s);
-                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                e = cudaMemcpyAsync(&hl, bt.loss, 4, cudaMemcpyDeviceToHost, tg.ts);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(tg.ts);
                 if (e != cudaSuccess) return cuda_fail(e, "surrogate loss");
                 if (first_loss < 0.0f) first_loss = hl / (float)p->batch;
                 last_loss = hl / (float)p->batch;
             }
         }
-        (void)ep_loss;
     }
+    e = cudaStreamSynchronize(tg.ts);
+    if (e != cudaSuccess) return cuda_fail(e, "surrogate training");
     if ((rc = check_err(bt, s))) return rc;
     sg->stats.steps = t;
     sg->stats.first_batch_loss = first_loss;
