@@ -75,22 +75,23 @@ __host__ __device__ constexpr uint32_t tmem_cols_for(int N)
     return N <= 32 ? 32u : N <= 64 ? 64u : N <= 128 ? 128u : 256u;
 }
 
-// part[kz][m][n] = sum over CTA column kz's K chunks of A(m, k) B(n, k); N multiple of 16, <= 256
+// part[kz][m][n] = sum over CTA column kz's K chunks of A(m, k) B(n, k), for the columns
+// [n0, n0 + NT) of CTA layer blockIdx.z (n0 = blockIdx.z * NT); N and NT multiples of 16, <= 256
 template <bool AT, bool BT>
 __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const bf16 *__restrict__ A, int lda,
                                                                const bf16 *__restrict__ B, int ldb, float *part, int M,
-                                                               int N, int K, int chunks_per_cta, uint32_t *err)
+                                                               int N, int K, int chunks_per_cta, int NT, uint32_t *err)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *sA = sm;                    // 128 x 64 BF16 = 16 KB
-    unsigned char *sB = sm + 16384;            // N x 64 BF16 <= 32 KB
+    unsigned char *sB = sm + 16384;            // NT x 64 BF16 <= 32 KB
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.x * 128, kz = blockIdx.y;
+    const int m0 = blockIdx.x * 128, kz = blockIdx.y, n0 = blockIdx.z * NT;
     const int nchunks = (K + 63) / 64;
     const int kc0 = kz * chunks_per_cta, kc1 = min(kc0 + chunks_per_cta, nchunks);
-    const uint32_t ncols = tmem_cols_for(N);
+    const uint32_t ncols = tmem_cols_for(NT);
 
     if (warp == 0) {
         tc::tmem_alloc(&tmem_base, ncols);
@@ -101,13 +102,13 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const bf16 *__res
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = tmem_base;
-    const uint32_t idesc = tc::make_idesc_bf16(128, (uint32_t)N);
+    const uint32_t idesc = tc::make_idesc_bf16(128, (uint32_t)NT);
 
     bool ok = true;
     uint32_t phase = 0;
     for (int kc = kc0; kc < kc1; ++kc) {
         stage_tile<AT>(sA, A, lda, m0, 128, M, kc * 64, K);
-        stage_tile<BT>(sB, B, ldb, 0, N, N, kc * 64, K);
+        stage_tile<BT>(sB, B, ldb, n0, NT, N, kc * 64, K);
         tc::fence_smem_to_async();
         __syncthreads();
         if (tid == 0) {
@@ -127,14 +128,14 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const bf16 *__res
 
     if (ok) {
         const int m = m0 + 32 * warp + lane;
-        float *dst = part + ((size_t)kz * (size_t)M + (size_t)m) * (size_t)N;
-        for (int c = 0; c < N; c += 32) {
+        float *dst = part + ((size_t)kz * (size_t)M + (size_t)m) * (size_t)N + n0;
+        for (int c = 0; c < NT; c += 32) {
             float v[32];
             if (kc1 > kc0) tc::tmem_ld32(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
             else
                 for (int i = 0; i < 32; ++i) v[i] = 0.0f;
             if (m < M)
-                for (int i = 0; i < 32 && c + i < N; i += 4)
+                for (int i = 0; i < 32 && c + i < NT; i += 4)
                     *reinterpret_cast<float4 *>(dst + c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
         }
     } else if (tid == 0) {
@@ -167,16 +168,21 @@ int tc_gemm(const bf16 *A, int lda, bool a_trans, const bf16 *B, int ldb, bool b
     const int nchunks = (K + 63) / 64;
     const int splits = std::max(1, std::min(ksplit, nchunks));
     const int per = (nchunks + splits - 1) / splits;
-    const int smem = 16384 + N * 128;
-    // at least 80 KB of shared memory per CTA: at most two CTAs (512 TMEM columns) per SM
-    const int smem_launch = std::max(smem, 80 * 1024);
-    const dim3 grid((unsigned)((M + 127) / 128), (unsigned)splits);
+    // columns per CTA: halved (in multiples of 16) until the grid has at least 128 CTAs
+    const int mtiles = (M + 127) / 128;
+    int NT = N;
+    while ((int64_t)mtiles * splits * (N / NT) < 128 && NT % 32 == 0 && N % (NT / 2) == 0) NT /= 2;
+    const int smem = 16384 + NT * 128;
+    // enough shared memory per CTA that no more CTAs fit an SM than its 512 TMEM columns hold
+    const int per_sm = 512 / (int)tmem_cols_for(NT);
+    const int smem_launch = std::max(smem, 233472 / (per_sm + 1));
+    const dim3 grid((unsigned)mtiles, (unsigned)splits, (unsigned)(N / NT));
     cudaError_t e;
 #define AIWCRF_TC_LAUNCH(AT, BT)                                                                                   \
     e = cudaFuncSetAttribute(tc_gemm_kernel<AT, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_launch);    \
     if (e == cudaSuccess) {                                                                                        \
         tc_gemm_kernel<AT, BT><<<grid, kGemmThreads, smem_launch, s>>>(A, lda, B, ldb, splits > 1 ? part : C, M,  \
-                                                                      N, K, per, d_err);                           \
+                                                                      N, K, per, NT, d_err);                       \
     }
     if (!a_trans && !b_trans) { AIWCRF_TC_LAUNCH(false, false) }
     else if (!a_trans && b_trans) { AIWCRF_TC_LAUNCH(false, true) }

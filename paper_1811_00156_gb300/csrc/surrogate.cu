@@ -182,21 +182,38 @@ __global__ void back1_kernel(const float *__restrict__ dh1, const float *__restr
     dz1b[i] = __float2bfloat16_rn(d);
 }
 
-// dst[j] = sum_b v[b][j] (* w[b]); one block per column, fixed summation order
-__global__ void __launch_bounds__(256) colsum_kernel(const float *__restrict__ v, int ld, int rows,
-                                                     const float *__restrict__ w, float *__restrict__ dst)
+// dst[j] = sum_b v[b][j] (* w[b]) for the kHid columns of v (leading dimension kHid), in two
+// fixed-order passes with coalesced reads: block (g, c) sums columns [32 g, 32 g + 32) over the
+// c-th of kColChunks row ranges (eight row lanes, then the lanes in order) into part; then
+// colsum_finish_kernel adds the kColChunks partial sums of each column in order.
+constexpr int kColChunks = 16;
+
+__global__ void __launch_bounds__(256) colsum_part_kernel(const float *__restrict__ v, int rows,
+                                                          const float *__restrict__ w, float *__restrict__ part)
 {
-    __shared__ float red[256];
-    const int j = blockIdx.x;
+    __shared__ float red[8][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + tx;
+    const int per = (rows + kColChunks - 1) / kColChunks;
+    const int r0 = blockIdx.y * per, r1 = min(rows, r0 + per);
     float s = 0.0f;
-    for (int b = threadIdx.x; b < rows; b += blockDim.x) s += v[(size_t)b * (size_t)ld + j] * (w ? w[b] : 1.0f);
-    red[threadIdx.x] = s;
+    for (int b = r0 + ty; b < r1; b += 8) s += v[(size_t)b * kHid + c] * (w ? w[b] : 1.0f);
+    red[ty][tx] = s;
     __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
+    if (ty == 0) {
+        float t = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t += red[k][tx];
+        part[blockIdx.y * kHid + c] = t;
     }
-    if (threadIdx.x == 0) dst[j] = red[0];
+}
+
+__global__ void colsum_finish_kernel(const float *__restrict__ part, float *__restrict__ dst)
+{
+    const int j = threadIdx.x;
+    float s = 0.0f;
+    for (int y = 0; y < kColChunks; ++y) s += part[y * kHid + j];
+    dst[j] = s;
 }
 
 // c12: when set, the bias corrections of step *step are c12[2 * step] and c12[2 * step + 1]
@@ -545,18 +562,21 @@ int forward_backward(const aiwcrf_surrogate *sg, Batch &bt, const float *X, int6
     act2_out_kernel<<<(B + 7) / 8, 256, 0, s>>>(bt.z2, P + ob2, P + ow3, P + ob3, bt.h2, bt.yb, B, bt.out, bt.dout,
                                                 bt.loss_rows);
     back2_kernel<<<(BH + 255) / 256, 256, 0, s>>>(bt.z2, P + ow3, bt.dout, bt.dz2b, bt.dz2f, BH);
-    colsum_kernel<<<kHid, 256, 0, s>>>(bt.h2, kHid, B, bt.dout, bt.grad + ow3);        // dw3
+    colsum_part_kernel<<<dim3(kHid / 32, kColChunks), 256, 0, s>>>(bt.h2, B, bt.dout, bt.part);    // dw3
+    colsum_finish_kernel<<<1, kHid, 0, s>>>(bt.part, bt.grad + ow3);
     sum_kernel<<<1, 256, 0, s>>>(bt.dout, B, bt.grad + ob3);                            // db3
-    colsum_kernel<<<kHid, 256, 0, s>>>(bt.dz2f, kHid, B, nullptr, bt.grad + ob2);       // db2
+    colsum_part_kernel<<<dim3(kHid / 32, kColChunks), 256, 0, s>>>(bt.dz2f, B, nullptr, bt.part);  // db2
+    colsum_finish_kernel<<<1, kHid, 0, s>>>(bt.part, bt.grad + ob2);
     sum_kernel<<<1, 256, 0, s>>>(bt.loss_rows, B, bt.loss);
-    count_launches(8);
+    count_launches(10);
     SG_LAUNCH_CHECK("surrogate forward");
     // dW2 = dz2^T h1 ; dh1 = dz2 W2 ; dz1 = dh1 GELU'(z1) ; dW1 = dz1^T xin
     if ((rc = tc_gemm(bt.dz2b, kHid, true, bt.h1, kHid, true, bt.grad + oW2, kHid, kHid, B, ks, bt.part, bt.err, s))) return rc;
     if ((rc = tc_gemm(bt.dz2b, kHid, false, sg->d_W2b, kHid, true, bt.dh1, B, kHid, kHid, 1, bt.part, bt.err, s))) return rc;
     back1_kernel<<<(BH + 255) / 256, 256, 0, s>>>(bt.dh1, bt.z1, bt.dz1b, bt.dz1f, BH);
-    colsum_kernel<<<kHid, 256, 0, s>>>(bt.dz1f, kHid, B, nullptr, bt.grad + ob1);       // db1
-    count_launches(2);
+    colsum_part_kernel<<<dim3(kHid / 32, kColChunks), 256, 0, s>>>(bt.dz1f, B, nullptr, bt.part);  // db1
+    colsum_finish_kernel<<<1, kHid, 0, s>>>(bt.part, bt.grad + ob1);
+    count_launches(3);
     if ((rc = tc_gemm(bt.dz1b, kHid, true, bt.xin, kIn, true, bt.grad + oW1, kHid, kIn, B, ks, bt.part, bt.err, s))) return rc;
     SG_LAUNCH_CHECK("surrogate backward");
     return AIWCRF_OK;
