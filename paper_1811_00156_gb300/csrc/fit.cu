@@ -909,8 +909,11 @@ __device__ __forceinline__ Cand list_search(const LevelArgs &a, const NodeRec &n
 // within the child's own segment.
 constexpr int kPartIlp = 8;
 
+// needL / needR: whether the left / right child will search its lists (the other side's entries
+// are not written: a child of at most 32 entries is searched from the entries, a stopping one not
+// at all).
 __device__ __forceinline__ void list_partition_feature(const LevelArgs &a, const NodeRec &nd, int f, uint32_t lenL,
-                                                       const uint32_t *np)
+                                                       const uint32_t *np, bool needL, bool needR)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
@@ -938,7 +941,7 @@ __device__ __forceinline__ void list_partition_feature(const LevelArgs &a, const
             const bool left = i < nd.len && d[u] < lenL;
             const uint32_t bal = __ballot_sync(kFull, left);
             const uint32_t before = (uint32_t)__popc(bal & lt);
-            if (i < nd.len)
+            if (i < nd.len && (left ? needL : needR))
                 Lo[AIWCRF_IDX(left ? rl + before : lenL + rr + ((uint32_t)lane - before), nd.len, kBoundOut)] =
                     left ? d[u] : d[u] - lenL;
             const uint32_t nl = (uint32_t)__popc(bal);
@@ -964,6 +967,12 @@ __global__ void __launch_bounds__(kPartThreads, kPartCtasPerSm) list_partition_k
         const SplitRes sr = a.res[j];
         if (sr.feature < 0) continue;                                // block-uniform: a leaf
         const NodeRec nd = a.nodes[j];
+        // a child needs its lists only if it is searched by the list kernel next depth
+        const int d1 = level_depth(a) + 1;
+        const bool deep = a.max_depth > 0 && d1 >= a.max_depth;
+        const bool needL = !deep && sr.lenL > (uint32_t)kSmallNodeRows && sr.nL > (uint32_t)a.min_node;
+        const bool needR = !deep && nd.len - sr.lenL > (uint32_t)kSmallNodeRows && nd.n - sr.nL > (uint32_t)a.min_node;
+        if (!needL && !needR) continue;                              // block-uniform
         const uint32_t *np = a.newpos + (size_t)nd.tree * (size_t)a.row_cap + nd.start;
         const bool staged = nd.len <= (uint32_t)kPartStage;
         __syncthreads();                                             // the previous node's copy is read
@@ -972,7 +981,7 @@ __global__ void __launch_bounds__(kPartThreads, kPartCtasPerSm) list_partition_k
             __syncthreads();
         }
         for (int f = warp; f < a.F; f += kPartThreads / 32)
-            list_partition_feature(a, nd, f, sr.lenL, staged ? s_np : np);
+            list_partition_feature(a, nd, f, sr.lenL, staged ? s_np : np, needL, needR);
     }
 }
 

@@ -105,11 +105,16 @@ __device__ __forceinline__ int64_t leaf_value(uint64_t nd)
 // written once, whole sectors at a time. A row is row_words 4-byte words; its padding is zero.
 constexpr int kCodeThreads = 128;
 
+// The binary searches of kCodeGroup features run side by side (their table loads in flight
+// together), each for a fixed steps = bit width of the largest table: the same lower bound as
+// a search that stops early.
+constexpr int kCodeGroup = 4;
+
 template <typename CT>
 __global__ void __launch_bounds__(kCodeThreads) code_queries_kernel(const float *__restrict__ Xq, int64_t Q, int F,
                                                                    const float *__restrict__ fvals, int64_t fstride,
                                                                    const uint32_t *__restrict__ fcard,
-                                                                   CT *__restrict__ codes, int row_words)
+                                                                   CT *__restrict__ codes, int row_words, int steps)
 {
     extern __shared__ __align__(16) uint32_t code_rows[];         // kCodeThreads * row_words words
     const int tid = threadIdx.x;
@@ -118,20 +123,34 @@ __global__ void __launch_bounds__(kCodeThreads) code_queries_kernel(const float 
     for (int w = 0; w < row_words; ++w) row[w] = 0u;
     if (q < Q) {
         CT *c = reinterpret_cast<CT *>(row);
-        for (int f = 0; f < F; ++f) {
-            const float x = __ldg(&Xq[(size_t)f * (size_t)Q + q]);
-            const float *V = fvals + (size_t)f * (size_t)fstride;
-            uint32_t lo = 0, hi = __ldg(&fcard[f]);
-            if (x != x) {
-                lo = hi;
-            } else {
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (__ldg(&V[mid]) < x) lo = mid + 1;
-                    else hi = mid;
+        for (int f0 = 0; f0 < F; f0 += kCodeGroup) {
+            float x[kCodeGroup];
+            uint32_t lo[kCodeGroup], len[kCodeGroup];
+#pragma unroll
+            for (int u = 0; u < kCodeGroup; ++u) {
+                const int f = f0 + u;
+                x[u] = f < F ? __ldg(&Xq[(size_t)f * (size_t)Q + q]) : 0.0f;
+                const uint32_t n = f < F ? __ldg(&fcard[f]) : 0u;
+                lo[u] = x[u] != x[u] ? n : 0u;                      // NaN: past every value
+                len[u] = x[u] != x[u] ? 0u : n;
+            }
+            for (int it = 0; it < steps; ++it) {
+#pragma unroll
+                for (int u = 0; u < kCodeGroup; ++u) {
+                    if (len[u]) {
+                        const uint32_t half = len[u] >> 1;
+                        if (__ldg(&fvals[(size_t)(f0 + u) * (size_t)fstride + lo[u] + half]) < x[u]) {
+                            lo[u] += half + 1u;
+                            len[u] -= half + 1u;
+                        } else {
+                            len[u] = half;
+                        }
+                    }
                 }
             }
-            c[f] = (CT)lo;
+#pragma unroll
+            for (int u = 0; u < kCodeGroup; ++u)
+                if (f0 + u < F) c[f0 + u] = (CT)lo[u];
         }
     }
     __syncthreads();
@@ -171,8 +190,9 @@ cudaError_t launch_code_queries(const aiwcrf_forest *f, const float *dXq, int64_
                                                    (int)smem);
         if (e != cudaSuccess) return e;
     }
+    const int steps = 32 - __builtin_clz(f->max_card | 1u);               // bit width of the largest table
     code_queries_kernel<CT><<<(unsigned)((Q + kCodeThreads - 1) / kCodeThreads), kCodeThreads, smem, s>>>(
-        dXq, Q, f->F, f->d_fvals, f->fstride, f->d_fcard, d_codes, row_words);
+        dXq, Q, f->F, f->d_fvals, f->fstride, f->d_fcard, d_codes, row_words, steps);
     count_launches(1);
     return cudaGetLastError();
 }
