@@ -417,6 +417,7 @@ def run_ours(args):
         out["oob"] = oob_report(A, wl, X, f)
         del f
         out["loko"] = loko_report(A, dev)
+        out["tune"] = tune_report(A, dev)
         out["per_row"] = per_row_report(A, dev)
         f = A.aiwcrf_fit(params, X, y)
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
@@ -550,6 +551,27 @@ def per_row_report(A, dev, n_trees: int = T_TREES, steps: int = 1):
                              "timing": "CUDA events around every level kernel launch of the fit"},
             "kernels_ms": {c: prof[c][1] / steps for c in ("level_small", "level_big", "list_partition", "finalize", "tree")
                            if c in prof and prof[c][0]}}
+
+
+def tune_report(A, dev, steps: int = 40):
+    """Simulated-annealing tuning of num.trees, mtry and min.node.size against the out-of-bag
+    error (Sec. III-C) on the 2,220-row workload: 40 candidates from (128, 10, 5), num.trees in
+    [16, 512], mtry in [1, 32], min.node.size in [1, 20]; every candidate a GPU fit and its
+    exact out-of-bag error."""
+    import torch
+    wl = synth.plain_forest_workload()
+    X, y = torch.from_numpy(wl.X).to(dev), torch.from_numpy(wl.y).to(dev)
+    tp = A.tune_params(steps=steps, trees=(16, 512), mtry=(1, 32), node=(1, 20), t0=0.1, cooling=0.93, seed=1811)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    best, mse, trace = A.aiwcrf_tune_sa(tp, A.params(128, MTRY, MIN_NODE, seed=synth.FOREST_SEED), X, y)
+    secs = time.perf_counter() - t0
+    distinct = len({(t["num_trees"], t["mtry"], t["min_node_size"]) for t in trace})
+    return {"workload": "aiwc-2220", "candidates": steps, "distinct_fits": distinct, "s": secs,
+            "start": {"num_trees": 128, "mtry": MTRY, "min_node_size": MIN_NODE, "oob_mse": trace[0]["oob_mse"]},
+            "best": {"num_trees": best.num_trees, "mtry": best.mtry, "min_node_size": best.min_node_size,
+                     "oob_mse": mse},
+            "accepted": sum(t["accepted"] for t in trace[1:])}
 
 
 def loko_report(A, dev, steps: int = 2):

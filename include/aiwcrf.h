@@ -146,6 +146,42 @@ int aiwcrf_oob(const aiwcrf_forest *forest, const float *X, int64_t n_rows, int6
 int aiwcrf_oob_error(const aiwcrf_forest *forest, const float *X, const int64_t *y, int64_t n_rows,
                      int64_t *out_pred, double *out_mse, int64_t *out_rows, void *cuda_stream);
 
+/* Tuning of num.trees, mtry and min.node.size at once against the out-of-bag error (Sec. III-C:
+ * the paper minimises the out-of-bag prediction error by simulated annealing over the three
+ * parameters; its annealer is an R package's, this one is stated here). Every evaluation is
+ * aiwcrf_fit with the candidate's three parameters (the rest from *start) followed by
+ * aiwcrf_oob_error on the same rows; a setting already evaluated is not fitted again.
+ *  - start: the first state, clamped into the bounds; its error E_0 sets the temperature
+ *    t_1 = t0 * E_0, and t_{i+1} = cooling * t_i.
+ *  - step i = 1..steps: one of the three parameters, chosen uniformly, moves to a value uniform in
+ *    [v - r, v + r] clamped into its bounds, r = max(1, ceil(0.25 * (max - min) * t_i / t_1));
+ *    a proposal equal to the current value moves by one instead (up if it can). The candidate is
+ *    accepted if its error E <= the current one, or if u < exp(-(E - E_cur) / t_i).
+ *  - random numbers: SplitMix64 from seed; u and the choices from its top 53 bits.
+ * trace (host, steps + 1 entries, or NULL): entry 0 the start, entry i the i-th candidate and
+ * whether it was accepted. *best receives *start with the lowest-error candidate's three
+ * parameters (the earliest on ties), *best_mse its error. X, y: as aiwcrf_fit (host or device). */
+typedef struct {
+    int32_t steps;                  /* candidates after the start (>= 0) */
+    int32_t trees_min, trees_max;   /* num.trees bounds (1 <= min <= max) */
+    int32_t mtry_min, mtry_max;     /* mtry bounds */
+    int32_t node_min, node_max;     /* min.node.size bounds */
+    int32_t reserved;               /* must be 0 */
+    double t0;                      /* initial temperature relative to the start's error (> 0) */
+    double cooling;                 /* temperature factor per step, (0, 1] */
+    uint64_t seed;
+} aiwcrf_tune_params;
+
+typedef struct {
+    int32_t num_trees, mtry, min_node_size;
+    int32_t accepted;               /* 1: the walk moved to this candidate */
+    double oob_mse;                 /* aiwcrf_oob_error's mean squared error */
+} aiwcrf_tune_step;
+
+int aiwcrf_tune_sa(const aiwcrf_tune_params *params, const aiwcrf_fit_params *start, const float *X,
+                   const int64_t *y, int64_t n_rows, int32_t n_features, void *cuda_stream,
+                   aiwcrf_tune_step *trace, aiwcrf_fit_params *best, double *best_mse);
+
 /* out[q] = floor((2 sums[q] + total_trees) / (2 total_trees)). */
 int aiwcrf_round_mean(const int64_t *sums, int64_t n, int64_t total_trees, int64_t *out,
                       void *cuda_stream);

@@ -36,6 +36,17 @@ class FitParams(C.Structure):
                 ("ctas_per_sm", C.c_int32), ("first_tree", C.c_int64)]
 
 
+class TuneParams(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("trees_min", C.c_int32), ("trees_max", C.c_int32), ("mtry_min", C.c_int32),
+                ("mtry_max", C.c_int32), ("node_min", C.c_int32), ("node_max", C.c_int32), ("reserved", C.c_int32),
+                ("t0", C.c_double), ("cooling", C.c_double), ("seed", C.c_uint64)]
+
+
+class TuneStep(C.Structure):
+    _fields_ = [("num_trees", C.c_int32), ("mtry", C.c_int32), ("min_node_size", C.c_int32),
+                ("accepted", C.c_int32), ("oob_mse", C.c_double)]
+
+
 class SurrogateParams(C.Structure):
     _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float),
                 ("beta2", C.c_float), ("eps", C.c_float), ("seed", C.c_uint64), ("n_devices", C.c_int32),
@@ -131,7 +142,7 @@ EXPORTS = ["aiwcrf_fit", "aiwcrf_fit_subsets", "aiwcrf_predict", "aiwcrf_predict
            "aiwcrf_server_refit", "aiwcrf_server_pause", "aiwcrf_server_stats", "aiwcrf_server_run_load",
            "aiwcrf_server_trace", "aiwcrf_server_destroy", "aiwcrf_select_device_gated",
            "aiwcrf_server_set_surrogate", "aiwcrf_server_submit_gated", "aiwcrf_server_wait_gated",
-           "aiwcrf_server_run_load_gated",
+           "aiwcrf_server_run_load_gated", "aiwcrf_tune_sa",
            "aiwcrf_fit_plan_create", "aiwcrf_fit_plan_run", "aiwcrf_fit_plan_tune", "aiwcrf_fit_plan_set_schedule",
            "aiwcrf_fit_plan_free", "aiwcrf_profile_classes", "aiwcrf_set_grower", "aiwcrf_debug_bounds"]
 
@@ -210,6 +221,8 @@ def load():
         L.aiwcrf_server_trace.argtypes = [_vp, _vp, C.c_int64, C.POINTER(C.c_int64), _vp, C.c_int64,
                                           C.POINTER(C.c_int64)]
         L.aiwcrf_server_set_surrogate.argtypes = [_vp, _vp, C.POINTER(GateParams)]
+        L.aiwcrf_tune_sa.argtypes = [C.POINTER(TuneParams), C.POINTER(FitParams), _vp, _vp, C.c_int64, C.c_int32, _vp,
+                                     _vp, C.POINTER(FitParams), C.POINTER(C.c_double)]
         L.aiwcrf_server_submit_gated.argtypes = [_vp, _vp, C.c_int32, C.c_int32, C.POINTER(C.c_int64)]
         L.aiwcrf_server_wait_gated.argtypes = [_vp, C.c_int64, C.c_int32, _vp, _vp, _vp, C.POINTER(C.c_int64)]
         L.aiwcrf_server_run_load_gated.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, _vp, _vp, C.c_int64, C.c_double,
@@ -669,6 +682,24 @@ def aiwcrf_set_grower(grower: int):
 def params(num_trees: int, mtry: int, min_node_size: int, max_depth: int = 0, seed: int = 156,
            bootstrap: bool = True, first_tree: int = 0, ctas_per_sm: int = 0) -> FitParams:
     return FitParams(num_trees, mtry, min_node_size, max_depth, seed, 1 if bootstrap else 0, ctas_per_sm, first_tree)
+
+
+def tune_params(steps=40, trees=(16, 512), mtry=(1, 32), node=(1, 20), t0=0.1, cooling=0.95,
+                seed=1) -> TuneParams:
+    return TuneParams(steps, trees[0], trees[1], mtry[0], mtry[1], node[0], node[1], 0, t0, cooling, seed)
+
+
+def aiwcrf_tune_sa(tp: TuneParams, start: FitParams, X, y, stream=None):
+    """Simulated-annealing tuning against the out-of-bag error (include/aiwcrf.h). Returns
+    (best FitParams, best OOB MSE, trace as a list of dicts)."""
+    F, N = _shape(X)
+    trace = (TuneStep * (tp.steps + 1))()
+    best = FitParams()
+    mse = C.c_double()
+    _check(load().aiwcrf_tune_sa(C.byref(tp), C.byref(start), _ptr(X), _ptr(y), N, F, _stream(stream), trace,
+                                 C.byref(best), C.byref(mse)))
+    steps = [{k: getattr(t, k) for k, _ in TuneStep._fields_} for t in trace]
+    return best, mse.value, steps
 
 
 def decode_forest(blob: bytes) -> dict:

@@ -18,7 +18,8 @@ LIB = os.path.join(HERE, "libaiwcrf.so")
 # the bounds-checking build (every gathered index and node id checked on the device)
 BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 LIB_DEBUG = os.path.join(HERE, "libaiwcrf_debug.so")
-SOURCES = ["fit.cu", "sort.cu", "predict.cu", "api.cu", "noalloc.cu", "mlp.cu", "surrogate.cu", "serve.cu", "gate.cu"]
+SOURCES = ["fit.cu", "sort.cu", "predict.cu", "api.cu", "noalloc.cu", "mlp.cu", "surrogate.cu", "serve.cu", "gate.cu",
+           "tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -126,6 +126,14 @@ def test_server_layouts_and_validation_without_gpu():
     t = C.c_int64()
     kf = np.zeros((F - 2, 1), np.float32)
     assert L.aiwcrf_server_set_surrogate(None, None, None) == -1
+    # the tuner checks its arguments before fitting
+    tp, best, mse = A.tune_params(), A.FitParams(), C.c_double()
+    assert L.aiwcrf_tune_sa(None, C.byref(fp), X.ctypes.data, y.ctypes.data, N, F, None, None, C.byref(best),
+                            C.byref(mse)) == -1
+    for badtp in (A.tune_params(trees=(0, 4)), A.tune_params(node=(3, 2)), A.tune_params(cooling=0.0)):
+        assert L.aiwcrf_tune_sa(C.byref(badtp), C.byref(fp), X.ctypes.data, y.ctypes.data, N, F, None, None,
+                                C.byref(best), C.byref(mse)) == -1
+    assert C.sizeof(A.TuneParams) == 56 and C.sizeof(A.TuneStep) == 24
     assert L.aiwcrf_server_submit_gated(None, kf.ctypes.data, 1, 0, C.byref(t)) == -1
     assert L.aiwcrf_server_wait_gated(None, 1, 0, None, None, None, None) == -1
     rep = A.LoadReport()
