@@ -11,6 +11,10 @@
 //  - every batch's device inputs and outputs come from a first-fit arena carved out of one
 //    allocation: a request is admitted into a batch only while its bytes fit the arena's free
 //    space, so the server's device footprint is fixed at creation;
+//  - gated requests (a surrogate resident beside the forest) share the batches: their kernels
+//    come first, go through the gate's steps (query expansion, surrogate, prefix variances,
+//    gate_kernel; gate.cu) and only those the gate sends back reach the selection kernel, whose
+//    CTAs for the others return at once; no host synchronisation inside a batch;
 //  - a refit thread fits new forests from the training rows plus appended rows on its own
 //    low-priority stream, as a background fit (one level-kernel CTA per SM, so that selection
 //    CTAs always find registers on every SM), and swaps them in; each batch holds a reference to the forest it was formed with,
