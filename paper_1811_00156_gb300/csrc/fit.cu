@@ -8,8 +8,10 @@
 //                      group: such rows fall on the same side of every threshold, so a tree
 //                      can carry one entry per group with the summed multiplicity and target.
 //                      Groups are ordered by a hash of their record.
-//   bootstrap_kernel   Philox draws per tree -> per-row multiplicities -> one entry
-//                      {row, sum w, sum w*y} per group that has an in-bag row
+//   boot_groups_kernel Philox draws per tree, each adding 1 and its row's y to the row's
+//                      group sums in shared memory -> one entry {row, sum w, sum w*y} per
+//                      group that has an in-bag row (bootstrap_kernel: the same through per-row
+//                      multiplicities, when the group sums do not fit shared memory)
 //   per depth d:
 //     level_big_kernel   one CTA per node with > 32 entries: mtry draw, shared-memory histogram
 //                        (sum w, sum w*y) per rank of every tried feature, block scan, exact
@@ -228,12 +230,17 @@ __global__ void group_offsets_kernel(const uint32_t *__restrict__ flags, const u
 // mark group starts, excl is their exclusive scan)
 __global__ void group_order_kernel(const uint32_t *__restrict__ rows, const uint32_t *__restrict__ flags,
                                    const uint32_t *__restrict__ excl, const int64_t *__restrict__ y, int64_t N,
-                                   int64_t *__restrict__ y_g, uint32_t *__restrict__ grp_of)
+                                   int64_t *__restrict__ y_g, uint32_t *__restrict__ grp_of, uint4 *__restrict__ rowrec)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
-    y_g[k] = y[rows[k]];
-    grp_of[k] = excl[k] + flags[k] - 1u;
+    const uint32_t row = rows[k];
+    const int64_t yr = y[row];
+    const uint32_t g = excl[k] + flags[k] - 1u;
+    y_g[k] = yr;
+    grp_of[k] = g;
+    // per row: y and its group, one 16-byte record (read by boot_groups_kernel's draws)
+    if (rowrec) rowrec[row] = make_uint4((uint32_t)(uint64_t)yr, (uint32_t)((uint64_t)yr >> 32), g, 0u);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -426,6 +433,128 @@ __global__ void __launch_bounds__(kBootThreads) bootstrap_kernel(BootArgs a)
         for (int w = 0; w < kBootThreads / 32; ++w) { sn += red_n[w]; ss += red_s[w]; }
         NodeRec r;
         // (a flagged overflow keeps the node inside its tree's slice; the fit then fails)
+        r.tree = (uint32_t)t; r.idx = 0u; r.start = 0u; r.len = (uint32_t)min((int64_t)running, a.row_cap);
+        r.n = (uint32_t)sn;
+        r.pad = 0u; r.S = ss;
+        a.root[t] = r;
+        if (running <= (uint32_t)kSmallNodeRows) a.small_list[atomicAdd(&a.counters[0], 1u)] = t;
+        else a.big_list[atomicAdd(&a.counters[1], 1u)] = t;
+    }
+}
+
+// The bootstrap with the draws summed per group directly (the fit's usual case: the groups'
+// sums and the in-bag bitmap fit shared memory). Each draw reads its row's 16-byte record
+// {y, group} and adds 1 and y to the group's shared-memory sums; no per-row counters and no
+// pass over the rows follow. Integer sums, so the entries equal bootstrap_kernel's.
+constexpr int kBootGThreads = 512;      // 40 registers: three CTAs per SM
+constexpr int kBootGIlp = 4;            // draws whose record loads a thread issues together
+constexpr int kBootGroupsSmemMax = 96 * 1024;      // at least two CTAs per SM
+#ifndef AIWCRF_BOOT_GROUPS
+#define AIWCRF_BOOT_GROUPS 1           // 0: always the per-row counters of bootstrap_kernel
+#endif
+
+__host__ __forceinline__ size_t boot_groups_smem(uint32_t G, int64_t inbag_words)
+{
+    return (size_t)G * 12u + (size_t)inbag_words * 4u;
+}
+
+__global__ void __launch_bounds__(kBootGThreads) boot_groups_kernel(BootArgs a, const uint4 *__restrict__ rowrec)
+{
+    extern __shared__ __align__(16) unsigned char boot_sm[];
+    __shared__ uint32_t warp_tmp[32];
+    __shared__ unsigned long long red_n[32];
+    __shared__ long long red_s[32];
+
+    const uint32_t G = a.G;
+    unsigned long long *gwy = reinterpret_cast<unsigned long long *>(boot_sm);     // G sums of y
+    uint32_t *gw = reinterpret_cast<uint32_t *>(gwy + G);                           // G draw counts
+    uint32_t *bits = gw + G;                                                        // in-bag bitmap
+    const int t = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t n = a.tree_pool_len[t];
+    const int64_t poff = a.tree_pool_off[t];
+    const int64_t nbits = a.inbag ? a.inbag_words : 0;
+
+    for (uint32_t g = tid; g < G; g += kBootGThreads) { gwy[g] = 0ull; gw[g] = 0u; }
+    for (int64_t k = tid; k < nbits; k += kBootGThreads) bits[k] = 0u;
+    __syncthreads();
+    const uint32_t tg = a.tree_rng[t];
+    const uint32_t nb4 = (n + 3u) / 4u;               // Philox blocks of four draws
+    constexpr int U = kBootGIlp / 4;                  // blocks per thread per round
+    for (uint32_t b0 = tid; b0 < nb4; b0 += kBootGThreads * U) {
+        uint32_t row[4 * U];
+        uint4 rec[4 * U];
+#pragma unroll
+        for (int v = 0; v < U; ++v) {           // all the round's record loads are issued together
+            const uint32_t b = b0 + (uint32_t)(v * kBootGThreads);
+            const uint4 u = philox10(make_uint4(tg, b, kDomBoot, 0u), a.seed_lo, a.seed_hi);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const uint32_t k = 4u * b + (uint32_t)w;
+                row[4 * v + w] = 0xFFFFFFFFu;
+                rec[4 * v + w] = make_uint4(0u, 0u, 0u, 0u);
+                if (b < nb4 && k < n) {
+                    const uint32_t j = __umulhi(uint4_word(u, w), n);
+                    row[4 * v + w] = AIWCRF_IDX(poff < 0 ? j : (uint32_t)a.sub_rows[poff + j], (uint32_t)a.N, kBoundRow);
+                    rec[4 * v + w] = __ldg(&rowrec[row[4 * v + w]]);
+                }
+            }
+        }
+#pragma unroll
+        for (int w = 0; w < 4 * U; ++w) {
+            if (row[w] != 0xFFFFFFFFu) {
+                const uint32_t g = AIWCRF_IDX(rec[w].z, G, kBoundRow);
+                atomicAdd(&gw[g], 1u);
+                // the 64-bit sum as two 32-bit shared atomics (low word, then the high word
+                // plus the low word's carry): a 64-bit shared atomic add costs more
+                uint32_t *h = reinterpret_cast<uint32_t *>(&gwy[g]);
+                const uint32_t old = atomicAdd(&h[0], rec[w].x);
+                const uint32_t hi = rec[w].y + ((old + rec[w].x < old) ? 1u : 0u);
+                if (hi) atomicAdd(&h[1], hi);
+                if (nbits) atomicOr(&bits[row[w] >> 5], 1u << (row[w] & 31u));
+            }
+        }
+    }
+    __syncthreads();
+    if (nbits) {
+        uint32_t *out_bits = a.inbag + (size_t)t * (size_t)a.inbag_words;
+        for (int64_t k = tid; k < nbits; k += kBootGThreads) out_bits[k] = bits[k];
+    }
+
+    // entries in group order: one per group with a draw
+    uint32_t running = 0;
+    unsigned long long acc_n = 0;
+    long long acc_s = 0;
+    Entry *out = a.rows_out + (size_t)t * (size_t)a.row_cap;
+    for (uint32_t g0 = 0; g0 < G; g0 += kBootGThreads) {
+        const uint32_t g = g0 + tid;
+        uint32_t sw = 0;
+        long long swy = 0;
+        if (g < G) { sw = gw[g]; swy = (long long)gwy[g]; }
+        uint32_t tot;
+        const uint32_t incl = block_incl_scan(sw > 0 ? 1u : 0u, warp_tmp, tot);
+        if (sw > 0) {
+            Entry en;
+            en.row = a.store_group ? g : a.grp_rows[a.grp_off[g]];
+            en.w = sw; en.wy = swy;
+            if ((int64_t)(running + incl - 1u) < a.row_cap) store_entry(&out[running + incl - 1u], en);
+            else atomicOr(a.err, kErrCapacity);
+            acc_n += sw;
+            acc_s += swy;
+        }
+        running += tot;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc_n += __shfl_xor_sync(kFull, acc_n, o);
+        acc_s += __shfl_xor_sync(kFull, acc_s, o);
+    }
+    if (lane == 0) { red_n[warp] = acc_n; red_s[warp] = acc_s; }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long sn = 0;
+        long long ss = 0;
+        for (int w = 0; w < kBootGThreads / 32; ++w) { sn += red_n[w]; ss += red_s[w]; }
+        NodeRec r;
         r.tree = (uint32_t)t; r.idx = 0u; r.start = 0u; r.len = (uint32_t)min((int64_t)running, a.row_cap);
         r.n = (uint32_t)sn;
         r.pad = 0u; r.S = ss;
@@ -2496,7 +2625,14 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     // the bootstrap's group-ordered pass: y in group order and every position's group
     int64_t *d_y_g = sc.get<int64_t>((size_t)N, &rc); if (rc) return rc;
     uint32_t *d_grp_of = sc.get<uint32_t>((size_t)N, &rc); if (rc) return rc;
-    group_order_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(vA, kB, vB, dy, N, d_y_g, d_grp_of);
+    // the bootstrap sums its draws per group in shared memory when the groups' sums and the
+    // in-bag bitmap fit there (it then reads one {y, group} record per drawn row)
+    const int64_t boot_inbag_words = d_sub_rows ? 0 : (N + 31) / 32;
+    const bool boot_groups = AIWCRF_BOOT_GROUPS && p.bootstrap &&
+                             boot_groups_smem(n_groups, boot_inbag_words) <= (size_t)kBootGroupsSmemMax;
+    uint4 *d_rowrec = nullptr;
+    if (boot_groups) { d_rowrec = sc.get<uint4>((size_t)N, &rc); if (rc) return rc; }
+    group_order_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(vA, kB, vB, dy, N, d_y_g, d_grp_of, d_rowrec);
     AIWCRF_LAUNCH_CHECK("group_order_kernel");
     sc.drop(d_R); sc.drop(kA); sc.drop(kB); sc.drop(vB); sc.drop(hist);
     row_cap = std::min<int64_t>(row_cap, (int64_t)n_groups);
@@ -2611,15 +2747,15 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         const uint32_t words = (uint32_t)((N + 3) / 4);
         uint32_t *gcnt = nullptr;
         int64_t gstride = 0;
-        if ((int)words > boot_smem_words) {
+        if (!boot_groups && (int)words > boot_smem_words) {
             gstride = words;
             gcnt = sc.get<uint32_t>((size_t)T * (size_t)words, &rc); if (rc) return rc;
         }
         // the group-ordered pass (counters in shared memory, per-group sums in a global scratch)
-        const bool grouped = !gcnt;
+        const bool grouped = !gcnt && !boot_groups;
         unsigned long long *d_gsum = nullptr;
         if (grouped) { d_gsum = sc.get<unsigned long long>((size_t)T * 2 * (size_t)n_groups, &rc); if (rc) return rc; }
-        const int smem_bytes = gcnt ? 0 : (int)words * 4;
+        const int smem_bytes = (gcnt || boot_groups) ? 0 : (int)words * 4;
         AIWCRF_CUDA(cudaFuncSetAttribute(bootstrap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          std::max(smem_bytes, 1)));
         BootArgs ba;
@@ -2637,8 +2773,16 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         ba.grp_of = grouped ? d_grp_of : nullptr;
         ba.gsum = d_gsum;
         prof_begin(s, kProfBoot);
-        bootstrap_kernel<<<(unsigned)T, kBootThreads, smem_bytes, s>>>(ba);
-        AIWCRF_LAUNCH_CHECK("bootstrap_kernel");
+        if (boot_groups) {
+            const size_t gsmem = boot_groups_smem(n_groups, boot_inbag_words);
+            AIWCRF_CUDA(cudaFuncSetAttribute(boot_groups_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             std::max((int)gsmem, 1)));
+            boot_groups_kernel<<<(unsigned)T, kBootGThreads, gsmem, s>>>(ba, d_rowrec);
+            AIWCRF_LAUNCH_CHECK("boot_groups_kernel");
+        } else {
+            bootstrap_kernel<<<(unsigned)T, kBootThreads, smem_bytes, s>>>(ba);
+            AIWCRF_LAUNCH_CHECK("bootstrap_kernel");
+        }
         prof_end(s, kProfBoot);
     }
 

@@ -129,7 +129,9 @@ __global__ void __launch_bounds__(kCodeThreads) code_queries_kernel(const float 
 #pragma unroll
             for (int u = 0; u < kCodeGroup; ++u) {
                 const int f = f0 + u;
-                x[u] = f < F ? __ldg(&Xq[(size_t)f * (size_t)Q + q]) : 0.0f;
+                // features are read once: streaming loads (evict first in L1 and L2) leave the
+                // codes written here resident in L2 for the key and walk kernels that read them
+                x[u] = f < F ? __ldcs(&Xq[(size_t)f * (size_t)Q + q]) : 0.0f;
                 const uint32_t n = f < F ? __ldg(&fcard[f]) : 0u;
                 lo[u] = x[u] != x[u] ? n : 0u;                      // NaN: past every value
                 len[u] = x[u] != x[u] ? 0u : n;
