@@ -116,7 +116,7 @@ void *pinned_scratch()
         ~Buf() { if (p) cudaFreeHost(p); }
     };
     static thread_local Buf b;
-    if (!b.p && cudaMallocHost(&b.p, 4096) != cudaSuccess) {
+    if (!b.p && cudaMallocHost(&b.p, kPinnedScratchBytes) != cudaSuccess) {
         cudaGetLastError();
         b.p = nullptr;
     }

@@ -50,6 +50,36 @@ inline int rank_bytes_for(uint32_t max_card)
     return max_card <= 256u ? 1 : (max_card <= 65536u ? 2 : 4);
 }
 
+// Small device-to-host reads (sizes, counts, error flags) staged through the host thread's
+// page-locked buffer, from byte 1,024 on (the level loop keeps its counts below that): the
+// copies are then asynchronous and one stream wait covers them all (a copy into pageable memory
+// waits by itself). Copies that do not fit go to their pageable destinations directly.
+struct HostReads {
+    struct Item { void *dst; const void *src; size_t bytes, off; };
+    Item items[8];
+    int n = 0;
+    size_t used = 1024;
+    void add(void *dst, const void *src, size_t bytes) { items[n++] = Item{dst, src, bytes, 0}; }
+    int run(cudaStream_t s)
+    {
+        unsigned char *pin = static_cast<unsigned char *>(pinned_scratch());
+        for (int i = 0; i < n; ++i) {
+            Item &it = items[i];
+            const size_t off = (used + 15) & ~(size_t)15;
+            const bool staged = pin && off + it.bytes <= kPinnedScratchBytes;
+            it.off = staged ? off : (size_t)-1;
+            if (staged) used = off + it.bytes;
+            const cudaError_t e = cudaMemcpyAsync(staged ? pin + off : it.dst, it.src, it.bytes, cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) return cuda_fail(e, "device-to-host read");
+        }
+        const cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "device-to-host read");
+        for (int i = 0; i < n; ++i)
+            if (items[i].off != (size_t)-1) std::memcpy(items[i].dst, pin + items[i].off, items[i].bytes);
+        return AIWCRF_OK;
+    }
+};
+
 struct Entry {            // one group of identical in-bag rows of one tree
     uint32_t row;         // a row of the group (all its rows have the same features)
     uint32_t w;           // summed bootstrap multiplicity
@@ -2400,6 +2430,7 @@ struct PackIn {
     int64_t slot_cap = 0;
     const uint32_t *d_levels = nullptr;   // when set, the level count is read here
     int grower = 1;                       // 1 level-synchronous, 2 tree-resident
+    const uint32_t *d_err = nullptr;      // when set, the growth's error flags: read with the sizes
 };
 
 // One forest per tree group, trees padded to an even node count (16-byte aligned); nodes placed
@@ -2411,12 +2442,18 @@ int package_forests(const PackIn &in, cudaStream_t s, std::vector<aiwcrf_forest 
     const int64_t T = in.T, Tper = in.Tper;
     const int32_t G = in.G, F = in.F;
     std::vector<uint32_t> h_tot((size_t)T);
-    AIWCRF_CUDA(cudaMemcpyAsync(h_tot.data(), in.tree_base, sizeof(uint32_t) * (size_t)T, cudaMemcpyDeviceToHost, s));
     GrowStats hs;
-    AIWCRF_CUDA(cudaMemcpyAsync(&hs, in.d_stats, sizeof(GrowStats), cudaMemcpyDeviceToHost, s));
     uint32_t h_levels = (uint32_t)in.levels;
-    if (in.d_levels) AIWCRF_CUDA(cudaMemcpyAsync(&h_levels, in.d_levels, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    AIWCRF_CUDA(cudaStreamSynchronize(s));
+    uint32_t h_err = 0;
+    {
+        HostReads hr;
+        hr.add(h_tot.data(), in.tree_base, sizeof(uint32_t) * (size_t)T);
+        hr.add(&hs, in.d_stats, sizeof(GrowStats));
+        if (in.d_levels) hr.add(&h_levels, in.d_levels, sizeof(uint32_t));
+        if (in.d_err) hr.add(&h_err, in.d_err, sizeof(uint32_t));
+        if ((rc = hr.run(s)) != AIWCRF_OK) return rc;
+    }
+    if (in.d_err && (rc = check_err_flags(h_err)) != AIWCRF_OK) return rc;     // before any size is used
 
     std::vector<aiwcrf_forest *> forests((size_t)G, nullptr);
     struct Guard {
@@ -2550,6 +2587,13 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     uint32_t *kB = sc.get<uint32_t>((size_t)F * (size_t)N + 1, &rc); if (rc) return rc;
     uint32_t *vB = sc.get<uint32_t>((size_t)F * (size_t)N + 1, &rc); if (rc) return rc;
     uint32_t *hist = sc.get<uint32_t>(radix_sort_hist_words(N, F), &rc); if (rc) return rc;
+    int64_t *d_pool_off = sc.get<int64_t>((size_t)T, &rc); if (rc) return rc;
+    uint32_t *d_pool_len = sc.get<uint32_t>((size_t)T, &rc); if (rc) return rc;
+    uint32_t *d_rng = sc.get<uint32_t>((size_t)T, &rc); if (rc) return rc;
+    LevelCounts *d_cnt = sc.get<LevelCounts>(1, &rc); if (rc) return rc;
+    LevelCounts c0;
+    c0.n_list[0][0] = c0.n_list[0][1] = c0.n_list[1][0] = c0.n_list[1][1] = 0u;
+    c0.C = (uint32_t)T; c0.levels = 0u; c0.packed_off = 0ull;
     uint32_t max_card = 0;
     {
         const unsigned yblocks = (unsigned)((N + 255) / 256);
@@ -2562,11 +2606,18 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         // the sort's histogram scratch is free again: it holds the chunk counts
         if ((rc = dense_ranks(kA, vA, N, F, hist, d_R, d_vals, d_card, s)) != AIWCRF_OK) return rc;
         prof_end(s, kProfRank);
+        // the per-tree pools and the first level's counts are staged while the presort runs
+        // (a copy from pageable memory costs host time, not a device wait)
+        AIWCRF_CUDA(cudaMemcpyAsync(d_pool_off, h_pool_off.data(), sizeof(int64_t) * (size_t)T, cudaMemcpyHostToDevice, s));
+        AIWCRF_CUDA(cudaMemcpyAsync(d_pool_len, h_pool_len.data(), sizeof(uint32_t) * (size_t)T, cudaMemcpyHostToDevice, s));
+        AIWCRF_CUDA(cudaMemcpyAsync(d_rng, h_rng.data(), sizeof(uint32_t) * (size_t)T, cudaMemcpyHostToDevice, s));
+        AIWCRF_CUDA(cudaMemcpyAsync(d_cnt, &c0, sizeof(LevelCounts), cudaMemcpyHostToDevice, s));
         std::vector<uint32_t> h_card((size_t)F);
         uint32_t h_err = 0;
-        AIWCRF_CUDA(cudaMemcpyAsync(h_card.data(), d_card, sizeof(uint32_t) * (size_t)F, cudaMemcpyDeviceToHost, s));
-        AIWCRF_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-        AIWCRF_CUDA(cudaStreamSynchronize(s));
+        HostReads hr;
+        hr.add(h_card.data(), d_card, sizeof(uint32_t) * (size_t)F);
+        hr.add(&h_err, d_err, sizeof(uint32_t));
+        if ((rc = hr.run(s)) != AIWCRF_OK) return rc;
         if ((rc = check_err_flags(h_err)) != AIWCRF_OK) return rc;
         max_card = *std::max_element(h_card.begin(), h_card.end());
     }
@@ -2605,8 +2656,9 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         count_launches(4);
         AIWCRF_LAUNCH_CHECK("grouping kernels");
         prof_end(s, kProfRank);
-        AIWCRF_CUDA(cudaMemcpyAsync(&n_groups, d_counters + 2, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-        AIWCRF_CUDA(cudaStreamSynchronize(s));
+        HostReads hr;
+        hr.add(&n_groups, d_counters + 2, sizeof(uint32_t));
+        if ((rc = hr.run(s)) != AIWCRF_OK) return rc;
     }
     const uint32_t *grp_rows = vA;            // rows in group order
     // the groups' representative rows in every column's order
@@ -2638,12 +2690,6 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     row_cap = std::min<int64_t>(row_cap, (int64_t)n_groups);
 
     // a2: bootstrap
-    int64_t *d_pool_off = sc.get<int64_t>((size_t)T, &rc); if (rc) return rc;
-    uint32_t *d_pool_len = sc.get<uint32_t>((size_t)T, &rc); if (rc) return rc;
-    uint32_t *d_rng = sc.get<uint32_t>((size_t)T, &rc); if (rc) return rc;
-    AIWCRF_CUDA(cudaMemcpyAsync(d_pool_off, h_pool_off.data(), sizeof(int64_t) * (size_t)T, cudaMemcpyHostToDevice, s));
-    AIWCRF_CUDA(cudaMemcpyAsync(d_pool_len, h_pool_len.data(), sizeof(uint32_t) * (size_t)T, cudaMemcpyHostToDevice, s));
-    AIWCRF_CUDA(cudaMemcpyAsync(d_rng, h_rng.data(), sizeof(uint32_t) * (size_t)T, cudaMemcpyHostToDevice, s));
 
     Entry *rows_a = sc.get<Entry>((size_t)T * (size_t)row_cap, &rc); if (rc) return rc;
     Entry *rows_b = sc.get<Entry>((size_t)T * (size_t)row_cap, &rc); if (rc) return rc;
@@ -2708,18 +2754,11 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         return AIWCRF_OK;
     };
 
-    LevelCounts *d_cnt = sc.get<LevelCounts>(1, &rc); if (rc) return rc;
     // in-bag bitmaps (forests fitted on all rows keep them for out-of-bag evaluation)
     const int64_t inbag_words = (N + 31) / 32;
     uint32_t *d_inbag = nullptr;
     if (!d_sub_rows) {
         d_inbag = sc.get<uint32_t>((size_t)T * (size_t)inbag_words, &rc); if (rc) return rc;
-    }
-    {
-        LevelCounts c0;
-        c0.n_list[0][0] = c0.n_list[0][1] = c0.n_list[1][0] = c0.n_list[1][1] = 0u;
-        c0.C = (uint32_t)T; c0.levels = 0u; c0.packed_off = 0ull;
-        AIWCRF_CUDA(cudaMemcpyAsync(d_cnt, &c0, sizeof(LevelCounts), cudaMemcpyHostToDevice, s));
     }
 
     // Tree-resident growth when every tree's entries fit in shared memory: one-byte ranks,
@@ -2839,10 +2878,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         tree_grow_kernel<<<(unsigned)grid, kTreeThreads, tree_smem, s>>>(ta);
         AIWCRF_LAUNCH_CHECK("tree_grow_kernel");
         prof_end(s, kProfTree);
-        uint32_t h_err = 0;
-        AIWCRF_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-        AIWCRF_CUDA(cudaStreamSynchronize(s));
-        if ((rc = check_err_flags(h_err)) != AIWCRF_OK) return rc;
+        // the error flags are read with the tree sizes (one wait instead of two)
         PackIn pin;
         pin.p = &p; pin.T = T; pin.Tper = Tper; pin.G = G; pin.N = N; pin.F = F; pin.device = device;
         pin.tree_base = counts; pin.d_stats = d_stats; pin.packed = nullptr; pin.packed_n = 0;
@@ -2850,6 +2886,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         pin.d_vals = d_vals; pin.d_card = d_card; pin.max_card = max_card; pin.rank_bytes = rank_bytes; pin.n_groups = n_groups;
         pin.slot_nodes = slot_nodes; pin.slot_cnodes = slot_cnodes; pin.slot_cap = node_cap; pin.d_levels = levels;
         pin.grower = AIWCRF_GROWER_TREE;
+        pin.d_err = d_err;
         rc = package_forests(pin, s, out);
         sc.release();
         if (rc == AIWCRF_OK) AIWCRF_CUDA(cudaStreamSynchronize(s));

@@ -476,6 +476,8 @@ int forest_build_compact(aiwcrf_forest *f, cudaStream_t s);
 // keep freed stream-ordered allocations cached in the device's default pool (once per device)
 void keep_pool_memory(int device);
 // a small pinned host buffer reused by the calling thread (at least 64 bytes)
+// a page-locked host buffer of kPinnedScratchBytes per host thread (null if it cannot be had)
+constexpr size_t kPinnedScratchBytes = 64 * 1024;
 void *pinned_scratch();
 }
 
