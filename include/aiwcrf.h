@@ -49,7 +49,9 @@ extern "C" {
  *   n_rows <= 4,194,303 (2^22 - 1); |y| <= 2^40 (|log10 t| < 256);
  *   n_features <= 128 (a column may hold as many distinct values as rows: ranks are stored in
  *   1, 2 or 4 bytes as the columns need);
- *   num_trees <= 1,048,576; a bootstrap multiplicity above 255 (probability ~ 1e-500) fails. */
+ *   num_trees <= 1,048,576; where a fit counts its draws per row in bytes (the groups' sums do
+ *   not fit shared memory), a bootstrap multiplicity above 255 (probability ~ 1e-500) fails;
+ *   where it sums them per group, any multiplicity is exact. */
 #define AIWCRF_MAX_ROWS       ((1 << 22) - 1)
 #define AIWCRF_MAX_FEATURES   128
 #define AIWCRF_MAX_ABS_Y      (1LL << 40)

@@ -937,7 +937,6 @@ __global__ void __launch_bounds__(1024) list_build_kernel(const uint32_t *__rest
 }
 
 constexpr int kBigThreads = 128;
-constexpr int kBigWarps = kBigThreads / 32;
 constexpr int kBigCtasPerSm = 6;       // resident CTAs per SM the big-node kernel is compiled for
 constexpr int kRowsPerIter = 4;   // rows per thread per pass: independent gathers in flight
 constexpr int kFeatChunk = 8;     // tried features whose ranks are loaded before their atomics
@@ -2577,13 +2576,20 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     AIWCRF_CUDA(cudaMemsetAsync(d_stats, 0, sizeof(GrowStats), s));
     AIWCRF_CUDA(cudaMemsetAsync(d_counters, 0, 4 * sizeof(uint32_t), s));
 
-    // a1: presort and rank
-    uint32_t *d_R = sc.get<uint32_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
-    float *d_vals = sc.get<float>((size_t)F * (size_t)N, &rc); if (rc) return rc;
-    uint32_t *d_card = sc.get<uint32_t>((size_t)F, &rc); if (rc) return rc;
+    // a1: presort and rank. The first kernels are enqueued before the rest of the scratch is
+    // allocated, so that the device works while the host allocates.
     // sort buffers (one spare word: the grouping's scan writes its total at [N])
     uint32_t *kA = sc.get<uint32_t>((size_t)F * (size_t)N + 1, &rc); if (rc) return rc;
     uint32_t *vA = sc.get<uint32_t>((size_t)F * (size_t)N + 1, &rc); if (rc) return rc;
+    const unsigned yblocks = (unsigned)((N + 255) / 256);
+    check_y_kernel<<<yblocks, 256, 0, s>>>(dy, N, d_err);
+    AIWCRF_LAUNCH_CHECK("check_y_kernel");
+    prof_begin(s, kProfRank);
+    key_init_kernel<<<dim3(yblocks, (unsigned)F), 256, 0, s>>>(dX, N, kA, vA, d_err);
+    AIWCRF_LAUNCH_CHECK("key_init_kernel");
+    uint32_t *d_R = sc.get<uint32_t>((size_t)F * (size_t)N, &rc); if (rc) return rc;
+    float *d_vals = sc.get<float>((size_t)F * (size_t)N, &rc); if (rc) return rc;
+    uint32_t *d_card = sc.get<uint32_t>((size_t)F, &rc); if (rc) return rc;
     uint32_t *kB = sc.get<uint32_t>((size_t)F * (size_t)N + 1, &rc); if (rc) return rc;
     uint32_t *vB = sc.get<uint32_t>((size_t)F * (size_t)N + 1, &rc); if (rc) return rc;
     uint32_t *hist = sc.get<uint32_t>(radix_sort_hist_words(N, F), &rc); if (rc) return rc;
@@ -2596,12 +2602,6 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     c0.C = (uint32_t)T; c0.levels = 0u; c0.packed_off = 0ull;
     uint32_t max_card = 0;
     {
-        const unsigned yblocks = (unsigned)((N + 255) / 256);
-        check_y_kernel<<<yblocks, 256, 0, s>>>(dy, N, d_err);
-        AIWCRF_LAUNCH_CHECK("check_y_kernel");
-        prof_begin(s, kProfRank);
-        key_init_kernel<<<dim3(yblocks, (unsigned)F), 256, 0, s>>>(dX, N, kA, vA, d_err);
-        AIWCRF_LAUNCH_CHECK("key_init_kernel");
         if ((rc = radix_sort_segments(kA, vA, kB, vB, N, F, N, hist, s)) != AIWCRF_OK) return rc;
         // the sort's histogram scratch is free again: it holds the chunk counts
         if ((rc = dense_ranks(kA, vA, N, F, hist, d_R, d_vals, d_card, s)) != AIWCRF_OK) return rc;
@@ -2638,6 +2638,9 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     // grouping of identical feature vectors
     uint32_t *grp_off = sc.get<uint32_t>((size_t)N + 1, &rc); if (rc) return rc;
     uint32_t n_groups = 0;
+    int64_t *d_y_g = nullptr;
+    uint32_t *d_grp_of = nullptr;
+    uint4 *d_rowrec = nullptr;
     {
         const unsigned rb = (unsigned)((N + 255) / 256);
         prof_begin(s, kProfRank);
@@ -2656,6 +2659,13 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         count_launches(4);
         AIWCRF_LAUNCH_CHECK("grouping kernels");
         prof_end(s, kProfRank);
+        // y in group order, every position's group and every row's {y, group} record (for the
+        // bootstrap), enqueued before the group count is read
+        d_y_g = sc.get<int64_t>((size_t)N, &rc); if (rc) return rc;
+        d_grp_of = sc.get<uint32_t>((size_t)N, &rc); if (rc) return rc;
+        if (AIWCRF_BOOT_GROUPS && p.bootstrap) { d_rowrec = sc.get<uint4>((size_t)N, &rc); if (rc) return rc; }
+        group_order_kernel<<<rb, 256, 0, s>>>(vA, kB, vB, dy, N, d_y_g, d_grp_of, d_rowrec);
+        AIWCRF_LAUNCH_CHECK("group_order_kernel");
         HostReads hr;
         hr.add(&n_groups, d_counters + 2, sizeof(uint32_t));
         if ((rc = hr.run(s)) != AIWCRF_OK) return rc;
@@ -2674,25 +2684,30 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         sc.drop(is_rep);
         sc.drop(d_ordF);
     }
-    // the bootstrap's group-ordered pass: y in group order and every position's group
-    int64_t *d_y_g = sc.get<int64_t>((size_t)N, &rc); if (rc) return rc;
-    uint32_t *d_grp_of = sc.get<uint32_t>((size_t)N, &rc); if (rc) return rc;
     // the bootstrap sums its draws per group in shared memory when the groups' sums and the
     // in-bag bitmap fit there (it then reads one {y, group} record per drawn row)
     const int64_t boot_inbag_words = d_sub_rows ? 0 : (N + 31) / 32;
-    const bool boot_groups = AIWCRF_BOOT_GROUPS && p.bootstrap &&
-                             boot_groups_smem(n_groups, boot_inbag_words) <= (size_t)kBootGroupsSmemMax;
-    uint4 *d_rowrec = nullptr;
-    if (boot_groups) { d_rowrec = sc.get<uint4>((size_t)N, &rc); if (rc) return rc; }
-    group_order_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(vA, kB, vB, dy, N, d_y_g, d_grp_of, d_rowrec);
-    AIWCRF_LAUNCH_CHECK("group_order_kernel");
+    const bool boot_groups = d_rowrec && boot_groups_smem(n_groups, boot_inbag_words) <= (size_t)kBootGroupsSmemMax;
     sc.drop(d_R); sc.drop(kA); sc.drop(kB); sc.drop(vB); sc.drop(hist);
     row_cap = std::min<int64_t>(row_cap, (int64_t)n_groups);
 
-    // a2: bootstrap
+    // Tree-resident growth when every tree's entries fit in shared memory: one-byte ranks,
+    // F <= 32, group ids and entry offsets in 16 bits
+    const int tree_bins = (int)std::max<uint32_t>(max_card, 1u);
+    const int tree_ecap = (int)std::max<int64_t>(row_cap, 1);
+    const int tree_big_cap = tree_ecap / (kSmallNodeRows + 1) + 1;
+    const size_t tree_smem = tree_smem_bytes(tree_ecap, tree_bins, tree_big_cap);
+    const bool tree_fits = rank8 && F <= 32 && n_groups <= 65535u && row_cap <= 65535 &&
+                           tree_smem + 1024 <= (size_t)max_smem_optin;
+    if (gmode == AIWCRF_GROWER_TREE && !tree_fits)
+        return fail(AIWCRF_E_LIMIT, "tree-resident growth needs one-byte ranks, F <= 32 and a tree's entries in shared memory");
+    const bool use_tree = tree_fits && !use_lists && gmode != AIWCRF_GROWER_LEVEL;
 
+    // a2: bootstrap (what it needs is allocated first; the growth's scratch is allocated while
+    // it runs)
     Entry *rows_a = sc.get<Entry>((size_t)T * (size_t)row_cap, &rc); if (rc) return rc;
-    Entry *rows_b = sc.get<Entry>((size_t)T * (size_t)row_cap, &rc); if (rc) return rc;
+    Entry *rows_b = nullptr;               // the level loop's second entry buffer
+    if (!use_tree) { rows_b = sc.get<Entry>((size_t)T * (size_t)row_cap, &rc); if (rc) return rc; }
 
     // Level-loop capacities. A depth holds at most C_max = T * row_cap nodes (each holds an
     // entry) and a tree at most 2 * row_cap - 1 nodes. Depths are enqueued in chunks without
@@ -2738,7 +2753,15 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         if (e2 != cudaSuccess) return cuda_fail(e2, "growing level tables");
         return AIWCRF_OK;
     };
-    if ((rc = grow_tables((size_t)std::max<int64_t>(T, 1024), 0)) != AIWCRF_OK) return rc;
+    if (use_tree) {
+        // the tree-resident grower reads only the roots and the bootstrap's list counts
+        nodes_cur = sc.get<NodeRec>((size_t)T, &rc); if (rc) return rc;
+        small_a = sc.get<int32_t>((size_t)T, &rc); if (rc) return rc;
+        big_a = sc.get<int32_t>((size_t)T, &rc); if (rc) return rc;
+        node_cap = (size_t)T;
+    } else if ((rc = grow_tables((size_t)std::max<int64_t>(T, 1024), 0)) != AIWCRF_OK) {
+        return rc;
+    }
     auto grow_packed = [&](size_t need, size_t keep) -> int {
         if (need <= packed_cap) return AIWCRF_OK;
         int rc2 = AIWCRF_OK;
@@ -2761,25 +2784,6 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         d_inbag = sc.get<uint32_t>((size_t)T * (size_t)inbag_words, &rc); if (rc) return rc;
     }
 
-    // Tree-resident growth when every tree's entries fit in shared memory: one-byte ranks,
-    // F <= 32, group ids and entry offsets in 16 bits
-    const int tree_bins = (int)std::max<uint32_t>(max_card, 1u);
-    const int tree_ecap = (int)std::max<int64_t>(row_cap, 1);
-    const int tree_big_cap = tree_ecap / (kSmallNodeRows + 1) + 1;
-    const size_t tree_smem = tree_smem_bytes(tree_ecap, tree_bins, tree_big_cap);
-    const bool tree_fits = rank8 && F <= 32 && n_groups <= 65535u && row_cap <= 65535 &&
-                           tree_smem + 1024 <= (size_t)max_smem_optin;
-    if (gmode == AIWCRF_GROWER_TREE && !tree_fits)
-        return fail(AIWCRF_E_LIMIT, "tree-resident growth needs one-byte ranks, F <= 32 and a tree's entries in shared memory");
-    const bool use_tree = tree_fits && !use_lists && gmode != AIWCRF_GROWER_LEVEL;
-    uint8_t *d_Rg = nullptr;
-    if (use_tree) {
-        d_Rg = sc.get<uint8_t>((size_t)n_groups * (size_t)F, &rc); if (rc) return rc;
-        const int64_t cells = (int64_t)n_groups * F;
-        group_records_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>((const uint8_t *)d_Rr, F, grp_off, grp_rows,
-                                                                           d_counters + 2, d_Rg);
-        AIWCRF_LAUNCH_CHECK("group_records_kernel");
-    }
 
     {
         const int boot_smem_words = std::min<int>((max_smem_optin - 2048) / 4, 56 * 1024);
@@ -2823,6 +2827,14 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
             AIWCRF_LAUNCH_CHECK("bootstrap_kernel");
         }
         prof_end(s, kProfBoot);
+    }
+    uint8_t *d_Rg = nullptr;
+    if (use_tree) {
+        d_Rg = sc.get<uint8_t>((size_t)n_groups * (size_t)F, &rc); if (rc) return rc;
+        const int64_t cells = (int64_t)n_groups * F;
+        group_records_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>((const uint8_t *)d_Rr, F, grp_off, grp_rows,
+                                                                           d_counters + 2, d_Rg);
+        AIWCRF_LAUNCH_CHECK("group_records_kernel");
     }
 
     // presorted lists of every tree: its entries by representative row, then per feature in rank order
