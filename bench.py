@@ -392,19 +392,32 @@ def run_ours(args):
 
     roofline = hbm_roofline(dom) if dom in ("predict", "level_big", "level_small") else issue_roofline(dom)
     if dom == "predict" and prof_dom.get("walk", (0, 0.0))[0]:
-        # the walk's real bound: shared-memory wavefronts (one per SM per cycle) and issue
+        # The predict call's dominant kernel is the walk, whose working set (tree slots and
+        # query codes) is in shared memory: it is bound by instruction issue and shared-memory
+        # wavefronts together. Reported against the issue peak, with the wavefront fraction and
+        # the whole call's HBM floor (136 B per query) beside it.
         n_w, ms_w = prof_dom["walk"]
         wf = ncu_counter("walk", "smem_wavefronts", source_sha("walk"))
         wi = ncu_counter("walk", "inst", source_sha("walk"))
         smem_peak = 152 * sm_mhz * 1e6 / 1e9                  # G wavefronts/s
-        roofline["walk"] = {"ms_per_launch": ms_w / n_w, "smem_wavefronts_per_launch": wf,
-                            "smem_peak_gwf_s": smem_peak, "inst_per_launch": wi,
-                            "issue_peak_tinst_s": 152 * 4 * sm_mhz * 1e6 / 1e12}
-        if wf:
-            roofline["walk"]["smem_achieved_gwf_s"] = wf / (ms_w / n_w / 1e3) / 1e9
-            roofline["smem_frac"] = roofline["walk"]["smem_achieved_gwf_s"] / smem_peak
-        if wi:
-            roofline["walk"]["issue_frac"] = wi / (ms_w / n_w / 1e3) / 1e12 / roofline["walk"]["issue_peak_tinst_s"]
+        issue_peak = 152 * 4 * sm_mhz * 1e6 / 1e12            # T warp-instructions/s
+        floor = roofline
+        if wi and wf:
+            t_w = ms_w / n_w / 1e3
+            roofline = {"kernel": "walk (predict4_kernel)", "bound": "alu", "unit": "T warp-inst/s",
+                        "achieved": wi / t_w / 1e12, "peak": issue_peak, "frac": wi / t_w / 1e12 / issue_peak,
+                        "peak_source": f"152 SMs x 4 issue slots x {sm_mhz:.0f} MHz (median sampled SM clock)",
+                        "traffic": ncu_traffic("walk", source_sha("walk")), "inst_per_launch": wi,
+                        "ms_per_launch": ms_w / n_w, "timing": timing,
+                        "smem": {"wavefronts_per_launch": wf, "achieved_gwf_s": wf / t_w / 1e9,
+                                 "peak_gwf_s": smem_peak, "frac": wf / t_w / 1e9 / smem_peak,
+                                 "peak_source": f"152 SMs x 1 wavefront x {sm_mhz:.0f} MHz"},
+                        "hbm_floor": floor}
+            roofline["smem_frac"] = roofline["smem"]["frac"]
+        else:
+            # counters not taken on these sources: the call's HBM floor alone
+            roofline["walk"] = {"ms_per_launch": ms_w / n_w, "smem_peak_gwf_s": smem_peak,
+                                "issue_peak_tinst_s": issue_peak}
     roofline_fit = (issue_roofline(dom_fit) if dom_fit == "tree" else hbm_roofline(dom_fit))
 
     out = {"metric": METRIC, "value": value, "unit": ROWS_TREES_UNIT, "n_gpus": world, "steps": K,
