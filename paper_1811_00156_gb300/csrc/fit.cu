@@ -647,6 +647,9 @@ __device__ __forceinline__ bool node_stops(const LevelArgs &a, const NodeRec &nd
     return nd.n <= (uint32_t)a.min_node || (a.max_depth > 0 && level_depth(a) >= a.max_depth);
 }
 
+#ifndef AIWCRF_MTRY_REDUX
+#define AIWCRF_MTRY_REDUX 1            // 1: the mtry smallest keys by warp min-reductions
+#endif
 // a3: the tried features of node (tree, depth, idx). Lane l of the warp evaluates the keys of
 // features l, l+32, ...; feature f is tried iff fewer than mtry features have a smaller
 // (key, index). Result: bit (f & 31) of mask[f >> 5].
@@ -672,6 +675,20 @@ __device__ __forceinline__ void warp_mtry_s(int F, int mtry, uint32_t depth, uin
         return;
     }
     if (nch == 1) {
+#if AIWCRF_MTRY_REDUX
+        // F <= 32: mtry rounds, each taking the smallest key not yet taken (the lowest lane on
+        // a tie: lanes >= F hold 0xFFFFFFFF and come after every feature of the same key)
+        uint32_t k = key[0], sel = 0u;
+        bool taken = false;
+        for (int r = 0; r < mtry; ++r) {
+            const uint32_t mn = __reduce_min_sync(kFull, k);
+            const uint32_t who = (uint32_t)__ffs(__ballot_sync(kFull, !taken && k == mn)) - 1u;
+            sel |= 1u << who;
+            if ((uint32_t)lane == who) { taken = true; k = 0xFFFFFFFFu; }
+        }
+        mask[0] = sel;
+        return;
+#endif
         // F <= 32: one key per lane; lanes >= F hold 0xFFFFFFFF, which never ranks below a
         // feature's key (on an equal key the higher index loses)
         uint32_t cnt0 = 0u;
@@ -1495,11 +1512,15 @@ struct TNode {            // an active node of a CTA's tree at the current depth
 };
 static_assert(sizeof(TNode) == 24, "TNode layout");
 
+// a group's rank record in the tree-resident grower: one byte per feature, padded to 32 bytes
+// (the grower needs F <= 32; a record is one 32-byte sector)
+constexpr int kRecBytes = 32;
+
 struct TreeArgs {
     const Entry *rows;            // bootstrap entries (row = group id), tree t at t * row_cap
     const NodeRec *root;          // bootstrap root record per tree (entry count, n, S)
     int64_t row_cap;
-    const uint8_t *Rg;            // group-major rank records [groups][F]
+    const uint8_t *Rg;            // group-major rank records [groups][kRecBytes] (F <= 32, zero padded)
     const float *vals;            // rank -> value tables [F][N]
     int64_t N;
     const uint32_t *card;         // values per feature (<= bins)
@@ -1654,7 +1675,7 @@ __device__ __forceinline__ void tree_small_node(const TreeArgs &a, const TreeSme
         const int ei = AIWCRF_IDX(ix[nd.start + pos], a.ecap, kBoundRow);
         ew = sm.w[ei]; ewy = sm.wy[ei]; eg = sm.g[ei];
     }
-    const uint8_t *rec = a.Rg + (size_t)AIWCRF_IDX(eg, a.n_groups, kBoundRow) * (size_t)a.F;
+    const uint8_t *rec = a.Rg + (size_t)AIWCRF_IDX(eg, a.n_groups, kBoundRow) * kRecBytes;
 
     uint32_t mask[4];
     warp_mtry_s(a.F, a.mtry, depth, a.seed_lo, a.seed_hi, tg, nd.idx, mask);
@@ -1714,10 +1735,10 @@ __device__ __forceinline__ void tree_small_node(const TreeArgs &a, const TreeSme
         return;
     }
     // partition: entry i on lane i
+    // (lane i < len holds entry i: segment 0, position i, and that entry's record)
     const bool lv = lane < len;
     const int el = lv ? AIWCRF_IDX(ix[nd.start + lane], a.ecap, kBoundRow) : 0;
-    const uint32_t rk =
-        lv ? (uint32_t)__ldg(&a.Rg[(size_t)AIWCRF_IDX(sm.g[el], a.n_groups, kBoundRow) * (size_t)a.F + best.f]) : kRankSentinel;
+    const uint32_t rk = lv ? (uint32_t)__ldg(&rec[best.f]) : kRankSentinel;
     const bool left = lv && rk <= best.r;
     const uint32_t bl = __ballot_sync(kFull, left), bv = __ballot_sync(kFull, lv);
     const uint32_t lenL = __popc(bl), lt = lanemask_lt();
@@ -1735,11 +1756,12 @@ __device__ __forceinline__ void tree_small_node(const TreeArgs &a, const TreeSme
 // Work item (big node, k-th tried feature): a warp-private histogram over the feature's ranks,
 // its scan, and the best candidate of the feature.
 __device__ __forceinline__ void tree_big_item(const TreeArgs &a, const TreeSmem &sm, const uint16_t *ix, const TNode &nd,
-                                              uint32_t tried, int k, uint32_t *bins, Cand *out, int lane)
+                                              uint32_t tried, int k, uint32_t *bins, Cand *out, int lane,
+                                              uint32_t card_lane)
 {
     uint32_t mask[4] = {tried, 0u, 0u, 0u};
     const int f = nth_feature(mask, k);
-    const int card = (int)__ldg(&a.card[f]);
+    const int card = (int)__shfl_sync(kFull, card_lane, f);       // lane f holds feature f's value count
     uint32_t *bw = bins, *blo = bins + a.bins;
     int32_t *bhi = reinterpret_cast<int32_t *>(bins + 2 * a.bins);
     for (int b = lane; b < card; b += 32) { bw[b] = 0u; blo[b] = 0u; bhi[b] = 0; }
@@ -1759,7 +1781,7 @@ __device__ __forceinline__ void tree_big_item(const TreeArgs &a, const TreeSmem 
                 wv[u] = sm.w[e];
                 lov[u] = (uint32_t)(uint64_t)y;
                 hiv[u] = (int32_t)(y >> 32);
-                rk[u] = AIWCRF_IDX((uint32_t)__ldg(&Rf[(size_t)AIWCRF_IDX(sm.g[e], a.n_groups, kBoundRow) * (size_t)a.F]),
+                rk[u] = AIWCRF_IDX((uint32_t)__ldg(&Rf[(size_t)AIWCRF_IDX(sm.g[e], a.n_groups, kBoundRow) * kRecBytes]),
                                    (uint32_t)card, kBoundBin);
             }
         }
@@ -1832,7 +1854,7 @@ __device__ __forceinline__ void tree_big_split(const TreeArgs &a, const TreeSmem
         for (int u = 0; u < kTreeIlp; ++u) {
             const int i = base + u * 32 + lane;
             rk[u] = i < len ? (uint32_t)__ldg(&Rf[(size_t)AIWCRF_IDX(sm.g[AIWCRF_IDX(ix[nd.start + i], a.ecap, kBoundRow)],
-                                                                     a.n_groups, kBoundRow) * (size_t)a.F])
+                                                                     a.n_groups, kBoundRow) * kRecBytes])
                             : kRankSentinel;
         }
 #pragma unroll
@@ -1886,7 +1908,11 @@ __global__ void __launch_bounds__(kTreeThreads, kTreeCtasPerSm) tree_grow_kernel
     Cand *const cands = a.cands + (size_t)blockIdx.x * (size_t)a.big_cap * 32;
     uint32_t *const wbins = sm.bins + (size_t)warp * (size_t)a.bins * 3;
     const int m = a.mtry < a.F ? a.mtry : a.F;
-    unsigned long long v[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+    const uint32_t card_lane = lane < a.F ? __ldg(&a.card[lane]) : 0u;   // F <= 32 here
+    // fit counters: 32-bit per thread within a tree, folded into per-warp 64-bit sums in
+    // shared memory after each tree (fewer live registers than 64-bit per-thread sums)
+    uint32_t v[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+    if (lane < 6) red[lane][warp] = 0ull;
     uint32_t max_levels = 0u;
 
     for (int t = blockIdx.x; t < a.T; t += gridDim.x) {
@@ -1937,7 +1963,8 @@ __global__ void __launch_bounds__(kTreeThreads, kTreeCtasPerSm) tree_grow_kernel
                 if (j < nb * (uint32_t)m) {
                     const uint32_t bi = j / (uint32_t)m, k = j - bi * (uint32_t)m;
                     const TNode nd = cn[AIWCRF_IDX(big[bi], a.ecap, kBoundNode)];
-                    tree_big_item(a, sm, ix, nd, sm.big_mask[bi], (int)k, wbins, &cands[(size_t)bi * 32 + k], lane);
+                    tree_big_item(a, sm, ix, nd, sm.big_mask[bi], (int)k, wbins, &cands[(size_t)bi * 32 + k], lane,
+                                  card_lane);
                 } else {
                     const uint32_t i = j - nb * (uint32_t)m;
                     const TNode nd = cn[i];
@@ -2016,15 +2043,14 @@ __global__ void __launch_bounds__(kTreeThreads, kTreeCtasPerSm) tree_grow_kernel
         }
         if (tid == 0) a.out_count[t] = base;
         max_levels = max(max_levels, depth);
-    }
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
+        for (int k = 0; k < 6; ++k) {
+            unsigned long long x = v[k];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], o);
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) red[k][warp] = v[k];
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+            if (lane == 0) red[k][warp] += x;
+            v[k] = 0u;
+        }
     }
     __syncthreads();
     if (tid < 6) {
@@ -2035,15 +2061,15 @@ __global__ void __launch_bounds__(kTreeThreads, kTreeCtasPerSm) tree_grow_kernel
     if (tid == 0 && max_levels) atomicMax(a.levels, max_levels);
 }
 
-// Rg[g][f] = the rank record of group g (all its rows share it)
+// Rg[g][f] = the rank record of group g (all its rows share it), kRecBytes per group, zero past F
 __global__ void group_records_kernel(const uint8_t *__restrict__ Rr, int F, const uint32_t *__restrict__ grp_off,
                                      const uint32_t *__restrict__ grp_rows, const uint32_t *n_groups, uint8_t *__restrict__ Rg)
 {
     const uint32_t G = *n_groups;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)G * F) return;
-    const uint32_t g = (uint32_t)(i / F), f = (uint32_t)(i - (int64_t)g * F);
-    Rg[i] = Rr[(size_t)grp_rows[grp_off[g]] * (size_t)F + f];
+    if (i >= (int64_t)G * kRecBytes) return;
+    const uint32_t g = (uint32_t)(i / kRecBytes), f = (uint32_t)(i - (int64_t)g * kRecBytes);
+    Rg[i] = (int)f < F ? Rr[(size_t)grp_rows[grp_off[g]] * (size_t)F + f] : (uint8_t)0;
 }
 
 // copy each tree's nodes from its output slot into the forest (and pad an odd count)
@@ -2830,8 +2856,8 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     }
     uint8_t *d_Rg = nullptr;
     if (use_tree) {
-        d_Rg = sc.get<uint8_t>((size_t)n_groups * (size_t)F, &rc); if (rc) return rc;
-        const int64_t cells = (int64_t)n_groups * F;
+        d_Rg = sc.get<uint8_t>((size_t)n_groups * kRecBytes, &rc); if (rc) return rc;
+        const int64_t cells = (int64_t)n_groups * kRecBytes;
         group_records_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>((const uint8_t *)d_Rr, F, grp_off, grp_rows,
                                                                            d_counters + 2, d_Rg);
         AIWCRF_LAUNCH_CHECK("group_records_kernel");
