@@ -1521,6 +1521,8 @@ struct TreeArgs {
     const NodeRec *root;          // bootstrap root record per tree (entry count, n, S)
     int64_t row_cap;
     const uint8_t *Rg;            // group-major rank records [groups][kRecBytes] (F <= 32, zero padded)
+    const uint8_t *RgT;           // the same ranks feature-major [F][groups] (a big item's gathers
+                                  // for one feature then stay within groups bytes)
     const float *vals;            // rank -> value tables [F][N]
     int64_t N;
     const uint32_t *card;         // values per feature (<= bins)
@@ -1767,7 +1769,7 @@ __device__ __forceinline__ void tree_big_item(const TreeArgs &a, const TreeSmem 
     for (int b = lane; b < card; b += 32) { bw[b] = 0u; blo[b] = 0u; bhi[b] = 0; }
     __syncwarp();
     const int len = nd.len;
-    const uint8_t *Rf = a.Rg + f;
+    const uint8_t *Rf = a.RgT + (size_t)f * a.n_groups;          // this feature's ranks, by group
     for (int base = 0; base < len; base += 32 * kTreeIlp) {
         uint32_t rk[kTreeIlp], wv[kTreeIlp], lov[kTreeIlp];
         int32_t hiv[kTreeIlp];
@@ -1781,7 +1783,7 @@ __device__ __forceinline__ void tree_big_item(const TreeArgs &a, const TreeSmem 
                 wv[u] = sm.w[e];
                 lov[u] = (uint32_t)(uint64_t)y;
                 hiv[u] = (int32_t)(y >> 32);
-                rk[u] = AIWCRF_IDX((uint32_t)__ldg(&Rf[(size_t)AIWCRF_IDX(sm.g[e], a.n_groups, kBoundRow) * kRecBytes]),
+                rk[u] = AIWCRF_IDX((uint32_t)__ldg(&Rf[AIWCRF_IDX(sm.g[e], a.n_groups, kBoundRow)]),
                                    (uint32_t)card, kBoundBin);
             }
         }
@@ -1846,7 +1848,7 @@ __device__ __forceinline__ void tree_big_split(const TreeArgs &a, const TreeSmem
         return;
     }
     const int len = nd.len;
-    const uint8_t *Rf = a.Rg + c.f;
+    const uint8_t *Rf = a.RgT + (size_t)c.f * a.n_groups;
     uint32_t cnt = 0u;
     for (int base = 0; base < len; base += 32 * kTreeIlp) {
         uint32_t rk[kTreeIlp];
@@ -1854,7 +1856,7 @@ __device__ __forceinline__ void tree_big_split(const TreeArgs &a, const TreeSmem
         for (int u = 0; u < kTreeIlp; ++u) {
             const int i = base + u * 32 + lane;
             rk[u] = i < len ? (uint32_t)__ldg(&Rf[(size_t)AIWCRF_IDX(sm.g[AIWCRF_IDX(ix[nd.start + i], a.ecap, kBoundRow)],
-                                                                     a.n_groups, kBoundRow) * kRecBytes])
+                                                                     a.n_groups, kBoundRow)])
                             : kRankSentinel;
         }
 #pragma unroll
@@ -2061,15 +2063,19 @@ __global__ void __launch_bounds__(kTreeThreads, kTreeCtasPerSm) tree_grow_kernel
     if (tid == 0 && max_levels) atomicMax(a.levels, max_levels);
 }
 
-// Rg[g][f] = the rank record of group g (all its rows share it), kRecBytes per group, zero past F
+// Rg[g][f] = the rank record of group g (all its rows share it), kRecBytes per group, zero past F;
+// RgT[f][g] the same ranks feature-major
 __global__ void group_records_kernel(const uint8_t *__restrict__ Rr, int F, const uint32_t *__restrict__ grp_off,
-                                     const uint32_t *__restrict__ grp_rows, const uint32_t *n_groups, uint8_t *__restrict__ Rg)
+                                     const uint32_t *__restrict__ grp_rows, const uint32_t *n_groups, uint8_t *__restrict__ Rg,
+                                     uint8_t *__restrict__ RgT)
 {
     const uint32_t G = *n_groups;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)G * kRecBytes) return;
     const uint32_t g = (uint32_t)(i / kRecBytes), f = (uint32_t)(i - (int64_t)g * kRecBytes);
-    Rg[i] = (int)f < F ? Rr[(size_t)grp_rows[grp_off[g]] * (size_t)F + f] : (uint8_t)0;
+    const uint8_t r = (int)f < F ? Rr[(size_t)grp_rows[grp_off[g]] * (size_t)F + f] : (uint8_t)0;
+    Rg[i] = r;
+    if ((int)f < F) RgT[(size_t)f * G + g] = r;
 }
 
 // copy each tree's nodes from its output slot into the forest (and pad an odd count)
@@ -2854,12 +2860,13 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         }
         prof_end(s, kProfBoot);
     }
-    uint8_t *d_Rg = nullptr;
+    uint8_t *d_Rg = nullptr, *d_RgT = nullptr;
     if (use_tree) {
         d_Rg = sc.get<uint8_t>((size_t)n_groups * kRecBytes, &rc); if (rc) return rc;
+        d_RgT = sc.get<uint8_t>((size_t)n_groups * (size_t)F, &rc); if (rc) return rc;
         const int64_t cells = (int64_t)n_groups * kRecBytes;
         group_records_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>((const uint8_t *)d_Rr, F, grp_off, grp_rows,
-                                                                           d_counters + 2, d_Rg);
+                                                                           d_counters + 2, d_Rg, d_RgT);
         AIWCRF_LAUNCH_CHECK("group_records_kernel");
     }
 
@@ -2904,7 +2911,7 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
         uint32_t *levels = counts + T;
         AIWCRF_CUDA(cudaMemsetAsync(levels, 0, sizeof(uint32_t), s));
         TreeArgs ta;
-        ta.rows = rows_a; ta.root = nodes_cur; ta.row_cap = row_cap; ta.Rg = d_Rg; ta.vals = d_vals; ta.N = N;
+        ta.rows = rows_a; ta.root = nodes_cur; ta.row_cap = row_cap; ta.Rg = d_Rg; ta.RgT = d_RgT; ta.vals = d_vals; ta.N = N;
         ta.card = d_card; ta.tree_rng = d_rng; ta.n_groups = n_groups; ta.T = (int)T; ta.F = F; ta.mtry = p.mtry;
         ta.min_node = p.min_node_size; ta.max_depth = p.max_depth;
         ta.seed_lo = (uint32_t)p.seed; ta.seed_hi = (uint32_t)(p.seed >> 32);
