@@ -1895,6 +1895,87 @@ __device__ __forceinline__ void tree_big_split(const TreeArgs &a, const TreeSmem
     }
 }
 
+// Phase B when the depth has fewer big nodes than warps: the W = warps / nb warps of a node
+// split its entries into W consecutive chunks; each flags and counts its chunk, the counts meet
+// in shared memory across one CTA barrier, and each writes its chunk's entries after the left
+// (or right) entries of the chunks before it: the same stable partition as one warp's.
+// Every warp of the CTA calls this once (it holds the depth's one barrier).
+__device__ __forceinline__ void tree_big_split_w(const TreeArgs &a, const TreeSmem &sm, const uint16_t *ix, uint16_t *ox,
+                                                 const TNode *cn, const uint16_t *big, uint32_t nb, int m,
+                                                 const Cand *cands, SplitRes *res, uint32_t *counts, int warp, int lane)
+{
+    const uint32_t W = (uint32_t)kTreeWarps / nb, bi = (uint32_t)warp / W, q = (uint32_t)warp % W;
+    const bool act = bi < nb;
+    Cand c = cand_none();
+    TNode nd;
+    uint32_t i = 0u, c0 = 0u, c1 = 0u, cnt = 0u;
+    if (act) {
+        i = AIWCRF_IDX(big[bi], a.ecap, kBoundNode);
+        nd = cn[i];
+        c = lane < m ? cands[(size_t)bi * 32 + lane] : cand_none();
+        c = warp_best(c, nd.n, nd.S);                   // the same in every warp of the node
+        if (c.h >= 0.0f) {
+            const uint32_t len = nd.len, chunk = ((len + W - 1u) / W + 31u) & ~31u;
+            c0 = min(len, q * chunk);
+            c1 = min(len, c0 + chunk);
+            const uint8_t *Rf = a.RgT + (size_t)c.f * a.n_groups;
+            for (uint32_t base = c0; base < c1; base += 32u * kTreeIlp) {
+                uint32_t rk[kTreeIlp];
+#pragma unroll
+                for (int u = 0; u < kTreeIlp; ++u) {
+                    const uint32_t e = base + 32u * u + (uint32_t)lane;
+                    rk[u] = e < c1 ? (uint32_t)__ldg(&Rf[AIWCRF_IDX(sm.g[AIWCRF_IDX(ix[nd.start + e], a.ecap, kBoundRow)],
+                                                                    a.n_groups, kBoundRow)])
+                                   : kRankSentinel;
+                }
+#pragma unroll
+                for (int u = 0; u < kTreeIlp; ++u) {
+                    const uint32_t e = base + 32u * u + (uint32_t)lane;
+                    if (e < c1) {
+                        const bool l = rk[u] <= c.r;
+                        sm.flag[nd.start + e] = l ? 1 : 0;
+                        cnt += l ? 1u : 0u;
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
+        } else if (q == 0 && lane == 0) {
+            write_leaf(&res[i], 0, -1, 0);
+        }
+    }
+    if (lane == 0) counts[warp] = cnt;
+    __syncthreads();
+    if (!act || c.h < 0.0f) return;
+    uint32_t lenL = 0u, offL = 0u;
+    for (uint32_t k = 0; k < W; ++k) {
+        const uint32_t ck = counts[bi * W + k];
+        lenL += ck;
+        if (k < q) offL += ck;
+    }
+    const uint32_t lt = lanemask_lt();
+    uint32_t run_l = offL, run_r = c0 - offL;           // the chunks before this one hold c0 entries
+    for (uint32_t b0 = c0; b0 < c1; b0 += 32u) {
+        const uint32_t e = b0 + (uint32_t)lane;
+        const bool v = e < c1;
+        const bool l = v && sm.flag[nd.start + e];
+        const uint32_t bl = __ballot_sync(kFull, l), bv = __ballot_sync(kFull, v);
+        if (v) {
+            const uint32_t p = l ? run_l + __popc(bl & lt) : lenL + run_r + __popc(bv & ~bl & lt);
+            ox[nd.start + AIWCRF_IDX(p, (uint32_t)nd.len, kBoundOut)] = ix[nd.start + e];
+        }
+        run_l += __popc(bl);
+        run_r += __popc(bv & ~bl);
+    }
+    if (q == 0 && lane == 0) {
+        SplitRes sr;
+        sr.feature = c.f; sr.rank = c.r;
+        sr.thr_bits = 0u;                                   // looked up where the node is encoded
+        sr.nL = c.nL; sr.lenL = lenL; sr.pad = 0u; sr.v = c.SL;
+        res[i] = sr;
+    }
+}
+
 __global__ void __launch_bounds__(kTreeThreads, kTreeCtasPerSm) tree_grow_kernel(TreeArgs a)
 {
     extern __shared__ __align__(16) unsigned char tree_sm[];
@@ -1981,10 +2062,15 @@ __global__ void __launch_bounds__(kTreeThreads, kTreeCtasPerSm) tree_grow_kernel
 #endif
             }
             __syncthreads();
-            // B: big nodes' decisions and partitions
-            for (uint32_t bi = (uint32_t)warp; bi < nb; bi += kTreeWarps) {
-                const uint32_t i = AIWCRF_IDX(big[bi], a.ecap, kBoundNode);
-                tree_big_split(a, sm, ix, ox, cn[i], m, &cands[(size_t)bi * 32], &res[i], lane);
+            // B: big nodes' decisions and partitions (a node per warp, or several warps per
+            // node when the depth has fewer big nodes than warps)
+            if (nb > 0u && nb < (uint32_t)kTreeWarps) {
+                tree_big_split_w(a, sm, ix, ox, cn, big, nb, m, cands, res, warp_tmp, warp, lane);
+            } else {
+                for (uint32_t bi = (uint32_t)warp; bi < nb; bi += kTreeWarps) {
+                    const uint32_t i = AIWCRF_IDX(big[bi], a.ecap, kBoundNode);
+                    tree_big_split(a, sm, ix, ox, cn[i], m, &cands[(size_t)bi * 32], &res[i], lane);
+                }
             }
             __syncthreads();
             // C: number the children, encode every node, list the next depth
