@@ -492,7 +492,8 @@ def e2e(A, wl, Xq_h, kfeat_h, params, devices, world, dev, steps):
     d2h = pred.nbytes + best.nbytes + selp.nbytes
     return {"value": wl.n_rows * params.num_trees * world * steps / secs, "unit": ROWS_TREES_UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * secs / steps,
-            "steps": steps, "note": "host clock around fit + predict + select with pinned host arrays"}
+            "steps": steps, "note": "host clock around fit + predict + select with pinned host arrays (X, y staged by "
+                                     "the library; the query features read in place by the coding kernel)"}
 
 
 def fit_graph_report(A, params, X, y, stats, steps: int = 5):

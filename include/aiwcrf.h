@@ -115,7 +115,9 @@ int aiwcrf_fit_subsets(const aiwcrf_fit_params *params, const float *X, const in
                        const int32_t *subset_rows, int32_t n_subsets, void *cuda_stream,
                        aiwcrf_forest **out);
 
-/* Predict (Sec. I, Sec. V). Xq: F x Q column-major float32. out_pred[q] = floor((2P + T)/(2T))
+/* Predict (Sec. I, Sec. V). Xq: F x Q column-major float32; page-locked host memory is read in
+ * place by the device (no staging copy) and must stay unchanged until the stream has passed
+ * the call, pageable host memory is copied as usual. out_pred[q] = floor((2P + T)/(2T))
  * with P the exact sum of the T leaf values reached (x <= threshold goes left; a NaN feature
  * goes right). out_var (or NULL): per query two uint64 words (low, high) of the exact
  * unsigned 128-bit V = T * sum(v^2) - P^2 (T^2 times the ensemble variance). */

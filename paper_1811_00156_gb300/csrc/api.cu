@@ -219,12 +219,29 @@ struct InArg {
     ~InArg() { if (owned) cudaFreeAsync(owned, s); }
 };
 
-int stage_in(InArg &a, const void *p, size_t bytes, int device, cudaStream_t s, const char *name)
+// The device address of page-locked host memory the device can read in place, or null.
+const void *mapped_host(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+// read_in_place: an input that one kernel streams through once may be read by the device
+// straight from page-locked host memory (no staging buffer, no separate copy)
+int stage_in(InArg &a, const void *p, size_t bytes, int device, cudaStream_t s, const char *name,
+             bool read_in_place = false)
 {
     a.s = s;
     const PtrKind k = classify(p, device);
     if (k == kPtrBad) return fail(AIWCRF_E_BAD_POINTER, std::string(name) + " is memory of another device");
     if (k == kPtrDevice) { a.dev = p; return AIWCRF_OK; }
+    if (read_in_place && bytes) {
+        if (const void *dp = mapped_host(p)) { a.dev = dp; return AIWCRF_OK; }
+    }
     cudaError_t e = cudaMallocAsync(&a.owned, bytes ? bytes : 1, s);
     if (e != cudaSuccess) return fail(AIWCRF_E_OOM, std::string("staging ") + name + ": " + cudaGetErrorString(e));
     if (bytes) {
@@ -513,7 +530,8 @@ static int predict_common(const aiwcrf_forest *f, const float *Xq, int64_t Q, in
     InArg aq;
     OutArg os, op, ov;
     if (Q == 0) return AIWCRF_OK;
-    if ((rc = stage_in(aq, Xq, sizeof(float) * (size_t)f->F * (size_t)Q, dev, s, "Xq"))) return rc;
+    // the query features are read once, by the coding kernel: page-locked host memory in place
+    if ((rc = stage_in(aq, Xq, sizeof(float) * (size_t)f->F * (size_t)Q, dev, s, "Xq", true))) return rc;
     if ((rc = stage_out(os, out_sum, sizeof(int64_t) * (size_t)Q, dev, s, "out_sum"))) return rc;
     if ((rc = stage_out(op, out_pred, sizeof(int64_t) * (size_t)Q, dev, s, "out_pred"))) return rc;
     if ((rc = stage_out(ov, out_var, 2 * sizeof(uint64_t) * (size_t)Q, dev, s, "out_var"))) return rc;

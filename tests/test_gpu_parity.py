@@ -167,6 +167,25 @@ def test_host_buffers_and_serialization_roundtrip():
     assert np.array_equal(out, gpu_predict(f_dev, Xq))
 
 
+def test_page_locked_queries_are_read_in_place():
+    """Page-locked host features are read by the device in place (no staging copy): the same
+    predictions as device features, on the unsorted (small) and the sorted (large) walk, with
+    host and device outputs."""
+    wl = synth.scaled_forest_workload()
+    f = gpu_fit(wl, 16, 10, 5)
+    for Q in (1_000, 70_001):
+        Xq = synth.queries(Q, seed=Q)
+        ref = gpu_predict(f, Xq)
+        pinned = torch.from_numpy(Xq).pin_memory()
+        out = np.zeros(Q, np.int64)
+        A.aiwcrf_predict(f, pinned.numpy(), out)                 # page-locked in, host out
+        assert np.array_equal(out, ref)
+        out_d = torch.empty(Q, dtype=torch.int64, device="cuda")
+        A.aiwcrf_predict(f, pinned.numpy(), out_d)               # page-locked in, device out
+        torch.cuda.synchronize()
+        assert np.array_equal(out_d.cpu().numpy(), ref)
+
+
 def test_background_fit_grids_give_the_same_forest():
     # the level kernels' grid only decides which CTA takes which node: fewer CTAs per SM (a
     # background fit) must give the same bytes, on the big-node and the small-node paths
