@@ -16,7 +16,8 @@
  *    synchronises the stream before returning. With device outputs the call is stream-ordered
  *    and the results are valid once the stream reaches that point.
  *  - The caller owns every array it passes. The library owns each aiwcrf_forest until
- *    aiwcrf_forest_free().
+ *    aiwcrf_forest_free(). A host thread that has fitted keeps up to 512 MiB of device scratch
+ *    for its next fits (released when the thread exits).
  *  - cuda_stream is a cudaStream_t (NULL = the legacy default stream). The device is the
  *    current CUDA device of the calling thread.
  *  - Matrices are column-major float32: element (feature f, row r) of an F x N matrix is at

@@ -2463,15 +2463,64 @@ struct DevBuf {                // stream-ordered scratch allocation
     size_t bytes = 0;
 };
 
+// A fit's scratch. Requests up to kArenaPiece bytes are carved from the calling host thread's
+// arena: device memory kept between fits and bump-allocated, so that a fit makes a few
+// allocation calls instead of dozens (each a host round trip while the device may be idle).
+// The arena grows, at the start of a later fit, to the largest carved total a fit asked for,
+// up to kArenaCap. Larger requests, and those past the arena, are stream-ordered allocations
+// freed at release. Scratches on one thread nest (last in, first out); release() returns the
+// carved part to the arena and first waits for the stream, so that no later fit on this thread
+// writes memory that queued work still reads.
+constexpr size_t kArenaPiece = (size_t)64 << 20;
+constexpr size_t kArenaCap = (size_t)512 << 20;
+
+struct Arena {
+    void *base = nullptr;
+    size_t cap = 0, used = 0, want = 0;
+    int device = -1;
+    ~Arena() { if (base) cudaFree(base); }
+};
+
+inline Arena &thread_arena()
+{
+    static thread_local Arena a;
+    return a;
+}
+
 class Scratch {
 public:
-    explicit Scratch(cudaStream_t s) : s_(s) {}
+    explicit Scratch(cudaStream_t s) : s_(s)
+    {
+        Arena &a = thread_arena();
+        int dev = -1;
+        if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return; }
+        if (a.used == 0 && (a.device != dev || a.want > a.cap)) {
+            // nothing of this thread's arena is in use: (re)size it on the current device
+            const size_t want = std::min(std::max(a.want, a.cap), kArenaCap);
+            if (a.base) { cudaFreeAsync(a.base, s_); a.base = nullptr; a.cap = 0; }
+            a.device = dev;
+            if (want && cudaMallocAsync(&a.base, want, s_) == cudaSuccess) a.cap = want;
+            else { cudaGetLastError(); a.base = nullptr; a.cap = 0; }
+        }
+        arena_ = a.device == dev ? &a : nullptr;
+        mark_ = arena_ ? arena_->used : 0;
+    }
     ~Scratch() { release(); }
     template <class T>
     T *get(size_t count, int *rc)
     {
-        void *p = nullptr;
         const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+        const size_t up = (bytes + 255) & ~(size_t)255;
+        if (arena_ && up <= kArenaPiece) {
+            carved_ += up;
+            arena_->want = std::max(arena_->want, mark_ + carved_);
+            if (arena_->used + up <= arena_->cap) {
+                void *p = static_cast<unsigned char *>(arena_->base) + arena_->used;
+                arena_->used += up;
+                return static_cast<T *>(p);
+            }
+        }
+        void *p = nullptr;
         cudaError_t e = cudaMallocAsync(&p, bytes, s_);
         if (e != cudaSuccess) {
             *rc = fail(AIWCRF_E_OOM, std::string("device allocation of ") + std::to_string(bytes) +
@@ -2481,6 +2530,7 @@ public:
         bufs_.push_back(p);
         return static_cast<T *>(p);
     }
+    // a buffer no longer needed (carved ones stay until release)
     void drop(void *p)
     {
         for (auto &b : bufs_)
@@ -2491,11 +2541,18 @@ public:
         for (auto b : bufs_)
             if (b) cudaFreeAsync(b, s_);
         bufs_.clear();
+        if (arena_ && arena_->used > mark_) {
+            cudaStreamSynchronize(s_);
+            arena_->used = mark_;
+        }
+        carved_ = 0;
     }
 
 private:
     cudaStream_t s_;
     std::vector<void *> bufs_;
+    Arena *arena_ = nullptr;
+    size_t mark_ = 0, carved_ = 0;
 };
 
 #define AIWCRF_LAUNCH_CHECK(what)                                   \
