@@ -186,6 +186,40 @@ def test_page_locked_queries_are_read_in_place():
         assert np.array_equal(out_d.cpu().numpy(), ref)
 
 
+def test_fit_scratch_reuse_across_sizes_and_threads():
+    """The fit's scratch arena (kept per host thread between fits) never leaks one fit's data
+    into the next: fits of alternating sizes repeat their bytes, and fits on two host threads at
+    once (two arenas, two streams) give the single-thread bytes."""
+    import threading
+    small = synth.small_case(7, 600, 9, card=20)
+    big = synth.scaled_forest_workload()
+    ref_small = gpu_fit(small, 8, 4, 2).serialize()
+    ref_big = gpu_fit(big, 24, 10, 5).serialize()
+    for _ in range(2):
+        assert gpu_fit(small, 8, 4, 2).serialize() == ref_small
+        assert gpu_fit(big, 24, 10, 5).serialize() == ref_big
+    out, errs = {}, []
+
+    def work(name, wl, T, m, mn):
+        try:
+            st = torch.cuda.Stream()
+            with torch.cuda.stream(st):
+                X, y = dev(wl.X), dev(wl.y)
+                blobs = [A.aiwcrf_fit(A.params(T, m, mn), X, y, stream=st).serialize() for _ in range(3)]
+            out[name] = blobs
+        except Exception as e:                                   # reported below
+            errs.append(repr(e))
+
+    th = [threading.Thread(target=work, args=("small", small, 8, 4, 2)),
+          threading.Thread(target=work, args=("big", big, 24, 10, 5))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errs, errs
+    assert out["small"] == [ref_small] * 3 and out["big"] == [ref_big] * 3
+
+
 def test_background_fit_grids_give_the_same_forest():
     # the level kernels' grid only decides which CTA takes which node: fewer CTAs per SM (a
     # background fit) must give the same bytes, on the big-node and the small-node paths
