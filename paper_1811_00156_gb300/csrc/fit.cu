@@ -205,12 +205,10 @@ __global__ void rank_rows_kernel(const uint32_t *__restrict__ Rcol, int64_t N, i
 // ------------------------------------------------------------------------------------------
 // grouping of rows with identical rank records
 // ------------------------------------------------------------------------------------------
+// 32-bit hash of a row's rank record (FNV-style steps, then a final mix)
 template <typename RT>
-__global__ void hash_rows_kernel(const RT *__restrict__ Rr, int64_t N, int F, uint32_t *keys, uint32_t *vals)
+__device__ __forceinline__ uint32_t record_hash(const RT *r, int F)
 {
-    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= N) return;
-    const RT *r = Rr + (size_t)row * (size_t)F;
     uint32_t h = 0x811C9DC5u;
     for (int f = 0; f < F; ++f) {
         h ^= (uint32_t)r[f];
@@ -220,7 +218,15 @@ __global__ void hash_rows_kernel(const RT *__restrict__ Rr, int64_t N, int F, ui
     h ^= h >> 16;
     h *= 0x85EBCA6Bu;
     h ^= h >> 13;
-    keys[row] = h;
+    return h;
+}
+
+template <typename RT>
+__global__ void hash_rows_kernel(const RT *__restrict__ Rr, int64_t N, int F, uint32_t *keys, uint32_t *vals)
+{
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= N) return;
+    keys[row] = record_hash(Rr + (size_t)row * (size_t)F, F);
     vals[row] = (uint32_t)row;
 }
 
@@ -270,6 +276,84 @@ __global__ void group_order_kernel(const uint32_t *__restrict__ rows, const uint
     y_g[k] = yr;
     grp_of[k] = g;
     // per row: y and its group, one 16-byte record (read by boot_groups_kernel's draws)
+    if (rowrec) rowrec[row] = make_uint4((uint32_t)(uint64_t)yr, (uint32_t)((uint64_t)yr >> 32), g, 0u);
+}
+
+// Grouping through a hash table instead of a sort (the fit's usual path). Open addressing over
+// a power-of-two table of 64-bit slots {hash, first row}: a row claims an empty slot with a
+// compare-and-swap or joins the slot whose row has the same record (compared in full when the
+// hashes agree), probing linearly, at most table-size probes. Groups are then numbered in slot
+// order; which row claims a slot, and so the numbering and the rows' order within a group, can
+// differ between runs, which changes no sum and no forest (entries are summed per group, and
+// splits and partitions do not depend on the entries' order).
+constexpr unsigned long long kSlotEmpty = ~0ull;
+
+template <typename RT>
+__global__ void group_insert_kernel(const RT *__restrict__ Rr, int64_t N, int F, unsigned long long *table,
+                                    uint32_t mask, uint32_t *__restrict__ slot_of_row, uint32_t *err)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    const uint32_t h = record_hash(Rr + (size_t)r * (size_t)F, F);
+    const unsigned long long mine = ((unsigned long long)h << 32) | (uint32_t)r;
+    uint32_t i = h & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        unsigned long long cur = table[i];
+        if (cur == kSlotEmpty) {
+            cur = atomicCAS(&table[i], kSlotEmpty, mine);
+            if (cur == kSlotEmpty) { slot_of_row[r] = i; return; }
+        }
+        if ((uint32_t)(cur >> 32) == h && same_record(Rr, F, (uint32_t)cur, (uint32_t)r)) {
+            slot_of_row[r] = i;
+            return;
+        }
+        i = (i + 1u) & mask;
+    }
+    atomicOr(err, kErrCapacity);                       // a full table (it holds at least 2N slots)
+    slot_of_row[r] = 0u;
+}
+
+__global__ void slot_flags_kernel(const unsigned long long *__restrict__ table, int64_t n, uint32_t *__restrict__ flags)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flags[i] = table[i] != kSlotEmpty ? 1u : 0u;
+}
+
+// the row's group (its slot's rank among the occupied slots), the groups' row counts, and G
+__global__ void row_group_kernel(const uint32_t *__restrict__ slot_of_row, const uint32_t *__restrict__ slot_excl,
+                                 int64_t n_slots, int64_t N, uint32_t *__restrict__ group_of_row, uint32_t *cnt,
+                                 uint32_t *n_groups)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r == 0) *n_groups = slot_excl[n_slots];
+    if (r >= N) return;
+    const uint32_t g = slot_excl[slot_of_row[r]];
+    group_of_row[r] = g;
+    atomicAdd(&cnt[g], 1u);
+}
+
+// rows in group order: each row takes the next place of its group
+__global__ void group_scatter_kernel(const uint32_t *__restrict__ group_of_row, const uint32_t *__restrict__ grp_off,
+                                     int64_t N, uint32_t *fill, uint32_t *__restrict__ grp_rows)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    const uint32_t g = group_of_row[r];
+    grp_rows[grp_off[g] + atomicAdd(&fill[g], 1u)] = (uint32_t)r;
+}
+
+// as group_order_kernel, with each row's group given
+__global__ void group_order_rows_kernel(const uint32_t *__restrict__ rows, const uint32_t *__restrict__ group_of_row,
+                                        const int64_t *__restrict__ y, int64_t N, int64_t *__restrict__ y_g,
+                                        uint32_t *__restrict__ grp_of, uint4 *__restrict__ rowrec)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const uint32_t row = rows[k];
+    const int64_t yr = y[row];
+    const uint32_t g = group_of_row[row];
+    y_g[k] = yr;
+    grp_of[k] = g;
     if (rowrec) rowrec[row] = make_uint4((uint32_t)(uint64_t)yr, (uint32_t)((uint64_t)yr >> 32), g, 0u);
 }
 
@@ -479,6 +563,9 @@ __global__ void __launch_bounds__(kBootThreads) bootstrap_kernel(BootArgs a)
 constexpr int kBootGThreads = 512;      // 40 registers: three CTAs per SM
 constexpr int kBootGIlp = 4;            // draws whose record loads a thread issues together
 constexpr int kBootGroupsSmemMax = 96 * 1024;      // at least two CTAs per SM
+#ifndef AIWCRF_GROUP_HASH
+#define AIWCRF_GROUP_HASH 1            // 0: the fit groups rows through a radix sort of their hashes
+#endif
 #ifndef AIWCRF_BOOT_GROUPS
 #define AIWCRF_BOOT_GROUPS 1           // 0: always the per-row counters of bootstrap_kernel
 #endif
@@ -2816,36 +2903,78 @@ int fit_batch(const aiwcrf_fit_params &p, const float *dX, const int64_t *dy, in
     int64_t *d_y_g = nullptr;
     uint32_t *d_grp_of = nullptr;
     uint4 *d_rowrec = nullptr;
+    const uint32_t *grp_rows = vA;            // rows in group order
     {
         const unsigned rb = (unsigned)((N + 255) / 256);
         prof_begin(s, kProfRank);
-        AIWCRF_BY_RANK(rank_bytes, rank_rows_kernel<RT><<<rb, 256, 0, s>>>(d_R, N, F, (RT *)d_Rr);
-                                   hash_rows_kernel<RT><<<rb, 256, 0, s>>>((const RT *)d_Rr, N, F, kA, vA))
-        count_launches(1);
-        AIWCRF_LAUNCH_CHECK("rank_rows / hash_rows");
-        if ((rc = radix_sort_segments(kA, vA, kB, vB, N, 1, N, hist, s)) != AIWCRF_OK) return rc;
-        // group starts (flags in kB), their exclusive scan (in vB), offsets
-        AIWCRF_BY_RANK(rank_bytes, group_flags_kernel<RT><<<rb, 256, 0, s>>>((const RT *)d_Rr, N, F, kA, vA, kB))
-        const int gblocks = (int)((N + kFlagTile - 1) / kFlagTile);
-        flag_scan_reduce_kernel<<<gblocks, kScanThreads, 0, s>>>(kB, N, hist);
-        scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(hist, gblocks);
-        flag_scan_write_kernel<<<gblocks, kScanThreads, 0, s>>>(kB, N, hist, gblocks, vB);
-        group_offsets_kernel<<<rb, 256, 0, s>>>(kB, vB, N, grp_off, d_counters + 2);
-        count_launches(4);
-        AIWCRF_LAUNCH_CHECK("grouping kernels");
+        AIWCRF_BY_RANK(rank_bytes, rank_rows_kernel<RT><<<rb, 256, 0, s>>>(d_R, N, F, (RT *)d_Rr))
+        AIWCRF_LAUNCH_CHECK("rank_rows_kernel");
+        uint32_t *group_of_row = nullptr;
+        if (AIWCRF_GROUP_HASH) {
+            // the hash table (at least 2N slots), groups numbered in slot order, then a counting
+            // sort of the rows by group
+            int64_t n_slots = 1024;
+            while (n_slots < 2 * N) n_slots *= 2;
+            unsigned long long *table = sc.get<unsigned long long>((size_t)n_slots, &rc); if (rc) return rc;
+            uint32_t *slot_of_row = sc.get<uint32_t>((size_t)N, &rc); if (rc) return rc;
+            uint32_t *slot_flags = sc.get<uint32_t>((size_t)n_slots + 1, &rc); if (rc) return rc;
+            uint32_t *slot_excl = sc.get<uint32_t>((size_t)n_slots + 1, &rc); if (rc) return rc;
+            uint32_t *cnt = sc.get<uint32_t>((size_t)N + 1, &rc); if (rc) return rc;
+            uint32_t *fill = sc.get<uint32_t>((size_t)N, &rc); if (rc) return rc;
+            uint32_t *rows_g = sc.get<uint32_t>((size_t)N, &rc); if (rc) return rc;
+            uint32_t *sblock = sc.get<uint32_t>((size_t)((std::max<int64_t>(n_slots, N) + kFlagTile - 1) / kFlagTile) + 2, &rc);
+            if (rc) return rc;
+            group_of_row = sc.get<uint32_t>((size_t)N, &rc); if (rc) return rc;
+            AIWCRF_CUDA(cudaMemsetAsync(table, 0xFF, sizeof(unsigned long long) * (size_t)n_slots, s));
+            AIWCRF_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * ((size_t)N + 1), s));
+            AIWCRF_CUDA(cudaMemsetAsync(fill, 0, sizeof(uint32_t) * (size_t)N, s));
+            AIWCRF_BY_RANK(rank_bytes, group_insert_kernel<RT><<<rb, 256, 0, s>>>((const RT *)d_Rr, N, F, table,
+                                                                                 (uint32_t)(n_slots - 1), slot_of_row, d_err))
+            const unsigned sb = (unsigned)((n_slots + 255) / 256);
+            slot_flags_kernel<<<sb, 256, 0, s>>>(table, n_slots, slot_flags);
+            const int sblocks = (int)((n_slots + kFlagTile - 1) / kFlagTile);
+            flag_scan_reduce_kernel<<<sblocks, kScanThreads, 0, s>>>(slot_flags, n_slots, sblock);
+            scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(sblock, sblocks);
+            flag_scan_write_kernel<<<sblocks, kScanThreads, 0, s>>>(slot_flags, n_slots, sblock, sblocks, slot_excl);
+            row_group_kernel<<<rb, 256, 0, s>>>(slot_of_row, slot_excl, n_slots, N, group_of_row, cnt, d_counters + 2);
+            // group offsets: the exclusive scan of the counts (past the last group it stays N)
+            const int gblocks = (int)((N + kFlagTile - 1) / kFlagTile);
+            flag_scan_reduce_kernel<<<gblocks, kScanThreads, 0, s>>>(cnt, N, sblock);
+            scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(sblock, gblocks);
+            flag_scan_write_kernel<<<gblocks, kScanThreads, 0, s>>>(cnt, N, sblock, gblocks, grp_off);
+            group_scatter_kernel<<<rb, 256, 0, s>>>(group_of_row, grp_off, N, fill, rows_g);
+            count_launches(9);
+            AIWCRF_LAUNCH_CHECK("grouping kernels");
+            grp_rows = rows_g;
+        } else {
+            AIWCRF_BY_RANK(rank_bytes, hash_rows_kernel<RT><<<rb, 256, 0, s>>>((const RT *)d_Rr, N, F, kA, vA))
+            AIWCRF_LAUNCH_CHECK("hash_rows_kernel");
+            if ((rc = radix_sort_segments(kA, vA, kB, vB, N, 1, N, hist, s)) != AIWCRF_OK) return rc;
+            // group starts (flags in kB), their exclusive scan (in vB), offsets
+            AIWCRF_BY_RANK(rank_bytes, group_flags_kernel<RT><<<rb, 256, 0, s>>>((const RT *)d_Rr, N, F, kA, vA, kB))
+            const int gblocks = (int)((N + kFlagTile - 1) / kFlagTile);
+            flag_scan_reduce_kernel<<<gblocks, kScanThreads, 0, s>>>(kB, N, hist);
+            scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(hist, gblocks);
+            flag_scan_write_kernel<<<gblocks, kScanThreads, 0, s>>>(kB, N, hist, gblocks, vB);
+            group_offsets_kernel<<<rb, 256, 0, s>>>(kB, vB, N, grp_off, d_counters + 2);
+            count_launches(4);
+            AIWCRF_LAUNCH_CHECK("grouping kernels");
+        }
         prof_end(s, kProfRank);
         // y in group order, every position's group and every row's {y, group} record (for the
         // bootstrap), enqueued before the group count is read
         d_y_g = sc.get<int64_t>((size_t)N, &rc); if (rc) return rc;
         d_grp_of = sc.get<uint32_t>((size_t)N, &rc); if (rc) return rc;
         if (AIWCRF_BOOT_GROUPS && p.bootstrap) { d_rowrec = sc.get<uint4>((size_t)N, &rc); if (rc) return rc; }
-        group_order_kernel<<<rb, 256, 0, s>>>(vA, kB, vB, dy, N, d_y_g, d_grp_of, d_rowrec);
+        if (group_of_row)
+            group_order_rows_kernel<<<rb, 256, 0, s>>>(grp_rows, group_of_row, dy, N, d_y_g, d_grp_of, d_rowrec);
+        else
+            group_order_kernel<<<rb, 256, 0, s>>>(vA, kB, vB, dy, N, d_y_g, d_grp_of, d_rowrec);
         AIWCRF_LAUNCH_CHECK("group_order_kernel");
         HostReads hr;
         hr.add(&n_groups, d_counters + 2, sizeof(uint32_t));
         if ((rc = hr.run(s)) != AIWCRF_OK) return rc;
     }
-    const uint32_t *grp_rows = vA;            // rows in group order
     // the groups' representative rows in every column's order
     uint32_t *d_ordG = nullptr;
     if (use_lists) {
